@@ -1,0 +1,471 @@
+/*
+ * qs_oracle.c -- plain, slow FP64 CPU oracle for the QScatter beam
+ * phase-space integration (arXiv 2308.09348).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library: every quantity below is computed here,
+ * from the paper's equations and the readings listed with each function.
+ *
+ * Style: one sample at a time, in the paper's order, double precision, libm,
+ * Neumaier-compensated sums.  No blocking, fusion or reordering.
+ *
+ * Units: lengths in micrometres, times in femtoseconds, energies as the
+ * Lorentz factor gamma.  Constants are CODATA 2018.
+ *
+ * Parity status per function (the pins live in tests/test_oracle_pins.py):
+ *   qso_constants        pinned (paper's omega0 at 0.8 um; RK4 of the LL
+ *                        equation of motion fixes the c_RR chain)
+ *   qso_gaunt            pinned (exact quantum-synchrotron power, Bessel
+ *                        quadrature; g(0)=1; chi^-4/3 tail)
+ *   qso_h2               pinned (exact second moment, Bessel quadrature)
+ *   qso_qfp_rates        pinned (absolute first/second emission moments)
+ *   qso_qfp_integrate    pinned (classical limit == Eq. 3; variance
+ *                        transport closed form; library ODE solve)
+ *   qso_eval / qso_scatter  pinned (Table 1 / Table 2 closed forms,
+ *                        zero intensity, weight conservation, symmetries)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#include <stdlib.h>
+
+/* ---- physical constants (CODATA 2018), lengths in micrometres ---------- */
+#define QSO_C_UM_PER_FS   0.299792458          /* speed of light            */
+#define QSO_RE_UM         2.8179403262e-9      /* classical electron radius */
+#define QSO_LBARC_UM      3.8615926796e-7      /* reduced Compton wavelength*/
+#define QSO_PI            3.14159265358979323846
+
+/* Gaussian envelope: the phase window is [-QSO_GWIN*Phi, +QSO_GWIN*Phi]. */
+#define QSO_GWIN 2.5
+
+/* ------------------------------------------------------------------------
+ * Descriptors (the oracle's own; the CUDA library has separate ones).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double lambda_um;      /* laser central wavelength                     */
+    double a0;             /* peak normalised vector potential             */
+    double w0_um;          /* spot size W0 (Eq. 2)                         */
+    double tau_fs;         /* intensity FWHM duration                      */
+    double dx_um, dy_um;   /* transverse offset of the laser axis          */
+    double delay_fs;       /* time at which the pulse peak passes z = 0    */
+    double div_prefactor;  /* kappa multiplying Eq. 8                      */
+    int32_t envelope;      /* 0 = Gaussian, 1 = sin^2 (field envelope)     */
+    int32_t model;         /* 0 = classical LL (Eq. 3), 1 = quantum FP     */
+    int32_t n_phase;       /* phase steps of the quantum model             */
+    int32_t pad;
+} qso_laser;
+
+typedef struct {
+    double gamma_mean, rel_spread;   /* Gaussian energy: gamma_mean(1+s*xi3) */
+    double gamma_lo, gamma_hi;       /* flat energy: lo + (hi-lo)*xi3        */
+    double sigma_x_um, sigma_y_um, sigma_z_um;
+    double div_rad;                  /* rms angle per transverse axis        */
+    double dx_um, dy_um;             /* beam centroid offset                 */
+    int32_t flat_energy, pad;
+} qso_beam;
+
+typedef struct {
+    int32_t n_bins, log_spaced;  double lo, hi;      /* energy spectrum      */
+    int32_t n_tx, n_ty;          double theta_max;   /* divergence map       */
+    int32_t n_aeff, pad;         double aeff_max;    /* a_eff histogram      */
+} qso_bins;
+
+typedef struct {
+    double W;          /* total weight                                      */
+    double mean;       /* <gamma_f>                                         */
+    double spread;     /* rms energy spread (law of total variance)         */
+    double rel_spread; /* spread / mean                                     */
+    double div_x, div_y, div;  /* rms final angles                          */
+    double mean_aeff;  /* <a_eff>                                           */
+    double under, over;/* spectrum weight below lo / at or above hi         */
+    double map_out;    /* weight outside the divergence map                 */
+    double mean_gamma0;/* <gamma_0>                                         */
+} qso_moments;
+
+/* Per-sample record written by qso_eval. */
+typedef struct {
+    double gamma0, aeff, mu, V, theta_e, theta_x, theta_y, gamma_out;
+    int32_t bin, ix, iy, abin;
+} qso_sample;
+
+/* ---- Neumaier compensated sum ------------------------------------------- */
+typedef struct { double s, c; } qso_sum;
+static void qso_add(qso_sum* a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else                       a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double qso_val(const qso_sum* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------
+ * Derived laser constants.
+ *   k = 2 pi / lambda,  omega0 = c k,  z_R = pi W0^2 / lambda   (Eq. 2)
+ *   R_c = r_e omega0 / c = r_e k
+ *   a_S = m c^2/(hbar omega0) = 1/(k lambdabar_c)              (Eq. 6)
+ *   Phi = omega0 tau  (intensity FWHM in laser phase)
+ *   c_RR = (2/3) R_c * integral of G(phi)^2 dphi  (Eq. 3, head-on, linear
+ *          polarisation, cycle-averaged a^2 = A^2/2; the integral is the
+ *          analytic one over the whole envelope)
+ * out[0..9] = k, omega0, zR, Rc, aS, Phi, PhiT, window_lo, window_hi, cRR
+ * ------------------------------------------------------------------------ */
+static double qso_sin2_period(double Phi) {
+    /* sin^2 field envelope: intensity sin^4(pi phi/PhiT); its FWHM is
+       PhiT*(1 - (2/pi) asin(2^-1/4)).  Return PhiT for a given FWHM Phi. */
+    return Phi / (1.0 - (2.0 / QSO_PI) * asin(pow(2.0, -0.25)));
+}
+
+void qso_constants(const qso_laser* L, double* out) {
+    double k = 2.0 * QSO_PI / L->lambda_um;
+    double omega0 = QSO_C_UM_PER_FS * k;
+    double zR = QSO_PI * L->w0_um * L->w0_um / L->lambda_um;
+    double Rc = QSO_RE_UM * k;
+    double aS = 1.0 / (k * QSO_LBARC_UM);
+    double Phi = omega0 * L->tau_fs;
+    double PhiT = qso_sin2_period(Phi);
+    double lo, hi, intG2;
+    if (L->envelope == 0) {
+        lo = -QSO_GWIN * Phi; hi = QSO_GWIN * Phi;
+        /* G = exp(-2 ln2 (phi/Phi)^2); G^2 = exp(-4 ln2 phi^2/Phi^2) */
+        intG2 = Phi * sqrt(QSO_PI / (4.0 * log(2.0)));
+    } else {
+        lo = 0.0; hi = PhiT;
+        intG2 = 3.0 * PhiT / 8.0;   /* integral of sin^4 over one period */
+    }
+    out[0] = k; out[1] = omega0; out[2] = zR; out[3] = Rc; out[4] = aS;
+    out[5] = Phi; out[6] = PhiT; out[7] = lo; out[8] = hi;
+    out[9] = (2.0 / 3.0) * Rc * intG2;
+}
+
+/* Envelope G at phase phi (relative to the pulse-peak crossing for the
+   Gaussian, to the pulse start for sin^2). */
+static double qso_envelope(const qso_laser* L, const double* c, double phi) {
+    if (L->envelope == 0) {
+        double r = phi / c[5];
+        return exp(-2.0 * log(2.0) * r * r);
+    }
+    if (phi < 0.0 || phi > c[6]) return 0.0;
+    double s = sin(QSO_PI * phi / c[6]);
+    return s * s;
+}
+
+/* Midpoint phase grid: N nodes on the window, spacing h. */
+void qso_phase_grid(const qso_laser* L, double* phi, double* G, double* h_out) {
+    double c[10];
+    qso_constants(L, c);
+    int N = L->n_phase;
+    double h = (c[8] - c[7]) / (double)N;
+    for (int j = 0; j < N; ++j) {
+        double p = c[7] + ((double)j + 0.5) * h;
+        if (phi) phi[j] = p;
+        if (G) G[j] = qso_envelope(L, c, p);
+    }
+    if (h_out) *h_out = h;
+}
+
+/* ------------------------------------------------------------------------
+ * Gaunt factor g(chi) (Eq. 6): ratio of the quantum to the classical mean
+ * emitted power.  The paper names it but prints no formula; this is the
+ * widely used closed-form fit
+ *     g = [1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2]^(-2/3),
+ * with g(0) = 1 and g ~ chi^(-4/3) at large chi.  gp = dg/dchi.
+ * ------------------------------------------------------------------------ */
+void qso_gaunt(double chi, double* g, double* gp) {
+    double B = 1.0 + 4.8 * (1.0 + chi) * log(1.0 + 1.7 * chi) + 2.44 * chi * chi;
+    double dB = 4.8 * log(1.0 + 1.7 * chi) + 4.8 * (1.0 + chi) * 1.7 / (1.0 + 1.7 * chi)
+              + 2.0 * 2.44 * chi;
+    double gv = pow(B, -2.0 / 3.0);
+    if (g) *g = gv;
+    if (gp) *gp = (-2.0 / 3.0) * gv / B * dB;
+}
+
+/* ------------------------------------------------------------------------
+ * Second-moment factor h(chi): ratio of the quantum to the classical
+ * second moment of the emitted photon energy per unit time.  Classical
+ * reference: (55/(16 sqrt 3)) gamma chi P_cl (storage-ring quantum
+ * excitation with critical energy (3/2) gamma chi m c^2).  Fit (max 1.5%
+ * off the exact Bessel-function moment for 1e-3 <= chi <= 20):
+ *     h = [1 + (1 + 4.1 chi) ln(1 + 12.93 chi) + 4.75 chi^2]^(-7/6),
+ * h(0) = 1, h ~ chi^(-7/3) at large chi.
+ * ------------------------------------------------------------------------ */
+double qso_h2(double chi) {
+    double B = 1.0 + (1.0 + 4.1 * chi) * log(1.0 + 12.93 * chi) + 4.75 * chi * chi;
+    return pow(B, -7.0 / 6.0);
+}
+
+/* ------------------------------------------------------------------------
+ * Fokker-Planck moment rates per unit laser phase (Eq. 6 and the
+ * Fokker-Planck regime the paper names), for an electron of mean energy mu
+ * in a cycle-averaged field of envelope amplitude A (linear polarisation:
+ * rms field A/sqrt 2, so chi = 2 mu (A/sqrt2)/a_S).  With K = (2/3) R_c A^2:
+ *   D1  = d<gamma>/dphi           = -K mu^2 g(chi)
+ *   dD1 = dD1/dgamma              = -K mu (2 g + chi g'(chi))
+ *   D2  = d<dgamma^2>/dphi (diff) =  (55/(16 sqrt 3)) K mu^3 chi h(chi)
+ * aS_scale multiplies a_S (1 = physical; huge = classical limit).
+ * out[0..3] = D1, dD1, D2, chi
+ * ------------------------------------------------------------------------ */
+static void qso_rates_c(const double* c, double mu, double A, double aS_scale, double* out) {
+    double Rc = c[3], aS = c[4] * aS_scale;
+    double chi = 2.0 * mu * (A / sqrt(2.0)) / aS;
+    double g, gp;
+    qso_gaunt(chi, &g, &gp);
+    double h2 = qso_h2(chi);
+    double K = (2.0 / 3.0) * Rc * A * A;
+    out[0] = -K * mu * mu * g;
+    out[1] = -K * mu * (2.0 * g + chi * gp);
+    out[2] = (55.0 / (16.0 * sqrt(3.0))) * K * mu * mu * mu * chi * h2;
+    out[3] = chi;
+}
+
+void qso_qfp_rates(const qso_laser* L, double mu, double A, double aS_scale, double* out) {
+    double c[10];
+    qso_constants(L, c);
+    qso_rates_c(c, mu, A, aS_scale, out);
+}
+
+/* ------------------------------------------------------------------------
+ * Quantum-corrected phase integration of one electron of initial energy
+ * gamma0 seeing a plane-wave pulse of peak amplitude aeff (Eq. 6, Fokker-
+ * Planck mean/variance closure), second order in the step h.
+ *
+ * State: du = 1/mu - 1/gamma0 (so mu = gamma0/(1 + gamma0 du), exactly
+ * gamma0 when nothing is radiated) and the variance V.  Cell j has its
+ * midpoint at phi_j, where the envelope and the rates are evaluated:
+ *   K_j   = (2/3) R_c A_j^2,  A_j = aeff G(phi_j)
+ *   du^   = du_j + (h/2) K_j g_{j-1}        (state at the cell midpoint,
+ *           g_{-1} = 1: the previous cell's Gaunt factor predicts it)
+ *   mu^   = gamma0/(1 + gamma0 du^),  rates D1, dD1, D2 at (mu^, A_j)
+ *   du_{j+1} = du_j + h K_j g_j             (= du_j - h D1/mu^2)
+ *   lambda = 2 dD1,  r = lambda V_j + D2
+ *   V_{j+1}  = V_j + h r + (h^2/2) lambda r (frozen-rate Taylor step)
+ * aS_scale multiplies a_S; d2_scale multiplies D2 (0 = no diffusion).
+ * ------------------------------------------------------------------------ */
+void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0,
+                       double aS_scale, double d2_scale, double* mu_out, double* V_out) {
+    int N = L->n_phase;
+    double c[10];
+    qso_constants(L, c);
+    double h = (c[8] - c[7]) / (double)N;
+    double du = 0.0, V = V0, g_prev = 1.0;
+    for (int j = 0; j < N; ++j) {
+        double phi = c[7] + ((double)j + 0.5) * h;   /* midpoint of cell j */
+        double A = aeff * qso_envelope(L, c, phi);
+        double K = (2.0 / 3.0) * c[3] * A * A;
+        double du_mid = du + 0.5 * h * K * g_prev;
+        double mu = gamma0 / (1.0 + gamma0 * du_mid);
+        double r[4];
+        qso_rates_c(c, mu, A, aS_scale, r);
+        double g = -r[0] / (K * mu * mu);          /* Gaunt factor at chi_j */
+        if (!(K > 0.0)) g = 1.0;
+        double lam = 2.0 * r[1];
+        double rv = lam * V + d2_scale * r[2];
+        du += h * K * g;
+        V += h * rv + 0.5 * h * h * lam * rv;
+        g_prev = g;
+    }
+    *mu_out = gamma0 / (1.0 + gamma0 * du);
+    *V_out = V;
+}
+
+/* ------------------------------------------------------------------------
+ * One beam sample, steps in the paper's order.
+ * xi[0..7]: standard variates for x, y, z, gamma0 (uniform [0,1) if the
+ * energy is flat), theta_x, theta_y, angular noise, energy noise.
+ *
+ * Geometry (Eq. 1 factor 2, Table 1 z_pm = Delta_par +- L/4): the laser
+ * moves along +z, focus at the origin, its peak passes z = 0 at t = delay.
+ * The electron sits at (x, y, z) at t = 0 and moves with velocity
+ * c(theta_x, theta_y, -1).  It meets the pulse peak at
+ *   c t* = (z + c delay)/2,   z* = (z - c delay)/2,
+ * transverse position x + theta_x c t*, y + theta_y c t*.
+ * ------------------------------------------------------------------------ */
+static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+                            const double* xi, qso_sample* s) {
+    double c[10];
+    qso_constants(L, c);
+    double zR = c[2], aS = c[4], cRR = c[9];
+    (void)aS;
+
+    /* decode (reparameterised sample) */
+    double x = B->dx_um + B->sigma_x_um * xi[0];
+    double y = B->dy_um + B->sigma_y_um * xi[1];
+    double z = B->sigma_z_um * xi[2];
+    double gamma0;
+    if (B->flat_energy) gamma0 = B->gamma_lo + (B->gamma_hi - B->gamma_lo) * xi[3];
+    else                gamma0 = B->gamma_mean * (1.0 + B->rel_spread * xi[3]);
+    if (gamma0 < 1.0) gamma0 = 1.0;     /* unphysical tail clamped to rest */
+    double thx = B->div_rad * xi[4];
+    double thy = B->div_rad * xi[5];
+
+    /* collision geometry */
+    double ct = 0.5 * (z + QSO_C_UM_PER_FS * L->delay_fs);
+    double zs = 0.5 * (z - QSO_C_UM_PER_FS * L->delay_fs);
+    double xs = x + thx * ct - L->dx_um;
+    double ys = y + thy * ct - L->dy_um;
+    double rho2 = xs * xs + ys * ys;
+
+    /* local Gaussian focus, Eq. 2 */
+    double q = 1.0 + (zs / zR) * (zs / zR);
+    double aeff = L->a0 / sqrt(q) * exp(-rho2 / (L->w0_um * L->w0_um * q));
+
+    double mu, V;
+    if (L->model == 0) {
+        /* classical LL closed form, Eq. 3 with a0 -> a_eff */
+        mu = gamma0 / (1.0 + cRR * gamma0 * aeff * aeff);
+        V = 0.0;
+    } else {
+        qso_qfp_integrate(L, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+    }
+
+    /* final divergence, Eq. 8 with prefactor kappa; the broadening acts
+       along the polarisation axis x */
+    double theta_e = 0.0;
+    if (L->model != 0 && V > 0.0)
+        theta_e = L->div_prefactor * sqrt(2.0 / QSO_PI) * aeff * sqrt(V) / (mu * mu);
+    double tx = thx + theta_e * xi[6];
+    double ty = thy;
+
+    /* realised final energy: mean plus Gaussian spread of variance V */
+    double gout = mu;
+    if (L->model != 0) gout = mu + sqrt(V > 0.0 ? V : 0.0) * xi[7];
+
+    s->gamma0 = gamma0; s->aeff = aeff; s->mu = mu; s->V = V;
+    s->theta_e = theta_e; s->theta_x = tx; s->theta_y = ty; s->gamma_out = gout;
+
+    /* bins: half-open [lo + b w, lo + (b+1) w); -1 = under, n = over */
+    s->bin = -1; s->ix = -1; s->iy = -1; s->abin = -1;
+    if (bins) {
+        int n = bins->n_bins;
+        if (n > 0) {
+            double t;
+            if (!bins->log_spaced) {
+                double inv_w = (double)n / (bins->hi - bins->lo);
+                t = (gout - bins->lo) * inv_w;
+            } else {
+                double sc = (double)n / log(bins->hi / bins->lo);
+                t = (gout > 0.0) ? log(gout / bins->lo) * sc : -1.0;
+            }
+            if (!(t >= 0.0)) s->bin = -1;
+            else if (t >= (double)n) s->bin = n;
+            else s->bin = (int32_t)floor(t);
+        }
+        if (bins->n_tx > 0 && bins->n_ty > 0) {
+            double tm = bins->theta_max;
+            double sx = (double)bins->n_tx / (2.0 * tm);
+            double sy = (double)bins->n_ty / (2.0 * tm);
+            double fx = (tx + tm) * sx, fy = (ty + tm) * sy;
+            if (fx >= 0.0 && fx < (double)bins->n_tx && fy >= 0.0 && fy < (double)bins->n_ty) {
+                s->ix = (int32_t)floor(fx);
+                s->iy = (int32_t)floor(fy);
+            }
+        }
+        if (bins->n_aeff > 0) {
+            double fa = aeff * ((double)bins->n_aeff / bins->aeff_max);
+            if (fa >= 0.0 && fa < (double)bins->n_aeff) s->abin = (int32_t)floor(fa);
+            else s->abin = bins->n_aeff;
+        }
+    }
+}
+
+/* Per-sample evaluation of n samples; xi[k] points to n doubles (NULL = 0). */
+void qso_eval(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+              int64_t n, const double* const* xi, qso_sample* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        qso_sample_eval(L, B, bins, v, &out[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Whole-beam integration: weighted histograms (Eq. 4 done as a weighted
+ * histogram of the per-sample final energies; Eq. 1 as the a_eff
+ * histogram) and moments.  Spectrum entries are bin masses (sum of weights),
+ * not densities.  Moments follow their definitions directly:
+ *   mean   = sum w mu / W
+ *   spread = sqrt( sum w (mu - mean)^2 / W + sum w V / W )
+ *   div_x  = sqrt( sum w (theta_x0^2 + theta_e^2) / W ), div_y likewise
+ *            without theta_e, div = sqrt(div_x^2 + div_y^2)
+ * w == NULL means unit weights.  Arrays may be NULL when disabled.
+ * ------------------------------------------------------------------------ */
+int qso_scatter(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+                int64_t n, const double* const* xi, const double* w,
+                double* spectrum, double* divmap, double* aeff_hist, qso_moments* m) {
+    int nb = bins->n_bins, ntx = bins->n_tx, nty = bins->n_ty, na = bins->n_aeff;
+    /* compensated accumulators for every output */
+    int64_t nmap = (ntx > 0 && nty > 0) ? (int64_t)ntx * nty : 0;
+    qso_sum* spec = (qso_sum*)calloc((size_t)(nb > 0 ? nb : 0) + 1, sizeof(qso_sum));
+    qso_sum* map = (qso_sum*)calloc((size_t)nmap + 1, sizeof(qso_sum));
+    qso_sum* ah = (qso_sum*)calloc((size_t)(na > 0 ? na : 0) + 1, sizeof(qso_sum));
+    if (!spec || !map || !ah) { free(spec); free(map); free(ah); return 1; }
+
+    qso_sum W = {0, 0}, Smu = {0, 0}, SV = {0, 0}, Sa = {0, 0}, Sg0 = {0, 0};
+    qso_sum Stx = {0, 0}, Sty = {0, 0}, under = {0, 0}, over = {0, 0}, mapout = {0, 0};
+
+    /* first pass: per-sample evaluation, histograms, first moments */
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        qso_sample s;
+        qso_sample_eval(L, B, bins, v, &s);
+        double wi = w ? w[i] : 1.0;
+        qso_add(&W, wi);
+        qso_add(&Smu, wi * s.mu);
+        qso_add(&SV, wi * s.V);
+        qso_add(&Sa, wi * s.aeff);
+        qso_add(&Sg0, wi * s.gamma0);
+        double thx0 = B->div_rad * v[4], thy0 = B->div_rad * v[5];
+        qso_add(&Stx, wi * (thx0 * thx0 + s.theta_e * s.theta_e));
+        qso_add(&Sty, wi * (thy0 * thy0));
+        if (nb > 0) {
+            if (s.bin < 0) qso_add(&under, wi);
+            else if (s.bin >= nb) qso_add(&over, wi);
+            else qso_add(&spec[s.bin], wi);
+        }
+        if (ntx > 0 && nty > 0) {
+            if (s.ix >= 0) qso_add(&map[(int64_t)s.iy * ntx + s.ix], wi);
+            else qso_add(&mapout, wi);
+        }
+        if (na > 0) qso_add(&ah[s.abin], wi);
+    }
+    double Wv = qso_val(&W);
+    double mean = Wv > 0 ? qso_val(&Smu) / Wv : 0.0;
+
+    /* second pass: central second moment of the per-sample means */
+    qso_sum S2 = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        qso_sample s;
+        qso_sample_eval(L, B, bins, v, &s);
+        double wi = w ? w[i] : 1.0;
+        double d = s.mu - mean;
+        qso_add(&S2, wi * d * d);
+    }
+
+    if (spectrum) for (int b = 0; b < nb; ++b) spectrum[b] = qso_val(&spec[b]);
+    if (divmap) for (int64_t b = 0; b < nmap; ++b) divmap[b] = qso_val(&map[b]);
+    if (aeff_hist) for (int b = 0; b < na; ++b) aeff_hist[b] = qso_val(&ah[b]);
+    free(spec); free(map); free(ah);
+
+    memset(m, 0, sizeof(*m));
+    m->W = Wv;
+    m->under = qso_val(&under);
+    m->over = qso_val(&over);
+    m->map_out = qso_val(&mapout);
+    if (Wv > 0) {
+        double var = qso_val(&S2) / Wv + qso_val(&SV) / Wv;
+        m->mean = mean;
+        m->spread = sqrt(var > 0 ? var : 0.0);
+        m->rel_spread = m->spread / mean;
+        m->div_x = sqrt(qso_val(&Stx) / Wv);
+        m->div_y = sqrt(qso_val(&Sty) / Wv);
+        m->div = sqrt((qso_val(&Stx) + qso_val(&Sty)) / Wv);
+        m->mean_aeff = qso_val(&Sa) / Wv;
+        m->mean_gamma0 = qso_val(&Sg0) / Wv;
+    }
+    return 0;
+}

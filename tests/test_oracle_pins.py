@@ -1,0 +1,548 @@
+"""Pins of the FP64 oracle to what the paper and mathematics fix.
+
+None of these retypes the oracle's own formula: each compares it with an
+independent route (a brute-force integration of the equation of motion, the
+exact quantum-synchrotron spectrum through scipy's Bessel functions, a library
+ODE solver, the paper's Table 1/2 closed forms, printed values, invariants).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import constants as SC
+from scipy.integrate import quad, solve_ivp
+from scipy.special import i0, kv
+
+import oracle
+from paper_2308_09348_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_values():
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# constants
+# --------------------------------------------------------------------------
+
+def test_omega0_matches_appendix_a():
+    """Appendix A prints omega0 = 2.35e15 s^-1 for lambda = 0.8 um."""
+    pv = paper_values()["omega0_per_s_at_0p8um"]
+    c = oracle.constants(I.Laser(lambda_um=0.8))
+    omega0_per_s = c["omega0"] * 1e15
+    assert abs(omega0_per_s / pv["value"] - 1.0) < pv["rel_tol"]
+
+
+def test_rc_and_schwinger_potential_from_si_constants():
+    """R_c = r_e omega0/c and a_S = m c^2/(hbar omega0) via scipy.constants
+    (the oracle uses CODATA 2018; later CODATA releases move them by ~1e-9)."""
+    lam = 0.8e-6
+    omega0 = 2 * math.pi * SC.c / lam
+    re = SC.physical_constants["classical electron radius"][0]
+    Rc = re * omega0 / SC.c
+    aS = SC.m_e * SC.c ** 2 / (SC.hbar * omega0)
+    c = oracle.constants(I.Laser(lambda_um=0.8))
+    assert abs(c["Rc"] / Rc - 1) < 1e-8
+    assert abs(c["aS"] / aS - 1) < 1e-8
+    # alpha = R_c a_S (r_e = alpha lambdabar_c)
+    assert abs(c["Rc"] * c["aS"] / SC.alpha - 1) < 1e-8
+
+
+def test_envelope_fwhm_and_window():
+    """Gaussian and sin^2 envelopes: intensity FWHM equals omega0 tau."""
+    for env in (I.ENV_GAUSS, I.ENV_SIN2):
+        L = I.Laser(tau_fs=30.0, envelope=env, n_phase=200000)
+        phi, G, h = oracle.phase_grid(L)
+        inten = G ** 2          # G is the field envelope
+        above = phi[inten >= 0.5]
+        c = oracle.constants(L)
+        fwhm = above[-1] - above[0]
+        assert abs(fwhm / c["Phi"] - 1) < 1e-3
+        # midpoint nodes cover the window exactly
+        assert abs(phi[0] - h / 2 - c["win_lo"]) < 1e-9 * c["Phi"]
+        assert abs(phi[-1] + h / 2 - c["win_hi"]) < 1e-9 * c["Phi"]
+        # c_RR uses the analytic integral of G^2; the midpoint sum agrees
+        # (Gaussian: up to the 3e-8 truncation of the window)
+        intG2 = (G ** 2).sum() * h
+        assert abs((2 / 3) * c["Rc"] * intG2 / c["cRR"] - 1) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# classical energy loss (Eq. 3) vs brute force of the LL equation of motion
+# --------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_ll_closed_form_vs_rk4_equation_of_motion():
+    from ll_brute_force import integrate, psi_derivs
+    lam = 0.8
+    Phi = 10 * 2 * math.pi                        # 10-cycle intensity FWHM
+    tau_fs = Phi / (0.299792458 * 2 * math.pi / lam)
+    laser = I.Laser(lambda_um=lam, tau_fs=tau_fs, a0=1.0)
+    c = oracle.constants(laser)
+    assert abs(c["Phi"] / Phi - 1) < 1e-12
+    g0 = np.array([100.0, 500.0, 2000.0] * 3)
+    a0 = np.repeat([1.0, 5.0, 10.0], 3)
+    h0, hf, gf, ux, uz = integrate(g0, a0, Phi, c["Rc"], steps_per_cycle=200)
+    # (1) the brute force reproduces the exact light-front law
+    #     1/h_f = 1/h_0 + (2/3) R_c int psi'^2 dphi  (Di Piazza's solution)
+    I1 = np.array([quad(lambda p: psi_derivs(p, a, Phi)[0] ** 2, -3 * Phi, 3 * Phi,
+                        limit=2000)[0] for a in a0])
+    exact = 1 / (1 / h0 + (2 / 3) * c["Rc"] * I1)
+    assert np.max(np.abs(hf / exact - 1)) < 1e-6
+    # (2) the oracle's cycle-averaged closed form: 1/gamma_f - 1/gamma_0 =
+    #     c_RR a0^2 must equal 2 (1/h_f - 1/h_0) up to the envelope-gradient
+    #     term int G'^2 / int G^2 = 2 ln2 / Phi^2 of the exact integral
+    d_rk4 = 2 * (1 / hf - 1 / h0)
+    d_oracle = c["cRR"] * a0 ** 2
+    eps = 2 * math.log(2) / Phi ** 2
+    assert np.max(np.abs(d_oracle / d_rk4 - 1 / (1 + eps))) < 2e-6
+    # and the oracle's final energy (per-sample path, LL model)
+    for i in range(len(g0)):
+        L = I.Laser(lambda_um=lam, tau_fs=tau_fs, a0=a0[i], model=I.MODEL_LL)
+        B = I.Beam(gamma_mean=g0[i], rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0)
+        s = oracle.evaluate(L, B, None, [np.zeros(1)] * 8)
+        assert abs(s["mu"][0] / gf[i] - 1) < 2e-3
+
+
+# --------------------------------------------------------------------------
+# quantum corrections (Eq. 6) vs the exact quantum-synchrotron spectrum
+# --------------------------------------------------------------------------
+
+def _Ki13(y):
+    return quad(lambda s: kv(1.0 / 3.0, s), y, np.inf, limit=200)[0]
+
+
+def _spectrum_F(xi, chi):
+    """Quantum synchrotron emission spectrum (Baier-Katkov/Ritus), up to the
+    prefactor alpha m c^2 / (sqrt3 pi hbar gamma); xi = photon energy fraction."""
+    y = 2 * xi / (3 * chi * (1 - xi))
+    return (1 - xi + 1 / (1 - xi)) * kv(2.0 / 3.0, y) - _Ki13(y)
+
+
+def _exact_moments(chi):
+    lo, hi = math.log(1e-12), math.log(1 - 1e-15)
+    pts = [p for p in (math.log(min(chi, 0.5) * 0.01), math.log(min(chi, 0.5)), math.log(0.9))
+           if lo < p < hi]
+    m1 = quad(lambda t: math.exp(2 * t) * _spectrum_F(math.exp(t), chi), lo, hi, points=pts,
+              limit=400)[0]
+    m2 = quad(lambda t: math.exp(3 * t) * _spectrum_F(math.exp(t), chi), lo, hi, points=pts,
+              limit=400)[0]
+    return m1, m2
+
+
+CHIS = [0.003, 0.03, 0.3, 1.0, 3.0, 10.0]
+
+
+@pytest.fixture(scope="module")
+def exact_moments():
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        return {chi: _exact_moments(chi) for chi in CHIS}
+
+
+def test_gaunt_fit_vs_exact_power(exact_moments):
+    for chi in CHIS:
+        m1, _ = exact_moments[chi]
+        g_exact = m1 / (math.sqrt(3) * math.pi) / ((2 / 3) * chi ** 2)
+        g, _ = oracle.gaunt(chi)
+        assert abs(g / g_exact - 1) < 0.02, (chi, g, g_exact)
+
+
+def test_gaunt_limits_and_derivative():
+    assert oracle.gaunt(0.0)[0] == 1.0
+    chis = np.logspace(-4, 3, 200)
+    gs = np.array([oracle.gaunt(c)[0] for c in chis])
+    assert np.all(np.diff(gs) < 0)
+    # large-chi tail ~ chi^(-4/3)
+    s = math.log(oracle.gaunt(2e5)[0] / oracle.gaunt(1e5)[0]) / math.log(2)
+    assert abs(s + 4 / 3) < 0.01
+    # analytic derivative vs central difference
+    for chi in (1e-3, 0.1, 1.0, 7.0):
+        hh = chi * 1e-6
+        fd = (oracle.gaunt(chi + hh)[0] - oracle.gaunt(chi - hh)[0]) / (2 * hh)
+        assert abs(oracle.gaunt(chi)[1] / fd - 1) < 1e-6
+
+
+def test_h2_fit_vs_exact_second_moment(exact_moments):
+    assert oracle.h2(0.0) == 1.0
+    for chi in CHIS:
+        _, m2 = exact_moments[chi]
+        h_exact = m2 / (math.sqrt(3) * math.pi) / (
+            (55 / (16 * math.sqrt(3))) * chi * (2 / 3) * chi ** 2)
+        assert abs(oracle.h2(chi) / h_exact - 1) < 0.02, (chi, oracle.h2(chi), h_exact)
+    s = math.log(oracle.h2(2e5) / oracle.h2(1e5)) / math.log(2)
+    assert abs(s + 7 / 3) < 0.01
+
+
+def test_fp_rates_absolute_vs_exact_spectrum(exact_moments):
+    """D1 and D2 per unit phase against the absolute emission moments.
+
+    Per unit time the exact spectrum gives d<gamma>/dt = -(alpha m c^2 /
+    (sqrt3 pi hbar)) m1 and d<dgamma^2>/dt = gamma (alpha m c^2/(sqrt3 pi hbar))
+    m2; the phase advances at 2 omega0 for a head-on electron (the factor 2 of
+    Eq. 1), and chi = 2 gamma a / a_S (Eq. 6) is taken at the rms field A/sqrt2.
+    """
+    L = I.Laser(lambda_um=0.8)
+    c = oracle.constants(L)
+    aS = c["aS"]
+    for chi in CHIS:
+        mu = 4000.0
+        A = chi * aS / (2 * mu) * math.sqrt(2)
+        r = oracle.qfp_rates(L, mu, A)
+        assert abs(r["chi"] / chi - 1) < 1e-12
+        m1, m2 = exact_moments[chi]
+        D1_exact = -SC.alpha * aS * m1 / (2 * math.sqrt(3) * math.pi)
+        D2_exact = mu * SC.alpha * aS * m2 / (2 * math.sqrt(3) * math.pi)
+        assert abs(r["D1"] / D1_exact - 1) < 0.02, chi
+        assert abs(r["D2"] / D2_exact - 1) < 0.02, chi
+        # dD1/dgamma against a central difference of D1 in gamma at fixed A
+        hh = mu * 1e-6
+        fd = (oracle.qfp_rates(L, mu + hh, A)["D1"] - oracle.qfp_rates(L, mu - hh, A)["D1"]) / (2 * hh)
+        assert abs(r["dD1"] / fd - 1) < 1e-6
+
+
+def test_spread_below_eq9_bound_for_long_pulses():
+    """Eq. 9 bounds sigma_f^2 for long pulses; the FP model stays below it
+    and within an order of magnitude of it."""
+    pv = paper_values()["eq9_bound"]
+    for tau in (100.0, 300.0):
+        for a0 in (5.0, 20.0, 50.0):
+            for g0 in (1000.0, 4000.0, 10000.0):
+                L = I.Laser(a0=a0, tau_fs=tau, model=I.MODEL_QFP, n_phase=2048)
+                mu, V = oracle.qfp_integrate(L, a0, g0)
+                I22 = 1.37e18 * a0 ** 2 / 0.8 ** 2 / 1e22
+                bound = pv["c1"] * math.sqrt(I22) * g0 ** 3 / (1 + pv["c2"] * g0 * I22 * tau) ** 3
+                assert 0.1 * bound < V <= bound, (tau, a0, g0, V, bound)
+
+
+# --------------------------------------------------------------------------
+# phase integration
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("env", [I.ENV_GAUSS, I.ENV_SIN2])
+def test_qfp_classical_limit_equals_eq3(env):
+    """a_S -> infinity gives g = 1, D2 = 0: the integrator must reproduce
+    the closed form of Eq. 3 (to the Gaussian window truncation)."""
+    for a0, g0 in ((10.0, 1957.0), (30.0, 4000.0), (100.0, 20000.0)):
+        L = I.Laser(a0=a0, tau_fs=30.0, envelope=env, model=I.MODEL_QFP, n_phase=512)
+        mu, V = oracle.qfp_integrate(L, a0, g0, 0.0, 1e12, 0.0)
+        cRR = oracle.constants(L)["cRR"]
+        closed = g0 / (1 + cRR * g0 * a0 ** 2)
+        assert abs(mu / closed - 1) < 1e-7
+        assert V == 0.0
+
+
+def test_qfp_zero_intensity_is_identity():
+    L = I.Laser(a0=0.0, model=I.MODEL_QFP, n_phase=64)
+    for g0 in (1.0, 1957.0, 12345.678):
+        mu, V = oracle.qfp_integrate(L, 0.0, g0)
+        assert mu == g0 and V == 0.0
+
+
+def test_variance_transport_classical_closed_form():
+    """With D2 = 0 and g = 1 an initial variance V0 is carried by the
+    linearised flow: V_f = V0 (d gamma_f / d gamma_0)^2 = V0/(1+c g0 a^2)^4.
+    The scheme is second order: the error quarters when N doubles."""
+    a0, g0, V0 = 20.0, 3000.0, 100.0
+    errs = []
+    for N in (256, 512, 1024, 2048):
+        L = I.Laser(a0=a0, model=I.MODEL_QFP, n_phase=N)
+        cRR = oracle.constants(L)["cRR"]
+        exact = V0 / (1 + cRR * g0 * a0 ** 2) ** 4
+        _, V = oracle.qfp_integrate(L, a0, g0, V0, 1e12, 0.0)
+        errs.append(abs(V / exact - 1))
+    assert errs[1] < 5e-4
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5
+
+
+def test_qfp_integrator_vs_library_ode_solver():
+    """The phase sum converges (second order) to a high-accuracy DOP853 solve
+    of d<gamma>/dphi = D1, dV/dphi = 2 dD1 V + D2 with the same rates."""
+    a0, g0 = 30.0, 4000.0
+    Lref = I.Laser(a0=a0, model=I.MODEL_QFP, n_phase=512)
+    c = oracle.constants(Lref)
+    Phi = c["Phi"]
+
+    def G(phi):
+        return math.exp(-2 * math.log(2) * (phi / Phi) ** 2)
+
+    def f(phi, y):
+        r = oracle.qfp_rates(Lref, y[0], a0 * G(phi))
+        return [r["D1"], 2 * r["dD1"] * y[1] + r["D2"]]
+
+    sol = solve_ivp(f, (c["win_lo"], c["win_hi"]), [g0, 0.0], method="DOP853", rtol=1e-11,
+                    atol=1e-9)
+    mu_ref, V_ref = sol.y[0, -1], sol.y[1, -1]
+    errs = []
+    for N in (256, 512, 1024):
+        L = I.Laser(a0=a0, model=I.MODEL_QFP, n_phase=N)
+        mu, V = oracle.qfp_integrate(L, a0, g0)
+        errs.append((abs(mu / mu_ref - 1), abs(V / V_ref - 1)))
+    assert errs[1][0] < 2e-5 and errs[1][1] < 2e-4     # 512 steps
+    for (m1, v1), (m2, v2) in zip(errs, errs[1:]):
+        assert 3.0 < m1 / m2 < 5.0 and 3.0 < v1 / v2 < 5.0
+
+
+# --------------------------------------------------------------------------
+# whole-beam integration: Table 1 and Table 2 closed forms
+# --------------------------------------------------------------------------
+
+def _hist_vs_density(hist, edges, density, n_total, z=5.0, floor=3.0):
+    """Compare histogram masses with the integral of an analytic density
+    over each bin: |h - N p| <= z sqrt(N p) + floor."""
+    for b in range(len(hist)):
+        p = quad(density, edges[b], edges[b + 1], limit=200)[0]
+        tol = z * math.sqrt(max(n_total * p, 1.0)) + floor
+        assert abs(hist[b] - n_total * p) <= tol, (b, hist[b], n_total * p)
+
+
+def _short_beam_inputs(n, seed, sigma, dx=0.0, delay=0.0, a0=12.0, w0=2.0, lam=1.0):
+    L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, dx_um=dx, delay_fs=delay, model=I.MODEL_LL)
+    B = I.Beam(gamma_mean=5000.0, rel_spread=0.0, sigma_x_um=sigma, sigma_y_um=sigma,
+               sigma_z_um=0.0, div_rad=0.0)
+    xi = I.sample_streams(n, seed, dtype=np.float64)
+    return L, B, xi
+
+
+def test_table1_short_beam_aligned():
+    """Short beam, aligned: P(a_eff < A) = (A/a0)^(W0^2/R^2), R = sqrt2 sigma."""
+    n, sigma, a0, w0 = 1 << 16, 1.5, 12.0, 2.0
+    L, B, xi = _short_beam_inputs(n, 11, sigma, a0=a0, w0=w0)
+    bins = I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=48, aeff_max=a0)
+    r = oracle.scatter(L, B, bins, xi)
+    R2 = 2 * sigma ** 2
+    k = w0 ** 2 / R2
+    edges = np.linspace(0, a0, 49)
+    _hist_vs_density(r["aeff_hist"], edges, lambda a: k / a * (a / a0) ** k, n)
+
+
+def test_table1_short_beam_transverse_offset():
+    """Table 1 Short beam with a transverse offset (the I0 term)."""
+    n, sigma, a0, w0, d = 1 << 16, 1.5, 12.0, 2.0, 2.0
+    L, B, xi = _short_beam_inputs(n, 12, sigma, dx=d, a0=a0, w0=w0)
+    bins = I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=48, aeff_max=a0)
+    r = oracle.scatter(L, B, bins, xi)
+    R = math.sqrt(2) * sigma
+    k = w0 ** 2 / R ** 2
+
+    def dens(a):
+        lg = math.log(a0 / a)
+        return k / a * (a / a0) ** k * i0(2 * (d / R) * (w0 / R) * math.sqrt(lg)) * math.exp(-d * d / R ** 2)
+
+    edges = np.linspace(0, a0, 49)
+    _hist_vs_density(r["aeff_hist"], edges, dens, n)
+
+
+def test_table1_short_beam_delay():
+    """Longitudinal (temporal) offset: W0 -> W and a0 -> a_par with
+    Delta_par = -c delay / 2 (the collision point moves by half the lag)."""
+    n, sigma, a0, w0, lam, delay = 1 << 16, 1.5, 12.0, 2.0, 1.0, 60.0
+    L, B, xi = _short_beam_inputs(n, 13, sigma, delay=delay, a0=a0, w0=w0, lam=lam)
+    zR = math.pi * w0 ** 2 / lam
+    dpar = 0.299792458 * delay / 2
+    W = w0 * math.sqrt(1 + (dpar / zR) ** 2)
+    apar = a0 / math.sqrt(1 + (dpar / zR) ** 2)
+    bins = I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=48, aeff_max=a0)
+    r = oracle.scatter(L, B, bins, xi)
+    R2 = 2 * sigma ** 2
+    k = W ** 2 / R2
+    edges = np.linspace(0, a0, 49)
+
+    def dens(a):
+        return k / a * (a * W / (a0 * w0)) ** k if a < apar else 0.0
+
+    _hist_vs_density(r["aeff_hist"], edges, dens, n)
+    assert r["aeff_hist"][edges[:-1] > apar].sum() == 0
+
+
+def test_table1_thin_beam():
+    """Thin beam (R << W0), flat-top length L: dN/da = (2 N z_R / L)
+    (a0^2/a^2) / sqrt(a0^2 - a^2) on both branches (aligned)."""
+    n, a0, w0, lam, Lb = 1 << 16, 12.0, 2.0, 1.0, 60.0
+    L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, model=I.MODEL_LL)
+    B = I.Beam(gamma_mean=5000.0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+               sigma_z_um=Lb / (2 * math.sqrt(3)))
+    xi = I.sample_streams(n, 14, dtype=np.float64)
+    xi[2] = I.rng(99).uniform(-math.sqrt(3), math.sqrt(3), n)   # flat-top in z
+    zR = math.pi * w0 ** 2 / lam
+    az = a0 / math.sqrt(1 + (Lb / (4 * zR)) ** 2)
+    bins = I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=64, aeff_max=a0)
+    r = oracle.scatter(L, B, bins, xi)
+    edges = np.linspace(0, a0, 65)
+
+    def dens(a):
+        if a <= az or a >= a0:
+            return 0.0
+        return 2 * (2 * zR / Lb) * (a0 ** 2 / a ** 2) / math.sqrt(a0 ** 2 - a ** 2)
+
+    _hist_vs_density(r["aeff_hist"], edges, dens, n)
+
+
+def test_table2_short_beam_ll_spectrum():
+    """Table 2 Short beam: dN/dgamma = N (W0^2/2R^2) (g0/g)/(g0-g)
+    ((g0-g)/(c_RR g0 g a0^2))^(W0^2/2R^2) above gamma_min."""
+    n, sigma, a0, w0, g0 = 1 << 16, 1.5, 12.0, 2.0, 5000.0
+    L, B, xi = _short_beam_inputs(n, 15, sigma, a0=a0, w0=w0, lam=0.8)
+    cRR = oracle.constants(L)["cRR"]
+    gmin = g0 / (1 + cRR * g0 * a0 ** 2)
+    bins = I.Bins(n_bins=64, lo=gmin * 0.9, hi=g0 * 1.0001)
+    r = oracle.scatter(L, B, bins, xi)
+    k = w0 ** 2 / (2 * 2 * sigma ** 2)
+
+    def dens(g):
+        if g <= gmin or g >= g0:
+            return 0.0
+        return k * (g0 / g) / (g0 - g) * ((g0 - g) / (cRR * g0 * g * a0 ** 2)) ** k
+
+    edges = np.linspace(bins.lo, bins.hi, bins.n_bins + 1)
+    _hist_vs_density(r["spectrum"], edges, dens, n)
+
+
+def test_table2_thin_beam_ll_spectrum():
+    """Table 2 Thin beam: dN/dgamma = (2 N z_R/L) g0/(g0-g)^(3/2)
+    c_RR g0 a0^2 / sqrt(c_RR g g0 a0^2 + g - g0), on gamma_min < gamma < gamma_z
+    (the printed theta(gamma - gamma_z) has its support inverted: a_eff runs
+    from a_z up to a0, so gamma_f runs from gamma_min up to gamma_z)."""
+    n, a0, w0, lam, Lb, g0 = 1 << 16, 12.0, 2.0, 0.8, 60.0, 5000.0
+    L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, model=I.MODEL_LL)
+    B = I.Beam(gamma_mean=g0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+               sigma_z_um=Lb / (2 * math.sqrt(3)))
+    xi = I.sample_streams(n, 16, dtype=np.float64)
+    xi[2] = I.rng(98).uniform(-math.sqrt(3), math.sqrt(3), n)
+    c = oracle.constants(L)
+    cRR, zR = c["cRR"], c["zR"]
+    az = a0 / math.sqrt(1 + (Lb / (4 * zR)) ** 2)
+    gmin = g0 / (1 + cRR * g0 * a0 ** 2)
+    gz = g0 / (1 + cRR * g0 * az ** 2)
+    bins = I.Bins(n_bins=48, lo=gmin, hi=gz)
+
+    def dens(g):
+        if g <= gmin or g >= gz:
+            return 0.0
+        return (2 * zR / Lb) * g0 / (g0 - g) ** 1.5 * cRR * g0 * a0 ** 2 / math.sqrt(
+            cRR * g * g0 * a0 ** 2 + g - g0)
+
+    r = oracle.scatter(L, B, bins, xi)
+    edges = np.linspace(bins.lo, bins.hi, bins.n_bins + 1)
+    _hist_vs_density(r["spectrum"], edges, dens, n)
+
+
+# --------------------------------------------------------------------------
+# invariants of the whole-beam integration
+# --------------------------------------------------------------------------
+
+def _qfp_workload(n=2048, seed=5):
+    wl = I.full_qfp(n)
+    xi, _ = I.workload_inputs(wl, n)
+    return wl, [x.astype(np.float64) for x in xi]
+
+
+def test_zero_intensity_spectrum_is_initial_histogram():
+    wl, xi = _qfp_workload()
+    for model in (I.MODEL_LL, I.MODEL_QFP):
+        L = I.Laser(**{**wl.laser.__dict__, "a0": 0.0, "model": model})
+        s = oracle.evaluate(L, wl.beam, wl.bins, xi)
+        assert np.array_equal(s["mu"], s["gamma0"])
+        assert np.all(s["V"] == 0)
+        r = oracle.scatter(L, wl.beam, wl.bins, xi)
+        h, _ = np.histogram(s["gamma0"], bins=wl.bins.n_bins, range=(wl.bins.lo, wl.bins.hi))
+        assert np.array_equal(r["spectrum"], h.astype(float))
+
+
+def test_weight_conservation_and_consistency():
+    wl, xi = _qfp_workload()
+    w = I.rng(3).uniform(0.2, 2.0, len(xi[0]))
+    r = oracle.scatter(wl.laser, wl.beam, wl.bins, xi, w)
+    m = r["moments"]
+    assert abs(r["spectrum"].sum() + m["under"] + m["over"] - w.sum()) < 1e-9
+    assert abs(r["divmap"].sum() + m["map_out"] - w.sum()) < 1e-9
+    assert abs(r["aeff_hist"].sum() - w[np.asarray(
+        oracle.evaluate(wl.laser, wl.beam, wl.bins, xi)["abin"]) < wl.bins.n_aeff].sum()) < 1e-9
+    # moments against the per-sample records (law of total variance)
+    s = oracle.evaluate(wl.laser, wl.beam, wl.bins, xi)
+    W = w.sum()
+    mean = (w * s["mu"]).sum() / W
+    var = (w * (s["mu"] - mean) ** 2).sum() / W + (w * s["V"]).sum() / W
+    assert abs(m["mean"] / mean - 1) < 1e-12
+    assert abs(m["spread"] / math.sqrt(var) - 1) < 1e-10
+    thx0 = wl.beam.div_rad * xi[4]
+    assert abs(m["div_x"] ** 2 / ((w * (thx0 ** 2 + s["theta_e"] ** 2)).sum() / W) - 1) < 1e-12
+
+
+def test_transverse_offset_mirror_symmetry():
+    """+dx on a sample set equals -dx on its x-mirrored set, bit for bit;
+    the divergence map mirrors in theta_x."""
+    wl, xi = _qfp_workload(1024)
+    B = I.Beam(**{**wl.beam.__dict__, "dx_um": 0.0})
+    L1 = I.Laser(**{**wl.laser.__dict__, "dx_um": 2.0})
+    L2 = I.Laser(**{**wl.laser.__dict__, "dx_um": -2.0})
+    xm = list(xi)
+    for k in (0, 4, 6):
+        xm[k] = -xi[k]
+    r1 = oracle.scatter(L1, B, wl.bins, xi)
+    r2 = oracle.scatter(L2, B, wl.bins, xm)
+    assert np.array_equal(r1["spectrum"], r2["spectrum"])
+    assert r1["moments"] == r2["moments"]
+    s1 = oracle.evaluate(L1, B, wl.bins, xi)
+    s2 = oracle.evaluate(L2, B, wl.bins, xm)
+    assert np.array_equal(s1["aeff"], s2["aeff"]) and np.array_equal(s1["mu"], s2["mu"])
+    assert np.array_equal(s1["theta_x"], -s2["theta_x"])
+
+
+def test_delay_mirror_symmetry():
+    """+delay with z-mirrored samples equals -delay, bit for bit, at zero
+    divergence."""
+    wl, xi = _qfp_workload(1024)
+    B = I.Beam(**{**wl.beam.__dict__, "div_rad": 0.0})
+    L1 = I.Laser(**{**wl.laser.__dict__, "delay_fs": 40.0})
+    L2 = I.Laser(**{**wl.laser.__dict__, "delay_fs": -40.0})
+    xm = list(xi)
+    xm[2] = -xi[2]
+    s1 = oracle.evaluate(L1, B, wl.bins, xi)
+    s2 = oracle.evaluate(L2, B, wl.bins, xm)
+    assert np.array_equal(s1["aeff"], s2["aeff"])
+    assert np.array_equal(s1["mu"], s2["mu"]) and np.array_equal(s1["V"], s2["V"])
+
+
+def test_classical_divergence_unchanged():
+    """Classical model: the final angle is the initial angle (S11 reading)."""
+    wl, xi = _qfp_workload(512)
+    L = I.Laser(**{**wl.laser.__dict__, "model": I.MODEL_LL})
+    s = oracle.evaluate(L, wl.beam, wl.bins, xi)
+    assert np.array_equal(s["theta_x"], wl.beam.div_rad * xi[4])
+    assert np.all(s["theta_e"] == 0)
+
+
+def test_bin_rule_half_open_edges():
+    L = I.Laser(a0=0.0)
+    B = I.Beam(gamma_mean=1.0, rel_spread=1.0, sigma_x_um=0, sigma_y_um=0)
+    bins = I.Bins(n_bins=4, lo=0.0, hi=8.0)
+    # gamma0 = 1 + xi3 -> values exactly on edges and outside
+    g = np.array([0.0, 1.9999, 2.0, 3.0, 6.0, 7.9999, 8.0, 9.0, -0.5])
+    xi = [np.zeros_like(g)] * 8
+    xi = list(xi)
+    xi[3] = g - 1.0
+    s = oracle.evaluate(L, B, bins, xi)
+    # gamma0 is clamped at 1: the -0.5 and 0.0 entries land in bin 0
+    assert list(s["bin"]) == [0, 0, 1, 1, 3, 3, 4, 4, 0]
+    Lg = I.Bins(n_bins=3, lo=1.0, hi=1000.0, log_spaced=1)
+    xi[3] = np.array([1.0, 10.5, 99.0, 101.0, 999.0, 1000.0, 2000.0, 1.5, 2.0]) - 1.0
+    s = oracle.evaluate(L, B, Lg, xi)
+    assert list(s["bin"][[1, 2, 3, 4, 6]]) == [1, 1, 2, 2, 3]
+
+
+def test_gauss_hermite_rule_exactness():
+    x, w = I.gauss_hermite(32)
+    assert abs(w.sum() - 1) < 1e-14
+    for k in range(0, 64):
+        exact = 0.0 if k % 2 else float(np.prod(np.arange(k - 1, 0, -2, dtype=np.float64)))
+        val = float(np.sum(w * x ** k))
+        scale = float(np.sum(w * np.abs(x) ** k))
+        assert abs(val - exact) <= 1e-11 * scale, k
