@@ -1,0 +1,356 @@
+"""Benchmark of the beam phase-space integration (one JSON line on rank 0).
+
+Workload: 2^26 Monte Carlo beam samples (gamma0 = 4000, 10% spread, 3 um x 3 um
+x 10 um, 1 mrad), laser a0 = 30, W0 = 2.5 um, 30 fs, 2 um transverse offset,
+40 fs delay; quantum-corrected Fokker-Planck model over 512 phase cells;
+512-bin spectrum, 128x128 divergence map, 256-bin a_eff histogram; FP32 bulk
+arithmetic with FP64 moments.  One step = one qs_scatter call over all
+samples.  Inputs (2.1 GB) are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank integrates its own 2^26 samples (weak scaling, no
+data-path collective); rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "beam-sample evals/s"
+UNIT = "samples/s"
+
+# Arithmetic per phase cell of the QFP integration (FP32 path), counted from
+# the model's expression ("Algorithmic work"):
+#   FMA-pipe operations (add, mul, fma each 1) and MUFU operations.
+QFP_FMA_OPS_PER_STEP = 49
+QFP_MUFU_OPS_PER_STEP = 8
+FMA_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 26, help="samples per rank")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--f64-steps", type=int, default=2, help="timed steps of the FP64 path")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        pass
+    return p
+
+
+def cpu_oracle_rate(wl, xi_host, seconds=12.0, chunk=2048):
+    """Oracle samples/s on one host core over a bounded prefix of the workload."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done + chunk <= len(xi_host[0]):
+        sub = [a[done:done + chunk].astype(np.float64) for a in xi_host]
+        oracle.scatter(wl.laser, wl.beam, wl.bins, sub)
+        done += chunk
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    import numpy as np
+    from paper_2308_09348_gb300 import inputs as I
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = I.full_qfp(args.n)
+    per_step = 1024
+    total = per_step * (args.steps + args.warmup)
+    xi = I.sample_streams(total, wl.seed, dtype=np.float32)
+    import oracle
+    oracle.build()
+    times = []
+    for s in range(args.warmup + args.steps):
+        sub = [a[s * per_step:(s + 1) * per_step].astype(np.float64) for a in xi]
+        t0 = time.perf_counter()
+        oracle.scatter(wl.laser, wl.beam, wl.bins, sub)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    v = per_step / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "n_samples_per_step": per_step,
+                                             "n_phase": wl.laser.n_phase, "model": "qfp"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} samples of the {wl.name} workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2308_09348_gb300 import inputs as I
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import build as _build
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    if rank == 0 or ws == 1:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+
+    wl = I.full_qfp(args.n)
+    n = args.n
+    dev = torch.device("cuda", local)
+    # seeded synthetic variates, generated on the device (rank-dependent seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    stream = torch.cuda.current_stream()
+    out = B.Outputs(wl.bins, n, dev, args.precision)
+
+    def step(events=None, precision=args.precision, o=out, streams=xi):
+        B.qs_scatter(wl.laser, wl.beam, streams, wl.bins, precision=precision, out=o,
+                     kernel_events=events)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ------------------------------------
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(kev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    kern_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * ws / (ms * 1e-3)
+
+    # ---- plain FP64 GPU path, same samples --------------------------------
+    f64 = None
+    if args.precision == "f32" and args.f64_steps > 0:
+        o64 = B.Outputs(wl.bins, n, dev, "f64")
+        step(precision="f64", o=o64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.f64_steps):
+            step(precision="f64", o=o64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / args.f64_steps
+        m32, m64 = out.moments_dict(), o64.moments_dict()
+        f64 = {"value": n / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+               "steps": args.f64_steps,
+               "f32_vs_f64_rel_err": {k: abs(m32[k] / m64[k] - 1) if m64[k] else 0.0
+                                      for k in ("mean", "spread", "div_x", "div_y")},
+               "f32_vs_f64_spectrum_l1": float((out.spectrum - o64.spectrum).abs().sum()) / n}
+        del o64
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = None
+    if not args.no_e2e:
+        host = [x.cpu().pin_memory() for x in xi]
+        dxi = [torch.empty_like(x) for x in xi]
+        res_host = torch.empty(out.moments.numel() + out.spectrum.numel() + out.divmap.numel()
+                               + out.aeff_hist.numel(), dtype=torch.float64).pin_memory()
+        h2d = sum(h.numel() * h.element_size() for h in host)
+        d2h = res_host.numel() * 8
+
+        def e2e_step():
+            for d, h in zip(dxi, host):
+                d.copy_(h, non_blocking=True)
+            step(streams=dxi)
+            flat = torch.cat([out.moments, out.spectrum, out.divmap, out.aeff_hist])
+            res_host.copy_(flat, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(2, args.steps // 2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / k2
+        if ws > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": n * ws / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+        del host, dxi
+
+    # ---- roofline of the evaluation kernel --------------------------------
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    pk = peaks()
+    fmax_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    steps_total = n * wl.laser.n_phase
+    fma_ops = QFP_FMA_OPS_PER_STEP * steps_total
+    mufu_ops = QFP_MUFU_OPS_PER_STEP * steps_total
+    peak_fma = sms * FMA_LANES_PER_SM * fmax_mhz * 1e6
+    peak_mufu = sms * MUFU_LANES_PER_SM * fmax_mhz * 1e6
+    t_k = kern_ms * 1e-3
+    t_bound = max(fma_ops / peak_fma, mufu_ops / peak_mufu)
+    bound_pipe = "mufu" if mufu_ops / peak_mufu >= fma_ops / peak_fma else "fma"
+    if bound_pipe == "mufu":
+        achieved, peak_v = mufu_ops / t_k / 1e12, peak_mufu / 1e12
+    else:
+        achieved, peak_v = fma_ops / t_k / 1e12, peak_fma / 1e12
+    roof = {"bound": "alu", "pipe": bound_pipe, "achieved": achieved, "peak": peak_v,
+            "unit": "Top/s", "frac": t_bound / t_k, "traffic": None,
+            "kernel": "k_scatter<float>", "kernel_ms": kern_ms,
+            "peak_source": f"{sms} SMs x {MUFU_LANES_PER_SM if bound_pipe == 'mufu' else FMA_LANES_PER_SM}"
+                           f" lanes x {fmax_mhz:.0f} MHz (max SM clock)",
+            "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nh = 1 << 16
+        xi_host = [x[:nh].cpu().numpy() for x in xi]
+        rate, done, dt = cpu_oracle_rate(wl, xi_host)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {done} samples of the workload ({dt:.1f} s, FP64 C oracle, "
+                         f"one thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                "data": "synthetic",
+                "config": {"workload": wl.name, "n_samples_per_gpu": n, "model": "qfp",
+                           "n_phase": wl.laser.n_phase, "spectrum_bins": wl.bins.n_bins,
+                           "divmap": f"{wl.bins.n_tx}x{wl.bins.n_ty}",
+                           "aeff_bins": wl.bins.n_aeff,
+                           "moments": "f64", "parallelism": f"dp{ws} (independent samples)",
+                           "l2": "inputs (2.1 GB per GPU) larger than L2; no flush"},
+                "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
+                "gpu": props.name}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * qscatter.h -- C ABI of libqscatter, a GB300 (sm_103a) implementation of
+ * the beam phase-space integration of QScatter (Amaro & Vranic,
+ * arXiv 2308.09348): for every electron-beam sample, the local
+ * Gaussian-focus field it crosses (Sec. 2, Eqs. 1-2), its final energy from
+ * the classical Landau-Lifshitz closed form (Eq. 3) or from the
+ * quantum-corrected Fokker-Planck mean/variance phase integration (Eq. 6 and
+ * the Fokker-Planck regime of Sec. 1), its final divergence (Eq. 8), then the
+ * weighted reduction into spectra (Eq. 4 as a histogram, Eq. 1 as the a_eff
+ * histogram) and moments (mean energy, energy spread, divergence).
+ *
+ * Conventions shared by every entry point
+ *  - Units: lengths in micrometres, times in femtoseconds, energies as the
+ *    Lorentz factor gamma, angles in radians.
+ *  - Pointers named d_* are DEVICE pointers (any CUDA allocation on the
+ *    current device); descriptor structs (qs_laser, ...) are HOST pointers
+ *    read during the call only.
+ *  - Ownership: the caller owns every buffer.  The library allocates no
+ *    memory and keeps no per-call state; scratch space is the caller's
+ *    workspace (size from qs_workspace_bytes, 256-byte aligned).
+ *  - Execution: asynchronous on the given CUDA stream (cudaStream_t passed
+ *    as void*; NULL = legacy default stream).  Outputs are valid once the
+ *    stream reaches the point of the call.  Calls that share a workspace
+ *    must be ordered on one stream.
+ *  - Errors: arguments are validated on the host before any launch; on a
+ *    non-QS_OK return nothing has been launched and no output was written
+ *    (QS_ERR_CUDA: a launch failed; outputs are then undefined).
+ *  - Determinism: histograms accumulate in integers (exact, order-free);
+ *    moments are reduced in a fixed order for a given device and
+ *    qs_exec; repeated calls give bit-identical results.
+ */
+#ifndef QSCATTER_H
+#define QSCATTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QS_VERSION 1
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_INVALID_ARG = 1,   /* a descriptor or pointer failed validation   */
+    QS_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed        */
+    QS_ERR_WORKSPACE = 3,     /* workspace missing, too small or misaligned  */
+    QS_ERR_UNSUPPORTED = 4,   /* valid request this build does not support   */
+    QS_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up          */
+} qs_status;
+
+typedef enum { QS_ENV_GAUSS = 0, QS_ENV_SIN2 = 1 } qs_envelope;
+typedef enum { QS_MODEL_LL = 0, QS_MODEL_QFP = 1 } qs_model;
+typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
+
+/*
+ * Laser (Sec. 2 Eq. 2; Eq. 3; Sec. 4; Appendix A).  The laser moves along +z
+ * with its focus at the origin; its pulse peak passes z = 0 at t = delay_fs.
+ *   lambda_um      central wavelength (> 0)
+ *   a0             peak normalised vector potential (>= 0)
+ *   w0_um          focal spot size W0 of Eq. 2 (> 0); z_R = pi W0^2/lambda
+ *   tau_fs         intensity FWHM duration (> 0)
+ *   dx_um, dy_um   position of the laser axis (transverse misalignment)
+ *   delay_fs       temporal misalignment
+ *   div_prefactor  kappa, the multiplicative prefactor of Eq. 8 (>= 0)
+ *   envelope       QS_ENV_GAUSS: field envelope exp(-2 ln2 (phi/Phi)^2),
+ *                  Phi = omega0 tau, phase window [-2.5 Phi, 2.5 Phi];
+ *                  QS_ENV_SIN2: field envelope sin^2(pi phi/Phi_T) on
+ *                  [0, Phi_T], Phi_T chosen so the intensity FWHM is Phi
+ *   model          QS_MODEL_LL (Eq. 3) or QS_MODEL_QFP (Eq. 6 + FP closure)
+ *   n_phase        phase cells of the QFP integration, 1..4096 (ignored by LL)
+ */
+typedef struct qs_laser {
+    double lambda_um, a0, w0_um, tau_fs;
+    double dx_um, dy_um, delay_fs, div_prefactor;
+    int32_t envelope, model, n_phase, reserved;
+} qs_laser;
+
+/*
+ * Electron beam (Sec. 1: broadband beams and divergence; each sample is a
+ * weighted volume element of the beam, as in Eq. 1).  A sample with
+ * variates xi[0..7] decodes to
+ *   x = dx_um + sigma_x_um xi0,  y = dy_um + sigma_y_um xi1,  z = sigma_z_um xi2
+ *   gamma0 = gamma_mean (1 + rel_spread xi3)            (flat_energy == 0)
+ *          = gamma_lo + (gamma_hi - gamma_lo) xi3        (flat_energy != 0)
+ *   gamma0 is clamped to >= 1
+ *   theta_x = div_rad xi4, theta_y = div_rad xi5
+ * (x, y, z) is the position at t = 0; the velocity is c(theta_x, theta_y, -1).
+ */
+typedef struct qs_beam {
+    double gamma_mean, rel_spread, gamma_lo, gamma_hi;
+    double sigma_x_um, sigma_y_um, sigma_z_um, div_rad, dx_um, dy_um;
+    int32_t flat_energy, reserved;
+} qs_beam;
+
+/*
+ * Samples: structure of arrays on the device.  xi[k] holds n elements of
+ * dtype (QS_F32 or QS_F64) each; xi[0..3] are required when n > 0, a NULL
+ * xi[4..7] reads as zeros.  xi[6] (angular noise) and xi[7] (energy noise)
+ * are only read by the QFP model.  w: n per-sample weights (>= 0, finite) of
+ * the same dtype, or NULL for unit weights.  Pointers must be aligned to the
+ * element size; 16-byte alignment enables vector loads.
+ */
+typedef struct qs_samples {
+    int64_t n;
+    const void* xi[8];
+    const void* w;
+    int32_t dtype, reserved;
+} qs_samples;
+
+/*
+ * Binning (Eq. 4 as a weighted histogram; Eq. 1 as the a_eff histogram).
+ *   Energy spectrum of the realised final energy gamma_out over [lo, hi):
+ *   n_bins bins (0 = off); uniform, or log-spaced (log_spaced != 0, lo > 0).
+ *   Bins are half-open; below lo goes to 'under', at or above hi to 'over'.
+ *   Divergence map over [-theta_max, theta_max)^2 of (theta_x, theta_y),
+ *   n_tx x n_ty bins, row-major [iy][ix] (0 = off).
+ *   a_eff histogram over [0, aeff_max), n_aeff bins (0 = off).
+ * Entries are bin masses (sums of weights), not densities.
+ */
+typedef struct qs_bins {
+    int32_t n_bins, log_spaced;
+    double lo, hi;
+    int32_t n_tx, n_ty;
+    double theta_max;
+    int32_t n_aeff, reserved;
+    double aeff_max;
+} qs_bins;
+
+/*
+ * Moments (observables of Sec. 1 and Sec. 5): written to device memory.
+ *   W            total weight
+ *   mean         <gamma_f> (weighted mean of the per-sample means)
+ *   spread       sqrt(<(mu - mean)^2> + <V>)  (law of total variance)
+ *   rel_spread   spread / mean
+ *   div_x        sqrt(<theta_x0^2 + theta_e^2>), theta_e the Eq. 8 broadening
+ *   div_y        sqrt(<theta_y0^2>),  div = sqrt(div_x^2 + div_y^2)
+ *   mean_aeff    <a_eff>,  mean_gamma0  <gamma0>
+ *   under, over  spectrum weight below lo / at or above hi
+ *   map_out      weight outside the divergence map
+ *   nonfinite    NUMBER of samples excluded from every other output because
+ *                their weight was negative or not finite, or their result
+ *                was not finite
+ * With W == 0 every field is 0.
+ */
+typedef struct qs_moments {
+    double W, mean, spread, rel_spread, div_x, div_y, div, mean_aeff;
+    double under, over, map_out, mean_gamma0, nonfinite;
+} qs_moments;
+
+/*
+ * Execution options (NULL = defaults).
+ *   precision         QS_F32: per-sample arithmetic in FP32 with FP64 moment
+ *                     accumulation and FP64 final-energy recombination;
+ *                     QS_F64: everything in FP64.
+ *   weight_frac_bits  fixed-point fraction bits of the weighted histograms
+ *                     (0 = 32).  Each weight is rounded to a multiple of
+ *                     2^-bits; every bin must stay below 2^(63-bits).
+ *   block, grid       launch shape of the evaluation kernel (0 = tuned).
+ *   ev_start, ev_stop optional cudaEvent_t handles (as void*): when set, they
+ *                     are recorded on the call's stream immediately before and
+ *                     after the evaluation kernel, so a caller can time that
+ *                     kernel alone.  The caller creates and owns the events.
+ */
+typedef struct qs_exec {
+    int32_t precision, weight_frac_bits, block, grid;
+    void* ev_start;
+    void* ev_stop;
+} qs_exec;
+
+/*
+ * Per-sample records of qs_eval_samples: device arrays of n elements, any
+ * may be NULL.  bin: energy bin, -1 under, n_bins over; ix/iy: map cell or
+ * -1 outside; abin: a_eff bin or n_aeff above.
+ */
+typedef struct qs_sample_out {
+    double *gamma0, *aeff, *mu, *V, *theta_e, *theta_x, *theta_y, *gamma_out;
+    int32_t *bin, *ix, *iy, *abin;
+} qs_sample_out;
+
+/* Version of this ABI (QS_VERSION). */
+int32_t qs_version(void);
+
+/* Static message for a status code. */
+const char* qs_status_string(int32_t status);
+
+/* Workspace bytes that qs_scatter needs for these bins, options and sample
+   count on the current device (0 if the arguments are invalid). */
+size_t qs_workspace_bytes(const qs_bins* bins, const qs_exec* exec, int64_t n_samples);
+
+/*
+ * qs_scatter: integrate the per-particle energy-loss model over the beam's
+ * phase space and reduce into spectra and moments (Sec. 2-5; Eqs. 1-4, 6, 8).
+ *   d_spectrum   n_bins doubles (required if n_bins > 0)
+ *   d_divmap     n_ty*n_tx doubles (required if the map is on)
+ *   d_aeff_hist  n_aeff doubles (required if n_aeff > 0)
+ *   d_moments    one qs_moments in device memory (required)
+ *   d_workspace  ws_bytes >= qs_workspace_bytes(...), 256-byte aligned
+ */
+int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
+                   const qs_bins* bins, const qs_exec* exec, double* d_spectrum,
+                   double* d_divmap, double* d_aeff_hist, qs_moments* d_moments,
+                   void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * qs_eval_samples: the per-sample part of qs_scatter (decode, collision
+ * geometry, Eq. 2, Eq. 3 or the QFP integration, Eq. 8, bin indices) with
+ * every intermediate written out, for inspection and element-wise checks.
+ * bins may be NULL (bin fields then read -1).  No workspace.
+ */
+int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
+                        const qs_bins* bins, const qs_exec* exec, const qs_sample_out* out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSCATTER_H */

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libqscatter (argument marshalling only).
+
+Every step of the beam phase-space integration runs in the library's CUDA
+kernels; this module converts workload descriptions and torch tensors into
+the C structs of ``include/qscatter.h`` and calls the entry points of the same
+names.  There is no CPU fallback: if the shared library is missing or fails to
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import inputs as _inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libqscatter.so")
+
+QS_OK, QS_ERR_INVALID_ARG, QS_ERR_CUDA, QS_ERR_WORKSPACE, QS_ERR_UNSUPPORTED, QS_ERR_TIMEOUT = range(6)
+QS_F32, QS_F64 = 0, 1
+
+
+class QsError(RuntimeError):
+    def __init__(self, status: int, fn: str):
+        msg = _lib().qs_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{fn}: {msg} (status {status})")
+        self.status = status
+
+
+class qs_laser(C.Structure):
+    _fields_ = [("lambda_um", C.c_double), ("a0", C.c_double), ("w0_um", C.c_double),
+                ("tau_fs", C.c_double), ("dx_um", C.c_double), ("dy_um", C.c_double),
+                ("delay_fs", C.c_double), ("div_prefactor", C.c_double),
+                ("envelope", C.c_int32), ("model", C.c_int32), ("n_phase", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class qs_beam(C.Structure):
+    _fields_ = [("gamma_mean", C.c_double), ("rel_spread", C.c_double),
+                ("gamma_lo", C.c_double), ("gamma_hi", C.c_double),
+                ("sigma_x_um", C.c_double), ("sigma_y_um", C.c_double),
+                ("sigma_z_um", C.c_double), ("div_rad", C.c_double),
+                ("dx_um", C.c_double), ("dy_um", C.c_double),
+                ("flat_energy", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qs_samples(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xi", C.c_void_p * 8), ("w", C.c_void_p),
+                ("dtype", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qs_bins(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("log_spaced", C.c_int32), ("lo", C.c_double),
+                ("hi", C.c_double), ("n_tx", C.c_int32), ("n_ty", C.c_int32),
+                ("theta_max", C.c_double), ("n_aeff", C.c_int32), ("reserved", C.c_int32),
+                ("aeff_max", C.c_double)]
+
+
+MOMENT_FIELDS = ("W", "mean", "spread", "rel_spread", "div_x", "div_y", "div", "mean_aeff",
+                 "under", "over", "map_out", "mean_gamma0", "nonfinite")
+
+
+class qs_moments(C.Structure):
+    _fields_ = [(k, C.c_double) for k in MOMENT_FIELDS]
+
+
+class qs_exec(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("weight_frac_bits", C.c_int32),
+                ("block", C.c_int32), ("grid", C.c_int32), ("ev_start", C.c_void_p),
+                ("ev_stop", C.c_void_p)]
+
+
+class qs_sample_out(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("gamma0", "aeff", "mu", "V", "theta_e", "theta_x",
+                                          "theta_y", "gamma_out", "bin", "ix", "iy", "abin")]
+
+
+_LIB = None
+_lock = threading.Lock()
+_VP = C.c_void_p
+
+
+def _lib():
+    global _LIB
+    with _lock:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libqscatter is not built ({LIB_PATH} missing); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            L.qs_version.restype = C.c_int32
+            L.qs_status_string.argtypes = [C.c_int32]
+            L.qs_status_string.restype = C.c_char_p
+            L.qs_workspace_bytes.argtypes = [C.POINTER(qs_bins), C.POINTER(qs_exec), C.c_int64]
+            L.qs_workspace_bytes.restype = C.c_size_t
+            L.qs_scatter.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                     C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                     C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP]
+            L.qs_scatter.restype = C.c_int32
+            L.qs_eval_samples.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                          C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                          C.POINTER(qs_exec), C.POINTER(qs_sample_out), _VP]
+            L.qs_eval_samples.restype = C.c_int32
+            _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded shared library (raises if it is not built)."""
+    return _lib()
+
+
+# ---- descriptor marshalling ---------------------------------------------
+
+def make_laser(p: _inputs.Laser) -> qs_laser:
+    return qs_laser(p.lambda_um, p.a0, p.w0_um, p.tau_fs, p.dx_um, p.dy_um, p.delay_fs,
+                    p.div_prefactor, int(p.envelope), int(p.model), int(p.n_phase), 0)
+
+
+def make_beam(b: _inputs.Beam) -> qs_beam:
+    return qs_beam(b.gamma_mean, b.rel_spread, b.gamma_lo, b.gamma_hi, b.sigma_x_um,
+                   b.sigma_y_um, b.sigma_z_um, b.div_rad, b.dx_um, b.dy_um,
+                   int(b.flat_energy), 0)
+
+
+def make_bins(b: _inputs.Bins) -> qs_bins:
+    return qs_bins(int(b.n_bins), int(b.log_spaced), b.lo, b.hi, int(b.n_tx), int(b.n_ty),
+                   b.theta_max, int(b.n_aeff), 0, b.aeff_max)
+
+
+def _event_handle(ev):
+    """cudaEvent_t of a torch.cuda.Event (torch creates it at first record)."""
+    if ev.cuda_event == 0:
+        ev.record()
+    return ev.cuda_event
+
+
+def make_exec(precision="f32", weight_frac_bits=0, block=0, grid=0, events=None) -> qs_exec:
+    prec = QS_F64 if precision in ("f64", QS_F64, torch.float64) else QS_F32
+    e0, e1 = (None, None) if events is None else (_event_handle(events[0]),
+                                                  _event_handle(events[1]))
+    return qs_exec(prec, int(weight_frac_bits), int(block), int(grid), e0, e1)
+
+
+def make_samples(xi, w=None) -> tuple[qs_samples, list]:
+    """xi: list of up to 8 CUDA tensors (None = zeros) of one float dtype."""
+    xs = list(xi) + [None] * (8 - len(xi))
+    ref = next((t for t in xs if t is not None), None)
+    if ref is None:
+        raise ValueError("at least one sample stream is required")
+    dt = ref.dtype
+    if dt not in (torch.float32, torch.float64):
+        raise TypeError("sample streams must be float32 or float64")
+    n = ref.numel()
+    keep = []
+    ptrs = []
+    for t in xs:
+        if t is None:
+            ptrs.append(None)
+            continue
+        if t.dtype != dt or t.numel() != n or not t.is_cuda:
+            raise ValueError("sample streams must be CUDA tensors of one dtype and length")
+        t = t.contiguous()
+        keep.append(t)
+        ptrs.append(t.data_ptr())
+    wp = None
+    if w is not None:
+        if w.dtype != dt or w.numel() != n or not w.is_cuda:
+            raise ValueError("weights must match the sample streams")
+        w = w.contiguous()
+        keep.append(w)
+        wp = w.data_ptr()
+    s = qs_samples(n, (C.c_void_p * 8)(*ptrs), wp, QS_F32 if dt == torch.float32 else QS_F64, 0)
+    return s, keep
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(status: int, fn: str):
+    if status != QS_OK:
+        raise QsError(status, fn)
+
+
+# ---- entry points ---------------------------------------------------------
+
+def workspace_bytes(bins: _inputs.Bins, n: int, precision="f32", block=0, grid=0) -> int:
+    b = make_bins(bins)
+    e = make_exec(precision, 0, block, grid)
+    v = _lib().qs_workspace_bytes(C.byref(b), C.byref(e), int(n))
+    if v == 0:
+        raise QsError(QS_ERR_INVALID_ARG, "qs_workspace_bytes")
+    return int(v)
+
+
+class Outputs:
+    """Device buffers of one qs_scatter call (reusable across calls)."""
+
+    def __init__(self, bins: _inputs.Bins, n: int, device=None, precision="f32", block=0,
+                 grid=0):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.bins = bins
+        self.spectrum = torch.zeros(max(bins.n_bins, 0), dtype=torch.float64, device=dev)
+        nmap = bins.n_tx * bins.n_ty if (bins.n_tx > 0 and bins.n_ty > 0) else 0
+        self.divmap = torch.zeros(nmap, dtype=torch.float64, device=dev)
+        self.aeff_hist = torch.zeros(max(bins.n_aeff, 0), dtype=torch.float64, device=dev)
+        self.moments = torch.zeros(len(MOMENT_FIELDS), dtype=torch.float64, device=dev)
+        nbytes = workspace_bytes(bins, n, precision, block, grid)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        self.ws_bytes = nbytes
+
+    def moments_dict(self) -> dict:
+        v = self.moments.cpu().tolist()
+        return dict(zip(MOMENT_FIELDS, v))
+
+    def result(self) -> dict:
+        nm = self.divmap
+        if self.bins.n_tx > 0:
+            nm = nm.view(self.bins.n_ty, self.bins.n_tx)
+        return dict(spectrum=self.spectrum, divmap=nm, aeff_hist=self.aeff_hist,
+                    moments=self.moments_dict())
+
+
+def _ptr_or_none(t):
+    return t.data_ptr() if (t is not None and t.numel() > 0) else None
+
+
+def qs_scatter(laser, beam, xi, bins, w=None, precision="f32", out: Outputs | None = None,
+               block=0, grid=0, weight_frac_bits=0, stream=None, kernel_events=None) -> Outputs:
+    """Integrate the beam phase space: spectra + moments (asynchronous).
+
+    ``kernel_events``: optional (start, stop) torch.cuda.Event pair recorded
+    around the evaluation kernel on the call's stream."""
+    s, keep = make_samples(xi, w)
+    if out is None:
+        out = Outputs(bins, s.n, keep[0].device, precision, block, grid)
+    L, B, Bn = make_laser(laser), make_beam(beam), make_bins(bins)
+    E = make_exec(precision, weight_frac_bits, block, grid, kernel_events)
+    st = _lib().qs_scatter(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
+                           _ptr_or_none(out.spectrum), _ptr_or_none(out.divmap),
+                           _ptr_or_none(out.aeff_hist), out.moments.data_ptr(), out.ws_ptr,
+                           out.ws_bytes, _stream_ptr(stream))
+    _check(st, "qs_scatter")
+    return out
+
+
+SAMPLE_FIELDS_F = ("gamma0", "aeff", "mu", "V", "theta_e", "theta_x", "theta_y", "gamma_out")
+SAMPLE_FIELDS_I = ("bin", "ix", "iy", "abin")
+
+
+def qs_eval_samples(laser, beam, xi, bins=None, precision="f32", stream=None) -> dict:
+    """Per-sample records (dict of CUDA tensors)."""
+    s, keep = make_samples(xi, None)
+    dev = keep[0].device
+    n = s.n
+    res = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in SAMPLE_FIELDS_F}
+    res.update({k: torch.empty(n, dtype=torch.int32, device=dev) for k in SAMPLE_FIELDS_I})
+    o = qs_sample_out(*[res[k].data_ptr() if n else None
+                        for k in SAMPLE_FIELDS_F + SAMPLE_FIELDS_I])
+    L, B = make_laser(laser), make_beam(beam)
+    Bn = make_bins(bins) if bins is not None else None
+    E = make_exec(precision)
+    st = _lib().qs_eval_samples(C.byref(L), C.byref(B), C.byref(s),
+                                C.byref(Bn) if Bn is not None else None, C.byref(E),
+                                C.byref(o), _stream_ptr(stream))
+    _check(st, "qs_eval_samples")
+    return res

@@ -1,0 +1,568 @@
+// qs_scatter.cu -- kernels and C ABI of libqscatter (single-shot path).
+//
+// K1 k_scatter   fused per-sample evaluation + integer histograms (shared
+//                memory, merged into global with integer atomics) + FP64
+//                moment partials per CTA, reduced in fixed lane/warp order.
+// K2 k_finalize  one CTA: per-CTA partials summed in CTA order (compensated),
+//                integer histograms converted to doubles, moments written.
+// K0 k_eval      per-sample records (qs_eval_samples).
+//
+// Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348 (Secs. 2-5).
+#include "qscatter.h"
+#include "qs_device.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// host: derived constants
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr double kC = 0.299792458;          // um / fs
+constexpr double kRe = 2.8179403262e-9;     // classical electron radius, um
+constexpr double kLbarC = 3.8615926796e-7;  // reduced Compton wavelength, um
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kGaussWindow = 2.5;        // half-window in units of Phi
+constexpr int kSmemLimit = 227 * 1024;
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+int32_t validate_laser(const qs_laser* L) {
+  if (!L) return QS_ERR_INVALID_ARG;
+  if (!finite_pos(L->lambda_um) || !finite_nonneg(L->a0) || !finite_pos(L->w0_um) ||
+      !finite_pos(L->tau_fs) || !std::isfinite(L->dx_um) || !std::isfinite(L->dy_um) ||
+      !std::isfinite(L->delay_fs) || !finite_nonneg(L->div_prefactor))
+    return QS_ERR_INVALID_ARG;
+  if (L->envelope != QS_ENV_GAUSS && L->envelope != QS_ENV_SIN2) return QS_ERR_INVALID_ARG;
+  if (L->model != QS_MODEL_LL && L->model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
+  if (L->model == QS_MODEL_QFP && (L->n_phase < 1 || L->n_phase > kMaxPhase))
+    return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+int32_t validate_beam(const qs_beam* B) {
+  if (!B) return QS_ERR_INVALID_ARG;
+  const double v[] = {B->gamma_mean, B->rel_spread, B->gamma_lo, B->gamma_hi, B->sigma_x_um,
+                      B->sigma_y_um, B->sigma_z_um, B->div_rad, B->dx_um, B->dy_um};
+  for (double x : v)
+    if (!std::isfinite(x)) return QS_ERR_INVALID_ARG;
+  if (B->sigma_x_um < 0 || B->sigma_y_um < 0 || B->sigma_z_um < 0 || B->div_rad < 0)
+    return QS_ERR_INVALID_ARG;
+  if (B->flat_energy) {
+    if (!(B->gamma_hi >= B->gamma_lo) || B->gamma_lo < 0) return QS_ERR_INVALID_ARG;
+  } else if (!(B->gamma_mean > 0) || B->rel_spread < 0) {
+    return QS_ERR_INVALID_ARG;
+  }
+  return QS_OK;
+}
+
+int32_t validate_bins(const qs_bins* b) {
+  if (!b) return QS_ERR_INVALID_ARG;
+  if (b->n_bins < 0 || b->n_tx < 0 || b->n_ty < 0 || b->n_aeff < 0) return QS_ERR_INVALID_ARG;
+  if (b->n_bins > (1 << 22) || b->n_aeff > (1 << 22)) return QS_ERR_INVALID_ARG;
+  if ((int64_t)b->n_tx * b->n_ty > (int64_t)1 << 24) return QS_ERR_INVALID_ARG;
+  if (b->n_bins > 0) {
+    if (!std::isfinite(b->lo) || !std::isfinite(b->hi) || !(b->hi > b->lo))
+      return QS_ERR_INVALID_ARG;
+    if (b->log_spaced && !(b->lo > 0)) return QS_ERR_INVALID_ARG;
+  }
+  if ((b->n_tx > 0) != (b->n_ty > 0)) return QS_ERR_INVALID_ARG;
+  if (b->n_tx > 0 && !finite_pos(b->theta_max)) return QS_ERR_INVALID_ARG;
+  if (b->n_aeff > 0 && !finite_pos(b->aeff_max)) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+int32_t validate_samples(const qs_samples* s) {
+  if (!s) return QS_ERR_INVALID_ARG;
+  if (s->n < 0) return QS_ERR_INVALID_ARG;
+  if (s->dtype != QS_F32 && s->dtype != QS_F64) return QS_ERR_INVALID_ARG;
+  if (s->n == 0) return QS_OK;
+  const uintptr_t esz = s->dtype == QS_F32 ? 4 : 8;
+  for (int k = 0; k < 4; ++k)
+    if (!s->xi[k]) return QS_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (s->xi[k] && ((uintptr_t)s->xi[k] % esz)) return QS_ERR_INVALID_ARG;
+  if (s->w && ((uintptr_t)s->w % esz)) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int* grid) {
+  *precision = e ? e->precision : QS_F32;
+  *wbits = (e && e->weight_frac_bits) ? e->weight_frac_bits : 32;
+  *block = (e && e->block) ? e->block : 256;
+  *grid = e ? e->grid : 0;
+  if (*precision != QS_F32 && *precision != QS_F64) return QS_ERR_INVALID_ARG;
+  if (*wbits < 0 || *wbits > 52) return QS_ERR_INVALID_ARG;
+  if (*block < 32 || *block > 512 || (*block % 32)) return QS_ERR_INVALID_ARG;
+  if (*grid < 0) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+void fill_params(Params& p, const qs_laser* L, const qs_beam* B, const qs_samples* S,
+                 const qs_bins* b, int wbits) {
+  std::memset(&p, 0, sizeof(p));
+  const double k = 2.0 * kPi / L->lambda_um;
+  const double omega0 = kC * k;
+  const double zR = kPi * L->w0_um * L->w0_um / L->lambda_um;
+  const double Rc = kRe * k;
+  const double aS = 1.0 / (k * kLbarC);
+  const double Phi = omega0 * L->tau_fs;
+  const double PhiT = Phi / (1.0 - (2.0 / kPi) * std::asin(std::pow(2.0, -0.25)));
+  double lo, hi, intG2;
+  if (L->envelope == QS_ENV_GAUSS) {
+    lo = -kGaussWindow * Phi;
+    hi = kGaussWindow * Phi;
+    intG2 = Phi * std::sqrt(kPi / (4.0 * std::log(2.0)));
+  } else {
+    lo = 0.0;
+    hi = PhiT;
+    intG2 = 3.0 * PhiT / 8.0;
+  }
+  p.a0 = L->a0;
+  p.inv_w0sq = 1.0 / (L->w0_um * L->w0_um);
+  p.inv_zR = 1.0 / zR;
+  p.ldx = L->dx_um;
+  p.ldy = L->dy_um;
+  p.c_delay = kC * L->delay_fs;
+  p.cRR = (2.0 / 3.0) * Rc * intG2;
+  p.cK = (2.0 / 3.0) * Rc;
+  p.cchi = std::sqrt(2.0) / aS;
+  p.n_phase = L->model == QS_MODEL_QFP ? L->n_phase : 1;
+  p.h = (hi - lo) / (double)p.n_phase;
+  p.win_lo = lo;
+  p.Phi = Phi;
+  p.PhiT = PhiT;
+  p.kappa_s = L->div_prefactor * std::sqrt(2.0 / kPi);
+  p.envelope = L->envelope;
+  p.model = L->model;
+
+  p.gmean = B->gamma_mean;
+  p.spread = B->rel_spread;
+  p.glo = B->gamma_lo;
+  p.gspan = B->gamma_hi - B->gamma_lo;
+  p.sx = B->sigma_x_um;
+  p.sy = B->sigma_y_um;
+  p.sz = B->sigma_z_um;
+  p.div = B->div_rad;
+  p.bdx = B->dx_um;
+  p.bdy = B->dy_um;
+  p.flat = B->flat_energy ? 1 : 0;
+
+  p.n = S->n;
+  for (int i = 0; i < 8; ++i) p.xi[i] = S->xi[i];
+  p.w = S->w;
+  p.dtype = S->dtype;
+  p.weighted = S->w != nullptr;
+
+  if (b) {
+    p.n_bins = b->n_bins;
+    p.log_spaced = b->log_spaced;
+    p.lo = b->lo;
+    if (b->n_bins > 0) {
+      p.inv_w = (double)b->n_bins / (b->hi - b->lo);
+      if (b->log_spaced) p.log_scale = (double)b->n_bins / std::log(b->hi / b->lo);
+    }
+    p.n_tx = b->n_tx;
+    p.n_ty = b->n_ty;
+    p.tmax = b->theta_max;
+    if (b->n_tx > 0) {
+      p.tsx = (double)b->n_tx / (2.0 * b->theta_max);
+      p.tsy = (double)b->n_ty / (2.0 * b->theta_max);
+    }
+    p.n_aeff = b->n_aeff;
+    if (b->n_aeff > 0) p.a_scale = (double)b->n_aeff / b->aeff_max;
+  }
+  p.wscale = std::ldexp(1.0, wbits);
+  p.gamma_ref = B->flat_energy ? 0.5 * (B->gamma_lo + B->gamma_hi) : B->gamma_mean;
+}
+
+struct DevInfo {
+  int sms = 0;
+  bool init = false;
+};
+std::mutex g_mu;
+DevInfo g_dev[64];
+
+int32_t device_sms(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_dev[dev].init) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return QS_ERR_CUDA;
+    g_dev[dev].sms = v;
+    g_dev[dev].init = true;
+  }
+  *sms = g_dev[dev].sms;
+  return QS_OK;
+}
+
+// Shared-memory plan of k_scatter.
+struct Plan {
+  int64_t nspec = 0, nmap = 0, naeff = 0;   // accumulator slots
+  size_t table_bytes = 0, hist_bytes = 0, red_bytes = 0, smem = 0;
+  bool hist_in_smem = false, wide = false;
+  int block = 256, grid = 1;
+  size_t ws_bytes = 0;
+  size_t off_spec = 0, off_map = 0, off_aeff = 0, off_part = 0;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void make_plan(Plan& pl, const qs_bins* b, int precision, bool weighted, int block, int grid_req,
+               int64_t n, int sms) {
+  pl.nspec = b->n_bins > 0 ? (int64_t)b->n_bins + 2 : 0;
+  pl.nmap = (b->n_tx > 0) ? (int64_t)b->n_tx * b->n_ty + 1 : 0;
+  pl.naeff = b->n_aeff > 0 ? (int64_t)b->n_aeff + 1 : 0;
+  pl.wide = weighted;
+  const size_t esz = weighted ? 8 : 4;
+  pl.table_bytes = align_up((size_t)kMaxPhase * (precision == QS_F64 ? 8 : 4), 16);
+  pl.red_bytes = (size_t)(1024 / 32) * kNumMom * sizeof(double);
+  pl.hist_bytes = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * esz, 16);
+  pl.hist_in_smem = pl.table_bytes + pl.red_bytes + pl.hist_bytes <= (size_t)kSmemLimit;
+  pl.smem = pl.table_bytes + pl.red_bytes + (pl.hist_in_smem ? pl.hist_bytes : 0);
+  pl.block = block;
+  // the grid is picked at launch from the occupancy of the kernel; the
+  // workspace holds partials for the largest grid that can be resident
+  int64_t gmax = (int64_t)sms * (2048 / block < 32 ? 2048 / block : 32);
+  if (grid_req > gmax) gmax = grid_req;
+  pl.grid = (int)gmax;
+  (void)n;
+  size_t off = 0;
+  pl.off_spec = off; off = align_up(off + (size_t)pl.nspec * 8, 256);
+  pl.off_map = off;  off = align_up(off + (size_t)pl.nmap * 8, 256);
+  pl.off_aeff = off; off = align_up(off + (size_t)pl.naeff * 8, 256);
+  pl.off_part = off; off = align_up(off + (size_t)gmax * kNumMom * 8, 256);
+  pl.ws_bytes = off;
+}
+
+// Persistent grid: as many CTAs as fit on the device at once, never more
+// than there are tiles of samples.
+int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int gmax) {
+  int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * (occ_per_sm > 0 ? occ_per_sm : 1);
+  int64_t tiles = (n + block - 1) / block;
+  if (tiles < 1) tiles = 1;
+  if (g > tiles) g = tiles;
+  if (g > gmax) g = gmax;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void build_table(const Params& p, T* sG) {
+  for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) sG[j] = (T)envelope_at(p, j);
+}
+
+// Fixed-order block reduction of kNumMom doubles; thread 0 returns sums.
+__device__ __forceinline__ void block_reduce_write(double (&acc)[kNumMom], double* red,
+                                                   double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNumMom; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp * kNumMom + k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumMom) {
+    const int nw = blockDim.x >> 5;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * kNumMom + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+template <typename T, typename H>
+__global__ void __launch_bounds__(512) k_scatter(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* sG = reinterpret_cast<T*>(smem);
+  double* red = reinterpret_cast<double*>(smem + (size_t)kMaxPhase * sizeof(T));
+  H* sh = reinterpret_cast<H*>(smem + (size_t)kMaxPhase * sizeof(T) +
+                               (size_t)(1024 / 32) * kNumMom * sizeof(double));
+  const int64_t nspec = p.n_bins > 0 ? (int64_t)p.n_bins + 2 : 0;
+  const int64_t nmap = p.n_tx > 0 ? (int64_t)p.n_tx * p.n_ty + 1 : 0;
+  const int64_t naeff = p.n_aeff > 0 ? (int64_t)p.n_aeff + 1 : 0;
+  H* hs = sh;
+  H* hm = sh + nspec;
+  H* ha = sh + nspec + nmap;
+
+  if (p.model != 0) build_table<T>(p, sG);
+  if (p.hist_in_smem)
+    for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+
+  double acc[kNumMom];
+#pragma unroll
+  for (int k = 0; k < kNumMom; ++k) acc[k] = 0.0;
+
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+    Sample s = eval_sample<T>(p, sG, i);
+    double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+    bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
+              isfinite(w) && w >= 0.0;
+    if (!ok) {
+      acc[8] += 1.0;
+      continue;
+    }
+    const double d = s.mu - p.gamma_ref;
+    acc[0] += w;
+    acc[1] += w * d;
+    acc[2] += w * d * d;
+    acc[3] += w * s.V;
+    acc[4] += w * (s.thx0 * s.thx0 + s.theta_e * s.theta_e);
+    acc[5] += w * (s.thy0 * s.thy0);
+    acc[6] += w * s.aeff;
+    acc[7] += w * s.gamma0;
+    const unsigned long long q =
+        p.weighted ? (unsigned long long)__double2ll_rn(w * p.wscale) : 1ull;
+    if (nspec) {
+      int b = energy_bin(p, s.gout);
+      int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+      if (p.hist_in_smem) atomicAdd(&hs[slot], (H)q);
+      else atomicAdd(&p.acc_spec[slot], q);
+    }
+    if (nmap) {
+      int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
+      int slot = c < 0 ? (int)(nmap - 1) : c;
+      if (p.hist_in_smem) atomicAdd(&hm[slot], (H)q);
+      else atomicAdd(&p.acc_map[slot], q);
+    }
+    if (naeff) {
+      int slot = aeff_bin(p, s.aeff);
+      if (p.hist_in_smem) atomicAdd(&ha[slot], (H)q);
+      else atomicAdd(&p.acc_aeff[slot], q);
+    }
+  }
+  block_reduce_write(acc, red, p.partials + (size_t)blockIdx.x * kNumMom);
+  if (p.hist_in_smem) {
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x)
+      if (hs[b]) atomicAdd(&p.acc_spec[b], (unsigned long long)hs[b]);
+    for (int64_t b = threadIdx.x; b < nmap; b += blockDim.x)
+      if (hm[b]) atomicAdd(&p.acc_map[b], (unsigned long long)hm[b]);
+    for (int64_t b = threadIdx.x; b < naeff; b += blockDim.x)
+      if (ha[b]) atomicAdd(&p.acc_aeff[b], (unsigned long long)ha[b]);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, double* spectrum,
+                                                   double* divmap, double* aeff_hist,
+                                                   qs_moments* mom) {
+  __shared__ double tot[kNumMom];
+  const double scale = p.weighted ? 1.0 / p.wscale : 1.0;
+  if (threadIdx.x < kNumMom) {
+    // Neumaier-compensated sum over CTA partials in CTA order
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < grid; ++b) {
+      double x = p.partials[(size_t)b * kNumMom + threadIdx.x];
+      double t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    tot[threadIdx.x] = s + c;
+  }
+  for (int b = threadIdx.x; b < p.n_bins; b += blockDim.x)
+    spectrum[b] = (double)p.acc_spec[b] * scale;
+  const int64_t nmap = p.n_tx > 0 ? (int64_t)p.n_tx * p.n_ty : 0;
+  for (int64_t b = threadIdx.x; b < nmap; b += blockDim.x) divmap[b] = (double)p.acc_map[b] * scale;
+  for (int b = threadIdx.x; b < p.n_aeff; b += blockDim.x)
+    aeff_hist[b] = (double)p.acc_aeff[b] * scale;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    qs_moments m;
+    const double W = tot[0];
+    m.W = W;
+    m.mean = m.spread = m.rel_spread = m.div_x = m.div_y = m.div = m.mean_aeff = 0.0;
+    m.mean_gamma0 = 0.0;
+    if (W > 0.0) {
+      const double m1 = tot[1] / W;
+      double var = tot[2] / W - m1 * m1 + tot[3] / W;
+      m.mean = p.gamma_ref + m1;
+      m.spread = sqrt(var > 0.0 ? var : 0.0);
+      m.rel_spread = m.spread / m.mean;
+      m.div_x = sqrt(tot[4] / W);
+      m.div_y = sqrt(tot[5] / W);
+      m.div = sqrt((tot[4] + tot[5]) / W);
+      m.mean_aeff = tot[6] / W;
+      m.mean_gamma0 = tot[7] / W;
+    }
+    m.under = p.n_bins > 0 ? (double)p.acc_spec[p.n_bins] * scale : 0.0;
+    m.over = p.n_bins > 0 ? (double)p.acc_spec[p.n_bins + 1] * scale : 0.0;
+    m.map_out = nmap ? (double)p.acc_map[nmap] * scale : 0.0;
+    m.nonfinite = tot[8];
+    *mom = m;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
+  __shared__ T sG[kMaxPhase];
+  if (p.model != 0) build_table<T>(p, sG);
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+    Sample s = eval_sample<T>(p, sG, i);
+    if (o.gamma0) o.gamma0[i] = s.gamma0;
+    if (o.aeff) o.aeff[i] = s.aeff;
+    if (o.mu) o.mu[i] = s.mu;
+    if (o.V) o.V[i] = s.V;
+    if (o.theta_e) o.theta_e[i] = s.theta_e;
+    if (o.theta_x) o.theta_x[i] = s.tx;
+    if (o.theta_y) o.theta_y[i] = s.ty;
+    if (o.gamma_out) o.gamma_out[i] = s.gout;
+    if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin(p, s.gout) : -1;
+    int ix = -1, iy = -1;
+    if (p.n_tx > 0) map_cell(p, s.tx, s.ty, &ix, &iy);
+    if (o.ix) o.ix[i] = ix;
+    if (o.iy) o.iy[i] = iy;
+    if (o.abin) o.abin[i] = p.n_aeff > 0 ? aeff_bin(p, s.aeff) : -1;
+  }
+}
+
+namespace {
+
+template <typename T, typename H>
+int32_t launch_scatter_t(const Params& p, const Plan& pl, int sms, int grid_req,
+                         cudaStream_t st, int* grid_out, const qs_exec* ex) {
+  auto kern = k_scatter<T, H>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
+        cudaSuccess)
+      return QS_ERR_CUDA;
+    attr_set[dev] = true;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem) !=
+      cudaSuccess)
+    return QS_ERR_CUDA;
+  const int grid = pick_grid(occ, sms, pl.block, grid_req, p.n, pl.grid);
+  if (ex && ex->ev_start &&
+      cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_start), st) != cudaSuccess)
+    return QS_ERR_CUDA;
+  kern<<<grid, pl.block, pl.smem, st>>>(p);
+  *grid_out = grid;
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  if (ex && ex->ev_stop &&
+      cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_stop), st) != cudaSuccess)
+    return QS_ERR_CUDA;
+  return QS_OK;
+}
+
+}  // namespace
+}  // namespace qs
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace qs;
+
+extern "C" int32_t qs_version(void) { return QS_VERSION; }
+
+extern "C" const char* qs_status_string(int32_t s) {
+  switch (s) {
+    case QS_OK: return "ok";
+    case QS_ERR_INVALID_ARG: return "invalid argument";
+    case QS_ERR_CUDA: return "CUDA error";
+    case QS_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case QS_ERR_UNSUPPORTED: return "unsupported";
+    case QS_ERR_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown status";
+  }
+}
+
+extern "C" size_t qs_workspace_bytes(const qs_bins* bins, const qs_exec* exec, int64_t n) {
+  int prec, wbits, block, grid, sms;
+  if (validate_bins(bins) != QS_OK || n < 0) return 0;
+  if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
+  if (device_sms(&sms) != QS_OK) return 0;
+  Plan pl;
+  // the weighted plan is never smaller than the unweighted one
+  make_plan(pl, bins, prec, true, block, grid, n, sms);
+  return pl.ws_bytes;
+}
+
+extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
+                              const qs_samples* samples, const qs_bins* bins,
+                              const qs_exec* exec, double* d_spectrum, double* d_divmap,
+                              double* d_aeff_hist, qs_moments* d_moments, void* d_workspace,
+                              size_t ws_bytes, void* stream) {
+  int32_t st;
+  if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
+      (st = validate_samples(samples)) || (st = validate_bins(bins)))
+    return st;
+  int prec, wbits, block, grid, sms;
+  if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
+  if (!d_moments) return QS_ERR_INVALID_ARG;
+  if (bins->n_bins > 0 && !d_spectrum) return QS_ERR_INVALID_ARG;
+  if (bins->n_tx > 0 && !d_divmap) return QS_ERR_INVALID_ARG;
+  if (bins->n_aeff > 0 && !d_aeff_hist) return QS_ERR_INVALID_ARG;
+  if ((st = device_sms(&sms))) return st;
+  Plan pl;
+  make_plan(pl, bins, prec, samples->w != nullptr, block, grid, samples->n, sms);
+  Plan plw;
+  make_plan(plw, bins, prec, true, block, grid, samples->n, sms);
+  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < plw.ws_bytes)
+    return QS_ERR_WORKSPACE;
+
+  Params p;
+  fill_params(p, laser, beam, samples, bins, wbits);
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  p.acc_spec = reinterpret_cast<unsigned long long*>(ws + pl.off_spec);
+  p.acc_map = reinterpret_cast<unsigned long long*>(ws + pl.off_map);
+  p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + pl.off_aeff);
+  p.partials = reinterpret_cast<double*>(ws + pl.off_part);
+  p.hist_in_smem = pl.hist_in_smem ? 1 : 0;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+
+  if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return QS_ERR_CUDA;
+  int g = 1;
+  if (prec == QS_F64) {
+    st = p.weighted ? launch_scatter_t<double, unsigned long long>(p, pl, sms, grid, cs, &g, exec)
+                    : launch_scatter_t<double, unsigned int>(p, pl, sms, grid, cs, &g, exec);
+  } else {
+    st = p.weighted ? launch_scatter_t<float, unsigned long long>(p, pl, sms, grid, cs, &g, exec)
+                    : launch_scatter_t<float, unsigned int>(p, pl, sms, grid, cs, &g, exec);
+  }
+  if (st) return st;
+  k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_moments);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
+                                   const qs_samples* samples, const qs_bins* bins,
+                                   const qs_exec* exec, const qs_sample_out* out, void* stream) {
+  int32_t st;
+  if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
+      (st = validate_samples(samples)))
+    return st;
+  if (bins && (st = validate_bins(bins))) return st;
+  if (!out) return QS_ERR_INVALID_ARG;
+  int prec, wbits, block, grid, sms;
+  if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
+  if ((st = device_sms(&sms))) return st;
+  if (samples->n == 0) return QS_OK;
+  Params p;
+  fill_params(p, laser, beam, samples, bins, wbits);
+  int64_t tiles = (samples->n + 255) / 256;
+  int g = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (prec == QS_F64) k_eval<double><<<g, 256, 0, cs>>>(p, *out);
+  else k_eval<float><<<g, 256, 0, cs>>>(p, *out);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}

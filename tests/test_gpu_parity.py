@@ -1,0 +1,384 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars (floating point): per-sample FP64 results to rel 1e-12; moments to rel
+1e-12 (FP64 path) and 1e-5 (FP32 path); spectra to 1e-4 of the total weight
+in L1.  Bin indices are bit-exact for every sample whose oracle value lies
+farther from a bin edge than the path's per-sample error bound.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_09348_gb300 import inputs as I
+from paper_2308_09348_gb300 import MOMENT_FIELDS, QsError, qs_eval_samples, qs_scatter
+from paper_2308_09348_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+# per-sample error bounds of the two paths (relative, on mu; V; gamma_out)
+TOL = {"f64": dict(mu=1e-12, V=1e-10, aeff=1e-13, gout=1e-12),
+       "f32": dict(mu=4e-6, V=2e-4, aeff=None, gout=4e-6)}
+MOM_TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_09348_gb300 import build
+    build.build()
+
+
+def dev(xi, w=None):
+    xt = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in xi]
+    wt = None if w is None else torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    return xt, wt
+
+
+def f64(xi):
+    return [None if a is None else a.astype(np.float64) for a in xi]
+
+
+def cfg2(n, **laser_kw):
+    wl = I.full_qfp(n)
+    L = I.Laser(**{**wl.laser.__dict__, **laser_kw})
+    xi, _ = I.workload_inputs(wl, n)
+    return wl, L, xi
+
+
+def away_from_edges(g_ref, tol_abs, bins):
+    """Mask of samples whose oracle energy is farther than tol_abs from any
+    energy-bin edge (or the under/over boundaries)."""
+    if bins.log_spaced:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.log(np.maximum(g_ref, 1e-300) / bins.lo) * (bins.n_bins / math.log(bins.hi / bins.lo))
+            dt = tol_abs / np.maximum(g_ref, 1e-300) * (bins.n_bins / math.log(bins.hi / bins.lo))
+    else:
+        t = (g_ref - bins.lo) * (bins.n_bins / (bins.hi - bins.lo))
+        dt = tol_abs * (bins.n_bins / (bins.hi - bins.lo))
+    frac = np.abs(t - np.round(t))
+    return frac > dt
+
+
+def _relerr(a, b, floor=0.0):
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+def compare_samples(rec, ref, prec, bins, check_bins=True):
+    """Element-wise comparison; prints the error profile before asserting."""
+    tol = TOL[prec]
+    g = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in rec.items()}
+    vmax = max(float(np.max(ref["V"])), 1e-300)
+    sv = math.sqrt(vmax)
+    # a_eff = a0 q^-1/2 exp(-X): in FP32 the argument X carries ~6 ulp of
+    # relative rounding (rho^2, 1/W0^2, 1/q, log2 e) that the exponential turns
+    # into an absolute error of X 6 2^-24; ex2, rsqrt and the products add a few
+    # ulp more: bound (3 X + 16) 2^-23
+    X = np.log(np.maximum(np.max(ref["aeff"]), 1e-300) / np.maximum(ref["aeff"], 1e-300))
+    a_tol = tol["aeff"] if prec == "f64" else (3.0 * X + 16.0) * 2.0 ** -23
+    gabs = tol["gout"] * np.abs(ref["gamma_out"]) + tol["V"] * sv * 6
+    prof = {"gamma0": float(np.max(_relerr(g["gamma0"], ref["gamma0"]))),
+            "aeff": float(np.max(_relerr(g["aeff"], ref["aeff"], 1e-300) / a_tol)),
+            "mu": float(np.max(_relerr(g["mu"], ref["mu"]))),
+            "V": float(np.max(np.abs(g["V"] - ref["V"]) / (np.abs(ref["V"]) + 1e-6 * vmax))),
+            "gout_abs/tol": float(np.max(np.abs(g["gamma_out"] - ref["gamma_out"]) / gabs))}
+    print(f"[{prec}] error profile:", prof)
+    assert prof["gamma0"] <= 1e-15
+    assert prof["aeff"] <= 1.0
+    assert prof["mu"] <= tol["mu"]
+    assert prof["V"] <= tol["V"]
+    assert prof["gout_abs/tol"] <= 1.0
+    if check_bins and bins is not None and bins.n_bins > 0:
+        ok = away_from_edges(ref["gamma_out"], gabs, bins)
+        print(f"[{prec}] samples near an energy-bin edge: {int((~ok).sum())} of {ok.size}")
+        assert ok.mean() > 0.99
+        np.testing.assert_array_equal(g["bin"][ok], ref["bin"][ok])
+    if bins is not None and bins.n_aeff > 0:
+        fa = ref["aeff"] * bins.n_aeff / bins.aeff_max
+        a_ok = np.abs(fa - np.round(fa)) > 2 * a_tol * fa + 1e-12
+        np.testing.assert_array_equal(g["abin"][a_ok], ref["abin"][a_ok])
+    return g
+
+
+# ---------------------------------------------------------------------------
+# per-sample records
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model,env", [(I.MODEL_LL, I.ENV_GAUSS), (I.MODEL_QFP, I.ENV_GAUSS),
+                                       (I.MODEL_QFP, I.ENV_SIN2)])
+def test_eval_matches_oracle_elementwise(prec, model, env):
+    n = 2500          # ~10 tiles of 256 and a ragged tail
+    wl, L, xi = cfg2(n, model=model, envelope=env)
+    xt, _ = dev(xi)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.evaluate(L, wl.beam, wl.bins, f64(xi))
+    compare_samples(rec, ref, prec, wl.bins)
+
+
+def test_eval_float64_streams_and_missing_optional_streams():
+    n = 777
+    wl, L, xi = cfg2(n)
+    xi64 = f64(xi)
+    xi64[5] = None      # theta_y stream absent: reads as zeros
+    xi64[6] = None
+    xt, _ = dev(xi64)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision="f64")
+    ref = oracle.evaluate(L, wl.beam, wl.bins, xi64)
+    compare_samples(rec, ref, "f64", wl.bins)
+
+
+# ---------------------------------------------------------------------------
+# whole-beam integration
+# ---------------------------------------------------------------------------
+
+def compare_scatter(out, ref, prec, W):
+    res = out.result()
+    m = res["moments"]
+    keys = ("W", "mean", "spread", "rel_spread", "div_x", "div_y", "div", "mean_aeff",
+            "mean_gamma0")
+    errs = {k: abs(m[k] - ref["moments"][k]) / max(abs(ref["moments"][k]), 1e-300) for k in keys}
+    spec = res["spectrum"].cpu().numpy()
+    l1 = np.abs(spec - ref["spectrum"]).sum() + abs(m["under"] - ref["moments"]["under"]) + \
+        abs(m["over"] - ref["moments"]["over"])
+    print(f"[{prec}] moment rel errors:", errs, "spectrum L1/W:", l1 / W)
+    for k in keys:
+        assert errs[k] <= MOM_TOL[prec], (k, m[k], ref["moments"][k])
+    assert l1 <= 1e-4 * W, l1 / W
+    if ref["divmap"].size:
+        dm = res["divmap"].cpu().numpy().reshape(ref["divmap"].shape)
+        assert np.abs(dm - ref["divmap"]).sum() <= 1e-4 * W
+    if ref["aeff_hist"].size:
+        assert np.abs(res["aeff_hist"].cpu().numpy() - ref["aeff_hist"]).sum() <= 1e-4 * W
+    assert m["nonfinite"] == 0
+    return res
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_scatter_matches_oracle(prec, model, weighted):
+    n = 5003
+    wl, L, xi = cfg2(n, model=model)
+    w = I.rng(7).uniform(0.25, 2.0, n).astype(np.float32) if weighted else None
+    xt, wt = dev(xi, w)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi), None if w is None else w.astype(np.float64))
+    W = float(n if w is None else w.astype(np.float64).sum())
+    res = compare_scatter(out, ref, prec, W)
+    if not weighted:
+        # unit weights: histogram entries are integer counts
+        spec = res["spectrum"].cpu().numpy()
+        assert np.array_equal(spec, np.round(spec))
+
+
+def test_gauss_hermite_tiny_config_f64():
+    """32^3 Gauss-Hermite nodes, LL model, 256-bin spectrum, weighted FP64."""
+    wl = I.tiny_gauss_hermite()
+    xi, w = I.workload_inputs(wl)
+    xt, wt = dev(xi, w)
+    out = qs_scatter(wl.laser, wl.beam, xt, wl.bins, w=wt, precision="f64", weight_frac_bits=48)
+    torch.cuda.synchronize()
+    ref = oracle.scatter(wl.laser, wl.beam, wl.bins, xi, w)
+    compare_scatter(out, ref, "f64", float(w.sum()))
+    # fixed-point weights: every bin within n * 2^-49 of the oracle's mass
+    spec = out.spectrum.cpu().numpy()
+    assert np.max(np.abs(spec - ref["spectrum"])) <= len(w) * 2.0 ** -49 + 1e-15
+
+
+def test_broadband_log_bins_flat_energy():
+    wl = I.broadband_qfp(4099)
+    L = I.Laser(**{**wl.laser.__dict__, "n_phase": 256})
+    xi, _ = I.workload_inputs(wl, 4099)
+    xt, _ = dev(xi)
+    for prec in ("f64", "f32"):
+        out = qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+        rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+        torch.cuda.synchronize()
+        ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi))
+        compare_scatter(out, ref, prec, 4099.0)
+        compare_samples(rec, oracle.evaluate(L, wl.beam, wl.bins, f64(xi)), prec, wl.bins)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_input():
+    wl, L, xi = cfg2(4)
+    xt = [torch.empty(0, dtype=torch.float32, device="cuda") for _ in range(8)]
+    out = qs_scatter(L, wl.beam, xt, wl.bins)
+    torch.cuda.synchronize()
+    assert all(v == 0 for v in out.moments.cpu().tolist())
+    assert float(out.spectrum.abs().sum()) == 0 and float(out.divmap.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("n", [1, 31, 255, 256, 257])
+def test_tiny_and_ragged_sizes(n):
+    wl, L, xi = cfg2(n)
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f64")
+    torch.cuda.synchronize()
+    compare_scatter(out, oracle.scatter(L, wl.beam, wl.bins, f64(xi)), "f64", float(n))
+
+
+def test_zero_intensity_is_identity():
+    wl, L, xi = cfg2(3000, a0=0.0)
+    xt, _ = dev(xi)
+    for prec in ("f64", "f32"):
+        rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+        assert torch.equal(rec["mu"], rec["gamma0"])
+        assert float(rec["V"].abs().max()) == 0.0
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f64")
+    g0 = rec["gamma0"].cpu().numpy()
+    h, _ = np.histogram(g0, bins=wl.bins.n_bins, range=(wl.bins.lo, wl.bins.hi))
+    assert np.array_equal(out.spectrum.cpu().numpy(), h.astype(float))
+
+
+@pytest.mark.parametrize("n_phase", [1, 4096])
+def test_phase_count_limits(n_phase):
+    wl, L, xi = cfg2(600, n_phase=n_phase)
+    xt, _ = dev(xi)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision="f64")
+    compare_samples(rec, oracle.evaluate(L, wl.beam, wl.bins, f64(xi)), "f64", wl.bins)
+
+
+def test_large_map_uses_global_accumulators():
+    """A 700x700 divergence map does not fit in shared memory."""
+    wl, L, xi = cfg2(3001)
+    bins = I.Bins(**{**wl.bins.__dict__, "n_tx": 700, "n_ty": 700})
+    xt, _ = dev(xi)
+    for prec in ("f64", "f32"):
+        out = qs_scatter(L, wl.beam, xt, bins, precision=prec)
+        torch.cuda.synchronize()
+        compare_scatter(out, oracle.scatter(L, wl.beam, bins, f64(xi)), prec, 3001.0)
+
+
+def test_everything_outside_the_bins():
+    wl, L, xi = cfg2(1000)
+    bins = I.Bins(n_bins=16, lo=1e6, hi=2e6, n_tx=8, n_ty=8, theta_max=1e-9, n_aeff=4,
+                  aeff_max=1e-12)
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, bins, precision="f64")
+    m = out.moments_dict()
+    assert m["under"] == 1000 and m["over"] == 0 and m["map_out"] == 1000
+    assert float(out.spectrum.sum()) == 0 and float(out.aeff_hist.sum()) == 0
+
+
+def test_zero_and_tiny_weights():
+    n = 2000
+    wl, L, xi = cfg2(n)
+    w = I.rng(8).uniform(0, 1, n)
+    w[::3] = 0.0
+    w = w.astype(np.float32)
+    xt, wt = dev(xi, w)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision="f64")
+    torch.cuda.synchronize()
+    ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi), w.astype(np.float64))
+    compare_scatter(out, ref, "f64", float(w.astype(np.float64).sum()))
+
+
+def test_nonfinite_samples_are_excluded_and_counted():
+    n = 1000
+    wl, L, xi = cfg2(n)
+    xi = [a.copy() for a in xi]
+    xi[0][[3, 500]] = np.nan
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f64")
+    m = out.moments_dict()
+    assert m["nonfinite"] == 2 and m["W"] == n - 2
+
+
+def test_workspace_too_small_is_rejected():
+    wl, L, xi = cfg2(100)
+    xt, _ = dev(xi)
+    out = B.Outputs(wl.bins, 100)
+    out.ws_bytes = 64
+    with pytest.raises(QsError) as e:
+        qs_scatter(L, wl.beam, xt, wl.bins, out=out)
+    assert e.value.status == B.QS_ERR_WORKSPACE
+
+
+# ---------------------------------------------------------------------------
+# determinism, launch shapes, graph capture
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_repeated_calls_are_bit_identical(prec):
+    wl, L, xi = cfg2(20000)
+    xt, _ = dev(xi)
+    a = qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+    ma, sa = a.moments.clone(), a.spectrum.clone()
+    b = qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+    assert torch.equal(ma, b.moments) and torch.equal(sa, b.spectrum)
+
+
+@pytest.mark.parametrize("block,grid", [(64, 3), (128, 0), (512, 0), (256, 1000)])
+def test_launch_shapes_agree(block, grid):
+    wl, L, xi = cfg2(9000)
+    xt, _ = dev(xi)
+    ref = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32")
+    o = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32", block=block, grid=grid)
+    assert torch.equal(ref.spectrum, o.spectrum) and torch.equal(ref.divmap, o.divmap)
+    rm, om = ref.moments.cpu().numpy(), o.moments.cpu().numpy()
+    np.testing.assert_allclose(om, rm, rtol=1e-13)
+
+
+def test_graph_capture_replay():
+    wl, L, xi = cfg2(8000)
+    xt, _ = dev(xi)
+    out = B.Outputs(wl.bins, 8000)
+    qs_scatter(L, wl.beam, xt, wl.bins, out=out)      # warm-up (first-use set-up)
+    torch.cuda.synchronize()
+    ref_m = out.moments.clone()
+    out.moments.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        qs_scatter(L, wl.beam, xt, wl.bins, out=out, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out.moments, ref_m)
+
+
+# ---------------------------------------------------------------------------
+# full-size workload (2^26 samples, QFP, 512 phase steps), as benchmarked
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_full_size_quantum_workload_sampled_parity():
+    wl = I.full_qfp()
+    n = wl.n
+    xi, _ = I.workload_inputs(wl)
+    xt, _ = dev(xi)
+    out = qs_scatter(wl.laser, wl.beam, xt, wl.bins, precision="f32")
+    rec = qs_eval_samples(wl.laser, wl.beam, xt, wl.bins, precision="f32")
+    torch.cuda.synchronize()
+    m = out.moments_dict()
+    # weight conservation at full size
+    assert m["W"] == n and m["nonfinite"] == 0
+    assert float(out.spectrum.sum()) + m["under"] + m["over"] == n
+    assert float(out.divmap.sum()) + m["map_out"] == n
+    # the fused histogram equals the histogram of the per-sample records
+    b = rec["bin"].long()
+    cnt = torch.bincount(b.clamp(min=0, max=wl.bins.n_bins - 1)[(b >= 0) & (b < wl.bins.n_bins)],
+                         minlength=wl.bins.n_bins)
+    assert torch.equal(cnt.double(), out.spectrum)
+    # fused moments equal moments of the per-sample records (reduction order only)
+    mu = rec["mu"]
+    mean = float(mu.mean())
+    var = float(((mu - mean) ** 2).mean() + rec["V"].mean())
+    assert abs(m["mean"] / mean - 1) < 1e-12
+    assert abs(m["spread"] / math.sqrt(var) - 1) < 1e-10
+    # sampled per-sample parity with the oracle across the whole index range
+    idx = np.unique(np.concatenate([np.arange(64), n - 1 - np.arange(64),
+                                    I.rng(9).integers(0, n, 1024)]))
+    sub = [a[idx].astype(np.float64) for a in xi]
+    ref = oracle.evaluate(wl.laser, wl.beam, wl.bins, sub)
+    got = {k: v[torch.from_numpy(idx).cuda()] for k, v in rec.items()}
+    compare_samples(got, ref, "f32", wl.bins)
