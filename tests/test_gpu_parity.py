@@ -19,8 +19,8 @@ from paper_2308_09348_gb300 import binding as B
 pytestmark = pytest.mark.gpu
 
 # per-sample error bounds of the two paths (relative, on mu; V; gamma_out)
-TOL = {"f64": dict(mu=1e-12, V=1e-10, aeff=1e-13, gout=1e-12),
-       "f32": dict(mu=4e-6, V=2e-4, aeff=None, gout=4e-6)}
+TOL = {"f64": dict(mu=1e-12, V=1e-10, aeff=1e-13),
+       "f32": dict(mu=4e-6, V=2e-5, aeff=None)}
 MOM_TOL = {"f64": 1e-12, "f32": 1e-5}
 
 
@@ -79,7 +79,10 @@ def compare_samples(rec, ref, prec, bins, check_bins=True):
     # ulp more: bound (3 X + 16) 2^-23
     X = np.log(np.maximum(np.max(ref["aeff"]), 1e-300) / np.maximum(ref["aeff"], 1e-300))
     a_tol = tol["aeff"] if prec == "f64" else (3.0 * X + 16.0) * 2.0 ** -23
-    gabs = tol["gout"] * np.abs(ref["gamma_out"]) + tol["V"] * sv * 6
+    # gamma_out = mu + sqrt(V) xi7: its error is bounded by that of mu plus half
+    # the relative error of V times |gamma_out - mu|
+    gabs = tol["mu"] * np.abs(ref["mu"]) + 0.5 * tol["V"] * np.abs(ref["gamma_out"] - ref["mu"]) \
+        + 1e-3 * tol["V"] * sv + 1e-300
     prof = {"gamma0": float(np.max(_relerr(g["gamma0"], ref["gamma0"]))),
             "aeff": float(np.max(_relerr(g["aeff"], ref["aeff"], 1e-300) / a_tol)),
             "mu": float(np.max(_relerr(g["mu"], ref["mu"]))),
