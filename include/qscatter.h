@@ -213,6 +213,37 @@ int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_sam
                         const qs_bins* bins, const qs_exec* exec, const qs_sample_out* out,
                         void* stream);
 
+/*
+ * qs_scatter_noalloc: qs_scatter for callers that cannot allocate device
+ * memory -- plugins and embedded components running inside a host
+ * application that owns every device allocation (a fixed pool, or no
+ * allocator handle at all), so neither they nor the library may call
+ * cudaMalloc.  The paper has no counterpart; this is a library convenience.
+ *
+ * Same arguments, validation and results as qs_scatter, minus the
+ * workspace: the scratch space (integer histogram accumulators and per-CTA
+ * moment partials) is a file-scope device array of QS_NOALLOC_SCRATCH_BYTES
+ * bytes that every GPU which loads the library holds until the process exits.
+ *   - Limit: a request whose scratch (qs_workspace_bytes of the same bins
+ *     and options) exceeds QS_NOALLOC_SCRATCH_BYTES returns QS_ERR_WORKSPACE
+ *     before any launch.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   - Sharing: all calls on a device share the one array; each call clears
+ *     the accumulators it uses before its kernels run.  Calls whose kernels
+ *     overlap on the GPU (different streams, or different host threads
+ *     without ordering) race on the array and corrupt each other's results:
+ *     order them on one stream.
+ *   - The library calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define QS_NOALLOC_SCRATCH_BYTES ((size_t)1 << 20)
+
+int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
+                           const qs_samples* samples, const qs_bins* bins, const qs_exec* exec,
+                           double* d_spectrum, double* d_divmap, double* d_aeff_hist,
+                           qs_moments* d_moments, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

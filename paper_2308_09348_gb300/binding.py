@@ -105,6 +105,10 @@ def _lib():
                                           C.POINTER(qs_samples), C.POINTER(qs_bins),
                                           C.POINTER(qs_exec), C.POINTER(qs_sample_out), _VP]
             L.qs_eval_samples.restype = C.c_int32
+            L.qs_scatter_noalloc.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                             C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                             C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP]
+            L.qs_scatter_noalloc.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -274,3 +278,36 @@ def qs_eval_samples(laser, beam, xi, bins=None, precision="f32", stream=None) ->
                                 C.byref(o), _stream_ptr(stream))
     _check(st, "qs_eval_samples")
     return res
+
+
+class _OutputsNoWorkspace(Outputs):
+    """Output buffers only (qs_scatter_noalloc needs no workspace)."""
+
+    def __init__(self, bins: _inputs.Bins, device):
+        self.bins = bins
+        self.spectrum = torch.zeros(max(bins.n_bins, 0), dtype=torch.float64, device=device)
+        nmap = bins.n_tx * bins.n_ty if (bins.n_tx > 0 and bins.n_ty > 0) else 0
+        self.divmap = torch.zeros(nmap, dtype=torch.float64, device=device)
+        self.aeff_hist = torch.zeros(max(bins.n_aeff, 0), dtype=torch.float64, device=device)
+        self.moments = torch.zeros(len(MOMENT_FIELDS), dtype=torch.float64, device=device)
+        self.workspace = None
+        self.ws_ptr = None
+        self.ws_bytes = 0
+
+
+def qs_scatter_noalloc(laser, beam, xi, bins, w=None, precision="f32", out: Outputs | None = None,
+                       block=0, grid=0, weight_frac_bits=0, stream=None) -> Outputs:
+    """qs_scatter without a workspace: the library's static device scratch is
+    used (for callers that cannot allocate device memory).  ``out`` supplies
+    the output buffers; its workspace, if any, is not touched."""
+    s, keep = make_samples(xi, w)
+    if out is None:
+        out = _OutputsNoWorkspace(bins, keep[0].device)
+    L, B, Bn = make_laser(laser), make_beam(beam), make_bins(bins)
+    E = make_exec(precision, weight_frac_bits, block, grid)
+    st = _lib().qs_scatter_noalloc(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
+                                   _ptr_or_none(out.spectrum), _ptr_or_none(out.divmap),
+                                   _ptr_or_none(out.aeff_hist), out.moments.data_ptr(),
+                                   _stream_ptr(stream))
+    _check(st, "qs_scatter_noalloc")
+    return out

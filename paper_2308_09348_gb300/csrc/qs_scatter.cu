@@ -566,3 +566,54 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   else k_eval<float><<<g, 256, 0, cs>>>(p, *out);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// qs_scatter_noalloc: the scratch space lives in a file-scope device array
+// instead of a caller workspace (for callers that cannot allocate).
+// ---------------------------------------------------------------------------
+namespace qs {
+namespace {
+
+// Shared by every call on a device; held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QS_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a stand-in for the symbol, never a device
+// address, so it is looked up once per device with that device current.
+int32_t noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+      return QS_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QS_OK;
+}
+
+}  // namespace
+}  // namespace qs
+
+extern "C" int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
+                                      const qs_samples* samples, const qs_bins* bins,
+                                      const qs_exec* exec, double* d_spectrum, double* d_divmap,
+                                      double* d_aeff_hist, qs_moments* d_moments, void* stream) {
+  // the size check comes first, so an oversized request fails before any
+  // device set-up; qs_scatter then validates everything else
+  if (validate_bins(bins) != QS_OK || !samples) return QS_ERR_INVALID_ARG;
+  const size_t need = qs_workspace_bytes(bins, exec, samples->n);
+  if (need == 0) return QS_ERR_INVALID_ARG;
+  if (need > QS_NOALLOC_SCRATCH_BYTES) return QS_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  int32_t st = noalloc_scratch(&scratch);
+  if (st != QS_OK) return st;
+  // qs_scatter zeroes the accumulators on the stream before its kernels run
+  return qs_scatter(laser, beam, samples, bins, exec, d_spectrum, d_divmap, d_aeff_hist,
+                    d_moments, scratch, QS_NOALLOC_SCRATCH_BYTES, stream);
+}
