@@ -30,18 +30,20 @@ METRIC = "beam-sample evals/s"
 UNIT = "samples/s"
 
 # Arithmetic per phase cell of the QFP integration (FP32 path), counted from
-# the model's expression: 4 base-2 logarithms, 2 base-2 exponentials and 2
-# reciprocals (MUFU; an ex2 issues at twice the rate of lg2/rcp on this GPU,
-# so it costs half a slot) and 42 FMA-pipe operations (add, mul, fma).
+# the model's expression: 4 base-2 logarithms (two logs, two powers), 1
+# reciprocal (the mean energy) and 3 base-2 exponentials (two powers, and
+# 1/(1+1.7 chi) as the exponential of a logarithm already taken) on the MUFU
+# pipe, where an ex2 issues at twice the rate of lg2/rcp on this GPU (half a
+# slot); and 42 FMA-pipe operations (add, mul, fma).
 QFP_FMA_OPS_PER_STEP = 42
-QFP_MUFU_SLOTS_PER_STEP = 4 + 2 + 2 * 0.5
+QFP_MUFU_SLOTS_PER_STEP = 4 + 1 + 3 * 0.5
 FMA_LANES_PER_SM = 128
 MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"eaa24b023ac21359": 8 * (268.83e6 + 4.01e6)}
+TRAFFIC_BY_SOURCE = {"cb4af76aae387b1f": 8 * (268.75e6 + 4.39e6)}
 
 
 def parse():

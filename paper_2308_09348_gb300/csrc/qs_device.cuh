@@ -94,6 +94,22 @@ __device__ __forceinline__ double envelope_at(const Params& p, int j) {
   return s * s;
 }
 
+// Shared-memory phase table: FP64 path G_j; FP32 path {G_j, G_j, G_j^2,
+// G_j^2} (the square taken in double, then rounded), so one 16-byte load
+// gives both operands already paired for the two samples a thread carries.
+template <typename T> struct Tab;
+template <> struct Tab<float> { using type = float4; };
+template <> struct Tab<double> { using type = double; };
+
+__device__ __forceinline__ void table_entry(const Params& p, int j, float4* t) {
+  const double G = envelope_at(p, j);
+  const float g = (float)G, g2 = (float)(G * G);
+  t[j] = make_float4(g, g, g2, g2);
+}
+__device__ __forceinline__ void table_entry(const Params& p, int j, double* t) {
+  t[j] = envelope_at(p, j);
+}
+
 struct Sample {
   double gamma0, aeff, mu, V, theta_e, thx0, thy0, tx, ty, gout;
 };
@@ -106,14 +122,16 @@ struct Sample {
 //   h2(chi) = B2^(-7/6), B2 = 1 + (1+4.1 chi) ln(1+12.93 chi) + 4.75 chi^2
 //   K = (2/3) R_c A^2, D1 = -K mu^2 g, dD1/dgamma = -K mu (2g + chi g'),
 //   D2 = (55/(16 sqrt3)) K mu^3 chi h2.
-// Returns du = 1/mu_f - 1/gamma0 and V_f.
-template <typename T>
-__device__ __forceinline__ void qfp_integrate(const Params& p, const T* __restrict__ sG, T a,
-                                              T g0, T& du_out, T& V_out) {
-  const T LN2 = (T)0.69314718055994530942;
-  const T cK = (T)p.cK, cchi = (T)p.cchi, h = (T)p.h;
-  const T c55 = (T)(55.0 / (16.0 * 1.7320508075688772935));
-  const T hh2 = (T)(0.5 * p.h * p.h);
+// Returns du = 1/mu_f - 1/gamma0 and V_f.  FP64 path: written as the
+// equations read.
+__device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
+                                              double a, double g0, double& du_out,
+                                              double& V_out) {
+  typedef double T;
+  const T LN2 = 0.69314718055994530942;
+  const T cK = p.cK, cchi = p.cchi, h = p.h;
+  const T c55 = 55.0 / (16.0 * 1.7320508075688772935);
+  const T hh2 = 0.5 * p.h * p.h;
   T du = 0, V = 0, gprev = 1;
   const int N = p.n_phase;
 #pragma unroll 2
@@ -121,25 +139,25 @@ __device__ __forceinline__ void qfp_integrate(const Params& p, const T* __restri
     T A = a * sG[j];
     T K = cK * A * A;
     T hK = h * K;
-    T dum = du + (T)0.5 * hK * gprev;
-    T mu = g0 * M<T>::rcp((T)1 + g0 * dum);
+    T dum = du + 0.5 * hK * gprev;
+    T mu = g0 / (1.0 + g0 * dum);
     T chi = cchi * mu * A;
     // Gaunt factor and chi g'(chi)
-    T x1 = (T)1 + (T)1.7 * chi;
-    T L1 = LN2 * M<T>::lg2(x1);
-    T opc = (T)1 + chi;
-    T B = (T)1 + (T)4.8 * opc * L1 + (T)2.44 * chi * chi;
-    T t = M<T>::ex2((T)(-1.0 / 3.0) * M<T>::lg2(B));     // B^(-1/3)
+    T x1 = 1.0 + 1.7 * chi;
+    T L1 = LN2 * log2(x1);
+    T opc = 1.0 + chi;
+    T B = 1.0 + 4.8 * opc * L1 + 2.44 * chi * chi;
+    T t = exp2((-1.0 / 3.0) * log2(B));     // B^(-1/3)
     T g = t * t;
-    T dB = (T)4.8 * L1 + (T)(4.8 * 1.7) * opc * M<T>::rcp(x1) + (T)4.88 * chi;
-    T chig1 = (T)(-2.0 / 3.0) * g * (t * t * t) * dB * chi;
+    T dB = 4.8 * L1 + (4.8 * 1.7) * opc / x1 + 4.88 * chi;
+    T chig1 = (-2.0 / 3.0) * g * (t * t * t) * dB * chi;
     // second-moment factor
-    T L2 = LN2 * M<T>::lg2((T)1 + (T)12.93 * chi);
-    T B2 = (T)1 + ((T)1 + (T)4.1 * chi) * L2 + (T)4.75 * chi * chi;
-    T h2 = M<T>::ex2((T)(-7.0 / 6.0) * M<T>::lg2(B2));
+    T L2 = LN2 * log2(1.0 + 12.93 * chi);
+    T B2 = 1.0 + (1.0 + 4.1 * chi) * L2 + 4.75 * chi * chi;
+    T h2 = exp2((-7.0 / 6.0) * log2(B2));
     // updates
     du = du + hK * g;
-    T lam = (T)-2 * K * mu * ((T)2 * g + chig1);
+    T lam = -2.0 * K * mu * (2.0 * g + chig1);
     T D2 = c55 * K * mu * mu * mu * chi * h2;
     T r = lam * V + D2;
     V = V + h * r + hh2 * lam * r;
@@ -149,12 +167,80 @@ __device__ __forceinline__ void qfp_integrate(const Params& p, const T* __restri
   V_out = V;
 }
 
-// One beam sample through the model, in the paper's order.
+// FP32 path of the same scheme for TWO samples at once, arranged for the
+// GB300 issue slots.  Every FMA-pipe operation is a packed f32x2 instruction
+// (fma/mul/add .rn on float2, sm_100+), so one issue slot serves both
+// samples; the transcendentals are single MUFU lg2/ex2/rcp instructions per
+// sample.  Per sample the constants c1 = h (2/3) R_c a^2 and ca = cchi a are
+// folded in; 1/(1+1.7 chi) is ex2(-lg2(1+1.7 chi)) (ex2 issues at twice the
+// rate of rcp); the step works with h-scaled rates:
+//   hK = c1 G^2, hlam = h lambda = -2 hK mu s, s = 2g + chi g', hr = h r.
+// The arithmetic per sample is identical whichever lane of the pair it
+// occupies.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lg2x2(float2 x) {
+  return make_float2(M<float>::lg2(x.x), M<float>::lg2(x.y));
+}
+__device__ __forceinline__ float2 ex2x2(float2 x) {
+  return make_float2(M<float>::ex2(x.x), M<float>::ex2(x.y));
+}
+__device__ __forceinline__ float2 rcpx2(float2 x) {
+  return make_float2(M<float>::rcp(x.x), M<float>::rcp(x.y));
+}
+
+__device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
+                                                    const float4* __restrict__ tab, float2 a,
+                                                    float2 g0, float2& du_out, float2& V_out) {
+  const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
+  const float2 C816 = f2((float)(4.8 * 1.7));
+  const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
+  const float2 LN2 = f2(0.69314718055994530942f);
+  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
+  const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
+  const float2 c1 = mul2(mul2(f2((float)(p.h * p.cK)), a), a);
+  const float2 ca = mul2(f2((float)p.cchi), a);
+  float2 du = f2(0.f), V = f2(0.f), gph = HALF;
+  const int N = p.n_phase;
+#pragma unroll 2
+  for (int j = 0; j < N; ++j) {
+    const float4 gg = tab[j];
+    const float2 G = make_float2(gg.x, gg.y), G2 = make_float2(gg.z, gg.w);
+    const float2 hK = mul2(c1, G2);
+    const float2 dum = fma2(hK, gph, du);
+    const float2 mu = mul2(g0, rcpx2(fma2(g0, dum, ONE)));
+    const float2 chi = mul2(mul2(ca, G), mu);
+    const float2 chi2 = mul2(chi, chi);
+    // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
+    const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
+    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
+    const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
+    const float2 g = mul2(t, t);
+    // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
+    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
+    const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
+    const float2 s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
+    // second-moment factor h2 = B2^(-7/6)
+    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
+    const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
+    const float2 h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
+    // updates
+    du = fma2(hK, g, du);
+    const float2 hKmu = mul2(hK, mu);
+    const float2 hlam = mul2(mul2(f2(-2.f), hKmu), s);
+    const float2 hD2 = mul2(C55, mul2(mul2(mul2(hKmu, chi), mul2(mu, mu)), h2));
+    const float2 hr = fma2(hlam, V, hD2);
+    V = fma2(hr, fma2(HALF, hlam, ONE), V);
+    gph = mul2(HALF, g);
+  }
+  du_out = du;
+  V_out = V;
+}
+
+// a_eff at the crossing point and the decoded sample (rows a1-a3).
 template <typename T>
-__device__ __forceinline__ Sample eval_sample(const Params& p, const T* __restrict__ sG,
-                                              int64_t i) {
-  Sample s;
-  // decode (reparameterised)
+__device__ __forceinline__ T focus(const Params& p, int64_t i, double& gamma0, T& thx, T& thy) {
   T xi0 = (T)load_elem(p.xi[0], i, p.dtype);
   T xi1 = (T)load_elem(p.xi[1], i, p.dtype);
   T xi2 = (T)load_elem(p.xi[2], i, p.dtype);
@@ -164,10 +250,10 @@ __device__ __forceinline__ Sample eval_sample(const Params& p, const T* __restri
   T x = (T)p.bdx + (T)p.sx * xi0;
   T y = (T)p.bdy + (T)p.sy * xi1;
   T z = (T)p.sz * xi2;
-  double gamma0 = p.flat ? p.glo + p.gspan * xi3 : p.gmean * (1.0 + p.spread * xi3);
+  gamma0 = p.flat ? p.glo + p.gspan * xi3 : p.gmean * (1.0 + p.spread * xi3);
   if (gamma0 < 1.0) gamma0 = 1.0;
-  T thx = (T)p.div * xi4;
-  T thy = (T)p.div * xi5;
+  thx = (T)p.div * xi4;
+  thy = (T)p.div * xi5;
   // collision geometry: crossing of the pulse peak (factor 2 of Eq. 1)
   T ct = (T)0.5 * (z + (T)p.c_delay);
   T zs = (T)0.5 * (z - (T)p.c_delay);
@@ -178,39 +264,89 @@ __device__ __forceinline__ Sample eval_sample(const Params& p, const T* __restri
   T zq = zs * (T)p.inv_zR;
   T q = (T)1 + zq * zq;
   T rq = M<T>::rcp(q);
-  T a;
   if (sizeof(T) == 4)
-    a = (T)p.a0 * M<T>::rsqrt(q) *
-        M<T>::ex2(-(T)1.4426950408889634074 * rho2 * (T)p.inv_w0sq * rq);
-  else
-    a = (T)p.a0 * M<T>::rsqrt(q) * (T)exp((double)(-rho2 * (T)p.inv_w0sq * rq));
+    return (T)p.a0 * M<T>::rsqrt(q) *
+           M<T>::ex2(-(T)1.4426950408889634074 * rho2 * (T)p.inv_w0sq * rq);
+  return (T)p.a0 * M<T>::rsqrt(q) * (T)exp((double)(-rho2 * (T)p.inv_w0sq * rq));
+}
+
+// One beam sample through the model, in the paper's order (rows a1-a6).
+// QFP selects the model at compile time; the table is unused by LL.  Used
+// for the FP64 path and the FP32 classical path.
+template <typename T, bool QFP>
+__device__ __forceinline__ Sample eval_sample(const Params& p,
+                                              const typename Tab<T>::type* __restrict__ tab,
+                                              int64_t i) {
+  Sample s;
+  double gamma0;
+  T thx, thy;
+  const T a = focus<T>(p, i, gamma0, thx, thy);
   double mu, V = 0.0;
-  if (p.model == 0) {
-    if (sizeof(T) == 4) {
-      T du = (T)p.cRR * a * a;          // Eq. 3 as 1/gamma_f - 1/gamma_0
-      mu = gamma0 / (1.0 + gamma0 * (double)du);
+  if (sizeof(T) == 8) {
+    // FP64 path
+    const double ad = (double)a;
+    if (!QFP) {
+      mu = gamma0 / (1.0 + p.cRR * gamma0 * ad * ad);    // Eq. 3, a0 -> a_eff
     } else {
-      double ad = (double)a;
-      mu = gamma0 / (1.0 + p.cRR * gamma0 * ad * ad);
+      double du;
+      qfp_integrate(p, reinterpret_cast<const double*>(tab), ad, gamma0, du, V);
+      mu = gamma0 / (1.0 + gamma0 * du);
     }
+    double theta_e = 0.0, gout = mu, tx = (double)thx;
+    if (QFP) {
+      const double sv = V > 0.0 ? sqrt(V) : 0.0;
+      theta_e = p.kappa_s * ad * sv / (mu * mu);          // Eq. 8
+      tx += theta_e * load_elem(p.xi[6], i, p.dtype);
+      gout = mu + sv * load_elem(p.xi[7], i, p.dtype);
+    }
+    s.theta_e = theta_e; s.tx = tx; s.gout = gout;
   } else {
-    T du, Vt;
-    qfp_integrate<T>(p, sG, a, (T)gamma0, du, Vt);
-    mu = gamma0 / (1.0 + gamma0 * (double)du);   // FP64 recombination
-    V = (double)Vt;
+    // FP32 path, classical model: 1/gamma_f - 1/gamma0 in FP32, recombined
+    // in FP64 with an FP32 reciprocal refined by one Newton step (relative
+    // error ~2^-46).  (The FP32 QFP path evaluates samples in pairs:
+    // eval_pair_f32_qfp.)
+    const float af = (float)a;
+    const float du = (float)p.cRR * af * af;                  // Eq. 3
+    const double den = fma(gamma0, (double)du, 1.0);
+    double r = (double)M<float>::rcp((float)den);
+    r = r * fma(-den, r, 2.0);
+    mu = gamma0 * r;
+    s.theta_e = 0.0; s.tx = (double)thx; s.gout = mu;
   }
-  double ad = (double)a;
-  double theta_e = 0.0, gout = mu;
-  double tx = (double)thx, ty = (double)thy;
-  if (p.model != 0) {
-    double sv = V > 0.0 ? sqrt(V) : 0.0;
-    theta_e = p.kappa_s * ad * sv / (mu * mu);       // Eq. 8
-    tx += theta_e * load_elem(p.xi[6], i, p.dtype);
-    gout = mu + sv * load_elem(p.xi[7], i, p.dtype);
-  }
-  s.gamma0 = gamma0; s.aeff = ad; s.mu = mu; s.V = V; s.theta_e = theta_e;
-  s.thx0 = (double)thx; s.thy0 = (double)thy; s.tx = tx; s.ty = ty; s.gout = gout;
+  s.gamma0 = gamma0; s.aeff = (double)a; s.mu = mu; s.V = V;
+  s.thx0 = (double)thx; s.thy0 = (double)thy; s.ty = (double)thy;
   return s;
+}
+
+// FP32 QFP path: samples i0 and i1 through the model together (the phase
+// integration runs packed); results per sample are those of eval_sample.
+__device__ __forceinline__ void finish_f32(const Params& p, int64_t i, double gamma0, float af,
+                                           float thx, float thy, float du, float Vf, Sample& s) {
+  const double den = fma(gamma0, (double)du, 1.0);
+  double r = (double)M<float>::rcp((float)den);
+  r = r * fma(-den, r, 2.0);
+  const double mu = gamma0 * r;
+  const float sv = Vf > 0.f ? sqrtf(Vf) : 0.f;
+  const float muf = (float)mu;
+  const float te = (float)p.kappa_s * af * sv * M<float>::rcp(muf * muf);   // Eq. 8
+  s.gamma0 = gamma0; s.aeff = (double)af; s.mu = mu; s.V = (double)Vf;
+  s.theta_e = (double)te;
+  s.thx0 = (double)thx; s.thy0 = (double)thy; s.ty = (double)thy;
+  s.tx = (double)fmaf(te, (float)load_elem(p.xi[6], i, p.dtype), thx);
+  s.gout = mu + (double)(sv * (float)load_elem(p.xi[7], i, p.dtype));
+}
+
+__device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
+                                                  int64_t i0, int64_t i1, Sample& s0,
+                                                  Sample& s1) {
+  double g00, g01;
+  float tx0, ty0, tx1, ty1;
+  const float a0 = focus<float>(p, i0, g00, tx0, ty0);
+  const float a1 = focus<float>(p, i1, g01, tx1, ty1);
+  float2 du, V;
+  qfp_integrate_f32x2(p, tab, make_float2(a0, a1), make_float2((float)g00, (float)g01), du, V);
+  finish_f32(p, i0, g00, a0, tx0, ty0, du.x, V.x, s0);
+  finish_f32(p, i1, g01, a1, tx1, ty1, du.y, V.y, s1);
 }
 
 // Energy bin: -1 under, n_bins over (half-open bins).

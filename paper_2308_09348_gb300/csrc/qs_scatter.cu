@@ -203,43 +203,52 @@ int32_t device_sms(int* sms) {
   return QS_OK;
 }
 
-// Shared-memory plan of k_scatter.
+// Workspace plan: u64 histogram accumulators (+ under/over/outside slots),
+// then FP64 moment partials for the largest grid that can be resident.
 struct Plan {
   int64_t nspec = 0, nmap = 0, naeff = 0;   // accumulator slots
-  size_t table_bytes = 0, hist_bytes = 0, red_bytes = 0, smem = 0;
-  bool hist_in_smem = false, wide = false;
-  int block = 256, grid = 1;
+  int gmax = 1;
   size_t ws_bytes = 0;
   size_t off_spec = 0, off_map = 0, off_aeff = 0, off_part = 0;
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-void make_plan(Plan& pl, const qs_bins* b, int precision, bool weighted, int block, int grid_req,
-               int64_t n, int sms) {
+void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
   pl.nspec = b->n_bins > 0 ? (int64_t)b->n_bins + 2 : 0;
   pl.nmap = (b->n_tx > 0) ? (int64_t)b->n_tx * b->n_ty + 1 : 0;
   pl.naeff = b->n_aeff > 0 ? (int64_t)b->n_aeff + 1 : 0;
-  pl.wide = weighted;
-  const size_t esz = weighted ? 8 : 4;
-  pl.table_bytes = align_up((size_t)kMaxPhase * (precision == QS_F64 ? 8 : 4), 16);
-  pl.red_bytes = (size_t)(1024 / 32) * kNumMom * sizeof(double);
-  pl.hist_bytes = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * esz, 16);
-  pl.hist_in_smem = pl.table_bytes + pl.red_bytes + pl.hist_bytes <= (size_t)kSmemLimit;
-  pl.smem = pl.table_bytes + pl.red_bytes + (pl.hist_in_smem ? pl.hist_bytes : 0);
-  pl.block = block;
-  // the grid is picked at launch from the occupancy of the kernel; the
-  // workspace holds partials for the largest grid that can be resident
   int64_t gmax = (int64_t)sms * (2048 / block < 32 ? 2048 / block : 32);
   if (grid_req > gmax) gmax = grid_req;
-  pl.grid = (int)gmax;
-  (void)n;
+  pl.gmax = (int)gmax;
   size_t off = 0;
   pl.off_spec = off; off = align_up(off + (size_t)pl.nspec * 8, 256);
   pl.off_map = off;  off = align_up(off + (size_t)pl.nmap * 8, 256);
   pl.off_aeff = off; off = align_up(off + (size_t)pl.naeff * 8, 256);
   pl.off_part = off; off = align_up(off + (size_t)gmax * kNumMom * 8, 256);
   pl.ws_bytes = off;
+}
+
+// Shared memory of k_scatter: phase table (QFP), reduction scratch, and the
+// histograms when they are kept in shared memory.  The QFP model spends
+// ~1000 cycles per sample, so its histograms go straight to global integer
+// atomics (negligible traffic) and the freed shared memory buys occupancy;
+// the LL model is memory-bound and keeps them in shared memory if they fit.
+struct Smem {
+  size_t bytes = 0;
+  bool hist = false;
+};
+
+Smem smem_plan(const Plan& pl, int precision, bool qfp, int n_phase, bool weighted, int block) {
+  Smem sm;
+  // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} (FP32 path)
+  const size_t tab = qfp ? align_up((size_t)n_phase * (precision == QS_F64 ? 8 : 16), 16) : 0;
+  const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
+  const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
+  sm.hist = !(qfp && n_phase >= 32) && tab + red + hist <= (size_t)kSmemLimit &&
+            (pl.nspec + pl.nmap + pl.naeff) > 0;
+  sm.bytes = tab + red + (sm.hist ? hist : 0);
+  return sm;
 }
 
 // Persistent grid: as many CTAs as fit on the device at once, never more
@@ -259,12 +268,7 @@ int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int g
 // kernels
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__device__ __forceinline__ void build_table(const Params& p, T* sG) {
-  for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) sG[j] = (T)envelope_at(p, j);
-}
-
-// Fixed-order block reduction of kNumMom doubles; thread 0 returns sums.
+// Fixed-order block reduction of kNumMom doubles into out[0..kNumMom).
 __device__ __forceinline__ void block_reduce_write(double (&acc)[kNumMom], double* red,
                                                    double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -284,13 +288,59 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[kNumMom], doubl
   }
 }
 
-template <typename T, typename H>
-__global__ void __launch_bounds__(512) k_scatter(const Params p) {
+// One evaluated sample into the moment partials and histograms (rows a7-a8).
+template <typename H, bool SHIST>
+__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i,
+                                           double (&acc)[kNumMom], H* hs, H* hm, H* ha,
+                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+  const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+  const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
+                  isfinite(w) && w >= 0.0;
+  if (!ok) {
+    acc[8] += 1.0;
+    return;
+  }
+  const double d = s.mu - p.gamma_ref;
+  acc[0] += w;
+  acc[1] = fma(w, d, acc[1]);
+  acc[2] = fma(w * d, d, acc[2]);
+  acc[3] = fma(w, s.V, acc[3]);
+  acc[4] = fma(w, fma(s.thx0, s.thx0, s.theta_e * s.theta_e), acc[4]);
+  acc[5] = fma(w, s.thy0 * s.thy0, acc[5]);
+  acc[6] = fma(w, s.aeff, acc[6]);
+  acc[7] = fma(w, s.gamma0, acc[7]);
+  const unsigned long long q =
+      p.weighted ? (unsigned long long)__double2ll_rn(w * p.wscale) : 1ull;
+  if (nspec) {
+    const int b = energy_bin(p, s.gout);
+    const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+    if (SHIST) atomicAdd(&hs[slot], (H)q);
+    else atomicAdd(&p.acc_spec[slot], q);
+  }
+  if (nmap) {
+    const int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
+    const int64_t slot = c < 0 ? nmap - 1 : c;
+    if (SHIST) atomicAdd(&hm[slot], (H)q);
+    else atomicAdd(&p.acc_map[slot], q);
+  }
+  if (naeff) {
+    const int slot = aeff_bin(p, s.aeff);
+    if (SHIST) atomicAdd(&ha[slot], (H)q);
+    else atomicAdd(&p.acc_aeff[slot], q);
+  }
+}
+
+// K1: fused evaluation + histograms + moment partials.  T: per-sample
+// arithmetic type; H: shared-memory histogram counter (u32 counts or u64
+// fixed-point weights); QFP: model; SHIST: histograms in shared memory.
+template <typename T, typename H, bool QFP, bool SHIST>
+__global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatter(const Params p) {
+  using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  T* sG = reinterpret_cast<T*>(smem);
-  double* red = reinterpret_cast<double*>(smem + (size_t)kMaxPhase * sizeof(T));
-  H* sh = reinterpret_cast<H*>(smem + (size_t)kMaxPhase * sizeof(T) +
-                               (size_t)(1024 / 32) * kNumMom * sizeof(double));
+  const size_t tab_bytes = QFP ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
+  TT* tab = reinterpret_cast<TT*>(smem);
+  double* red = reinterpret_cast<double*>(smem + tab_bytes);
+  H* sh = reinterpret_cast<H*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumMom * sizeof(double));
   const int64_t nspec = p.n_bins > 0 ? (int64_t)p.n_bins + 2 : 0;
   const int64_t nmap = p.n_tx > 0 ? (int64_t)p.n_tx * p.n_ty + 1 : 0;
   const int64_t naeff = p.n_aeff > 0 ? (int64_t)p.n_aeff + 1 : 0;
@@ -298,8 +348,9 @@ __global__ void __launch_bounds__(512) k_scatter(const Params p) {
   H* hm = sh + nspec;
   H* ha = sh + nspec + nmap;
 
-  if (p.model != 0) build_table<T>(p, sG);
-  if (p.hist_in_smem)
+  if (QFP)
+    for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
   __syncthreads();
 
@@ -308,46 +359,24 @@ __global__ void __launch_bounds__(512) k_scatter(const Params p) {
   for (int k = 0; k < kNumMom; ++k) acc[k] = 0.0;
 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-    Sample s = eval_sample<T>(p, sG, i);
-    double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
-    bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
-              isfinite(w) && w >= 0.0;
-    if (!ok) {
-      acc[8] += 1.0;
-      continue;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (QFP && sizeof(T) == 4) {
+    // FP32 QFP: each thread carries samples 2k and 2k+1 (packed f32x2)
+    for (int64_t k = t0; 2 * k < p.n; k += stride) {
+      const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+      Sample s0, s1;
+      eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+      accumulate<H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
+      if (i1 != i0) accumulate<H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
     }
-    const double d = s.mu - p.gamma_ref;
-    acc[0] += w;
-    acc[1] += w * d;
-    acc[2] += w * d * d;
-    acc[3] += w * s.V;
-    acc[4] += w * (s.thx0 * s.thx0 + s.theta_e * s.theta_e);
-    acc[5] += w * (s.thy0 * s.thy0);
-    acc[6] += w * s.aeff;
-    acc[7] += w * s.gamma0;
-    const unsigned long long q =
-        p.weighted ? (unsigned long long)__double2ll_rn(w * p.wscale) : 1ull;
-    if (nspec) {
-      int b = energy_bin(p, s.gout);
-      int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
-      if (p.hist_in_smem) atomicAdd(&hs[slot], (H)q);
-      else atomicAdd(&p.acc_spec[slot], q);
-    }
-    if (nmap) {
-      int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
-      int slot = c < 0 ? (int)(nmap - 1) : c;
-      if (p.hist_in_smem) atomicAdd(&hm[slot], (H)q);
-      else atomicAdd(&p.acc_map[slot], q);
-    }
-    if (naeff) {
-      int slot = aeff_bin(p, s.aeff);
-      if (p.hist_in_smem) atomicAdd(&ha[slot], (H)q);
-      else atomicAdd(&p.acc_aeff[slot], q);
+  } else {
+    for (int64_t i = t0; i < p.n; i += stride) {
+      const Sample s = eval_sample<T, QFP>(p, tab, i);
+      accumulate<H, SHIST>(p, s, i, acc, hs, hm, ha, nspec, nmap, naeff);
     }
   }
   block_reduce_write(acc, red, p.partials + (size_t)blockIdx.x * kNumMom);
-  if (p.hist_in_smem) {
+  if (SHIST) {
     __syncthreads();
     for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x)
       if (hs[b]) atomicAdd(&p.acc_spec[b], (unsigned long long)hs[b]);
@@ -407,37 +436,54 @@ __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, dou
   }
 }
 
-template <typename T>
+__device__ __forceinline__ void write_record(const Params& p, const qs_sample_out& o,
+                                             const Sample& s, int64_t i) {
+  if (o.gamma0) o.gamma0[i] = s.gamma0;
+  if (o.aeff) o.aeff[i] = s.aeff;
+  if (o.mu) o.mu[i] = s.mu;
+  if (o.V) o.V[i] = s.V;
+  if (o.theta_e) o.theta_e[i] = s.theta_e;
+  if (o.theta_x) o.theta_x[i] = s.tx;
+  if (o.theta_y) o.theta_y[i] = s.ty;
+  if (o.gamma_out) o.gamma_out[i] = s.gout;
+  if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin(p, s.gout) : -1;
+  int ix = -1, iy = -1;
+  if (p.n_tx > 0) map_cell(p, s.tx, s.ty, &ix, &iy);
+  if (o.ix) o.ix[i] = ix;
+  if (o.iy) o.iy[i] = iy;
+  if (o.abin) o.abin[i] = p.n_aeff > 0 ? aeff_bin(p, s.aeff) : -1;
+}
+
+// K0: per-sample records; the same per-sample code path as k_scatter.
+template <typename T, bool QFP>
 __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
-  __shared__ T sG[kMaxPhase];
-  if (p.model != 0) build_table<T>(p, sG);
+  using TT = typename Tab<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  TT* tab = reinterpret_cast<TT*>(smem);
+  if (QFP)
+    for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-    Sample s = eval_sample<T>(p, sG, i);
-    if (o.gamma0) o.gamma0[i] = s.gamma0;
-    if (o.aeff) o.aeff[i] = s.aeff;
-    if (o.mu) o.mu[i] = s.mu;
-    if (o.V) o.V[i] = s.V;
-    if (o.theta_e) o.theta_e[i] = s.theta_e;
-    if (o.theta_x) o.theta_x[i] = s.tx;
-    if (o.theta_y) o.theta_y[i] = s.ty;
-    if (o.gamma_out) o.gamma_out[i] = s.gout;
-    if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin(p, s.gout) : -1;
-    int ix = -1, iy = -1;
-    if (p.n_tx > 0) map_cell(p, s.tx, s.ty, &ix, &iy);
-    if (o.ix) o.ix[i] = ix;
-    if (o.iy) o.iy[i] = iy;
-    if (o.abin) o.abin[i] = p.n_aeff > 0 ? aeff_bin(p, s.aeff) : -1;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (QFP && sizeof(T) == 4) {
+    for (int64_t k = t0; 2 * k < p.n; k += stride) {
+      const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+      Sample s0, s1;
+      eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+      write_record(p, o, s0, i0);
+      if (i1 != i0) write_record(p, o, s1, i1);
+    }
+  } else {
+    for (int64_t i = t0; i < p.n; i += stride) write_record(p, o, eval_sample<T, QFP>(p, tab, i), i);
   }
 }
 
 namespace {
 
-template <typename T, typename H>
-int32_t launch_scatter_t(const Params& p, const Plan& pl, int sms, int grid_req,
+template <typename T, typename H, bool QFP, bool SHIST>
+int32_t launch_scatter_t(const Params& p, int block, size_t smem, int sms, int grid_req, int gmax,
                          cudaStream_t st, int* grid_out, const qs_exec* ex) {
-  auto kern = k_scatter<T, H>;
+  auto kern = k_scatter<T, H, QFP, SHIST>;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
@@ -448,20 +494,35 @@ int32_t launch_scatter_t(const Params& p, const Plan& pl, int sms, int grid_req,
     attr_set[dev] = true;
   }
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return QS_ERR_CUDA;
-  const int grid = pick_grid(occ, sms, pl.block, grid_req, p.n, pl.grid);
+  const int grid = pick_grid(occ, sms, block, grid_req, p.n, gmax);
   if (ex && ex->ev_start &&
       cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_start), st) != cudaSuccess)
     return QS_ERR_CUDA;
-  kern<<<grid, pl.block, pl.smem, st>>>(p);
+  kern<<<grid, block, smem, st>>>(p);
   *grid_out = grid;
   if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
   if (ex && ex->ev_stop &&
       cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_stop), st) != cudaSuccess)
     return QS_ERR_CUDA;
   return QS_OK;
+}
+
+template <typename T>
+int32_t launch_scatter_prec(const Params& p, bool qfp, const Smem& sm, int block, int sms,
+                            int grid_req, int gmax, cudaStream_t st, int* g, const qs_exec* ex) {
+  typedef unsigned int U32;
+  typedef unsigned long long U64;
+  const size_t b = sm.bytes;
+  if (qfp) {
+    if (!sm.hist) return launch_scatter_t<T, U32, true, false>(p, block, b, sms, grid_req, gmax, st, g, ex);
+    return p.weighted ? launch_scatter_t<T, U64, true, true>(p, block, b, sms, grid_req, gmax, st, g, ex)
+                      : launch_scatter_t<T, U32, true, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  }
+  if (!sm.hist) return launch_scatter_t<T, U32, false, false>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  return p.weighted ? launch_scatter_t<T, U64, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex)
+                    : launch_scatter_t<T, U32, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
 }
 
 }  // namespace
@@ -492,8 +553,7 @@ extern "C" size_t qs_workspace_bytes(const qs_bins* bins, const qs_exec* exec, i
   if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
   if (device_sms(&sms) != QS_OK) return 0;
   Plan pl;
-  // the weighted plan is never smaller than the unweighted one
-  make_plan(pl, bins, prec, true, block, grid, n, sms);
+  make_plan(pl, bins, block, grid, sms);
   return pl.ws_bytes;
 }
 
@@ -514,11 +574,11 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (bins->n_aeff > 0 && !d_aeff_hist) return QS_ERR_INVALID_ARG;
   if ((st = device_sms(&sms))) return st;
   Plan pl;
-  make_plan(pl, bins, prec, samples->w != nullptr, block, grid, samples->n, sms);
-  Plan plw;
-  make_plan(plw, bins, prec, true, block, grid, samples->n, sms);
-  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < plw.ws_bytes)
+  make_plan(pl, bins, block, grid, sms);
+  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < pl.ws_bytes)
     return QS_ERR_WORKSPACE;
+  const bool qfp = laser->model == QS_MODEL_QFP;
+  const Smem sm = smem_plan(pl, prec, qfp, qfp ? laser->n_phase : 0, samples->w != nullptr, block);
 
   Params p;
   fill_params(p, laser, beam, samples, bins, wbits);
@@ -527,18 +587,15 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.acc_map = reinterpret_cast<unsigned long long*>(ws + pl.off_map);
   p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + pl.off_aeff);
   p.partials = reinterpret_cast<double*>(ws + pl.off_part);
-  p.hist_in_smem = pl.hist_in_smem ? 1 : 0;
+  p.hist_in_smem = sm.hist ? 1 : 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return QS_ERR_CUDA;
   int g = 1;
-  if (prec == QS_F64) {
-    st = p.weighted ? launch_scatter_t<double, unsigned long long>(p, pl, sms, grid, cs, &g, exec)
-                    : launch_scatter_t<double, unsigned int>(p, pl, sms, grid, cs, &g, exec);
-  } else {
-    st = p.weighted ? launch_scatter_t<float, unsigned long long>(p, pl, sms, grid, cs, &g, exec)
-                    : launch_scatter_t<float, unsigned int>(p, pl, sms, grid, cs, &g, exec);
-  }
+  if (prec == QS_F64)
+    st = launch_scatter_prec<double>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);
+  else
+    st = launch_scatter_prec<float>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);
   if (st) return st;
   k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_moments);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
@@ -562,8 +619,27 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   int64_t tiles = (samples->n + 255) / 256;
   int g = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  if (prec == QS_F64) k_eval<double><<<g, 256, 0, cs>>>(p, *out);
-  else k_eval<float><<<g, 256, 0, cs>>>(p, *out);
+  const bool qfp = laser->model == QS_MODEL_QFP;
+  const size_t tb = qfp ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4)) : 0;
+  if (prec == QS_F64) {
+    if (qfp) k_eval<double, true><<<g, 256, tb, cs>>>(p, *out);
+    else k_eval<double, false><<<g, 256, 0, cs>>>(p, *out);
+  } else {
+    if (qfp) {
+      static bool attr[64] = {};
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
+      if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if (cudaFuncSetAttribute(k_eval<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxPhase * (int)sizeof(float4)) != cudaSuccess)
+          return QS_ERR_CUDA;
+        attr[dev] = true;
+      }
+      k_eval<float, true><<<g, 256, tb, cs>>>(p, *out);
+    } else {
+      k_eval<float, false><<<g, 256, 0, cs>>>(p, *out);
+    }
+  }
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
 
