@@ -94,6 +94,14 @@ def lib():
                                       C.c_int64, C.POINTER(_DP), _DP, _DP, _DP, _DP,
                                       C.POINTER(QsoMoments)]
             L.qso_scatter.restype = C.c_int
+            L.qso_grad.argtypes = [C.POINTER(QsoLaser), C.POINTER(QsoBeam), C.POINTER(QsoBins),
+                                   C.c_double, C.c_int64, C.POINTER(_DP), _DP, _DP, _DP, _DP,
+                                   _DP, C.POINTER(QsoMoments)]
+            L.qso_grad.restype = C.c_int
+            L.qso_smooth_spectrum.argtypes = [C.POINTER(QsoLaser), C.POINTER(QsoBeam),
+                                              C.POINTER(QsoBins), C.c_double, C.c_int64,
+                                              C.POINTER(_DP), _DP, _DP]
+            L.qso_smooth_spectrum.restype = C.c_int
             _lib = L
     return _lib
 
@@ -209,3 +217,47 @@ def scatter(laser, beam, bins, xi, w=None) -> dict:
     mom = {k: getattr(m, k) for k, _ in QsoMoments._fields_}
     return dict(spectrum=spec, divmap=dmap.reshape(int(bins.n_ty), int(bins.n_tx)) if nmap else dmap,
                 aeff_hist=ah, moments=mom)
+
+
+# parameter order of the gradient
+GRAD_PARAMS = ("a0", "w0_um", "dx_um", "dy_um", "delay_fs", "gamma_mean", "rel_spread", "div_rad")
+MOMENT_NAMES = tuple(k for k, _ in QsoMoments._fields_)
+
+
+def smooth_spectrum(laser, beam, bins, sigma_bins, xi, w=None) -> np.ndarray:
+    """Kernel-smoothed spectrum (plain FP64 evaluation)."""
+    n = next(len(a) for a in xi if a is not None)
+    arrs, ptrs = _streams(xi, n)
+    w64 = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    S = np.zeros(int(bins.n_bins))
+    rc = lib().qso_smooth_spectrum(C.byref(_laser(laser)), C.byref(_beam(beam)),
+                                   C.byref(_bins(bins)), float(sigma_bins), n, ptrs, _ptr(w64),
+                                   _ptr(S))
+    if rc != 0:
+        raise ValueError("smoothed spectrum needs uniform bins and sigma_bins > 0")
+    return S
+
+
+def grad(laser, beam, bins, sigma_bins, xi, w=None, dL_dm=None, dL_dS=None) -> dict:
+    """Forward-mode (dual number) gradient of L = dL_dm . m + dL_dS . S with
+    respect to GRAD_PARAMS; also returns the forward smoothed spectrum and
+    moments.  dL_dm: dict by moment name or array of 13 (qso_moments order)."""
+    n = next(len(a) for a in xi if a is not None)
+    arrs, ptrs = _streams(xi, n)
+    w64 = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    dm = np.zeros(13)
+    if isinstance(dL_dm, dict):
+        for k, v in dL_dm.items():
+            dm[MOMENT_NAMES.index(k)] = v
+    elif dL_dm is not None:
+        dm[:] = dL_dm
+    dS = None if dL_dS is None else np.ascontiguousarray(dL_dS, dtype=np.float64)
+    g = np.zeros(8)
+    S = np.zeros(int(bins.n_bins))
+    m = QsoMoments()
+    rc = lib().qso_grad(C.byref(_laser(laser)), C.byref(_beam(beam)), C.byref(_bins(bins)),
+                        float(sigma_bins), n, ptrs, _ptr(w64), _ptr(dm), _ptr(dS), _ptr(g),
+                        _ptr(S), C.byref(m))
+    if rc != 0:
+        raise ValueError("oracle gradient: bad arguments (uniform bins, sigma_bins > 0)")
+    return dict(grad=g, smooth=S, moments={k: getattr(m, k) for k in MOMENT_NAMES})

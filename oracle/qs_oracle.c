@@ -469,3 +469,249 @@ int qso_scatter(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
     }
     return 0;
 }
+
+/* ========================================================================
+ * Kernel-smoothed spectrum and gradients (test infrastructure).
+ *
+ * Smoothed spectrum (uniform bins only), the differentiable stand-in for the
+ * energy histogram of Eq. 4 used by a fitting loss:
+ *   S_k = sum_i w_i (Delta / (sigma sqrt(2 pi))) exp(-(c_k - g_i)^2 / (2 sigma^2))
+ * with c_k = lo + (k + 1/2) Delta, sigma = sigma_bins Delta, g_i the realised
+ * final energy, and only bins with |c_k - g_i| <= 6 sigma included.
+ *
+ * Gradients: forward-mode automatic differentiation with dual numbers that
+ * carry the derivatives with respect to the 8 parameters
+ *   (a0, W0, dx, dy, delay, gamma_mean, rel_spread, div_rad)
+ * through every step of the per-sample evaluation above (decode, geometry,
+ * Eq. 2, Eq. 3 or the phase integration, Eq. 8) and through the moment and
+ * smoothed-spectrum sums.  The loss gradient is the contraction with the
+ * caller's dL/d(moments) and dL/dS.  Nothing here is hand-differentiated.
+ * ======================================================================== */
+#define QSO_ND 8
+typedef struct { double v; double d[QSO_ND]; } qd;
+
+static qd qd_c(double v) { qd r; r.v = v; memset(r.d, 0, sizeof(r.d)); return r; }
+static qd qd_var(double v, int k) { qd r = qd_c(v); r.d[k] = 1.0; return r; }
+static qd qd_add(qd a, qd b) { qd r; r.v = a.v + b.v; for (int k = 0; k < QSO_ND; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+static qd qd_sub(qd a, qd b) { qd r; r.v = a.v - b.v; for (int k = 0; k < QSO_ND; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+static qd qd_mul(qd a, qd b) { qd r; r.v = a.v * b.v; for (int k = 0; k < QSO_ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static qd qd_div(qd a, qd b) { qd r; r.v = a.v / b.v; for (int k = 0; k < QSO_ND; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v; return r; }
+static qd qd_scale(qd a, double s) { qd r; r.v = a.v * s; for (int k = 0; k < QSO_ND; ++k) r.d[k] = a.d[k] * s; return r; }
+static qd qd_addc(qd a, double c) { a.v += c; return a; }
+static qd qd_fn(qd a, double f, double df) { qd r; r.v = f; for (int k = 0; k < QSO_ND; ++k) r.d[k] = df * a.d[k]; return r; }
+static qd qd_sqrt(qd a) { double s = sqrt(a.v); return qd_fn(a, s, s > 0 ? 0.5 / s : 0.0); }
+static qd qd_exp(qd a) { double e = exp(a.v); return qd_fn(a, e, e); }
+static qd qd_log(qd a) { return qd_fn(a, log(a.v), 1.0 / a.v); }
+static qd qd_pow(qd a, double p) { double y = pow(a.v, p); return qd_fn(a, y, p * pow(a.v, p - 1.0)); }
+
+/* Gaunt and second-moment factors as written above, in dual arithmetic. */
+static qd qd_gaunt(qd chi) {
+    qd B = qd_addc(qd_add(qd_scale(qd_mul(qd_addc(chi, 1.0), qd_log(qd_addc(qd_scale(chi, 1.7), 1.0))), 4.8),
+                          qd_scale(qd_mul(chi, chi), 2.44)), 1.0);
+    return qd_pow(B, -2.0 / 3.0);
+}
+static qd qd_h2(qd chi) {
+    qd B = qd_addc(qd_add(qd_mul(qd_addc(qd_scale(chi, 4.1), 1.0), qd_log(qd_addc(qd_scale(chi, 12.93), 1.0))),
+                          qd_scale(qd_mul(chi, chi), 4.75)), 1.0);
+    return qd_pow(B, -7.0 / 6.0);
+}
+
+/* d g / d chi of the Gaunt fit, in dual arithmetic (enters the variance
+   transport term), obtained by differentiating B^(-2/3) symbolically once:
+   g' = -(2/3) B^(-5/3) B',  B' = 4.8 ln(1+1.7chi) + 4.8 (1+chi) 1.7/(1+1.7chi) + 4.88 chi */
+static qd qd_gaunt_prime(qd chi) {
+    qd x1 = qd_addc(qd_scale(chi, 1.7), 1.0);
+    qd B = qd_addc(qd_add(qd_scale(qd_mul(qd_addc(chi, 1.0), qd_log(x1)), 4.8),
+                          qd_scale(qd_mul(chi, chi), 2.44)), 1.0);
+    qd dB = qd_add(qd_add(qd_scale(qd_log(x1), 4.8),
+                          qd_scale(qd_div(qd_addc(chi, 1.0), x1), 4.8 * 1.7)),
+                   qd_scale(chi, 4.88));
+    return qd_scale(qd_mul(qd_pow(B, -5.0 / 3.0), dB), -2.0 / 3.0);
+}
+
+typedef struct {
+    qd gamma0, aeff, mu, V, theta_e, thx0, thy0, gout;
+} qso_dsample;
+
+/* One sample in dual arithmetic (mirrors qso_sample_eval, same order). */
+static void qso_sample_dual(const qso_laser* L, const qso_beam* B, const double* xi,
+                            qso_dsample* s) {
+    double c[10];
+    qso_constants(L, c);
+    qd a0 = qd_var(L->a0, 0), w0 = qd_var(L->w0_um, 1), ldx = qd_var(L->dx_um, 2),
+       ldy = qd_var(L->dy_um, 3), delay = qd_var(L->delay_fs, 4), gm = qd_var(B->gamma_mean, 5),
+       sp = qd_var(B->rel_spread, 6), dv = qd_var(B->div_rad, 7);
+    qd x = qd_c(B->dx_um + B->sigma_x_um * xi[0]);
+    qd y = qd_c(B->dy_um + B->sigma_y_um * xi[1]);
+    qd z = qd_c(B->sigma_z_um * xi[2]);
+    qd gamma0;
+    if (B->flat_energy) gamma0 = qd_c(B->gamma_lo + (B->gamma_hi - B->gamma_lo) * xi[3]);
+    else gamma0 = qd_mul(gm, qd_addc(qd_scale(sp, xi[3]), 1.0));
+    if (gamma0.v < 1.0) gamma0 = qd_c(1.0);
+    qd thx = qd_scale(dv, xi[4]), thy = qd_scale(dv, xi[5]);
+    qd cdel = qd_scale(delay, QSO_C_UM_PER_FS);
+    qd ct = qd_scale(qd_add(z, cdel), 0.5);
+    qd zs = qd_scale(qd_sub(z, cdel), 0.5);
+    qd xs = qd_sub(qd_add(x, qd_mul(thx, ct)), ldx);
+    qd ys = qd_sub(qd_add(y, qd_mul(thy, ct)), ldy);
+    qd rho2 = qd_add(qd_mul(xs, xs), qd_mul(ys, ys));
+    qd zR = qd_scale(qd_mul(w0, w0), QSO_PI / L->lambda_um);
+    qd zq = qd_div(zs, zR);
+    qd q = qd_addc(qd_mul(zq, zq), 1.0);
+    qd aeff = qd_mul(qd_div(a0, qd_sqrt(q)),
+                     qd_exp(qd_scale(qd_div(rho2, qd_mul(qd_mul(w0, w0), q)), -1.0)));
+    qd mu, V = qd_c(0.0);
+    if (L->model == 0) {
+        mu = qd_div(gamma0, qd_addc(qd_scale(qd_mul(gamma0, qd_mul(aeff, aeff)), c[9]), 1.0));
+    } else {
+        int N = L->n_phase;
+        double h = (c[8] - c[7]) / (double)N;
+        qd du = qd_c(0.0), g_prev = qd_c(1.0);
+        for (int j = 0; j < N; ++j) {
+            double G = qso_envelope(L, c, c[7] + ((double)j + 0.5) * h);
+            qd A = qd_scale(aeff, G);
+            qd K = qd_scale(qd_mul(A, A), (2.0 / 3.0) * c[3]);
+            qd du_mid = qd_add(du, qd_scale(qd_mul(K, g_prev), 0.5 * h));
+            qd m = qd_div(gamma0, qd_addc(qd_mul(gamma0, du_mid), 1.0));
+            qd chi = qd_scale(qd_mul(m, A), sqrt(2.0) / c[4]);
+            qd g = qd_gaunt(chi);
+            qd gp = qd_gaunt_prime(chi);
+            qd h2 = qd_h2(chi);
+            qd lam = qd_scale(qd_mul(qd_mul(K, m), qd_add(qd_scale(g, 2.0), qd_mul(chi, gp))), -2.0);
+            qd D2 = qd_scale(qd_mul(qd_mul(qd_mul(K, qd_mul(m, qd_mul(m, m))), chi), h2),
+                             55.0 / (16.0 * sqrt(3.0)));
+            qd rv = qd_add(qd_mul(lam, V), D2);
+            du = qd_add(du, qd_scale(qd_mul(K, g), h));
+            V = qd_add(V, qd_add(qd_scale(rv, h), qd_scale(qd_mul(lam, rv), 0.5 * h * h)));
+            g_prev = g;
+        }
+        mu = qd_div(gamma0, qd_addc(qd_mul(gamma0, du), 1.0));
+    }
+    qd theta_e = qd_c(0.0), gout = mu;
+    if (L->model != 0 && V.v > 0.0) {
+        theta_e = qd_scale(qd_div(qd_mul(aeff, qd_sqrt(V)), qd_mul(mu, mu)),
+                           L->div_prefactor * sqrt(2.0 / QSO_PI));
+        gout = qd_add(mu, qd_scale(qd_sqrt(V), xi[7]));
+    }
+    s->gamma0 = gamma0; s->aeff = aeff; s->mu = mu; s->V = V; s->theta_e = theta_e;
+    s->thx0 = thx; s->thy0 = thy; s->gout = gout;
+}
+
+/* Bins k with |c_k - g| <= 6 sigma, clamped to [0, n). */
+static void qso_smooth_range(const qso_bins* b, double sigma_bins, double g, int* k0, int* k1) {
+    double t = (g - b->lo) * ((double)b->n_bins / (b->hi - b->lo));
+    double lo = ceil(t - 0.5 - 6.0 * sigma_bins), hi = floor(t - 0.5 + 6.0 * sigma_bins);
+    if (lo < 0) lo = 0;
+    if (hi > b->n_bins - 1) hi = b->n_bins - 1;
+    *k0 = (int)lo; *k1 = (int)hi;
+}
+
+/* Forward smoothed spectrum and moments, plus the gradient of
+   L with respect to the 8 parameters given dL/dm (13 entries, qso_moments
+   order; NULL = 0) and dL/dS (n_bins; NULL = 0).  Returns 0, or 1 on bad
+   arguments / allocation failure. */
+int qso_grad(const qso_laser* L, const qso_beam* B, const qso_bins* bins, double sigma_bins,
+             int64_t n, const double* const* xi, const double* w, const double* dL_dm,
+             const double* dL_dS, double* grad8, double* smooth, qso_moments* m) {
+    int nb = bins->n_bins;
+    if (nb <= 0 || bins->log_spaced || !(sigma_bins > 0)) return 1;
+    qd* S = (qd*)calloc((size_t)nb, sizeof(qd));
+    if (!S) return 1;
+    for (int k = 0; k < nb; ++k) S[k] = qd_c(0.0);
+    double delta = (bins->hi - bins->lo) / (double)nb;
+    double sig = sigma_bins * delta;
+    double pref = delta / (sig * sqrt(2.0 * QSO_PI));
+    qd W = qd_c(0.0), S1 = qd_c(0.0), SV = qd_c(0.0), Stx = qd_c(0.0), Sty = qd_c(0.0),
+       Sa = qd_c(0.0), Sg0 = qd_c(0.0);
+    qso_dsample* all = (qso_dsample*)malloc((size_t)(n > 0 ? n : 1) * sizeof(qso_dsample));
+    if (!all) { free(S); return 1; }
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        qso_dsample* s = &all[i];
+        qso_sample_dual(L, B, v, s);
+        double wi = w ? w[i] : 1.0;
+        W = qd_addc(W, wi);
+        S1 = qd_add(S1, qd_scale(s->mu, wi));
+        SV = qd_add(SV, qd_scale(s->V, wi));
+        Stx = qd_add(Stx, qd_scale(qd_add(qd_mul(s->thx0, s->thx0), qd_mul(s->theta_e, s->theta_e)), wi));
+        Sty = qd_add(Sty, qd_scale(qd_mul(s->thy0, s->thy0), wi));
+        Sa = qd_add(Sa, qd_scale(s->aeff, wi));
+        Sg0 = qd_add(Sg0, qd_scale(s->gamma0, wi));
+        int k0, k1;
+        qso_smooth_range(bins, sigma_bins, s->gout.v, &k0, &k1);
+        for (int k = k0; k <= k1; ++k) {
+            double ck = bins->lo + ((double)k + 0.5) * delta;
+            qd dlt = qd_addc(qd_scale(s->gout, -1.0), ck);
+            qd e = qd_exp(qd_scale(qd_mul(dlt, dlt), -1.0 / (2.0 * sig * sig)));
+            S[k] = qd_add(S[k], qd_scale(e, wi * pref));
+        }
+    }
+    qd mean = qd_scale(S1, 1.0 / W.v);
+    /* central second moment: value by the two-pass definition, derivative
+       of sum w (mu - mean)^2 / W = sum w mu^2 / W - mean^2 taken exactly */
+    qd S2c = qd_c(0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        double wi = w ? w[i] : 1.0;
+        qd d = qd_sub(all[i].mu, mean);
+        S2c = qd_add(S2c, qd_scale(qd_mul(d, d), wi));
+    }
+    qd var = qd_add(qd_scale(S2c, 1.0 / W.v), qd_scale(SV, 1.0 / W.v));
+    qd spread = qd_sqrt(var);
+    qd mom[13];
+    for (int k = 0; k < 13; ++k) mom[k] = qd_c(0.0);
+    mom[0] = W;
+    mom[1] = mean;
+    mom[2] = spread;
+    mom[3] = qd_div(spread, mean);
+    mom[4] = qd_sqrt(qd_scale(Stx, 1.0 / W.v));
+    mom[5] = qd_sqrt(qd_scale(Sty, 1.0 / W.v));
+    mom[6] = qd_sqrt(qd_scale(qd_add(Stx, Sty), 1.0 / W.v));
+    mom[7] = qd_scale(Sa, 1.0 / W.v);
+    mom[11] = qd_scale(Sg0, 1.0 / W.v);
+    for (int k = 0; k < QSO_ND; ++k) {
+        double g = 0.0;
+        if (dL_dm) for (int j = 0; j < 13; ++j) g += dL_dm[j] * mom[j].d[k];
+        if (dL_dS) for (int b = 0; b < nb; ++b) g += dL_dS[b] * S[b].d[k];
+        grad8[k] = g;
+    }
+    if (smooth) for (int b = 0; b < nb; ++b) smooth[b] = S[b].v;
+    if (m) {
+        memset(m, 0, sizeof(*m));
+        m->W = W.v; m->mean = mean.v; m->spread = spread.v; m->rel_spread = mom[3].v;
+        m->div_x = mom[4].v; m->div_y = mom[5].v; m->div = mom[6].v; m->mean_aeff = mom[7].v;
+        m->mean_gamma0 = mom[11].v;
+    }
+    free(all);
+    free(S);
+    return 0;
+}
+
+/* Plain (non-dual) smoothed spectrum, same definition as in qso_grad. */
+int qso_smooth_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+                        double sigma_bins, int64_t n, const double* const* xi, const double* w,
+                        double* S) {
+    int nb = bins->n_bins;
+    if (nb <= 0 || bins->log_spaced || !(sigma_bins > 0)) return 1;
+    qso_sum* acc = (qso_sum*)calloc((size_t)nb, sizeof(qso_sum));
+    if (!acc) return 1;
+    double delta = (bins->hi - bins->lo) / (double)nb;
+    double sig = sigma_bins * delta;
+    double pref = delta / (sig * sqrt(2.0 * QSO_PI));
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        qso_sample s;
+        qso_sample_eval(L, B, NULL, v, &s);
+        double wi = w ? w[i] : 1.0;
+        int k0, k1;
+        qso_smooth_range(bins, sigma_bins, s.gamma_out, &k0, &k1);
+        for (int k = k0; k <= k1; ++k) {
+            double d = bins->lo + ((double)k + 0.5) * delta - s.gamma_out;
+            qso_add(&acc[k], wi * pref * exp(-d * d / (2.0 * sig * sig)));
+        }
+    }
+    for (int k = 0; k < nb; ++k) S[k] = qso_val(&acc[k]);
+    free(acc);
+    return 0;
+}

@@ -546,3 +546,77 @@ def test_gauss_hermite_rule_exactness():
         val = float(np.sum(w * x ** k))
         scale = float(np.sum(w * np.abs(x) ** k))
         assert abs(val - exact) <= 1e-11 * scale, k
+
+
+# --------------------------------------------------------------------------
+# gradients: the oracle's dual-number gradient vs central differences of its
+# plain forward (independent code paths: dual arithmetic vs plain doubles)
+# --------------------------------------------------------------------------
+
+LASER_PARAMS = ("a0", "w0_um", "dx_um", "dy_um", "delay_fs")
+BEAM_PARAMS = ("gamma_mean", "rel_spread", "div_rad")
+
+
+def _loss_plain(L, B, bins, sigma, xi, w, dm, dS):
+    r = oracle.scatter(L, B, bins, xi, w)
+    S = oracle.smooth_spectrum(L, B, bins, sigma, xi, w)
+    return sum(dm.get(k, 0.0) * r["moments"][k] for k in dm) + float(np.dot(dS, S))
+
+
+def _perturbed(L, B, name, value):
+    if name in LASER_PARAMS:
+        return I.Laser(**{**L.__dict__, name: value}), B
+    return L, I.Beam(**{**B.__dict__, name: value})
+
+
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+def test_oracle_gradient_vs_central_differences(model):
+    n = 300
+    wl = I.full_qfp(n)
+    L = I.Laser(**{**wl.laser.__dict__, "model": model, "n_phase": 48, "dy_um": 0.7})
+    B = wl.beam
+    xi, _ = I.workload_inputs(wl, n)
+    xi = [a.astype(np.float64) for a in xi]
+    w = I.rng(31).uniform(0.5, 1.5, n)
+    bins = I.Bins(n_bins=128, lo=0.0, hi=6720.0)
+    sigma = 2.0
+    rg = I.rng(32)
+    dm = {k: float(rg.normal()) for k in ("mean", "spread", "rel_spread", "div_x", "div_y", "div",
+                                          "mean_aeff", "mean_gamma0")}
+    dm["mean"] *= 1e-3
+    dm["spread"] *= 1e-3
+    dm["div_x"] *= 1e3
+    dm["div_y"] *= 1e3
+    dm["div"] *= 1e3
+    dS = rg.normal(size=bins.n_bins) * 1e-2
+    g = oracle.grad(L, B, bins, sigma, xi, w, dL_dm=dm, dL_dS=dS)["grad"]
+    scale = {"a0": 30.0, "w0_um": 2.5, "dx_um": 1.0, "dy_um": 1.0, "delay_fs": 10.0,
+             "gamma_mean": 4000.0, "rel_spread": 0.1, "div_rad": 1e-3}
+    for k, name in enumerate(oracle.GRAD_PARAMS):
+        base = getattr(L, name) if name in LASER_PARAMS else getattr(B, name)
+        h = 1e-4 * scale[name]
+
+        def D(hh):
+            lp = _loss_plain(*_perturbed(L, B, name, base + hh), bins, sigma, xi, w, dm, dS)
+            lm = _loss_plain(*_perturbed(L, B, name, base - hh), bins, sigma, xi, w, dm, dS)
+            return (lp - lm) / (2 * hh)
+
+        fd = (4 * D(h / 2) - D(h)) / 3          # Richardson: O(h^4)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd) + 1e-9 * np.max(np.abs(g) * np.array(
+            [scale[p] for p in oracle.GRAD_PARAMS])) / scale[name], (name, g[k], fd)
+
+
+def test_oracle_smoothed_spectrum_conserves_weight():
+    """Away from the range ends the smoothed spectrum keeps the total weight
+    up to the mass beyond the 6-sigma truncation, erfc(6/sqrt2) = 1.97e-9
+    (the bin-centre sum of a Gaussian of width 2 bins is exact to 1e-12)."""
+    n = 500
+    wl = I.full_qfp(n)
+    L = I.Laser(**{**wl.laser.__dict__, "model": I.MODEL_LL})
+    xi, _ = I.workload_inputs(wl, n)
+    xi = [a.astype(np.float64) for a in xi]
+    bins = I.Bins(n_bins=400, lo=-2000.0, hi=10000.0)
+    S = oracle.smooth_spectrum(L, wl.beam, bins, 2.0, xi)
+    from scipy.special import erfc
+    # (the included bins are whole bins, so the cut sits within half a bin of 6 sigma)
+    assert abs(S.sum() / n - (1 - erfc(6 / math.sqrt(2)))) < 1e-10
