@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 1
+#define QS_VERSION 2
 
 typedef enum {
     QS_OK = 0,
@@ -117,6 +117,14 @@ typedef struct qs_samples {
  *   Divergence map over [-theta_max, theta_max)^2 of (theta_x, theta_y),
  *   n_tx x n_ty bins, row-major [iy][ix] (0 = off).
  *   a_eff histogram over [0, aeff_max), n_aeff bins (0 = off).
+ *   Kernel-smoothed spectrum (smooth_sigma_bins > 0, uniform energy bins
+ *   only): each sample deposits its weight as a Gaussian of standard
+ *   deviation smooth_sigma_bins bin widths centred on its realised energy,
+ *   sampled at the bin centres and cut at 6 standard deviations:
+ *     S_k = sum_i w_i exp(-(k + 1/2 - t_i)^2 / (2 s^2)) / (s sqrt(2 pi)),
+ *     t_i = (gamma_out_i - lo) n_bins / (hi - lo),  s = smooth_sigma_bins.
+ *   It is the differentiable stand-in for the histogram in fitting losses
+ *   (Sec. 6: reconstruction of experimental parameters).
  * Entries are bin masses (sums of weights), not densities.
  */
 typedef struct qs_bins {
@@ -126,6 +134,7 @@ typedef struct qs_bins {
     double theta_max;
     int32_t n_aeff, reserved;
     double aeff_max;
+    double smooth_sigma_bins;
 } qs_bins;
 
 /*
@@ -195,12 +204,14 @@ size_t qs_workspace_bytes(const qs_bins* bins, const qs_exec* exec, int64_t n_sa
  *   d_spectrum   n_bins doubles (required if n_bins > 0)
  *   d_divmap     n_ty*n_tx doubles (required if the map is on)
  *   d_aeff_hist  n_aeff doubles (required if n_aeff > 0)
+ *   d_spec_smooth n_bins doubles (required if smooth_sigma_bins > 0)
  *   d_moments    one qs_moments in device memory (required)
  *   d_workspace  ws_bytes >= qs_workspace_bytes(...), 256-byte aligned
  */
 int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
                    const qs_bins* bins, const qs_exec* exec, double* d_spectrum,
-                   double* d_divmap, double* d_aeff_hist, qs_moments* d_moments,
+                   double* d_divmap, double* d_aeff_hist, double* d_spec_smooth,
+                   qs_moments* d_moments,
                    void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
@@ -212,6 +223,38 @@ int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam, const qs_samples*
 int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
                         const qs_bins* bins, const qs_exec* exec, const qs_sample_out* out,
                         void* stream);
+
+/*
+ * Parameter order of qs_scatter_grad (the reconstruction use of Sec. 6):
+ * laser a0, laser w0_um, laser dx_um, laser dy_um, laser delay_fs,
+ * beam gamma_mean, beam rel_spread, beam div_rad.
+ */
+enum { QS_G_A0 = 0, QS_G_W0, QS_G_DX, QS_G_DY, QS_G_DELAY, QS_G_GAMMA, QS_G_SPREAD, QS_G_DIV,
+       QS_NUM_GRAD };
+
+/*
+ * qs_scatter_grad: gradient of a loss L with respect to the 8 parameters
+ * above, given the upstream gradient of L with respect to the outputs of
+ * qs_scatter (adjoint of Eqs. 2, 3, 6, 8 and of the moment and smoothed-
+ * spectrum reductions).  Every sample's forward evaluation is recomputed
+ * with two tangents (d/d a_eff, d/d gamma0) carried through the discretised
+ * phase integration -- the exact derivative of the discrete scheme -- and
+ * nothing per sample is stored between the forward and this call.
+ *   d_moments     the forward qs_moments of the same call (device)
+ *   d_dL_dmoments 13 doubles (device), dL/d(each qs_moments field) in field
+ *                 order; W, under, over, map_out and nonfinite do not
+ *                 depend on the parameters and are ignored
+ *   d_dL_dsmooth  n_bins doubles (device) dL/dS_k of the smoothed spectrum,
+ *                 or NULL (then smooth_sigma_bins is not needed)
+ *   d_grad8       QS_NUM_GRAD doubles (device), written (not accumulated)
+ *   d_workspace   as for qs_scatter (qs_workspace_bytes)
+ * Samples at the gamma0 >= 1 clamp contribute no energy-parameter gradient.
+ * The reduction is in a fixed order: repeated calls are bit-identical.
+ */
+int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
+                        const qs_bins* bins, const qs_exec* exec, const qs_moments* d_moments,
+                        const double* d_dL_dmoments, const double* d_dL_dsmooth,
+                        double* d_grad8, void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
  * qs_scatter_noalloc: qs_scatter for callers that cannot allocate device
@@ -242,7 +285,7 @@ int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_sam
 int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
                            const qs_samples* samples, const qs_bins* bins, const qs_exec* exec,
                            double* d_spectrum, double* d_divmap, double* d_aeff_hist,
-                           qs_moments* d_moments, void* stream);
+                           double* d_spec_smooth, qs_moments* d_moments, void* stream);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,7 @@ class qs_bins(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("log_spaced", C.c_int32), ("lo", C.c_double),
                 ("hi", C.c_double), ("n_tx", C.c_int32), ("n_ty", C.c_int32),
                 ("theta_max", C.c_double), ("n_aeff", C.c_int32), ("reserved", C.c_int32),
-                ("aeff_max", C.c_double)]
+                ("aeff_max", C.c_double), ("smooth_sigma_bins", C.c_double)]
 
 
 MOMENT_FIELDS = ("W", "mean", "spread", "rel_spread", "div_x", "div_y", "div", "mean_aeff",
@@ -99,7 +99,8 @@ def _lib():
             L.qs_workspace_bytes.restype = C.c_size_t
             L.qs_scatter.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
                                      C.POINTER(qs_samples), C.POINTER(qs_bins),
-                                     C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP]
+                                     C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP, _VP,
+                                     C.c_size_t, _VP]
             L.qs_scatter.restype = C.c_int32
             L.qs_eval_samples.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
                                           C.POINTER(qs_samples), C.POINTER(qs_bins),
@@ -107,8 +108,13 @@ def _lib():
             L.qs_eval_samples.restype = C.c_int32
             L.qs_scatter_noalloc.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
                                              C.POINTER(qs_samples), C.POINTER(qs_bins),
-                                             C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP]
+                                             C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP, _VP]
             L.qs_scatter_noalloc.restype = C.c_int32
+            L.qs_scatter_grad.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                          C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                          C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP,
+                                          C.c_size_t, _VP]
+            L.qs_scatter_grad.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -133,7 +139,7 @@ def make_beam(b: _inputs.Beam) -> qs_beam:
 
 def make_bins(b: _inputs.Bins) -> qs_bins:
     return qs_bins(int(b.n_bins), int(b.log_spaced), b.lo, b.hi, int(b.n_tx), int(b.n_ty),
-                   b.theta_max, int(b.n_aeff), 0, b.aeff_max)
+                   b.theta_max, int(b.n_aeff), 0, b.aeff_max, float(b.smooth_sigma_bins))
 
 
 def _event_handle(ev):
@@ -215,6 +221,8 @@ class Outputs:
         nmap = bins.n_tx * bins.n_ty if (bins.n_tx > 0 and bins.n_ty > 0) else 0
         self.divmap = torch.zeros(nmap, dtype=torch.float64, device=dev)
         self.aeff_hist = torch.zeros(max(bins.n_aeff, 0), dtype=torch.float64, device=dev)
+        self.spec_smooth = torch.zeros(max(bins.n_bins, 0) if bins.smooth_sigma_bins > 0 else 0,
+                                       dtype=torch.float64, device=dev)
         self.moments = torch.zeros(len(MOMENT_FIELDS), dtype=torch.float64, device=dev)
         nbytes = workspace_bytes(bins, n, precision, block, grid)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -231,7 +239,7 @@ class Outputs:
         if self.bins.n_tx > 0:
             nm = nm.view(self.bins.n_ty, self.bins.n_tx)
         return dict(spectrum=self.spectrum, divmap=nm, aeff_hist=self.aeff_hist,
-                    moments=self.moments_dict())
+                    spec_smooth=self.spec_smooth, moments=self.moments_dict())
 
 
 def _ptr_or_none(t):
@@ -251,8 +259,8 @@ def qs_scatter(laser, beam, xi, bins, w=None, precision="f32", out: Outputs | No
     E = make_exec(precision, weight_frac_bits, block, grid, kernel_events)
     st = _lib().qs_scatter(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
                            _ptr_or_none(out.spectrum), _ptr_or_none(out.divmap),
-                           _ptr_or_none(out.aeff_hist), out.moments.data_ptr(), out.ws_ptr,
-                           out.ws_bytes, _stream_ptr(stream))
+                           _ptr_or_none(out.aeff_hist), _ptr_or_none(out.spec_smooth),
+                           out.moments.data_ptr(), out.ws_ptr, out.ws_bytes, _stream_ptr(stream))
     _check(st, "qs_scatter")
     return out
 
@@ -289,6 +297,8 @@ class _OutputsNoWorkspace(Outputs):
         nmap = bins.n_tx * bins.n_ty if (bins.n_tx > 0 and bins.n_ty > 0) else 0
         self.divmap = torch.zeros(nmap, dtype=torch.float64, device=device)
         self.aeff_hist = torch.zeros(max(bins.n_aeff, 0), dtype=torch.float64, device=device)
+        self.spec_smooth = torch.zeros(max(bins.n_bins, 0) if bins.smooth_sigma_bins > 0 else 0,
+                                       dtype=torch.float64, device=device)
         self.moments = torch.zeros(len(MOMENT_FIELDS), dtype=torch.float64, device=device)
         self.workspace = None
         self.ws_ptr = None
@@ -307,7 +317,33 @@ def qs_scatter_noalloc(laser, beam, xi, bins, w=None, precision="f32", out: Outp
     E = make_exec(precision, weight_frac_bits, block, grid)
     st = _lib().qs_scatter_noalloc(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
                                    _ptr_or_none(out.spectrum), _ptr_or_none(out.divmap),
-                                   _ptr_or_none(out.aeff_hist), out.moments.data_ptr(),
-                                   _stream_ptr(stream))
+                                   _ptr_or_none(out.aeff_hist), _ptr_or_none(out.spec_smooth),
+                                   out.moments.data_ptr(), _stream_ptr(stream))
     _check(st, "qs_scatter_noalloc")
     return out
+
+
+GRAD_PARAMS = ("a0", "w0_um", "dx_um", "dy_um", "delay_fs", "gamma_mean", "rel_spread", "div_rad")
+
+
+def qs_scatter_grad(laser, beam, xi, bins, moments, dL_dmoments, dL_dsmooth=None, w=None,
+                    precision="f32", out: Outputs | None = None, block=0, grid=0,
+                    stream=None) -> torch.Tensor:
+    """Gradient (8 doubles, GRAD_PARAMS order) of a loss given its upstream
+    gradient with respect to the 13 moments (and the smoothed spectrum)."""
+    s, keep = make_samples(xi, w)
+    dev = keep[0].device
+    if out is None:
+        out = Outputs(bins, s.n, dev, precision, block, grid)
+    mom = moments.to(device=dev, dtype=torch.float64).contiguous()
+    dm = dL_dmoments.to(device=dev, dtype=torch.float64).contiguous()
+    dS = None if dL_dsmooth is None else dL_dsmooth.to(device=dev, dtype=torch.float64).contiguous()
+    g = torch.empty(8, dtype=torch.float64, device=dev)
+    L, B, Bn = make_laser(laser), make_beam(beam), make_bins(bins)
+    E = make_exec(precision, 0, block, grid)
+    st = _lib().qs_scatter_grad(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
+                                mom.data_ptr(), dm.data_ptr(),
+                                dS.data_ptr() if dS is not None else None, g.data_ptr(),
+                                out.ws_ptr, out.ws_bytes, _stream_ptr(stream))
+    _check(st, "qs_scatter_grad")
+    return g

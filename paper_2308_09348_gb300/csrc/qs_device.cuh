@@ -48,7 +48,12 @@ struct Params {
   unsigned long long* acc_map;
   unsigned long long* acc_aeff;
   double* partials;
-  int32_t hist_in_smem, pad3;
+  int32_t hist_in_smem, smooth_in_smem;
+  // kernel-smoothed spectrum (n_bins accumulators when smooth_sigma > 0)
+  double smooth_sigma;     // in bins
+  double smooth_pref;      // 1 / (sigma sqrt(2 pi))
+  double smooth_c;         // log2(e) / (2 sigma^2)
+  unsigned long long* acc_smooth;
 };
 
 // ---- math policy --------------------------------------------------------
@@ -372,6 +377,15 @@ __device__ __forceinline__ int map_cell(const Params& p, double tx, double ty, i
   if (ix_o) *ix_o = -1;
   if (iy_o) *iy_o = -1;
   return -1;
+}
+
+// Bins k with |k + 1/2 - t| <= 6 sigma of the smoothed spectrum, clamped.
+__device__ __forceinline__ void smooth_range(const Params& p, double t, int* k0, int* k1) {
+  double lo = ceil(t - 0.5 - 6.0 * p.smooth_sigma), hi = floor(t - 0.5 + 6.0 * p.smooth_sigma);
+  if (lo < 0.0) lo = 0.0;
+  if (hi > (double)(p.n_bins - 1)) hi = (double)(p.n_bins - 1);
+  *k0 = (int)lo;
+  *k1 = (int)hi;
 }
 
 __device__ __forceinline__ int aeff_bin(const Params& p, double a) {

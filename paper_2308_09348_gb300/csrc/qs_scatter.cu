@@ -10,6 +10,7 @@
 // Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348 (Secs. 2-5).
 #include "qscatter.h"
 #include "qs_device.cuh"
+#include "qs_host.hpp"
 
 #include <cmath>
 #include <cstring>
@@ -18,19 +19,17 @@
 namespace qs {
 
 // ---------------------------------------------------------------------------
-// host: derived constants
+// host: derived constants (shared with the gradient translation unit)
 // ---------------------------------------------------------------------------
-namespace {
+namespace detail {
 
 constexpr double kC = 0.299792458;          // um / fs
 constexpr double kRe = 2.8179403262e-9;     // classical electron radius, um
 constexpr double kLbarC = 3.8615926796e-7;  // reduced Compton wavelength, um
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kGaussWindow = 2.5;        // half-window in units of Phi
-constexpr int kSmemLimit = 227 * 1024;
-
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 int32_t validate_laser(const qs_laser* L) {
   if (!L) return QS_ERR_INVALID_ARG;
@@ -74,6 +73,9 @@ int32_t validate_bins(const qs_bins* b) {
   if ((b->n_tx > 0) != (b->n_ty > 0)) return QS_ERR_INVALID_ARG;
   if (b->n_tx > 0 && !finite_pos(b->theta_max)) return QS_ERR_INVALID_ARG;
   if (b->n_aeff > 0 && !finite_pos(b->aeff_max)) return QS_ERR_INVALID_ARG;
+  if (!finite_nonneg(b->smooth_sigma_bins)) return QS_ERR_INVALID_ARG;
+  if (b->smooth_sigma_bins > 0 && (b->n_bins <= 0 || b->log_spaced || b->smooth_sigma_bins > 64))
+    return QS_ERR_INVALID_ARG;
   return QS_OK;
 }
 
@@ -176,6 +178,12 @@ void fill_params(Params& p, const qs_laser* L, const qs_beam* B, const qs_sample
     }
     p.n_aeff = b->n_aeff;
     if (b->n_aeff > 0) p.a_scale = (double)b->n_aeff / b->aeff_max;
+    if (b->smooth_sigma_bins > 0) {
+      const double sg = b->smooth_sigma_bins;
+      p.smooth_sigma = sg;
+      p.smooth_pref = 1.0 / (sg * std::sqrt(2.0 * kPi));
+      p.smooth_c = 1.4426950408889634074 / (2.0 * sg * sg);
+    }
   }
   p.wscale = std::ldexp(1.0, wbits);
   p.gamma_ref = B->flat_energy ? 0.5 * (B->gamma_lo + B->gamma_hi) : B->gamma_mean;
@@ -185,8 +193,8 @@ struct DevInfo {
   int sms = 0;
   bool init = false;
 };
-std::mutex g_mu;
-DevInfo g_dev[64];
+static std::mutex g_mu;
+static DevInfo g_dev[64];
 
 int32_t device_sms(int* sms) {
   int dev = 0;
@@ -205,19 +213,13 @@ int32_t device_sms(int* sms) {
 
 // Workspace plan: u64 histogram accumulators (+ under/over/outside slots),
 // then FP64 moment partials for the largest grid that can be resident.
-struct Plan {
-  int64_t nspec = 0, nmap = 0, naeff = 0;   // accumulator slots
-  int gmax = 1;
-  size_t ws_bytes = 0;
-  size_t off_spec = 0, off_map = 0, off_aeff = 0, off_part = 0;
-};
-
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
   pl.nspec = b->n_bins > 0 ? (int64_t)b->n_bins + 2 : 0;
   pl.nmap = (b->n_tx > 0) ? (int64_t)b->n_tx * b->n_ty + 1 : 0;
   pl.naeff = b->n_aeff > 0 ? (int64_t)b->n_aeff + 1 : 0;
+  pl.nsmooth = b->smooth_sigma_bins > 0 ? (int64_t)b->n_bins : 0;
   int64_t gmax = (int64_t)sms * (2048 / block < 32 ? 2048 / block : 32);
   if (grid_req > gmax) gmax = grid_req;
   pl.gmax = (int)gmax;
@@ -225,6 +227,7 @@ void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
   pl.off_spec = off; off = align_up(off + (size_t)pl.nspec * 8, 256);
   pl.off_map = off;  off = align_up(off + (size_t)pl.nmap * 8, 256);
   pl.off_aeff = off; off = align_up(off + (size_t)pl.naeff * 8, 256);
+  pl.off_smooth = off; off = align_up(off + (size_t)pl.nsmooth * 8, 256);
   pl.off_part = off; off = align_up(off + (size_t)gmax * kNumMom * 8, 256);
   pl.ws_bytes = off;
 }
@@ -234,11 +237,6 @@ void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
 // ~1000 cycles per sample, so its histograms go straight to global integer
 // atomics (negligible traffic) and the freed shared memory buys occupancy;
 // the LL model is memory-bound and keeps them in shared memory if they fit.
-struct Smem {
-  size_t bytes = 0;
-  bool hist = false;
-};
-
 Smem smem_plan(const Plan& pl, int precision, bool qfp, int n_phase, bool weighted, int block) {
   Smem sm;
   // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} (FP32 path)
@@ -248,6 +246,9 @@ Smem smem_plan(const Plan& pl, int precision, bool qfp, int n_phase, bool weight
   sm.hist = !(qfp && n_phase >= 32) && tab + red + hist <= (size_t)kSmemLimit &&
             (pl.nspec + pl.nmap + pl.naeff) > 0;
   sm.bytes = tab + red + (sm.hist ? hist : 0);
+  // smoothed-spectrum accumulators (u64) stay in shared memory when small
+  sm.smooth = pl.nsmooth > 0 && pl.nsmooth * 8 <= 32 * 1024 && sm.bytes + pl.nsmooth * 8 <= (size_t)kSmemLimit;
+  if (sm.smooth) sm.bytes += align_up((size_t)pl.nsmooth * 8, 16);
   return sm;
 }
 
@@ -262,7 +263,9 @@ int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int g
   return (int)(g < 1 ? 1 : g);
 }
 
-}  // namespace
+}  // namespace detail
+
+using namespace detail;
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -289,10 +292,30 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[kNumMom], doubl
 }
 
 // One evaluated sample into the moment partials and histograms (rows a7-a8).
-template <typename H, bool SHIST>
+// Smoothed-spectrum deposit of one sample (fixed point, like the weighted
+// histograms): S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)).
+template <typename T>
+__device__ __forceinline__ void deposit_smooth(const Params& p, double gout, double w,
+                                               unsigned long long* dst) {
+  const double t = (gout - p.lo) * p.inv_w;
+  if (!(t > -1e9 && t < 1e9)) return;
+  int k0, k1;
+  smooth_range(p, t, &k0, &k1);
+  const double wq = w * p.smooth_pref * p.wscale;
+  for (int k = k0; k <= k1; ++k) {
+    const double d = (double)k + 0.5 - t;
+    double e;
+    if (sizeof(T) == 4) e = (double)M<float>::ex2(-(float)(d * d * p.smooth_c));
+    else e = exp2(-d * d * p.smooth_c);
+    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * e));
+  }
+}
+
+template <typename T, typename H, bool SHIST>
 __device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i,
                                            double (&acc)[kNumMom], H* hs, H* hm, H* ha,
-                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+                                           unsigned long long* hsm, int64_t nspec, int64_t nmap,
+                                           int64_t naeff) {
   const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
   const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
                   isfinite(w) && w >= 0.0;
@@ -328,6 +351,7 @@ __device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int
     if (SHIST) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
+  if (hsm) deposit_smooth<T>(p, s.gout, w, hsm);
 }
 
 // K1: fused evaluation + histograms + moment partials.  T: per-sample
@@ -347,11 +371,18 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
   H* hs = sh;
   H* hm = sh + nspec;
   H* ha = sh + nspec + nmap;
+  const size_t hist_bytes =
+      SHIST ? (((size_t)(nspec + nmap + naeff) * sizeof(H) + 15) & ~(size_t)15) : 0;
+  const int64_t nsm = p.smooth_sigma > 0.0 ? (int64_t)p.n_bins : 0;
+  unsigned long long* ssm = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(sh) + hist_bytes);
+  unsigned long long* hsm = nsm ? (p.smooth_in_smem ? ssm : p.acc_smooth) : nullptr;
 
   if (QFP)
     for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
+  if (nsm && p.smooth_in_smem)
+    for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x) ssm[b] = 0;
   __syncthreads();
 
   double acc[kNumMom];
@@ -366,16 +397,21 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
       Sample s0, s1;
       eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-      accumulate<H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
-      if (i1 != i0) accumulate<H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
+      accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+      if (i1 != i0) accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
   } else {
     for (int64_t i = t0; i < p.n; i += stride) {
       const Sample s = eval_sample<T, QFP>(p, tab, i);
-      accumulate<H, SHIST>(p, s, i, acc, hs, hm, ha, nspec, nmap, naeff);
+      accumulate<T, H, SHIST>(p, s, i, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
   }
   block_reduce_write(acc, red, p.partials + (size_t)blockIdx.x * kNumMom);
+  if (nsm && p.smooth_in_smem) {
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x)
+      if (ssm[b]) atomicAdd(&p.acc_smooth[b], ssm[b]);
+  }
   if (SHIST) {
     __syncthreads();
     for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x)
@@ -389,7 +425,7 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
 
 __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, double* spectrum,
                                                    double* divmap, double* aeff_hist,
-                                                   qs_moments* mom) {
+                                                   double* smooth, qs_moments* mom) {
   __shared__ double tot[kNumMom];
   const double scale = p.weighted ? 1.0 / p.wscale : 1.0;
   if (threadIdx.x < kNumMom) {
@@ -409,6 +445,9 @@ __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, dou
   for (int64_t b = threadIdx.x; b < nmap; b += blockDim.x) divmap[b] = (double)p.acc_map[b] * scale;
   for (int b = threadIdx.x; b < p.n_aeff; b += blockDim.x)
     aeff_hist[b] = (double)p.acc_aeff[b] * scale;
+  if (p.smooth_sigma > 0.0)
+    for (int b = threadIdx.x; b < p.n_bins; b += blockDim.x)
+      smooth[b] = (double)p.acc_smooth[b] / p.wscale;
   __syncthreads();
   if (threadIdx.x == 0) {
     qs_moments m;
@@ -560,8 +599,8 @@ extern "C" size_t qs_workspace_bytes(const qs_bins* bins, const qs_exec* exec, i
 extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
                               const qs_samples* samples, const qs_bins* bins,
                               const qs_exec* exec, double* d_spectrum, double* d_divmap,
-                              double* d_aeff_hist, qs_moments* d_moments, void* d_workspace,
-                              size_t ws_bytes, void* stream) {
+                              double* d_aeff_hist, double* d_spec_smooth, qs_moments* d_moments,
+                              void* d_workspace, size_t ws_bytes, void* stream) {
   int32_t st;
   if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
       (st = validate_samples(samples)) || (st = validate_bins(bins)))
@@ -572,6 +611,7 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (bins->n_bins > 0 && !d_spectrum) return QS_ERR_INVALID_ARG;
   if (bins->n_tx > 0 && !d_divmap) return QS_ERR_INVALID_ARG;
   if (bins->n_aeff > 0 && !d_aeff_hist) return QS_ERR_INVALID_ARG;
+  if (bins->smooth_sigma_bins > 0 && !d_spec_smooth) return QS_ERR_INVALID_ARG;
   if ((st = device_sms(&sms))) return st;
   Plan pl;
   make_plan(pl, bins, block, grid, sms);
@@ -586,8 +626,10 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.acc_spec = reinterpret_cast<unsigned long long*>(ws + pl.off_spec);
   p.acc_map = reinterpret_cast<unsigned long long*>(ws + pl.off_map);
   p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + pl.off_aeff);
+  p.acc_smooth = reinterpret_cast<unsigned long long*>(ws + pl.off_smooth);
   p.partials = reinterpret_cast<double*>(ws + pl.off_part);
   p.hist_in_smem = sm.hist ? 1 : 0;
+  p.smooth_in_smem = sm.smooth ? 1 : 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return QS_ERR_CUDA;
@@ -597,7 +639,8 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   else
     st = launch_scatter_prec<float>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);
   if (st) return st;
-  k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_moments);
+  k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_spec_smooth,
+                                 d_moments);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
 
@@ -679,7 +722,8 @@ int32_t noalloc_scratch(void** out) {
 extern "C" int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
                                       const qs_samples* samples, const qs_bins* bins,
                                       const qs_exec* exec, double* d_spectrum, double* d_divmap,
-                                      double* d_aeff_hist, qs_moments* d_moments, void* stream) {
+                                      double* d_aeff_hist, double* d_spec_smooth,
+                                      qs_moments* d_moments, void* stream) {
   // the size check comes first, so an oversized request fails before any
   // device set-up; qs_scatter then validates everything else
   if (validate_bins(bins) != QS_OK || !samples) return QS_ERR_INVALID_ARG;
@@ -691,5 +735,5 @@ extern "C" int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam
   if (st != QS_OK) return st;
   // qs_scatter zeroes the accumulators on the stream before its kernels run
   return qs_scatter(laser, beam, samples, bins, exec, d_spectrum, d_divmap, d_aeff_hist,
-                    d_moments, scratch, QS_NOALLOC_SCRATCH_BYTES, stream);
+                    d_spec_smooth, d_moments, scratch, QS_NOALLOC_SCRATCH_BYTES, stream);
 }

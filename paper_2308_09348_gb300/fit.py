@@ -1,0 +1,118 @@
+"""Differentiable forward model and gradient fit (reconstruction of laser and
+beam parameters from observables, the use the paper names in Sec. 6).
+
+``ScatterFn`` is a ``torch.autograd.Function``: its forward runs qs_scatter
+(moments + kernel-smoothed spectrum), its backward runs qs_scatter_grad, which
+recomputes every sample with tangents instead of storing per-sample state.
+The 8 parameters are (a0, w0_um, dx_um, dy_um, delay_fs, gamma_mean,
+rel_spread, div_rad).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+
+import torch
+
+from . import binding as B
+from . import inputs as I
+
+PARAMS = B.GRAD_PARAMS
+LASER_FIELDS = PARAMS[:5]
+BEAM_FIELDS = PARAMS[5:]
+
+
+@dataclass
+class Problem:
+    """Everything fixed during a fit: descriptor templates, samples, bins."""
+    laser: I.Laser
+    beam: I.Beam
+    bins: I.Bins
+    xi: list
+    w: torch.Tensor | None = None
+    precision: str = "f32"
+    out: B.Outputs | None = None
+
+    def descriptors(self, theta) -> tuple[I.Laser, I.Beam]:
+        v = [float(x) for x in theta]
+        lz = replace(self.laser, **dict(zip(LASER_FIELDS, v[:5])))
+        bm = replace(self.beam, **dict(zip(BEAM_FIELDS, v[5:])))
+        return lz, bm
+
+    def theta_of(self, laser=None, beam=None) -> torch.Tensor:
+        lz = laser or self.laser
+        bm = beam or self.beam
+        return torch.tensor([getattr(lz, k) for k in LASER_FIELDS] +
+                            [getattr(bm, k) for k in BEAM_FIELDS], dtype=torch.float64)
+
+
+class ScatterFn(torch.autograd.Function):
+    """theta (8,) -> (moments (13,), smoothed spectrum (n_bins,))."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, prob: Problem):
+        lz, bm = prob.descriptors(theta.detach().cpu())
+        if prob.out is None:
+            prob.out = B.Outputs(prob.bins, prob.xi[0].numel(), prob.xi[0].device, prob.precision)
+        out = B.qs_scatter(lz, bm, prob.xi, prob.bins, w=prob.w, precision=prob.precision,
+                           out=prob.out)
+        mom = out.moments.clone()
+        S = out.spec_smooth.clone()
+        ctx.prob = prob
+        ctx.desc = (lz, bm)
+        ctx.save_for_backward(mom)
+        ctx.theta_meta = (theta.dtype, theta.device)
+        return mom, S
+
+    @staticmethod
+    def backward(ctx, g_mom, g_S):
+        (mom,) = ctx.saved_tensors
+        prob = ctx.prob
+        lz, bm = ctx.desc
+        if g_mom is None:
+            g_mom = torch.zeros_like(mom)
+        g = B.qs_scatter_grad(lz, bm, prob.xi, prob.bins, mom, g_mom, g_S, w=prob.w,
+                              precision=prob.precision, out=prob.out)
+        dt, dev = ctx.theta_meta
+        return g.to(device=dev, dtype=dt), None
+
+
+MOMENT_INDEX = {k: i for i, k in enumerate(B.MOMENT_FIELDS)}
+
+
+def loss_fn(mom, S, target_mom, target_S, moment_weights: dict, spectrum_weight: float):
+    """Weighted squared error of selected moments (relative) and of the
+    smoothed spectrum (normalised by the target's total weight)."""
+    L = torch.zeros((), dtype=torch.float64, device=mom.device)
+    for k, c in moment_weights.items():
+        i = MOMENT_INDEX[k]
+        ref = target_mom[i]
+        L = L + c * ((mom[i] - ref) / (ref.abs() + 1e-30)) ** 2
+    if spectrum_weight and S.numel():
+        norm = target_S.sum().clamp_min(1e-30)
+        L = L + spectrum_weight * (((S - target_S) / norm) ** 2).sum() * S.numel()
+    return L
+
+
+DEFAULT_MOMENT_WEIGHTS = {"mean": 1.0, "spread": 1.0, "div_x": 1.0, "div_y": 1.0,
+                          "mean_aeff": 1.0}
+
+
+def fit(prob: Problem, theta0: torch.Tensor, target_mom, target_S, steps: int = 100,
+        lr: float = 0.02, scale: torch.Tensor | None = None, moment_weights=None,
+        spectrum_weight: float = 1.0, callback=None):
+    """Adam on theta / scale (unit-free steps).  Returns (theta, history)."""
+    mw = DEFAULT_MOMENT_WEIGHTS if moment_weights is None else moment_weights
+    scale = theta0.abs().clamp_min(1e-12) if scale is None else scale
+    z = (theta0 / scale).clone().requires_grad_(True)
+    opt = torch.optim.Adam([z], lr=lr)
+    hist = []
+    for it in range(steps):
+        opt.zero_grad()
+        mom, S = ScatterFn.apply(z * scale, prob)
+        L = loss_fn(mom, S, target_mom, target_S, mw, spectrum_weight)
+        L.backward()
+        opt.step()
+        hist.append(float(L))
+        if callback is not None:
+            callback(it, z.detach() * scale, float(L))
+    return (z.detach() * scale), hist

@@ -72,6 +72,7 @@ class Bins:
     theta_max: float = 0.0
     n_aeff: int = 0
     aeff_max: float = 0.0
+    smooth_sigma_bins: float = 0.0   # kernel-smoothed spectrum (0 = off)
 
 
 @dataclass(frozen=True)
@@ -122,6 +123,19 @@ def full_ll(n: int = 1 << 26) -> Workload:
     """The same beam and laser with the classical LL model (HBM-bound case)."""
     w = full_qfp(n)
     return replace(w, name="mc2p26_ll_4000", laser=replace(w.laser, model=MODEL_LL))
+
+
+def fit_qfp(n: int = 1 << 24) -> Workload:
+    """Differentiable fit: 2^24 FP32 samples, QFP, loss on the moments and a
+    256-bin spectrum smoothed with a Gaussian kernel of 2 bins."""
+    return Workload(
+        name="mc2p24_fit_qfp512",
+        laser=Laser(lambda_um=0.8, a0=20.0, w0_um=4.0, tau_fs=30.0, model=MODEL_QFP,
+                    dx_um=1.0, dy_um=-0.5, delay_fs=10.0, n_phase=512),
+        beam=Beam(gamma_mean=6000.0, rel_spread=0.08, sigma_x_um=3.0, sigma_y_um=3.0,
+                  sigma_z_um=10.0, div_rad=1.0e-3),
+        bins=Bins(n_bins=256, lo=0.0, hi=1.2 * 6000.0 * 1.32, smooth_sigma_bins=2.0),
+        n=n, seed=0x23080904, dtype="f32")
 
 
 def broadband_qfp(n: int = 1 << 27) -> Workload:

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.qs_version() == 1
+    assert lib.qs_version() == 2
     for s in range(6):
         assert lib.qs_status_string(s)
     assert lib.qs_status_string(99) == b"unknown status"
@@ -49,7 +49,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(B.qs_laser) == 8 * 8 + 4 * 4
     assert C.sizeof(B.qs_beam) == 10 * 8 + 2 * 4
     assert C.sizeof(B.qs_samples) == 8 + 8 * 8 + 8 + 2 * 4
-    assert C.sizeof(B.qs_bins) == 4 * 2 + 8 * 2 + 4 * 2 + 8 + 4 * 2 + 8
+    assert C.sizeof(B.qs_bins) == 4 * 2 + 8 * 2 + 4 * 2 + 8 + 4 * 2 + 8 + 8
     assert C.sizeof(B.qs_moments) == 13 * 8
     assert C.sizeof(B.qs_exec) == 16 + 2 * 8
 
@@ -61,8 +61,8 @@ def _call(lib, laser=None, beam=None, samples=None, bins=None, exe=None, moments
     S = samples or B.qs_samples(0, (C.c_void_p * 8)(), None, 0, 0)
     Bn = bins or B.make_bins(I.Bins())
     return lib.qs_scatter(C.byref(L), C.byref(Bm), C.byref(S), C.byref(Bn),
-                          C.byref(exe) if exe is not None else None, 256, 512, 768, moments,
-                          ws, ws_bytes, None)
+                          C.byref(exe) if exe is not None else None, 256, 512, 768, 1024,
+                          moments, ws, ws_bytes, None)
 
 
 def test_host_validation_rejects_bad_descriptors(lib):
@@ -77,7 +77,9 @@ def test_host_validation_rejects_bad_descriptors(lib):
         assert _call(lib, beam=B.make_beam(b)) == B.QS_ERR_INVALID_ARG, b
     bad_bins = [I.Bins(n_bins=4, lo=1.0, hi=1.0), I.Bins(n_bins=4, lo=0.0, hi=1.0, log_spaced=1),
                 I.Bins(n_tx=4, n_ty=0, theta_max=1.0), I.Bins(n_tx=4, n_ty=4, theta_max=0.0),
-                I.Bins(n_aeff=8, aeff_max=0.0), I.Bins(n_bins=-1)]
+                I.Bins(n_aeff=8, aeff_max=0.0), I.Bins(n_bins=-1),
+                I.Bins(n_bins=8, lo=1.0, hi=10.0, log_spaced=1, smooth_sigma_bins=2.0),
+                I.Bins(n_bins=0, smooth_sigma_bins=2.0), I.Bins(smooth_sigma_bins=-1.0)]
     for b in bad_bins:
         assert _call(lib, bins=B.make_bins(b)) == B.QS_ERR_INVALID_ARG, b
     # samples: n > 0 with a required stream missing, negative n, bad dtype
