@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 2
+#define QS_VERSION 3
 
 typedef enum {
     QS_OK = 0,
@@ -167,6 +167,8 @@ typedef struct qs_moments {
  *                     (0 = 32).  Each weight is rounded to a multiple of
  *                     2^-bits; every bin must stay below 2^(63-bits).
  *   block, grid       launch shape of the evaluation kernel (0 = tuned).
+ *   tile              samples per work item of qs_scatter_batch (0 = 2048;
+ *                     a multiple of 64, at most 1<<20); ignored elsewhere.
  *   ev_start, ev_stop optional cudaEvent_t handles (as void*): when set, they
  *                     are recorded on the call's stream immediately before and
  *                     after the evaluation kernel, so a caller can time that
@@ -174,6 +176,7 @@ typedef struct qs_moments {
  */
 typedef struct qs_exec {
     int32_t precision, weight_frac_bits, block, grid;
+    int32_t tile, reserved;
     void* ev_start;
     void* ev_stop;
 } qs_exec;
@@ -223,6 +226,40 @@ int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam, const qs_samples*
 int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_samples* samples,
                         const qs_bins* bins, const qs_exec* exec, const qs_sample_out* out,
                         void* stream);
+
+/*
+ * Batched shots (the paper's parallel plane-wave runs, Sec. 3.2, and the
+ * high-repetition-rate data sets of Sec. 6): n_shots independent
+ * integrations, each with its own laser and beam, in one persistent launch.
+ * Shot s owns samples [offsets[s], offsets[s+1]) of one concatenated
+ * structure of arrays.  Work items are tiles of exec->tile samples of one
+ * shot, pulled from a device counter; each tile's moment partials go to a
+ * slot of its own and are reduced per shot in tile order, so results do not
+ * depend on scheduling (repeated calls are bit-identical).
+ *   d_lasers, d_beams n_shots descriptors in DEVICE memory (validated on the
+ *                 device; an invalid shot, or one with n_phase > max_phase,
+ *                 gets W = 0 and nonfinite = -1 and no work)
+ *   d_offsets     n_shots + 1 non-decreasing int64 (device), offsets[0] >= 0,
+ *                 offsets[n_shots] <= samples->n (checked on the device: a
+ *                 shot whose range is invalid is treated as invalid)
+ *   samples       the concatenated streams (as for qs_scatter)
+ *   bins          energy spectrum only (n_tx = n_aeff = 0, no smoothing);
+ *                 shared bin count, range per shot from d_ranges if not NULL
+ *                 (n_shots pairs {lo, hi}, device) else bins->lo/hi
+ *   max_phase     upper bound of the shots' n_phase (QFP), 1..4096
+ *   d_spectra     n_shots x n_bins doubles (row per shot), or NULL if n_bins == 0
+ *   d_moments     n_shots qs_moments
+ * The call is a fixed sequence of one memset and five kernels on the stream
+ * and contains no host synchronisation.
+ */
+size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins* bins,
+                                int32_t max_phase, const qs_exec* exec);
+
+int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_beam* d_beams,
+                         const int64_t* d_offsets, const qs_samples* samples,
+                         const qs_bins* bins, const double* d_ranges, int32_t max_phase,
+                         const qs_exec* exec, double* d_spectra, qs_moments* d_moments,
+                         void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
  * Parameter order of qs_scatter_grad (the reconstruction use of Sec. 6):

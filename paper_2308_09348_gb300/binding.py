@@ -69,8 +69,8 @@ class qs_moments(C.Structure):
 
 class qs_exec(C.Structure):
     _fields_ = [("precision", C.c_int32), ("weight_frac_bits", C.c_int32),
-                ("block", C.c_int32), ("grid", C.c_int32), ("ev_start", C.c_void_p),
-                ("ev_stop", C.c_void_p)]
+                ("block", C.c_int32), ("grid", C.c_int32), ("tile", C.c_int32),
+                ("reserved", C.c_int32), ("ev_start", C.c_void_p), ("ev_stop", C.c_void_p)]
 
 
 class qs_sample_out(C.Structure):
@@ -115,6 +115,13 @@ def _lib():
                                           C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP,
                                           C.c_size_t, _VP]
             L.qs_scatter_grad.restype = C.c_int32
+            L.qs_batch_workspace_bytes.argtypes = [C.c_int32, C.c_int64, C.POINTER(qs_bins),
+                                                   C.c_int32, C.POINTER(qs_exec)]
+            L.qs_batch_workspace_bytes.restype = C.c_size_t
+            L.qs_scatter_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
+                                           C.POINTER(qs_bins), _VP, C.c_int32,
+                                           C.POINTER(qs_exec), _VP, _VP, _VP, C.c_size_t, _VP]
+            L.qs_scatter_batch.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -149,11 +156,12 @@ def _event_handle(ev):
     return ev.cuda_event
 
 
-def make_exec(precision="f32", weight_frac_bits=0, block=0, grid=0, events=None) -> qs_exec:
+def make_exec(precision="f32", weight_frac_bits=0, block=0, grid=0, events=None,
+              tile=0) -> qs_exec:
     prec = QS_F64 if precision in ("f64", QS_F64, torch.float64) else QS_F32
     e0, e1 = (None, None) if events is None else (_event_handle(events[0]),
                                                   _event_handle(events[1]))
-    return qs_exec(prec, int(weight_frac_bits), int(block), int(grid), e0, e1)
+    return qs_exec(prec, int(weight_frac_bits), int(block), int(grid), int(tile), 0, e0, e1)
 
 
 def make_samples(xi, w=None) -> tuple[qs_samples, list]:
@@ -347,3 +355,62 @@ def qs_scatter_grad(laser, beam, xi, bins, moments, dL_dmoments, dL_dsmooth=None
                                 out.ws_ptr, out.ws_bytes, _stream_ptr(stream))
     _check(st, "qs_scatter_grad")
     return g
+
+
+# ---- batched shots ----------------------------------------------------------
+
+def _struct_array_to_device(structs, ctype, device) -> torch.Tensor:
+    arr = (ctype * len(structs))(*structs)
+    raw = bytes(memoryview(arr).cast("B"))
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+class Batch:
+    """Device-side descriptors, outputs and workspace of one qs_scatter_batch
+    problem shape (reusable across calls and capturable in a CUDA graph)."""
+
+    def __init__(self, lasers, beams, offsets, bins: _inputs.Bins, n_total: int, device=None,
+                 ranges=None, precision="f32", tile=0, block=0, grid=0, max_phase=None):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.n_shots = len(lasers)
+        assert len(beams) == self.n_shots
+        self.bins = bins
+        self.precision = precision
+        self.tile, self.block, self.grid = tile, block, grid
+        self.max_phase = int(max_phase or max(int(l.n_phase) if l.model == _inputs.MODEL_QFP else 1
+                                              for l in lasers))
+        self.d_lasers = _struct_array_to_device([make_laser(l) for l in lasers], qs_laser, dev)
+        self.d_beams = _struct_array_to_device([make_beam(b) for b in beams], qs_beam, dev)
+        off = torch.as_tensor(offsets, dtype=torch.int64)
+        assert off.numel() == self.n_shots + 1
+        self.d_offsets = off.to(dev)
+        self.d_ranges = None if ranges is None else torch.as_tensor(
+            ranges, dtype=torch.float64).reshape(-1, 2).contiguous().to(dev)
+        self.spectra = torch.zeros(self.n_shots, max(bins.n_bins, 0), dtype=torch.float64, device=dev)
+        self.moments = torch.zeros(self.n_shots, len(MOMENT_FIELDS), dtype=torch.float64, device=dev)
+        e = make_exec(precision, 0, block, grid, None, tile)
+        b = make_bins(bins)
+        nbytes = _lib().qs_batch_workspace_bytes(self.n_shots, int(n_total), C.byref(b),
+                                                 self.max_phase, C.byref(e))
+        if nbytes == 0:
+            raise QsError(QS_ERR_INVALID_ARG, "qs_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        self.ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.ws_bytes = nbytes
+
+    def run(self, xi, w=None, stream=None):
+        s, keep = make_samples(xi, w)
+        self._keep = keep
+        b = make_bins(self.bins)
+        e = make_exec(self.precision, 0, self.block, self.grid, None, self.tile)
+        st = _lib().qs_scatter_batch(
+            self.n_shots, self.d_lasers.data_ptr(), self.d_beams.data_ptr(),
+            self.d_offsets.data_ptr(), C.byref(s), C.byref(b),
+            self.d_ranges.data_ptr() if self.d_ranges is not None else None, self.max_phase,
+            C.byref(e), self.spectra.data_ptr() if self.spectra.numel() else None,
+            self.moments.data_ptr(), self.ws_ptr, self.ws_bytes, _stream_ptr(stream))
+        _check(st, "qs_scatter_batch")
+        return self
+
+    def moments_dicts(self) -> list[dict]:
+        return [dict(zip(MOMENT_FIELDS, row)) for row in self.moments.cpu().tolist()]

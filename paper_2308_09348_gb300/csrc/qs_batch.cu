@@ -1,0 +1,415 @@
+// qs_batch.cu -- many shots in one persistent launch (qs_scatter_batch).
+//
+// B0 k_bsetup   one thread per shot: validate the device-side descriptors,
+//               derive the shot's launch constants, point them at its slice
+//               of the samples and of the accumulators, count its tiles.
+// B1 k_btable   one thread per (shot, phase cell): the shot's envelope table.
+// B2 k_bscan    one CTA: exclusive prefix sum of the tile counts.
+// B3 k_batch    persistent grid; each CTA pulls tiles from a device counter,
+//               stages the tile's shot constants and table in shared memory,
+//               evaluates the samples exactly as k_scatter does, writes the
+//               tile's moment partials to the tile's own slot and merges its
+//               shared-memory histogram into the shot's accumulators.
+// B4 k_bfinal   one warp per shot: partials summed in tile order, histograms
+//               converted, moments written.
+//
+// Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348 (Sec. 3.2: parallel
+// plane-wave runs; Sec. 6: high-repetition-rate data).
+#include "qscatter.h"
+#include "qs_device.cuh"
+#include "qs_derive.cuh"
+#include "qs_host.hpp"
+
+namespace qs {
+
+struct BatchArgs {
+  int32_t n_shots, max_phase, tile, wbits;
+  const qs_laser* lasers;
+  const qs_beam* beams;
+  const int64_t* offsets;
+  qs_samples samples;
+  qs_bins bins;
+  const double* ranges;
+  Params* shot;                 // [n_shots]
+  int64_t* tiles;               // [n_shots + 1] counts, then exclusive offsets
+  void* tables;                 // [n_shots * max_phase] float4 (FP32) or double (FP64)
+  unsigned long long* acc;      // [n_shots * (n_bins + 2)]
+  double* partials;             // [tiles * kNumMom]
+  unsigned long long* counter;  // work counter
+  int32_t precision, pad;
+};
+
+__global__ void k_bsetup(const BatchArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n_shots) return;
+  Params& p = a.shot[s];
+  const qs_laser L = a.lasers[s];
+  const qs_beam B = a.beams[s];
+  qs_bins b = a.bins;
+  if (a.ranges) {
+    b.lo = a.ranges[2 * s];
+    b.hi = a.ranges[2 * s + 1];
+  }
+  const int64_t o0 = a.offsets[s], o1 = a.offsets[s + 1];
+  bool ok = check_laser(L) == QS_OK && check_beam(B) == QS_OK && check_bins(b) == QS_OK &&
+            o0 >= 0 && o1 >= o0 && o1 <= a.samples.n &&
+            (L.model != QS_MODEL_QFP || L.n_phase <= a.max_phase);
+  if (!ok) {
+    memset(&p, 0, sizeof(Params));
+    p.n = -1;                    // invalid shot
+    a.tiles[s] = 0;
+    return;
+  }
+  derive_params(p, L, B, &b, a.wbits);
+  const size_t esz = a.samples.dtype == QS_F32 ? 4 : 8;
+  p.n = o1 - o0;
+  for (int k = 0; k < 8; ++k)
+    p.xi[k] = a.samples.xi[k] ? static_cast<const unsigned char*>(a.samples.xi[k]) + o0 * esz
+                              : nullptr;
+  p.w = a.samples.w ? static_cast<const unsigned char*>(a.samples.w) + o0 * esz : nullptr;
+  p.dtype = a.samples.dtype;
+  p.weighted = a.samples.w != nullptr;
+  p.acc_spec = a.bins.n_bins > 0 ? a.acc + (size_t)s * (a.bins.n_bins + 2) : nullptr;
+  a.tiles[s] = (p.n + a.tile - 1) / a.tile;
+}
+
+__global__ void k_btable(const BatchArgs a) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (int)(idx / a.max_phase), j = (int)(idx % a.max_phase);
+  if (s >= a.n_shots) return;
+  const Params& p = a.shot[s];
+  if (p.n < 0 || p.model != QS_MODEL_QFP || j >= p.n_phase) return;
+  if (a.precision == QS_F32)
+    table_entry(p, j, static_cast<float4*>(a.tables) + (size_t)s * a.max_phase);
+  else
+    table_entry(p, j, static_cast<double*>(a.tables) + (size_t)s * a.max_phase);
+}
+
+// Exclusive prefix sum of tiles[0..n) in place, total in tiles[n].
+__global__ void __launch_bounds__(1024) k_bscan(const BatchArgs a) {
+  __shared__ int64_t part[1024];
+  const int n = a.n_shots;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+  int64_t s = 0;
+  for (int i = b0; i < b1; ++i) s += a.tiles[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int64_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    a.tiles[n] = run;
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int i = b0; i < b1; ++i) {
+    const int64_t v = a.tiles[i];
+    a.tiles[i] = run;
+    run += v;
+  }
+}
+
+template <typename T, typename H>
+__global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const BatchArgs a) {
+  using TT = typename Tab<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Params& p = *reinterpret_cast<Params*>(smem);
+  const size_t par_bytes = (sizeof(Params) + 15) & ~(size_t)15;
+  TT* tab = reinterpret_cast<TT*>(smem + par_bytes);
+  const size_t tab_bytes = ((size_t)a.max_phase * sizeof(TT) + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem + par_bytes + tab_bytes);
+  H* hs = reinterpret_cast<H*>(smem + par_bytes + tab_bytes +
+                               (size_t)(blockDim.x >> 5) * kNumMom * sizeof(double));
+  // work-item broadcast slots live in the dynamic allocation, after the
+  // histogram, so the kernel has no static shared memory
+  const size_t hist_bytes =
+      ((size_t)(a.bins.n_bins > 0 ? a.bins.n_bins + 2 : 0) * sizeof(H) + 15) & ~(size_t)15;
+  int64_t& s_tile = *reinterpret_cast<int64_t*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes);
+  int& s_shot = *reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes + 8);
+  const int64_t total = a.tiles[a.n_shots];
+  const int64_t nspec = a.bins.n_bins > 0 ? (int64_t)a.bins.n_bins + 2 : 0;
+  int cur = -1;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)atomicAdd(a.counter, 1ull);
+      s_tile = t;
+      int s = -1;
+      if (t < total) {
+        // last shot whose first tile is <= t (shots with no tiles are skipped)
+        int lo = 0, hi = a.n_shots - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.tiles[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        s = lo;
+      }
+      s_shot = s;
+    }
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int s = s_shot;
+    if (t >= total) break;
+    if (s != cur) {
+      // stage the shot's constants and envelope table
+      const int nw = (int)(sizeof(Params) / 4);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.shot[s]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&p);
+      for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      if (p.model == QS_MODEL_QFP) {
+        const TT* tg = static_cast<const TT*>(a.tables) + (size_t)s * a.max_phase;
+        for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) tab[j] = tg[j];
+      }
+      cur = s;
+    }
+    for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x) hs[b] = 0;
+    __syncthreads();
+
+    double acc[kNumAcc];
+    acc_init(acc);
+    const int64_t first = (t - a.tiles[s]) * a.tile;
+    const int64_t last = min(p.n, first + a.tile);
+    if (sizeof(T) == 4 && p.model == QS_MODEL_QFP) {
+      for (int64_t k = first / 2 + threadIdx.x; 2 * k < last; k += blockDim.x) {
+        const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
+        Sample s0, s1;
+        eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+        accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+        if (i1 != i0) accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+      }
+    } else if (p.model == QS_MODEL_QFP) {
+      for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+        const Sample sm = eval_sample<T, true>(p, tab, i);
+        accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+      }
+    } else {
+      for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+        const Sample sm = eval_sample<T, false>(p, tab, i);
+        accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+      }
+    }
+    block_reduce_write(acc, red, a.partials + (size_t)t * kNumMom);
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x)
+      if (hs[b]) atomicAdd(&p.acc_spec[b], (unsigned long long)hs[b]);
+    __syncthreads();
+  }
+}
+
+// One warp per shot: moments from its tiles' partials in tile order.
+__global__ void k_bfinal(const BatchArgs a, double* spectra, qs_moments* moments) {
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= a.n_shots) return;
+  const Params& p = a.shot[s];
+  const int nb = a.bins.n_bins;
+  qs_moments m;
+  memset(&m, 0, sizeof(m));
+  if (p.n < 0) {
+    for (int b = lane; b < nb; b += 32) spectra[(size_t)s * nb + b] = 0.0;
+    if (lane == 0) {
+      m.nonfinite = -1.0;
+      moments[s] = m;
+    }
+    return;
+  }
+  const double scale = p.weighted ? 1.0 / p.wscale : 1.0;
+  const int64_t t0 = a.tiles[s], t1 = (s + 1 < a.n_shots) ? a.tiles[s + 1] : a.tiles[a.n_shots];
+  double tot = 0.0, mean_l0 = 0.0, m2_l0 = 0.0;
+  if (lane == 0) {
+    // (W, mean, M2) merged over the shot's tiles in tile order
+    double W = 0.0, mm = 0.0, M2 = 0.0;
+    for (int64_t t = t0; t < t1; ++t) {
+      const double* q = a.partials + (size_t)t * kNumMom;
+      welford_merge(W, mm, M2, q[0], q[1], q[2]);
+    }
+    tot = W;
+    mean_l0 = mm;
+    m2_l0 = M2;
+  } else if (lane >= 3 && lane < kNumMom) {
+    // Neumaier-compensated sums over the shot's tiles in tile order
+    double sm = 0.0, c = 0.0;
+    for (int64_t t = t0; t < t1; ++t) {
+      const double x = a.partials[(size_t)t * kNumMom + lane];
+      const double u = sm + x;
+      c += fabs(sm) >= fabs(x) ? (sm - u) + x : (x - u) + sm;
+      sm = u;
+    }
+    tot = sm + c;
+  }
+  double v[kNumMom];
+#pragma unroll
+  for (int k = 0; k < kNumMom; ++k) v[k] = __shfl_sync(0xffffffffu, tot, k);
+  v[1] = __shfl_sync(0xffffffffu, mean_l0, 0);
+  v[2] = __shfl_sync(0xffffffffu, m2_l0, 0);
+  const unsigned long long* acc = p.acc_spec;
+  for (int b = lane; b < nb; b += 32) spectra[(size_t)s * nb + b] = (double)acc[b] * scale;
+  if (lane == 0) {
+    const double W = v[0];
+    m.W = W;
+    if (W > 0.0) {
+      const double var = v[2] / W + v[3] / W;
+      m.mean = v[1];
+      m.spread = sqrt(var > 0.0 ? var : 0.0);
+      m.rel_spread = m.spread / m.mean;
+      m.div_x = sqrt(v[4] / W);
+      m.div_y = sqrt(v[5] / W);
+      m.div = sqrt((v[4] + v[5]) / W);
+      m.mean_aeff = v[6] / W;
+      m.mean_gamma0 = v[7] / W;
+    }
+    m.under = nb > 0 ? (double)acc[nb] * scale : 0.0;
+    m.over = nb > 0 ? (double)acc[nb + 1] * scale : 0.0;
+    m.nonfinite = v[8];
+    moments[s] = m;
+  }
+}
+
+}  // namespace qs
+
+using namespace qs;
+using namespace qs::detail;
+
+namespace {
+
+struct BatchPlan {
+  size_t off_counter = 0, off_params = 0, off_tiles = 0, off_tables = 0, off_acc = 0,
+         off_part = 0, bytes = 0;
+  int64_t max_tiles = 0;
+};
+
+bool batch_plan(BatchPlan& bp, int32_t n_shots, int64_t n_total, const qs_bins* bins,
+                int32_t max_phase, int precision, int tile) {
+  if (n_shots < 1 || n_total < 0 || max_phase < 1 || max_phase > kMaxPhase) return false;
+  bp.max_tiles = n_total / tile + n_shots + 1;
+  size_t off = 0;
+  bp.off_counter = off; off = align_up(off + 8, 256);
+  bp.off_params = off; off = align_up(off + (size_t)n_shots * sizeof(Params), 256);
+  bp.off_tiles = off; off = align_up(off + (size_t)(n_shots + 1) * 8, 256);
+  bp.off_tables = off;
+  off = align_up(off + (size_t)n_shots * max_phase * (precision == QS_F64 ? 8 : 16), 256);
+  bp.off_acc = off;
+  off = align_up(off + (size_t)n_shots * (bins->n_bins > 0 ? bins->n_bins + 2 : 0) * 8, 256);
+  bp.off_part = off; off = align_up(off + (size_t)bp.max_tiles * kNumMom * 8, 256);
+  bp.bytes = off;
+  return true;
+}
+
+int32_t batch_checks(int32_t n_shots, const qs_samples* samples, const qs_bins* bins,
+                     int32_t max_phase, const qs_exec* exec, int* prec, int* wbits, int* block,
+                     int* grid, int* tile) {
+  int32_t st;
+  if (n_shots < 1 || max_phase < 1 || max_phase > kMaxPhase) return QS_ERR_INVALID_ARG;
+  if ((st = validate_samples(samples)) || (st = validate_bins(bins))) return st;
+  if (bins->n_tx > 0 || bins->n_aeff > 0 || bins->smooth_sigma_bins > 0)
+    return QS_ERR_UNSUPPORTED;
+  if ((st = exec_opts(exec, prec, wbits, block, grid))) return st;
+  if ((st = exec_tile(exec, tile))) return st;
+  return QS_OK;
+}
+
+template <typename T, typename H>
+int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaStream_t st) {
+  using TT = typename Tab<T>::type;
+  const size_t smem = align_up(sizeof(Params), 16) + align_up((size_t)a.max_phase * sizeof(TT), 16) +
+                      (size_t)(block / 32) * kNumMom * sizeof(double) +
+                      align_up((size_t)(a.bins.n_bins > 0 ? a.bins.n_bins + 2 : 0) * sizeof(H), 16) +
+                      16;
+  if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
+  auto kern = k_batch<T, H>;
+  static bool attr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
+        cudaSuccess)
+      return cuda_fail();
+    attr[dev] = true;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
+    return cuda_fail();
+  const int grid = grid_req > 0 ? grid_req : sms * (occ > 0 ? occ : 1);
+  kern<<<grid, block, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins* bins,
+                                           int32_t max_phase, const qs_exec* exec) {
+  int prec, wbits, block, grid, tile;
+  if (!bins || validate_bins(bins) != QS_OK) return 0;
+  if (exec_opts(exec, &prec, &wbits, &block, &grid) || exec_tile(exec, &tile)) return 0;
+  BatchPlan bp;
+  if (!batch_plan(bp, n_shots, n_total, bins, max_phase, prec, tile)) return 0;
+  return bp.bytes;
+}
+
+extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
+                                    const qs_beam* d_beams, const int64_t* d_offsets,
+                                    const qs_samples* samples, const qs_bins* bins,
+                                    const double* d_ranges, int32_t max_phase,
+                                    const qs_exec* exec, double* d_spectra,
+                                    qs_moments* d_moments, void* d_workspace, size_t ws_bytes,
+                                    void* stream) {
+  int prec, wbits, block, grid, tile, sms;
+  int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
+                            &tile);
+  if (st) return st;
+  if (!d_lasers || !d_beams || !d_offsets || !d_moments) return QS_ERR_INVALID_ARG;
+  if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
+  if (block > 256) block = 256;
+  if ((st = device_sms(&sms))) return st;
+  BatchPlan bp;
+  if (!batch_plan(bp, n_shots, samples->n, bins, max_phase, prec, tile)) return QS_ERR_INVALID_ARG;
+  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < bp.bytes)
+    return QS_ERR_WORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_shots = n_shots;
+  a.max_phase = max_phase;
+  a.tile = tile;
+  a.wbits = wbits;
+  a.lasers = d_lasers;
+  a.beams = d_beams;
+  a.offsets = d_offsets;
+  a.samples = *samples;
+  a.bins = *bins;
+  a.ranges = d_ranges;
+  a.shot = reinterpret_cast<Params*>(ws + bp.off_params);
+  a.tiles = reinterpret_cast<int64_t*>(ws + bp.off_tiles);
+  a.tables = ws + bp.off_tables;
+  a.acc = reinterpret_cast<unsigned long long*>(ws + bp.off_acc);
+  a.partials = reinterpret_cast<double*>(ws + bp.off_part);
+  a.counter = reinterpret_cast<unsigned long long*>(ws + bp.off_counter);
+  a.precision = prec;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  // zero the work counter and the histogram accumulators
+  if (cudaMemsetAsync(ws + bp.off_counter, 0, 8, cs) != cudaSuccess) return cuda_fail();
+  if (bp.off_part > bp.off_acc &&
+      cudaMemsetAsync(ws + bp.off_acc, 0, bp.off_part - bp.off_acc, cs) != cudaSuccess)
+    return cuda_fail();
+  k_bsetup<<<(n_shots + 127) / 128, 128, 0, cs>>>(a);
+  const int64_t cells = (int64_t)n_shots * max_phase;
+  k_btable<<<(unsigned)((cells + 255) / 256), 256, 0, cs>>>(a);
+  k_bscan<<<1, 1024, 0, cs>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  if (prec == QS_F64)
+    st = samples->w ? launch_batch<double, unsigned long long>(a, block, grid, sms, cs)
+                    : launch_batch<double, unsigned int>(a, block, grid, sms, cs);
+  else
+    st = samples->w ? launch_batch<float, unsigned long long>(a, block, grid, sms, cs)
+                    : launch_batch<float, unsigned int>(a, block, grid, sms, cs);
+  if (st) return st;
+  const int64_t thr = (int64_t)n_shots * 32;
+  k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_moments);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}

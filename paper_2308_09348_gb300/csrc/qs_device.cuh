@@ -11,8 +11,14 @@
 namespace qs {
 
 constexpr int kMaxPhase = 4096;
-constexpr int kNumMom = 9;   // W, sum w d, sum w d^2, sum w V, sum w thx^2,
-                             // sum w thy^2, sum w a_eff, sum w gamma0, #excluded
+// Moment slot (per CTA or per tile) layout:
+//   0 W, 1 mean of mu, 2 M2 = sum w (mu - mean)^2, 3 sum w V, 4 sum w thx^2,
+//   5 sum w thy^2, 6 sum w a_eff, 7 sum w gamma0, 8 #excluded
+// (W, mean, M2) triples merge with the parallel-variance formula, the rest add.
+constexpr int kNumMom = 9;
+// Per-thread accumulator: as the slot, but entries 1 and 2 hold sum w d and
+// sum w d^2 with d = mu - shift, shift (entry 9) = the thread's first mu.
+constexpr int kNumAcc = 10;
 
 // Everything a launch needs, derived on the host from the descriptors and
 // passed by value (kernel parameter space: uniform, cached, stream-safe).
@@ -132,40 +138,43 @@ struct Sample {
 __device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
                                               double a, double g0, double& du_out,
                                               double& V_out) {
-  typedef double T;
-  const T LN2 = 0.69314718055994530942;
-  const T cK = p.cK, cchi = p.cchi, h = p.h;
-  const T c55 = 55.0 / (16.0 * 1.7320508075688772935);
-  const T hh2 = 0.5 * p.h * p.h;
-  T du = 0, V = 0, gprev = 1;
+  // explicit (uncontracted) operations: see op_fma below
+  const double LN2 = 0.69314718055994530942;
+  const double cK = p.cK, cchi = p.cchi, h = p.h;
+  const double c55 = 55.0 / (16.0 * 1.7320508075688772935);
+  const double hh2 = 0.5 * p.h * p.h;
+  double du = 0, V = 0, gprev = 1;
   const int N = p.n_phase;
 #pragma unroll 2
   for (int j = 0; j < N; ++j) {
-    T A = a * sG[j];
-    T K = cK * A * A;
-    T hK = h * K;
-    T dum = du + 0.5 * hK * gprev;
-    T mu = g0 / (1.0 + g0 * dum);
-    T chi = cchi * mu * A;
+    const double A = __dmul_rn(a, sG[j]);
+    const double K = __dmul_rn(__dmul_rn(cK, A), A);
+    const double hK = __dmul_rn(h, K);
+    const double dum = __fma_rn(__dmul_rn(0.5, hK), gprev, du);
+    const double mu = g0 / __fma_rn(g0, dum, 1.0);
+    const double chi = __dmul_rn(__dmul_rn(cchi, mu), A);
     // Gaunt factor and chi g'(chi)
-    T x1 = 1.0 + 1.7 * chi;
-    T L1 = LN2 * log2(x1);
-    T opc = 1.0 + chi;
-    T B = 1.0 + 4.8 * opc * L1 + 2.44 * chi * chi;
-    T t = exp2((-1.0 / 3.0) * log2(B));     // B^(-1/3)
-    T g = t * t;
-    T dB = 4.8 * L1 + (4.8 * 1.7) * opc / x1 + 4.88 * chi;
-    T chig1 = (-2.0 / 3.0) * g * (t * t * t) * dB * chi;
+    const double x1 = __fma_rn(1.7, chi, 1.0);
+    const double L1 = __dmul_rn(LN2, log2(x1));
+    const double opc = __dadd_rn(1.0, chi);
+    const double B = __fma_rn(__dmul_rn(4.8, opc), L1, __fma_rn(__dmul_rn(2.44, chi), chi, 1.0));
+    const double t = exp2(__dmul_rn(-1.0 / 3.0, log2(B)));     // B^(-1/3)
+    const double g = __dmul_rn(t, t);
+    const double dB = __fma_rn(4.8, L1, __fma_rn(4.8 * 1.7, opc / x1, __dmul_rn(4.88, chi)));
+    const double chig1 =
+        __dmul_rn(__dmul_rn(__dmul_rn(-2.0 / 3.0, g), __dmul_rn(__dmul_rn(t, t), t)),
+                  __dmul_rn(dB, chi));
     // second-moment factor
-    T L2 = LN2 * log2(1.0 + 12.93 * chi);
-    T B2 = 1.0 + (1.0 + 4.1 * chi) * L2 + 4.75 * chi * chi;
-    T h2 = exp2((-7.0 / 6.0) * log2(B2));
+    const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
+    const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
+    const double h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
     // updates
-    du = du + hK * g;
-    T lam = -2.0 * K * mu * (2.0 * g + chig1);
-    T D2 = c55 * K * mu * mu * mu * chi * h2;
-    T r = lam * V + D2;
-    V = V + h * r + hh2 * lam * r;
+    du = __fma_rn(hK, g, du);
+    const double lam = __dmul_rn(__dmul_rn(__dmul_rn(-2.0, K), mu), __fma_rn(2.0, g, chig1));
+    const double D2 = __dmul_rn(__dmul_rn(__dmul_rn(c55, K), __dmul_rn(__dmul_rn(mu, mu), mu)),
+                                __dmul_rn(chi, h2));
+    const double r = __fma_rn(lam, V, D2);
+    V = __fma_rn(__dmul_rn(hh2, lam), r, __fma_rn(h, r, V));
     gprev = g;
   }
   du_out = du;
@@ -243,36 +252,51 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
   V_out = V;
 }
 
+// Uncontracted IEEE operations (the _rn intrinsics are never fused), so the
+// per-sample arithmetic is the same instruction sequence in every kernel
+// that inlines it (fused histograms equal histograms of per-sample records,
+// batched shots equal single-shot calls, bit for bit).
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // a_eff at the crossing point and the decoded sample (rows a1-a3).
 template <typename T>
 __device__ __forceinline__ T focus(const Params& p, int64_t i, double& gamma0, T& thx, T& thy) {
-  T xi0 = (T)load_elem(p.xi[0], i, p.dtype);
-  T xi1 = (T)load_elem(p.xi[1], i, p.dtype);
-  T xi2 = (T)load_elem(p.xi[2], i, p.dtype);
-  double xi3 = load_elem(p.xi[3], i, p.dtype);
-  T xi4 = (T)load_elem(p.xi[4], i, p.dtype);
-  T xi5 = (T)load_elem(p.xi[5], i, p.dtype);
-  T x = (T)p.bdx + (T)p.sx * xi0;
-  T y = (T)p.bdy + (T)p.sy * xi1;
-  T z = (T)p.sz * xi2;
-  gamma0 = p.flat ? p.glo + p.gspan * xi3 : p.gmean * (1.0 + p.spread * xi3);
+  const T xi0 = (T)load_elem(p.xi[0], i, p.dtype);
+  const T xi1 = (T)load_elem(p.xi[1], i, p.dtype);
+  const T xi2 = (T)load_elem(p.xi[2], i, p.dtype);
+  const double xi3 = load_elem(p.xi[3], i, p.dtype);
+  const T xi4 = (T)load_elem(p.xi[4], i, p.dtype);
+  const T xi5 = (T)load_elem(p.xi[5], i, p.dtype);
+  // decode (reparameterised)
+  const T x = op_fma((T)p.sx, xi0, (T)p.bdx);
+  const T y = op_fma((T)p.sy, xi1, (T)p.bdy);
+  const T z = op_mul((T)p.sz, xi2);
+  gamma0 = p.flat ? __fma_rn(p.gspan, xi3, p.glo) : __dmul_rn(p.gmean, __fma_rn(p.spread, xi3, 1.0));
   if (gamma0 < 1.0) gamma0 = 1.0;
-  thx = (T)p.div * xi4;
-  thy = (T)p.div * xi5;
+  thx = op_mul((T)p.div, xi4);
+  thy = op_mul((T)p.div, xi5);
   // collision geometry: crossing of the pulse peak (factor 2 of Eq. 1)
-  T ct = (T)0.5 * (z + (T)p.c_delay);
-  T zs = (T)0.5 * (z - (T)p.c_delay);
-  T xs = x + thx * ct - (T)p.ldx;
-  T ys = y + thy * ct - (T)p.ldy;
-  T rho2 = xs * xs + ys * ys;
+  const T cdel = (T)p.c_delay;
+  const T ct = op_mul((T)0.5, op_add(z, cdel));
+  const T zs = op_mul((T)0.5, op_sub(z, cdel));
+  const T xs = op_sub(op_fma(thx, ct, x), (T)p.ldx);
+  const T ys = op_sub(op_fma(thy, ct, y), (T)p.ldy);
+  const T rho2 = op_fma(xs, xs, op_mul(ys, ys));
   // local Gaussian focus, Eq. 2
-  T zq = zs * (T)p.inv_zR;
-  T q = (T)1 + zq * zq;
-  T rq = M<T>::rcp(q);
+  const T zq = op_mul(zs, (T)p.inv_zR);
+  const T q = op_fma(zq, zq, (T)1);
+  const T E = op_mul(op_mul(rho2, (T)p.inv_w0sq), M<T>::rcp(q));
   if (sizeof(T) == 4)
-    return (T)p.a0 * M<T>::rsqrt(q) *
-           M<T>::ex2(-(T)1.4426950408889634074 * rho2 * (T)p.inv_w0sq * rq);
-  return (T)p.a0 * M<T>::rsqrt(q) * (T)exp((double)(-rho2 * (T)p.inv_w0sq * rq));
+    return op_mul(op_mul((T)p.a0, M<T>::rsqrt(q)),
+                  M<T>::ex2(op_mul(-(T)1.4426950408889634074, E)));
+  return op_mul(op_mul((T)p.a0, M<T>::rsqrt(q)), (T)exp(-(double)E));
 }
 
 // One beam sample through the model, in the paper's order (rows a1-a6).
@@ -291,18 +315,19 @@ __device__ __forceinline__ Sample eval_sample(const Params& p,
     // FP64 path
     const double ad = (double)a;
     if (!QFP) {
-      mu = gamma0 / (1.0 + p.cRR * gamma0 * ad * ad);    // Eq. 3, a0 -> a_eff
+      // Eq. 3, a0 -> a_eff
+      mu = gamma0 / __fma_rn(__dmul_rn(__dmul_rn(p.cRR, gamma0), ad), ad, 1.0);
     } else {
       double du;
       qfp_integrate(p, reinterpret_cast<const double*>(tab), ad, gamma0, du, V);
-      mu = gamma0 / (1.0 + gamma0 * du);
+      mu = gamma0 / __fma_rn(gamma0, du, 1.0);
     }
     double theta_e = 0.0, gout = mu, tx = (double)thx;
     if (QFP) {
       const double sv = V > 0.0 ? sqrt(V) : 0.0;
-      theta_e = p.kappa_s * ad * sv / (mu * mu);          // Eq. 8
-      tx += theta_e * load_elem(p.xi[6], i, p.dtype);
-      gout = mu + sv * load_elem(p.xi[7], i, p.dtype);
+      theta_e = __dmul_rn(__dmul_rn(p.kappa_s, ad), sv) / __dmul_rn(mu, mu);   // Eq. 8
+      tx = __fma_rn(theta_e, load_elem(p.xi[6], i, p.dtype), tx);
+      gout = __fma_rn(sv, load_elem(p.xi[7], i, p.dtype), mu);
     }
     s.theta_e = theta_e; s.tx = tx; s.gout = gout;
   } else {
@@ -392,6 +417,139 @@ __device__ __forceinline__ int aeff_bin(const Params& p, double a) {
   double f = a * p.a_scale;
   if (f >= 0.0 && f < (double)p.n_aeff) return (int)f;
   return p.n_aeff;
+}
+
+// Merge of two (weight, mean, central sum of squares) triples (the parallel
+// form of the variance recurrence): exact when one side is empty, no
+// cancellation between large raw moments.
+__device__ __forceinline__ void welford_merge(double& W, double& m, double& M2, double Wb,
+                                              double mb, double M2b) {
+  if (!(Wb > 0.0)) return;
+  if (!(W > 0.0)) {
+    W = Wb;
+    m = mb;
+    M2 = M2b;
+    return;
+  }
+  const double Wn = W + Wb;
+  const double d = mb - m;
+  const double f = Wb / Wn;
+  m = fma(d, f, m);
+  M2 = M2 + M2b + d * d * W * f;
+  W = Wn;
+}
+
+__device__ __forceinline__ void acc_init(double (&acc)[kNumAcc]) {
+#pragma unroll
+  for (int k = 0; k < kNumAcc; ++k) acc[k] = 0.0;
+  acc[9] = __longlong_as_double(0x7ff8000000000000ll);   // no shift yet (NaN)
+}
+
+// Fixed-order block reduction of the per-thread accumulators into one
+// moment slot out[0..kNumMom): warp shuffle tree, then warps in order.
+__device__ __forceinline__ void block_reduce_write(double (&acc)[kNumAcc], double* red,
+                                                   double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[kNumMom];
+  v[0] = acc[0];
+  v[1] = 0.0;
+  v[2] = 0.0;
+  if (acc[0] > 0.0) {
+    const double q = acc[1] / acc[0];
+    v[1] = acc[9] + q;
+    v[2] = fmax(acc[2] - acc[1] * q, 0.0);
+  }
+#pragma unroll
+  for (int k = 3; k < kNumMom; ++k) v[k] = acc[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double u[kNumMom];
+#pragma unroll
+    for (int k = 0; k < kNumMom; ++k) u[k] = __shfl_down_sync(0xffffffffu, v[k], o);
+    welford_merge(v[0], v[1], v[2], u[0], u[1], u[2]);
+#pragma unroll
+    for (int k = 3; k < kNumMom; ++k) v[k] += u[k];
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < kNumMom; ++k) red[warp * kNumMom + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double W = 0.0, m = 0.0, M2 = 0.0, sm[kNumMom] = {};
+    for (int w = 0; w < nw; ++w) {
+      welford_merge(W, m, M2, red[w * kNumMom], red[w * kNumMom + 1], red[w * kNumMom + 2]);
+      for (int k = 3; k < kNumMom; ++k) sm[k] += red[w * kNumMom + k];
+    }
+    out[0] = W;
+    out[1] = m;
+    out[2] = M2;
+    for (int k = 3; k < kNumMom; ++k) out[k] = sm[k];
+  }
+}
+
+// Smoothed-spectrum deposit of one sample (fixed point, like the weighted
+// histograms): S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)).
+template <typename T>
+__device__ __forceinline__ void deposit_smooth(const Params& p, double gout, double w,
+                                               unsigned long long* dst) {
+  const double t = (gout - p.lo) * p.inv_w;
+  if (!(t > -1e9 && t < 1e9)) return;
+  int k0, k1;
+  smooth_range(p, t, &k0, &k1);
+  const double wq = w * p.smooth_pref * p.wscale;
+  for (int k = k0; k <= k1; ++k) {
+    const double d = (double)k + 0.5 - t;
+    double e;
+    if (sizeof(T) == 4) e = (double)M<float>::ex2(-(float)(d * d * p.smooth_c));
+    else e = exp2(-d * d * p.smooth_c);
+    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * e));
+  }
+}
+
+// One evaluated sample into the moment partials and histograms (rows a7-a8).
+template <typename T, typename H, bool SHIST>
+__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i,
+                                           double (&acc)[kNumAcc], H* hs, H* hm, H* ha,
+                                           unsigned long long* hsm, int64_t nspec, int64_t nmap,
+                                           int64_t naeff) {
+  const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+  const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
+                  isfinite(w) && w >= 0.0;
+  if (!ok) {
+    acc[8] += 1.0;
+    return;
+  }
+  if (isnan(acc[9])) acc[9] = s.mu;                      // the thread's shift
+  const double d = s.mu - acc[9];
+  acc[0] += w;
+  acc[1] = fma(w, d, acc[1]);
+  acc[2] = fma(w * d, d, acc[2]);
+  acc[3] = fma(w, s.V, acc[3]);
+  acc[4] = fma(w, fma(s.thx0, s.thx0, s.theta_e * s.theta_e), acc[4]);
+  acc[5] = fma(w, s.thy0 * s.thy0, acc[5]);
+  acc[6] = fma(w, s.aeff, acc[6]);
+  acc[7] = fma(w, s.gamma0, acc[7]);
+  const unsigned long long q =
+      p.weighted ? (unsigned long long)__double2ll_rn(w * p.wscale) : 1ull;
+  if (nspec) {
+    const int b = energy_bin(p, s.gout);
+    const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+    if (SHIST) atomicAdd(&hs[slot], (H)q);
+    else atomicAdd(&p.acc_spec[slot], q);
+  }
+  if (nmap) {
+    const int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
+    const int64_t slot = c < 0 ? nmap - 1 : c;
+    if (SHIST) atomicAdd(&hm[slot], (H)q);
+    else atomicAdd(&p.acc_map[slot], q);
+  }
+  if (naeff) {
+    const int slot = aeff_bin(p, s.aeff);
+    if (SHIST) atomicAdd(&ha[slot], (H)q);
+    else atomicAdd(&p.acc_aeff[slot], q);
+  }
+  if (hsm) deposit_smooth<T>(p, s.gout, w, hsm);
 }
 
 }  // namespace qs

@@ -341,12 +341,12 @@ int32_t launch_grad(const Params& p, int block, int sms, int grid_req, int gmax,
   if (dev >= 0 && dev < 64 && !attr[dev]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
         cudaSuccess)
-      return QS_ERR_CUDA;
+      return cuda_fail();
     attr[dev] = true;
   }
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
-    return QS_ERR_CUDA;
+    return cuda_fail();
   const int grid = pick_grid(occ, sms, block, grid_req, p.n, gmax);
   kern<<<grid, block, smem, st>>>(p, mom, dLdm, dLdS);
   *grid_out = grid;

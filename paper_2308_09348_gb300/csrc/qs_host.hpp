@@ -18,6 +18,7 @@ int32_t validate_beam(const qs_beam* B);
 int32_t validate_bins(const qs_bins* b);
 int32_t validate_samples(const qs_samples* s);
 int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int* grid);
+int32_t exec_tile(const qs_exec* e, int* tile);
 void fill_params(Params& p, const qs_laser* L, const qs_beam* B, const qs_samples* S,
                  const qs_bins* b, int wbits);
 int32_t device_sms(int* sms);
@@ -41,6 +42,13 @@ struct Smem {
 };
 Smem smem_plan(const Plan& pl, int precision, bool qfp, int n_phase, bool weighted, int block);
 int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int gmax);
+
+// A failed runtime call: clear the (non-sticky) error state so that it does
+// not surface in the caller's next, unrelated CUDA call, and report it.
+inline int32_t cuda_fail() {
+  (void)cudaGetLastError();
+  return QS_ERR_CUDA;
+}
 
 }  // namespace detail
 }  // namespace qs

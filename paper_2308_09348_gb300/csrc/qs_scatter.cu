@@ -11,6 +11,7 @@
 #include "qscatter.h"
 #include "qs_device.cuh"
 #include "qs_host.hpp"
+#include "qs_derive.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -23,61 +24,9 @@ namespace qs {
 // ---------------------------------------------------------------------------
 namespace detail {
 
-constexpr double kC = 0.299792458;          // um / fs
-constexpr double kRe = 2.8179403262e-9;     // classical electron radius, um
-constexpr double kLbarC = 3.8615926796e-7;  // reduced Compton wavelength, um
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kGaussWindow = 2.5;        // half-window in units of Phi
-static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
-
-int32_t validate_laser(const qs_laser* L) {
-  if (!L) return QS_ERR_INVALID_ARG;
-  if (!finite_pos(L->lambda_um) || !finite_nonneg(L->a0) || !finite_pos(L->w0_um) ||
-      !finite_pos(L->tau_fs) || !std::isfinite(L->dx_um) || !std::isfinite(L->dy_um) ||
-      !std::isfinite(L->delay_fs) || !finite_nonneg(L->div_prefactor))
-    return QS_ERR_INVALID_ARG;
-  if (L->envelope != QS_ENV_GAUSS && L->envelope != QS_ENV_SIN2) return QS_ERR_INVALID_ARG;
-  if (L->model != QS_MODEL_LL && L->model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
-  if (L->model == QS_MODEL_QFP && (L->n_phase < 1 || L->n_phase > kMaxPhase))
-    return QS_ERR_INVALID_ARG;
-  return QS_OK;
-}
-
-int32_t validate_beam(const qs_beam* B) {
-  if (!B) return QS_ERR_INVALID_ARG;
-  const double v[] = {B->gamma_mean, B->rel_spread, B->gamma_lo, B->gamma_hi, B->sigma_x_um,
-                      B->sigma_y_um, B->sigma_z_um, B->div_rad, B->dx_um, B->dy_um};
-  for (double x : v)
-    if (!std::isfinite(x)) return QS_ERR_INVALID_ARG;
-  if (B->sigma_x_um < 0 || B->sigma_y_um < 0 || B->sigma_z_um < 0 || B->div_rad < 0)
-    return QS_ERR_INVALID_ARG;
-  if (B->flat_energy) {
-    if (!(B->gamma_hi >= B->gamma_lo) || B->gamma_lo < 0) return QS_ERR_INVALID_ARG;
-  } else if (!(B->gamma_mean > 0) || B->rel_spread < 0) {
-    return QS_ERR_INVALID_ARG;
-  }
-  return QS_OK;
-}
-
-int32_t validate_bins(const qs_bins* b) {
-  if (!b) return QS_ERR_INVALID_ARG;
-  if (b->n_bins < 0 || b->n_tx < 0 || b->n_ty < 0 || b->n_aeff < 0) return QS_ERR_INVALID_ARG;
-  if (b->n_bins > (1 << 22) || b->n_aeff > (1 << 22)) return QS_ERR_INVALID_ARG;
-  if ((int64_t)b->n_tx * b->n_ty > (int64_t)1 << 24) return QS_ERR_INVALID_ARG;
-  if (b->n_bins > 0) {
-    if (!std::isfinite(b->lo) || !std::isfinite(b->hi) || !(b->hi > b->lo))
-      return QS_ERR_INVALID_ARG;
-    if (b->log_spaced && !(b->lo > 0)) return QS_ERR_INVALID_ARG;
-  }
-  if ((b->n_tx > 0) != (b->n_ty > 0)) return QS_ERR_INVALID_ARG;
-  if (b->n_tx > 0 && !finite_pos(b->theta_max)) return QS_ERR_INVALID_ARG;
-  if (b->n_aeff > 0 && !finite_pos(b->aeff_max)) return QS_ERR_INVALID_ARG;
-  if (!finite_nonneg(b->smooth_sigma_bins)) return QS_ERR_INVALID_ARG;
-  if (b->smooth_sigma_bins > 0 && (b->n_bins <= 0 || b->log_spaced || b->smooth_sigma_bins > 64))
-    return QS_ERR_INVALID_ARG;
-  return QS_OK;
-}
+int32_t validate_laser(const qs_laser* L) { return L ? check_laser(*L) : QS_ERR_INVALID_ARG; }
+int32_t validate_beam(const qs_beam* B) { return B ? check_beam(*B) : QS_ERR_INVALID_ARG; }
+int32_t validate_bins(const qs_bins* b) { return b ? check_bins(*b) : QS_ERR_INVALID_ARG; }
 
 int32_t validate_samples(const qs_samples* s) {
   if (!s) return QS_ERR_INVALID_ARG;
@@ -90,6 +39,12 @@ int32_t validate_samples(const qs_samples* s) {
   for (int k = 0; k < 8; ++k)
     if (s->xi[k] && ((uintptr_t)s->xi[k] % esz)) return QS_ERR_INVALID_ARG;
   if (s->w && ((uintptr_t)s->w % esz)) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+int32_t exec_tile(const qs_exec* e, int* tile) {
+  *tile = (e && e->tile) ? e->tile : 2048;
+  if (*tile < 64 || *tile > (1 << 20) || (*tile % 64)) return QS_ERR_INVALID_ARG;
   return QS_OK;
 }
 
@@ -107,86 +62,12 @@ int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int*
 
 void fill_params(Params& p, const qs_laser* L, const qs_beam* B, const qs_samples* S,
                  const qs_bins* b, int wbits) {
-  std::memset(&p, 0, sizeof(p));
-  const double k = 2.0 * kPi / L->lambda_um;
-  const double omega0 = kC * k;
-  const double zR = kPi * L->w0_um * L->w0_um / L->lambda_um;
-  const double Rc = kRe * k;
-  const double aS = 1.0 / (k * kLbarC);
-  const double Phi = omega0 * L->tau_fs;
-  const double PhiT = Phi / (1.0 - (2.0 / kPi) * std::asin(std::pow(2.0, -0.25)));
-  double lo, hi, intG2;
-  if (L->envelope == QS_ENV_GAUSS) {
-    lo = -kGaussWindow * Phi;
-    hi = kGaussWindow * Phi;
-    intG2 = Phi * std::sqrt(kPi / (4.0 * std::log(2.0)));
-  } else {
-    lo = 0.0;
-    hi = PhiT;
-    intG2 = 3.0 * PhiT / 8.0;
-  }
-  p.a0 = L->a0;
-  p.inv_w0sq = 1.0 / (L->w0_um * L->w0_um);
-  p.inv_zR = 1.0 / zR;
-  p.ldx = L->dx_um;
-  p.ldy = L->dy_um;
-  p.c_delay = kC * L->delay_fs;
-  p.cRR = (2.0 / 3.0) * Rc * intG2;
-  p.cK = (2.0 / 3.0) * Rc;
-  p.cchi = std::sqrt(2.0) / aS;
-  p.n_phase = L->model == QS_MODEL_QFP ? L->n_phase : 1;
-  p.h = (hi - lo) / (double)p.n_phase;
-  p.win_lo = lo;
-  p.Phi = Phi;
-  p.PhiT = PhiT;
-  p.kappa_s = L->div_prefactor * std::sqrt(2.0 / kPi);
-  p.envelope = L->envelope;
-  p.model = L->model;
-
-  p.gmean = B->gamma_mean;
-  p.spread = B->rel_spread;
-  p.glo = B->gamma_lo;
-  p.gspan = B->gamma_hi - B->gamma_lo;
-  p.sx = B->sigma_x_um;
-  p.sy = B->sigma_y_um;
-  p.sz = B->sigma_z_um;
-  p.div = B->div_rad;
-  p.bdx = B->dx_um;
-  p.bdy = B->dy_um;
-  p.flat = B->flat_energy ? 1 : 0;
-
+  derive_params(p, *L, *B, b, wbits);
   p.n = S->n;
   for (int i = 0; i < 8; ++i) p.xi[i] = S->xi[i];
   p.w = S->w;
   p.dtype = S->dtype;
   p.weighted = S->w != nullptr;
-
-  if (b) {
-    p.n_bins = b->n_bins;
-    p.log_spaced = b->log_spaced;
-    p.lo = b->lo;
-    if (b->n_bins > 0) {
-      p.inv_w = (double)b->n_bins / (b->hi - b->lo);
-      if (b->log_spaced) p.log_scale = (double)b->n_bins / std::log(b->hi / b->lo);
-    }
-    p.n_tx = b->n_tx;
-    p.n_ty = b->n_ty;
-    p.tmax = b->theta_max;
-    if (b->n_tx > 0) {
-      p.tsx = (double)b->n_tx / (2.0 * b->theta_max);
-      p.tsy = (double)b->n_ty / (2.0 * b->theta_max);
-    }
-    p.n_aeff = b->n_aeff;
-    if (b->n_aeff > 0) p.a_scale = (double)b->n_aeff / b->aeff_max;
-    if (b->smooth_sigma_bins > 0) {
-      const double sg = b->smooth_sigma_bins;
-      p.smooth_sigma = sg;
-      p.smooth_pref = 1.0 / (sg * std::sqrt(2.0 * kPi));
-      p.smooth_c = 1.4426950408889634074 / (2.0 * sg * sg);
-    }
-  }
-  p.wscale = std::ldexp(1.0, wbits);
-  p.gamma_ref = B->flat_energy ? 0.5 * (B->gamma_lo + B->gamma_hi) : B->gamma_mean;
 }
 
 struct DevInfo {
@@ -271,89 +152,6 @@ using namespace detail;
 // kernels
 // ---------------------------------------------------------------------------
 
-// Fixed-order block reduction of kNumMom doubles into out[0..kNumMom).
-__device__ __forceinline__ void block_reduce_write(double (&acc)[kNumMom], double* red,
-                                                   double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kNumMom; ++k) {
-    double v = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp * kNumMom + k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNumMom) {
-    const int nw = blockDim.x >> 5;
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w * kNumMom + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-}
-
-// One evaluated sample into the moment partials and histograms (rows a7-a8).
-// Smoothed-spectrum deposit of one sample (fixed point, like the weighted
-// histograms): S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)).
-template <typename T>
-__device__ __forceinline__ void deposit_smooth(const Params& p, double gout, double w,
-                                               unsigned long long* dst) {
-  const double t = (gout - p.lo) * p.inv_w;
-  if (!(t > -1e9 && t < 1e9)) return;
-  int k0, k1;
-  smooth_range(p, t, &k0, &k1);
-  const double wq = w * p.smooth_pref * p.wscale;
-  for (int k = k0; k <= k1; ++k) {
-    const double d = (double)k + 0.5 - t;
-    double e;
-    if (sizeof(T) == 4) e = (double)M<float>::ex2(-(float)(d * d * p.smooth_c));
-    else e = exp2(-d * d * p.smooth_c);
-    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * e));
-  }
-}
-
-template <typename T, typename H, bool SHIST>
-__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i,
-                                           double (&acc)[kNumMom], H* hs, H* hm, H* ha,
-                                           unsigned long long* hsm, int64_t nspec, int64_t nmap,
-                                           int64_t naeff) {
-  const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
-  const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
-                  isfinite(w) && w >= 0.0;
-  if (!ok) {
-    acc[8] += 1.0;
-    return;
-  }
-  const double d = s.mu - p.gamma_ref;
-  acc[0] += w;
-  acc[1] = fma(w, d, acc[1]);
-  acc[2] = fma(w * d, d, acc[2]);
-  acc[3] = fma(w, s.V, acc[3]);
-  acc[4] = fma(w, fma(s.thx0, s.thx0, s.theta_e * s.theta_e), acc[4]);
-  acc[5] = fma(w, s.thy0 * s.thy0, acc[5]);
-  acc[6] = fma(w, s.aeff, acc[6]);
-  acc[7] = fma(w, s.gamma0, acc[7]);
-  const unsigned long long q =
-      p.weighted ? (unsigned long long)__double2ll_rn(w * p.wscale) : 1ull;
-  if (nspec) {
-    const int b = energy_bin(p, s.gout);
-    const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
-    if (SHIST) atomicAdd(&hs[slot], (H)q);
-    else atomicAdd(&p.acc_spec[slot], q);
-  }
-  if (nmap) {
-    const int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
-    const int64_t slot = c < 0 ? nmap - 1 : c;
-    if (SHIST) atomicAdd(&hm[slot], (H)q);
-    else atomicAdd(&p.acc_map[slot], q);
-  }
-  if (naeff) {
-    const int slot = aeff_bin(p, s.aeff);
-    if (SHIST) atomicAdd(&ha[slot], (H)q);
-    else atomicAdd(&p.acc_aeff[slot], q);
-  }
-  if (hsm) deposit_smooth<T>(p, s.gout, w, hsm);
-}
-
 // K1: fused evaluation + histograms + moment partials.  T: per-sample
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
@@ -385,9 +183,8 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
     for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x) ssm[b] = 0;
   __syncthreads();
 
-  double acc[kNumMom];
-#pragma unroll
-  for (int k = 0; k < kNumMom; ++k) acc[k] = 0.0;
+  double acc[kNumAcc];
+  acc_init(acc);
 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,8 +225,18 @@ __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, dou
                                                    double* smooth, qs_moments* mom) {
   __shared__ double tot[kNumMom];
   const double scale = p.weighted ? 1.0 / p.wscale : 1.0;
-  if (threadIdx.x < kNumMom) {
-    // Neumaier-compensated sum over CTA partials in CTA order
+  if (threadIdx.x == 0) {
+    // (W, mean, M2) merged over CTA slots in CTA order
+    double W = 0.0, m = 0.0, M2 = 0.0;
+    for (int b = 0; b < grid; ++b) {
+      const double* q = p.partials + (size_t)b * kNumMom;
+      welford_merge(W, m, M2, q[0], q[1], q[2]);
+    }
+    tot[0] = W;
+    tot[1] = m;
+    tot[2] = M2;
+  } else if (threadIdx.x >= 3 && threadIdx.x < kNumMom) {
+    // Neumaier-compensated sum over CTA slots in CTA order
     double s = 0.0, c = 0.0;
     for (int b = 0; b < grid; ++b) {
       double x = p.partials[(size_t)b * kNumMom + threadIdx.x];
@@ -456,9 +263,8 @@ __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, dou
     m.mean = m.spread = m.rel_spread = m.div_x = m.div_y = m.div = m.mean_aeff = 0.0;
     m.mean_gamma0 = 0.0;
     if (W > 0.0) {
-      const double m1 = tot[1] / W;
-      double var = tot[2] / W - m1 * m1 + tot[3] / W;
-      m.mean = p.gamma_ref + m1;
+      const double var = tot[2] / W + tot[3] / W;
+      m.mean = tot[1];
       m.spread = sqrt(var > 0.0 ? var : 0.0);
       m.rel_spread = m.spread / m.mean;
       m.div_x = sqrt(tot[4] / W);
@@ -529,12 +335,12 @@ int32_t launch_scatter_t(const Params& p, int block, size_t smem, int sms, int g
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
         cudaSuccess)
-      return QS_ERR_CUDA;
+      return cuda_fail();
     attr_set[dev] = true;
   }
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
-    return QS_ERR_CUDA;
+    return cuda_fail();
   const int grid = pick_grid(occ, sms, block, grid_req, p.n, gmax);
   if (ex && ex->ev_start &&
       cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_start), st) != cudaSuccess)
@@ -632,7 +438,7 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.smooth_in_smem = sm.smooth ? 1 : 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
-  if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return QS_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return cuda_fail();
   int g = 1;
   if (prec == QS_F64)
     st = launch_scatter_prec<double>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);

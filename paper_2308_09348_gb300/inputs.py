@@ -242,3 +242,54 @@ def workload_inputs(wl: Workload, n: int | None = None):
     if wl.weighted:
         w = rng(wl.seed + 1).uniform(0.5, 1.5, n).astype(dt)
     return xi, w
+
+
+# ---------------------------------------------------------------------------
+# Batched shots
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class BatchWorkload:
+    name: str
+    lasers: tuple
+    beams: tuple
+    counts: np.ndarray        # samples per shot
+    offsets: np.ndarray       # n_shots + 1, exclusive prefix sums of counts
+    ranges: np.ndarray        # (n_shots, 2) spectrum range per shot
+    bins: Bins
+    seed: int
+
+
+def batch_shots(n_shots: int = 4096, seed: int = 0x23080903, log10_range=(3.0, 6.0),
+                n_phase: int = 512, n_bins: int = 512, model_mix: bool = False) -> BatchWorkload:
+    """Independent shots with per-shot parameters drawn from seed:
+    n_s = round(10^U[lo, hi]); a0 ~ U[5, 50]; W0 ~ U[2, 10] um; dx, dy ~ N(0, 2) um;
+    delay ~ N(0, 30) fs; gamma_mean ~ U[1e3, 2e4]; rel_spread ~ U[0.01, 0.2];
+    sigma_perp = 3 um, sigma_z = 10 um, 1 mrad.  Spectrum range per shot
+    [0, 1.2 gamma_mean (1 + 4 s)].  model_mix alternates the quantum and
+    classical models (even shots quantum)."""
+    g = rng(seed)
+    lo, hi = log10_range
+    counts = np.rint(10.0 ** g.uniform(lo, hi, n_shots)).astype(np.int64)
+    a0 = g.uniform(5, 50, n_shots)
+    w0 = g.uniform(2, 10, n_shots)
+    dx = g.normal(0, 2, n_shots)
+    dy = g.normal(0, 2, n_shots)
+    delay = g.normal(0, 30, n_shots)
+    gm = g.uniform(1e3, 2e4, n_shots)
+    sp = g.uniform(0.01, 0.2, n_shots)
+    lasers, beams, ranges = [], [], []
+    for k in range(n_shots):
+        model = MODEL_QFP if (not model_mix or k % 2 == 0) else MODEL_LL
+        lasers.append(Laser(lambda_um=0.8, a0=float(a0[k]), w0_um=float(w0[k]), tau_fs=30.0,
+                            model=model, dx_um=float(dx[k]), dy_um=float(dy[k]),
+                            delay_fs=float(delay[k]), n_phase=n_phase))
+        beams.append(Beam(gamma_mean=float(gm[k]), rel_spread=float(sp[k]), sigma_x_um=3.0,
+                          sigma_y_um=3.0, sigma_z_um=10.0, div_rad=1.0e-3))
+        ranges.append((0.0, 1.2 * gm[k] * (1 + 4 * sp[k])))
+    offsets = np.zeros(n_shots + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    return BatchWorkload(name=f"batch{n_shots}_qfp{n_phase}", lasers=tuple(lasers),
+                         beams=tuple(beams), counts=counts, offsets=offsets,
+                         ranges=np.array(ranges), bins=Bins(n_bins=n_bins, lo=0.0, hi=1.0),
+                         seed=seed)

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.qs_version() == 2
+    assert lib.qs_version() == 3
     for s in range(6):
         assert lib.qs_status_string(s)
     assert lib.qs_status_string(99) == b"unknown status"
@@ -51,7 +51,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(B.qs_samples) == 8 + 8 * 8 + 8 + 2 * 4
     assert C.sizeof(B.qs_bins) == 4 * 2 + 8 * 2 + 4 * 2 + 8 + 4 * 2 + 8 + 8
     assert C.sizeof(B.qs_moments) == 13 * 8
-    assert C.sizeof(B.qs_exec) == 16 + 2 * 8
+    assert C.sizeof(B.qs_exec) == 24 + 2 * 8
 
 
 def _call(lib, laser=None, beam=None, samples=None, bins=None, exe=None, moments=1,

@@ -1,0 +1,134 @@
+"""qs_scatter_batch: many shots in one persistent launch, checked shot by
+shot against single-shot qs_scatter calls and against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_09348_gb300 import binding as B
+from paper_2308_09348_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_09348_gb300 import build
+    build.build()
+
+
+def _small_batch(n_shots=37, seed=5, n_phase=64, log10_range=(0.0, 3.7)):
+    bw = I.batch_shots(n_shots, seed=seed, log10_range=log10_range, n_phase=n_phase,
+                       n_bins=96, model_mix=True)
+    counts = bw.counts.copy()
+    # ragged edge cases: empty, single, around the pair and tile boundaries
+    special = [0, 1, 2, 63, 64, 65, 2047, 2048, 2049]
+    counts[:len(special)] = special
+    offsets = np.zeros(n_shots + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    n = int(offsets[-1])
+    xi = I.sample_streams(n, seed + 100, dtype=np.float32)
+    return bw, counts, offsets, xi
+
+
+def _run_batch(bw, offsets, xi, prec, w=None, tile=0, block=0):
+    xt = [torch.from_numpy(a).cuda() for a in xi]
+    wt = None if w is None else torch.from_numpy(w).cuda()
+    bt = B.Batch(bw.lasers, bw.beams, offsets, bw.bins, len(xi[0]), ranges=bw.ranges,
+                 precision=prec, tile=tile, block=block)
+    bt.run(xt, wt)
+    torch.cuda.synchronize()
+    return bt, xt, wt
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_batch_equals_single_shot_calls(prec, weighted):
+    bw, counts, offsets, xi = _small_batch()
+    w = I.rng(77).uniform(0.5, 1.5, len(xi[0])).astype(np.float32) if weighted else None
+    bt, xt, wt = _run_batch(bw, offsets, xi, prec, w)
+    spectra = bt.spectra.cpu().numpy()
+    mom = bt.moments.cpu().numpy()
+    for s in range(len(counts)):
+        o0, o1 = int(offsets[s]), int(offsets[s + 1])
+        bins = I.Bins(n_bins=bw.bins.n_bins, lo=float(bw.ranges[s, 0]), hi=float(bw.ranges[s, 1]))
+        if o1 == o0:
+            assert mom[s, 0] == 0 and spectra[s].sum() == 0
+            continue
+        sub = [x[o0:o1] for x in xt]
+        ws = None if wt is None else wt[o0:o1]
+        ref = B.qs_scatter(bw.lasers[s], bw.beams[s], sub, bins, w=ws, precision=prec)
+        torch.cuda.synchronize()
+        # identical per-sample code: integer histograms agree exactly
+        assert np.array_equal(spectra[s], ref.spectrum.cpu().numpy()), s
+        r = ref.moments.cpu().numpy()
+        np.testing.assert_allclose(mom[s], r, rtol=1e-12, atol=1e-300)
+
+
+def test_batch_matches_oracle_f64():
+    bw, counts, offsets, xi = _small_batch(n_shots=12, seed=6, log10_range=(1.0, 3.0))
+    bt, _, _ = _run_batch(bw, offsets, xi, "f64")
+    mom = bt.moments_dicts()
+    spectra = bt.spectra.cpu().numpy()
+    for s in range(12):
+        o0, o1 = int(offsets[s]), int(offsets[s + 1])
+        if o1 == o0:
+            continue
+        bins = I.Bins(n_bins=bw.bins.n_bins, lo=float(bw.ranges[s, 0]), hi=float(bw.ranges[s, 1]))
+        ref = oracle.scatter(bw.lasers[s], bw.beams[s], bins,
+                             [a[o0:o1].astype(np.float64) for a in xi])
+        for k in ("W", "mean", "spread", "div_x", "div_y", "mean_aeff", "mean_gamma0"):
+            assert abs(mom[s][k] - ref["moments"][k]) <= 1e-12 * abs(ref["moments"][k]), (s, k)
+        assert np.abs(spectra[s] - ref["spectrum"]).sum() <= 1e-4 * (o1 - o0)
+
+
+def test_invalid_shot_is_flagged_and_others_unaffected():
+    bw, counts, offsets, xi = _small_batch(n_shots=10, seed=7, log10_range=(2.0, 3.0))
+    lasers = list(bw.lasers)
+    lasers[4] = I.Laser(**{**lasers[4].__dict__, "w0_um": -1.0})
+    bad = I.BatchWorkload(bw.name, tuple(lasers), bw.beams, bw.counts, bw.offsets, bw.ranges,
+                          bw.bins, bw.seed)
+    bt, _, _ = _run_batch(bad, offsets, xi, "f32")
+    good, _, _ = _run_batch(bw, offsets, xi, "f32")
+    m, mg = bt.moments.cpu().numpy(), good.moments.cpu().numpy()
+    assert m[4, 0] == 0 and m[4, B.MOMENT_FIELDS.index("nonfinite")] == -1
+    for s in range(10):
+        if s != 4:
+            assert np.array_equal(m[s], mg[s])
+
+
+@pytest.mark.parametrize("tile,block", [(64, 64), (512, 128), (4096, 256)])
+def test_schedule_does_not_change_results(tile, block):
+    bw, counts, offsets, xi = _small_batch(seed=8)
+    ref, _, _ = _run_batch(bw, offsets, xi, "f32")
+    bt, _, _ = _run_batch(bw, offsets, xi, "f32", tile=tile, block=block)
+    assert torch.equal(bt.spectra, ref.spectra)
+    np.testing.assert_allclose(bt.moments.cpu().numpy(), ref.moments.cpu().numpy(), rtol=1e-13)
+
+
+def test_batch_repeated_and_graph_replay_identical():
+    bw, counts, offsets, xi = _small_batch(seed=9)
+    bt, xt, _ = _run_batch(bw, offsets, xi, "f32")
+    m1, s1 = bt.moments.clone(), bt.spectra.clone()
+    bt.run(xt)
+    torch.cuda.synchronize()
+    assert torch.equal(bt.moments, m1) and torch.equal(bt.spectra, s1)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        bt.run(xt, stream=st)
+    bt.moments.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(bt.moments, m1) and torch.equal(bt.spectra, s1)
+
+
+def test_all_empty_shots():
+    bw = I.batch_shots(5, seed=10, log10_range=(1, 2), n_bins=16)
+    offsets = np.zeros(6, dtype=np.int64)
+    xi = [np.zeros(4, dtype=np.float32) for _ in range(8)]
+    bt, _, _ = _run_batch(bw, offsets, xi, "f32")
+    assert float(bt.moments.abs().sum()) == 0 and float(bt.spectra.abs().sum()) == 0
