@@ -228,6 +228,32 @@ int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_sam
                         void* stream);
 
 /*
+ * qs_scatter_host: qs_scatter for samples in HOST memory.  The samples are
+ * streamed to the device in chunks of `chunk` samples through two staging
+ * buffers in the workspace: the copy of chunk c+1 runs on an internal copy
+ * stream while chunk c is evaluated on `stream`, so the host-to-device
+ * transfer hides behind the computation.  Outputs are written to HOST
+ * memory when the stream reaches the end of the call (pinned host memory
+ * for every host buffer gives asynchronous copies; pageable memory works
+ * but serialises the copies).  Results equal qs_scatter's: identical
+ * histograms, moments up to the order of the reduction.
+ *   h_samples   qs_samples whose xi[] and w point to host memory
+ *   chunk       samples per chunk, a positive multiple of 1024 (0 = 1<<22)
+ *   h_*         host output buffers (same sizes and rules as qs_scatter)
+ *   d_workspace qs_host_workspace_bytes(...) bytes of device memory
+ * The first call on a device creates one copy stream and four events that
+ * are kept until the process exits (no device memory is allocated).
+ */
+size_t qs_host_workspace_bytes(const qs_bins* bins, const qs_exec* exec, const qs_samples* h_samples,
+                               int64_t chunk);
+
+int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_samples* h_samples,
+                        const qs_bins* bins, const qs_exec* exec, int64_t chunk,
+                        double* h_spectrum, double* h_divmap, double* h_aeff_hist,
+                        double* h_spec_smooth, qs_moments* h_moments, void* d_workspace,
+                        size_t ws_bytes, void* stream);
+
+/*
  * Batched shots (the paper's parallel plane-wave runs, Sec. 3.2, and the
  * high-repetition-rate data sets of Sec. 6): n_shots independent
  * integrations, each with its own laser and beam, in one persistent launch.

@@ -115,6 +115,14 @@ def _lib():
                                           C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP,
                                           C.c_size_t, _VP]
             L.qs_scatter_grad.restype = C.c_int32
+            L.qs_host_workspace_bytes.argtypes = [C.POINTER(qs_bins), C.POINTER(qs_exec),
+                                                  C.POINTER(qs_samples), C.c_int64]
+            L.qs_host_workspace_bytes.restype = C.c_size_t
+            L.qs_scatter_host.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                          C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                          C.POINTER(qs_exec), C.c_int64, _VP, _VP, _VP, _VP,
+                                          _VP, _VP, C.c_size_t, _VP]
+            L.qs_scatter_host.restype = C.c_int32
             L.qs_batch_workspace_bytes.argtypes = [C.c_int32, C.c_int64, C.POINTER(qs_bins),
                                                    C.c_int32, C.POINTER(qs_exec)]
             L.qs_batch_workspace_bytes.restype = C.c_size_t
@@ -414,3 +422,80 @@ class Batch:
 
     def moments_dicts(self) -> list[dict]:
         return [dict(zip(MOMENT_FIELDS, row)) for row in self.moments.cpu().tolist()]
+
+
+# ---- host-resident samples ------------------------------------------------
+
+def make_host_samples(xi, w=None) -> tuple[qs_samples, list]:
+    """xi: list of up to 8 CPU tensors (pinned for asynchronous copies)."""
+    xs = list(xi) + [None] * (8 - len(xi))
+    ref = next(t for t in xs if t is not None)
+    dt = ref.dtype
+    n = ref.numel()
+    keep, ptrs = [], []
+    for t in xs:
+        if t is None:
+            ptrs.append(None)
+            continue
+        if t.is_cuda or t.dtype != dt or t.numel() != n:
+            raise ValueError("host sample streams must be CPU tensors of one dtype and length")
+        t = t.contiguous()
+        keep.append(t)
+        ptrs.append(t.data_ptr())
+    wp = None
+    if w is not None:
+        w = w.contiguous()
+        keep.append(w)
+        wp = w.data_ptr()
+    s = qs_samples(n, (C.c_void_p * 8)(*ptrs), wp, QS_F32 if dt == torch.float32 else QS_F64, 0)
+    return s, keep
+
+
+class HostOutputs:
+    """Pinned host outputs plus the device workspace of qs_scatter_host."""
+
+    def __init__(self, bins: _inputs.Bins, xi_host, w=None, chunk=0, precision="f32", device=None,
+                 block=0, grid=0):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.bins = bins
+        self.chunk = int(chunk)
+        pin = dict(dtype=torch.float64, pin_memory=True)
+        self.spectrum = torch.zeros(max(bins.n_bins, 0), **pin)
+        nmap = bins.n_tx * bins.n_ty if (bins.n_tx > 0 and bins.n_ty > 0) else 0
+        self.divmap = torch.zeros(nmap, **pin)
+        self.aeff_hist = torch.zeros(max(bins.n_aeff, 0), **pin)
+        self.spec_smooth = torch.zeros(max(bins.n_bins, 0) if bins.smooth_sigma_bins > 0 else 0,
+                                       **pin)
+        self.moments = torch.zeros(len(MOMENT_FIELDS), **pin)
+        s, _ = make_host_samples(xi_host, w)
+        e = make_exec(precision, 0, block, grid)
+        b = make_bins(bins)
+        nbytes = _lib().qs_host_workspace_bytes(C.byref(b), C.byref(e), C.byref(s), self.chunk)
+        if nbytes == 0:
+            raise QsError(QS_ERR_INVALID_ARG, "qs_host_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        self.ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.ws_bytes = nbytes
+
+    def moments_dict(self) -> dict:
+        return dict(zip(MOMENT_FIELDS, self.moments.tolist()))
+
+
+def qs_scatter_host(laser, beam, xi_host, bins, w=None, precision="f32",
+                    out: HostOutputs | None = None, chunk=0, block=0, grid=0,
+                    weight_frac_bits=0, stream=None) -> HostOutputs:
+    """Integrate host-resident samples; copies overlap the kernels.  The
+    outputs in ``out`` are valid once the stream reaches the end of the call."""
+    s, keep = make_host_samples(xi_host, w)
+    if out is None:
+        out = HostOutputs(bins, xi_host, w, chunk, precision, None, block, grid)
+    L, B, Bn = make_laser(laser), make_beam(beam), make_bins(bins)
+    E = make_exec(precision, weight_frac_bits, block, grid)
+    hp = lambda t: t.data_ptr() if t.numel() else None  # noqa: E731
+    st = _lib().qs_scatter_host(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
+                                out.chunk, hp(out.spectrum), hp(out.divmap), hp(out.aeff_hist),
+                                hp(out.spec_smooth), out.moments.data_ptr(), out.ws_ptr,
+                                out.ws_bytes, _stream_ptr(stream))
+    _check(st, "qs_scatter_host")
+    out._keep = keep
+    return out

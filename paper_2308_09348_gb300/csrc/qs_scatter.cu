@@ -223,28 +223,49 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
 __global__ void __launch_bounds__(1024) k_finalize(const Params p, int grid, double* spectrum,
                                                    double* divmap, double* aeff_hist,
                                                    double* smooth, qs_moments* mom) {
+  // Moment slots [0, grid) reduced in a fixed order: thread t merges the
+  // contiguous slots [t*per, (t+1)*per) in order, then threads are merged by
+  // a warp shuffle tree and warps in order.  (W, mean, M2) use the
+  // parallel-variance merge; the other entries are compensated sums.
   __shared__ double tot[kNumMom];
+  __shared__ double wred[32 * kNumMom];
   const double scale = p.weighted ? 1.0 / p.wscale : 1.0;
-  if (threadIdx.x == 0) {
-    // (W, mean, M2) merged over CTA slots in CTA order
-    double W = 0.0, m = 0.0, M2 = 0.0;
-    for (int b = 0; b < grid; ++b) {
+  {
+    const int per = (grid + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(grid, b0 + per);
+    double v[kNumMom] = {};
+    double comp[kNumMom] = {};
+    for (int b = b0; b < b1; ++b) {
       const double* q = p.partials + (size_t)b * kNumMom;
-      welford_merge(W, m, M2, q[0], q[1], q[2]);
+      welford_merge(v[0], v[1], v[2], q[0], q[1], q[2]);
+      for (int k = 3; k < kNumMom; ++k) {
+        const double x = q[k], t = v[k] + x;
+        comp[k] += fabs(v[k]) >= fabs(x) ? (v[k] - t) + x : (x - t) + v[k];
+        v[k] = t;
+      }
     }
-    tot[0] = W;
-    tot[1] = m;
-    tot[2] = M2;
-  } else if (threadIdx.x >= 3 && threadIdx.x < kNumMom) {
-    // Neumaier-compensated sum over CTA slots in CTA order
-    double s = 0.0, c = 0.0;
-    for (int b = 0; b < grid; ++b) {
-      double x = p.partials[(size_t)b * kNumMom + threadIdx.x];
-      double t = s + x;
-      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
-      s = t;
+    for (int k = 3; k < kNumMom; ++k) v[k] += comp[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+      double u[kNumMom];
+      for (int k = 0; k < kNumMom; ++k) u[k] = __shfl_down_sync(0xffffffffu, v[k], o);
+      welford_merge(v[0], v[1], v[2], u[0], u[1], u[2]);
+      for (int k = 3; k < kNumMom; ++k) v[k] += u[k];
     }
-    tot[threadIdx.x] = s + c;
+    if (lane == 0)
+      for (int k = 0; k < kNumMom; ++k) wred[warp * kNumMom + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double W = 0.0, m = 0.0, M2 = 0.0, sm[kNumMom] = {};
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        welford_merge(W, m, M2, wred[w * kNumMom], wred[w * kNumMom + 1], wred[w * kNumMom + 2]);
+        for (int k = 3; k < kNumMom; ++k) sm[k] += wred[w * kNumMom + k];
+      }
+      tot[0] = W;
+      tot[1] = m;
+      tot[2] = M2;
+      for (int k = 3; k < kNumMom; ++k) tot[k] = sm[k];
+    }
   }
   for (int b = threadIdx.x; b < p.n_bins; b += blockDim.x)
     spectrum[b] = (double)p.acc_spec[b] * scale;
@@ -542,4 +563,188 @@ extern "C" int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam
   // qs_scatter zeroes the accumulators on the stream before its kernels run
   return qs_scatter(laser, beam, samples, bins, exec, d_spectrum, d_divmap, d_aeff_hist,
                     d_spec_smooth, d_moments, scratch, QS_NOALLOC_SCRATCH_BYTES, stream);
+}
+
+// ---------------------------------------------------------------------------
+// qs_scatter_host: host-resident samples, chunked and double-buffered so
+// that host-to-device copies overlap the evaluation kernel.
+// ---------------------------------------------------------------------------
+namespace qs {
+namespace {
+
+struct HostPipe {
+  bool init = false;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipe[64];
+
+int32_t host_pipe(HostPipe** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail();
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe& hp = g_pipe[dev];
+  if (!hp.init) {
+    if (cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail();
+    cudaEvent_t* evs[5] = {&hp.start, &hp.copied[0], &hp.copied[1], &hp.consumed[0], &hp.consumed[1]};
+    for (cudaEvent_t* e : evs)
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return cuda_fail();
+    hp.init = true;
+  }
+  *out = &hp;
+  return QS_OK;
+}
+
+struct HostPlan {
+  Plan pl;               // accumulators; partial slots for n_chunks * gmax CTAs
+  int64_t chunk = 0, n_chunks = 0;
+  int n_streams = 0;     // present sample streams (+ weights)
+  size_t esz = 4, off_out = 0, off_stage = 0, stage_bytes = 0, bytes = 0;
+  size_t out_spec = 0, out_map = 0, out_aeff = 0, out_smooth = 0, out_mom = 0;
+};
+
+bool host_plan(HostPlan& hp, const qs_bins* b, int block, int grid, int sms,
+               const qs_samples* s, int64_t chunk) {
+  hp.chunk = chunk > 0 ? chunk : ((int64_t)1 << 22);
+  if (hp.chunk % 1024) return false;
+  hp.n_chunks = s->n > 0 ? (s->n + hp.chunk - 1) / hp.chunk : 0;
+  make_plan(hp.pl, b, block, grid, sms);
+  // partial slots for every chunk's CTAs (the plan's region holds one chunk)
+  const size_t part_bytes = (size_t)(hp.n_chunks > 0 ? hp.n_chunks : 1) * hp.pl.gmax * kNumMom * 8;
+  size_t off = hp.pl.off_part + align_up(part_bytes, 256);
+  hp.off_out = off;
+  hp.out_spec = off; off = align_up(off + (size_t)(b->n_bins > 0 ? b->n_bins : 0) * 8, 256);
+  hp.out_map = off;  off = align_up(off + (size_t)(b->n_tx > 0 ? (int64_t)b->n_tx * b->n_ty : 0) * 8, 256);
+  hp.out_aeff = off; off = align_up(off + (size_t)(b->n_aeff > 0 ? b->n_aeff : 0) * 8, 256);
+  hp.out_smooth = off; off = align_up(off + (size_t)(b->smooth_sigma_bins > 0 ? b->n_bins : 0) * 8, 256);
+  hp.out_mom = off;  off = align_up(off + sizeof(qs_moments), 256);
+  hp.esz = s->dtype == QS_F32 ? 4 : 8;
+  hp.n_streams = 0;
+  for (int k = 0; k < 8; ++k) hp.n_streams += s->xi[k] ? 1 : 0;
+  hp.n_streams += s->w ? 1 : 0;
+  hp.stage_bytes = align_up((size_t)hp.chunk * hp.esz, 256);
+  hp.off_stage = off;
+  off += 2 * (size_t)hp.n_streams * hp.stage_bytes;
+  hp.bytes = off;
+  return true;
+}
+
+}  // namespace
+}  // namespace qs
+
+extern "C" size_t qs_host_workspace_bytes(const qs_bins* bins, const qs_exec* exec,
+                                          const qs_samples* h_samples, int64_t chunk) {
+  int prec, wbits, block, grid, sms;
+  if (validate_bins(bins) != QS_OK || validate_samples(h_samples) != QS_OK) return 0;
+  if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
+  if (device_sms(&sms) != QS_OK) return 0;
+  HostPlan hp;
+  if (!host_plan(hp, bins, block, grid, sms, h_samples, chunk)) return 0;
+  return hp.bytes;
+}
+
+extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
+                                   const qs_samples* h_samples, const qs_bins* bins,
+                                   const qs_exec* exec, int64_t chunk, double* h_spectrum,
+                                   double* h_divmap, double* h_aeff_hist, double* h_spec_smooth,
+                                   qs_moments* h_moments, void* d_workspace, size_t ws_bytes,
+                                   void* stream) {
+  int32_t st;
+  if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
+      (st = validate_samples(h_samples)) || (st = validate_bins(bins)))
+    return st;
+  int prec, wbits, block, grid, sms;
+  if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
+  if (!h_moments) return QS_ERR_INVALID_ARG;
+  if (bins->n_bins > 0 && !h_spectrum) return QS_ERR_INVALID_ARG;
+  if (bins->n_tx > 0 && !h_divmap) return QS_ERR_INVALID_ARG;
+  if (bins->n_aeff > 0 && !h_aeff_hist) return QS_ERR_INVALID_ARG;
+  if (bins->smooth_sigma_bins > 0 && !h_spec_smooth) return QS_ERR_INVALID_ARG;
+  if (chunk < 0) return QS_ERR_INVALID_ARG;
+  if ((st = device_sms(&sms))) return st;
+  HostPlan hp;
+  if (!host_plan(hp, bins, block, grid, sms, h_samples, chunk)) return QS_ERR_INVALID_ARG;
+  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < hp.bytes)
+    return QS_ERR_WORKSPACE;
+  HostPipe* pipe = nullptr;
+  if ((st = host_pipe(&pipe))) return st;
+  const bool qfp = laser->model == QS_MODEL_QFP;
+  const Smem sm = smem_plan(hp.pl, prec, qfp, qfp ? laser->n_phase : 0, h_samples->w != nullptr,
+                            block);
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  Params p;
+  fill_params(p, laser, beam, h_samples, bins, wbits);
+  p.acc_spec = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_spec);
+  p.acc_map = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_map);
+  p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_aeff);
+  p.acc_smooth = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_smooth);
+  p.hist_in_smem = sm.hist ? 1 : 0;
+  p.smooth_in_smem = sm.smooth ? 1 : 0;
+  double* part0 = reinterpret_cast<double*>(ws + hp.pl.off_part);
+
+  // accumulators and every partial slot start at zero; copies wait for the
+  // caller's earlier work on `stream` (it may still use the workspace)
+  if (cudaMemsetAsync(ws, 0, hp.off_out, cs) != cudaSuccess) return cuda_fail();
+  if (cudaEventRecord(pipe->start, cs) != cudaSuccess) return cuda_fail();
+  if (cudaStreamWaitEvent(pipe->copy, pipe->start, 0) != cudaSuccess) return cuda_fail();
+
+  const void* hsrc[9];
+  int ns = 0;
+  for (int k = 0; k < 8; ++k)
+    if (h_samples->xi[k]) hsrc[ns++] = h_samples->xi[k];
+  if (h_samples->w) hsrc[ns++] = h_samples->w;
+  for (int64_t c = 0; c < hp.n_chunks; ++c) {
+    const int b = (int)(c & 1);
+    const int64_t i0 = c * hp.chunk;
+    const int64_t cn = (h_samples->n - i0) < hp.chunk ? (h_samples->n - i0) : hp.chunk;
+    unsigned char* stage = ws + hp.off_stage + (size_t)b * hp.n_streams * hp.stage_bytes;
+    if (c >= 2 && cudaStreamWaitEvent(pipe->copy, pipe->consumed[b], 0) != cudaSuccess)
+      return cuda_fail();
+    for (int k = 0; k < ns; ++k)
+      if (cudaMemcpyAsync(stage + (size_t)k * hp.stage_bytes,
+                          static_cast<const unsigned char*>(hsrc[k]) + (size_t)i0 * hp.esz,
+                          (size_t)cn * hp.esz, cudaMemcpyHostToDevice, pipe->copy) != cudaSuccess)
+        return cuda_fail();
+    if (cudaEventRecord(pipe->copied[b], pipe->copy) != cudaSuccess) return cuda_fail();
+    if (cudaStreamWaitEvent(cs, pipe->copied[b], 0) != cudaSuccess) return cuda_fail();
+    // point the launch at the staged chunk
+    Params pc = p;
+    pc.n = cn;
+    int k2 = 0;
+    for (int k = 0; k < 8; ++k)
+      pc.xi[k] = h_samples->xi[k] ? stage + (size_t)(k2++) * hp.stage_bytes : nullptr;
+    pc.w = h_samples->w ? stage + (size_t)(k2++) * hp.stage_bytes : nullptr;
+    pc.partials = part0 + (size_t)c * hp.pl.gmax * kNumMom;
+    int g = 1;
+    const qs_exec* ex = (c == 0) ? exec : nullptr;
+    if (prec == QS_F64)
+      st = launch_scatter_prec<double>(pc, qfp, sm, block, sms, grid, hp.pl.gmax, cs, &g, ex);
+    else
+      st = launch_scatter_prec<float>(pc, qfp, sm, block, sms, grid, hp.pl.gmax, cs, &g, ex);
+    if (st) return st;
+    if (cudaEventRecord(pipe->consumed[b], cs) != cudaSuccess) return cuda_fail();
+  }
+  // finalize over every chunk's slots, in chunk then CTA order
+  p.partials = part0;
+  double* d_spec = reinterpret_cast<double*>(ws + hp.out_spec);
+  double* d_map = reinterpret_cast<double*>(ws + hp.out_map);
+  double* d_aeff = reinterpret_cast<double*>(ws + hp.out_aeff);
+  double* d_smooth = reinterpret_cast<double*>(ws + hp.out_smooth);
+  qs_moments* d_mom = reinterpret_cast<qs_moments*>(ws + hp.out_mom);
+  const int slots = (int)((hp.n_chunks > 0 ? hp.n_chunks : 1) * hp.pl.gmax);
+  k_finalize<<<1, 1024, 0, cs>>>(p, slots, d_spec, d_map, d_aeff, d_smooth, d_mom);
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  // results to the host
+  struct Out { void* h; const void* d; size_t n; } outs[5] = {
+      {h_spectrum, d_spec, (size_t)(bins->n_bins > 0 ? bins->n_bins : 0) * 8},
+      {h_divmap, d_map, (size_t)(bins->n_tx > 0 ? (int64_t)bins->n_tx * bins->n_ty : 0) * 8},
+      {h_aeff_hist, d_aeff, (size_t)(bins->n_aeff > 0 ? bins->n_aeff : 0) * 8},
+      {h_spec_smooth, d_smooth, (size_t)(bins->smooth_sigma_bins > 0 ? bins->n_bins : 0) * 8},
+      {h_moments, d_mom, sizeof(qs_moments)}};
+  for (const Out& o : outs)
+    if (o.n && cudaMemcpyAsync(o.h, o.d, o.n, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      return cuda_fail();
+  return QS_OK;
 }
