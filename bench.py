@@ -59,6 +59,13 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=1, help="timed steps of the FP64 path")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-shots measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-broadband", action="store_true",
+                    help="skip the broadband single-shot and delay-sweep measurements")
+    ap.add_argument("--no-ll", action="store_true", help="skip the classical-model measurement")
+    ap.add_argument("--batch-shots", type=int, default=4096)
+    ap.add_argument("--grad-n", type=int, default=1 << 24)
+    ap.add_argument("--broadband-n", type=int, default=1 << 27)
+    ap.add_argument("--ll-n", type=int, default=1 << 26)
     return ap.parse_args()
 
 
@@ -195,7 +202,83 @@ def run_reference(args):
     return 0
 
 
-def bench_batch(dev, rank, steps=3):
+def _events(n=2):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def bench_broadband(dev, rank, n, sweep_n=1 << 20, n_delays=512, steps=2):
+    """Broadband beam: flat gamma0 on [1e3, 2e4], 2 mrad, 5 um offset, a0 = 100,
+    W0 = 2 um, quantum model with 1024 phase cells, 1024 log-spaced bins; and
+    the same laser swept over 512 delays on [-100, 100] fs in one batched
+    launch over 2^20 shared samples."""
+    import numpy as np
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.broadband_qfp(n)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    xi[3] = torch.rand(n, generator=gen, device=dev, dtype=torch.float32)   # flat energy
+    out = B.Outputs(wl.bins, n, dev, "f32")
+    B.qs_scatter(wl.laser, wl.beam, xi, wl.bins, out=out)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(steps):
+        B.qs_scatter(wl.laser, wl.beam, xi, wl.bins, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    res = {"metric": "beam-sample evals/s", "value": n / (ms * 1e-3), "unit": "samples/s",
+           "ms_per_step": ms, "n_samples": n, "n_phase": wl.laser.n_phase,
+           "bins": f"{wl.bins.n_bins} log-spaced", "workload": wl.name}
+    # delay sweep over shared samples
+    delays = np.linspace(-100.0, 100.0, n_delays)
+    lasers = [I.Laser(**{**wl.laser.__dict__, "delay_fs": float(d)}) for d in delays]
+    sub = [x[:sweep_n] for x in xi]
+    bt = B.Batch(lasers, [wl.beam] * n_delays, None, wl.bins, sweep_n, dev, precision="f32")
+    bt.run(sub)
+    torch.cuda.synchronize()
+    a.record()
+    bt.run(sub)
+    b.record()
+    torch.cuda.synchronize()
+    ms2 = a.elapsed_time(b)
+    res["delay_sweep"] = {"metric": "shots/s", "value": n_delays / (ms2 * 1e-3), "unit": "shots/s",
+                          "sample_evals_per_s": n_delays * sweep_n / (ms2 * 1e-3),
+                          "ms_per_launch": ms2, "n_delays": n_delays,
+                          "shared_samples": sweep_n, "delay_range_fs": [-100.0, 100.0]}
+    return res
+
+
+def bench_ll(dev, rank, n=1 << 26, steps=5):
+    """Classical LL model on the bench beam (HBM-bound: 24 B/sample read)."""
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.full_ll(n)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(6)]
+    out = B.Outputs(wl.bins, n, dev, "f32")
+    B.qs_scatter(wl.laser, wl.beam, xi, wl.bins, out=out)
+    torch.cuda.synchronize()
+    kev = [tuple(_events()) for _ in range(steps)]
+    for k in range(steps):
+        B.qs_scatter(wl.laser, wl.beam, xi, wl.bins, out=out, kernel_events=kev[k])
+    torch.cuda.synchronize()
+    kms = sum(x.elapsed_time(y) for x, y in kev) / steps
+    gbs = n * 24 / (kms * 1e-3) / 1e9
+    pk = peaks().get("hbm_gbs", 6784.5)
+    return {"metric": "beam-sample evals/s", "value": n / (kms * 1e-3), "unit": "samples/s",
+            "kernel_ms": kms, "n_samples": n, "bytes_per_sample": 24,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s",
+                         "frac": gbs / pk}, "workload": wl.name}
+
+
+def bench_batch(dev, rank, steps=3, n_shots=4096):
     """4096 shots, sample counts log-uniform in [1e3, 1e6], per-shot laser and
     beam drawn from seed, quantum model with 512 phase cells, FP32 with FP64
     moments, one persistent launch per step; schedule from the autotuner."""
@@ -203,7 +286,7 @@ def bench_batch(dev, rank, steps=3):
     from paper_2308_09348_gb300 import binding as B
     from paper_2308_09348_gb300 import inputs as I
     from paper_2308_09348_gb300 import tune
-    bw = I.batch_shots(4096)
+    bw = I.batch_shots(n_shots)
     n = int(bw.offsets[-1])
     gen = torch.Generator(device=dev)
     gen.manual_seed(bw.seed + 7919 * rank)
@@ -230,22 +313,21 @@ def bench_batch(dev, rank, steps=3):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     bad = int((bt.moments[:, B.MOMENT_FIELDS.index("nonfinite")] != 0).sum())
-    return {"metric": "shots/s", "value": 4096 / (ms * 1e-3), "unit": "shots/s",
+    return {"metric": "shots/s", "value": n_shots / (ms * 1e-3), "unit": "shots/s",
             "samples_per_s": n / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
-            "n_shots": 4096, "n_samples": n, "n_phase": 512, "schedule": {"block": best[0],
+            "n_shots": n_shots, "n_samples": n, "n_phase": 512, "schedule": {"block": best[0],
                                                                              "tile": best[1]},
             "tuned_ms": {f"{k[0]}x{k[1]}": v for k, v in times.items()},
             "shots_flagged": bad, "workload": bw.name}
 
 
-def bench_grad(dev, rank, steps=3):
+def bench_grad(dev, rank, steps=3, n=1 << 24):
     """Forward + adjoint of 2^24 FP32 samples (quantum model, 512 cells) with a
     loss on the moments and the 2-bin-smoothed 256-bin spectrum."""
     import torch
     from paper_2308_09348_gb300 import binding as B
     from paper_2308_09348_gb300 import inputs as I
-    wl = I.fit_qfp()
-    n = wl.n
+    wl = I.fit_qfp(n)
     gen = torch.Generator(device=dev)
     gen.manual_seed(wl.seed + 7919 * rank)
     xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
@@ -436,8 +518,10 @@ def main():
                            f" per clock x {fmax_mhz:.0f} MHz (max SM clock)",
             "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k}
 
-    batch = None if args.no_batch else bench_batch(dev, rank)
-    grad = None if args.no_grad else bench_grad(dev, rank)
+    batch = None if args.no_batch else bench_batch(dev, rank, n_shots=args.batch_shots)
+    grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)
+    broad = None if args.no_broadband else bench_broadband(dev, rank, args.broadband_n)
+    ll = None if args.no_ll else bench_ll(dev, rank, n=args.ll_n)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -461,7 +545,8 @@ def main():
                            "l2": "inputs (2.1 GB per GPU) larger than L2; no flush"},
                 "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
-                "batch_shots": batch, "grad": grad, "gpu": props.name}
+                "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
+                "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

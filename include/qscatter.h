@@ -267,7 +267,9 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *                 gets W = 0 and nonfinite = -1 and no work)
  *   d_offsets     n_shots + 1 non-decreasing int64 (device), offsets[0] >= 0,
  *                 offsets[n_shots] <= samples->n (checked on the device: a
- *                 shot whose range is invalid is treated as invalid)
+ *                 shot whose range is invalid is treated as invalid); or
+ *                 NULL: every shot integrates ALL samples (a parameter sweep,
+ *                 e.g. over the delay, on one sampled beam)
  *   samples       the concatenated streams (as for qs_scatter)
  *   bins          energy spectrum only (n_tx = n_aeff = 0, no smoothing);
  *                 shared bin count, range per shot from d_ranges if not NULL
@@ -275,11 +277,14 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *   max_phase     upper bound of the shots' n_phase (QFP), 1..4096
  *   d_spectra     n_shots x n_bins doubles (row per shot), or NULL if n_bins == 0
  *   d_moments     n_shots qs_moments
+ * The workspace size (qs_batch_workspace_bytes) depends on shared_samples:
+ * nonzero for the sweep form (d_offsets == NULL), whose tile slots grow with
+ * n_shots x n_total / tile.
  * The call is a fixed sequence of one memset and five kernels on the stream
  * and contains no host synchronisation.
  */
 size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins* bins,
-                                int32_t max_phase, const qs_exec* exec);
+                                int32_t max_phase, const qs_exec* exec, int32_t shared_samples);
 
 int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_beam* d_beams,
                          const int64_t* d_offsets, const qs_samples* samples,

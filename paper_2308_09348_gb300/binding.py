@@ -124,7 +124,7 @@ def _lib():
                                           _VP, _VP, C.c_size_t, _VP]
             L.qs_scatter_host.restype = C.c_int32
             L.qs_batch_workspace_bytes.argtypes = [C.c_int32, C.c_int64, C.POINTER(qs_bins),
-                                                   C.c_int32, C.POINTER(qs_exec)]
+                                                   C.c_int32, C.POINTER(qs_exec), C.c_int32]
             L.qs_batch_workspace_bytes.restype = C.c_size_t
             L.qs_scatter_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
                                            C.POINTER(qs_bins), _VP, C.c_int32,
@@ -389,9 +389,12 @@ class Batch:
                                               for l in lasers))
         self.d_lasers = _struct_array_to_device([make_laser(l) for l in lasers], qs_laser, dev)
         self.d_beams = _struct_array_to_device([make_beam(b) for b in beams], qs_beam, dev)
-        off = torch.as_tensor(offsets, dtype=torch.int64)
-        assert off.numel() == self.n_shots + 1
-        self.d_offsets = off.to(dev)
+        if offsets is None:          # parameter sweep: every shot uses all samples
+            self.d_offsets = None
+        else:
+            off = torch.as_tensor(offsets, dtype=torch.int64)
+            assert off.numel() == self.n_shots + 1
+            self.d_offsets = off.to(dev)
         self.d_ranges = None if ranges is None else torch.as_tensor(
             ranges, dtype=torch.float64).reshape(-1, 2).contiguous().to(dev)
         self.spectra = torch.zeros(self.n_shots, max(bins.n_bins, 0), dtype=torch.float64, device=dev)
@@ -399,7 +402,8 @@ class Batch:
         e = make_exec(precision, 0, block, grid, None, tile)
         b = make_bins(bins)
         nbytes = _lib().qs_batch_workspace_bytes(self.n_shots, int(n_total), C.byref(b),
-                                                 self.max_phase, C.byref(e))
+                                                 self.max_phase, C.byref(e),
+                                                 1 if self.d_offsets is None else 0)
         if nbytes == 0:
             raise QsError(QS_ERR_INVALID_ARG, "qs_batch_workspace_bytes")
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -413,7 +417,8 @@ class Batch:
         e = make_exec(self.precision, 0, self.block, self.grid, None, self.tile)
         st = _lib().qs_scatter_batch(
             self.n_shots, self.d_lasers.data_ptr(), self.d_beams.data_ptr(),
-            self.d_offsets.data_ptr(), C.byref(s), C.byref(b),
+            self.d_offsets.data_ptr() if self.d_offsets is not None else None, C.byref(s),
+            C.byref(b),
             self.d_ranges.data_ptr() if self.d_ranges is not None else None, self.max_phase,
             C.byref(e), self.spectra.data_ptr() if self.spectra.numel() else None,
             self.moments.data_ptr(), self.ws_ptr, self.ws_bytes, _stream_ptr(stream))

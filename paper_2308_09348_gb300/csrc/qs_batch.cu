@@ -50,7 +50,9 @@ __global__ void k_bsetup(const BatchArgs a) {
     b.lo = a.ranges[2 * s];
     b.hi = a.ranges[2 * s + 1];
   }
-  const int64_t o0 = a.offsets[s], o1 = a.offsets[s + 1];
+  // shared samples (parameter sweep) when no offsets are given
+  const int64_t o0 = a.offsets ? a.offsets[s] : 0;
+  const int64_t o1 = a.offsets ? a.offsets[s + 1] : a.samples.n;
   bool ok = check_laser(L) == QS_OK && check_beam(B) == QS_OK && check_bins(b) == QS_OK &&
             o0 >= 0 && o1 >= o0 && o1 <= a.samples.n &&
             (L.model != QS_MODEL_QFP || L.n_phase <= a.max_phase);
@@ -171,27 +173,37 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
     for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x) hs[b] = 0;
     __syncthreads();
 
-    double acc[kNumAcc];
+    typename AccT<T>::type acc;
     acc_init(acc);
     const int64_t first = (t - a.tiles[s]) * a.tile;
     const int64_t last = min(p.n, first + a.tile);
-    if (sizeof(T) == 4 && p.model == QS_MODEL_QFP) {
-      for (int64_t k = first / 2 + threadIdx.x; 2 * k < last; k += blockDim.x) {
-        const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
-        Sample s0, s1;
-        eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-        accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
-        if (i1 != i0) accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
-      }
-    } else if (p.model == QS_MODEL_QFP) {
-      for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-        const Sample sm = eval_sample<T, true>(p, tab, i);
-        accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+    if constexpr (sizeof(T) == 4) {
+      if (p.model == QS_MODEL_QFP) {
+        for (int64_t k = first / 2 + threadIdx.x; 2 * k < last; k += blockDim.x) {
+          const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
+          SampleF s0, s1;
+          eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+          accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+          if (i1 != i0)
+            accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+        }
+      } else {
+        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+          const auto sm = eval_one<T, false>(p, tab, i);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+        }
       }
     } else {
-      for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-        const Sample sm = eval_sample<T, false>(p, tab, i);
-        accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+      if (p.model == QS_MODEL_QFP) {
+        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+          const auto sm = eval_one<T, true>(p, tab, i);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+        }
+      } else {
+        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
+          const auto sm = eval_one<T, false>(p, tab, i);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+        }
       }
     }
     block_reduce_write(acc, red, a.partials + (size_t)t * kNumMom);
@@ -285,9 +297,12 @@ struct BatchPlan {
 };
 
 bool batch_plan(BatchPlan& bp, int32_t n_shots, int64_t n_total, const qs_bins* bins,
-                int32_t max_phase, int precision, int tile) {
+                int32_t max_phase, int precision, int tile, bool shared) {
   if (n_shots < 1 || n_total < 0 || max_phase < 1 || max_phase > kMaxPhase) return false;
-  bp.max_tiles = n_total / tile + n_shots + 1;
+  // tile slots: disjoint shots need at most n_total/tile + n_shots; a sweep
+  // (every shot covers all samples) needs n_shots * ceil(n_total/tile)
+  bp.max_tiles = shared ? (int64_t)n_shots * ((n_total + tile - 1) / tile) + 1
+                        : n_total / tile + n_shots + 1;
   size_t off = 0;
   bp.off_counter = off; off = align_up(off + 8, 256);
   bp.off_params = off; off = align_up(off + (size_t)n_shots * sizeof(Params), 256);
@@ -343,12 +358,14 @@ int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaS
 }  // namespace
 
 extern "C" size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins* bins,
-                                           int32_t max_phase, const qs_exec* exec) {
+                                           int32_t max_phase, const qs_exec* exec,
+                                           int32_t shared_samples) {
   int prec, wbits, block, grid, tile;
   if (!bins || validate_bins(bins) != QS_OK) return 0;
   if (exec_opts(exec, &prec, &wbits, &block, &grid) || exec_tile(exec, &tile)) return 0;
   BatchPlan bp;
-  if (!batch_plan(bp, n_shots, n_total, bins, max_phase, prec, tile)) return 0;
+  if (!batch_plan(bp, n_shots, n_total, bins, max_phase, prec, tile, shared_samples != 0))
+    return 0;
   return bp.bytes;
 }
 
@@ -363,12 +380,13 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
                             &tile);
   if (st) return st;
-  if (!d_lasers || !d_beams || !d_offsets || !d_moments) return QS_ERR_INVALID_ARG;
+  if (!d_lasers || !d_beams || !d_moments) return QS_ERR_INVALID_ARG;
   if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
   BatchPlan bp;
-  if (!batch_plan(bp, n_shots, samples->n, bins, max_phase, prec, tile)) return QS_ERR_INVALID_ARG;
+  if (!batch_plan(bp, n_shots, samples->n, bins, max_phase, prec, tile, d_offsets == nullptr))
+    return QS_ERR_INVALID_ARG;
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < bp.bytes)
     return QS_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);

@@ -156,7 +156,12 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
     p.lo = b->lo;
     if (b->n_bins > 0) {
       p.inv_w = (double)b->n_bins / (b->hi - b->lo);
-      if (b->log_spaced) p.log_scale = (double)b->n_bins / log(b->hi / b->lo);
+      if (b->log_spaced) {
+        p.log_scale = (double)b->n_bins / log(b->hi / b->lo);
+        const double l2 = log2(b->hi / b->lo);
+        p.log2_scale = (float)((double)b->n_bins / l2);
+        p.log2_offset = (float)(log2(b->lo) * ((double)b->n_bins / l2));
+      }
     }
     p.n_tx = b->n_tx;
     p.n_ty = b->n_ty;

@@ -60,6 +60,8 @@ struct Params {
   double smooth_pref;      // 1 / (sigma sqrt(2 pi))
   double smooth_c;         // log2(e) / (2 sigma^2)
   unsigned long long* acc_smooth;
+  // FP32 path, log-spaced bins: t = lg2(gamma) * log2_scale - log2_offset
+  float log2_scale, log2_offset;
 };
 
 // ---- math policy --------------------------------------------------------
@@ -92,6 +94,15 @@ __device__ __forceinline__ double load_elem(const void* p, int64_t i, int dtype)
   if (p == nullptr) return 0.0;
   if (dtype == 0) return (double)__ldg(static_cast<const float*>(p) + i);
   return __ldg(static_cast<const double*>(p) + i);
+}
+
+// Load in the arithmetic type (no FP64 round trip for FP32 streams on the
+// FP32 path).
+template <typename T>
+__device__ __forceinline__ T load_t(const void* p, int64_t i, int dtype) {
+  if (p == nullptr) return (T)0;
+  if (dtype == 0) return (T)__ldg(static_cast<const float*>(p) + i);
+  return (T)__ldg(static_cast<const double*>(p) + i);
 }
 
 // Phase-cell envelope G(phi_j) at the midpoint of cell j, in double.
@@ -268,18 +279,21 @@ __device__ __forceinline__ double op_fma(double a, double b, double c) { return 
 // a_eff at the crossing point and the decoded sample (rows a1-a3).
 template <typename T>
 __device__ __forceinline__ T focus(const Params& p, int64_t i, double& gamma0, T& thx, T& thy) {
-  const T xi0 = (T)load_elem(p.xi[0], i, p.dtype);
-  const T xi1 = (T)load_elem(p.xi[1], i, p.dtype);
-  const T xi2 = (T)load_elem(p.xi[2], i, p.dtype);
-  const double xi3 = load_elem(p.xi[3], i, p.dtype);
-  const T xi4 = (T)load_elem(p.xi[4], i, p.dtype);
-  const T xi5 = (T)load_elem(p.xi[5], i, p.dtype);
-  // decode (reparameterised)
+  const T xi0 = load_t<T>(p.xi[0], i, p.dtype);
+  const T xi1 = load_t<T>(p.xi[1], i, p.dtype);
+  const T xi2 = load_t<T>(p.xi[2], i, p.dtype);
+  const T xi3 = load_t<T>(p.xi[3], i, p.dtype);
+  const T xi4 = load_t<T>(p.xi[4], i, p.dtype);
+  const T xi5 = load_t<T>(p.xi[5], i, p.dtype);
+  // decode (reparameterised); gamma0 in the arithmetic type (exactly
+  // representable in FP64 for the FP64 recombination)
   const T x = op_fma((T)p.sx, xi0, (T)p.bdx);
   const T y = op_fma((T)p.sy, xi1, (T)p.bdy);
   const T z = op_mul((T)p.sz, xi2);
-  gamma0 = p.flat ? __fma_rn(p.gspan, xi3, p.glo) : __dmul_rn(p.gmean, __fma_rn(p.spread, xi3, 1.0));
-  if (gamma0 < 1.0) gamma0 = 1.0;
+  T g0 = p.flat ? op_fma((T)p.gspan, xi3, (T)p.glo)
+                : op_mul((T)p.gmean, op_fma((T)p.spread, xi3, (T)1));
+  if (g0 < (T)1) g0 = (T)1;
+  gamma0 = (double)g0;
   thx = op_mul((T)p.div, xi4);
   thy = op_mul((T)p.div, xi5);
   // collision geometry: crossing of the pulse peak (factor 2 of Eq. 1)
@@ -348,27 +362,41 @@ __device__ __forceinline__ Sample eval_sample(const Params& p,
   return s;
 }
 
-// FP32 QFP path: samples i0 and i1 through the model together (the phase
-// integration runs packed); results per sample are those of eval_sample.
+// FP32-path per-sample record: FP64 only where the path keeps FP64 (gamma0,
+// the recombined mean energy, the realised energy), FP32 elsewhere.
+struct SampleF {
+  double gamma0, mu, gout;
+  float aeff, V, theta_e, thx0, thy0, tx, ty;
+};
+
+template <typename T> struct SampleT;
+template <> struct SampleT<double> { using type = Sample; };
+template <> struct SampleT<float> { using type = SampleF; };
+
+// 1/gamma_f = 1/gamma0 + du recombined in FP64 with an FP32 reciprocal
+// refined by one Newton step (relative error ~2^-46), then Eq. 8 and the
+// realised energy.
 __device__ __forceinline__ void finish_f32(const Params& p, int64_t i, double gamma0, float af,
-                                           float thx, float thy, float du, float Vf, Sample& s) {
+                                           float thx, float thy, float du, float Vf, SampleF& s) {
   const double den = fma(gamma0, (double)du, 1.0);
   double r = (double)M<float>::rcp((float)den);
   r = r * fma(-den, r, 2.0);
   const double mu = gamma0 * r;
   const float sv = Vf > 0.f ? sqrtf(Vf) : 0.f;
   const float muf = (float)mu;
-  const float te = (float)p.kappa_s * af * sv * M<float>::rcp(muf * muf);   // Eq. 8
-  s.gamma0 = gamma0; s.aeff = (double)af; s.mu = mu; s.V = (double)Vf;
-  s.theta_e = (double)te;
-  s.thx0 = (double)thx; s.thy0 = (double)thy; s.ty = (double)thy;
-  s.tx = (double)fmaf(te, (float)load_elem(p.xi[6], i, p.dtype), thx);
-  s.gout = mu + (double)(sv * (float)load_elem(p.xi[7], i, p.dtype));
+  const float te = __fmul_rn(__fmul_rn(__fmul_rn((float)p.kappa_s, af), sv),
+                             M<float>::rcp(__fmul_rn(muf, muf)));   // Eq. 8
+  s.gamma0 = gamma0; s.aeff = af; s.mu = mu; s.V = Vf; s.theta_e = te;
+  s.thx0 = thx; s.thy0 = thy; s.ty = thy;
+  s.tx = __fmaf_rn(te, load_t<float>(p.xi[6], i, p.dtype), thx);
+  s.gout = mu + (double)__fmul_rn(sv, load_t<float>(p.xi[7], i, p.dtype));
 }
 
+// FP32 QFP path: samples i0 and i1 through the model together (the phase
+// integration runs packed).
 __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
-                                                  int64_t i0, int64_t i1, Sample& s0,
-                                                  Sample& s1) {
+                                                  int64_t i0, int64_t i1, SampleF& s0,
+                                                  SampleF& s1) {
   double g00, g01;
   float tx0, ty0, tx1, ty1;
   const float a0 = focus<float>(p, i0, g00, tx0, ty0);
@@ -377,6 +405,36 @@ __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4*
   qfp_integrate_f32x2(p, tab, make_float2(a0, a1), make_float2((float)g00, (float)g01), du, V);
   finish_f32(p, i0, g00, a0, tx0, ty0, du.x, V.x, s0);
   finish_f32(p, i1, g01, a1, tx1, ty1, du.y, V.y, s1);
+}
+
+// FP32 classical path (Eq. 3 as 1/gamma_f - 1/gamma0 = c_RR a^2).
+__device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
+  SampleF s;
+  double gamma0;
+  float thx, thy;
+  const float a = focus<float>(p, i, gamma0, thx, thy);
+  const float du = __fmul_rn(__fmul_rn((float)p.cRR, a), a);
+  finish_f32(p, i, gamma0, a, thx, thy, du, 0.f, s);
+  s.theta_e = 0.f;
+  s.tx = thx;
+  s.gout = s.mu;
+  return s;
+}
+
+// One sample of the path selected by T and QFP (FP32 QFP samples are
+// normally evaluated in pairs; a single one runs as a pair with itself).
+template <typename T, bool QFP>
+__device__ __forceinline__ typename SampleT<T>::type eval_one(
+    const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i) {
+  if constexpr (sizeof(T) == 8) {
+    return eval_sample<double, QFP>(p, tab, i);
+  } else if constexpr (QFP) {
+    SampleF s0, s1;
+    eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1);
+    return s0;
+  } else {
+    return eval_ll_f32(p, i);
+  }
 }
 
 // Energy bin: -1 under, n_bins over (half-open bins).
@@ -419,6 +477,39 @@ __device__ __forceinline__ int aeff_bin(const Params& p, double a) {
   return p.n_aeff;
 }
 
+// FP32-path binning: energy index from the FP64 final energy (uniform bins:
+// one FP64 subtract and multiply; log bins: an FP32 base-2 logarithm), map
+// and a_eff indices in FP32.  Decisions differ from the FP64 path only for
+// values within the FP32 error of a bin edge.
+__device__ __forceinline__ int energy_bin_f32(const Params& p, double g) {
+  if (!p.log_spaced) {
+    const float tf = __fmul_rn((float)(g - p.lo), (float)p.inv_w);
+    if (!(tf >= 0.f)) return -1;
+    if (tf >= (float)p.n_bins) return p.n_bins;
+    return (int)tf;
+  }
+  const float t =
+      (g > 0.0) ? __fsub_rn(__fmul_rn(M<float>::lg2((float)g), p.log2_scale), p.log2_offset) : -1.f;
+  if (!(t >= 0.f)) return -1;
+  if (t >= (float)p.n_bins) return p.n_bins;
+  return (int)t;
+}
+
+__device__ __forceinline__ int map_cell_f32(const Params& p, float tx, float ty) {
+  const float tm = (float)p.tmax;
+  const float fx = __fmul_rn(__fadd_rn(tx, tm), (float)p.tsx);
+  const float fy = __fmul_rn(__fadd_rn(ty, tm), (float)p.tsy);
+  if (fx >= 0.f && fx < (float)p.n_tx && fy >= 0.f && fy < (float)p.n_ty)
+    return (int)fy * p.n_tx + (int)fx;
+  return -1;
+}
+
+__device__ __forceinline__ int aeff_bin_f32(const Params& p, float a) {
+  const float f = __fmul_rn(a, (float)p.a_scale);
+  if (f >= 0.f && f < (float)p.n_aeff) return (int)f;
+  return p.n_aeff;
+}
+
 // Merge of two (weight, mean, central sum of squares) triples (the parallel
 // form of the variance recurrence): exact when one side is empty, no
 // cancellation between large raw moments.
@@ -439,28 +530,83 @@ __device__ __forceinline__ void welford_merge(double& W, double& m, double& M2, 
   W = Wn;
 }
 
-__device__ __forceinline__ void acc_init(double (&acc)[kNumAcc]) {
+// Per-thread moment accumulators.  FP64 path: plain FP64 sums.  FP32 path:
+// compensated (Kahan) FP32 sums, converted to FP64 once per thread; the
+// reductions across threads, CTAs and tiles are FP64.  Entries:
+//   0 W, 1 sum w d, 2 sum w d^2 (d = mu - shift, shift = the thread's first
+//   mu), 3 sum w V, 4 sum w (thx0^2 + theta_e^2), 5 sum w thy0^2,
+//   6 sum w a_eff, 7 sum w gamma0; plus the excluded count and the shift.
+struct AccD {
+  double a[kNumAcc];
+};
+struct AccF {
+  float s[8], c[8];
+  float nonfinite, shift;
+};
+template <typename T> struct AccT;
+template <> struct AccT<double> { using type = AccD; };
+template <> struct AccT<float> { using type = AccF; };
+
+__device__ __forceinline__ void acc_init(AccD& A) {
 #pragma unroll
-  for (int k = 0; k < kNumAcc; ++k) acc[k] = 0.0;
-  acc[9] = __longlong_as_double(0x7ff8000000000000ll);   // no shift yet (NaN)
+  for (int k = 0; k < kNumAcc; ++k) A.a[k] = 0.0;
+  A.a[9] = __longlong_as_double(0x7ff8000000000000ll);   // no shift yet (NaN)
+}
+__device__ __forceinline__ void acc_init(AccF& A) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    A.s[k] = 0.f;
+    A.c[k] = 0.f;
+  }
+  A.nonfinite = 0.f;
+  A.shift = __int_as_float(0x7fc00000);                  // no shift yet (NaN)
+}
+
+// Kahan step in FP32 (explicit _rn operations: never contracted).
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+// Thread's accumulator as a moment slot (W, mean, M2, sums...).
+__device__ __forceinline__ void acc_slot(const AccD& A, double (&v)[kNumMom]) {
+  v[0] = A.a[0];
+  v[1] = 0.0;
+  v[2] = 0.0;
+  if (A.a[0] > 0.0) {
+    const double q = A.a[1] / A.a[0];
+    v[1] = A.a[9] + q;
+    v[2] = fmax(A.a[2] - A.a[1] * q, 0.0);
+  }
+#pragma unroll
+  for (int k = 3; k < kNumMom; ++k) v[k] = A.a[k];
+}
+__device__ __forceinline__ void acc_slot(const AccF& A, double (&v)[kNumMom]) {
+  double t[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t[k] = (double)A.s[k] - (double)A.c[k];
+  v[0] = t[0];
+  v[1] = 0.0;
+  v[2] = 0.0;
+  if (t[0] > 0.0) {
+    const double q = t[1] / t[0];
+    v[1] = (double)A.shift + q;
+    v[2] = fmax(t[2] - t[1] * q, 0.0);
+  }
+#pragma unroll
+  for (int k = 3; k < 8; ++k) v[k] = t[k];
+  v[8] = (double)A.nonfinite;
 }
 
 // Fixed-order block reduction of the per-thread accumulators into one
 // moment slot out[0..kNumMom): warp shuffle tree, then warps in order.
-__device__ __forceinline__ void block_reduce_write(double (&acc)[kNumAcc], double* red,
-                                                   double* out) {
+template <typename A>
+__device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v[kNumMom];
-  v[0] = acc[0];
-  v[1] = 0.0;
-  v[2] = 0.0;
-  if (acc[0] > 0.0) {
-    const double q = acc[1] / acc[0];
-    v[1] = acc[9] + q;
-    v[2] = fmax(acc[2] - acc[1] * q, 0.0);
-  }
-#pragma unroll
-  for (int k = 3; k < kNumMom; ++k) v[k] = acc[k];
+  acc_slot(acc, v);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     double u[kNumMom];
@@ -490,7 +636,8 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[kNumAcc], doubl
 
 // Smoothed-spectrum deposit of one sample (fixed point, like the weighted
 // histograms): S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)).
-template <typename T>
+// FP64 path in FP64; FP32 path: bin position in FP64, Gaussian weights in
+// FP32 (relative error ~1e-7 per deposit).
 __device__ __forceinline__ void deposit_smooth(const Params& p, double gout, double w,
                                                unsigned long long* dst) {
   const double t = (gout - p.lo) * p.inv_w;
@@ -500,19 +647,31 @@ __device__ __forceinline__ void deposit_smooth(const Params& p, double gout, dou
   const double wq = w * p.smooth_pref * p.wscale;
   for (int k = k0; k <= k1; ++k) {
     const double d = (double)k + 0.5 - t;
-    double e;
-    if (sizeof(T) == 4) e = (double)M<float>::ex2(-(float)(d * d * p.smooth_c));
-    else e = exp2(-d * d * p.smooth_c);
-    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * e));
+    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * exp2(-d * d * p.smooth_c)));
+  }
+}
+__device__ __forceinline__ void deposit_smooth_f32(const Params& p, double gout, float w,
+                                                   unsigned long long* dst) {
+  const double t = (gout - p.lo) * p.inv_w;
+  if (!(t > -1e9 && t < 1e9)) return;
+  int k0, k1;
+  smooth_range(p, t, &k0, &k1);
+  const float tf = (float)(t - (double)k0);             // position relative to bin k0
+  const float wq = (float)((double)w * p.smooth_pref * p.wscale);
+  const float c = (float)p.smooth_c;
+  for (int k = k0; k <= k1; ++k) {
+    const float d = __fsub_rn((float)(k - k0) + 0.5f, tf);
+    const float e = M<float>::ex2(-__fmul_rn(__fmul_rn(d, d), c));
+    atomicAdd(&dst[k], (unsigned long long)__float2ll_rn(__fmul_rn(wq, e)));
   }
 }
 
 // One evaluated sample into the moment partials and histograms (rows a7-a8).
 template <typename T, typename H, bool SHIST>
-__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i,
-                                           double (&acc)[kNumAcc], H* hs, H* hm, H* ha,
-                                           unsigned long long* hsm, int64_t nspec, int64_t nmap,
-                                           int64_t naeff) {
+__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i, AccD& A,
+                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
+                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+  double* acc = A.a;
   const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
   const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
                   isfinite(w) && w >= 0.0;
@@ -549,7 +708,52 @@ __device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int
     if (SHIST) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
-  if (hsm) deposit_smooth<T>(p, s.gout, w, hsm);
+  if (hsm) deposit_smooth(p, s.gout, w, hsm);
+}
+
+template <typename T, typename H, bool SHIST>
+__device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
+                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
+                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+  const float w = p.weighted ? load_t<float>(p.w, i, p.dtype) : 1.f;
+  const float muf = (float)s.mu;
+  const bool ok = isfinite(muf) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
+                  isfinite(w) && w >= 0.f;
+  if (!ok) {
+    A.nonfinite = __fadd_rn(A.nonfinite, 1.f);
+    return;
+  }
+  if (isnan(A.shift)) A.shift = muf;                     // the thread's shift
+  const float d = __fsub_rn(muf, A.shift);
+  const float wd = __fmul_rn(w, d);
+  kahan(A.s[0], A.c[0], w);
+  kahan(A.s[1], A.c[1], wd);
+  kahan(A.s[2], A.c[2], __fmul_rn(wd, d));
+  kahan(A.s[3], A.c[3], __fmul_rn(w, s.V));
+  kahan(A.s[4], A.c[4], __fmul_rn(w, __fmaf_rn(s.thx0, s.thx0, __fmul_rn(s.theta_e, s.theta_e))));
+  kahan(A.s[5], A.c[5], __fmul_rn(w, __fmul_rn(s.thy0, s.thy0)));
+  kahan(A.s[6], A.c[6], __fmul_rn(w, s.aeff));
+  kahan(A.s[7], A.c[7], __fmul_rn(w, (float)s.gamma0));
+  const unsigned long long q =
+      p.weighted ? (unsigned long long)__double2ll_rn((double)w * p.wscale) : 1ull;
+  if (nspec) {
+    const int b = energy_bin_f32(p, s.gout);
+    const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+    if (SHIST) atomicAdd(&hs[slot], (H)q);
+    else atomicAdd(&p.acc_spec[slot], q);
+  }
+  if (nmap) {
+    const int c = map_cell_f32(p, s.tx, s.ty);
+    const int64_t slot = c < 0 ? nmap - 1 : c;
+    if (SHIST) atomicAdd(&hm[slot], (H)q);
+    else atomicAdd(&p.acc_map[slot], q);
+  }
+  if (naeff) {
+    const int slot = aeff_bin_f32(p, s.aeff);
+    if (SHIST) atomicAdd(&ha[slot], (H)q);
+    else atomicAdd(&p.acc_aeff[slot], q);
+  }
+  if (hsm) deposit_smooth_f32(p, s.gout, w, hsm);
 }
 
 }  // namespace qs

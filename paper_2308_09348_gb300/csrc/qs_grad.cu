@@ -250,9 +250,21 @@ __global__ void __launch_bounds__(256) k_grad(const Params p, const qs_moments* 
         int k0, k1;
         smooth_range(p, tt, &k0, &k1);
         const double sg2 = p.smooth_sigma * p.smooth_sigma;
-        for (int k = k0; k <= k1; ++k) {
-          const double d = (double)k + 0.5 - tt;
-          g_out += dLdS[k] * exp2(-d * d * p.smooth_c) * d;
+        if (sizeof(T) == 4) {
+          // FP32 path: Gaussian weights in FP32 (as in the forward deposit)
+          const float tf = (float)(tt - (double)k0);
+          const float c = (float)p.smooth_c;
+          float ga = 0.f;
+          for (int k = k0; k <= k1; ++k) {
+            const float d = (float)(k - k0) + 0.5f - tf;
+            ga = fmaf((float)dLdS[k] * M<float>::ex2(-(d * d) * c), d, ga);
+          }
+          g_out = (double)ga;
+        } else {
+          for (int k = k0; k <= k1; ++k) {
+            const double d = (double)k + 0.5 - tt;
+            g_out += dLdS[k] * exp2(-d * d * p.smooth_c) * d;
+          }
         }
         g_out *= w * p.smooth_pref * p.inv_w / sg2;
       }

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
     for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x) ssm[b] = 0;
   __syncthreads();
 
-  double acc[kNumAcc];
+  typename AccT<T>::type acc;
   acc_init(acc);
 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -192,14 +192,14 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
     // FP32 QFP: each thread carries samples 2k and 2k+1 (packed f32x2)
     for (int64_t k = t0; 2 * k < p.n; k += stride) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
-      Sample s0, s1;
+      SampleF s0, s1;
       eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
       accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
       if (i1 != i0) accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
   } else {
     for (int64_t i = t0; i < p.n; i += stride) {
-      const Sample s = eval_sample<T, QFP>(p, tab, i);
+      const auto s = eval_one<T, QFP>(p, tab, i);
       accumulate<T, H, SHIST>(p, s, i, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
   }
@@ -320,6 +320,31 @@ __device__ __forceinline__ void write_record(const Params& p, const qs_sample_ou
   if (o.abin) o.abin[i] = p.n_aeff > 0 ? aeff_bin(p, s.aeff) : -1;
 }
 
+// FP32-path record: bins from the same FP32-path helpers as k_scatter.
+__device__ __forceinline__ void write_record(const Params& p, const qs_sample_out& o,
+                                             const SampleF& s, int64_t i) {
+  if (o.gamma0) o.gamma0[i] = s.gamma0;
+  if (o.aeff) o.aeff[i] = (double)s.aeff;
+  if (o.mu) o.mu[i] = s.mu;
+  if (o.V) o.V[i] = (double)s.V;
+  if (o.theta_e) o.theta_e[i] = (double)s.theta_e;
+  if (o.theta_x) o.theta_x[i] = (double)s.tx;
+  if (o.theta_y) o.theta_y[i] = (double)s.ty;
+  if (o.gamma_out) o.gamma_out[i] = s.gout;
+  if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin_f32(p, s.gout) : -1;
+  int ix = -1, iy = -1;
+  if (p.n_tx > 0) {
+    const int c = map_cell_f32(p, s.tx, s.ty);
+    if (c >= 0) {
+      ix = c % p.n_tx;
+      iy = c / p.n_tx;
+    }
+  }
+  if (o.ix) o.ix[i] = ix;
+  if (o.iy) o.iy[i] = iy;
+  if (o.abin) o.abin[i] = p.n_aeff > 0 ? aeff_bin_f32(p, s.aeff) : -1;
+}
+
 // K0: per-sample records; the same per-sample code path as k_scatter.
 template <typename T, bool QFP>
 __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
@@ -334,13 +359,13 @@ __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
   if constexpr (QFP && sizeof(T) == 4) {
     for (int64_t k = t0; 2 * k < p.n; k += stride) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
-      Sample s0, s1;
+      SampleF s0, s1;
       eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
       write_record(p, o, s0, i0);
       if (i1 != i0) write_record(p, o, s1, i1);
     }
   } else {
-    for (int64_t i = t0; i < p.n; i += stride) write_record(p, o, eval_sample<T, QFP>(p, tab, i), i);
+    for (int64_t i = t0; i < p.n; i += stride) write_record(p, o, eval_one<T, QFP>(p, tab, i), i);
   }
 }
 

@@ -10,6 +10,9 @@ from paper_2308_09348_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+# agreement of moments between different sample partitions of one problem
+MOM_RTOL = {"f64": 1e-12, "f32": 1e-8}
+
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
@@ -64,7 +67,9 @@ def test_batch_equals_single_shot_calls(prec, weighted):
         # identical per-sample code: integer histograms agree exactly
         assert np.array_equal(spectra[s], ref.spectrum.cpu().numpy()), s
         r = ref.moments.cpu().numpy()
-        np.testing.assert_allclose(mom[s], r, rtol=1e-12, atol=1e-300)
+        # FP32 path: per-thread compensated FP32 sums over different sample
+        # partitions (batch tiles vs single-shot grid) differ in rounding
+        np.testing.assert_allclose(mom[s], r, rtol=MOM_RTOL[prec], atol=1e-300)
 
 
 def test_batch_matches_oracle_f64():
@@ -105,7 +110,8 @@ def test_schedule_does_not_change_results(tile, block):
     ref, _, _ = _run_batch(bw, offsets, xi, "f32")
     bt, _, _ = _run_batch(bw, offsets, xi, "f32", tile=tile, block=block)
     assert torch.equal(bt.spectra, ref.spectra)
-    np.testing.assert_allclose(bt.moments.cpu().numpy(), ref.moments.cpu().numpy(), rtol=1e-13)
+    np.testing.assert_allclose(bt.moments.cpu().numpy(), ref.moments.cpu().numpy(),
+                               rtol=MOM_RTOL["f32"])
 
 
 def test_batch_repeated_and_graph_replay_identical():
@@ -132,3 +138,27 @@ def test_all_empty_shots():
     xi = [np.zeros(4, dtype=np.float32) for _ in range(8)]
     bt, _, _ = _run_batch(bw, offsets, xi, "f32")
     assert float(bt.moments.abs().sum()) == 0 and float(bt.spectra.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_delay_sweep_over_shared_samples(prec):
+    """A sweep (no offsets): every shot integrates the same samples with its
+    own delay; each equals a single-shot call with that delay."""
+    wl = I.broadband_qfp(3001)
+    L0 = I.Laser(**{**wl.laser.__dict__, "n_phase": 128})
+    delays = np.linspace(-100.0, 100.0, 9)
+    lasers = [I.Laser(**{**L0.__dict__, "delay_fs": float(d)}) for d in delays]
+    beams = [wl.beam] * len(delays)
+    xi, _ = I.workload_inputs(wl, 3001)
+    xt = [torch.from_numpy(a).cuda() for a in xi]
+    bt = B.Batch(lasers, beams, None, wl.bins, 3001, precision=prec)
+    bt.run(xt)
+    torch.cuda.synchronize()
+    for k, L in enumerate(lasers):
+        ref = B.qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(bt.spectra[k], ref.spectrum), k
+        np.testing.assert_allclose(bt.moments[k].cpu().numpy(), ref.moments.cpu().numpy(),
+                                   rtol=MOM_RTOL[prec])
+    # the sweep is symmetric in nothing in particular, but the spectra differ
+    assert not torch.equal(bt.spectra[0], bt.spectra[4])

@@ -37,7 +37,9 @@ def test_host_equals_device(chunk, prec, model):
     assert torch.equal(out.divmap, ref.divmap.cpu())
     assert torch.equal(out.aeff_hist, ref.aeff_hist.cpu())
     assert torch.equal(out.spec_smooth, ref.spec_smooth.cpu())
-    np.testing.assert_allclose(out.moments.numpy(), ref.moments.cpu().numpy(), rtol=1e-13)
+    # chunked launches partition the samples differently from one launch
+    np.testing.assert_allclose(out.moments.numpy(), ref.moments.cpu().numpy(),
+                               rtol=1e-13 if prec == "f64" else 1e-8)
 
 
 def test_host_pageable_memory_and_repeat():

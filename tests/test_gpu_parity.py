@@ -89,7 +89,9 @@ def compare_samples(rec, ref, prec, bins, check_bins=True):
             "V": float(np.max(np.abs(g["V"] - ref["V"]) / (np.abs(ref["V"]) + 1e-6 * vmax))),
             "gout_abs/tol": float(np.max(np.abs(g["gamma_out"] - ref["gamma_out"]) / gabs))}
     print(f"[{prec}] error profile:", prof)
-    assert prof["gamma0"] <= 1e-15
+    # FP32 path: gamma0 = gamma_mean (1 + s xi3) is formed in FP32 (then
+    # promoted exactly for the FP64 recombination)
+    assert prof["gamma0"] <= (1e-15 if prec == "f64" else 2.0 ** -22)
     assert prof["aeff"] <= 1.0
     assert prof["mu"] <= tol["mu"]
     assert prof["V"] <= tol["V"]
@@ -329,7 +331,8 @@ def test_launch_shapes_agree(block, grid):
     o = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32", block=block, grid=grid)
     assert torch.equal(ref.spectrum, o.spectrum) and torch.equal(ref.divmap, o.divmap)
     rm, om = ref.moments.cpu().numpy(), o.moments.cpu().numpy()
-    np.testing.assert_allclose(om, rm, rtol=1e-13)
+    # per-thread compensated FP32 sums over a different partition of samples
+    np.testing.assert_allclose(om, rm, rtol=1e-8)
 
 
 def test_graph_capture_replay():
@@ -372,12 +375,13 @@ def test_full_size_quantum_workload_sampled_parity():
     cnt = torch.bincount(b.clamp(min=0, max=wl.bins.n_bins - 1)[(b >= 0) & (b < wl.bins.n_bins)],
                          minlength=wl.bins.n_bins)
     assert torch.equal(cnt.double(), out.spectrum)
-    # fused moments equal moments of the per-sample records (reduction order only)
+    # fused moments equal moments of the per-sample records up to the FP32
+    # path's compensated per-thread accumulation
     mu = rec["mu"]
     mean = float(mu.mean())
     var = float(((mu - mean) ** 2).mean() + rec["V"].mean())
-    assert abs(m["mean"] / mean - 1) < 1e-12
-    assert abs(m["spread"] / math.sqrt(var) - 1) < 1e-10
+    assert abs(m["mean"] / mean - 1) < 1e-8
+    assert abs(m["spread"] / math.sqrt(var) - 1) < 1e-8
     # sampled per-sample parity with the oracle across the whole index range
     idx = np.unique(np.concatenate([np.arange(64), n - 1 - np.arange(64),
                                     I.rng(9).integers(0, n, 1024)]))
