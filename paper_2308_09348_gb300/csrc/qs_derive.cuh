@@ -181,6 +181,24 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   }
   p.wscale = ldexp(1.0, wbits);
   p.gamma_ref = B.flat_energy ? 0.5 * (B.gamma_lo + B.gamma_hi) : B.gamma_mean;
+
+  // FP32 copies (each double rounded once to nearest)
+  Params::F& f = p.f;
+  f.a0 = (float)p.a0; f.inv_w0sq = (float)p.inv_w0sq; f.inv_zR = (float)p.inv_zR;
+  f.ldx = (float)p.ldx; f.ldy = (float)p.ldy; f.c_delay = (float)p.c_delay;
+  f.cRR = (float)p.cRR; f.h = (float)p.h; f.cK = (float)p.cK; f.hcK = (float)(p.h * p.cK);
+  f.cchi = (float)p.cchi; f.kappa_s = (float)p.kappa_s;
+  f.gmean = (float)p.gmean; f.spread = (float)p.spread; f.glo = (float)p.glo;
+  f.gspan = (float)p.gspan; f.sx = (float)p.sx; f.sy = (float)p.sy; f.sz = (float)p.sz;
+  f.div = (float)p.div; f.bdx = (float)p.bdx; f.bdy = (float)p.bdy;
+  f.lo = (float)p.lo; f.inv_w = (float)p.inv_w; f.tmax = (float)p.tmax;
+  f.tsx = (float)p.tsx; f.tsy = (float)p.tsy; f.a_scale = (float)p.a_scale;
+  f.n_bins = (float)p.n_bins; f.n_tx = (float)p.n_tx; f.n_ty = (float)p.n_ty;
+  f.n_aeff = (float)p.n_aeff; f.smooth_c = (float)p.smooth_c;
+  f.wscale = (float)p.wscale;
+  f.smooth_pw = (float)(p.smooth_pref * p.wscale);
+  f.smooth_lo = (float)(0.5 + 6.0 * p.smooth_sigma);
+  f.smooth_hi = (float)(6.0 * p.smooth_sigma - 0.5);
 }
 
 }  // namespace qs

@@ -62,7 +62,26 @@ struct Params {
   unsigned long long* acc_smooth;
   // FP32 path, log-spaced bins: t = lg2(gamma) * log2_scale - log2_offset
   float log2_scale, log2_offset;
+  // FP32 copies of the per-sample constants, each the double above rounded
+  // once to nearest when the constants are derived: the FP32 path then reads
+  // them as they are (no per-sample double-to-float conversion, which runs
+  // on the FP64 pipe).  hcK = h * cK rounded once.
+  struct F {
+    float a0, inv_w0sq, inv_zR, ldx, ldy, c_delay, cRR, h, cK, hcK, cchi, kappa_s;
+    float gmean, spread, glo, gspan, sx, sy, sz, div, bdx, bdy;
+    float lo, inv_w, tmax, tsx, tsy, a_scale, n_bins, n_tx, n_ty, n_aeff, smooth_c;
+    float wscale;                  // 2^weight_frac_bits (exact)
+    float smooth_pw;               // smooth_pref * wscale
+    float smooth_lo, smooth_hi;    // 0.5 + 6 sigma, 6 sigma - 0.5 (bins)
+  } f;
 };
+
+// A per-sample constant in the arithmetic type T: the double for the FP64
+// path, its FP32 copy for the FP32 path.
+template <typename T> __device__ __forceinline__ T pv(double d, float f);
+template <> __device__ __forceinline__ float pv<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pv<double>(double d, float) { return d; }
+#define QS_PV(T, field) ::qs::pv<T>(p.field, p.f.field)
 
 // ---- math policy --------------------------------------------------------
 template <typename T> struct M;
@@ -103,6 +122,23 @@ __device__ __forceinline__ T load_t(const void* p, int64_t i, int dtype) {
   if (p == nullptr) return (T)0;
   if (dtype == 0) return (T)__ldg(static_cast<const float*>(p) + i);
   return (T)__ldg(static_cast<const double*>(p) + i);
+}
+
+// A finite non-negative float rounded to the nearest integer (ties to even)
+// as an unsigned 64-bit value, saturating at 2^63 - 1 as the PTX conversion
+// does.  Integer operations only: a 64-bit float-to-integer conversion is an
+// FP64-pipe instruction, and the FP64 pipe issues at a small fraction of the
+// FP32 rate on this GPU.
+__device__ __forceinline__ unsigned long long f2u64_rn(float x) {
+  const unsigned u = __float_as_uint(x);
+  const int e = (int)(u >> 23);                        // biased exponent (sign is 0)
+  const unsigned long long m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int sh = (e ? e : 1) - 150;                    // x = m 2^sh
+  if (sh >= 0) return sh >= 40 ? 0x7fffffffffffffffull : m << sh;
+  if (sh <= -25) return 0ull;                          // x < 1/2
+  const int r = -sh;
+  const unsigned long long q = m >> r, rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+  return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
 // Phase-cell envelope G(phi_j) at the midpoint of cell j, in double.
@@ -224,8 +260,8 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
   const float2 LN2 = f2(0.69314718055994530942f);
   const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
   const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
-  const float2 c1 = mul2(mul2(f2((float)(p.h * p.cK)), a), a);
-  const float2 ca = mul2(f2((float)p.cchi), a);
+  const float2 c1 = mul2(mul2(f2(p.f.hcK), a), a);
+  const float2 ca = mul2(f2(p.f.cchi), a);
   float2 du = f2(0.f), V = f2(0.f), gph = HALF;
   const int N = p.n_phase;
 #pragma unroll 2
@@ -276,96 +312,81 @@ __device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// a_eff at the crossing point and the decoded sample (rows a1-a3).
+// a_eff at the crossing point and the decoded sample (rows a1-a3), from the
+// sample's six normal deviates.
 template <typename T>
-__device__ __forceinline__ T focus(const Params& p, int64_t i, double& gamma0, T& thx, T& thy) {
-  const T xi0 = load_t<T>(p.xi[0], i, p.dtype);
-  const T xi1 = load_t<T>(p.xi[1], i, p.dtype);
-  const T xi2 = load_t<T>(p.xi[2], i, p.dtype);
-  const T xi3 = load_t<T>(p.xi[3], i, p.dtype);
-  const T xi4 = load_t<T>(p.xi[4], i, p.dtype);
-  const T xi5 = load_t<T>(p.xi[5], i, p.dtype);
-  // decode (reparameterised); gamma0 in the arithmetic type (exactly
-  // representable in FP64 for the FP64 recombination)
-  const T x = op_fma((T)p.sx, xi0, (T)p.bdx);
-  const T y = op_fma((T)p.sy, xi1, (T)p.bdy);
-  const T z = op_mul((T)p.sz, xi2);
-  T g0 = p.flat ? op_fma((T)p.gspan, xi3, (T)p.glo)
-                : op_mul((T)p.gmean, op_fma((T)p.spread, xi3, (T)1));
+__device__ __forceinline__ T focus_xi(const Params& p, T xi0, T xi1, T xi2, T xi3, T xi4, T xi5,
+                                      T& gamma0, T& thx, T& thy) {
+  // decode (reparameterised); gamma0 in the arithmetic type
+  const T x = op_fma(QS_PV(T, sx), xi0, QS_PV(T, bdx));
+  const T y = op_fma(QS_PV(T, sy), xi1, QS_PV(T, bdy));
+  const T z = op_mul(QS_PV(T, sz), xi2);
+  T g0 = p.flat ? op_fma(QS_PV(T, gspan), xi3, QS_PV(T, glo))
+                : op_mul(QS_PV(T, gmean), op_fma(QS_PV(T, spread), xi3, (T)1));
   if (g0 < (T)1) g0 = (T)1;
-  gamma0 = (double)g0;
-  thx = op_mul((T)p.div, xi4);
-  thy = op_mul((T)p.div, xi5);
+  gamma0 = g0;
+  thx = op_mul(QS_PV(T, div), xi4);
+  thy = op_mul(QS_PV(T, div), xi5);
   // collision geometry: crossing of the pulse peak (factor 2 of Eq. 1)
-  const T cdel = (T)p.c_delay;
+  const T cdel = QS_PV(T, c_delay);
   const T ct = op_mul((T)0.5, op_add(z, cdel));
   const T zs = op_mul((T)0.5, op_sub(z, cdel));
-  const T xs = op_sub(op_fma(thx, ct, x), (T)p.ldx);
-  const T ys = op_sub(op_fma(thy, ct, y), (T)p.ldy);
+  const T xs = op_sub(op_fma(thx, ct, x), QS_PV(T, ldx));
+  const T ys = op_sub(op_fma(thy, ct, y), QS_PV(T, ldy));
   const T rho2 = op_fma(xs, xs, op_mul(ys, ys));
   // local Gaussian focus, Eq. 2
-  const T zq = op_mul(zs, (T)p.inv_zR);
+  const T zq = op_mul(zs, QS_PV(T, inv_zR));
   const T q = op_fma(zq, zq, (T)1);
-  const T E = op_mul(op_mul(rho2, (T)p.inv_w0sq), M<T>::rcp(q));
+  const T E = op_mul(op_mul(rho2, QS_PV(T, inv_w0sq)), M<T>::rcp(q));
   if (sizeof(T) == 4)
-    return op_mul(op_mul((T)p.a0, M<T>::rsqrt(q)),
+    return op_mul(op_mul(QS_PV(T, a0), M<T>::rsqrt(q)),
                   M<T>::ex2(op_mul(-(T)1.4426950408889634074, E)));
-  return op_mul(op_mul((T)p.a0, M<T>::rsqrt(q)), (T)exp(-(double)E));
+  return op_mul(op_mul(QS_PV(T, a0), M<T>::rsqrt(q)), (T)exp(-(double)E));
+}
+
+template <typename T>
+__device__ __forceinline__ T focus(const Params& p, int64_t i, T& gamma0, T& thx, T& thy) {
+  return focus_xi<T>(p, load_t<T>(p.xi[0], i, p.dtype), load_t<T>(p.xi[1], i, p.dtype),
+                     load_t<T>(p.xi[2], i, p.dtype), load_t<T>(p.xi[3], i, p.dtype),
+                     load_t<T>(p.xi[4], i, p.dtype), load_t<T>(p.xi[5], i, p.dtype), gamma0,
+                     thx, thy);
 }
 
 // One beam sample through the model, in the paper's order (rows a1-a6).
-// QFP selects the model at compile time; the table is unused by LL.  Used
-// for the FP64 path and the FP32 classical path.
-template <typename T, bool QFP>
-__device__ __forceinline__ Sample eval_sample(const Params& p,
-                                              const typename Tab<T>::type* __restrict__ tab,
+// FP64 path: one sample through the model selected at compile time by QFP
+// (the table is unused by LL).
+template <bool QFP>
+__device__ __forceinline__ Sample eval_sample(const Params& p, const double* __restrict__ tab,
                                               int64_t i) {
   Sample s;
-  double gamma0;
-  T thx, thy;
-  const T a = focus<T>(p, i, gamma0, thx, thy);
-  double mu, V = 0.0;
-  if (sizeof(T) == 8) {
-    // FP64 path
-    const double ad = (double)a;
-    if (!QFP) {
-      // Eq. 3, a0 -> a_eff
-      mu = gamma0 / __fma_rn(__dmul_rn(__dmul_rn(p.cRR, gamma0), ad), ad, 1.0);
-    } else {
-      double du;
-      qfp_integrate(p, reinterpret_cast<const double*>(tab), ad, gamma0, du, V);
-      mu = gamma0 / __fma_rn(gamma0, du, 1.0);
-    }
-    double theta_e = 0.0, gout = mu, tx = (double)thx;
-    if (QFP) {
-      const double sv = V > 0.0 ? sqrt(V) : 0.0;
-      theta_e = __dmul_rn(__dmul_rn(p.kappa_s, ad), sv) / __dmul_rn(mu, mu);   // Eq. 8
-      tx = __fma_rn(theta_e, load_elem(p.xi[6], i, p.dtype), tx);
-      gout = __fma_rn(sv, load_elem(p.xi[7], i, p.dtype), mu);
-    }
-    s.theta_e = theta_e; s.tx = tx; s.gout = gout;
+  double gamma0, thx, thy, mu, V = 0.0;
+  const double a = focus<double>(p, i, gamma0, thx, thy);
+  if (!QFP) {
+    // Eq. 3, a0 -> a_eff
+    mu = gamma0 / __fma_rn(__dmul_rn(__dmul_rn(p.cRR, gamma0), a), a, 1.0);
   } else {
-    // FP32 path, classical model: 1/gamma_f - 1/gamma0 in FP32, recombined
-    // in FP64 with an FP32 reciprocal refined by one Newton step (relative
-    // error ~2^-46).  (The FP32 QFP path evaluates samples in pairs:
-    // eval_pair_f32_qfp.)
-    const float af = (float)a;
-    const float du = (float)p.cRR * af * af;                  // Eq. 3
-    const double den = fma(gamma0, (double)du, 1.0);
-    double r = (double)M<float>::rcp((float)den);
-    r = r * fma(-den, r, 2.0);
-    mu = gamma0 * r;
-    s.theta_e = 0.0; s.tx = (double)thx; s.gout = mu;
+    double du;
+    qfp_integrate(p, tab, a, gamma0, du, V);
+    mu = gamma0 / __fma_rn(gamma0, du, 1.0);
   }
-  s.gamma0 = gamma0; s.aeff = (double)a; s.mu = mu; s.V = V;
-  s.thx0 = (double)thx; s.thy0 = (double)thy; s.ty = (double)thy;
+  double theta_e = 0.0, gout = mu, tx = thx;
+  if (QFP) {
+    const double sv = V > 0.0 ? sqrt(V) : 0.0;
+    theta_e = __dmul_rn(__dmul_rn(p.kappa_s, a), sv) / __dmul_rn(mu, mu);   // Eq. 8
+    tx = __fma_rn(theta_e, load_elem(p.xi[6], i, p.dtype), tx);
+    gout = __fma_rn(sv, load_elem(p.xi[7], i, p.dtype), mu);
+  }
+  s.theta_e = theta_e; s.tx = tx; s.gout = gout;
+  s.gamma0 = gamma0; s.aeff = a; s.mu = mu; s.V = V;
+  s.thx0 = thx; s.thy0 = thy; s.ty = thy;
   return s;
 }
 
-// FP32-path per-sample record: FP64 only where the path keeps FP64 (gamma0,
-// the recombined mean energy, the realised energy), FP32 elsewhere.
+// FP32-path per-sample record.  The mean energy and the realised energy are
+// kept as unevaluated sums of two floats (hi + lo, ~2^-44 relative); the
+// rest is FP32.
 struct SampleF {
-  double gamma0, mu, gout;
+  float g0, mu_hi, mu_lo, go_hi, go_lo;
   float aeff, V, theta_e, thx0, thy0, tx, ty;
 };
 
@@ -373,23 +394,45 @@ template <typename T> struct SampleT;
 template <> struct SampleT<double> { using type = Sample; };
 template <> struct SampleT<float> { using type = SampleF; };
 
-// 1/gamma_f = 1/gamma0 + du recombined in FP64 with an FP32 reciprocal
-// refined by one Newton step (relative error ~2^-46), then Eq. 8 and the
-// realised energy.
-__device__ __forceinline__ void finish_f32(const Params& p, int64_t i, double gamma0, float af,
+// mu = g0 / (1 + g0 du) in two-float arithmetic on the FP32 pipes (the
+// "1/gamma recombination": 1/gamma_f = 1/gamma0 + du).  g0 du and 1 + g0 du
+// are formed exactly as float pairs (FMA product error, two-sum), the
+// quotient from an FP32 reciprocal is corrected once with its FMA residual:
+// relative error ~2^-44, and mu == g0 exactly when du == 0.
+__device__ __forceinline__ void recombine_f2(float g0, float du, float& hi, float& lo) {
+  const float p = __fmul_rn(g0, du);
+  const float pe = __fmaf_rn(g0, du, -p);                  // g0 du = p + pe exactly
+  const float s = __fadd_rn(1.f, p);                       // 1 + p = s + se exactly
+  const float bb = __fsub_rn(s, 1.f);
+  const float se = __fadd_rn(__fsub_rn(1.f, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float t = __fadd_rn(se, pe);
+  const float dh = __fadd_rn(s, t);                        // den = dh + dl
+  const float dl = __fsub_rn(t, __fsub_rn(dh, s));
+  const float r0 = M<float>::rcp(dh);
+  const float q0 = __fmul_rn(g0, r0);
+  const float e1 = __fmaf_rn(-q0, dh, g0);                 // residual g0 - q0 den
+  const float e2 = __fmaf_rn(-q0, dl, e1);
+  const float c = __fmul_rn(e2, r0);
+  hi = __fadd_rn(q0, c);
+  lo = __fsub_rn(c, __fsub_rn(hi, q0));
+}
+
+// Recombination, then Eq. 8 and the realised energy (rows a5-a6, FP32 path).
+__device__ __forceinline__ void finish_f32(const Params& p, int64_t i, float g0, float af,
                                            float thx, float thy, float du, float Vf, SampleF& s) {
-  const double den = fma(gamma0, (double)du, 1.0);
-  double r = (double)M<float>::rcp((float)den);
-  r = r * fma(-den, r, 2.0);
-  const double mu = gamma0 * r;
+  float hi, lo;
+  recombine_f2(g0, du, hi, lo);
   const float sv = Vf > 0.f ? sqrtf(Vf) : 0.f;
-  const float muf = (float)mu;
-  const float te = __fmul_rn(__fmul_rn(__fmul_rn((float)p.kappa_s, af), sv),
-                             M<float>::rcp(__fmul_rn(muf, muf)));   // Eq. 8
-  s.gamma0 = gamma0; s.aeff = af; s.mu = mu; s.V = Vf; s.theta_e = te;
+  const float te = __fmul_rn(__fmul_rn(__fmul_rn(p.f.kappa_s, af), sv),
+                             M<float>::rcp(__fmul_rn(hi, hi)));   // Eq. 8
+  const float x = __fmul_rn(sv, load_t<float>(p.xi[7], i, p.dtype));
+  const float xl = __fadd_rn(lo, x);
+  const float gh = __fadd_rn(hi, xl);
+  s.g0 = g0; s.aeff = af; s.mu_hi = hi; s.mu_lo = lo; s.V = Vf; s.theta_e = te;
   s.thx0 = thx; s.thy0 = thy; s.ty = thy;
   s.tx = __fmaf_rn(te, load_t<float>(p.xi[6], i, p.dtype), thx);
-  s.gout = mu + (double)__fmul_rn(sv, load_t<float>(p.xi[7], i, p.dtype));
+  s.go_hi = gh;
+  s.go_lo = __fsub_rn(xl, __fsub_rn(gh, hi));
 }
 
 // FP32 QFP path: samples i0 and i1 through the model together (the phase
@@ -397,28 +440,35 @@ __device__ __forceinline__ void finish_f32(const Params& p, int64_t i, double ga
 __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
                                                   int64_t i0, int64_t i1, SampleF& s0,
                                                   SampleF& s1) {
-  double g00, g01;
-  float tx0, ty0, tx1, ty1;
-  const float a0 = focus<float>(p, i0, g00, tx0, ty0);
-  const float a1 = focus<float>(p, i1, g01, tx1, ty1);
+  float g0f, g1f, tx0, ty0, tx1, ty1;
+  const float a0 = focus<float>(p, i0, g0f, tx0, ty0);
+  const float a1 = focus<float>(p, i1, g1f, tx1, ty1);
   float2 du, V;
-  qfp_integrate_f32x2(p, tab, make_float2(a0, a1), make_float2((float)g00, (float)g01), du, V);
-  finish_f32(p, i0, g00, a0, tx0, ty0, du.x, V.x, s0);
-  finish_f32(p, i1, g01, a1, tx1, ty1, du.y, V.y, s1);
+  qfp_integrate_f32x2(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V);
+  finish_f32(p, i0, g0f, a0, tx0, ty0, du.x, V.x, s0);
+  finish_f32(p, i1, g1f, a1, tx1, ty1, du.y, V.y, s1);
 }
 
 // FP32 classical path (Eq. 3 as 1/gamma_f - 1/gamma0 = c_RR a^2).
-__device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
+__device__ __forceinline__ SampleF eval_ll_f32_xi(const Params& p, float xi0, float xi1,
+                                                  float xi2, float xi3, float xi4, float xi5) {
   SampleF s;
-  double gamma0;
-  float thx, thy;
-  const float a = focus<float>(p, i, gamma0, thx, thy);
-  const float du = __fmul_rn(__fmul_rn((float)p.cRR, a), a);
-  finish_f32(p, i, gamma0, a, thx, thy, du, 0.f, s);
-  s.theta_e = 0.f;
-  s.tx = thx;
-  s.gout = s.mu;
+  float gamma0, thx, thy;
+  const float a = focus_xi<float>(p, xi0, xi1, xi2, xi3, xi4, xi5, gamma0, thx, thy);
+  const float du = __fmul_rn(__fmul_rn(p.f.cRR, a), a);
+  float hi, lo;
+  recombine_f2(gamma0, du, hi, lo);
+  s.g0 = gamma0; s.aeff = a; s.mu_hi = hi; s.mu_lo = lo; s.V = 0.f; s.theta_e = 0.f;
+  s.thx0 = thx; s.thy0 = thy; s.tx = thx; s.ty = thy;
+  s.go_hi = hi;
+  s.go_lo = lo;
   return s;
+}
+
+__device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
+  return eval_ll_f32_xi(p, load_t<float>(p.xi[0], i, p.dtype), load_t<float>(p.xi[1], i, p.dtype),
+                        load_t<float>(p.xi[2], i, p.dtype), load_t<float>(p.xi[3], i, p.dtype),
+                        load_t<float>(p.xi[4], i, p.dtype), load_t<float>(p.xi[5], i, p.dtype));
 }
 
 // One sample of the path selected by T and QFP (FP32 QFP samples are
@@ -427,7 +477,7 @@ template <typename T, bool QFP>
 __device__ __forceinline__ typename SampleT<T>::type eval_one(
     const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i) {
   if constexpr (sizeof(T) == 8) {
-    return eval_sample<double, QFP>(p, tab, i);
+    return eval_sample<QFP>(p, reinterpret_cast<const double*>(tab), i);
   } else if constexpr (QFP) {
     SampleF s0, s1;
     eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1);
@@ -471,6 +521,15 @@ __device__ __forceinline__ void smooth_range(const Params& p, double t, int* k0,
   *k1 = (int)hi;
 }
 
+// FP32 path: the same window with the offsets rounded to FP32.
+__device__ __forceinline__ void smooth_range_f32(const Params& p, float t, int* k0, int* k1) {
+  float lo = ceilf(__fsub_rn(t, p.f.smooth_lo)), hi = floorf(__fadd_rn(t, p.f.smooth_hi));
+  if (lo < 0.f) lo = 0.f;
+  if (hi > __fsub_rn(p.f.n_bins, 1.f)) hi = __fsub_rn(p.f.n_bins, 1.f);
+  *k0 = (int)lo;
+  *k1 = (int)hi;
+}
+
 __device__ __forceinline__ int aeff_bin(const Params& p, double a) {
   double f = a * p.a_scale;
   if (f >= 0.0 && f < (double)p.n_aeff) return (int)f;
@@ -481,32 +540,33 @@ __device__ __forceinline__ int aeff_bin(const Params& p, double a) {
 // one FP64 subtract and multiply; log bins: an FP32 base-2 logarithm), map
 // and a_eff indices in FP32.  Decisions differ from the FP64 path only for
 // values within the FP32 error of a bin edge.
-__device__ __forceinline__ int energy_bin_f32(const Params& p, double g) {
+__device__ __forceinline__ int energy_bin_f32(const Params& p, float gh, float gl) {
   if (!p.log_spaced) {
-    const float tf = __fmul_rn((float)(g - p.lo), (float)p.inv_w);
+    const float tf = __fmul_rn(__fadd_rn(__fsub_rn(gh, p.f.lo), gl), p.f.inv_w);
     if (!(tf >= 0.f)) return -1;
-    if (tf >= (float)p.n_bins) return p.n_bins;
+    if (tf >= p.f.n_bins) return p.n_bins;
     return (int)tf;
   }
+  const float g = __fadd_rn(gh, gl);
   const float t =
-      (g > 0.0) ? __fsub_rn(__fmul_rn(M<float>::lg2((float)g), p.log2_scale), p.log2_offset) : -1.f;
+      (g > 0.f) ? __fsub_rn(__fmul_rn(M<float>::lg2(g), p.log2_scale), p.log2_offset) : -1.f;
   if (!(t >= 0.f)) return -1;
-  if (t >= (float)p.n_bins) return p.n_bins;
+  if (t >= p.f.n_bins) return p.n_bins;
   return (int)t;
 }
 
 __device__ __forceinline__ int map_cell_f32(const Params& p, float tx, float ty) {
-  const float tm = (float)p.tmax;
-  const float fx = __fmul_rn(__fadd_rn(tx, tm), (float)p.tsx);
-  const float fy = __fmul_rn(__fadd_rn(ty, tm), (float)p.tsy);
-  if (fx >= 0.f && fx < (float)p.n_tx && fy >= 0.f && fy < (float)p.n_ty)
+  const float tm = p.f.tmax;
+  const float fx = __fmul_rn(__fadd_rn(tx, tm), p.f.tsx);
+  const float fy = __fmul_rn(__fadd_rn(ty, tm), p.f.tsy);
+  if (fx >= 0.f && fx < p.f.n_tx && fy >= 0.f && fy < p.f.n_ty)
     return (int)fy * p.n_tx + (int)fx;
   return -1;
 }
 
 __device__ __forceinline__ int aeff_bin_f32(const Params& p, float a) {
-  const float f = __fmul_rn(a, (float)p.a_scale);
-  if (f >= 0.f && f < (float)p.n_aeff) return (int)f;
+  const float f = __fmul_rn(a, p.f.a_scale);
+  if (f >= 0.f && f < p.f.n_aeff) return (int)f;
   return p.n_aeff;
 }
 
@@ -650,19 +710,19 @@ __device__ __forceinline__ void deposit_smooth(const Params& p, double gout, dou
     atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * exp2(-d * d * p.smooth_c)));
   }
 }
-__device__ __forceinline__ void deposit_smooth_f32(const Params& p, double gout, float w,
+__device__ __forceinline__ void deposit_smooth_f32(const Params& p, float gh, float gl, float w,
                                                    unsigned long long* dst) {
-  const double t = (gout - p.lo) * p.inv_w;
-  if (!(t > -1e9 && t < 1e9)) return;
+  const float tt = __fmul_rn(__fadd_rn(__fsub_rn(gh, p.f.lo), gl), p.f.inv_w);
+  if (!(tt > -1e9f && tt < 1e9f)) return;
   int k0, k1;
-  smooth_range(p, t, &k0, &k1);
-  const float tf = (float)(t - (double)k0);             // position relative to bin k0
-  const float wq = (float)((double)w * p.smooth_pref * p.wscale);
-  const float c = (float)p.smooth_c;
+  smooth_range_f32(p, tt, &k0, &k1);
+  const float tf = __fsub_rn(tt, (float)k0);            // position relative to bin k0
+  const float wq = __fmul_rn(w, p.f.smooth_pw);
+  const float c = p.f.smooth_c;
   for (int k = k0; k <= k1; ++k) {
     const float d = __fsub_rn((float)(k - k0) + 0.5f, tf);
     const float e = M<float>::ex2(-__fmul_rn(__fmul_rn(d, d), c));
-    atomicAdd(&dst[k], (unsigned long long)__float2ll_rn(__fmul_rn(wq, e)));
+    atomicAdd(&dst[k], f2u64_rn(__fmul_rn(wq, e)));
   }
 }
 
@@ -711,13 +771,12 @@ __device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int
   if (hsm) deposit_smooth(p, s.gout, w, hsm);
 }
 
-template <typename T, typename H, bool SHIST>
-__device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
-                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
-                                           int64_t nspec, int64_t nmap, int64_t naeff) {
-  const float w = p.weighted ? load_t<float>(p.w, i, p.dtype) : 1.f;
-  const float muf = (float)s.mu;
-  const bool ok = isfinite(muf) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
+template <typename H, bool SHIST>
+__device__ __forceinline__ void accumulate_w(const Params& p, const SampleF& s, float w, AccF& A,
+                                             H* hs, H* hm, H* ha, unsigned long long* hsm,
+                                             int64_t nspec, int64_t nmap, int64_t naeff) {
+  const float muf = s.mu_hi;
+  const bool ok = isfinite(muf) && isfinite(s.V) && isfinite(s.go_hi) && isfinite(s.tx) &&
                   isfinite(w) && w >= 0.f;
   if (!ok) {
     A.nonfinite = __fadd_rn(A.nonfinite, 1.f);
@@ -733,11 +792,11 @@ __device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, in
   kahan(A.s[4], A.c[4], __fmul_rn(w, __fmaf_rn(s.thx0, s.thx0, __fmul_rn(s.theta_e, s.theta_e))));
   kahan(A.s[5], A.c[5], __fmul_rn(w, __fmul_rn(s.thy0, s.thy0)));
   kahan(A.s[6], A.c[6], __fmul_rn(w, s.aeff));
-  kahan(A.s[7], A.c[7], __fmul_rn(w, (float)s.gamma0));
-  const unsigned long long q =
-      p.weighted ? (unsigned long long)__double2ll_rn((double)w * p.wscale) : 1ull;
+  kahan(A.s[7], A.c[7], __fmul_rn(w, s.g0));
+  // w 2^bits is exact in FP32, so this equals the FP64 path's rounding
+  const unsigned long long q = p.weighted ? f2u64_rn(__fmul_rn(w, p.f.wscale)) : 1ull;
   if (nspec) {
-    const int b = energy_bin_f32(p, s.gout);
+    const int b = energy_bin_f32(p, s.go_hi, s.go_lo);
     const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
     if (SHIST) atomicAdd(&hs[slot], (H)q);
     else atomicAdd(&p.acc_spec[slot], q);
@@ -753,7 +812,15 @@ __device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, in
     if (SHIST) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
-  if (hsm) deposit_smooth_f32(p, s.gout, w, hsm);
+  if (hsm) deposit_smooth_f32(p, s.go_hi, s.go_lo, w, hsm);
+}
+
+template <typename T, typename H, bool SHIST>
+__device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
+                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
+                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+  const float w = p.weighted ? load_t<float>(p.w, i, p.dtype) : 1.f;
+  accumulate_w<H, SHIST>(p, s, w, A, hs, hm, ha, hsm, nspec, nmap, naeff);
 }
 
 }  // namespace qs

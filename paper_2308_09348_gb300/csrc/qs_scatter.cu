@@ -198,7 +198,35 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
       if (i1 != i0) accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
   } else {
-    for (int64_t i = t0; i < p.n; i += stride) {
+    int64_t i = t0;
+    if constexpr (!QFP && sizeof(T) == 4) {
+      // FP32 classical path (memory-bound): four consecutive samples per
+      // thread through 16-byte loads of every stream, when all streams are
+      // FP32 and 16-byte aligned; the remaining samples below.
+      bool vec = p.dtype == QS_F32;
+      for (int k = 0; k < 6; ++k) vec = vec && p.xi[k] && ((uintptr_t)p.xi[k] & 15) == 0;
+      if (p.weighted) vec = vec && ((uintptr_t)p.w & 15) == 0;
+      if (vec) {
+        const int64_t n4 = p.n >> 2;
+        for (int64_t k = t0; k < n4; k += stride) {
+          float4 v[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
+          const float4 wv = p.weighted ? __ldg(static_cast<const float4*>(p.w) + k)
+                                       : make_float4(1.f, 1.f, 1.f, 1.f);
+          const SampleF s0 = eval_ll_f32_xi(p, v[0].x, v[1].x, v[2].x, v[3].x, v[4].x, v[5].x);
+          accumulate_w<H, SHIST>(p, s0, wv.x, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          const SampleF s1 = eval_ll_f32_xi(p, v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y);
+          accumulate_w<H, SHIST>(p, s1, wv.y, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          const SampleF s2 = eval_ll_f32_xi(p, v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z);
+          accumulate_w<H, SHIST>(p, s2, wv.z, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          const SampleF s3 = eval_ll_f32_xi(p, v[0].w, v[1].w, v[2].w, v[3].w, v[4].w, v[5].w);
+          accumulate_w<H, SHIST>(p, s3, wv.w, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+        }
+        i = 4 * n4 + t0;
+      }
+    }
+    for (; i < p.n; i += stride) {
       const auto s = eval_one<T, QFP>(p, tab, i);
       accumulate<T, H, SHIST>(p, s, i, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
     }
@@ -323,15 +351,15 @@ __device__ __forceinline__ void write_record(const Params& p, const qs_sample_ou
 // FP32-path record: bins from the same FP32-path helpers as k_scatter.
 __device__ __forceinline__ void write_record(const Params& p, const qs_sample_out& o,
                                              const SampleF& s, int64_t i) {
-  if (o.gamma0) o.gamma0[i] = s.gamma0;
+  if (o.gamma0) o.gamma0[i] = (double)s.g0;
   if (o.aeff) o.aeff[i] = (double)s.aeff;
-  if (o.mu) o.mu[i] = s.mu;
+  if (o.mu) o.mu[i] = (double)s.mu_hi + (double)s.mu_lo;
   if (o.V) o.V[i] = (double)s.V;
   if (o.theta_e) o.theta_e[i] = (double)s.theta_e;
   if (o.theta_x) o.theta_x[i] = (double)s.tx;
   if (o.theta_y) o.theta_y[i] = (double)s.ty;
-  if (o.gamma_out) o.gamma_out[i] = s.gout;
-  if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin_f32(p, s.gout) : -1;
+  if (o.gamma_out) o.gamma_out[i] = (double)s.go_hi + (double)s.go_lo;
+  if (o.bin) o.bin[i] = p.n_bins > 0 ? energy_bin_f32(p, s.go_hi, s.go_lo) : -1;
   int ix = -1, iy = -1;
   if (p.n_tx > 0) {
     const int c = map_cell_f32(p, s.tx, s.ty);

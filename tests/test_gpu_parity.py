@@ -182,6 +182,33 @@ def test_scatter_matches_oracle(prec, model, weighted):
         assert np.array_equal(spec, np.round(spec))
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_ll_f32_aligned_and_unaligned_streams_agree(weighted):
+    """The FP32 classical path reads 16-byte-aligned FP32 streams four
+    samples at a time and other streams one at a time; both give the same
+    integer histograms (moments within the FP32 path's partition bar)."""
+    n = 4 * 3001 + 3
+    wl, L, xi = cfg2(n, model=I.MODEL_LL)
+    w = I.rng(9).uniform(0.25, 2.0, n).astype(np.float32) if weighted else None
+    xa, wa = dev(xi, w)
+
+    def shifted(a):                       # same values at a 4-byte offset
+        t = torch.empty(a.numel() + 1, dtype=a.dtype, device=a.device)
+        t[1:] = a
+        return t[1:]
+
+    xu = [None if a is None else shifted(a) for a in xa]
+    wu = None if wa is None else shifted(wa)
+    assert xu[0].data_ptr() % 16 == 4
+    oa = qs_scatter(L, wl.beam, xa, wl.bins, w=wa, precision="f32")
+    ou = qs_scatter(L, wl.beam, xu, wl.bins, w=wu, precision="f32")
+    torch.cuda.synchronize()
+    assert torch.equal(oa.spectrum, ou.spectrum)
+    assert torch.equal(oa.divmap, ou.divmap)
+    assert torch.equal(oa.aeff_hist, ou.aeff_hist)
+    np.testing.assert_allclose(oa.moments.cpu().numpy(), ou.moments.cpu().numpy(), rtol=1e-8)
+
+
 def test_gauss_hermite_tiny_config_f64():
     """32^3 Gauss-Hermite nodes, LL model, 256-bin spectrum, weighted FP64."""
     wl = I.tiny_gauss_hermite()
@@ -286,6 +313,36 @@ def test_zero_and_tiny_weights():
     torch.cuda.synchronize()
     ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi), w.astype(np.float64))
     compare_scatter(out, ref, "f64", float(w.astype(np.float64).sum()))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_weight_fixed_point_rounds_to_nearest_even(prec):
+    """Weights enter the integer histograms as round-to-nearest-even of
+    w 2^bits.  With 4 fraction bits and weights k/64 every quarter (ties
+    included) occurs; the histogram totals equal the host's rounding exactly,
+    and a weight above 2^59 saturates at 2^63 - 1 units."""
+    n = 4096
+    wl, L, xi = cfg2(n, n_phase=16)
+    k = I.rng(12).integers(0, 1 << 16, n)
+    k[:8] = [0, 1, 2, 3, 4, 5, 6, 7]                      # 0, 1/4, 1/2, 3/4, ... of a unit
+    w = (k / 64.0).astype(np.float32)
+    xt, wt = dev(xi, w)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision=prec, weight_frac_bits=4)
+    torch.cuda.synchronize()
+    m = out.moments_dict()
+    expect = np.rint(k / 4.0).sum() / 16.0                 # numpy rint: ties to even
+    total = float(out.spectrum.double().sum()) + m["under"] + m["over"]
+    assert total == expect
+    assert float(out.aeff_hist.double().sum()) <= expect
+    # saturation: one sample carrying 2^60 at 4 fraction bits
+    w1 = np.zeros(n, dtype=np.float32)
+    w1[0] = 2.0 ** 60
+    xt, wt = dev(xi, w1)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision=prec, weight_frac_bits=4)
+    torch.cuda.synchronize()
+    m = out.moments_dict()
+    total = float(out.spectrum.double().sum()) + m["under"] + m["over"]
+    assert total == float((1 << 63) - 1) / 16.0
 
 
 def test_nonfinite_samples_are_excluded_and_counted():
