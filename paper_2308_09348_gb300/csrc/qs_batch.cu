@@ -183,26 +183,26 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
           const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
           SampleF s0, s1;
           eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-          accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+          accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
           if (i1 != i0)
-            accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+            accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
         }
       } else {
         for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
           const auto sm = eval_one<T, false>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
         }
       }
     } else {
       if (p.model == QS_MODEL_QFP) {
         for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
           const auto sm = eval_one<T, true>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
         }
       } else {
         for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
           const auto sm = eval_one<T, false>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nullptr, nspec, 0, 0);
+          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
         }
       }
     }

@@ -660,12 +660,24 @@ __device__ __forceinline__ void acc_slot(const AccF& A, double (&v)[kNumMom]) {
   v[8] = (double)A.nonfinite;
 }
 
-// Fixed-order block reduction of the per-thread accumulators into one
-// moment slot out[0..kNumMom): warp shuffle tree, then warps in order.
-template <typename A>
-__device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double v[kNumMom];
+// Error-free sum of two floats: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (h, l) += (bh, bl) for unevaluated float pairs (relative error ~2^-44).
+__device__ __forceinline__ void pair_add(float& h, float& l, float bh, float bl) {
+  float sm, e;
+  two_sum(h, bh, sm, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(sm, e);
+  l = __fsub_rn(e, __fsub_rn(h, sm));
+}
+
+// Warp tree of the per-thread accumulators, leaving the warp's moment slot
+// in lane 0's v.
+__device__ __forceinline__ void warp_reduce(const AccD& acc, double (&v)[kNumMom]) {
   acc_slot(acc, v);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -676,6 +688,66 @@ __device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* 
 #pragma unroll
     for (int k = 3; k < kNumMom; ++k) v[k] += u[k];
   }
+}
+// FP32 path: the plain sums travel the tree as float pairs, and the energy
+// moments as FP64 sums (W, S1, S2) about the lower lane's shift: merging b
+// into a moves b's sums to a's shift s_a with d = s_b - s_a,
+//   S1 += S1_b + W_b d,   S2 += S2_b + 2 d S1_b + W_b d^2,
+// which needs no division (the FP64 pipe of this GPU issues slowly).
+__device__ __forceinline__ void warp_reduce(const AccF& acc, double (&v)[kNumMom]) {
+  float h[5], l[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) two_sum(acc.s[k + 3], -acc.c[k + 3], h[k], l[k]);
+  float nf = acc.nonfinite;
+  double W = (double)acc.s[0] - (double)acc.c[0];
+  double S1 = (double)acc.s[1] - (double)acc.c[1];
+  double S2 = (double)acc.s[2] - (double)acc.c[2];
+  double sh = W > 0.0 ? (double)acc.shift : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double Wb = __shfl_down_sync(0xffffffffu, W, o);
+    const double S1b = __shfl_down_sync(0xffffffffu, S1, o);
+    const double S2b = __shfl_down_sync(0xffffffffu, S2, o);
+    const double shb = __shfl_down_sync(0xffffffffu, sh, o);
+    if (Wb > 0.0) {
+      if (W > 0.0) {
+        const double d = shb - sh;
+        const double t = __fma_rn(Wb, d, S1b);
+        S2 = S2 + __fma_rn(d, S1b + t, S2b);
+        S1 = S1 + t;
+        W = W + Wb;
+      } else {
+        W = Wb; S1 = S1b; S2 = S2b; sh = shb;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float bh = __shfl_down_sync(0xffffffffu, h[k], o);
+      const float bl = __shfl_down_sync(0xffffffffu, l[k], o);
+      pair_add(h[k], l[k], bh, bl);
+    }
+    nf = __fadd_rn(nf, __shfl_down_sync(0xffffffffu, nf, o));
+  }
+  v[0] = W;
+  v[1] = 0.0;
+  v[2] = 0.0;
+  if (W > 0.0) {
+    const double q = S1 / W;
+    v[1] = sh + q;
+    v[2] = fmax(S2 - S1 * q, 0.0);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k + 3] = (double)h[k] + (double)l[k];
+  v[8] = (double)nf;
+}
+
+// Fixed-order block reduction of the per-thread accumulators into one
+// moment slot out[0..kNumMom): warp shuffle tree, then warps in order.
+template <typename A>
+__device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[kNumMom];
+  warp_reduce(acc, v);
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < kNumMom; ++k) red[warp * kNumMom + k] = v[k];
@@ -694,50 +766,18 @@ __device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* 
   }
 }
 
-// Smoothed-spectrum deposit of one sample (fixed point, like the weighted
-// histograms): S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)).
-// FP64 path in FP64; FP32 path: bin position in FP64, Gaussian weights in
-// FP32 (relative error ~1e-7 per deposit).
-__device__ __forceinline__ void deposit_smooth(const Params& p, double gout, double w,
-                                               unsigned long long* dst) {
-  const double t = (gout - p.lo) * p.inv_w;
-  if (!(t > -1e9 && t < 1e9)) return;
-  int k0, k1;
-  smooth_range(p, t, &k0, &k1);
-  const double wq = w * p.smooth_pref * p.wscale;
-  for (int k = k0; k <= k1; ++k) {
-    const double d = (double)k + 0.5 - t;
-    atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(wq * exp2(-d * d * p.smooth_c)));
-  }
-}
-__device__ __forceinline__ void deposit_smooth_f32(const Params& p, float gh, float gl, float w,
-                                                   unsigned long long* dst) {
-  const float tt = __fmul_rn(__fadd_rn(__fsub_rn(gh, p.f.lo), gl), p.f.inv_w);
-  if (!(tt > -1e9f && tt < 1e9f)) return;
-  int k0, k1;
-  smooth_range_f32(p, tt, &k0, &k1);
-  const float tf = __fsub_rn(tt, (float)k0);            // position relative to bin k0
-  const float wq = __fmul_rn(w, p.f.smooth_pw);
-  const float c = p.f.smooth_c;
-  for (int k = k0; k <= k1; ++k) {
-    const float d = __fsub_rn((float)(k - k0) + 0.5f, tf);
-    const float e = M<float>::ex2(-__fmul_rn(__fmul_rn(d, d), c));
-    atomicAdd(&dst[k], f2u64_rn(__fmul_rn(wq, e)));
-  }
-}
-
 // One evaluated sample into the moment partials and histograms (rows a7-a8).
 template <typename T, typename H, bool SHIST>
-__device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int64_t i, AccD& A,
-                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
-                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+__device__ __forceinline__ bool accumulate(const Params& p, const Sample& s, int64_t i, AccD& A,
+                                           H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,
+                                           int64_t naeff) {
   double* acc = A.a;
   const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
   const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
                   isfinite(w) && w >= 0.0;
   if (!ok) {
     acc[8] += 1.0;
-    return;
+    return false;
   }
   if (isnan(acc[9])) acc[9] = s.mu;                      // the thread's shift
   const double d = s.mu - acc[9];
@@ -768,19 +808,22 @@ __device__ __forceinline__ void accumulate(const Params& p, const Sample& s, int
     if (SHIST) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
-  if (hsm) deposit_smooth(p, s.gout, w, hsm);
+  return true;
 }
 
-template <typename H, bool SHIST>
-__device__ __forceinline__ void accumulate_w(const Params& p, const SampleF& s, float w, AccF& A,
-                                             H* hs, H* hm, H* ha, unsigned long long* hsm,
-                                             int64_t nspec, int64_t nmap, int64_t naeff) {
+// QFP = false drops the terms that vanish in the classical model (V = 0,
+// theta_e = 0, gamma_out = mu): the same sums, with fewer instructions.
+// Returns whether the sample entered the sums (false: counted as excluded).
+template <typename H, bool SHIST, bool QFP = true>
+__device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, float w, AccF& A,
+                                             H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,
+                                             int64_t naeff) {
   const float muf = s.mu_hi;
-  const bool ok = isfinite(muf) && isfinite(s.V) && isfinite(s.go_hi) && isfinite(s.tx) &&
-                  isfinite(w) && w >= 0.f;
+  const bool ok = isfinite(muf) && (!QFP || (isfinite(s.V) && isfinite(s.go_hi))) &&
+                  isfinite(s.tx) && isfinite(w) && w >= 0.f;
   if (!ok) {
     A.nonfinite = __fadd_rn(A.nonfinite, 1.f);
-    return;
+    return false;
   }
   if (isnan(A.shift)) A.shift = muf;                     // the thread's shift
   const float d = __fsub_rn(muf, A.shift);
@@ -788,8 +831,12 @@ __device__ __forceinline__ void accumulate_w(const Params& p, const SampleF& s, 
   kahan(A.s[0], A.c[0], w);
   kahan(A.s[1], A.c[1], wd);
   kahan(A.s[2], A.c[2], __fmul_rn(wd, d));
-  kahan(A.s[3], A.c[3], __fmul_rn(w, s.V));
-  kahan(A.s[4], A.c[4], __fmul_rn(w, __fmaf_rn(s.thx0, s.thx0, __fmul_rn(s.theta_e, s.theta_e))));
+  if (QFP) {
+    kahan(A.s[3], A.c[3], __fmul_rn(w, s.V));
+    kahan(A.s[4], A.c[4], __fmul_rn(w, __fmaf_rn(s.thx0, s.thx0, __fmul_rn(s.theta_e, s.theta_e))));
+  } else {
+    kahan(A.s[4], A.c[4], __fmul_rn(w, __fmul_rn(s.thx0, s.thx0)));
+  }
   kahan(A.s[5], A.c[5], __fmul_rn(w, __fmul_rn(s.thy0, s.thy0)));
   kahan(A.s[6], A.c[6], __fmul_rn(w, s.aeff));
   kahan(A.s[7], A.c[7], __fmul_rn(w, s.g0));
@@ -812,15 +859,87 @@ __device__ __forceinline__ void accumulate_w(const Params& p, const SampleF& s, 
     if (SHIST) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
-  if (hsm) deposit_smooth_f32(p, s.go_hi, s.go_lo, w, hsm);
+  return true;
 }
 
 template <typename T, typename H, bool SHIST>
-__device__ __forceinline__ void accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
-                                           H* hs, H* hm, H* ha, unsigned long long* hsm,
-                                           int64_t nspec, int64_t nmap, int64_t naeff) {
+__device__ __forceinline__ bool accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
+                                           H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,
+                                           int64_t naeff) {
   const float w = p.weighted ? load_t<float>(p.w, i, p.dtype) : 1.f;
-  accumulate_w<H, SHIST>(p, s, w, A, hs, hm, ha, hsm, nspec, nmap, naeff);
+  return accumulate_w<H, SHIST>(p, s, w, A, hs, hm, ha, nspec, nmap, naeff);
+}
+
+// Smoothed-spectrum deposits (fixed point, like the weighted histograms):
+// S_k += w exp(-(k + 1/2 - t)^2 / (2 s^2)) / (s sqrt(2 pi)) over the bins
+// within 6 s of t.  FP64 path in FP64; FP32 path in FP32 (relative error
+// ~1e-7 per deposit).  All 32 lanes call these together (valid = the lane's
+// sample entered the sums): the warp's samples are taken one at a time and
+// the lanes share out that sample's window of bins, so one atomic
+// instruction updates up to 32 consecutive accumulators instead of 32 lanes
+// piling onto the same few bins.  Integer sums do not depend on the order.
+__device__ __forceinline__ void deposit_smooth_warp(const Params& p, bool valid, double gout,
+                                                    double w, unsigned long long* dst) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const double t = (gout - p.lo) * p.inv_w;
+  int k0 = 0, k1 = -1;
+  if (valid && t > -1e9 && t < 1e9) smooth_range(p, t, &k0, &k1);
+  const double wq = w * p.smooth_pref * p.wscale;
+  unsigned m = __ballot_sync(full, k1 >= k0);
+  while (m) {
+    const int j = __ffs(m) - 1;
+    m &= m - 1;
+    const int a0 = __shfl_sync(full, k0, j), a1 = __shfl_sync(full, k1, j);
+    const double tj = __shfl_sync(full, t, j), qj = __shfl_sync(full, wq, j);
+    for (int k = a0 + lane; k <= a1; k += 32) {
+      const double d = (double)k + 0.5 - tj;
+      atomicAdd(&dst[k], (unsigned long long)__double2ll_rn(qj * exp2(-d * d * p.smooth_c)));
+    }
+  }
+}
+__device__ __forceinline__ void deposit_smooth_warp_f32(const Params& p, bool valid, float gh,
+                                                        float gl, float w,
+                                                        unsigned long long* dst) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const float tt = __fmul_rn(__fadd_rn(__fsub_rn(gh, p.f.lo), gl), p.f.inv_w);
+  int k0 = 0, k1 = -1;
+  if (valid && tt > -1e9f && tt < 1e9f) smooth_range_f32(p, tt, &k0, &k1);
+  const float tf = __fsub_rn(tt, (float)k0);            // position relative to bin k0
+  const float wq = __fmul_rn(w, p.f.smooth_pw);
+  const float c = p.f.smooth_c;
+  unsigned m = __ballot_sync(full, k1 >= k0);
+  while (m) {
+    const int j = __ffs(m) - 1;
+    m &= m - 1;
+    const int a0 = __shfl_sync(full, k0, j), a1 = __shfl_sync(full, k1, j);
+    const float fj = __shfl_sync(full, tf, j), qj = __shfl_sync(full, wq, j);
+    for (int k = a0 + lane; k <= a1; k += 32) {
+      const float d = __fsub_rn((float)(k - a0) + 0.5f, fj);
+      const float e = M<float>::ex2(-__fmul_rn(__fmul_rn(d, d), c));
+      const float x = __fmul_rn(qj, e);
+      atomicAdd(&dst[k], x < 4294967296.f ? (unsigned long long)__float2uint_rn(x) : f2u64_rn(x));
+    }
+  }
+}
+// What a deposit needs of a sample: its realised energy.
+struct DepD { double g = 0.0; };
+struct DepF { float gh = 0.f, gl = 0.f; };
+template <typename T> struct DepT;
+template <> struct DepT<double> { using type = DepD; };
+template <> struct DepT<float> { using type = DepF; };
+__device__ __forceinline__ void dep_set(DepD& d, const Sample& s) { d.g = s.gout; }
+__device__ __forceinline__ void dep_set(DepF& d, const SampleF& s) { d.gh = s.go_hi; d.gl = s.go_lo; }
+__device__ __forceinline__ void deposit_warp(const Params& p, bool valid, const DepD& d,
+                                             int64_t i, unsigned long long* dst) {
+  const double w = valid && p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+  deposit_smooth_warp(p, valid, d.g, w, dst);
+}
+__device__ __forceinline__ void deposit_warp(const Params& p, bool valid, const DepF& d,
+                                             int64_t i, unsigned long long* dst) {
+  const float w = valid && p.weighted ? load_t<float>(p.w, i, p.dtype) : 1.f;
+  deposit_smooth_warp_f32(p, valid, d.gh, d.gl, w, dst);
 }
 
 }  // namespace qs

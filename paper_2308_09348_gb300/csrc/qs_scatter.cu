@@ -155,8 +155,15 @@ using namespace detail;
 // K1: fused evaluation + histograms + moment partials.  T: per-sample
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
+// Register budget per thread (blocks of up to 512 threads): FP32 QFP 64
+// (two 256-thread CTAs or more per SM for the MUFU-bound loop), FP32
+// classical 80 (three 256-thread CTAs per SM keep enough loads in flight
+// for the HBM-bound path), FP64 128.
+template <typename T, bool QFP>
+constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : (QFP ? 64 : 80);
+
 template <typename T, typename H, bool QFP, bool SHIST>
-__global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatter(const Params p) {
+__global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t tab_bytes = QFP ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
@@ -186,25 +193,41 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
   typename AccT<T>::type acc;
   acc_init(acc);
 
+  // The loops advance warp by warp (bounds uniform across the lanes), so
+  // that the smoothed deposits can run warp-cooperatively after each step.
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   if constexpr (QFP && sizeof(T) == 4) {
     // FP32 QFP: each thread carries samples 2k and 2k+1 (packed f32x2)
-    for (int64_t k = t0; 2 * k < p.n; k += stride) {
+    for (int64_t kb = t0 - lane; 2 * kb < p.n; kb += stride) {
+      const int64_t k = kb + lane;
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
-      SampleF s0, s1;
-      eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-      accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
-      if (i1 != i0) accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+      DepF d0, d1;
+      bool ok0 = false, ok1 = false;
+      if (i0 < p.n) {
+        SampleF s0, s1;
+        eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+        ok0 = accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
+        if (i1 != i0)
+          ok1 = accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
+        dep_set(d0, s0);
+        dep_set(d1, s1);
+      }
+      if (hsm) {
+        deposit_warp(p, ok0, d0, i0, hsm);
+        deposit_warp(p, ok1, d1, i1, hsm);
+      }
     }
   } else {
     int64_t i = t0;
     if constexpr (!QFP && sizeof(T) == 4) {
       // FP32 classical path (memory-bound): four consecutive samples per
       // thread through 16-byte loads of every stream, when all streams are
-      // FP32 and 16-byte aligned; the remaining samples below.
-      bool vec = p.dtype == QS_F32;
-      for (int k = 0; k < 6; ++k) vec = vec && p.xi[k] && ((uintptr_t)p.xi[k] & 15) == 0;
+      // FP32 and 16-byte aligned and there is no smoothed spectrum; the
+      // remaining samples below.
+      bool vec = p.dtype == QS_F32 && hsm == nullptr;
+      for (int c = 0; c < 6; ++c) vec = vec && p.xi[c] && ((uintptr_t)p.xi[c] & 15) == 0;
       if (p.weighted) vec = vec && ((uintptr_t)p.w & 15) == 0;
       if (vec) {
         const int64_t n4 = p.n >> 2;
@@ -215,20 +238,27 @@ __global__ void __launch_bounds__(512, (QFP && sizeof(T) == 4) ? 2 : 1) k_scatte
           const float4 wv = p.weighted ? __ldg(static_cast<const float4*>(p.w) + k)
                                        : make_float4(1.f, 1.f, 1.f, 1.f);
           const SampleF s0 = eval_ll_f32_xi(p, v[0].x, v[1].x, v[2].x, v[3].x, v[4].x, v[5].x);
-          accumulate_w<H, SHIST>(p, s0, wv.x, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          accumulate_w<H, SHIST, false>(p, s0, wv.x, acc, hs, hm, ha, nspec, nmap, naeff);
           const SampleF s1 = eval_ll_f32_xi(p, v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y);
-          accumulate_w<H, SHIST>(p, s1, wv.y, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          accumulate_w<H, SHIST, false>(p, s1, wv.y, acc, hs, hm, ha, nspec, nmap, naeff);
           const SampleF s2 = eval_ll_f32_xi(p, v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z);
-          accumulate_w<H, SHIST>(p, s2, wv.z, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          accumulate_w<H, SHIST, false>(p, s2, wv.z, acc, hs, hm, ha, nspec, nmap, naeff);
           const SampleF s3 = eval_ll_f32_xi(p, v[0].w, v[1].w, v[2].w, v[3].w, v[4].w, v[5].w);
-          accumulate_w<H, SHIST>(p, s3, wv.w, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+          accumulate_w<H, SHIST, false>(p, s3, wv.w, acc, hs, hm, ha, nspec, nmap, naeff);
         }
         i = 4 * n4 + t0;
       }
     }
-    for (; i < p.n; i += stride) {
-      const auto s = eval_one<T, QFP>(p, tab, i);
-      accumulate<T, H, SHIST>(p, s, i, acc, hs, hm, ha, hsm, nspec, nmap, naeff);
+    for (int64_t ib = i - lane; ib < p.n; ib += stride) {
+      const int64_t ii = ib + lane;
+      typename DepT<T>::type d;
+      bool ok = false;
+      if (ii < p.n) {
+        const auto s = eval_one<T, QFP>(p, tab, ii);
+        ok = accumulate<T, H, SHIST>(p, s, ii, acc, hs, hm, ha, nspec, nmap, naeff);
+        dep_set(d, s);
+      }
+      if (hsm) deposit_warp(p, ok, d, ii, hsm);
     }
   }
   block_reduce_write(acc, red, p.partials + (size_t)blockIdx.x * kNumMom);

@@ -209,6 +209,31 @@ def test_ll_f32_aligned_and_unaligned_streams_agree(weighted):
     np.testing.assert_allclose(oa.moments.cpu().numpy(), ou.moments.cpu().numpy(), rtol=1e-8)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+@pytest.mark.parametrize("sigma", [0.3, 5.5])
+def test_smoothed_spectrum_windows_narrow_and_wider_than_a_warp(prec, model, sigma):
+    """Kernel-smoothed spectrum against the oracle for a window of a few bins
+    and one of 67 bins (more than one pass of 32 lanes), ragged n."""
+    n = 777
+    wl, L, xi = cfg2(n, model=model, n_phase=64)
+    bins = I.Bins(**{**wl.bins.__dict__, "smooth_sigma_bins": sigma})
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, bins, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.smooth_spectrum(L, wl.beam, bins, sigma, f64(xi))
+    S = out.spec_smooth.cpu().numpy()
+    l1 = np.abs(S - ref).sum() / n
+    print(f"[{prec}, model {model}, sigma {sigma}] smoothed L1/W:", l1)
+    # fixed-point rounding: at most half a unit of 2^-32 per deposit; FP32:
+    # a kernel moved by eps bins changes by at most 2 eps / (sigma sqrt(2 pi))
+    # in L1, eps from the path's per-sample bound on gamma_out
+    eps = TOL["f32"]["mu"] * bins.hi * bins.n_bins / (bins.hi - bins.lo)
+    bound = 1e-12 if prec == "f64" else 2 * eps / (sigma * math.sqrt(2 * math.pi))
+    assert l1 <= bound + 13 * sigma * 2.0 ** -32
+    assert abs(S.sum() - ref.sum()) <= 1e-5 * n
+
+
 def test_gauss_hermite_tiny_config_f64():
     """32^3 Gauss-Hermite nodes, LL model, 256-bin spectrum, weighted FP64."""
     wl = I.tiny_gauss_hermite()
