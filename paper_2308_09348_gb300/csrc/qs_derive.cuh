@@ -199,6 +199,8 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   f.smooth_pw = (float)(p.smooth_pref * p.wscale);
   f.smooth_lo = (float)(0.5 + 6.0 * p.smooth_sigma);
   f.smooth_hi = (float)(6.0 * p.smooth_sigma - 0.5);
+  f.smooth_sigma = (float)p.smooth_sigma;
+  f.smooth_pref = (float)p.smooth_pref;
 }
 
 }  // namespace qs

@@ -73,6 +73,7 @@ struct Params {
     float wscale;                  // 2^weight_frac_bits (exact)
     float smooth_pw;               // smooth_pref * wscale
     float smooth_lo, smooth_hi;    // 0.5 + 6 sigma, 6 sigma - 0.5 (bins)
+    float smooth_sigma, smooth_pref;
   } f;
 };
 

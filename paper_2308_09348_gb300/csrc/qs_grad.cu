@@ -126,11 +126,308 @@ __device__ __forceinline__ void qfp_tangent(const Params& p,
   o.du = du; o.V = V; o.du_a = du_a; o.du_g = du_g; o.V_a = V_a; o.V_g = V_g;
 }
 
-// Upstream gradient, reduced to the per-sample coefficients it needs.
+// Packed FP32 version of qfp_tangent for two samples at once (f32x2 FMA-pipe
+// instructions, per-sample MUFU), the same recursion written with explicit
+// fused multiply-adds.
+__device__ __forceinline__ void qfp_tangent_x2(const Params& p, const float4* __restrict__ tab,
+                                               float2 a, float2 g0, QfpTan<float>& o0,
+                                               QfpTan<float>& o1) {
+  const float2 ONE = f2(1.f), HALF = f2(0.5f), THREE = f2(3.f), M2 = f2(-2.f);
+  const float2 LN2 = f2(0.69314718055994530942f);
+  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
+  const float hcK = p.f.h * p.f.cK;
+  const float2 c1 = mul2(mul2(f2(hcK), a), a), c1a = mul2(f2(2.f * hcK), a);
+  const float2 CCHI = f2(p.f.cchi), ca = mul2(CCHI, a);
+  const float2 NG0 = make_float2(-g0.x, -g0.y);
+  float2 du = f2(0.f), V = f2(0.f), gph = HALF, du_a = f2(0.f), du_g = f2(0.f), V_a = f2(0.f),
+         V_g = f2(0.f), gph_a = f2(0.f), gph_g = f2(0.f);
+  const int N = p.n_phase;
+  for (int j = 0; j < N; ++j) {
+    const float4 e = tab[j];
+    const float2 G = make_float2(e.x, e.y), G2 = make_float2(e.z, e.w);
+    const float2 hK = mul2(c1, G2), hK_a = mul2(c1a, G2);
+    const float2 dum = fma2(hK, gph, du);
+    const float2 dum_a = fma2(hK, gph_a, fma2(hK_a, gph, du_a));
+    const float2 dum_g = fma2(hK, gph_g, du_g);
+    const float2 r = rcpx2(fma2(g0, dum, ONE));
+    const float2 mu = mul2(g0, r);
+    const float2 nmur = mul2(NG0, mul2(r, r));                        // -mu r
+    const float2 mu_a = mul2(mul2(nmur, g0), dum_a);
+    const float2 mu_g = fma2(nmur, fma2(g0, dum_g, dum), r);
+    const float2 cg = mul2(ca, G);
+    const float2 chi = mul2(cg, mu);
+    const float2 chi_a = fma2(mul2(CCHI, G), mu, mul2(cg, mu_a));
+    const float2 chi_g = mul2(cg, mu_g);
+    // Gaunt factor and derivatives
+    const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
+    const float2 L1 = mul2(LN2, l1);
+    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));
+    const float2 opc = __fadd2_rn(chi, ONE);
+    const float2 B = fma2(mul2(f2(4.8f), opc), L1, fma2(mul2(f2(2.44f), chi), chi, ONE));
+    const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));
+    const float2 g = mul2(t, t), iB = mul2(g, t), giB = mul2(g, iB);
+    const float2 Bp = fma2(f2(4.8f), L1, fma2(mul2(f2(8.16f), opc), r1, mul2(f2(4.88f), chi)));
+    const float2 Bpp = fma2(fma2(f2(-5.712f), r1, f2(8.16f)), r1, f2(4.88f));
+    const float2 gp = mul2(mul2(f2(-2.f / 3.f), giB), Bp);
+    const float2 gpp =
+        mul2(giB, fma2(mul2(mul2(f2(10.f / 9.f), iB), Bp), Bp, mul2(f2(-2.f / 3.f), Bpp)));
+    const float2 s = fma2(chi, gp, mul2(f2(2.f), g));
+    const float2 s_chi = fma2(chi, gpp, mul2(THREE, gp));
+    // second-moment factor and derivative
+    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
+    const float2 L2 = mul2(LN2, l2);
+    const float2 r2 = ex2x2(make_float2(-l2.x, -l2.y));
+    const float2 o41 = fma2(f2(4.1f), chi, ONE);
+    const float2 B2 = fma2(o41, L2, fma2(mul2(f2(4.75f), chi), chi, ONE));
+    const float2 lb2 = lg2x2(B2);
+    const float2 h2 = ex2x2(mul2(f2(-7.f / 6.f), lb2));
+    const float2 iB2 = ex2x2(make_float2(-lb2.x, -lb2.y));
+    const float2 B2p = fma2(f2(4.1f), L2, fma2(mul2(f2(12.93f), o41), r2, mul2(f2(9.5f), chi)));
+    const float2 h2p = mul2(mul2(mul2(f2(-7.f / 6.f), h2), iB2), B2p);
+    // mean
+    const float2 hKgp = mul2(hK, gp);
+    const float2 du_n = fma2(hK, g, du);
+    const float2 du_a_n = fma2(hKgp, chi_a, fma2(hK_a, g, du_a));
+    const float2 du_g_n = fma2(hKgp, chi_g, du_g);
+    // variance
+    const float2 hKmu = mul2(hK, mu), hKmus = mul2(hKmu, s_chi);
+    const float2 hlam = mul2(mul2(M2, hKmu), s);
+    const float2 hlam_a = mul2(M2, fma2(hKmus, chi_a, mul2(s, fma2(hK_a, mu, mul2(hK, mu_a)))));
+    const float2 hlam_g = mul2(M2, fma2(hKmus, chi_g, mul2(mul2(hK, mu_g), s)));
+    const float2 m2 = mul2(mu, mu), chih2 = mul2(chi, h2), C55m2 = mul2(C55, m2);
+    const float2 hD2 = mul2(mul2(C55m2, hKmu), chih2);
+    const float2 hh = fma2(chi, h2p, h2);
+    const float2 hK3 = mul2(THREE, hK), hKmuh = mul2(hKmu, hh);
+    const float2 hD2_a = mul2(C55m2, fma2(fma2(hK_a, mu, mul2(hK3, mu_a)), chih2, mul2(hKmuh, chi_a)));
+    const float2 hD2_g = mul2(C55m2, fma2(mul2(hK3, mu_g), chih2, mul2(hKmuh, chi_g)));
+    const float2 hr = fma2(hlam, V, hD2);
+    const float2 hr_a = fma2(hlam, V_a, fma2(hlam_a, V, hD2_a));
+    const float2 hr_g = fma2(hlam, V_g, fma2(hlam_g, V, hD2_g));
+    const float2 fac = fma2(HALF, hlam, ONE), hhr = mul2(HALF, hr);
+    V = fma2(hr, fac, V);
+    V_a = fma2(hhr, hlam_a, fma2(hr_a, fac, V_a));
+    V_g = fma2(hhr, hlam_g, fma2(hr_g, fac, V_g));
+    du = du_n; du_a = du_a_n; du_g = du_g_n;
+    gph = mul2(HALF, g);
+    const float2 hgp = mul2(HALF, gp);
+    gph_a = mul2(hgp, chi_a);
+    gph_g = mul2(hgp, chi_g);
+  }
+  o0.du = du.x; o0.V = V.x; o0.du_a = du_a.x; o0.du_g = du_g.x; o0.V_a = V_a.x; o0.V_g = V_g.x;
+  o1.du = du.y; o1.V = V.y; o1.du_a = du_a.y; o1.du_g = du_g.y; o1.V_a = V_a.y; o1.V_g = V_g.y;
+}
+
+// Upstream gradient, reduced to the per-sample coefficients it needs (in
+// the path's arithmetic type).
+template <typename T>
 struct Seeds {
-  double invW, mean, spread, dxr, dyr;        // forward moments
-  double gM, gSp, gDx, gDy, gA, gG0;          // effective dL/d(mean, spread, div_x, div_y, a, g0)
+  T invW, mean, spread, dxr, dyr;             // forward moments
+  T gM, gSp, gDx, gDy, gA, gG0;               // effective dL/d(mean, spread, div_x, div_y, a, g0)
 };
+
+// A sample's decode and focus with the derivatives of ln a (rows a1-a3).
+template <typename T>
+struct GFront {
+  T w, xi3, xi4, xi5, gamma0, a, a_over_a0;
+  T dla_w0, dla_dx, dla_dy, dla_thx, dla_thy, dla_del, thx, thy;
+  bool ok, clamped;
+};
+
+template <typename T>
+__device__ __forceinline__ void grad_front(const Params& p, int64_t i, T w0, GFront<T>& f) {
+  const T xi0 = load_t<T>(p.xi[0], i, p.dtype), xi1 = load_t<T>(p.xi[1], i, p.dtype);
+  const T xi2 = load_t<T>(p.xi[2], i, p.dtype);
+  f.xi3 = load_t<T>(p.xi[3], i, p.dtype);
+  f.xi4 = load_t<T>(p.xi[4], i, p.dtype);
+  f.xi5 = load_t<T>(p.xi[5], i, p.dtype);
+  f.w = p.weighted ? load_t<T>(p.w, i, p.dtype) : (T)1;
+  f.ok = f.w >= (T)0 && isfinite(f.w);
+  const T x = QS_PV(T, bdx) + QS_PV(T, sx) * xi0;
+  const T y = QS_PV(T, bdy) + QS_PV(T, sy) * xi1;
+  const T z = QS_PV(T, sz) * xi2;
+  T gamma0 = p.flat ? QS_PV(T, glo) + QS_PV(T, gspan) * f.xi3
+                    : QS_PV(T, gmean) * ((T)1 + QS_PV(T, spread) * f.xi3);
+  f.clamped = gamma0 < (T)1;
+  if (f.clamped) gamma0 = (T)1;
+  f.gamma0 = gamma0;
+  const T thx = QS_PV(T, div) * f.xi4, thy = QS_PV(T, div) * f.xi5;
+  f.thx = thx;
+  f.thy = thy;
+  const T cdel = QS_PV(T, c_delay);
+  const T ct = (T)0.5 * (z + cdel);
+  const T zs = (T)0.5 * (z - cdel);
+  const T xs = x + thx * ct - QS_PV(T, ldx);
+  const T ys = y + thy * ct - QS_PV(T, ldy);
+  const T rho2 = xs * xs + ys * ys;
+  const T izR = QS_PV(T, inv_zR), iw2 = QS_PV(T, inv_w0sq);
+  const T zq = zs * izR;
+  const T q = (T)1 + zq * zq;
+  const T rq = M<T>::rcp(q);
+  const T E = rho2 * iw2 * rq;                         // a = a0 q^-1/2 exp(-E)
+  if (sizeof(T) == 4)
+    f.a_over_a0 = M<T>::rsqrt(q) * M<T>::ex2(-(T)1.4426950408889634074 * E);
+  else
+    f.a_over_a0 = M<T>::rsqrt(q) * (T)exp(-(double)E);
+  f.a = QS_PV(T, a0) * f.a_over_a0;
+  // d ln a / d(parameter)
+  const T k2 = (T)2 * iw2 * rq;                        // 2 / (W0^2 q)
+  f.dla_dx = k2 * xs;
+  f.dla_dy = k2 * ys;
+  f.dla_thx = -k2 * xs * ct;
+  f.dla_thy = -k2 * ys * ct;
+  const T cc = (T)0.299792458;
+  const T dq_del = -cc * zq * izR;                     // dq/d delay
+  const T drho_del = cc * (xs * thx + ys * thy);       // d rho^2 / d delay
+  f.dla_del = (E - (T)0.5) * dq_del * rq - drho_del * iw2 * rq;
+  const T dq_w0 = (T)-4 * zq * zq / w0;                // dq/dW0 (z_R ~ W0^2)
+  f.dla_w0 = (T)-0.5 * dq_w0 * rq + E * ((T)2 / w0 + dq_w0 * rq);
+}
+
+// Per-thread gradient partials: FP64 sums (FP64 path), compensated FP32
+// sums (FP32 path).
+template <typename T> struct GAcc;
+template <> struct GAcc<double> {
+  double s[kNumGrad];
+  __device__ __forceinline__ void init() {
+    for (int k = 0; k < kNumGrad; ++k) s[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
+  __device__ __forceinline__ double get(int k) const { return s[k]; }
+};
+template <> struct GAcc<float> {
+  float s[kNumGrad], c[kNumGrad];
+  __device__ __forceinline__ void init() {
+    for (int k = 0; k < kNumGrad; ++k) s[k] = c[k] = 0.f;
+  }
+  __device__ __forceinline__ void add(int k, float x) { kahan(s[k], c[k], x); }
+  __device__ __forceinline__ double get(int k) const { return (double)s[k] - (double)c[k]; }
+};
+
+// The model with its tangents, the sample's outputs, its share of dL/d(outputs)
+// (adjoint of rows a8-a9) and the chain rule to the parameters (rows a4-a6).
+// dLdS: upstream gradient of the smoothed spectrum (NULL: none).
+template <typename T, bool QFP, typename S>
+__device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
+                                          const S* __restrict__ dLdS, int64_t i,
+                                          const GFront<T>& f, const QfpTan<T>& o, GAcc<T>& acc) {
+  const T g0 = f.gamma0, a = f.a;
+  T mu, V = 0, mu_a, mu_g, V_a = 0, V_g = 0;
+  if (!QFP) {
+    mu = g0 / ((T)1 + QS_PV(T, cRR) * g0 * a * a);
+    mu_a = -mu * mu * (T)2 * QS_PV(T, cRR) * a;
+    mu_g = mu * mu / (g0 * g0);
+  } else {
+    mu = g0 / ((T)1 + g0 * o.du);
+    mu_a = -mu * mu * o.du_a;
+    mu_g = mu * mu * ((T)1 / (g0 * g0) - o.du_g);
+    V = o.V;
+    V_a = o.V_a;
+    V_g = o.V_g;
+  }
+  if (!isfinite(mu) || !isfinite(V)) return;
+  // outputs of the sample (row a6)
+  T theta_e = 0, gout = mu, sv = 0;
+  const T xi7 = QFP ? load_t<T>(p.xi[7], i, p.dtype) : (T)0;
+  if (QFP && V > (T)0) {
+    sv = sqrt(V);
+    theta_e = QS_PV(T, kappa_s) * a * sv / (mu * mu);
+    gout = mu + sv * xi7;
+  }
+  // sample's share of dL/d(outputs)
+  const T wn = f.w * sd.invW;
+  T g_out = 0;                                          // dL/d gamma_out
+  if (dLdS != nullptr) {
+    const T tt = (gout - QS_PV(T, lo)) * QS_PV(T, inv_w);
+    if (tt > (T)-1e9 && tt < (T)1e9) {
+      int k0, k1;
+      T c;
+      if constexpr (sizeof(T) == 4) {
+        smooth_range_f32(p, tt, &k0, &k1);
+        c = p.f.smooth_c;
+      } else {
+        smooth_range(p, tt, &k0, &k1);
+        c = p.smooth_c;
+      }
+      const T tf = tt - (T)k0;
+      for (int k = k0; k <= k1; ++k) {
+        const T d = (T)(k - k0) + (T)0.5 - tf;
+        T e;
+        if constexpr (sizeof(T) == 4) e = M<float>::ex2(-(d * d) * c);
+        else e = exp2(-d * d * c);
+        g_out += (T)dLdS[k] * e * d;
+      }
+      const T sg = QS_PV(T, smooth_sigma);
+      g_out *= f.w * QS_PV(T, smooth_pref) * QS_PV(T, inv_w) / (sg * sg);
+    }
+  }
+  T g_mu = sd.gM * wn + g_out;
+  if (sd.spread > (T)0) g_mu += sd.gSp * wn * (mu - sd.mean) / sd.spread;
+  T g_V = (sd.spread > (T)0 ? sd.gSp * wn * (T)0.5 / sd.spread : (T)0);
+  if (QFP && V > (T)0) g_V += g_out * xi7 * (T)0.5 / sv;
+  const T g_te = sd.gDx * wn * theta_e * sd.dxr;
+  const T g_thx = sd.gDx * wn * f.thx * sd.dxr;
+  const T g_thy = sd.gDy * wn * f.thy * sd.dyr;
+  T g_a = sd.gA * wn;
+  T g_g0 = sd.gG0 * wn;
+  // theta_e = kappa_s a sqrt(V) / mu^2
+  if (QFP && V > (T)0) {
+    const T ks = QS_PV(T, kappa_s);
+    g_a += g_te * ks * sv / (mu * mu);
+    g_V += g_te * ks * a * (T)0.5 / (sv * mu * mu);
+    g_mu += g_te * ((T)-2 * theta_e / mu);
+  }
+  // (mu, V) = F(a, gamma0)
+  g_a += g_mu * mu_a + g_V * V_a;
+  g_g0 += g_mu * mu_g + g_V * V_g;
+  // chain to the parameters
+  const T ga = g_a * a;                                 // dL/d ln a
+  acc.add(QS_G_A0, QS_PV(T, a0) > (T)0 ? g_a * f.a_over_a0 : (T)0);
+  acc.add(QS_G_W0, ga * f.dla_w0);
+  acc.add(QS_G_DX, ga * f.dla_dx);
+  acc.add(QS_G_DY, ga * f.dla_dy);
+  acc.add(QS_G_DELAY, ga * f.dla_del);
+  if (!p.flat && !f.clamped) {
+    acc.add(QS_G_GAMMA, g_g0 * ((T)1 + QS_PV(T, spread) * f.xi3));
+    acc.add(QS_G_SPREAD, g_g0 * QS_PV(T, gmean) * f.xi3);
+  }
+  acc.add(QS_G_DIV, (g_thx + ga * f.dla_thx) * f.xi4 + (g_thy + ga * f.dla_thy) * f.xi5);
+}
+
+// The kernel's sample loop: FP32 QFP takes two samples per thread through
+// the packed tangent integration, the other paths one.
+template <typename T, bool QFP, typename S>
+__device__ __forceinline__ void grad_loop(const Params& p,
+                                          const typename Tab<T>::type* __restrict__ tab,
+                                          const Seeds<T>& sd, const S* dS, T w0, GAcc<T>& acc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (QFP && sizeof(T) == 4) {
+    for (int64_t k = t0; 2 * k < p.n; k += stride) {
+      const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+      GFront<T> f0, f1;
+      grad_front<T>(p, i0, w0, f0);
+      grad_front<T>(p, i1, w0, f1);
+      QfpTan<T> o0, o1;
+      qfp_tangent_x2(p, reinterpret_cast<const float4*>(tab), make_float2(f0.a, f1.a),
+                     make_float2(f0.gamma0, f1.gamma0), o0, o1);
+      if (f0.ok) grad_back<T, QFP, S>(p, sd, dS, i0, f0, o0, acc);
+      if (i1 != i0 && f1.ok) grad_back<T, QFP, S>(p, sd, dS, i1, f1, o1, acc);
+    }
+  } else {
+    for (int64_t i = t0; i < p.n; i += stride) {
+      GFront<T> f;
+      grad_front<T>(p, i, w0, f);
+      if (!f.ok) continue;
+      QfpTan<T> o{};
+      if (QFP) qfp_tangent<T>(p, tab, f.a, f.gamma0, o);
+      grad_back<T, QFP, S>(p, sd, dS, i, f, o, acc);
+    }
+  }
+}
+
+// Largest smoothed spectrum whose upstream gradient is staged in shared
+// memory (FP32 path); larger ones are read from global memory.
+constexpr int kGradStageBins = 8192;
 
 template <typename T, bool QFP>
 __global__ void __launch_bounds__(256) k_grad(const Params p, const qs_moments* __restrict__ mom,
@@ -141,172 +438,49 @@ __global__ void __launch_bounds__(256) k_grad(const Params p, const qs_moments* 
   TT* tab = reinterpret_cast<TT*>(smem);
   const size_t tab_bytes = QFP ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
   double* red = reinterpret_cast<double*>(smem + tab_bytes);
+  T* sdS = reinterpret_cast<T*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumGrad * sizeof(double));
   if (QFP)
     for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  // FP32 path: the upstream gradient of the smoothed spectrum staged in
+  // shared memory as floats when it is small
+  const bool smooth = dLdS != nullptr && p.smooth_sigma > 0.0;
+  if (smooth && sizeof(T) == 4 && p.n_bins <= kGradStageBins)
+    for (int k = threadIdx.x; k < p.n_bins; k += blockDim.x) sdS[k] = (T)dLdS[k];
 
   // effective upstream coefficients (rel_spread = spread/mean,
   // div = sqrt(div_x^2 + div_y^2) folded into mean, spread, div_x, div_y)
-  Seeds sd;
+  Seeds<T> sd;
   {
-    const double W = mom->W;
-    sd.invW = W > 0.0 ? 1.0 / W : 0.0;
-    sd.mean = mom->mean;
-    sd.spread = mom->spread;
+    const double W = mom->W, mean = mom->mean, spread = mom->spread;
     const double Dx = mom->div_x, Dy = mom->div_y, D = mom->div;
     const double d1 = dLdm[1], d2 = dLdm[2], d3 = dLdm[3], d4 = dLdm[4], d5 = dLdm[5],
                  d6 = dLdm[6];
-    sd.gM = d1 - (sd.mean != 0.0 ? d3 * sd.spread / (sd.mean * sd.mean) : 0.0);
-    sd.gSp = d2 + (sd.mean != 0.0 ? d3 / sd.mean : 0.0);
-    sd.gDx = d4 + (D > 0.0 ? d6 * Dx / D : 0.0);
-    sd.gDy = d5 + (D > 0.0 ? d6 * Dy / D : 0.0);
-    sd.dxr = Dx > 0.0 ? 1.0 / Dx : 0.0;
-    sd.dyr = Dy > 0.0 ? 1.0 / Dy : 0.0;
-    sd.gA = dLdm[7];
-    sd.gG0 = dLdm[11];
+    sd.invW = (T)(W > 0.0 ? 1.0 / W : 0.0);
+    sd.mean = (T)mean;
+    sd.spread = (T)spread;
+    sd.gM = (T)(d1 - (mean != 0.0 ? d3 * spread / (mean * mean) : 0.0));
+    sd.gSp = (T)(d2 + (mean != 0.0 ? d3 / mean : 0.0));
+    sd.gDx = (T)(d4 + (D > 0.0 ? d6 * Dx / D : 0.0));
+    sd.gDy = (T)(d5 + (D > 0.0 ? d6 * Dy / D : 0.0));
+    sd.dxr = (T)(Dx > 0.0 ? 1.0 / Dx : 0.0);
+    sd.dyr = (T)(Dy > 0.0 ? 1.0 / Dy : 0.0);
+    sd.gA = (T)dLdm[7];
+    sd.gG0 = (T)dLdm[11];
   }
+  const T w0 = (T)sqrt(1.0 / p.inv_w0sq);
   __syncthreads();
 
-  double acc[kNumGrad];
-#pragma unroll
-  for (int k = 0; k < kNumGrad; ++k) acc[k] = 0.0;
-
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-    // ---- decode and focus with derivatives (rows a1-a3) ----
-    const double xi0 = load_elem(p.xi[0], i, p.dtype), xi1 = load_elem(p.xi[1], i, p.dtype);
-    const double xi2 = load_elem(p.xi[2], i, p.dtype), xi3 = load_elem(p.xi[3], i, p.dtype);
-    const double xi4 = load_elem(p.xi[4], i, p.dtype), xi5 = load_elem(p.xi[5], i, p.dtype);
-    const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
-    if (!(w >= 0.0) || !isfinite(w)) continue;
-    const T x = (T)p.bdx + (T)p.sx * (T)xi0;
-    const T y = (T)p.bdy + (T)p.sy * (T)xi1;
-    const T z = (T)p.sz * (T)xi2;
-    double gamma0 = p.flat ? p.glo + p.gspan * xi3 : p.gmean * (1.0 + p.spread * xi3);
-    const bool clamped = gamma0 < 1.0;
-    if (clamped) gamma0 = 1.0;
-    const T thx = (T)p.div * (T)xi4, thy = (T)p.div * (T)xi5;
-    const T ct = (T)0.5 * (z + (T)p.c_delay);
-    const T zs = (T)0.5 * (z - (T)p.c_delay);
-    const T xs = x + thx * ct - (T)p.ldx;
-    const T ys = y + thy * ct - (T)p.ldy;
-    const T rho2 = xs * xs + ys * ys;
-    const T zq = zs * (T)p.inv_zR;
-    const T q = (T)1 + zq * zq;
-    const T rq = M<T>::rcp(q);
-    const T E = rho2 * (T)p.inv_w0sq * rq;              // a = a0 q^-1/2 exp(-E)
-    T a_over_a0;
-    if (sizeof(T) == 4)
-      a_over_a0 = M<T>::rsqrt(q) * M<T>::ex2(-(T)1.4426950408889634074 * E);
-    else
-      a_over_a0 = M<T>::rsqrt(q) * (T)exp(-(double)E);
-    const T a = (T)p.a0 * a_over_a0;
-    // d ln a / d(parameter)
-    const T w0 = (T)sqrt(1.0 / p.inv_w0sq);
-    const T k2 = (T)2 * (T)p.inv_w0sq * rq;             // 2 / (W0^2 q)
-    const T dla_dx = k2 * xs, dla_dy = k2 * ys;
-    const T dla_thx = -k2 * xs * ct, dla_thy = -k2 * ys * ct;
-    const T cc = (T)0.299792458;
-    const T dq_del = -cc * zq * (T)p.inv_zR;             // dq/d delay
-    const T drho_del = cc * (xs * thx + ys * thy);       // d rho^2 / d delay
-    const T dla_del = (E - (T)0.5) * dq_del * rq - drho_del * (T)p.inv_w0sq * rq;
-    const T dq_w0 = (T)-4 * zq * zq / w0;                // dq/dW0 (z_R ~ W0^2)
-    const T dla_w0 = (T)-0.5 * dq_w0 * rq + E * ((T)2 / w0 + dq_w0 * rq);
-
-    // ---- model with tangents (rows a4-a5) ----
-    double mu, V = 0.0, mu_a, mu_g, V_a = 0.0, V_g = 0.0;
-    if (!QFP) {
-      const double ad = (double)a;
-      mu = gamma0 / (1.0 + p.cRR * gamma0 * ad * ad);
-      mu_a = -mu * mu * 2.0 * p.cRR * ad;
-      mu_g = mu * mu / (gamma0 * gamma0);
-    } else {
-      QfpTan<T> o;
-      qfp_tangent<T>(p, tab, a, (T)gamma0, o);
-      mu = gamma0 / (1.0 + gamma0 * (double)o.du);
-      mu_a = -mu * mu * (double)o.du_a;
-      mu_g = mu * mu * (1.0 / (gamma0 * gamma0) - (double)o.du_g);
-      V = (double)o.V;
-      V_a = (double)o.V_a;
-      V_g = (double)o.V_g;
-    }
-    if (!isfinite(mu) || !isfinite(V)) continue;
-    // ---- outputs of the sample (row a6) ----
-    const double ad = (double)a;
-    double theta_e = 0.0, gout = mu, sv = 0.0;
-    const double xi7 = QFP ? load_elem(p.xi[7], i, p.dtype) : 0.0;
-    if (QFP && V > 0.0) {
-      sv = sqrt(V);
-      theta_e = p.kappa_s * ad * sv / (mu * mu);
-      gout = mu + sv * xi7;
-    }
-    const double thx0 = (double)thx, thy0 = (double)thy;
-
-    // ---- sample's share of dL/d(outputs) (adjoint of rows a8-a9) ----
-    const double wn = w * sd.invW;
-    double g_out = 0.0;                                   // dL/d gamma_out
-    if (dLdS != nullptr && p.smooth_sigma > 0.0) {
-      const double tt = (gout - p.lo) * p.inv_w;
-      if (tt > -1e9 && tt < 1e9) {
-        int k0, k1;
-        smooth_range(p, tt, &k0, &k1);
-        const double sg2 = p.smooth_sigma * p.smooth_sigma;
-        if (sizeof(T) == 4) {
-          // FP32 path: Gaussian weights in FP32 (as in the forward deposit)
-          const float tf = (float)(tt - (double)k0);
-          const float c = (float)p.smooth_c;
-          float ga = 0.f;
-          for (int k = k0; k <= k1; ++k) {
-            const float d = (float)(k - k0) + 0.5f - tf;
-            ga = fmaf((float)dLdS[k] * M<float>::ex2(-(d * d) * c), d, ga);
-          }
-          g_out = (double)ga;
-        } else {
-          for (int k = k0; k <= k1; ++k) {
-            const double d = (double)k + 0.5 - tt;
-            g_out += dLdS[k] * exp2(-d * d * p.smooth_c) * d;
-          }
-        }
-        g_out *= w * p.smooth_pref * p.inv_w / sg2;
-      }
-    }
-    double g_mu = sd.gM * wn + g_out;
-    if (sd.spread > 0.0) g_mu += sd.gSp * wn * (mu - sd.mean) / sd.spread;
-    double g_V = (sd.spread > 0.0 ? sd.gSp * wn * 0.5 / sd.spread : 0.0);
-    if (QFP && V > 0.0) g_V += g_out * xi7 * 0.5 / sv;
-    const double g_te = sd.gDx * wn * theta_e * sd.dxr;
-    double g_thx = sd.gDx * wn * thx0 * sd.dxr;
-    double g_thy = sd.gDy * wn * thy0 * sd.dyr;
-    double g_a = sd.gA * wn;
-    double g_g0 = sd.gG0 * wn;
-    // theta_e = kappa_s a sqrt(V) / mu^2
-    if (QFP && V > 0.0) {
-      g_a += g_te * p.kappa_s * sv / (mu * mu);
-      g_V += g_te * p.kappa_s * ad * 0.5 / (sv * mu * mu);
-      g_mu += g_te * (-2.0 * theta_e / mu);
-    }
-    // (mu, V) = F(a, gamma0)
-    g_a += g_mu * mu_a + g_V * V_a;
-    g_g0 += g_mu * mu_g + g_V * V_g;
-
-    // ---- chain to the parameters ----
-    const double ga = g_a * ad;                           // dL/d ln a
-    acc[QS_G_A0] += p.a0 > 0.0 ? g_a * (double)a_over_a0 : 0.0;
-    acc[QS_G_W0] += ga * (double)dla_w0;
-    acc[QS_G_DX] += ga * (double)dla_dx;
-    acc[QS_G_DY] += ga * (double)dla_dy;
-    acc[QS_G_DELAY] += ga * (double)dla_del;
-    if (!p.flat && !clamped) {
-      acc[QS_G_GAMMA] += g_g0 * (1.0 + p.spread * xi3);
-      acc[QS_G_SPREAD] += g_g0 * p.gmean * xi3;
-    }
-    acc[QS_G_DIV] += (g_thx + ga * (double)dla_thx) * xi4 + (g_thy + ga * (double)dla_thy) * xi5;
-  }
+  GAcc<T> acc;
+  acc.init();
+  if (!smooth) grad_loop<T, QFP, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc);
+  else if (sizeof(T) == 4 && p.n_bins <= kGradStageBins) grad_loop<T, QFP, T>(p, tab, sd, sdS, w0, acc);
+  else grad_loop<T, QFP, double>(p, tab, sd, dLdS, w0, acc);
 
   // fixed-order block reduction into this CTA's slot
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kNumGrad; ++k) {
-    double v = acc[k];
+    double v = acc.get(k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp * kNumGrad + k] = v;
@@ -345,7 +519,10 @@ int32_t launch_grad(const Params& p, int block, int sms, int grid_req, int gmax,
                     cudaStream_t st, int* grid_out) {
   using TT = typename Tab<T>::type;
   const size_t tab = QFP ? align_up((size_t)p.n_phase * sizeof(TT), 16) : 0;
-  const size_t smem = tab + (size_t)(block / 32) * kNumGrad * sizeof(double);
+  const bool stage = sizeof(T) == 4 && dLdS != nullptr && p.smooth_sigma > 0.0 &&
+                     p.n_bins <= kGradStageBins;
+  const size_t smem = tab + (size_t)(block / 32) * kNumGrad * sizeof(double) +
+                      (stage ? (size_t)p.n_bins * sizeof(float) : 0);
   auto kern = k_grad<T, QFP>;
   static bool attr[64] = {};
   int dev = 0;
