@@ -43,7 +43,7 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"cb4af76aae387b1f": 8 * (268.75e6 + 4.39e6)}
+TRAFFIC_BY_SOURCE = {"fa82680b2c452c00": 8 * (269.90e6 + 3.74e6)}
 
 
 def parse():
