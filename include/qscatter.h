@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 3
+#define QS_VERSION 4
 
 typedef enum {
     QS_OK = 0,
@@ -52,6 +52,7 @@ typedef enum {
 
 typedef enum { QS_ENV_GAUSS = 0, QS_ENV_SIN2 = 1 } qs_envelope;
 typedef enum { QS_MODEL_LL = 0, QS_MODEL_QFP = 1 } qs_model;
+typedef enum { QS_FOCUS_CROSSING = 0, QS_FOCUS_PER_CELL = 1 } qs_focus;
 typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
 
 /*
@@ -69,12 +70,28 @@ typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
  *                  QS_ENV_SIN2: field envelope sin^2(pi phi/Phi_T) on
  *                  [0, Phi_T], Phi_T chosen so the intensity FWHM is Phi
  *   model          QS_MODEL_LL (Eq. 3) or QS_MODEL_QFP (Eq. 6 + FP closure)
- *   n_phase        phase cells of the QFP integration, 1..4096 (ignored by LL)
+ *   n_phase        phase cells of the integration, 1..4096 (ignored by LL
+ *                  with QS_FOCUS_CROSSING)
+ *   focus          QS_FOCUS_CROSSING: Eq. 2 evaluated once, where the
+ *                  electron crosses the pulse peak (the paper neglects the
+ *                  focus variation during the crossing, Sec. 2);
+ *                  QS_FOCUS_PER_CELL: Eq. 2 evaluated in every phase cell
+ *                  at the electron's position there.  In cell j at phase
+ *                  phi_j (0 at the crossing) the electron has moved by
+ *                  s_j = phi_j/(2k) along -z (it meets the counter-moving
+ *                  phase at twice the frequency), so z_j = z* - s_j and the
+ *                  transverse offsets grow by theta s_j; the local peak is
+ *                  a_j = a0 q_j^-1/2 exp(-rho_j^2/(W0^2 q_j)) and the field
+ *                  envelope A_j = a_j G(phi_j).  LL then integrates Eq. 3's
+ *                  exponent cell by cell: 1/gamma_f = 1/gamma0 +
+ *                  (2/3) R_c h sum_j A_j^2.  a_eff (its histogram, its
+ *                  moment and Eq. 8) stays the value at the crossing.
+ *                  The gradient entry point supports QS_FOCUS_CROSSING only.
  */
 typedef struct qs_laser {
     double lambda_um, a0, w0_um, tau_fs;
     double dx_um, dy_um, delay_fs, div_prefactor;
-    int32_t envelope, model, n_phase, reserved;
+    int32_t envelope, model, n_phase, focus;
 } qs_laser;
 
 /*

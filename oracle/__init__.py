@@ -42,7 +42,7 @@ class QsoLaser(C.Structure):
                 ("tau_fs", C.c_double), ("dx_um", C.c_double), ("dy_um", C.c_double),
                 ("delay_fs", C.c_double), ("div_prefactor", C.c_double),
                 ("envelope", C.c_int32), ("model", C.c_int32), ("n_phase", C.c_int32),
-                ("pad", C.c_int32)]
+                ("focus", C.c_int32)]
 
 
 class QsoBeam(C.Structure):
@@ -110,7 +110,8 @@ def lib():
 
 def _laser(p) -> QsoLaser:
     return QsoLaser(p.lambda_um, p.a0, p.w0_um, p.tau_fs, p.dx_um, p.dy_um, p.delay_fs,
-                    p.div_prefactor, int(p.envelope), int(p.model), int(p.n_phase), 0)
+                    p.div_prefactor, int(p.envelope), int(p.model), int(p.n_phase),
+                    int(getattr(p, "focus", 0)))
 
 
 def _beam(b) -> QsoBeam:

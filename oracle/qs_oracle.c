@@ -25,6 +25,9 @@
  *                        transport closed form; library ODE solve)
  *   qso_eval / qso_scatter  pinned (Table 1 / Table 2 closed forms,
  *                        zero intensity, weight conservation, symmetries)
+ *   per-cell focus       pinned (adaptive quadrature of Eq. 3's exponent
+ *                        along the electron's path; reduces to the crossing
+ *                        focus for a straight path in a long focus)
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,8 +57,8 @@ typedef struct {
     double div_prefactor;  /* kappa multiplying Eq. 8                      */
     int32_t envelope;      /* 0 = Gaussian, 1 = sin^2 (field envelope)     */
     int32_t model;         /* 0 = classical LL (Eq. 3), 1 = quantum FP     */
-    int32_t n_phase;       /* phase steps of the quantum model             */
-    int32_t pad;
+    int32_t n_phase;       /* phase cells of the integration               */
+    int32_t focus;         /* 0 = Eq. 2 at the crossing, 1 = in every cell */
 } qso_laser;
 
 typedef struct {
@@ -243,8 +246,11 @@ void qso_qfp_rates(const qso_laser* L, double mu, double A, double aS_scale, dou
  *   V_{j+1}  = V_j + h r + (h^2/2) lambda r (frozen-rate Taylor step)
  * aS_scale multiplies a_S; d2_scale multiplies D2 (0 = no diffusion).
  * ------------------------------------------------------------------------ */
-void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0,
-                       double aS_scale, double d2_scale, double* mu_out, double* V_out) {
+/* a_cell[j] (NULL: aeff in every cell) is the local peak amplitude of the
+   focus in cell j (the per-cell focus variant). */
+static void qso_qfp_run(const qso_laser* L, const double* a_cell, double aeff, double gamma0,
+                        double V0, double aS_scale, double d2_scale, double* mu_out,
+                        double* V_out) {
     int N = L->n_phase;
     double c[10];
     qso_constants(L, c);
@@ -252,7 +258,7 @@ void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0
     double du = 0.0, V = V0, g_prev = 1.0;
     for (int j = 0; j < N; ++j) {
         double phi = c[7] + ((double)j + 0.5) * h;   /* midpoint of cell j */
-        double A = aeff * qso_envelope(L, c, phi);
+        double A = (a_cell ? a_cell[j] : aeff) * qso_envelope(L, c, phi);
         double K = (2.0 / 3.0) * c[3] * A * A;
         double du_mid = du + 0.5 * h * K * g_prev;
         double mu = gamma0 / (1.0 + gamma0 * du_mid);
@@ -268,6 +274,48 @@ void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0
     }
     *mu_out = gamma0 / (1.0 + gamma0 * du);
     *V_out = V;
+}
+
+void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0,
+                       double aS_scale, double d2_scale, double* mu_out, double* V_out) {
+    qso_qfp_run(L, NULL, aeff, gamma0, V0, aS_scale, d2_scale, mu_out, V_out);
+}
+
+/* ------------------------------------------------------------------------
+ * Local Gaussian focus, Eq. 2, at longitudinal position zz and transverse
+ * offsets (xx, yy) from the laser axis.
+ * ------------------------------------------------------------------------ */
+static double qso_focus(const qso_laser* L, double zR, double zz, double xx, double yy) {
+    double q = 1.0 + (zz / zR) * (zz / zR);
+    return L->a0 / sqrt(q) * exp(-(xx * xx + yy * yy) / (L->w0_um * L->w0_um * q));
+}
+
+/* Phase of the pulse peak on the envelope's phase axis. */
+static double qso_peak_phase(const qso_laser* L, const double* c) {
+    return L->envelope == 0 ? 0.0 : 0.5 * c[6];
+}
+
+/* ------------------------------------------------------------------------
+ * Per-cell focus (the variant of Eq. 2 without the paper's neglect of the
+ * focus change during the crossing).  The electron (velocity
+ * c(theta_x, theta_y, -1)) meets the counter-propagating phase at twice the
+ * laser frequency, so between the crossing of the pulse peak and the
+ * midpoint of cell j (phase phi_j, the peak at phi_c) it travels
+ * s_j = (phi_j - phi_c)/(2k) along -z and theta s_j sideways:
+ *   z_j = z* - s_j,  x_j = xs + theta_x s_j,  y_j = ys + theta_y s_j,
+ *   a_j = Eq. 2 at (z_j, x_j, y_j).
+ * ------------------------------------------------------------------------ */
+static void qso_focus_cells(const qso_laser* L, double zs, double xs, double ys, double thx,
+                            double thy, double* a_cell) {
+    double c[10];
+    qso_constants(L, c);
+    int N = L->n_phase;
+    double h = (c[8] - c[7]) / (double)N, phic = qso_peak_phase(L, c);
+    for (int j = 0; j < N; ++j) {
+        double phi = c[7] + ((double)j + 0.5) * h;
+        double sj = (phi - phic) / (2.0 * c[0]);
+        a_cell[j] = qso_focus(L, c[2], zs - sj, xs + thx * sj, ys + thy * sj);
+    }
 }
 
 /* ------------------------------------------------------------------------
@@ -312,12 +360,33 @@ static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bin
     double aeff = L->a0 / sqrt(q) * exp(-rho2 / (L->w0_um * L->w0_um * q));
 
     double mu, V;
-    if (L->model == 0) {
-        /* classical LL closed form, Eq. 3 with a0 -> a_eff */
-        mu = gamma0 / (1.0 + cRR * gamma0 * aeff * aeff);
-        V = 0.0;
+    if (!L->focus) {
+        if (L->model == 0) {
+            /* classical LL closed form, Eq. 3 with a0 -> a_eff */
+            mu = gamma0 / (1.0 + cRR * gamma0 * aeff * aeff);
+            V = 0.0;
+        } else {
+            qso_qfp_integrate(L, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+        }
     } else {
-        qso_qfp_integrate(L, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+        double* a_cell = (double*)malloc(sizeof(double) * (size_t)L->n_phase);
+        qso_focus_cells(L, zs, xs, ys, thx, thy, a_cell);
+        if (L->model == 0) {
+            /* Eq. 3's exponent cell by cell: 1/gamma_f = 1/gamma0 +
+               (2/3) R_c h sum_j (a_j G_j)^2 (compensated sum) */
+            double h = (c[8] - c[7]) / (double)L->n_phase;
+            qso_sum acc = {0.0, 0.0};
+            for (int j = 0; j < L->n_phase; ++j) {
+                double A = a_cell[j] * qso_envelope(L, c, c[7] + ((double)j + 0.5) * h);
+                qso_add(&acc, A * A);
+            }
+            double du = (2.0 / 3.0) * c[3] * h * qso_val(&acc);
+            mu = gamma0 / (1.0 + gamma0 * du);
+            V = 0.0;
+        } else {
+            qso_qfp_run(L, a_cell, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+        }
+        free(a_cell);
     }
 
     /* final divergence, Eq. 8 with prefactor kappa; the broadening acts
@@ -615,6 +684,7 @@ int qso_grad(const qso_laser* L, const qso_beam* B, const qso_bins* bins, double
              const double* dL_dS, double* grad8, double* smooth, qso_moments* m) {
     int nb = bins->n_bins;
     if (nb <= 0 || bins->log_spaced || !(sigma_bins > 0)) return 1;
+    if (L->focus) return 1;                /* gradient of the crossing focus only */
     qd* S = (qd*)calloc((size_t)nb, sizeof(qd));
     if (!S) return 1;
     for (int k = 0; k < nb; ++k) S[k] = qd_c(0.0);

@@ -51,7 +51,9 @@ QS_HD int32_t check_laser(const qs_laser& L) {
     return QS_ERR_INVALID_ARG;
   if (L.envelope != QS_ENV_GAUSS && L.envelope != QS_ENV_SIN2) return QS_ERR_INVALID_ARG;
   if (L.model != QS_MODEL_LL && L.model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
-  if (L.model == QS_MODEL_QFP && (L.n_phase < 1 || L.n_phase > kMaxPhase))
+  if (L.focus != QS_FOCUS_CROSSING && L.focus != QS_FOCUS_PER_CELL) return QS_ERR_INVALID_ARG;
+  if ((L.model == QS_MODEL_QFP || L.focus == QS_FOCUS_PER_CELL) &&
+      (L.n_phase < 1 || L.n_phase > kMaxPhase))
     return QS_ERR_INVALID_ARG;
   return QS_OK;
 }

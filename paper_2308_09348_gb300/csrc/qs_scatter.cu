@@ -24,7 +24,12 @@ namespace qs {
 // ---------------------------------------------------------------------------
 namespace detail {
 
-int32_t validate_laser(const qs_laser* L) { return L ? check_laser(*L) : QS_ERR_INVALID_ARG; }
+int32_t validate_laser(const qs_laser* L) {
+  if (!L) return QS_ERR_INVALID_ARG;
+  const int32_t st = check_laser(*L);
+  if (st) return st;
+  return L->focus == QS_FOCUS_PER_CELL ? QS_ERR_UNSUPPORTED : QS_OK;
+}
 int32_t validate_beam(const qs_beam* B) { return B ? check_beam(*B) : QS_ERR_INVALID_ARG; }
 int32_t validate_bins(const qs_bins* b) { return b ? check_bins(*b) : QS_ERR_INVALID_ARG; }
 

@@ -291,6 +291,116 @@ def test_qfp_integrator_vs_library_ode_solver():
 
 
 # --------------------------------------------------------------------------
+# per-cell focus: Eq. 2 along the electron's path
+# --------------------------------------------------------------------------
+
+def _path_sample(L, B, v):
+    """One decoded sample and the local field seen along its straight path,
+    parameterised by time.  The electron sits at (x, y, z) at t = 0 and moves
+    with velocity c(theta_x, theta_y, -1); the pulse envelope moves along +z
+    with its peak at z = 0 at t = delay.  Returns gamma0 and the functions
+    psi(t) (envelope phase from the peak) and a(t) (Eq. 2 at the electron)."""
+    c = oracle.constants(L)
+    k, om, zR = c["k"], c["omega0"], c["zR"]
+    cl = SC.c * 1e6 / 1e15                                  # um / fs
+    x = B.dx_um + B.sigma_x_um * v[0]
+    y = B.dy_um + B.sigma_y_um * v[1]
+    z = B.sigma_z_um * v[2]
+    g0 = B.gamma_mean * (1 + B.rel_spread * v[3])
+    thx, thy = B.div_rad * v[4], B.div_rad * v[5]
+
+    def psi(t):                      # omega0 (t - delay) - k z_e(t)
+        return om * (t - L.delay_fs) - k * (z - cl * t)
+
+    def a(t):
+        ze = z - cl * t
+        xe, ye = x + thx * cl * t - L.dx_um, y + thy * cl * t - L.dy_um
+        q = 1 + (ze / zR) ** 2
+        return L.a0 / math.sqrt(q) * math.exp(-(xe * xe + ye * ye) / (L.w0_um ** 2 * q))
+
+    # times at which psi spans the window (psi is linear in t, slope 2 omega0)
+    t_lo = (c["win_lo"] + om * L.delay_fs + k * z) / (2 * om)
+    t_hi = (c["win_hi"] + om * L.delay_fs + k * z) / (2 * om)
+    return g0, psi, a, (t_lo, t_hi), c
+
+
+def _focus_case(model, n_phase, focus=I.FOCUS_PER_CELL, w0=2.5, div=5e-3):
+    L = I.Laser(a0=20.0, w0_um=w0, tau_fs=30.0, dx_um=1.5, dy_um=-0.7, delay_fs=40.0,
+                model=model, n_phase=n_phase, focus=focus)
+    B = I.Beam(gamma_mean=4000.0, rel_spread=0.0, sigma_x_um=3.0, sigma_y_um=3.0,
+               sigma_z_um=10.0, div_rad=div)
+    V = np.array([[0.3, -0.8, 1.2, 0.0, 1.0, -0.5, 0, 0],
+                  [-1.1, 0.4, -0.9, 0.0, -1.5, 0.7, 0, 0],
+                  [0.0, 0.0, 2.0, 0.0, 0.2, 0.1, 0, 0],
+                  [0.7, 0.9, -2.2, 0.0, 0.0, -1.2, 0, 0]])
+    return L, B, V
+
+
+def test_per_cell_focus_ll_vs_time_domain_quadrature():
+    """LL with the per-cell focus: 1/gamma_f - 1/gamma0 equals the adaptive
+    quadrature, over time along the straight path, of (2/3) R_c (a G)^2
+    dpsi/dt; and differs from the crossing focus for these geometries."""
+    L, B, V = _focus_case(I.MODEL_LL, 4096, w0=1.5)
+    rec = oracle.evaluate(L, B, None, [V[:, k].copy() for k in range(8)])
+    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    rec_x = oracle.evaluate(Lx, B, None, [V[:, k].copy() for k in range(8)])
+    for s, v in enumerate(V):
+        g0, psi, a, (t0, t1), c = _path_sample(L, B, v)
+        Phi = c["Phi"]
+        dpsi = 2 * c["omega0"]
+
+        def integrand(t):
+            G = math.exp(-2 * math.log(2) * (psi(t) / Phi) ** 2)
+            return (2 / 3) * c["Rc"] * (a(t) * G) ** 2 * dpsi
+
+        du_ref = quad(integrand, t0, t1, epsabs=0, epsrel=1e-12, limit=400)[0]
+        du = 1 / rec["mu"][s] - 1 / rec["gamma0"][s]
+        assert abs(du / du_ref - 1) < 1e-6, (s, du, du_ref)
+        du_x = 1 / rec_x["mu"][s] - 1 / rec_x["gamma0"][s]
+        assert abs(du_x / du_ref - 1) > 1e-3, (s, du_x / du_ref - 1)   # the variant matters
+
+
+def test_per_cell_focus_qfp_vs_library_ode_solver():
+    """QFP with the per-cell focus: the phase sum converges (second order) to
+    a DOP853 solve over time of the moment equations with the field a(t) G
+    seen along the path."""
+    L, B, V = _focus_case(I.MODEL_QFP, 512)
+    v = V[0]
+    g0, psi, a, (t0, t1), c = _path_sample(L, B, v)
+    Phi, dpsi = c["Phi"], 2 * c["omega0"]
+
+    def f(t, y):
+        G = math.exp(-2 * math.log(2) * (psi(t) / Phi) ** 2)
+        r = oracle.qfp_rates(L, y[0], a(t) * G)
+        return [dpsi * r["D1"], dpsi * (2 * r["dD1"] * y[1] + r["D2"])]
+
+    sol = solve_ivp(f, (t0, t1), [g0, 0.0], method="DOP853", rtol=1e-11, atol=1e-9)
+    mu_ref, V_ref = sol.y[0, -1], sol.y[1, -1]
+    errs = []
+    for N in (512, 1024, 2048):
+        LN = I.Laser(**{**L.__dict__, "n_phase": N})
+        r = oracle.evaluate(LN, B, None, [np.array([x]) for x in v])
+        errs.append((abs(r["mu"][0] / mu_ref - 1), abs(r["V"][0] / V_ref - 1)))
+    assert errs[0][0] < 2e-5 and errs[0][1] < 2e-4
+    for (m1, v1), (m2, v2) in zip(errs, errs[1:]):
+        assert 3.0 < m1 / m2 < 5.0 and 3.0 < v1 / v2 < 5.0
+
+
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+def test_per_cell_focus_reduces_to_crossing_for_straight_path_in_long_focus(model):
+    """No divergence and a Rayleigh length 1e4 times the path: the field is
+    the same in every cell, so both focus readings agree (LL to the midpoint
+    rule and window truncation of the G^2 integral, QFP exactly)."""
+    L, B, V = _focus_case(model, 2048, w0=250.0, div=0.0)
+    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    xi = [V[:, k].copy() for k in range(8)]
+    r, rx = oracle.evaluate(L, B, None, xi), oracle.evaluate(Lx, B, None, xi)
+    tol = 1e-7 if model == I.MODEL_LL else 1e-9
+    np.testing.assert_allclose(r["mu"], rx["mu"], rtol=tol)
+    np.testing.assert_allclose(r["V"], rx["V"], rtol=1e-7, atol=0)
+
+
+# --------------------------------------------------------------------------
 # whole-beam integration: Table 1 and Table 2 closed forms
 # --------------------------------------------------------------------------
 
