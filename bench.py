@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--grad-n", type=int, default=1 << 24)
     ap.add_argument("--broadband-n", type=int, default=1 << 27)
     ap.add_argument("--ll-n", type=int, default=1 << 26)
+    ap.add_argument("--no-cell", action="store_true", help="skip the per-cell focus measurement")
+    ap.add_argument("--cell-n", type=int, default=1 << 24)
     return ap.parse_args()
 
 
@@ -276,6 +278,50 @@ def bench_ll(dev, rank, n=1 << 26, steps=5):
             "kernel_ms": kms, "n_samples": n, "bytes_per_sample": 24,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s",
                          "frac": gbs / pk}, "workload": wl.name}
+
+
+# Per-cell focus adds, per sample-step, the local amplitude of Eq. 2 along
+# the path: one rsqrt (a full MUFU slot) and one ex2 (half a slot), and a net
+# 14 FMA-pipe operations.
+CELL_MUFU_SLOTS_PER_STEP = QFP_MUFU_SLOTS_PER_STEP + 1 + 0.5
+CELL_FMA_OPS_PER_STEP = QFP_FMA_OPS_PER_STEP + 14
+
+
+def bench_cell_focus(dev, rank, n=1 << 24, steps=3):
+    """The bench beam and laser with Eq. 2 evaluated in every phase cell
+    along the electron's path (quantum model, 512 cells, FP32)."""
+    import torch
+    from dataclasses import replace
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.full_qfp(n)
+    L = replace(wl.laser, focus=I.FOCUS_PER_CELL)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    out = B.Outputs(wl.bins, n, dev, "f32")
+    B.qs_scatter(L, wl.beam, xi, wl.bins, out=out)
+    torch.cuda.synchronize()
+    kev = [tuple(_events()) for _ in range(steps)]
+    for k in range(steps):
+        B.qs_scatter(L, wl.beam, xi, wl.bins, out=out, kernel_events=kev[k])
+    torch.cuda.synchronize()
+    kms = sum(x.elapsed_time(y) for x, y in kev) / steps
+    props = torch.cuda.get_device_properties(dev)
+    fmax = float(peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    steps_total = n * L.n_phase
+    peak_mufu = props.multi_processor_count * MUFU_SLOTS_PER_SM * fmax
+    peak_fma = props.multi_processor_count * FMA_LANES_PER_SM * fmax
+    t_mufu = CELL_MUFU_SLOTS_PER_STEP * steps_total / peak_mufu
+    t_fma = CELL_FMA_OPS_PER_STEP * steps_total / peak_fma
+    t = kms * 1e-3
+    return {"metric": "beam-sample evals/s", "value": n / t, "unit": "samples/s",
+            "kernel_ms": kms, "n_samples": n, "n_phase": L.n_phase, "focus": "per cell",
+            "roofline": {"bound": "alu", "pipe": "mufu" if t_mufu >= t_fma else "fma",
+                         "achieved": CELL_MUFU_SLOTS_PER_STEP * steps_total / t / 1e12,
+                         "peak": peak_mufu / 1e12, "unit": "Top/s",
+                         "frac": max(t_mufu, t_fma) / t},
+            "workload": wl.name + "_cellfocus"}
 
 
 def bench_batch(dev, rank, steps=3, n_shots=4096):
@@ -522,6 +568,7 @@ def main():
     grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)
     broad = None if args.no_broadband else bench_broadband(dev, rank, args.broadband_n)
     ll = None if args.no_ll else bench_ll(dev, rank, n=args.ll_n)
+    cell = None if args.no_cell else bench_cell_focus(dev, rank, n=args.cell_n)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -546,6 +593,7 @@ def main():
                 "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
+                "cell_focus": cell,
                 "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:

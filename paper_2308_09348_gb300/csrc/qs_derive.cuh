@@ -131,7 +131,7 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   p.cRR = (2.0 / 3.0) * Rc * intG2;
   p.cK = (2.0 / 3.0) * Rc;
   p.cchi = kSqrt2 / aS;
-  p.n_phase = L.model == QS_MODEL_QFP ? L.n_phase : 1;
+  p.n_phase = (L.model == QS_MODEL_QFP || L.focus == QS_FOCUS_PER_CELL) ? L.n_phase : 1;
   p.h = (hi - lo) / (double)p.n_phase;
   p.win_lo = lo;
   p.Phi = Phi;
@@ -139,6 +139,9 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   p.kappa_s = L.div_prefactor * kSqrt2OverPi;
   p.envelope = L.envelope;
   p.model = L.model;
+  p.focus = L.focus;
+  p.phic = L.envelope == QS_ENV_GAUSS ? 0.0 : 0.5 * PhiT;   // pulse peak on the window axis
+  p.inv2k = 1.0 / (2.0 * k);
 
   p.gmean = B.gamma_mean;
   p.spread = B.rel_spread;

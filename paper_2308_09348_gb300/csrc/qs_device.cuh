@@ -29,8 +29,9 @@ struct Params {
   double cK;           // (2/3) R_c: K = cK A^2, loss per phase   (Eq. 6)
   double cchi;         // sqrt2 / a_S: chi = cchi mu A at rms field
   double h, win_lo, Phi, PhiT;
+  double phic, inv2k;  // phase of the pulse peak on the window axis; 1/(2k)
   double kappa_s;      // kappa sqrt(2/pi)                         (Eq. 8)
-  int32_t envelope, model, n_phase, pad0;
+  int32_t envelope, model, n_phase, focus;   // focus: 0 crossing, 1 per cell
   // beam
   double gmean, spread, glo, gspan, sx, sy, sz, div, bdx, bdy;
   int32_t flat, pad1;
@@ -153,6 +154,12 @@ __device__ __forceinline__ double envelope_at(const Params& p, int j) {
   return s * s;
 }
 
+// Per-cell focus: shift s_j = (phi_j - phi_c)/(2k) of cell j's midpoint
+// from the pulse-peak crossing along the electron's path.
+__device__ __forceinline__ double cell_shift(const Params& p, int j) {
+  return (p.win_lo + ((double)j + 0.5) * p.h - p.phic) * p.inv2k;
+}
+
 // Shared-memory phase table: FP64 path G_j; FP32 path {G_j, G_j, G_j^2,
 // G_j^2} (the square taken in double, then rounded), so one 16-byte load
 // gives both operands already paired for the two samples a thread carries.
@@ -162,8 +169,14 @@ template <> struct Tab<double> { using type = double; };
 
 __device__ __forceinline__ void table_entry(const Params& p, int j, float4* t) {
   const double G = envelope_at(p, j);
-  const float g = (float)G, g2 = (float)(G * G);
-  t[j] = make_float4(g, g, g2, g2);
+  const float g = (float)G;
+  if (p.focus) {                       // per-cell focus: {G, G, s_j, s_j}
+    const float sj = (float)cell_shift(p, j);
+    t[j] = make_float4(g, g, sj, sj);
+  } else {
+    const float g2 = (float)(G * G);
+    t[j] = make_float4(g, g, g2, g2);
+  }
 }
 __device__ __forceinline__ void table_entry(const Params& p, int j, double* t) {
   t[j] = envelope_at(p, j);
@@ -172,6 +185,44 @@ __device__ __forceinline__ void table_entry(const Params& p, int j, double* t) {
 struct Sample {
   double gamma0, aeff, mu, V, theta_e, thx0, thy0, tx, ty, gout;
 };
+
+// Uncontracted IEEE operations (the _rn intrinsics are never fused), so the
+// per-sample arithmetic is the same instruction sequence in every kernel
+// that inlines it (fused histograms equal histograms of per-sample records,
+// batched shots equal single-shot calls, bit for bit).
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Per-cell focus (laser focus == QS_FOCUS_PER_CELL): Eq. 2 evaluated in
+// every phase cell at the electron's position there.  Between the crossing
+// of the pulse peak and the midpoint of cell j the electron (velocity
+// c(theta_x, theta_y, -1)) meets the counter-moving phase at twice the laser
+// frequency, so it moves s_j = (phi_j - phi_c)/(2k) along -z and theta s_j
+// sideways: z_j = z* - s_j, transverse offsets xs + theta_x s_j,
+// ys + theta_y s_j.  Path holds z*/z_R, the offsets at the crossing and the
+// angles.
+template <typename T> struct Path { T zq, xs, ys, thx, thy; };
+
+// a_j = a0 q^-1/2 exp(-rho^2/(W0^2 q)), q = 1 + (z_j/z_R)^2, 1/q = (q^-1/2)^2.
+template <typename T>
+__device__ __forceinline__ T a_cell(const Params& p, const Path<T>& g, T s) {
+  const T zq = op_fma(-s, QS_PV(T, inv_zR), g.zq);
+  const T q = op_fma(zq, zq, (T)1);
+  const T xj = op_fma(g.thx, s, g.xs), yj = op_fma(g.thy, s, g.ys);
+  const T rho2 = op_fma(xj, xj, op_mul(yj, yj));
+  const T rs = M<T>::rsqrt(q);
+  const T E = op_mul(op_mul(rho2, QS_PV(T, inv_w0sq)), op_mul(rs, rs));
+  if constexpr (sizeof(T) == 4)
+    return op_mul(op_mul(QS_PV(T, a0), rs), M<T>::ex2(op_mul(-(T)1.4426950408889634074, E)));
+  else
+    return op_mul(op_mul(QS_PV(T, a0), rs), exp(-E));
+}
 
 // Quantum-corrected Fokker-Planck phase integration (Eq. 6; mean/variance
 // closure of the Fokker-Planck regime), second order in the cell width h:
@@ -183,9 +234,11 @@ struct Sample {
 //   D2 = (55/(16 sqrt3)) K mu^3 chi h2.
 // Returns du = 1/mu_f - 1/gamma0 and V_f.  FP64 path: written as the
 // equations read.
+// LOC: per-cell focus, the peak amplitude a_j of cell j from the path.
+template <bool LOC>
 __device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
                                               double a, double g0, double& du_out,
-                                              double& V_out) {
+                                              double& V_out, const Path<double>& path) {
   // explicit (uncontracted) operations: see op_fma below
   const double LN2 = 0.69314718055994530942;
   const double cK = p.cK, cchi = p.cchi, h = p.h;
@@ -195,7 +248,8 @@ __device__ __forceinline__ void qfp_integrate(const Params& p, const double* __r
   const int N = p.n_phase;
 #pragma unroll 2
   for (int j = 0; j < N; ++j) {
-    const double A = __dmul_rn(a, sG[j]);
+    const double aj = LOC ? a_cell<double>(p, path, cell_shift(p, j)) : a;
+    const double A = __dmul_rn(aj, sG[j]);
     const double K = __dmul_rn(__dmul_rn(cK, A), A);
     const double hK = __dmul_rn(h, K);
     const double dum = __fma_rn(__dmul_rn(0.5, hK), gprev, du);
@@ -251,28 +305,55 @@ __device__ __forceinline__ float2 ex2x2(float2 x) {
 __device__ __forceinline__ float2 rcpx2(float2 x) {
   return make_float2(M<float>::rcp(x.x), M<float>::rcp(x.y));
 }
+__device__ __forceinline__ float2 rsqrtx2(float2 x) {
+  return make_float2(M<float>::rsqrt(x.x), M<float>::rsqrt(x.y));
+}
 
+// LOC: per-cell focus; the table then holds {G, G, s_j, s_j} and the two
+// samples' paths give the per-cell amplitudes (same operations as a_cell).
+template <bool LOC>
 __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
                                                     const float4* __restrict__ tab, float2 a,
-                                                    float2 g0, float2& du_out, float2& V_out) {
+                                                    float2 g0, float2& du_out, float2& V_out,
+                                                    const Path<float>& P0, const Path<float>& P1) {
   const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
   const float2 C816 = f2((float)(4.8 * 1.7));
   const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
   const float2 LN2 = f2(0.69314718055994530942f);
   const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
   const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
-  const float2 c1 = mul2(mul2(f2(p.f.hcK), a), a);
-  const float2 ca = mul2(f2(p.f.cchi), a);
+  const float2 c1 = LOC ? f2(p.f.hcK) : mul2(mul2(f2(p.f.hcK), a), a);
+  const float2 ca = LOC ? f2(p.f.cchi) : mul2(f2(p.f.cchi), a);
+  // per-cell focus: the paths of the two samples
+  const float2 zq0 = make_float2(P0.zq, P1.zq), xs = make_float2(P0.xs, P1.xs),
+               ys = make_float2(P0.ys, P1.ys), tx = make_float2(P0.thx, P1.thx),
+               ty = make_float2(P0.thy, P1.thy);
   float2 du = f2(0.f), V = f2(0.f), gph = HALF;
   const int N = p.n_phase;
 #pragma unroll 2
   for (int j = 0; j < N; ++j) {
     const float4 gg = tab[j];
-    const float2 G = make_float2(gg.x, gg.y), G2 = make_float2(gg.z, gg.w);
-    const float2 hK = mul2(c1, G2);
+    const float2 G = make_float2(gg.x, gg.y);
+    float2 hK, cg;
+    if constexpr (LOC) {
+      const float2 S = make_float2(gg.z, gg.w);
+      const float2 zq = fma2(S, f2(-p.f.inv_zR), zq0);
+      const float2 q = fma2(zq, zq, ONE);
+      const float2 xj = fma2(tx, S, xs), yj = fma2(ty, S, ys);
+      const float2 rho2 = fma2(xj, xj, mul2(yj, yj));
+      const float2 rs = rsqrtx2(q);
+      const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), mul2(rs, rs));
+      const float2 aj = mul2(mul2(f2(p.f.a0), rs), ex2x2(mul2(f2(-1.4426950408889634074f), E)));
+      const float2 AG = mul2(aj, G);
+      hK = mul2(c1, mul2(AG, AG));
+      cg = mul2(ca, AG);
+    } else {
+      hK = mul2(c1, make_float2(gg.z, gg.w));
+      cg = mul2(ca, G);
+    }
     const float2 dum = fma2(hK, gph, du);
     const float2 mu = mul2(g0, rcpx2(fma2(g0, dum, ONE)));
-    const float2 chi = mul2(mul2(ca, G), mu);
+    const float2 chi = mul2(cg, mu);
     const float2 chi2 = mul2(chi, chi);
     // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
     const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
@@ -300,24 +381,12 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
   V_out = V;
 }
 
-// Uncontracted IEEE operations (the _rn intrinsics are never fused), so the
-// per-sample arithmetic is the same instruction sequence in every kernel
-// that inlines it (fused histograms equal histograms of per-sample records,
-// batched shots equal single-shot calls, bit for bit).
-__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-
 // a_eff at the crossing point and the decoded sample (rows a1-a3), from the
 // sample's six normal deviates.
+// path (optional) receives the crossing geometry for the per-cell focus.
 template <typename T>
 __device__ __forceinline__ T focus_xi(const Params& p, T xi0, T xi1, T xi2, T xi3, T xi4, T xi5,
-                                      T& gamma0, T& thx, T& thy) {
+                                      T& gamma0, T& thx, T& thy, Path<T>* path = nullptr) {
   // decode (reparameterised); gamma0 in the arithmetic type
   const T x = op_fma(QS_PV(T, sx), xi0, QS_PV(T, bdx));
   const T y = op_fma(QS_PV(T, sy), xi1, QS_PV(T, bdy));
@@ -337,6 +406,7 @@ __device__ __forceinline__ T focus_xi(const Params& p, T xi0, T xi1, T xi2, T xi
   const T rho2 = op_fma(xs, xs, op_mul(ys, ys));
   // local Gaussian focus, Eq. 2
   const T zq = op_mul(zs, QS_PV(T, inv_zR));
+  if (path) *path = Path<T>{zq, xs, ys, thx, thy};
   const T q = op_fma(zq, zq, (T)1);
   const T E = op_mul(op_mul(rho2, QS_PV(T, inv_w0sq)), M<T>::rcp(q));
   if (sizeof(T) == 4)
@@ -346,28 +416,39 @@ __device__ __forceinline__ T focus_xi(const Params& p, T xi0, T xi1, T xi2, T xi
 }
 
 template <typename T>
-__device__ __forceinline__ T focus(const Params& p, int64_t i, T& gamma0, T& thx, T& thy) {
+__device__ __forceinline__ T focus(const Params& p, int64_t i, T& gamma0, T& thx, T& thy,
+                                   Path<T>* path = nullptr) {
   return focus_xi<T>(p, load_t<T>(p.xi[0], i, p.dtype), load_t<T>(p.xi[1], i, p.dtype),
                      load_t<T>(p.xi[2], i, p.dtype), load_t<T>(p.xi[3], i, p.dtype),
                      load_t<T>(p.xi[4], i, p.dtype), load_t<T>(p.xi[5], i, p.dtype), gamma0,
-                     thx, thy);
+                     thx, thy, path);
 }
 
 // One beam sample through the model, in the paper's order (rows a1-a6).
 // FP64 path: one sample through the model selected at compile time by QFP
 // (the table is unused by LL).
-template <bool QFP>
+// LOC: per-cell focus (LL: Eq. 3's exponent summed cell by cell).
+template <bool QFP, bool LOC = false>
 __device__ __forceinline__ Sample eval_sample(const Params& p, const double* __restrict__ tab,
                                               int64_t i) {
   Sample s;
   double gamma0, thx, thy, mu, V = 0.0;
-  const double a = focus<double>(p, i, gamma0, thx, thy);
-  if (!QFP) {
+  Path<double> path;
+  const double a = focus<double>(p, i, gamma0, thx, thy, LOC ? &path : nullptr);
+  if (!QFP && !LOC) {
     // Eq. 3, a0 -> a_eff
     mu = gamma0 / __fma_rn(__dmul_rn(__dmul_rn(p.cRR, gamma0), a), a, 1.0);
+  } else if (!QFP) {
+    // 1/gamma_f = 1/gamma0 + (2/3) R_c h sum_j (a_j G_j)^2
+    double acc = 0.0;
+    for (int j = 0; j < p.n_phase; ++j) {
+      const double A = __dmul_rn(a_cell<double>(p, path, cell_shift(p, j)), tab[j]);
+      acc = __fma_rn(A, A, acc);
+    }
+    mu = gamma0 / __fma_rn(gamma0, __dmul_rn(__dmul_rn(p.h, p.cK), acc), 1.0);
   } else {
     double du;
-    qfp_integrate(p, tab, a, gamma0, du, V);
+    qfp_integrate<LOC>(p, tab, a, gamma0, du, V, path);
     mu = gamma0 / __fma_rn(gamma0, du, 1.0);
   }
   double theta_e = 0.0, gout = mu, tx = thx;
@@ -438,14 +519,16 @@ __device__ __forceinline__ void finish_f32(const Params& p, int64_t i, float g0,
 
 // FP32 QFP path: samples i0 and i1 through the model together (the phase
 // integration runs packed).
+template <bool LOC = false>
 __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
                                                   int64_t i0, int64_t i1, SampleF& s0,
                                                   SampleF& s1) {
   float g0f, g1f, tx0, ty0, tx1, ty1;
-  const float a0 = focus<float>(p, i0, g0f, tx0, ty0);
-  const float a1 = focus<float>(p, i1, g1f, tx1, ty1);
+  Path<float> P0{}, P1{};
+  const float a0 = focus<float>(p, i0, g0f, tx0, ty0, LOC ? &P0 : nullptr);
+  const float a1 = focus<float>(p, i1, g1f, tx1, ty1, LOC ? &P1 : nullptr);
   float2 du, V;
-  qfp_integrate_f32x2(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V);
+  qfp_integrate_f32x2<LOC>(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V, P0, P1);
   finish_f32(p, i0, g0f, a0, tx0, ty0, du.x, V.x, s0);
   finish_f32(p, i1, g1f, a1, tx1, ty1, du.y, V.y, s1);
 }
@@ -472,17 +555,42 @@ __device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
                         load_t<float>(p.xi[4], i, p.dtype), load_t<float>(p.xi[5], i, p.dtype));
 }
 
-// One sample of the path selected by T and QFP (FP32 QFP samples are
+// FP32 classical path with the per-cell focus: the exponent of Eq. 3 summed
+// cell by cell, 1/gamma_f - 1/gamma0 = h (2/3) R_c sum_j (a_j G_j)^2.
+__device__ __forceinline__ SampleF eval_ll_f32_cells(const Params& p,
+                                                     const float4* __restrict__ tab, int64_t i) {
+  SampleF s;
+  float gamma0, thx, thy;
+  Path<float> path;
+  const float a = focus<float>(p, i, gamma0, thx, thy, &path);
+  float acc = 0.f;
+  for (int j = 0; j < p.n_phase; ++j) {
+    const float4 e = tab[j];
+    const float A = __fmul_rn(a_cell<float>(p, path, e.z), e.x);
+    acc = __fmaf_rn(A, A, acc);
+  }
+  float hi, lo;
+  recombine_f2(gamma0, __fmul_rn(p.f.hcK, acc), hi, lo);
+  s.g0 = gamma0; s.aeff = a; s.mu_hi = hi; s.mu_lo = lo; s.V = 0.f; s.theta_e = 0.f;
+  s.thx0 = thx; s.thy0 = thy; s.tx = thx; s.ty = thy;
+  s.go_hi = hi;
+  s.go_lo = lo;
+  return s;
+}
+
+// One sample of the path selected by T, QFP and LOC (FP32 QFP samples are
 // normally evaluated in pairs; a single one runs as a pair with itself).
-template <typename T, bool QFP>
+template <typename T, bool QFP, bool LOC = false>
 __device__ __forceinline__ typename SampleT<T>::type eval_one(
     const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i) {
   if constexpr (sizeof(T) == 8) {
-    return eval_sample<QFP>(p, reinterpret_cast<const double*>(tab), i);
+    return eval_sample<QFP, LOC>(p, reinterpret_cast<const double*>(tab), i);
   } else if constexpr (QFP) {
     SampleF s0, s1;
-    eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1);
+    eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1);
     return s0;
+  } else if constexpr (LOC) {
+    return eval_ll_f32_cells(p, reinterpret_cast<const float4*>(tab), i);
   } else {
     return eval_ll_f32(p, i);
   }

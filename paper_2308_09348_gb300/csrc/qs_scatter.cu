@@ -24,12 +24,7 @@ namespace qs {
 // ---------------------------------------------------------------------------
 namespace detail {
 
-int32_t validate_laser(const qs_laser* L) {
-  if (!L) return QS_ERR_INVALID_ARG;
-  const int32_t st = check_laser(*L);
-  if (st) return st;
-  return L->focus == QS_FOCUS_PER_CELL ? QS_ERR_UNSUPPORTED : QS_OK;
-}
+int32_t validate_laser(const qs_laser* L) { return L ? check_laser(*L) : QS_ERR_INVALID_ARG; }
 int32_t validate_beam(const qs_beam* B) { return B ? check_beam(*B) : QS_ERR_INVALID_ARG; }
 int32_t validate_bins(const qs_bins* b) { return b ? check_bins(*b) : QS_ERR_INVALID_ARG; }
 
@@ -123,13 +118,17 @@ void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
 // ~1000 cycles per sample, so its histograms go straight to global integer
 // atomics (negligible traffic) and the freed shared memory buys occupancy;
 // the LL model is memory-bound and keeps them in shared memory if they fit.
-Smem smem_plan(const Plan& pl, int precision, bool qfp, int n_phase, bool weighted, int block) {
+// cells: phase-table entries (QFP or the per-cell focus, 0 otherwise);
+// cell_focus: the per-cell focus (histograms always global).
+Smem smem_plan(const Plan& pl, int precision, int cells, bool cell_focus, bool weighted,
+               int block) {
   Smem sm;
-  // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} (FP32 path)
-  const size_t tab = qfp ? align_up((size_t)n_phase * (precision == QS_F64 ? 8 : 16), 16) : 0;
+  // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} or
+  // {G, G, s_j, s_j} (FP32 path)
+  const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16);
   const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
   const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
-  sm.hist = !(qfp && n_phase >= 32) && tab + red + hist <= (size_t)kSmemLimit &&
+  sm.hist = !cell_focus && cells < 32 && tab + red + hist <= (size_t)kSmemLimit &&
             (pl.nspec + pl.nmap + pl.naeff) > 0;
   sm.bytes = tab + red + (sm.hist ? hist : 0);
   // smoothed-spectrum accumulators (u64) stay in shared memory when small
@@ -160,18 +159,21 @@ using namespace detail;
 // K1: fused evaluation + histograms + moment partials.  T: per-sample
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
+// LOC: the per-cell focus.
 // Register budget per thread (blocks of up to 512 threads): FP32 QFP 64
 // (two 256-thread CTAs or more per SM for the MUFU-bound loop), FP32
 // classical 80 (three 256-thread CTAs per SM keep enough loads in flight
-// for the HBM-bound path), FP64 128.
-template <typename T, bool QFP>
-constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : (QFP ? 64 : 80);
+// for the HBM-bound path), FP32 per-cell focus 80 (the paths of two
+// samples stay live in the loop), FP64 128.
+template <typename T, bool QFP, bool LOC>
+constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && !LOC) ? 64 : 80);
 
-template <typename T, typename H, bool QFP, bool SHIST>
-__global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
+template <typename T, typename H, bool QFP, bool SHIST, bool LOC>
+__global__ void __maxnreg__((kScatterRegs<T, QFP, LOC>)) k_scatter(const Params p) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  const size_t tab_bytes = QFP ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
+  const size_t tab_bytes =
+      (QFP || LOC) ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
   TT* tab = reinterpret_cast<TT*>(smem);
   double* red = reinterpret_cast<double*>(smem + tab_bytes);
   H* sh = reinterpret_cast<H*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumMom * sizeof(double));
@@ -187,7 +189,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
   unsigned long long* ssm = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(sh) + hist_bytes);
   unsigned long long* hsm = nsm ? (p.smooth_in_smem ? ssm : p.acc_smooth) : nullptr;
 
-  if (QFP)
+  if (QFP || LOC)
     for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
@@ -212,7 +214,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
       bool ok0 = false, ok1 = false;
       if (i0 < p.n) {
         SampleF s0, s1;
-        eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+        eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
         ok0 = accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
         if (i1 != i0)
           ok1 = accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
@@ -226,7 +228,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
     }
   } else {
     int64_t i = t0;
-    if constexpr (!QFP && sizeof(T) == 4) {
+    if constexpr (!QFP && !LOC && sizeof(T) == 4) {
       // FP32 classical path (memory-bound): four consecutive samples per
       // thread through 16-byte loads of every stream, when all streams are
       // FP32 and 16-byte aligned and there is no smoothed spectrum; the
@@ -259,7 +261,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP>)) k_scatter(const Params p) {
       typename DepT<T>::type d;
       bool ok = false;
       if (ii < p.n) {
-        const auto s = eval_one<T, QFP>(p, tab, ii);
+        const auto s = eval_one<T, QFP, LOC>(p, tab, ii);
         ok = accumulate<T, H, SHIST>(p, s, ii, acc, hs, hm, ha, nspec, nmap, naeff);
         dep_set(d, s);
       }
@@ -409,12 +411,12 @@ __device__ __forceinline__ void write_record(const Params& p, const qs_sample_ou
 }
 
 // K0: per-sample records; the same per-sample code path as k_scatter.
-template <typename T, bool QFP>
+template <typename T, bool QFP, bool LOC>
 __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   TT* tab = reinterpret_cast<TT*>(smem);
-  if (QFP)
+  if (QFP || LOC)
     for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -423,21 +425,41 @@ __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
     for (int64_t k = t0; 2 * k < p.n; k += stride) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
       SampleF s0, s1;
-      eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+      eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
       write_record(p, o, s0, i0);
       if (i1 != i0) write_record(p, o, s1, i1);
     }
   } else {
-    for (int64_t i = t0; i < p.n; i += stride) write_record(p, o, eval_one<T, QFP>(p, tab, i), i);
+    for (int64_t i = t0; i < p.n; i += stride)
+      write_record(p, o, eval_one<T, QFP, LOC>(p, tab, i), i);
   }
 }
 
 namespace {
 
-template <typename T, typename H, bool QFP, bool SHIST>
+// k_eval with its dynamic shared memory (phase table) allowed up to the
+// largest table.
+template <typename T, bool QFP, bool LOC>
+int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
+                    const qs_sample_out& o) {
+  auto kern = k_eval<T, QFP, LOC>;
+  static bool attr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxPhase * (int)sizeof(float4)) != cudaSuccess)
+      return cuda_fail();
+    attr[dev] = true;
+  }
+  kern<<<grid, 256, tb, st>>>(p, o);
+  return QS_OK;
+}
+
+template <typename T, typename H, bool QFP, bool SHIST, bool LOC = false>
 int32_t launch_scatter_t(const Params& p, int block, size_t smem, int sms, int grid_req, int gmax,
                          cudaStream_t st, int* grid_out, const qs_exec* ex) {
-  auto kern = k_scatter<T, H, QFP, SHIST>;
+  auto kern = k_scatter<T, H, QFP, SHIST, LOC>;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
@@ -469,6 +491,10 @@ int32_t launch_scatter_prec(const Params& p, bool qfp, const Smem& sm, int block
   typedef unsigned int U32;
   typedef unsigned long long U64;
   const size_t b = sm.bytes;
+  if (p.focus) {           // per-cell focus: global histograms (smem_plan)
+    if (qfp) return launch_scatter_t<T, U32, true, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
+    return launch_scatter_t<T, U32, false, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  }
   if (qfp) {
     if (!sm.hist) return launch_scatter_t<T, U32, true, false>(p, block, b, sms, grid_req, gmax, st, g, ex);
     return p.weighted ? launch_scatter_t<T, U64, true, true>(p, block, b, sms, grid_req, gmax, st, g, ex)
@@ -533,7 +559,9 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < pl.ws_bytes)
     return QS_ERR_WORKSPACE;
   const bool qfp = laser->model == QS_MODEL_QFP;
-  const Smem sm = smem_plan(pl, prec, qfp, qfp ? laser->n_phase : 0, samples->w != nullptr, block);
+  const bool cells = qfp || laser->focus == QS_FOCUS_PER_CELL;
+  const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, laser->focus == QS_FOCUS_PER_CELL,
+                            samples->w != nullptr, block);
 
   Params p;
   fill_params(p, laser, beam, samples, bins, wbits);
@@ -577,27 +605,23 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   int64_t tiles = (samples->n + 255) / 256;
   int g = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  const bool qfp = laser->model == QS_MODEL_QFP;
-  const size_t tb = qfp ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4)) : 0;
+  const bool qfp = laser->model == QS_MODEL_QFP, loc = laser->focus == QS_FOCUS_PER_CELL;
+  const size_t tb = (qfp || loc)
+                        ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
+                        : 0;
+  int32_t est;
   if (prec == QS_F64) {
-    if (qfp) k_eval<double, true><<<g, 256, tb, cs>>>(p, *out);
-    else k_eval<double, false><<<g, 256, 0, cs>>>(p, *out);
+    if (loc) est = qfp ? launch_eval<double, true, true>(g, tb, cs, p, *out)
+                       : launch_eval<double, false, true>(g, tb, cs, p, *out);
+    else est = qfp ? launch_eval<double, true, false>(g, tb, cs, p, *out)
+                   : launch_eval<double, false, false>(g, tb, cs, p, *out);
   } else {
-    if (qfp) {
-      static bool attr[64] = {};
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-      if (dev >= 0 && dev < 64 && !attr[dev]) {
-        if (cudaFuncSetAttribute(k_eval<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kMaxPhase * (int)sizeof(float4)) != cudaSuccess)
-          return QS_ERR_CUDA;
-        attr[dev] = true;
-      }
-      k_eval<float, true><<<g, 256, tb, cs>>>(p, *out);
-    } else {
-      k_eval<float, false><<<g, 256, 0, cs>>>(p, *out);
-    }
+    if (loc) est = qfp ? launch_eval<float, true, true>(g, tb, cs, p, *out)
+                       : launch_eval<float, false, true>(g, tb, cs, p, *out);
+    else est = qfp ? launch_eval<float, true, false>(g, tb, cs, p, *out)
+                   : launch_eval<float, false, false>(g, tb, cs, p, *out);
   }
+  if (est) return est;
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
 
@@ -758,8 +782,9 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   HostPipe* pipe = nullptr;
   if ((st = host_pipe(&pipe))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
-  const Smem sm = smem_plan(hp.pl, prec, qfp, qfp ? laser->n_phase : 0, h_samples->w != nullptr,
-                            block);
+  const bool cells = qfp || laser->focus == QS_FOCUS_PER_CELL;
+  const Smem sm = smem_plan(hp.pl, prec, cells ? laser->n_phase : 0,
+                            laser->focus == QS_FOCUS_PER_CELL, h_samples->w != nullptr, block);
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Params p;

@@ -138,6 +138,70 @@ def test_eval_float64_streams_and_missing_optional_streams():
 
 
 # ---------------------------------------------------------------------------
+# per-cell focus (Eq. 2 along the electron's path)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model,env", [(I.MODEL_LL, I.ENV_GAUSS), (I.MODEL_QFP, I.ENV_GAUSS),
+                                       (I.MODEL_QFP, I.ENV_SIN2), (I.MODEL_LL, I.ENV_SIN2)])
+def test_per_cell_focus_eval_matches_oracle(prec, model, env):
+    n = 1500
+    wl, L, xi = cfg2(n, model=model, envelope=env, n_phase=256, focus=I.FOCUS_PER_CELL)
+    xt, _ = dev(xi)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.evaluate(L, wl.beam, wl.bins, f64(xi))
+    compare_samples(rec, ref, prec, wl.bins)
+    # the variant changes the result at this focus (z_R = 24.5 um, 40 fs delay)
+    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    refx = oracle.evaluate(Lx, wl.beam, wl.bins, f64(xi))
+    assert np.max(np.abs(refx["mu"] / ref["mu"] - 1)) > 1e-3
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+def test_per_cell_focus_scatter_matches_oracle_and_records(prec, model):
+    n = 3001
+    wl, L, xi = cfg2(n, model=model, n_phase=128, focus=I.FOCUS_PER_CELL)
+    w = I.rng(17).uniform(0.25, 2.0, n).astype(np.float32)
+    xt, wt = dev(xi, w)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi), w.astype(np.float64))
+    compare_scatter(out, ref, prec, float(w.astype(np.float64).sum()))
+    # unit weights: the fused spectrum is the histogram of the per-sample records
+    out1 = qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+    torch.cuda.synchronize()
+    b = rec["bin"].cpu().numpy()
+    hist = np.bincount(b[(b >= 0) & (b < wl.bins.n_bins)], minlength=wl.bins.n_bins)
+    np.testing.assert_array_equal(out1.spectrum.cpu().numpy(), hist.astype(np.float64))
+
+
+def test_per_cell_focus_gradient_is_unsupported_and_batch_shot_flagged():
+    n = 300
+    wl, L, xi = cfg2(n, n_phase=64, focus=I.FOCUS_PER_CELL)
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32")
+    with pytest.raises(QsError):
+        B.qs_scatter_grad(L, wl.beam, xt, wl.bins, out.moments,
+                          torch.zeros(13, dtype=torch.float64), None, precision="f32", out=out)
+    bw = I.batch_shots(3, seed=21, log10_range=(2.0, 2.5), n_phase=64, n_bins=32)
+    lasers = list(bw.lasers)
+    lasers[1] = I.Laser(**{**lasers[1].__dict__, "focus": I.FOCUS_PER_CELL})
+    offsets = np.zeros(4, dtype=np.int64)
+    offsets[1:] = np.cumsum(bw.counts)
+    xs = [torch.from_numpy(a).cuda() for a in I.sample_streams(int(offsets[-1]), 22,
+                                                                 dtype=np.float32)]
+    bt = B.Batch(lasers, bw.beams, offsets, bw.bins, int(offsets[-1]), ranges=bw.ranges)
+    bt.run(xs)
+    torch.cuda.synchronize()
+    m = bt.moments.cpu().numpy()
+    assert m[1, 0] == 0 and m[1, B.MOMENT_FIELDS.index("nonfinite")] == -1
+    assert m[0, 0] > 0 and m[2, 0] > 0
+
+
+# ---------------------------------------------------------------------------
 # whole-beam integration
 # ---------------------------------------------------------------------------
 
