@@ -295,7 +295,7 @@ def bench_cell_focus(dev, rank, n=1 << 24, steps=3):
     from paper_2308_09348_gb300 import binding as B
     from paper_2308_09348_gb300 import inputs as I
     wl = I.full_qfp(n)
-    L = replace(wl.laser, focus=I.FOCUS_PER_CELL)
+    L = replace(wl.laser, variant=I.VAR_CELL_FOCUS)
     gen = torch.Generator(device=dev)
     gen.manual_seed(wl.seed + 7919 * rank)
     xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]

@@ -52,7 +52,7 @@ typedef enum {
 
 typedef enum { QS_ENV_GAUSS = 0, QS_ENV_SIN2 = 1 } qs_envelope;
 typedef enum { QS_MODEL_LL = 0, QS_MODEL_QFP = 1 } qs_model;
-typedef enum { QS_FOCUS_CROSSING = 0, QS_FOCUS_PER_CELL = 1 } qs_focus;
+typedef enum { QS_VARIANT_CELL_FOCUS = 1, QS_VARIANT_CYCLE_CHI = 2 } qs_variant;
 typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
 
 /*
@@ -71,12 +71,12 @@ typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
  *                  [0, Phi_T], Phi_T chosen so the intensity FWHM is Phi
  *   model          QS_MODEL_LL (Eq. 3) or QS_MODEL_QFP (Eq. 6 + FP closure)
  *   n_phase        phase cells of the integration, 1..4096 (ignored by LL
- *                  with QS_FOCUS_CROSSING)
- *   focus          QS_FOCUS_CROSSING: Eq. 2 evaluated once, where the
- *                  electron crosses the pulse peak (the paper neglects the
- *                  focus variation during the crossing, Sec. 2);
- *                  QS_FOCUS_PER_CELL: Eq. 2 evaluated in every phase cell
- *                  at the electron's position there.  In cell j at phase
+ *                  without QS_VARIANT_CELL_FOCUS)
+ *   variant        bit flags, 0 = the paper's model as read here:
+ *                  QS_VARIANT_CELL_FOCUS: Eq. 2 evaluated in every phase
+ *                  cell at the electron's position there, instead of once
+ *                  where it crosses the pulse peak (the paper neglects the
+ *                  focus variation during the crossing, Sec. 2).  In cell j at phase
  *                  phi_j (0 at the crossing) the electron has moved by
  *                  s_j = phi_j/(2k) along -z (it meets the counter-moving
  *                  phase at twice the frequency), so z_j = z* - s_j and the
@@ -86,12 +86,20 @@ typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
  *                  exponent cell by cell: 1/gamma_f = 1/gamma0 +
  *                  (2/3) R_c h sum_j A_j^2.  a_eff (its histogram, its
  *                  moment and Eq. 8) stays the value at the crossing.
- *                  The gradient entry point supports QS_FOCUS_CROSSING only.
+ *                  QS_VARIANT_CYCLE_CHI (quantum model): the Gaunt factor
+ *                  and the diffusion factor averaged over the laser cycle
+ *                  of a linearly polarised field, chi(psi) = sqrt2 chi
+ *                  |cos psi| with chi the value at the rms field, instead
+ *                  of taken at the rms field: g -> G(chi) =
+ *                  <2 cos^2 psi g(chi(psi))>, 2g + chi g' -> 2G + chi G',
+ *                  h -> H(chi) = <2 sqrt2 |cos psi|^3 h(chi(psi))> (Eq. 6
+ *                  written for the instantaneous field).
+ *                  The gradient and batched entry points support variant 0.
  */
 typedef struct qs_laser {
     double lambda_um, a0, w0_um, tau_fs;
     double dx_um, dy_um, delay_fs, div_prefactor;
-    int32_t envelope, model, n_phase, focus;
+    int32_t envelope, model, n_phase, variant;
 } qs_laser;
 
 /*

@@ -42,7 +42,7 @@ class QsoLaser(C.Structure):
                 ("tau_fs", C.c_double), ("dx_um", C.c_double), ("dy_um", C.c_double),
                 ("delay_fs", C.c_double), ("div_prefactor", C.c_double),
                 ("envelope", C.c_int32), ("model", C.c_int32), ("n_phase", C.c_int32),
-                ("focus", C.c_int32)]
+                ("variant", C.c_int32)]
 
 
 class QsoBeam(C.Structure):
@@ -85,6 +85,7 @@ def lib():
             L.qso_gaunt.argtypes = [C.c_double, _DP, _DP]
             L.qso_h2.argtypes = [C.c_double]
             L.qso_h2.restype = C.c_double
+            L.qso_cycle_factors.argtypes = [C.c_double, _DP, _DP, _DP]
             L.qso_qfp_rates.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double, _DP]
             L.qso_qfp_integrate.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_double, _DP, _DP]
@@ -111,7 +112,7 @@ def lib():
 def _laser(p) -> QsoLaser:
     return QsoLaser(p.lambda_um, p.a0, p.w0_um, p.tau_fs, p.dx_um, p.dy_um, p.delay_fs,
                     p.div_prefactor, int(p.envelope), int(p.model), int(p.n_phase),
-                    int(getattr(p, "focus", 0)))
+                    int(getattr(p, "variant", 0)))
 
 
 def _beam(b) -> QsoBeam:
@@ -170,6 +171,13 @@ def gaunt(chi: float):
 
 def h2(chi: float) -> float:
     return float(lib().qso_h2(float(chi)))
+
+
+def cycle_factors(chi: float):
+    """Cycle-resolved Gaunt and diffusion factors (G, S = 2G + chi G', H)."""
+    G, S, H = C.c_double(), C.c_double(), C.c_double()
+    lib().qso_cycle_factors(float(chi), C.byref(G), C.byref(S), C.byref(H))
+    return G.value, S.value, H.value
 
 
 def qfp_rates(laser, mu: float, A: float, aS_scale: float = 1.0) -> dict:

@@ -25,6 +25,9 @@
  *                        transport closed form; library ODE solve)
  *   qso_eval / qso_scatter  pinned (Table 1 / Table 2 closed forms,
  *                        zero intensity, weight conservation, symmetries)
+ *   qso_cycle_factors    pinned (small-chi limits and large-chi tails in
+ *                        closed form; adaptive quadrature; the cycle mean
+ *                        of the exact quantum-synchrotron power)
  *   per-cell focus       pinned (adaptive quadrature of Eq. 3's exponent
  *                        along the electron's path; reduces to the crossing
  *                        focus for a straight path in a long focus)
@@ -58,7 +61,8 @@ typedef struct {
     int32_t envelope;      /* 0 = Gaussian, 1 = sin^2 (field envelope)     */
     int32_t model;         /* 0 = classical LL (Eq. 3), 1 = quantum FP     */
     int32_t n_phase;       /* phase cells of the integration               */
-    int32_t focus;         /* 0 = Eq. 2 at the crossing, 1 = in every cell */
+    int32_t variant;       /* bit 0: Eq. 2 in every cell (else at the
+                              crossing); bit 1: cycle-resolved chi       */
 } qso_laser;
 
 typedef struct {
@@ -200,6 +204,72 @@ double qso_h2(double chi) {
 }
 
 /* ------------------------------------------------------------------------
+ * n-point Gauss-Legendre rule on [a, b]: nodes are the roots of P_n, found
+ * by Newton's method from cos(pi (i + 3/4)/(n + 1/2)); the weights are
+ * 2/((1 - z^2) P_n'(z)^2), scaled to the interval.
+ * ------------------------------------------------------------------------ */
+static void qso_gauss_legendre(int n, double a, double b, double* x, double* w) {
+    double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(QSO_PI * (i + 0.75) / (n + 0.5)), pn = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            pn = p0;
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = pn / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = mid - half * z;
+        x[n - 1 - i] = mid + half * z;
+        w[i] = w[n - 1 - i] = 2.0 * half / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Cycle-resolved chi (variant bit 1).  Over one cycle of a linearly
+ * polarised field the instantaneous chi is sqrt2 chi |cos psi| (chi: the
+ * value at the rms field).  The classical power follows the field squared
+ * (2 cos^2 psi times its cycle mean) and the classical second moment its
+ * cube (2 sqrt2 |cos psi|^3), so the Fokker-Planck rates take
+ *   G(chi) = < 2 cos^2 psi g(sqrt2 chi |cos psi|) >
+ *   S(chi) = 2 G + chi dG/dchi
+ *   H(chi) = < 2 sqrt2 |cos psi|^3 h(sqrt2 chi |cos psi|) >
+ * in place of g, 2g + chi g' and h.  Cycle means over the quarter period
+ * (the integrands are smooth there) with a 128-point Gauss-Legendre rule
+ * (relative error below 1e-13 for chi <= 40; the branch point of g where
+ * 1 + 1.7 sqrt2 chi cos psi = 0 nears the interval as chi grows).
+ * ------------------------------------------------------------------------ */
+#define QSO_CYC_N 128
+void qso_cycle_factors(double chi, double* G, double* S, double* H) {
+    static double x[QSO_CYC_N], w[QSO_CYC_N];
+    static int ready = 0;
+    if (!ready) {
+        qso_gauss_legendre(QSO_CYC_N, 0.0, 0.5 * QSO_PI, x, w);
+        ready = 1;
+    }
+    qso_sum sg = {0.0, 0.0}, sd = {0.0, 0.0}, sh = {0.0, 0.0};
+    for (int k = 0; k < QSO_CYC_N; ++k) {
+        double cp = cos(x[k]);
+        double ci = sqrt(2.0) * chi * cp;
+        double g, gp;
+        qso_gaunt(ci, &g, &gp);
+        qso_add(&sg, w[k] * 2.0 * cp * cp * g);
+        qso_add(&sd, w[k] * 2.0 * cp * cp * gp * sqrt(2.0) * cp);
+        qso_add(&sh, w[k] * 2.0 * sqrt(2.0) * cp * cp * cp * qso_h2(ci));
+    }
+    double nrm = 2.0 / QSO_PI;            /* mean over the quarter period */
+    *G = nrm * qso_val(&sg);
+    *S = 2.0 * (*G) + chi * nrm * qso_val(&sd);
+    *H = nrm * qso_val(&sh);
+}
+
+/* ------------------------------------------------------------------------
  * Fokker-Planck moment rates per unit laser phase (Eq. 6 and the
  * Fokker-Planck regime the paper names), for an electron of mean energy mu
  * in a cycle-averaged field of envelope amplitude A (linear polarisation:
@@ -210,15 +280,21 @@ double qso_h2(double chi) {
  * aS_scale multiplies a_S (1 = physical; huge = classical limit).
  * out[0..3] = D1, dD1, D2, chi
  * ------------------------------------------------------------------------ */
-static void qso_rates_c(const double* c, double mu, double A, double aS_scale, double* out) {
+static void qso_rates_c(const double* c, double mu, double A, double aS_scale, int cycle,
+                        double* out) {
     double Rc = c[3], aS = c[4] * aS_scale;
     double chi = 2.0 * mu * (A / sqrt(2.0)) / aS;
-    double g, gp;
-    qso_gaunt(chi, &g, &gp);
-    double h2 = qso_h2(chi);
+    double g, gp, h2, sf;
+    if (cycle) {
+        qso_cycle_factors(chi, &g, &sf, &h2);
+    } else {
+        qso_gaunt(chi, &g, &gp);
+        h2 = qso_h2(chi);
+        sf = 2.0 * g + chi * gp;
+    }
     double K = (2.0 / 3.0) * Rc * A * A;
     out[0] = -K * mu * mu * g;
-    out[1] = -K * mu * (2.0 * g + chi * gp);
+    out[1] = -K * mu * sf;
     out[2] = (55.0 / (16.0 * sqrt(3.0))) * K * mu * mu * mu * chi * h2;
     out[3] = chi;
 }
@@ -226,7 +302,7 @@ static void qso_rates_c(const double* c, double mu, double A, double aS_scale, d
 void qso_qfp_rates(const qso_laser* L, double mu, double A, double aS_scale, double* out) {
     double c[10];
     qso_constants(L, c);
-    qso_rates_c(c, mu, A, aS_scale, out);
+    qso_rates_c(c, mu, A, aS_scale, (L->variant & 2) != 0, out);
 }
 
 /* ------------------------------------------------------------------------
@@ -263,7 +339,7 @@ static void qso_qfp_run(const qso_laser* L, const double* a_cell, double aeff, d
         double du_mid = du + 0.5 * h * K * g_prev;
         double mu = gamma0 / (1.0 + gamma0 * du_mid);
         double r[4];
-        qso_rates_c(c, mu, A, aS_scale, r);
+        qso_rates_c(c, mu, A, aS_scale, (L->variant & 2) != 0, r);
         double g = -r[0] / (K * mu * mu);          /* Gaunt factor at chi_j */
         if (!(K > 0.0)) g = 1.0;
         double lam = 2.0 * r[1];
@@ -360,7 +436,7 @@ static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bin
     double aeff = L->a0 / sqrt(q) * exp(-rho2 / (L->w0_um * L->w0_um * q));
 
     double mu, V;
-    if (!L->focus) {
+    if (!(L->variant & 1)) {
         if (L->model == 0) {
             /* classical LL closed form, Eq. 3 with a0 -> a_eff */
             mu = gamma0 / (1.0 + cRR * gamma0 * aeff * aeff);
@@ -684,7 +760,7 @@ int qso_grad(const qso_laser* L, const qso_beam* B, const qso_bins* bins, double
              const double* dL_dS, double* grad8, double* smooth, qso_moments* m) {
     int nb = bins->n_bins;
     if (nb <= 0 || bins->log_spaced || !(sigma_bins > 0)) return 1;
-    if (L->focus) return 1;                /* gradient of the crossing focus only */
+    if (L->variant) return 1;              /* gradient of variant 0 only          */
     qd* S = (qd*)calloc((size_t)nb, sizeof(qd));
     if (!S) return 1;
     for (int k = 0; k < nb; ++k) S[k] = qd_c(0.0);

@@ -35,7 +35,7 @@ class qs_laser(C.Structure):
                 ("tau_fs", C.c_double), ("dx_um", C.c_double), ("dy_um", C.c_double),
                 ("delay_fs", C.c_double), ("div_prefactor", C.c_double),
                 ("envelope", C.c_int32), ("model", C.c_int32), ("n_phase", C.c_int32),
-                ("focus", C.c_int32)]
+                ("variant", C.c_int32)]
 
 
 class qs_beam(C.Structure):
@@ -144,7 +144,7 @@ def lib():
 def make_laser(p: _inputs.Laser) -> qs_laser:
     return qs_laser(p.lambda_um, p.a0, p.w0_um, p.tau_fs, p.dx_um, p.dy_um, p.delay_fs,
                     p.div_prefactor, int(p.envelope), int(p.model), int(p.n_phase),
-                    int(p.focus))
+                    int(p.variant))
 
 
 def make_beam(b: _inputs.Beam) -> qs_beam:

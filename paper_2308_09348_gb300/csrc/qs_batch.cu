@@ -53,8 +53,8 @@ __global__ void k_bsetup(const BatchArgs a) {
   // shared samples (parameter sweep) when no offsets are given
   const int64_t o0 = a.offsets ? a.offsets[s] : 0;
   const int64_t o1 = a.offsets ? a.offsets[s + 1] : a.samples.n;
-  // (batched shots use the crossing focus; a per-cell-focus shot is flagged)
-  bool ok = check_laser(L) == QS_OK && L.focus == QS_FOCUS_CROSSING &&
+  // (batched shots use model variant 0; a shot with another one is flagged)
+  bool ok = check_laser(L) == QS_OK && L.variant == 0 &&
             check_beam(B) == QS_OK && check_bins(b) == QS_OK &&
             o0 >= 0 && o1 >= o0 && o1 <= a.samples.n &&
             (L.model != QS_MODEL_QFP || L.n_phase <= a.max_phase);

@@ -51,8 +51,9 @@ QS_HD int32_t check_laser(const qs_laser& L) {
     return QS_ERR_INVALID_ARG;
   if (L.envelope != QS_ENV_GAUSS && L.envelope != QS_ENV_SIN2) return QS_ERR_INVALID_ARG;
   if (L.model != QS_MODEL_LL && L.model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
-  if (L.focus != QS_FOCUS_CROSSING && L.focus != QS_FOCUS_PER_CELL) return QS_ERR_INVALID_ARG;
-  if ((L.model == QS_MODEL_QFP || L.focus == QS_FOCUS_PER_CELL) &&
+  if (L.variant & ~(QS_VARIANT_CELL_FOCUS | QS_VARIANT_CYCLE_CHI)) return QS_ERR_INVALID_ARG;
+  if ((L.variant & QS_VARIANT_CYCLE_CHI) && L.model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
+  if ((L.model == QS_MODEL_QFP || (L.variant & QS_VARIANT_CELL_FOCUS)) &&
       (L.n_phase < 1 || L.n_phase > kMaxPhase))
     return QS_ERR_INVALID_ARG;
   return QS_OK;
@@ -131,7 +132,7 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   p.cRR = (2.0 / 3.0) * Rc * intG2;
   p.cK = (2.0 / 3.0) * Rc;
   p.cchi = kSqrt2 / aS;
-  p.n_phase = (L.model == QS_MODEL_QFP || L.focus == QS_FOCUS_PER_CELL) ? L.n_phase : 1;
+  p.n_phase = (L.model == QS_MODEL_QFP || (L.variant & QS_VARIANT_CELL_FOCUS)) ? L.n_phase : 1;
   p.h = (hi - lo) / (double)p.n_phase;
   p.win_lo = lo;
   p.Phi = Phi;
@@ -139,7 +140,8 @@ QS_HD void derive_params(Params& p, const qs_laser& L, const qs_beam& B, const q
   p.kappa_s = L.div_prefactor * kSqrt2OverPi;
   p.envelope = L.envelope;
   p.model = L.model;
-  p.focus = L.focus;
+  p.focus = (L.variant & QS_VARIANT_CELL_FOCUS) ? 1 : 0;
+  p.cycle = (L.variant & QS_VARIANT_CYCLE_CHI) ? 1 : 0;
   p.phic = L.envelope == QS_ENV_GAUSS ? 0.0 : 0.5 * PhiT;   // pulse peak on the window axis
   p.inv2k = 1.0 / (2.0 * k);
 

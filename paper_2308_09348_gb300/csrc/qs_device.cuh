@@ -34,7 +34,7 @@ struct Params {
   int32_t envelope, model, n_phase, focus;   // focus: 0 crossing, 1 per cell
   // beam
   double gmean, spread, glo, gspan, sx, sy, sz, div, bdx, bdy;
-  int32_t flat, pad1;
+  int32_t flat, cycle;     // cycle: cycle-resolved chi (QS_VARIANT_CYCLE_CHI)
   // samples
   int64_t n;
   const void* xi[8];
@@ -199,7 +199,7 @@ __device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// Per-cell focus (laser focus == QS_FOCUS_PER_CELL): Eq. 2 evaluated in
+// Per-cell focus (QS_VARIANT_CELL_FOCUS): Eq. 2 evaluated in
 // every phase cell at the electron's position there.  Between the crossing
 // of the pulse peak and the midpoint of cell j the electron (velocity
 // c(theta_x, theta_y, -1)) meets the counter-moving phase at twice the laser

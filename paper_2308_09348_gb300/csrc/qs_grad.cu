@@ -554,7 +554,7 @@ extern "C" int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam,
   if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
       (st = validate_samples(samples)) || (st = validate_bins(bins)))
     return st;
-  if (laser->focus != QS_FOCUS_CROSSING) return QS_ERR_UNSUPPORTED;
+  if (laser->variant != 0) return QS_ERR_UNSUPPORTED;
   int prec, wbits, block, grid, sms;
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (block > 256) block = 256;

@@ -559,8 +559,8 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < pl.ws_bytes)
     return QS_ERR_WORKSPACE;
   const bool qfp = laser->model == QS_MODEL_QFP;
-  const bool cells = qfp || laser->focus == QS_FOCUS_PER_CELL;
-  const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, laser->focus == QS_FOCUS_PER_CELL,
+  const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
+  const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, (laser->variant & QS_VARIANT_CELL_FOCUS) != 0,
                             samples->w != nullptr, block);
 
   Params p;
@@ -605,7 +605,7 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   int64_t tiles = (samples->n + 255) / 256;
   int g = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  const bool qfp = laser->model == QS_MODEL_QFP, loc = laser->focus == QS_FOCUS_PER_CELL;
+  const bool qfp = laser->model == QS_MODEL_QFP, loc = (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
   const size_t tb = (qfp || loc)
                         ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
                         : 0;
@@ -782,9 +782,9 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   HostPipe* pipe = nullptr;
   if ((st = host_pipe(&pipe))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
-  const bool cells = qfp || laser->focus == QS_FOCUS_PER_CELL;
+  const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
   const Smem sm = smem_plan(hp.pl, prec, cells ? laser->n_phase : 0,
-                            laser->focus == QS_FOCUS_PER_CELL, h_samples->w != nullptr, block);
+                            (laser->variant & QS_VARIANT_CELL_FOCUS) != 0, h_samples->w != nullptr, block);
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Params p;

@@ -27,7 +27,7 @@ import numpy as np
 
 ENV_GAUSS, ENV_SIN2 = 0, 1
 MODEL_LL, MODEL_QFP = 0, 1
-FOCUS_CROSSING, FOCUS_PER_CELL = 0, 1
+VAR_CELL_FOCUS, VAR_CYCLE_CHI = 1, 2   # model variants (bit flags)
 
 GAMMA_PER_GEV = 1.0e3 / 0.51099895  # 1 GeV in units of m_e c^2
 
@@ -45,7 +45,7 @@ class Laser:
     delay_fs: float = 0.0         # pulse-peak arrival at the focal plane
     n_phase: int = 512
     div_prefactor: float = 1.0
-    focus: int = FOCUS_CROSSING     # Eq. 2 at the crossing, or in every phase cell
+    variant: int = 0               # VAR_* flags; 0 = the paper's model as read
 
 
 @dataclass(frozen=True)

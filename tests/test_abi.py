@@ -68,8 +68,8 @@ def _call(lib, laser=None, beam=None, samples=None, bins=None, exe=None, moments
 def test_host_validation_rejects_bad_descriptors(lib):
     bad_lasers = [I.Laser(w0_um=0.0), I.Laser(lambda_um=-1.0), I.Laser(tau_fs=float("nan")),
                   I.Laser(model=I.MODEL_QFP, n_phase=0), I.Laser(model=I.MODEL_QFP, n_phase=5000),
-                  I.Laser(envelope=7), I.Laser(a0=-1.0), I.Laser(focus=2),
-                  I.Laser(focus=I.FOCUS_PER_CELL, n_phase=0)]
+                  I.Laser(envelope=7), I.Laser(a0=-1.0), I.Laser(variant=4), I.Laser(variant=I.VAR_CYCLE_CHI),
+                  I.Laser(variant=I.VAR_CELL_FOCUS, n_phase=0)]
     for L in bad_lasers:
         assert _call(lib, laser=B.make_laser(L)) == B.QS_ERR_INVALID_ARG, L
     bad_beams = [I.Beam(gamma_mean=0.0), I.Beam(sigma_x_um=-1.0),

@@ -146,14 +146,14 @@ def test_eval_float64_streams_and_missing_optional_streams():
                                        (I.MODEL_QFP, I.ENV_SIN2), (I.MODEL_LL, I.ENV_SIN2)])
 def test_per_cell_focus_eval_matches_oracle(prec, model, env):
     n = 1500
-    wl, L, xi = cfg2(n, model=model, envelope=env, n_phase=256, focus=I.FOCUS_PER_CELL)
+    wl, L, xi = cfg2(n, model=model, envelope=env, n_phase=256, variant=I.VAR_CELL_FOCUS)
     xt, _ = dev(xi)
     rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
     torch.cuda.synchronize()
     ref = oracle.evaluate(L, wl.beam, wl.bins, f64(xi))
     compare_samples(rec, ref, prec, wl.bins)
     # the variant changes the result at this focus (z_R = 24.5 um, 40 fs delay)
-    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    Lx = I.Laser(**{**L.__dict__, "variant": 0})
     refx = oracle.evaluate(Lx, wl.beam, wl.bins, f64(xi))
     assert np.max(np.abs(refx["mu"] / ref["mu"] - 1)) > 1e-3
 
@@ -162,7 +162,7 @@ def test_per_cell_focus_eval_matches_oracle(prec, model, env):
 @pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
 def test_per_cell_focus_scatter_matches_oracle_and_records(prec, model):
     n = 3001
-    wl, L, xi = cfg2(n, model=model, n_phase=128, focus=I.FOCUS_PER_CELL)
+    wl, L, xi = cfg2(n, model=model, n_phase=128, variant=I.VAR_CELL_FOCUS)
     w = I.rng(17).uniform(0.25, 2.0, n).astype(np.float32)
     xt, wt = dev(xi, w)
     out = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision=prec)
@@ -180,7 +180,7 @@ def test_per_cell_focus_scatter_matches_oracle_and_records(prec, model):
 
 def test_per_cell_focus_gradient_is_unsupported_and_batch_shot_flagged():
     n = 300
-    wl, L, xi = cfg2(n, n_phase=64, focus=I.FOCUS_PER_CELL)
+    wl, L, xi = cfg2(n, n_phase=64, variant=I.VAR_CELL_FOCUS)
     xt, _ = dev(xi)
     out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32")
     with pytest.raises(QsError):
@@ -188,7 +188,7 @@ def test_per_cell_focus_gradient_is_unsupported_and_batch_shot_flagged():
                           torch.zeros(13, dtype=torch.float64), None, precision="f32", out=out)
     bw = I.batch_shots(3, seed=21, log10_range=(2.0, 2.5), n_phase=64, n_bins=32)
     lasers = list(bw.lasers)
-    lasers[1] = I.Laser(**{**lasers[1].__dict__, "focus": I.FOCUS_PER_CELL})
+    lasers[1] = I.Laser(**{**lasers[1].__dict__, "variant": I.VAR_CELL_FOCUS})
     offsets = np.zeros(4, dtype=np.int64)
     offsets[1:] = np.cumsum(bw.counts)
     xs = [torch.from_numpy(a).cuda() for a in I.sample_streams(int(offsets[-1]), 22,

@@ -207,6 +207,89 @@ def test_fp_rates_absolute_vs_exact_spectrum(exact_moments):
         assert abs(r["dD1"] / fd - 1) < 1e-6
 
 
+# cycle-resolved chi: Gaunt and diffusion factors averaged over the cycle
+
+def _cos_power_mean(p):
+    """Cycle mean of |cos psi|^p in closed form (a Beta integral)."""
+    from scipy.special import gamma
+    return gamma((p + 1) / 2) / (math.sqrt(math.pi) * gamma(p / 2 + 1))
+
+
+def test_cycle_factors_limits_and_tails():
+    """chi -> 0: G = <2 cos^2> = 1, S = 2, H = 2 sqrt2 <|cos|^3>; large chi:
+    g ~ chi^-4/3 and h ~ chi^-7/3 make G/g(sqrt2 chi) and H/h(sqrt2 chi)
+    tend to 2 <|cos|^(2/3)> and 2 sqrt2 <|cos|^(2/3)>."""
+    G, S, H = oracle.cycle_factors(0.0)
+    assert abs(G - 1) < 1e-14 and abs(S - 2) < 1e-14
+    assert abs(H / (2 * math.sqrt(2) * _cos_power_mean(3)) - 1) < 1e-14
+    chi = 1e6
+    G, S, H = oracle.cycle_factors(chi)
+    r = 2 * _cos_power_mean(2 / 3)
+    assert abs(G / oracle.gaunt(math.sqrt(2) * chi)[0] / r - 1) < 0.01
+    assert abs(H / oracle.h2(math.sqrt(2) * chi) / (math.sqrt(2) * r) - 1) < 0.01
+    # S = 2G + chi G' -> (2 - 4/3) G in the power-law tail
+    assert abs(S / G - 2 / 3) < 0.01
+
+
+def test_cycle_factors_vs_adaptive_quadrature_and_differences():
+    for chi in (1e-3, 0.1, 1.0, 5.0, 40.0):
+        G, S, H = oracle.cycle_factors(chi)
+        qg = quad(lambda p: 2 * math.cos(p) ** 2 * oracle.gaunt(math.sqrt(2) * chi * math.cos(p))[0],
+                  0, math.pi / 2, epsabs=0, epsrel=1e-13)[0] * 2 / math.pi
+        qh = quad(lambda p: 2 * math.sqrt(2) * math.cos(p) ** 3 *
+                  oracle.h2(math.sqrt(2) * chi * math.cos(p)), 0, math.pi / 2, epsabs=0,
+                  epsrel=1e-13)[0] * 2 / math.pi
+        assert abs(G / qg - 1) < 1e-12 and abs(H / qh - 1) < 1e-12, chi
+        hh = chi * 1e-5
+        dG = (oracle.cycle_factors(chi + hh)[0] - oracle.cycle_factors(chi - hh)[0]) / (2 * hh)
+        assert abs(S / (2 * G + chi * dG) - 1) < 1e-8, chi
+
+
+def test_cycle_gaunt_vs_cycle_mean_of_exact_power():
+    """The cycle-resolved mean loss equals the cycle mean of the exact
+    quantum-synchrotron power (to the 2 % of the Gaunt fit)."""
+    import warnings
+    xs, ws = np.polynomial.legendre.leggauss(8)
+    ps = (xs + 1) * math.pi / 4
+    for chi in (0.3, 3.0):
+        acc = 0.0
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            for p, w in zip(ps, ws):
+                ci = math.sqrt(2) * chi * math.cos(p)
+                m1, _ = _exact_moments(ci)
+                g_exact = m1 / (math.sqrt(3) * math.pi) / ((2 / 3) * ci ** 2)
+                acc += w * math.pi / 4 * 2 * math.cos(p) ** 2 * g_exact
+        G_exact = acc * 2 / math.pi
+        assert abs(oracle.cycle_factors(chi)[0] / G_exact - 1) < 0.03, chi
+
+
+def test_cycle_resolved_integration_vs_library_ode_solver():
+    """QFP with cycle-resolved chi: the phase sum converges (second order) to
+    a DOP853 solve with the same rates; the variant lowers the loss."""
+    a0, g0 = 30.0, 4000.0
+    Lc = I.Laser(a0=a0, model=I.MODEL_QFP, n_phase=512, variant=I.VAR_CYCLE_CHI)
+    c = oracle.constants(Lc)
+    Phi = c["Phi"]
+
+    def f(phi, y):
+        r = oracle.qfp_rates(Lc, y[0], a0 * math.exp(-2 * math.log(2) * (phi / Phi) ** 2))
+        return [r["D1"], 2 * r["dD1"] * y[1] + r["D2"]]
+
+    sol = solve_ivp(f, (c["win_lo"], c["win_hi"]), [g0, 0.0], method="DOP853", rtol=1e-11,
+                    atol=1e-9)
+    mu_ref, V_ref = sol.y[0, -1], sol.y[1, -1]
+    errs = []
+    for N in (256, 512, 1024):
+        mu, V = oracle.qfp_integrate(I.Laser(**{**Lc.__dict__, "n_phase": N}), a0, g0)
+        errs.append((abs(mu / mu_ref - 1), abs(V / V_ref - 1)))
+    assert errs[1][0] < 2e-5 and errs[1][1] < 2e-4
+    for (m1, v1), (m2, v2) in zip(errs, errs[1:]):
+        assert 3.0 < m1 / m2 < 5.0 and 3.0 < v1 / v2 < 5.0
+    mu_std, _ = oracle.qfp_integrate(I.Laser(a0=a0, model=I.MODEL_QFP, n_phase=512), a0, g0)
+    assert mu_ref > mu_std * 1.005
+
+
 def test_spread_below_eq9_bound_for_long_pulses():
     """Eq. 9 bounds sigma_f^2 for long pulses; the FP model stays below it
     and within an order of magnitude of it."""
@@ -324,9 +407,9 @@ def _path_sample(L, B, v):
     return g0, psi, a, (t_lo, t_hi), c
 
 
-def _focus_case(model, n_phase, focus=I.FOCUS_PER_CELL, w0=2.5, div=5e-3):
+def _focus_case(model, n_phase, variant=I.VAR_CELL_FOCUS, w0=2.5, div=5e-3):
     L = I.Laser(a0=20.0, w0_um=w0, tau_fs=30.0, dx_um=1.5, dy_um=-0.7, delay_fs=40.0,
-                model=model, n_phase=n_phase, focus=focus)
+                model=model, n_phase=n_phase, variant=variant)
     B = I.Beam(gamma_mean=4000.0, rel_spread=0.0, sigma_x_um=3.0, sigma_y_um=3.0,
                sigma_z_um=10.0, div_rad=div)
     V = np.array([[0.3, -0.8, 1.2, 0.0, 1.0, -0.5, 0, 0],
@@ -342,7 +425,7 @@ def test_per_cell_focus_ll_vs_time_domain_quadrature():
     dpsi/dt; and differs from the crossing focus for these geometries."""
     L, B, V = _focus_case(I.MODEL_LL, 4096, w0=1.5)
     rec = oracle.evaluate(L, B, None, [V[:, k].copy() for k in range(8)])
-    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    Lx = I.Laser(**{**L.__dict__, "variant": 0})
     rec_x = oracle.evaluate(Lx, B, None, [V[:, k].copy() for k in range(8)])
     for s, v in enumerate(V):
         g0, psi, a, (t0, t1), c = _path_sample(L, B, v)
@@ -392,7 +475,7 @@ def test_per_cell_focus_reduces_to_crossing_for_straight_path_in_long_focus(mode
     the same in every cell, so both focus readings agree (LL to the midpoint
     rule and window truncation of the G^2 integral, QFP exactly)."""
     L, B, V = _focus_case(model, 2048, w0=250.0, div=0.0)
-    Lx = I.Laser(**{**L.__dict__, "focus": I.FOCUS_CROSSING})
+    Lx = I.Laser(**{**L.__dict__, "variant": 0})
     xi = [V[:, k].copy() for k in range(8)]
     r, rx = oracle.evaluate(L, B, None, xi), oracle.evaluate(Lx, B, None, xi)
     tol = 1e-7 if model == I.MODEL_LL else 1e-9
