@@ -61,6 +61,11 @@ struct Params {
   double smooth_pref;      // 1 / (sigma sqrt(2 pi))
   double smooth_c;         // log2(e) / (2 sigma^2)
   unsigned long long* acc_smooth;
+  // cycle-resolved chi: Gauss-Legendre cos(psi_k) and weights (FP64 path),
+  // Hermite tables of (G, S) and H over u = log2(1 + chi/chi_s) (FP32 path)
+  const double* cyc_gl;
+  const float4* cyc_a;
+  const float2* cyc_b;
   // FP32 path, log-spaced bins: t = lg2(gamma) * log2_scale - log2_offset
   float log2_scale, log2_offset;
   // FP32 copies of the per-sample constants, each the double above rounded
@@ -199,6 +204,99 @@ __device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Model variant bits of the kernels' VAR template argument.
+constexpr int kVarCell = 1;    // per-cell focus
+constexpr int kVarCycle = 2;   // cycle-resolved chi
+
+// Cycle-resolved chi (QS_VARIANT_CYCLE_CHI).  Over one cycle of a linearly
+// polarised field chi(psi) = sqrt2 chi |cos psi|; the rates take the cycle
+// means G = <2 cos^2 g(chi(psi))>, S = 2G + chi G', H = <2 sqrt2 |cos|^3
+// h(chi(psi))> in place of g, 2g + chi g', h.  FP64 path: a 128-point
+// Gauss-Legendre rule over the quarter period; FP32 path: cubic Hermite
+// interpolation in u = log2(1 + chi/chi_s) on kCycN nodes tabulated (in
+// FP64) from the same rule: relative error below 1e-8 for chi up to
+// chi_s (2^U - 1) = 327 (chi_s resolves the steep start of h at 1/12.93).
+constexpr int kCycGL = 128;
+constexpr int kCycN = 512;
+constexpr double kCycChiS = 0.02;
+constexpr double kCycU = 14.0;
+constexpr double kCycDu = kCycU / (kCycN - 1);
+
+// Closed forms of the fits (Eq. 6 reading): g, g', g'' and h, h'.
+__device__ __forceinline__ void gaunt_d(double x, double& g, double& g1, double& g2) {
+  const double L = log1p(1.7 * x), r = 1.0 / (1.0 + 1.7 * x);
+  const double B = 1.0 + 4.8 * (1.0 + x) * L + 2.44 * x * x;
+  const double B1 = 4.8 * L + 8.16 * (1.0 + x) * r + 4.88 * x;
+  const double B2 = 8.16 * r - 5.712 * r * r + 4.88;
+  const double iB = 1.0 / B;
+  g = pow(B, -2.0 / 3.0);
+  g1 = (-2.0 / 3.0) * g * iB * B1;
+  g2 = (10.0 / 9.0) * g * iB * iB * B1 * B1 - (2.0 / 3.0) * g * iB * B2;
+}
+__device__ __forceinline__ void h2_d(double x, double& h, double& h1) {
+  const double L = log1p(12.93 * x);
+  const double B = 1.0 + (1.0 + 4.1 * x) * L + 4.75 * x * x;
+  const double B1 = 4.1 * L + 12.93 * (1.0 + 4.1 * x) / (1.0 + 12.93 * x) + 9.5 * x;
+  h = pow(B, -7.0 / 6.0);
+  h1 = (-7.0 / 6.0) * h * B1 / B;
+}
+
+// FP64 path: G, S, H and the chi-derivatives G', S' = 3G' + chi G'', H'
+// (the derivatives only where asked).  gl: cos psi_k, then the weights with
+// the 2/pi of the cycle mean folded in.
+__device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, double chi,
+                                                double& G, double& S, double& H,
+                                                double* dG = nullptr, double* dS = nullptr,
+                                                double* dH = nullptr) {
+  const double r2 = 1.4142135623730950488;
+  double sg = 0.0, sg1 = 0.0, sg2 = 0.0, sh = 0.0, sh1 = 0.0;
+  for (int k = 0; k < kCycGL; ++k) {
+    const double c = gl[k], w = gl[kCycGL + k];
+    const double x = r2 * chi * c, c2 = 2.0 * c * c;
+    double g, g1, g2, h, h1;
+    gaunt_d(x, g, g1, g2);
+    h2_d(x, h, h1);
+    sg += w * c2 * g;
+    sg1 += w * c2 * g1 * r2 * c;
+    sg2 += w * c2 * g2 * 2.0 * c * c;
+    sh += w * r2 * c * c2 * h;
+    sh1 += w * r2 * c * c2 * h1 * r2 * c;
+  }
+  G = sg;
+  S = 2.0 * sg + chi * sg1;
+  H = sh;
+  if (dG) *dG = sg1;
+  if (dS) *dS = 3.0 * sg1 + chi * sg2;
+  if (dH) *dH = sh1;
+}
+
+// FP32 path: one lane's cubic Hermite lookup.  A[n] = {G, G_u du, S, S_u du},
+// B[n] = {H, H_u du} at u_n = n du (the derivatives in u, times the spacing).
+__device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A,
+                                             const float2* __restrict__ B, float chi, float& G,
+                                             float& S, float& H) {
+  const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
+  const float x = fminf(fmaxf(__fmul_rn(u, (float)(1.0 / kCycDu)), 0.f),
+                        (float)(kCycN - 1) - 1e-3f);
+  // floor without a conversion instruction: x + 2^23 rounds x to an integer
+  const float xm = __fadd_rn(x, 8388608.f);
+  float r = __fsub_rn(xm, 8388608.f);
+  int idx = __float_as_int(xm) - 0x4B000000;
+  if (r > x) {
+    r = __fsub_rn(r, 1.f);
+    idx -= 1;
+  }
+  const float t = __fsub_rn(x, r), t2 = __fmul_rn(t, t);
+  const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));       // 3t^2 - 2t^3
+  const float h11 = __fmaf_rn(t2, t, -t2);                         // t^3 - t^2
+  const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);              // t - 2t^2 + t^3
+  const float4 a0 = A[idx], a1 = A[idx + 1];
+  const float2 b0 = B[idx], b1 = B[idx + 1];
+  G = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, __fsub_rn(a1.x, a0.x), a0.x)));
+  S = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
+  H = __fmaf_rn(h11, b1.y, __fmaf_rn(h10, b0.y, __fmaf_rn(h01, __fsub_rn(b1.x, b0.x), b0.x)));
+}
+
 // Per-cell focus (QS_VARIANT_CELL_FOCUS): Eq. 2 evaluated in
 // every phase cell at the electron's position there.  Between the crossing
 // of the pulse peak and the midpoint of cell j the electron (velocity
@@ -234,8 +332,9 @@ __device__ __forceinline__ T a_cell(const Params& p, const Path<T>& g, T s) {
 //   D2 = (55/(16 sqrt3)) K mu^3 chi h2.
 // Returns du = 1/mu_f - 1/gamma0 and V_f.  FP64 path: written as the
 // equations read.
-// LOC: per-cell focus, the peak amplitude a_j of cell j from the path.
-template <bool LOC>
+// VAR: kVarCell -- the peak amplitude a_j of cell j from the path;
+// kVarCycle -- cycle-resolved Gaunt and diffusion factors.
+template <int VAR>
 __device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
                                               double a, double g0, double& du_out,
                                               double& V_out, const Path<double>& path) {
@@ -248,31 +347,37 @@ __device__ __forceinline__ void qfp_integrate(const Params& p, const double* __r
   const int N = p.n_phase;
 #pragma unroll 2
   for (int j = 0; j < N; ++j) {
-    const double aj = LOC ? a_cell<double>(p, path, cell_shift(p, j)) : a;
+    const double aj = (VAR & kVarCell) ? a_cell<double>(p, path, cell_shift(p, j)) : a;
     const double A = __dmul_rn(aj, sG[j]);
     const double K = __dmul_rn(__dmul_rn(cK, A), A);
     const double hK = __dmul_rn(h, K);
     const double dum = __fma_rn(__dmul_rn(0.5, hK), gprev, du);
     const double mu = g0 / __fma_rn(g0, dum, 1.0);
     const double chi = __dmul_rn(__dmul_rn(cchi, mu), A);
-    // Gaunt factor and chi g'(chi)
-    const double x1 = __fma_rn(1.7, chi, 1.0);
-    const double L1 = __dmul_rn(LN2, log2(x1));
-    const double opc = __dadd_rn(1.0, chi);
-    const double B = __fma_rn(__dmul_rn(4.8, opc), L1, __fma_rn(__dmul_rn(2.44, chi), chi, 1.0));
-    const double t = exp2(__dmul_rn(-1.0 / 3.0, log2(B)));     // B^(-1/3)
-    const double g = __dmul_rn(t, t);
-    const double dB = __fma_rn(4.8, L1, __fma_rn(4.8 * 1.7, opc / x1, __dmul_rn(4.88, chi)));
-    const double chig1 =
-        __dmul_rn(__dmul_rn(__dmul_rn(-2.0 / 3.0, g), __dmul_rn(__dmul_rn(t, t), t)),
-                  __dmul_rn(dB, chi));
-    // second-moment factor
-    const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
-    const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
-    const double h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
+    double g, sf, h2;                       // g, 2g + chi g', h (or their cycle means)
+    if constexpr ((VAR & kVarCycle) != 0) {
+      cycle_factors_d(p.cyc_gl, chi, g, sf, h2);
+    } else {
+      // Gaunt factor and chi g'(chi)
+      const double x1 = __fma_rn(1.7, chi, 1.0);
+      const double L1 = __dmul_rn(LN2, log2(x1));
+      const double opc = __dadd_rn(1.0, chi);
+      const double B = __fma_rn(__dmul_rn(4.8, opc), L1, __fma_rn(__dmul_rn(2.44, chi), chi, 1.0));
+      const double t = exp2(__dmul_rn(-1.0 / 3.0, log2(B)));     // B^(-1/3)
+      g = __dmul_rn(t, t);
+      const double dB = __fma_rn(4.8, L1, __fma_rn(4.8 * 1.7, opc / x1, __dmul_rn(4.88, chi)));
+      const double chig1 =
+          __dmul_rn(__dmul_rn(__dmul_rn(-2.0 / 3.0, g), __dmul_rn(__dmul_rn(t, t), t)),
+                    __dmul_rn(dB, chi));
+      sf = __fma_rn(2.0, g, chig1);
+      // second-moment factor
+      const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
+      const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
+      h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
+    }
     // updates
     du = __fma_rn(hK, g, du);
-    const double lam = __dmul_rn(__dmul_rn(__dmul_rn(-2.0, K), mu), __fma_rn(2.0, g, chig1));
+    const double lam = __dmul_rn(__dmul_rn(__dmul_rn(-2.0, K), mu), sf);
     const double D2 = __dmul_rn(__dmul_rn(__dmul_rn(c55, K), __dmul_rn(__dmul_rn(mu, mu), mu)),
                                 __dmul_rn(chi, h2));
     const double r = __fma_rn(lam, V, D2);
@@ -309,13 +414,18 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
   return make_float2(M<float>::rsqrt(x.x), M<float>::rsqrt(x.y));
 }
 
-// LOC: per-cell focus; the table then holds {G, G, s_j, s_j} and the two
-// samples' paths give the per-cell amplitudes (same operations as a_cell).
-template <bool LOC>
+// VAR & kVarCell: per-cell focus; the table then holds {G, G, s_j, s_j} and
+// the two samples' paths give the per-cell amplitudes (same operations as
+// a_cell).  VAR & kVarCycle: cycle-resolved factors from the Hermite tables
+// cA, cB (shared memory).
+template <int VAR>
 __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
                                                     const float4* __restrict__ tab, float2 a,
                                                     float2 g0, float2& du_out, float2& V_out,
-                                                    const Path<float>& P0, const Path<float>& P1) {
+                                                    const Path<float>& P0, const Path<float>& P1,
+                                                    const float4* __restrict__ cA = nullptr,
+                                                    const float2* __restrict__ cB = nullptr) {
+  constexpr bool LOC = (VAR & kVarCell) != 0;
   const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
   const float2 C816 = f2((float)(4.8 * 1.7));
   const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
@@ -354,20 +464,26 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
     const float2 dum = fma2(hK, gph, du);
     const float2 mu = mul2(g0, rcpx2(fma2(g0, dum, ONE)));
     const float2 chi = mul2(cg, mu);
-    const float2 chi2 = mul2(chi, chi);
-    // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
-    const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
-    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
-    const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
-    const float2 g = mul2(t, t);
-    // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
-    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
-    const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
-    const float2 s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
-    // second-moment factor h2 = B2^(-7/6)
-    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
-    const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
-    const float2 h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
+    float2 g, s, h2;
+    if constexpr ((VAR & kVarCycle) != 0) {
+      cycle_lookup(cA, cB, chi.x, g.x, s.x, h2.x);
+      cycle_lookup(cA, cB, chi.y, g.y, s.y, h2.y);
+    } else {
+      const float2 chi2 = mul2(chi, chi);
+      // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
+      const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
+      const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
+      const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
+      g = mul2(t, t);
+      // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
+      const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
+      const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
+      s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
+      // second-moment factor h2 = B2^(-7/6)
+      const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
+      const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
+      h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
+    }
     // updates
     du = fma2(hK, g, du);
     const float2 hKmu = mul2(hK, mu);
@@ -427,10 +543,12 @@ __device__ __forceinline__ T focus(const Params& p, int64_t i, T& gamma0, T& thx
 // One beam sample through the model, in the paper's order (rows a1-a6).
 // FP64 path: one sample through the model selected at compile time by QFP
 // (the table is unused by LL).
-// LOC: per-cell focus (LL: Eq. 3's exponent summed cell by cell).
-template <bool QFP, bool LOC = false>
+// VAR: model variant bits (per-cell focus; LL then sums Eq. 3's exponent
+// cell by cell; cycle-resolved chi).
+template <bool QFP, int VAR = 0>
 __device__ __forceinline__ Sample eval_sample(const Params& p, const double* __restrict__ tab,
                                               int64_t i) {
+  constexpr bool LOC = (VAR & kVarCell) != 0;
   Sample s;
   double gamma0, thx, thy, mu, V = 0.0;
   Path<double> path;
@@ -448,7 +566,7 @@ __device__ __forceinline__ Sample eval_sample(const Params& p, const double* __r
     mu = gamma0 / __fma_rn(gamma0, __dmul_rn(__dmul_rn(p.h, p.cK), acc), 1.0);
   } else {
     double du;
-    qfp_integrate<LOC>(p, tab, a, gamma0, du, V, path);
+    qfp_integrate<VAR>(p, tab, a, gamma0, du, V, path);
     mu = gamma0 / __fma_rn(gamma0, du, 1.0);
   }
   double theta_e = 0.0, gout = mu, tx = thx;
@@ -519,16 +637,19 @@ __device__ __forceinline__ void finish_f32(const Params& p, int64_t i, float g0,
 
 // FP32 QFP path: samples i0 and i1 through the model together (the phase
 // integration runs packed).
-template <bool LOC = false>
+template <int VAR = 0>
 __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
                                                   int64_t i0, int64_t i1, SampleF& s0,
-                                                  SampleF& s1) {
+                                                  SampleF& s1, const float4* cA = nullptr,
+                                                  const float2* cB = nullptr) {
+  constexpr bool LOC = (VAR & kVarCell) != 0;
   float g0f, g1f, tx0, ty0, tx1, ty1;
   Path<float> P0{}, P1{};
   const float a0 = focus<float>(p, i0, g0f, tx0, ty0, LOC ? &P0 : nullptr);
   const float a1 = focus<float>(p, i1, g1f, tx1, ty1, LOC ? &P1 : nullptr);
   float2 du, V;
-  qfp_integrate_f32x2<LOC>(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V, P0, P1);
+  qfp_integrate_f32x2<VAR>(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V, P0, P1,
+                           cA, cB);
   finish_f32(p, i0, g0f, a0, tx0, ty0, du.x, V.x, s0);
   finish_f32(p, i1, g1f, a1, tx1, ty1, du.y, V.y, s1);
 }
@@ -578,18 +699,19 @@ __device__ __forceinline__ SampleF eval_ll_f32_cells(const Params& p,
   return s;
 }
 
-// One sample of the path selected by T, QFP and LOC (FP32 QFP samples are
+// One sample of the path selected by T, QFP and VAR (FP32 QFP samples are
 // normally evaluated in pairs; a single one runs as a pair with itself).
-template <typename T, bool QFP, bool LOC = false>
+template <typename T, bool QFP, int VAR = 0>
 __device__ __forceinline__ typename SampleT<T>::type eval_one(
-    const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i) {
+    const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i,
+    const float4* cA = nullptr, const float2* cB = nullptr) {
   if constexpr (sizeof(T) == 8) {
-    return eval_sample<QFP, LOC>(p, reinterpret_cast<const double*>(tab), i);
+    return eval_sample<QFP, VAR>(p, reinterpret_cast<const double*>(tab), i);
   } else if constexpr (QFP) {
     SampleF s0, s1;
-    eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1);
+    eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1, cA, cB);
     return s0;
-  } else if constexpr (LOC) {
+  } else if constexpr ((VAR & kVarCell) != 0) {
     return eval_ll_f32_cells(p, reinterpret_cast<const float4*>(tab), i);
   } else {
     return eval_ll_f32(p, i);

@@ -119,13 +119,17 @@ void make_plan(Plan& pl, const qs_bins* b, int block, int grid_req, int sms) {
 // atomics (negligible traffic) and the freed shared memory buys occupancy;
 // the LL model is memory-bound and keeps them in shared memory if they fit.
 // cells: phase-table entries (QFP or the per-cell focus, 0 otherwise);
-// cell_focus: the per-cell focus (histograms always global).
-Smem smem_plan(const Plan& pl, int precision, int cells, bool cell_focus, bool weighted,
-               int block) {
+// variant: the model variant bits (histograms always global for a variant;
+// FP32 cycle-resolved chi adds its Hermite tables).
+Smem smem_plan(const Plan& pl, int precision, int cells, int variant, bool weighted, int block) {
   Smem sm;
+  const bool cell_focus = variant != 0;
   // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} or
-  // {G, G, s_j, s_j} (FP32 path)
-  const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16);
+  // {G, G, s_j, s_j} (FP32 path); then the cycle tables
+  const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16) +
+                     ((variant & QS_VARIANT_CYCLE_CHI) && precision == QS_F32
+                          ? (size_t)kCycN * (sizeof(float4) + sizeof(float2))
+                          : 0);
   const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
   const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
   sm.hist = !cell_focus && cells < 32 && tab + red + hist <= (size_t)kSmemLimit &&
@@ -159,22 +163,53 @@ using namespace detail;
 // K1: fused evaluation + histograms + moment partials.  T: per-sample
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
-// LOC: the per-cell focus.
+// VAR: model variant bits (kVarCell, kVarCycle).
 // Register budget per thread (blocks of up to 512 threads): FP32 QFP 64
 // (two 256-thread CTAs or more per SM for the MUFU-bound loop), FP32
 // classical 80 (three 256-thread CTAs per SM keep enough loads in flight
-// for the HBM-bound path), FP32 per-cell focus 80 (the paths of two
-// samples stay live in the loop), FP64 128.
-template <typename T, bool QFP, bool LOC>
-constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && !LOC) ? 64 : 80);
+// for the HBM-bound path), FP32 variants 80, FP64 128.
+template <typename T, bool QFP, int VAR>
+constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 64 : 80);
 
-template <typename T, typename H, bool QFP, bool SHIST, bool LOC>
-__global__ void __maxnreg__((kScatterRegs<T, QFP, LOC>)) k_scatter(const Params p) {
+// Shared memory of the phase table and, FP32 cycle-resolved chi, the cycle
+// tables behind it.
+template <typename T, bool QFP, int VAR>
+__device__ __forceinline__ size_t table_bytes(const Params& p) {
   using TT = typename Tab<T>::type;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const size_t tab_bytes =
-      (QFP || LOC) ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
+  constexpr bool cells = QFP || (VAR & kVarCell);
+  constexpr bool cyc = sizeof(T) == 4 && (VAR & kVarCycle);
+  return (cells ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0) +
+         (cyc ? (size_t)kCycN * (sizeof(float4) + sizeof(float2)) : 0);
+}
+template <typename T, bool QFP, int VAR>
+__device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem,
+                                            const float4** cA, const float2** cB) {
+  using TT = typename Tab<T>::type;
   TT* tab = reinterpret_cast<TT*>(smem);
+  if (QFP || (VAR & kVarCell))
+    for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  if constexpr (sizeof(T) == 4 && (VAR & kVarCycle)) {
+    float4* A = reinterpret_cast<float4*>(smem + (((size_t)p.n_phase * sizeof(TT) + 15) &
+                                                  ~(size_t)15));
+    float2* B = reinterpret_cast<float2*>(A + kCycN);
+    for (int j = threadIdx.x; j < kCycN; j += blockDim.x) {
+      A[j] = p.cyc_a[j];
+      B[j] = p.cyc_b[j];
+    }
+    *cA = A;
+    *cB = B;
+  }
+}
+
+template <typename T, typename H, bool QFP, bool SHIST, int VAR>
+__global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params p) {
+  using TT = typename Tab<T>::type;
+  constexpr bool LOC = (VAR & kVarCell) != 0;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t tab_bytes = table_bytes<T, QFP, VAR>(p);
+  TT* tab = reinterpret_cast<TT*>(smem);
+  const float4* cA = nullptr;
+  const float2* cB = nullptr;
   double* red = reinterpret_cast<double*>(smem + tab_bytes);
   H* sh = reinterpret_cast<H*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumMom * sizeof(double));
   const int64_t nspec = p.n_bins > 0 ? (int64_t)p.n_bins + 2 : 0;
@@ -189,8 +224,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, LOC>)) k_scatter(const Params 
   unsigned long long* ssm = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(sh) + hist_bytes);
   unsigned long long* hsm = nsm ? (p.smooth_in_smem ? ssm : p.acc_smooth) : nullptr;
 
-  if (QFP || LOC)
-    for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  load_tables<T, QFP, VAR>(p, smem, &cA, &cB);
   if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
   if (nsm && p.smooth_in_smem)
@@ -214,7 +248,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, LOC>)) k_scatter(const Params 
       bool ok0 = false, ok1 = false;
       if (i0 < p.n) {
         SampleF s0, s1;
-        eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+        eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA, cB);
         ok0 = accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
         if (i1 != i0)
           ok1 = accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
@@ -261,7 +295,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, LOC>)) k_scatter(const Params 
       typename DepT<T>::type d;
       bool ok = false;
       if (ii < p.n) {
-        const auto s = eval_one<T, QFP, LOC>(p, tab, ii);
+        const auto s = eval_one<T, QFP, VAR>(p, tab, ii, cA, cB);
         ok = accumulate<T, H, SHIST>(p, s, ii, acc, hs, hm, ha, nspec, nmap, naeff);
         dep_set(d, s);
       }
@@ -411,13 +445,14 @@ __device__ __forceinline__ void write_record(const Params& p, const qs_sample_ou
 }
 
 // K0: per-sample records; the same per-sample code path as k_scatter.
-template <typename T, bool QFP, bool LOC>
+template <typename T, bool QFP, int VAR>
 __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   TT* tab = reinterpret_cast<TT*>(smem);
-  if (QFP || LOC)
-    for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  const float4* cA = nullptr;
+  const float2* cB = nullptr;
+  load_tables<T, QFP, VAR>(p, smem, &cA, &cB);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -425,30 +460,106 @@ __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
     for (int64_t k = t0; 2 * k < p.n; k += stride) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
       SampleF s0, s1;
-      eval_pair_f32_qfp<LOC>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+      eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA, cB);
       write_record(p, o, s0, i0);
       if (i1 != i0) write_record(p, o, s1, i1);
     }
   } else {
     for (int64_t i = t0; i < p.n; i += stride)
-      write_record(p, o, eval_one<T, QFP, LOC>(p, tab, i), i);
+      write_record(p, o, eval_one<T, QFP, VAR>(p, tab, i, cA, cB), i);
   }
 }
 
 namespace {
 
+// Cycle-resolved chi: the Gauss-Legendre rule and the FP32 Hermite tables,
+// built once per device by k_cycle_setup (FP64) and kept for the process.
+__device__ double g_cyc_gl[2 * kCycGL];
+__device__ float4 g_cyc_a[kCycN];
+__device__ float2 g_cyc_b[kCycN];
+
+// One CTA of kCycGL/2 threads: thread i finds the i-th root z of P_n (n =
+// kCycGL) by Newton's method from cos(pi (i + 3/4)/(n + 1/2)) and its
+// mirror; psi = (pi/4)(1 -+ z) on the quarter period, weight 2/((1 - z^2)
+// P_n'(z)^2) times pi/4 times the 2/pi of the cycle mean.  Then the table
+// nodes u_n = n du, chi_n = chi_s (2^u_n - 1): G, S, H with their
+// u-derivatives (dchi/du = ln2 (chi + chi_s)) times du.
+__global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
+  __shared__ double gl[2 * kCycGL];
+  const int n = kCycGL, i = threadIdx.x;
+  double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double p0 = 1.0, p1 = 0.0;
+    for (int k = 1; k <= n; ++k) {
+      const double p2 = p1;
+      p1 = p0;
+      p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+    }
+    dp = n * (z * p0 - p1) / (z * z - 1.0);
+    const double dz = p0 / dp;
+    z -= dz;
+    if (fabs(dz) < 1e-16) break;
+  }
+  const double q = 0.25 * 3.14159265358979323846, w = 1.0 / ((1.0 - z * z) * dp * dp);
+  gl[i] = cos(q * (1.0 - z));
+  gl[n - 1 - i] = cos(q * (1.0 + z));
+  gl[n + i] = w;
+  gl[2 * n - 1 - i] = w;
+  __syncthreads();
+  for (int k = i; k < 2 * n; k += blockDim.x) g_cyc_gl[k] = gl[k];
+  for (int m = i; m < kCycN; m += blockDim.x) {
+    const double u = m * kCycDu, chi = kCycChiS * (exp2(u) - 1.0);
+    const double dchi = 0.69314718055994530942 * (chi + kCycChiS) * kCycDu;
+    double G, S, H, dG, dS, dH;
+    cycle_factors_d(gl, chi, G, S, H, &dG, &dS, &dH);
+    g_cyc_a[m] = make_float4((float)G, (float)(dG * dchi), (float)S, (float)(dS * dchi));
+    g_cyc_b[m] = make_float2((float)H, (float)(dH * dchi));
+  }
+}
+
+std::mutex g_cyc_mu;
+bool g_cyc_ready[64] = {};
+
+// Points p at the cycle tables, building them on first use on this device
+// (one launch on `st`, then a wait for it; not allowed while `st` is being
+// captured into a graph).
+int32_t cycle_tables(Params& p, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_cyc_mu);
+  if (!g_cyc_ready[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cuda_fail();
+    if (cap != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
+    k_cycle_setup<<<1, kCycGL / 2, 0, st>>>();
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return cuda_fail();
+    g_cyc_ready[dev] = true;
+  }
+  void *gl = nullptr, *a = nullptr, *b = nullptr;
+  if (cudaGetSymbolAddress(&gl, g_cyc_gl) != cudaSuccess ||
+      cudaGetSymbolAddress(&a, g_cyc_a) != cudaSuccess ||
+      cudaGetSymbolAddress(&b, g_cyc_b) != cudaSuccess)
+    return cuda_fail();
+  p.cyc_gl = static_cast<const double*>(gl);
+  p.cyc_a = static_cast<const float4*>(a);
+  p.cyc_b = static_cast<const float2*>(b);
+  return QS_OK;
+}
+
 // k_eval with its dynamic shared memory (phase table) allowed up to the
 // largest table.
-template <typename T, bool QFP, bool LOC>
+template <typename T, bool QFP, int VAR>
 int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
                     const qs_sample_out& o) {
-  auto kern = k_eval<T, QFP, LOC>;
+  auto kern = k_eval<T, QFP, VAR>;
   static bool attr[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
   if (dev >= 0 && dev < 64 && !attr[dev]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMaxPhase * (int)sizeof(float4)) != cudaSuccess)
+                             kMaxPhase * (int)sizeof(float4) +
+                                 kCycN * (int)(sizeof(float4) + sizeof(float2))) != cudaSuccess)
       return cuda_fail();
     attr[dev] = true;
   }
@@ -456,10 +567,10 @@ int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
   return QS_OK;
 }
 
-template <typename T, typename H, bool QFP, bool SHIST, bool LOC = false>
+template <typename T, typename H, bool QFP, bool SHIST, int VAR = 0>
 int32_t launch_scatter_t(const Params& p, int block, size_t smem, int sms, int grid_req, int gmax,
                          cudaStream_t st, int* grid_out, const qs_exec* ex) {
-  auto kern = k_scatter<T, H, QFP, SHIST, LOC>;
+  auto kern = k_scatter<T, H, QFP, SHIST, VAR>;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
@@ -491,9 +602,14 @@ int32_t launch_scatter_prec(const Params& p, bool qfp, const Smem& sm, int block
   typedef unsigned int U32;
   typedef unsigned long long U64;
   const size_t b = sm.bytes;
-  if (p.focus) {           // per-cell focus: global histograms (smem_plan)
-    if (qfp) return launch_scatter_t<T, U32, true, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
-    return launch_scatter_t<T, U32, false, false, true>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  // model variants: global histograms (smem_plan)
+  if (p.cycle && p.focus)
+    return launch_scatter_t<T, U32, true, false, 3>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  if (p.cycle)
+    return launch_scatter_t<T, U32, true, false, 2>(p, block, b, sms, grid_req, gmax, st, g, ex);
+  if (p.focus) {
+    if (qfp) return launch_scatter_t<T, U32, true, false, 1>(p, block, b, sms, grid_req, gmax, st, g, ex);
+    return launch_scatter_t<T, U32, false, false, 1>(p, block, b, sms, grid_req, gmax, st, g, ex);
   }
   if (qfp) {
     if (!sm.hist) return launch_scatter_t<T, U32, true, false>(p, block, b, sms, grid_req, gmax, st, g, ex);
@@ -560,7 +676,7 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
     return QS_ERR_WORKSPACE;
   const bool qfp = laser->model == QS_MODEL_QFP;
   const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
-  const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, (laser->variant & QS_VARIANT_CELL_FOCUS) != 0,
+  const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, laser->variant,
                             samples->w != nullptr, block);
 
   Params p;
@@ -574,6 +690,7 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.hist_in_smem = sm.hist ? 1 : 0;
   p.smooth_in_smem = sm.smooth ? 1 : 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
 
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return cuda_fail();
   int g = 1;
@@ -605,21 +722,34 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   int64_t tiles = (samples->n + 255) / 256;
   int g = (int)(tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  const bool qfp = laser->model == QS_MODEL_QFP, loc = (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
-  const size_t tb = (qfp || loc)
-                        ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
-                        : 0;
+  const bool qfp = laser->model == QS_MODEL_QFP;
+  const int var = laser->variant;
+  if ((var & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
+  const size_t tb = ((qfp || (var & QS_VARIANT_CELL_FOCUS))
+                         ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
+                         : 0) +
+                    ((var & QS_VARIANT_CYCLE_CHI) && prec == QS_F32
+                         ? (size_t)kCycN * (sizeof(float4) + sizeof(float2))
+                         : 0);
   int32_t est;
   if (prec == QS_F64) {
-    if (loc) est = qfp ? launch_eval<double, true, true>(g, tb, cs, p, *out)
-                       : launch_eval<double, false, true>(g, tb, cs, p, *out);
-    else est = qfp ? launch_eval<double, true, false>(g, tb, cs, p, *out)
-                   : launch_eval<double, false, false>(g, tb, cs, p, *out);
+    switch (var) {
+      case 1: est = qfp ? launch_eval<double, true, 1>(g, tb, cs, p, *out)
+                        : launch_eval<double, false, 1>(g, tb, cs, p, *out); break;
+      case 2: est = launch_eval<double, true, 2>(g, tb, cs, p, *out); break;
+      case 3: est = launch_eval<double, true, 3>(g, tb, cs, p, *out); break;
+      default: est = qfp ? launch_eval<double, true, 0>(g, tb, cs, p, *out)
+                         : launch_eval<double, false, 0>(g, tb, cs, p, *out);
+    }
   } else {
-    if (loc) est = qfp ? launch_eval<float, true, true>(g, tb, cs, p, *out)
-                       : launch_eval<float, false, true>(g, tb, cs, p, *out);
-    else est = qfp ? launch_eval<float, true, false>(g, tb, cs, p, *out)
-                   : launch_eval<float, false, false>(g, tb, cs, p, *out);
+    switch (var) {
+      case 1: est = qfp ? launch_eval<float, true, 1>(g, tb, cs, p, *out)
+                        : launch_eval<float, false, 1>(g, tb, cs, p, *out); break;
+      case 2: est = launch_eval<float, true, 2>(g, tb, cs, p, *out); break;
+      case 3: est = launch_eval<float, true, 3>(g, tb, cs, p, *out); break;
+      default: est = qfp ? launch_eval<float, true, 0>(g, tb, cs, p, *out)
+                         : launch_eval<float, false, 0>(g, tb, cs, p, *out);
+    }
   }
   if (est) return est;
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
@@ -783,12 +913,13 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   if ((st = host_pipe(&pipe))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
   const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
-  const Smem sm = smem_plan(hp.pl, prec, cells ? laser->n_phase : 0,
-                            (laser->variant & QS_VARIANT_CELL_FOCUS) != 0, h_samples->w != nullptr, block);
+  const Smem sm = smem_plan(hp.pl, prec, cells ? laser->n_phase : 0, laser->variant,
+                            h_samples->w != nullptr, block);
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Params p;
   fill_params(p, laser, beam, h_samples, bins, wbits);
+  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
   p.acc_spec = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_spec);
   p.acc_map = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_map);
   p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_aeff);

@@ -178,6 +178,33 @@ def test_per_cell_focus_scatter_matches_oracle_and_records(prec, model):
     np.testing.assert_array_equal(out1.spectrum.cpu().numpy(), hist.astype(np.float64))
 
 
+@pytest.mark.parametrize("prec,n,n_phase", [("f64", 300, 64), ("f32", 2500, 256)])
+@pytest.mark.parametrize("variant", [I.VAR_CYCLE_CHI, I.VAR_CYCLE_CHI | I.VAR_CELL_FOCUS])
+def test_cycle_resolved_chi_eval_matches_oracle(prec, n, n_phase, variant):
+    """Cycle-resolved Gaunt and diffusion factors: FP64 by the same
+    128-point cycle quadrature as the oracle, FP32 by the Hermite tables."""
+    wl, L, xi = cfg2(n, model=I.MODEL_QFP, n_phase=n_phase, variant=variant)
+    xt, _ = dev(xi)
+    rec = qs_eval_samples(L, wl.beam, xt, wl.bins, precision=prec)
+    torch.cuda.synchronize()
+    ref = oracle.evaluate(L, wl.beam, wl.bins, f64(xi))
+    compare_samples(rec, ref, prec, wl.bins)
+    # the variant matters for this beam (chi ~ 1 at the peak)
+    L0 = I.Laser(**{**L.__dict__, "variant": variant & I.VAR_CELL_FOCUS})
+    ref0 = oracle.evaluate(L0, wl.beam, wl.bins, f64(xi))
+    assert np.max(np.abs(ref0["mu"] / ref["mu"] - 1)) > 1e-3
+
+
+def test_cycle_resolved_chi_scatter_matches_oracle():
+    n = 2001
+    wl, L, xi = cfg2(n, model=I.MODEL_QFP, n_phase=64, variant=I.VAR_CYCLE_CHI)
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32")
+    torch.cuda.synchronize()
+    ref = oracle.scatter(L, wl.beam, wl.bins, f64(xi))
+    compare_scatter(out, ref, "f32", float(n))
+
+
 def test_per_cell_focus_gradient_is_unsupported_and_batch_shot_flagged():
     n = 300
     wl, L, xi = cfg2(n, n_phase=64, variant=I.VAR_CELL_FOCUS)
