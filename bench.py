@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--grad-n", type=int, default=1 << 24)
     ap.add_argument("--broadband-n", type=int, default=1 << 27)
     ap.add_argument("--ll-n", type=int, default=1 << 26)
-    ap.add_argument("--no-cell", action="store_true", help="skip the per-cell focus measurement")
+    ap.add_argument("--no-cell", action="store_true",
+                    help="skip the model-variant measurements (per-cell focus, cycle-resolved chi)")
     ap.add_argument("--cell-n", type=int, default=1 << 24)
     return ap.parse_args()
 
@@ -287,15 +288,16 @@ CELL_MUFU_SLOTS_PER_STEP = QFP_MUFU_SLOTS_PER_STEP + 1 + 0.5
 CELL_FMA_OPS_PER_STEP = QFP_FMA_OPS_PER_STEP + 14
 
 
-def bench_cell_focus(dev, rank, n=1 << 24, steps=3):
-    """The bench beam and laser with Eq. 2 evaluated in every phase cell
-    along the electron's path (quantum model, 512 cells, FP32)."""
+def bench_variant(dev, rank, variant, n=1 << 24, steps=3):
+    """The bench beam and laser with a model variant: Eq. 2 evaluated in
+    every phase cell along the electron's path, or the Gaunt and diffusion
+    factors averaged over the laser cycle (quantum model, 512 cells, FP32)."""
     import torch
     from dataclasses import replace
     from paper_2308_09348_gb300 import binding as B
     from paper_2308_09348_gb300 import inputs as I
     wl = I.full_qfp(n)
-    L = replace(wl.laser, variant=I.VAR_CELL_FOCUS)
+    L = replace(wl.laser, variant=variant)
     gen = torch.Generator(device=dev)
     gen.manual_seed(wl.seed + 7919 * rank)
     xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
@@ -315,13 +317,15 @@ def bench_cell_focus(dev, rank, n=1 << 24, steps=3):
     t_mufu = CELL_MUFU_SLOTS_PER_STEP * steps_total / peak_mufu
     t_fma = CELL_FMA_OPS_PER_STEP * steps_total / peak_fma
     t = kms * 1e-3
-    return {"metric": "beam-sample evals/s", "value": n / t, "unit": "samples/s",
-            "kernel_ms": kms, "n_samples": n, "n_phase": L.n_phase, "focus": "per cell",
-            "roofline": {"bound": "alu", "pipe": "mufu" if t_mufu >= t_fma else "fma",
-                         "achieved": CELL_MUFU_SLOTS_PER_STEP * steps_total / t / 1e12,
-                         "peak": peak_mufu / 1e12, "unit": "Top/s",
-                         "frac": max(t_mufu, t_fma) / t},
-            "workload": wl.name + "_cellfocus"}
+    line = {"metric": "beam-sample evals/s", "value": n / t, "unit": "samples/s",
+            "kernel_ms": kms, "n_samples": n, "n_phase": L.n_phase,
+            "workload": wl.name + ("_cellfocus" if variant == I.VAR_CELL_FOCUS else "_cyclechi")}
+    if variant == I.VAR_CELL_FOCUS:
+        line["roofline"] = {"bound": "alu", "pipe": "mufu" if t_mufu >= t_fma else "fma",
+                            "achieved": CELL_MUFU_SLOTS_PER_STEP * steps_total / t / 1e12,
+                            "peak": peak_mufu / 1e12, "unit": "Top/s",
+                            "frac": max(t_mufu, t_fma) / t}
+    return line
 
 
 def bench_batch(dev, rank, steps=3, n_shots=4096):
@@ -568,7 +572,8 @@ def main():
     grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)
     broad = None if args.no_broadband else bench_broadband(dev, rank, args.broadband_n)
     ll = None if args.no_ll else bench_ll(dev, rank, n=args.ll_n)
-    cell = None if args.no_cell else bench_cell_focus(dev, rank, n=args.cell_n)
+    cell = None if args.no_cell else bench_variant(dev, rank, 1, n=args.cell_n)
+    cyc = None if args.no_cell else bench_variant(dev, rank, 2, n=args.cell_n)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -593,7 +598,7 @@ def main():
                 "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
-                "cell_focus": cell,
+                "cell_focus": cell, "cycle_chi": cyc,
                 "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:
