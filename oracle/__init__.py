@@ -86,6 +86,13 @@ def lib():
             L.qso_h2.argtypes = [C.c_double]
             L.qso_h2.restype = C.c_double
             L.qso_cycle_factors.argtypes = [C.c_double, _DP, _DP, _DP]
+            L.qso_bessel_pair.argtypes = [C.c_double, _DP, _DP]
+            L.qso_photon_rate.argtypes = [C.c_double] * 4
+            L.qso_photon_rate.restype = C.c_double
+            L.qso_photon_spectrum.argtypes = [C.POINTER(QsoLaser), C.POINTER(QsoBeam),
+                                              C.POINTER(QsoBins), C.c_int64, C.POINTER(_DP),
+                                              _DP, _DP]
+            L.qso_photon_spectrum.restype = C.c_int
             L.qso_qfp_rates.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double, _DP]
             L.qso_qfp_integrate.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_double, _DP, _DP]
@@ -270,3 +277,30 @@ def grad(laser, beam, bins, sigma_bins, xi, w=None, dL_dm=None, dL_dS=None) -> d
     if rc != 0:
         raise ValueError("oracle gradient: bad arguments (uniform bins, sigma_bins > 0)")
     return dict(grad=g, smooth=S, moments={k: getattr(m, k) for k in MOMENT_NAMES})
+
+
+def bessel_pair(y: float):
+    """(K_{2/3}(y), integral of K_{1/3} from y to infinity)."""
+    a, b = C.c_double(), C.c_double()
+    lib().qso_bessel_pair(float(y), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def photon_rate(aS: float, mu: float, chi: float, eps: float) -> float:
+    """Photons per unit phase and unit photon energy (m c^2) of an electron of
+    mean energy mu at chi (LCFA quantum-synchrotron spectrum)."""
+    return lib().qso_photon_rate(float(aS), float(mu), float(chi), float(eps))
+
+
+def photon_spectrum(laser, beam, pbins, xi, w=None) -> np.ndarray:
+    """Beam photon spectrum dN/deps at the centres of the photon-energy bins
+    ``pbins`` (n_bins, lo, hi, log_spaced; eps in m c^2)."""
+    n = next(len(a) for a in xi if a is not None)
+    arrs, ptrs = _streams(xi, n)
+    w64 = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(int(pbins.n_bins))
+    rc = lib().qso_photon_spectrum(C.byref(_laser(laser)), C.byref(_beam(beam)),
+                                   C.byref(_bins(pbins)), n, ptrs, _ptr(w64), _ptr(out))
+    if rc != 0:
+        raise ValueError("photon spectrum needs the quantum model and valid bins")
+    return out

@@ -28,6 +28,11 @@
  *   qso_cycle_factors    pinned (small-chi limits and large-chi tails in
  *                        closed form; adaptive quadrature; the cycle mean
  *                        of the exact quantum-synchrotron power)
+ *   qso_bessel_pair      pinned (scipy's modified Bessel functions and
+ *                        their adaptive integral)
+ *   qso_photon_spectrum  pinned (energy balance with the electrons' loss
+ *                        to the Gaunt fit's accuracy; exact moments of
+ *                        the spectrum; classical synchrotron limit)
  *   per-cell focus       pinned (adaptive quadrature of Eq. 3's exponent
  *                        along the electron's path; reduces to the crossing
  *                        focus for a straight path in a long focus)
@@ -324,9 +329,11 @@ void qso_qfp_rates(const qso_laser* L, double mu, double A, double aS_scale, dou
  * ------------------------------------------------------------------------ */
 /* a_cell[j] (NULL: aeff in every cell) is the local peak amplitude of the
    focus in cell j (the per-cell focus variant). */
+/* mu_cell, chi_cell (optional): the mean energy at each cell midpoint (the
+   state the cell's rates use) and the cell's chi. */
 static void qso_qfp_run(const qso_laser* L, const double* a_cell, double aeff, double gamma0,
                         double V0, double aS_scale, double d2_scale, double* mu_out,
-                        double* V_out) {
+                        double* V_out, double* mu_cell, double* chi_cell) {
     int N = L->n_phase;
     double c[10];
     qso_constants(L, c);
@@ -340,6 +347,8 @@ static void qso_qfp_run(const qso_laser* L, const double* a_cell, double aeff, d
         double mu = gamma0 / (1.0 + gamma0 * du_mid);
         double r[4];
         qso_rates_c(c, mu, A, aS_scale, (L->variant & 2) != 0, r);
+        if (mu_cell) mu_cell[j] = mu;
+        if (chi_cell) chi_cell[j] = r[3];
         double g = -r[0] / (K * mu * mu);          /* Gaunt factor at chi_j */
         if (!(K > 0.0)) g = 1.0;
         double lam = 2.0 * r[1];
@@ -354,7 +363,7 @@ static void qso_qfp_run(const qso_laser* L, const double* a_cell, double aeff, d
 
 void qso_qfp_integrate(const qso_laser* L, double aeff, double gamma0, double V0,
                        double aS_scale, double d2_scale, double* mu_out, double* V_out) {
-    qso_qfp_run(L, NULL, aeff, gamma0, V0, aS_scale, d2_scale, mu_out, V_out);
+    qso_qfp_run(L, NULL, aeff, gamma0, V0, aS_scale, d2_scale, mu_out, V_out, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------
@@ -406,8 +415,9 @@ static void qso_focus_cells(const qso_laser* L, double zs, double xs, double ys,
  *   c t* = (z + c delay)/2,   z* = (z - c delay)/2,
  * transverse position x + theta_x c t*, y + theta_y c t*.
  * ------------------------------------------------------------------------ */
-static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
-                            const double* xi, qso_sample* s) {
+static void qso_sample_eval_x(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+                              const double* xi, qso_sample* s, double* mu_cell,
+                              double* chi_cell) {
     double c[10];
     qso_constants(L, c);
     double zR = c[2], aS = c[4], cRR = c[9];
@@ -442,7 +452,7 @@ static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bin
             mu = gamma0 / (1.0 + cRR * gamma0 * aeff * aeff);
             V = 0.0;
         } else {
-            qso_qfp_integrate(L, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+            qso_qfp_run(L, NULL, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V, mu_cell, chi_cell);
         }
     } else {
         double* a_cell = (double*)malloc(sizeof(double) * (size_t)L->n_phase);
@@ -460,7 +470,7 @@ static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bin
             mu = gamma0 / (1.0 + gamma0 * du);
             V = 0.0;
         } else {
-            qso_qfp_run(L, a_cell, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V);
+            qso_qfp_run(L, a_cell, aeff, gamma0, 0.0, 1.0, 1.0, &mu, &V, mu_cell, chi_cell);
         }
         free(a_cell);
     }
@@ -513,6 +523,11 @@ static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bin
             else s->abin = bins->n_aeff;
         }
     }
+}
+
+static void qso_sample_eval(const qso_laser* L, const qso_beam* B, const qso_bins* bins,
+                            const double* xi, qso_sample* s) {
+    qso_sample_eval_x(L, B, bins, xi, s, NULL, NULL);
 }
 
 /* Per-sample evaluation of n samples; xi[k] points to n doubles (NULL = 0). */
@@ -859,5 +874,91 @@ int qso_smooth_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* b
     }
     for (int k = 0; k < nb; ++k) S[k] = qso_val(&acc[k]);
     free(acc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Photon spectrum (Sec. 4): for every phase cell the electron's mean energy
+ * mu_j and the field give chi_j; the quantum-synchrotron spectrum in the
+ * locally-constant-field approximation at (mu_j, chi_j) is integrated over
+ * the phase and summed over the beam.  The paper names the LCFA spectrum
+ * without printing it; the standard form (Baier-Katkov / Ritus), per unit
+ * time and photon energy fraction xi = eps/gamma (eps in m c^2):
+ *   d2N/(dt dxi) = (alpha m c^2/(sqrt3 pi hbar gamma)) F(xi, chi),
+ *   F = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y),
+ *   y = 2 xi/(3 chi (1 - xi)),  Ki_{1/3}(y) = int_y^inf K_{1/3}(s) ds.
+ * Per unit phase (head-on, the phase advances at 2 omega0, m c^2/(hbar
+ * omega0) = a_S) and per unit eps:
+ *   d2N/(dphi deps) = (alpha a_S/(2 sqrt3 pi mu^2)) F(eps/mu, chi),  eps < mu.
+ * The output is the beam's photon number per unit eps at the bin centres,
+ * S(eps_b) = sum_i w_i sum_j h d2N/(dphi deps)(eps_b; mu_ij, chi_ij).
+ * ------------------------------------------------------------------------ */
+#define QSO_ALPHA 7.2973525693e-3
+
+/* K_{2/3}(y) and Ki_{1/3}(y) from
+ *   K_nu(y) = int_0^inf exp(-y cosh t) cosh(nu t) dt,
+ *   Ki_{1/3}(y) = int_0^inf exp(-y cosh t) cosh(t/3)/cosh(t) dt
+ * (the second by integrating the first over y), trapezoidal rule in t with
+ * step 1/32 until y cosh t > 800: the integrands are analytic in a strip
+ * and decay doubly exponentially, so the rule converges geometrically. */
+void qso_bessel_pair(double y, double* k23, double* ki13) {
+    const double dt = 1.0 / 32.0;
+    qso_sum a = {0.0, 0.0}, b = {0.0, 0.0};
+    for (int k = 0;; ++k) {
+        double t = k * dt, ch = cosh(t), e = exp(-y * ch);
+        double wt = (k == 0) ? 0.5 : 1.0;
+        qso_add(&a, wt * e * cosh(2.0 * t / 3.0));
+        qso_add(&b, wt * e * cosh(t / 3.0) / ch);
+        if (y * ch > 800.0 || t > 60.0) break;
+    }
+    *k23 = dt * qso_val(&a);
+    *ki13 = dt * qso_val(&b);
+}
+
+/* d2N/(dphi deps) at photon energy eps for an electron of mean energy mu
+   at chi (0 for eps <= 0, eps >= mu or chi <= 0). */
+double qso_photon_rate(double aS, double mu, double chi, double eps) {
+    if (!(eps > 0.0) || !(eps < mu) || !(chi > 0.0)) return 0.0;
+    double xi = eps / mu;
+    double y = 2.0 * xi / (3.0 * chi * (1.0 - xi));
+    double k23, ki13;
+    qso_bessel_pair(y, &k23, &ki13);
+    double F = (1.0 - xi + 1.0 / (1.0 - xi)) * k23 - ki13;
+    return QSO_ALPHA * aS / (2.0 * sqrt(3.0) * QSO_PI * mu * mu) * F;
+}
+
+/* Photon spectrum of the beam (quantum model; returns 1 for the classical
+   model or invalid bins).  pb: n_bins, lo, hi, log_spaced of the photon
+   energy axis (eps in m c^2); out: n_bins values at the bin centres. */
+int qso_photon_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* pb, int64_t n,
+                        const double* const* xi, const double* w, double* out) {
+    int nb = pb->n_bins, N = L->n_phase;
+    if (L->model == 0 || nb <= 0 || !(pb->hi > pb->lo) || (pb->log_spaced && !(pb->lo > 0.0)))
+        return 1;
+    double c[10];
+    qso_constants(L, c);
+    double h = (c[8] - c[7]) / (double)N, aS = c[4];
+    double* eps = (double*)malloc(sizeof(double) * (size_t)nb);
+    double* mu_cell = (double*)malloc(sizeof(double) * (size_t)N);
+    double* chi_cell = (double*)malloc(sizeof(double) * (size_t)N);
+    qso_sum* acc = (qso_sum*)calloc((size_t)nb, sizeof(qso_sum));
+    if (!eps || !mu_cell || !chi_cell || !acc) return 1;
+    for (int b = 0; b < nb; ++b)
+        eps[b] = pb->log_spaced ? pb->lo * pow(pb->hi / pb->lo, (b + 0.5) / nb)
+                                : pb->lo + (b + 0.5) * (pb->hi - pb->lo) / nb;
+    for (int64_t i = 0; i < n; ++i) {
+        double v[8];
+        for (int k = 0; k < 8; ++k) v[k] = xi[k] ? xi[k][i] : 0.0;
+        double wi = w ? w[i] : 1.0;
+        if (!(wi >= 0.0) || !isfinite(wi) || wi == 0.0) continue;
+        qso_sample s;
+        qso_sample_eval_x(L, B, NULL, v, &s, mu_cell, chi_cell);
+        if (!isfinite(s.mu)) continue;
+        for (int j = 0; j < N; ++j)
+            for (int b = 0; b < nb; ++b)
+                qso_add(&acc[b], wi * h * qso_photon_rate(aS, mu_cell[j], chi_cell[j], eps[b]));
+    }
+    for (int b = 0; b < nb; ++b) out[b] = qso_val(&acc[b]);
+    free(eps); free(mu_cell); free(chi_cell); free(acc);
     return 0;
 }

@@ -290,6 +290,89 @@ def test_cycle_resolved_integration_vs_library_ode_solver():
     assert mu_ref > mu_std * 1.005
 
 
+# photon spectrum (Sec. 4): LCFA quantum-synchrotron emission along the phase
+
+def test_bessel_pair_vs_library():
+    """K_{2/3} against scipy's modified Bessel function; the tail integral of
+    K_{1/3} against mpmath's (30 digits)."""
+    import mpmath
+    from scipy.special import kv
+    for y in np.logspace(-8, 1.7, 25):
+        k23, _ = oracle.bessel_pair(y)
+        assert abs(k23 / kv(2 / 3, y) - 1) < 1e-13, y
+    mpmath.mp.dps = 30
+    for y in (1e-8, 1e-3, 0.1, 1.0, 5.0, 20.0):
+        _, ki = oracle.bessel_pair(y)
+        ref = mpmath.quad(lambda t: mpmath.besselk(mpmath.mpf(1) / 3, t), [y, y + 1, y + 10,
+                                                                           mpmath.inf])
+        assert abs(ki / float(ref) - 1) < 1e-12, y
+
+
+def _rate_moments(aS, mu, chi):
+    """Photon number and energy emitted per unit phase: integrals of the
+    oracle's rate over eps in (0, mu), in the variable xi = eps/mu."""
+    # in t = ln xi, with break points around the spectrum's scale xi ~ chi
+    lo, hi = math.log(1e-14), math.log(1 - 1e-14)
+    pts = sorted(p for p in (math.log(min(chi, 0.5) * f) for f in (0.01, 0.1, 1.0, 10.0))
+                 if lo < p < hi)
+
+    def r(t):
+        x = math.exp(t)
+        return oracle.photon_rate(aS, mu, chi, x * mu) * mu * x
+    f0 = quad(r, lo, hi, points=pts, limit=400, epsrel=1e-11)[0]
+    f1 = quad(lambda t: r(t) * math.exp(t) * mu, lo, hi, points=pts, limit=400,
+              epsrel=1e-11)[0]
+    return f0, f1
+
+
+def test_photon_rate_classical_limits():
+    """chi -> 0: the emitted energy per phase is the classical loss
+    K mu^2 = alpha a_S chi^2/3 (Larmor, Eq. 3's rate), and the photon number
+    per phase the classical 5 alpha a_S chi/(4 sqrt3 mu) (Gamma-function
+    integrals of K_nu)."""
+    L = I.Laser(lambda_um=0.8)
+    aS = oracle.constants(L)["aS"]
+    mu = 3000.0
+    for chi in (1e-4, 1e-3):
+        n, e = _rate_moments(aS, mu, chi)
+        e_cl = SC.alpha * aS * chi ** 2 / 3
+        n_cl = 5 * SC.alpha * aS * chi / (4 * math.sqrt(3) * mu)
+        assert abs(e / e_cl - 1) < 10 * chi, chi        # O(chi) quantum corrections
+        assert abs(n / n_cl - 1) < 10 * chi, chi
+
+
+def test_photon_rate_energy_equals_gaunt_loss():
+    """At any chi the emitted energy per phase equals the mean loss of the
+    model, K mu^2 g(chi), to the 2 % of the Gaunt fit."""
+    L = I.Laser(lambda_um=0.8)
+    aS = oracle.constants(L)["aS"]
+    mu = 3000.0
+    for chi in (0.03, 0.3, 1.0, 3.0):
+        _, e = _rate_moments(aS, mu, chi)
+        g, _ = oracle.gaunt(chi)
+        assert abs(e / (SC.alpha * aS * chi ** 2 / 3 * g) - 1) < 0.02, chi
+
+
+def test_beam_photon_spectrum_energy_balance():
+    """The energy carried by the beam's photon spectrum equals the energy the
+    electrons lose in the same model (Gaunt-fit accuracy, log-bin
+    quadrature)."""
+    n = 16
+    L = I.Laser(a0=20.0, w0_um=3.0, model=I.MODEL_QFP, n_phase=128)
+    B = I.Beam(gamma_mean=3000.0, rel_spread=0.05, sigma_x_um=1.0, sigma_y_um=1.0,
+               sigma_z_um=2.0, div_rad=0.0)
+    xi = I.sample_streams(n, 31, dtype=np.float64)
+    pb = I.Bins(n_bins=400, lo=1e-6, hi=3500.0, log_spaced=1)
+    S = oracle.photon_spectrum(L, B, pb, xi)
+    edges = pb.lo * (pb.hi / pb.lo) ** (np.arange(401) / 400)
+    centres = np.sqrt(edges[1:] * edges[:-1])
+    e_ph = float(np.sum(S * centres * np.diff(edges)))
+    rec = oracle.evaluate(L, B, None, xi)
+    e_el = float(np.sum(rec["gamma0"] - rec["mu"]))
+    assert e_el > 10 * n                                   # a real interaction
+    assert abs(e_ph / e_el - 1) < 0.03, (e_ph, e_el)
+
+
 def test_spread_below_eq9_bound_for_long_pulses():
     """Eq. 9 bounds sigma_f^2 for long pulses; the FP model stays below it
     and within an order of magnitude of it."""
