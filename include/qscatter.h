@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 4
+#define QS_VERSION 5
 
 typedef enum {
     QS_OK = 0,
@@ -379,6 +379,39 @@ int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
                            const qs_samples* samples, const qs_bins* bins, const qs_exec* exec,
                            double* d_spectrum, double* d_divmap, double* d_aeff_hist,
                            double* d_spec_smooth, qs_moments* d_moments, void* stream);
+
+/*
+ * qs_photon_spectrum: photon spectrum of the beam (Sec. 4: the cumulative
+ * spectrum from the mean energy along the phase and the local field).  In
+ * every phase cell j of the quantum model (QS_MODEL_QFP; variant 0 or
+ * QS_VARIANT_CELL_FOCUS) the electron's mean energy mu_j at the cell midpoint
+ * (the state the cell's rates use) and chi_j give the quantum-synchrotron
+ * emission of a locally constant field, which the paper names; its standard
+ * (Baier-Katkov / Ritus) form per unit phase (head-on: the phase advances at
+ * 2 omega0, and m c^2/(hbar omega0) = a_S) and photon energy eps (m c^2):
+ *   d2N/(dphi deps) = alpha a_S / (2 sqrt3 pi mu^2) F(eps/mu, chi),  eps < mu,
+ *   F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - int_y^inf K_{1/3}(s) ds,
+ *   y = 2 xi / (3 chi (1 - xi)).
+ * Output: the beam's photon number per unit eps at the bin centres,
+ *   S(eps_b) = sum_i w_i sum_j h d2N/(dphi deps)(eps_b; mu_ij, chi_ij),
+ * into d_spectrum (device, pbins->n_bins doubles).  pbins: n_bins 1..512,
+ * 0 <= lo < hi (lo > 0 when log_spaced); its map, a_eff and smoothing
+ * fields are ignored.  Photons with y > 60 (relative weight e^-60) are
+ * dropped.  FP64: the Bessel functions from their integral representations
+ * (slow: for checks); FP32: cubic Hermite tables of log K in log y (relative
+ * error ~3e-7), built on the device by the first FP32 call on that device
+ * (one launch and a wait: make that call before any stream capture; a
+ * capturing first call returns QS_ERR_UNSUPPORTED).  Sums are in a fixed
+ * order (repeatable bit for bit).  Workspace: qs_photon_workspace_bytes.
+ * Errors: QS_ERR_INVALID_ARG (descriptors, the classical model),
+ * QS_ERR_UNSUPPORTED (QS_VARIANT_CYCLE_CHI), QS_ERR_WORKSPACE, QS_ERR_CUDA.
+ */
+size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec* exec, int64_t n);
+
+int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
+                           const qs_samples* samples, const qs_bins* pbins,
+                           const qs_exec* exec, double* d_spectrum, void* d_workspace,
+                           size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -130,6 +130,13 @@ def _lib():
                                            C.POINTER(qs_bins), _VP, C.c_int32,
                                            C.POINTER(qs_exec), _VP, _VP, _VP, C.c_size_t, _VP]
             L.qs_scatter_batch.restype = C.c_int32
+            L.qs_photon_workspace_bytes.argtypes = [C.POINTER(qs_bins), C.POINTER(qs_exec),
+                                                    C.c_int64]
+            L.qs_photon_workspace_bytes.restype = C.c_size_t
+            L.qs_photon_spectrum.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
+                                             C.POINTER(qs_samples), C.POINTER(qs_bins),
+                                             C.POINTER(qs_exec), _VP, _VP, C.c_size_t, _VP]
+            L.qs_photon_spectrum.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -337,6 +344,30 @@ def qs_scatter_noalloc(laser, beam, xi, bins, w=None, precision="f32", out: Outp
                                    _ptr_or_none(out.aeff_hist), _ptr_or_none(out.spec_smooth),
                                    out.moments.data_ptr(), _stream_ptr(stream))
     _check(st, "qs_scatter_noalloc")
+    return out
+
+
+def qs_photon_spectrum(laser, beam, xi, pbins, w=None, precision="f32", out=None,
+                       workspace=None, block=0, grid=0, stream=None,
+                       kernel_events=None) -> torch.Tensor:
+    """Photon spectrum dN/deps (eps in m c^2) of the beam at the centres of
+    the photon-energy bins ``pbins`` (n_bins, lo, hi, log_spaced)."""
+    s, keep = make_samples(xi, w)
+    dev = keep[0].device
+    Bn = make_bins(pbins)
+    E = make_exec(precision, 0, block, grid, kernel_events)
+    if out is None:
+        out = torch.zeros(int(pbins.n_bins), dtype=torch.float64, device=dev)
+    nbytes = int(_lib().qs_photon_workspace_bytes(C.byref(Bn), C.byref(E), s.n))
+    if nbytes == 0:
+        _check(QS_ERR_INVALID_ARG, "qs_photon_workspace_bytes")
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    L, B = make_laser(laser), make_beam(beam)
+    st = _lib().qs_photon_spectrum(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
+                                   out.data_ptr(), workspace.data_ptr(), nbytes,
+                                   _stream_ptr(stream))
+    _check(st, "qs_photon_spectrum")
     return out
 
 

@@ -334,56 +334,66 @@ __device__ __forceinline__ T a_cell(const Params& p, const Path<T>& g, T s) {
 // equations read.
 // VAR: kVarCell -- the peak amplitude a_j of cell j from the path;
 // kVarCycle -- cycle-resolved Gaunt and diffusion factors.
+// One cell j of the FP64 scheme (state du, V, gprev); also hands out the
+// cell's midpoint energy and chi (for the photon spectrum).
 template <int VAR>
-__device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
-                                              double a, double g0, double& du_out,
-                                              double& V_out, const Path<double>& path) {
+__device__ __forceinline__ void qfp_cell(const Params& p, double Gj, int j, double a, double g0,
+                                         const Path<double>& path, double& du, double& V,
+                                         double& gprev, double* mu_out = nullptr,
+                                         double* chi_out = nullptr) {
   // explicit (uncontracted) operations: see op_fma below
   const double LN2 = 0.69314718055994530942;
   const double cK = p.cK, cchi = p.cchi, h = p.h;
   const double c55 = 55.0 / (16.0 * 1.7320508075688772935);
   const double hh2 = 0.5 * p.h * p.h;
+  const double aj = (VAR & kVarCell) ? a_cell<double>(p, path, cell_shift(p, j)) : a;
+  const double A = __dmul_rn(aj, Gj);
+  const double K = __dmul_rn(__dmul_rn(cK, A), A);
+  const double hK = __dmul_rn(h, K);
+  const double dum = __fma_rn(__dmul_rn(0.5, hK), gprev, du);
+  const double mu = g0 / __fma_rn(g0, dum, 1.0);
+  const double chi = __dmul_rn(__dmul_rn(cchi, mu), A);
+  if (mu_out) *mu_out = mu;
+  if (chi_out) *chi_out = chi;
+  double g, sf, h2;                       // g, 2g + chi g', h (or their cycle means)
+  if constexpr ((VAR & kVarCycle) != 0) {
+    cycle_factors_d(p.cyc_gl, chi, g, sf, h2);
+  } else {
+    // Gaunt factor and chi g'(chi)
+    const double x1 = __fma_rn(1.7, chi, 1.0);
+    const double L1 = __dmul_rn(LN2, log2(x1));
+    const double opc = __dadd_rn(1.0, chi);
+    const double B = __fma_rn(__dmul_rn(4.8, opc), L1, __fma_rn(__dmul_rn(2.44, chi), chi, 1.0));
+    const double t = exp2(__dmul_rn(-1.0 / 3.0, log2(B)));     // B^(-1/3)
+    g = __dmul_rn(t, t);
+    const double dB = __fma_rn(4.8, L1, __fma_rn(4.8 * 1.7, opc / x1, __dmul_rn(4.88, chi)));
+    const double chig1 =
+        __dmul_rn(__dmul_rn(__dmul_rn(-2.0 / 3.0, g), __dmul_rn(__dmul_rn(t, t), t)),
+                  __dmul_rn(dB, chi));
+    sf = __fma_rn(2.0, g, chig1);
+    // second-moment factor
+    const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
+    const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
+    h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
+  }
+  // updates
+  du = __fma_rn(hK, g, du);
+  const double lam = __dmul_rn(__dmul_rn(__dmul_rn(-2.0, K), mu), sf);
+  const double D2 = __dmul_rn(__dmul_rn(__dmul_rn(c55, K), __dmul_rn(__dmul_rn(mu, mu), mu)),
+                              __dmul_rn(chi, h2));
+  const double r = __fma_rn(lam, V, D2);
+  V = __fma_rn(__dmul_rn(hh2, lam), r, __fma_rn(h, r, V));
+  gprev = g;
+}
+
+template <int VAR>
+__device__ __forceinline__ void qfp_integrate(const Params& p, const double* __restrict__ sG,
+                                              double a, double g0, double& du_out,
+                                              double& V_out, const Path<double>& path) {
   double du = 0, V = 0, gprev = 1;
   const int N = p.n_phase;
 #pragma unroll 2
-  for (int j = 0; j < N; ++j) {
-    const double aj = (VAR & kVarCell) ? a_cell<double>(p, path, cell_shift(p, j)) : a;
-    const double A = __dmul_rn(aj, sG[j]);
-    const double K = __dmul_rn(__dmul_rn(cK, A), A);
-    const double hK = __dmul_rn(h, K);
-    const double dum = __fma_rn(__dmul_rn(0.5, hK), gprev, du);
-    const double mu = g0 / __fma_rn(g0, dum, 1.0);
-    const double chi = __dmul_rn(__dmul_rn(cchi, mu), A);
-    double g, sf, h2;                       // g, 2g + chi g', h (or their cycle means)
-    if constexpr ((VAR & kVarCycle) != 0) {
-      cycle_factors_d(p.cyc_gl, chi, g, sf, h2);
-    } else {
-      // Gaunt factor and chi g'(chi)
-      const double x1 = __fma_rn(1.7, chi, 1.0);
-      const double L1 = __dmul_rn(LN2, log2(x1));
-      const double opc = __dadd_rn(1.0, chi);
-      const double B = __fma_rn(__dmul_rn(4.8, opc), L1, __fma_rn(__dmul_rn(2.44, chi), chi, 1.0));
-      const double t = exp2(__dmul_rn(-1.0 / 3.0, log2(B)));     // B^(-1/3)
-      g = __dmul_rn(t, t);
-      const double dB = __fma_rn(4.8, L1, __fma_rn(4.8 * 1.7, opc / x1, __dmul_rn(4.88, chi)));
-      const double chig1 =
-          __dmul_rn(__dmul_rn(__dmul_rn(-2.0 / 3.0, g), __dmul_rn(__dmul_rn(t, t), t)),
-                    __dmul_rn(dB, chi));
-      sf = __fma_rn(2.0, g, chig1);
-      // second-moment factor
-      const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
-      const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
-      h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
-    }
-    // updates
-    du = __fma_rn(hK, g, du);
-    const double lam = __dmul_rn(__dmul_rn(__dmul_rn(-2.0, K), mu), sf);
-    const double D2 = __dmul_rn(__dmul_rn(__dmul_rn(c55, K), __dmul_rn(__dmul_rn(mu, mu), mu)),
-                                __dmul_rn(chi, h2));
-    const double r = __fma_rn(lam, V, D2);
-    V = __fma_rn(__dmul_rn(hh2, lam), r, __fma_rn(h, r, V));
-    gprev = g;
-  }
+  for (int j = 0; j < N; ++j) qfp_cell<VAR>(p, sG[j], j, a, g0, path, du, V, gprev);
   du_out = du;
   V_out = V;
 }
@@ -417,7 +427,95 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
 // VAR & kVarCell: per-cell focus; the table then holds {G, G, s_j, s_j} and
 // the two samples' paths give the per-cell amplitudes (same operations as
 // a_cell).  VAR & kVarCycle: cycle-resolved factors from the Hermite tables
-// cA, cB (shared memory).
+// cA, cB (shared memory).  The pair's constants and state, and one cell of
+// the scheme (which also hands out the cell's midpoint energy and chi, for
+// the photon spectrum):
+struct PairConst {
+  float2 c1, ca, g0, zq0, xs, ys, tx, ty;
+};
+struct PairState {
+  float2 du, V, gph;
+};
+template <int VAR>
+__device__ __forceinline__ PairConst pair_const(const Params& p, float2 a, float2 g0,
+                                                const Path<float>& P0, const Path<float>& P1) {
+  constexpr bool LOC = (VAR & kVarCell) != 0;
+  PairConst k;
+  k.c1 = LOC ? f2(p.f.hcK) : mul2(mul2(f2(p.f.hcK), a), a);
+  k.ca = LOC ? f2(p.f.cchi) : mul2(f2(p.f.cchi), a);
+  k.g0 = g0;
+  k.zq0 = make_float2(P0.zq, P1.zq);
+  k.xs = make_float2(P0.xs, P1.xs);
+  k.ys = make_float2(P0.ys, P1.ys);
+  k.tx = make_float2(P0.thx, P1.thx);
+  k.ty = make_float2(P0.thy, P1.thy);
+  return k;
+}
+
+template <int VAR>
+__device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, const PairConst& k,
+                                          PairState& st, const float4* __restrict__ cA,
+                                          const float2* __restrict__ cB, float2* mu_out = nullptr,
+                                          float2* chi_out = nullptr) {
+  const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
+  const float2 C816 = f2((float)(4.8 * 1.7));
+  const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
+  const float2 LN2 = f2(0.69314718055994530942f);
+  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
+  const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
+  const float2 G = make_float2(gg.x, gg.y);
+  float2 hK, cg;
+  if constexpr ((VAR & kVarCell) != 0) {
+    const float2 S = make_float2(gg.z, gg.w);
+    const float2 zq = fma2(S, f2(-p.f.inv_zR), k.zq0);
+    const float2 q = fma2(zq, zq, ONE);
+    const float2 xj = fma2(k.tx, S, k.xs), yj = fma2(k.ty, S, k.ys);
+    const float2 rho2 = fma2(xj, xj, mul2(yj, yj));
+    const float2 rs = rsqrtx2(q);
+    const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), mul2(rs, rs));
+    const float2 aj = mul2(mul2(f2(p.f.a0), rs), ex2x2(mul2(f2(-1.4426950408889634074f), E)));
+    const float2 AG = mul2(aj, G);
+    hK = mul2(k.c1, mul2(AG, AG));
+    cg = mul2(k.ca, AG);
+  } else {
+    hK = mul2(k.c1, make_float2(gg.z, gg.w));
+    cg = mul2(k.ca, G);
+  }
+  const float2 dum = fma2(hK, st.gph, st.du);
+  const float2 mu = mul2(k.g0, rcpx2(fma2(k.g0, dum, ONE)));
+  const float2 chi = mul2(cg, mu);
+  if (mu_out) *mu_out = mu;
+  if (chi_out) *chi_out = chi;
+  float2 g, s, h2;
+  if constexpr ((VAR & kVarCycle) != 0) {
+    cycle_lookup(cA, cB, chi.x, g.x, s.x, h2.x);
+    cycle_lookup(cA, cB, chi.y, g.y, s.y, h2.y);
+  } else {
+    const float2 chi2 = mul2(chi, chi);
+    // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
+    const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
+    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
+    const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
+    g = mul2(t, t);
+    // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
+    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
+    const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
+    s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
+    // second-moment factor h2 = B2^(-7/6)
+    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
+    const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
+    h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
+  }
+  // updates
+  st.du = fma2(hK, g, st.du);
+  const float2 hKmu = mul2(hK, mu);
+  const float2 hlam = mul2(mul2(f2(-2.f), hKmu), s);
+  const float2 hD2 = mul2(C55, mul2(mul2(mul2(hKmu, chi), mul2(mu, mu)), h2));
+  const float2 hr = fma2(hlam, st.V, hD2);
+  st.V = fma2(hr, fma2(HALF, hlam, ONE), st.V);
+  st.gph = mul2(HALF, g);
+}
+
 template <int VAR>
 __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
                                                     const float4* __restrict__ tab, float2 a,
@@ -425,76 +523,13 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
                                                     const Path<float>& P0, const Path<float>& P1,
                                                     const float4* __restrict__ cA = nullptr,
                                                     const float2* __restrict__ cB = nullptr) {
-  constexpr bool LOC = (VAR & kVarCell) != 0;
-  const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
-  const float2 C816 = f2((float)(4.8 * 1.7));
-  const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
-  const float2 LN2 = f2(0.69314718055994530942f);
-  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
-  const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
-  const float2 c1 = LOC ? f2(p.f.hcK) : mul2(mul2(f2(p.f.hcK), a), a);
-  const float2 ca = LOC ? f2(p.f.cchi) : mul2(f2(p.f.cchi), a);
-  // per-cell focus: the paths of the two samples
-  const float2 zq0 = make_float2(P0.zq, P1.zq), xs = make_float2(P0.xs, P1.xs),
-               ys = make_float2(P0.ys, P1.ys), tx = make_float2(P0.thx, P1.thx),
-               ty = make_float2(P0.thy, P1.thy);
-  float2 du = f2(0.f), V = f2(0.f), gph = HALF;
+  const PairConst k = pair_const<VAR>(p, a, g0, P0, P1);
+  PairState st{f2(0.f), f2(0.f), f2(0.5f)};
   const int N = p.n_phase;
 #pragma unroll 2
-  for (int j = 0; j < N; ++j) {
-    const float4 gg = tab[j];
-    const float2 G = make_float2(gg.x, gg.y);
-    float2 hK, cg;
-    if constexpr (LOC) {
-      const float2 S = make_float2(gg.z, gg.w);
-      const float2 zq = fma2(S, f2(-p.f.inv_zR), zq0);
-      const float2 q = fma2(zq, zq, ONE);
-      const float2 xj = fma2(tx, S, xs), yj = fma2(ty, S, ys);
-      const float2 rho2 = fma2(xj, xj, mul2(yj, yj));
-      const float2 rs = rsqrtx2(q);
-      const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), mul2(rs, rs));
-      const float2 aj = mul2(mul2(f2(p.f.a0), rs), ex2x2(mul2(f2(-1.4426950408889634074f), E)));
-      const float2 AG = mul2(aj, G);
-      hK = mul2(c1, mul2(AG, AG));
-      cg = mul2(ca, AG);
-    } else {
-      hK = mul2(c1, make_float2(gg.z, gg.w));
-      cg = mul2(ca, G);
-    }
-    const float2 dum = fma2(hK, gph, du);
-    const float2 mu = mul2(g0, rcpx2(fma2(g0, dum, ONE)));
-    const float2 chi = mul2(cg, mu);
-    float2 g, s, h2;
-    if constexpr ((VAR & kVarCycle) != 0) {
-      cycle_lookup(cA, cB, chi.x, g.x, s.x, h2.x);
-      cycle_lookup(cA, cB, chi.y, g.y, s.y, h2.y);
-    } else {
-      const float2 chi2 = mul2(chi, chi);
-      // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
-      const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
-      const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
-      const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
-      g = mul2(t, t);
-      // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
-      const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
-      const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
-      s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
-      // second-moment factor h2 = B2^(-7/6)
-      const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
-      const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
-      h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
-    }
-    // updates
-    du = fma2(hK, g, du);
-    const float2 hKmu = mul2(hK, mu);
-    const float2 hlam = mul2(mul2(f2(-2.f), hKmu), s);
-    const float2 hD2 = mul2(C55, mul2(mul2(mul2(hKmu, chi), mul2(mu, mu)), h2));
-    const float2 hr = fma2(hlam, V, hD2);
-    V = fma2(hr, fma2(HALF, hlam, ONE), V);
-    gph = mul2(HALF, g);
-  }
-  du_out = du;
-  V_out = V;
+  for (int j = 0; j < N; ++j) pair_cell<VAR>(p, tab[j], k, st, cA, cB);
+  du_out = st.du;
+  V_out = st.V;
 }
 
 // a_eff at the crossing point and the decoded sample (rows a1-a3), from the

@@ -40,8 +40,7 @@ struct Smem {
   bool hist = false;
   bool smooth = false;
 };
-Smem smem_plan(const Plan& pl, int precision, int cells, bool cell_focus, bool weighted,
-               int block);
+Smem smem_plan(const Plan& pl, int precision, int cells, int variant, bool weighted, int block);
 int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int gmax);
 
 // A failed runtime call: clear the (non-sticky) error state so that it does

@@ -1,0 +1,401 @@
+// qs_photon.cu -- photon spectrum of the beam (qs_photon_spectrum).
+//
+// K6 k_photon_setup  once per device: Hermite table (FP64-built) of the two
+//                    Bessel functions of the synchrotron spectrum.
+// K7 k_photon        per sample: the quantum model's phase integration; in
+//                    every cell the locally-constant-field quantum-
+//                    synchrotron spectrum at the cell's (mu, chi) is added
+//                    to the photon-energy bins, warp-cooperatively (each
+//                    lane owns bins b = lane + 32 k and takes the warp's
+//                    samples one at a time); per-CTA partials in fixed order.
+// K8 k_photon_final  one CTA: partials summed in CTA order.
+//
+// Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348, Sec. 4 (cumulative
+// photon spectrum from the mean energy along the phase and the local field;
+// the LCFA spectrum the paper names, in its standard form, is stated with
+// qs_photon_spectrum in qscatter.h).
+#include "qscatter.h"
+#include "qs_device.cuh"
+#include "qs_host.hpp"
+
+#include <cmath>
+#include <mutex>
+
+namespace qs {
+
+constexpr int kPhMaxBins = 512;               // photon-energy bins (16 per lane)
+constexpr int kPhK = kPhMaxBins / 32;
+constexpr int kPhN = 1024;                    // table nodes in u = log2 y
+constexpr double kPhUmin = -40.0, kPhUmax = 6.0;
+constexpr double kPhDu = (kPhUmax - kPhUmin) / (kPhN - 1);
+constexpr double kPhYmax = 60.0;              // F ~ e^-y: photons beyond are dropped
+constexpr double kAlpha = 7.2973525693e-3;    // fine-structure constant (CODATA 2018)
+constexpr double kLog2e = 1.4426950408889634074;
+
+// K_{2/3}(y), Ki_{1/3}(y) = int_y^inf K_{1/3}, and the derivatives -K_{2/3}'
+// and K_{1/3} (= -Ki_{1/3}'), from K_nu(y) = int_0^inf exp(-y cosh t)
+// cosh(nu t) dt by the trapezoidal rule (step 1/32 until y cosh t > 800):
+// the integrands are analytic in a strip and decay doubly exponentially.
+__device__ void bessel_d(double y, double& k23, double& ki13, double* mk23p = nullptr,
+                         double* k13 = nullptr) {
+  const double dt = 1.0 / 32.0;
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+  for (int k = 0;; ++k) {
+    const double t = k * dt, ch = cosh(t), e = exp(-y * ch);
+    const double wt = k == 0 ? 0.5 : 1.0;
+    const double c23 = cosh(2.0 * t / 3.0), c13 = cosh(t / 3.0);
+    a += wt * e * c23;
+    b += wt * e * c13 / ch;
+    c += wt * e * c23 * ch;
+    d += wt * e * c13;
+    if (y * ch > 800.0 || t > 60.0) break;
+  }
+  k23 = dt * a;
+  ki13 = dt * b;
+  if (mk23p) *mk23p = dt * c;
+  if (k13) *k13 = dt * d;
+}
+
+// Table node n at u_n = umin + n du, y = 2^u: {q23, dq23/du du, q13,
+// dq13/du du} with q23 = log2 K_{2/3} + y log2 e + (2/3) u and
+// q13 = log2 Ki_{1/3} + y log2 e (both O(1) over the range: the small-y
+// power and the large-y exponential are taken out).
+__device__ float4 g_ph_tab[kPhN];
+
+__global__ void __launch_bounds__(256) k_photon_setup() {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < kPhN; m += gridDim.x * blockDim.x) {
+    const double u = kPhUmin + m * kPhDu, y = exp2(u);
+    double k23, ki13, mk23p, k13;
+    bessel_d(y, k23, ki13, &mk23p, &k13);
+    const double q23 = log2(k23) + y * kLog2e + (2.0 / 3.0) * u;
+    const double q13 = log2(ki13) + y * kLog2e;
+    const double d23 = y * (1.0 - mk23p / k23) + 2.0 / 3.0;   // dq23/du
+    const double d13 = y * (1.0 - k13 / ki13);                // dq13/du
+    g_ph_tab[m] = make_float4((float)q23, (float)(d23 * kPhDu), (float)q13, (float)(d13 * kPhDu));
+  }
+}
+
+// FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
+// table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
+__device__ __forceinline__ float synch_F(const float4* __restrict__ T, float xi, float r1,
+                                         float y) {
+  const float u = M<float>::lg2(y);
+  const float x = fminf(fmaxf(__fmul_rn(__fsub_rn(u, (float)kPhUmin), (float)(1.0 / kPhDu)), 0.f),
+                        (float)(kPhN - 1) - 1e-3f);
+  const float xm = __fadd_rn(x, 8388608.f);          // floor without a conversion
+  float r = __fsub_rn(xm, 8388608.f);
+  int idx = __float_as_int(xm) - 0x4B000000;
+  if (r > x) {
+    r = __fsub_rn(r, 1.f);
+    idx -= 1;
+  }
+  const float t = __fsub_rn(x, r), t2 = __fmul_rn(t, t);
+  const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));
+  const float h11 = __fmaf_rn(t2, t, -t2);
+  const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);
+  const float4 a0 = T[idx], a1 = T[idx + 1];
+  const float q23 = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, __fsub_rn(a1.x, a0.x), a0.x)));
+  const float q13 = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
+  const float ylog = __fmul_rn(y, (float)kLog2e);
+  const float k23 = M<float>::ex2(__fsub_rn(__fmaf_rn(-2.f / 3.f, u, q23), ylog));
+  const float ki13 = M<float>::ex2(__fsub_rn(q13, ylog));
+  // 1 - xi + 1/(1 - xi), with r1 = 1/(1 - xi)
+  return __fmaf_rn(__fadd_rn(__fsub_rn(1.f, xi), r1), k23, -ki13);
+}
+
+// FP64: the same F from the integrals.
+__device__ __forceinline__ double synch_F_d(double xi, double y) {
+  double k23, ki13;
+  bessel_d(y, k23, ki13);
+  return (1.0 - xi + 1.0 / (1.0 - xi)) * k23 - ki13;
+}
+
+// One emitting sample seen by the whole warp: mean energy mu, chi, and the
+// factor c = w h alpha a_S/(2 sqrt3 pi mu^2); adds c F(eps_b/mu, chi) to the
+// lane's bins.  Bins are ascending in eps; groups of 32 whose first energy
+// lies beyond the cut (y > ymax) are skipped by the whole warp.
+template <typename T, typename A>
+__device__ __forceinline__ void photon_add(const float4* __restrict__ tab, const T* __restrict__ eps,
+                                           int nb, T mu, T chi, T c, A& acc) {
+  const int lane = threadIdx.x & 31;
+  const T imu = (T)1 / mu, gy = (T)2 / ((T)3 * chi);
+  const T yc = (T)1.5 * chi * (T)kPhYmax;              // xi/(1 - xi) below this
+  const T ecut = mu * yc / ((T)1 + yc);
+#pragma unroll
+  for (int k = 0; k < kPhK; ++k) {                     // unrolled: acc stays in registers
+    if (32 * k >= nb || !(eps[32 * k] < ecut)) break;
+    const int b = 32 * k + lane;
+    if (b < nb && eps[b] < ecut) {
+      const T xi = eps[b] * imu;
+      if constexpr (sizeof(T) == 4) {
+        const float r1 = M<float>::rcp(__fsub_rn(1.f, xi));
+        const float y = __fmul_rn(__fmul_rn(gy, xi), r1);
+        acc.add(k, __fmul_rn(c, synch_F(tab, xi, r1, y)));
+      } else {
+        const double y = gy * xi / (1.0 - xi);
+        acc.add(k, c * synch_F_d(xi, y));
+      }
+    }
+  }
+}
+
+// Per-lane bin accumulators: compensated FP32 sums (FP32 path), FP64 sums.
+template <typename T> struct PhAcc;
+template <> struct PhAcc<float> {
+  float s[kPhK], c[kPhK];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int k = 0; k < kPhK; ++k) s[k] = c[k] = 0.f;
+  }
+  __device__ __forceinline__ void add(int k, float x) { kahan(s[k], c[k], x); }
+  __device__ __forceinline__ double get(int k) const { return (double)s[k] - (double)c[k]; }
+};
+template <> struct PhAcc<double> {
+  double s[kPhK];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int k = 0; k < kPhK; ++k) s[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
+  __device__ __forceinline__ double get(int k) const { return s[k]; }
+};
+
+// Shared memory: phase table, photon table (FP32), bin energies, per-warp
+// partial spectra for the CTA's fixed-order reduction.
+template <typename T>
+__host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block) {
+  const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
+  const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
+  const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
+  return tab + pt + e + (size_t)(block / 32) * nb * sizeof(double);
+}
+
+// K7.  pref = h alpha a_S/(2 sqrt3 pi); eps_b at the bin centres.
+template <typename T, int VAR>
+__global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double lo, double hi,
+                                                int log_spaced, double* __restrict__ partials) {
+  using TT = typename Tab<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t tb = ((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15;
+  TT* tab = reinterpret_cast<TT*>(smem);
+  float4* ptab = reinterpret_cast<float4*>(smem + tb);
+  T* eps = reinterpret_cast<T*>(smem + tb + (sizeof(T) == 4 ? kPhN * sizeof(float4) : 0));
+  double* part = reinterpret_cast<double*>(
+      reinterpret_cast<unsigned char*>(eps) + (((size_t)nb * sizeof(T) + 15) & ~(size_t)15));
+  for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  if (sizeof(T) == 4)
+    for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    eps[b] = (T)(log_spaced ? lo * exp2(log2(hi / lo) * (b + 0.5) / nb)
+                            : lo + (b + 0.5) * (hi - lo) / nb);
+  __syncthreads();
+
+  const double pref = p.h * kAlpha / (2.0 * 1.7320508075688772935 * 3.14159265358979323846 *
+                                      p.cchi / 1.4142135623730950488);   // h alpha a_S/(2 sqrt3 pi)
+  PhAcc<T> acc;
+  acc.init();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    const float prf = (float)pref;
+    // two samples per thread through the packed scheme, warp by warp
+    for (int64_t kb = t0 - lane; 2 * kb < p.n; kb += stride) {
+      const int64_t k = kb + lane, i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+      const bool act = i0 < p.n;
+      float g0f = 1.f, g1f = 1.f, tx, ty, a0 = 0.f, a1 = 0.f, w0 = 0.f, w1 = 0.f;
+      Path<float> P0{}, P1{};
+      if (act) {
+        a0 = focus<float>(p, i0, g0f, tx, ty, (VAR & kVarCell) ? &P0 : nullptr);
+        a1 = focus<float>(p, i1, g1f, tx, ty, (VAR & kVarCell) ? &P1 : nullptr);
+        w0 = p.weighted ? load_t<float>(p.w, i0, p.dtype) : 1.f;
+        w1 = i1 != i0 ? (p.weighted ? load_t<float>(p.w, i1, p.dtype) : 1.f) : 0.f;
+        if (!(w0 >= 0.f) || !isfinite(w0) || !isfinite(a0) || !isfinite(g0f)) w0 = 0.f;
+        if (!(w1 >= 0.f) || !isfinite(w1) || !isfinite(a1) || !isfinite(g1f)) w1 = 0.f;
+      }
+      const PairConst kc = pair_const<VAR>(p, make_float2(a0, a1), make_float2(g0f, g1f), P0, P1);
+      PairState st{f2(0.f), f2(0.f), f2(0.5f)};
+      for (int j = 0; j < p.n_phase; ++j) {
+        float2 mu, chi;
+        pair_cell<VAR>(p, reinterpret_cast<const float4*>(tab)[j], kc, st, nullptr, nullptr, &mu,
+                       &chi);
+        const float c0 = (w0 > 0.f && chi.x > 0.f) ? __fmul_rn(__fmul_rn(prf, w0), M<float>::rcp(__fmul_rn(mu.x, mu.x))) : 0.f;
+        const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;
+        unsigned m0 = __ballot_sync(0xffffffffu, c0 > 0.f), m1 = __ballot_sync(0xffffffffu, c1 > 0.f);
+        while (m0 | m1) {
+          const bool first = m0 != 0;
+          const int s = __ffs(first ? m0 : m1) - 1;
+          if (first) m0 &= m0 - 1; else m1 &= m1 - 1;
+          const float ms = __shfl_sync(0xffffffffu, first ? mu.x : mu.y, s);
+          const float cs = __shfl_sync(0xffffffffu, first ? chi.x : chi.y, s);
+          const float cc = __shfl_sync(0xffffffffu, first ? c0 : c1, s);
+          photon_add<float>(ptab, eps, nb, ms, cs, cc, acc);
+        }
+      }
+    }
+  } else {
+    for (int64_t ib = t0 - lane; ib < p.n; ib += stride) {
+      const int64_t i = ib + lane;
+      double g0 = 1.0, tx, ty, a = 0.0, w = 0.0;
+      Path<double> P{};
+      if (i < p.n) {
+        a = focus<double>(p, i, g0, tx, ty, (VAR & kVarCell) ? &P : nullptr);
+        w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+        if (!(w >= 0.0) || !isfinite(w) || !isfinite(a) || !isfinite(g0)) w = 0.0;
+      }
+      double du = 0.0, V = 0.0, gprev = 1.0;
+      for (int j = 0; j < p.n_phase; ++j) {
+        double mu, chi;
+        qfp_cell<VAR>(p, reinterpret_cast<const double*>(tab)[j], j, a, g0, P, du, V, gprev, &mu,
+                      &chi);
+        const double c = (w > 0.0 && chi > 0.0) ? pref * w / (mu * mu) : 0.0;
+        unsigned m = __ballot_sync(0xffffffffu, c > 0.0);
+        while (m) {
+          const int s = __ffs(m) - 1;
+          m &= m - 1;
+          photon_add<double>(nullptr, eps, nb, __shfl_sync(0xffffffffu, mu, s),
+                             __shfl_sync(0xffffffffu, chi, s), __shfl_sync(0xffffffffu, c, s),
+                             acc);
+        }
+      }
+    }
+  }
+
+  // fixed-order reduction: lanes own distinct bins; warps in order
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kPhK; ++k)
+    if (32 * k + lane < nb) part[warp * nb + 32 * k + lane] = acc.get(k);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double s = 0.0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += part[wv * nb + b];
+    partials[(size_t)blockIdx.x * nb + b] = s;
+  }
+}
+
+// K8: CTA partials in CTA order (compensated).
+__global__ void k_photon_final(int grid, int nb, const double* __restrict__ partials,
+                               double* __restrict__ out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int g = 0; g < grid; ++g) {
+      const double x = partials[(size_t)g * nb + b], t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    out[b] = s + c;
+  }
+}
+
+namespace {
+
+std::mutex g_ph_mu;
+bool g_ph_ready[64] = {};
+
+// The photon table, built on first use on this device (one launch on `st`
+// and a wait for it; not while `st` is being captured).
+int32_t photon_table(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_ph_mu);
+  if (g_ph_ready[dev]) return QS_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return detail::cuda_fail();
+  if (cap != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
+  k_photon_setup<<<kPhN / 256, 256, 0, st>>>();
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return detail::cuda_fail();
+  g_ph_ready[dev] = true;
+  return QS_OK;
+}
+
+int32_t check_pbins(const qs_bins* b) {
+  if (!b) return QS_ERR_INVALID_ARG;
+  if (b->n_bins < 1 || b->n_bins > kPhMaxBins) return QS_ERR_INVALID_ARG;
+  if (!std::isfinite(b->lo) || !std::isfinite(b->hi) || !(b->hi > b->lo) || b->lo < 0.0)
+    return QS_ERR_INVALID_ARG;
+  if (b->log_spaced && !(b->lo > 0.0)) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+int photon_grid(int sms, int block, int grid_req, int64_t n) {
+  const int64_t per = 2 * (int64_t)block;                 // samples per CTA pass
+  int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * 2;
+  const int64_t need = (n + per - 1) / per;
+  if (g > need) g = need;
+  if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T, int VAR>
+int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int grid, size_t smem,
+                      double* partials, cudaStream_t st) {
+  auto kern = k_photon<T, VAR>;
+  static bool attr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             detail::kSmemLimit) != cudaSuccess)
+      return detail::cuda_fail();
+    attr[dev] = true;
+  }
+  kern<<<grid, block, smem, st>>>(p, pb->n_bins, pb->lo, pb->hi, pb->log_spaced, partials);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+using namespace qs::detail;
+
+extern "C" size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec* exec,
+                                            int64_t n) {
+  int prec, wbits, block, grid, sms;
+  if (check_pbins(pbins) != QS_OK || n < 0) return 0;
+  if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
+  if (block > 256) block = 256;
+  if (device_sms(&sms) != QS_OK) return 0;
+  const int g = photon_grid(sms, block, grid, n);
+  return align_up((size_t)g * pbins->n_bins * sizeof(double), 256);
+}
+
+extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
+                                      const qs_samples* samples, const qs_bins* pbins,
+                                      const qs_exec* exec, double* d_spectrum,
+                                      void* d_workspace, size_t ws_bytes, void* stream) {
+  int32_t st;
+  if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
+      (st = validate_samples(samples)) || (st = check_pbins(pbins)))
+    return st;
+  if (laser->model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
+  if (laser->variant & ~QS_VARIANT_CELL_FOCUS) return QS_ERR_UNSUPPORTED;
+  if (!d_spectrum) return QS_ERR_INVALID_ARG;
+  int prec, wbits, block, grid, sms;
+  if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
+  if (block > 256) block = 256;
+  if ((st = device_sms(&sms))) return st;
+  const int g = photon_grid(sms, block, grid, samples->n);
+  const size_t need = align_up((size_t)g * pbins->n_bins * sizeof(double), 256);
+  if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < need) return QS_ERR_WORKSPACE;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (prec == QS_F32 && (st = photon_table(cs))) return st;
+  Params p;
+  fill_params(p, laser, beam, samples, nullptr, wbits);
+  double* part = static_cast<double*>(d_workspace);
+  const bool loc = (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
+  const size_t smem = prec == QS_F64 ? photon_smem<double>(p.n_phase, pbins->n_bins, block)
+                                     : photon_smem<float>(p.n_phase, pbins->n_bins, block);
+  if (smem > (size_t)kSmemLimit) return QS_ERR_INVALID_ARG;
+  if (prec == QS_F64)
+    st = loc ? launch_photon<double, kVarCell>(p, pbins, block, g, smem, part, cs)
+             : launch_photon<double, 0>(p, pbins, block, g, smem, part, cs);
+  else
+    st = loc ? launch_photon<float, kVarCell>(p, pbins, block, g, smem, part, cs)
+             : launch_photon<float, 0>(p, pbins, block, g, smem, part, cs);
+  if (st) return st;
+  k_photon_final<<<(pbins->n_bins + 127) / 128, 128, 0, cs>>>(g, pbins->n_bins, part, d_spectrum);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
