@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-cell", action="store_true",
                     help="skip the model-variant measurements (per-cell focus, cycle-resolved chi)")
     ap.add_argument("--cell-n", type=int, default=1 << 24)
+    ap.add_argument("--no-photon", action="store_true", help="skip the photon-spectrum measurement")
+    ap.add_argument("--photon-n", type=int, default=1 << 19)
     return ap.parse_args()
 
 
@@ -328,6 +330,31 @@ def bench_variant(dev, rank, variant, n=1 << 24, steps=3):
     return line
 
 
+def bench_photon(dev, rank, n=1 << 19, steps=2):
+    """Photon spectrum of the bench beam (quantum model, 512 cells): LCFA
+    emission of every cell into 256 log-spaced photon-energy bins on
+    [1e-3, 6720] m c^2, FP32."""
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.full_qfp(n)
+    pb = I.Bins(n_bins=256, lo=1e-3, hi=6720.0, log_spaced=1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    out = B.qs_photon_spectrum(wl.laser, wl.beam, xi, pb)
+    torch.cuda.synchronize()
+    kev = [tuple(_events()) for _ in range(steps)]
+    for k in range(steps):
+        B.qs_photon_spectrum(wl.laser, wl.beam, xi, pb, out=out, kernel_events=kev[k])
+    torch.cuda.synchronize()
+    kms = sum(x.elapsed_time(y) for x, y in kev) / steps
+    return {"metric": "beam-sample evals/s", "value": n / (kms * 1e-3), "unit": "samples/s",
+            "kernel_ms": kms, "n_samples": n, "n_phase": wl.laser.n_phase,
+            "photon_bins": "256 log-spaced on [1e-3, 6720] m c^2",
+            "workload": "mc2p19_photon_qfp512"}
+
+
 def bench_batch(dev, rank, steps=3, n_shots=4096):
     """4096 shots, sample counts log-uniform in [1e3, 1e6], per-shot laser and
     beam drawn from seed, quantum model with 512 phase cells, FP32 with FP64
@@ -574,6 +601,7 @@ def main():
     ll = None if args.no_ll else bench_ll(dev, rank, n=args.ll_n)
     cell = None if args.no_cell else bench_variant(dev, rank, 1, n=args.cell_n)
     cyc = None if args.no_cell else bench_variant(dev, rank, 2, n=args.cell_n)
+    phot = None if args.no_photon else bench_photon(dev, rank, n=args.photon_n)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -598,7 +626,7 @@ def main():
                 "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
-                "cell_focus": cell, "cycle_chi": cyc,
+                "cell_focus": cell, "cycle_chi": cyc, "photon": phot,
                 "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:

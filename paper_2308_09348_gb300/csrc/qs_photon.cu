@@ -139,6 +139,15 @@ __device__ __forceinline__ void photon_add(const float4* __restrict__ tab, const
   }
 }
 
+// FP32 emitter of one cell: {1/mu, 2/(3 chi), eps cut where y = ymax, c}
+// (a zero cut when c = 0: nothing emitted).
+__device__ __forceinline__ float4 emitter(float mu, float chi, float c) {
+  if (!(c > 0.f)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float yc = __fmul_rn(__fmul_rn(1.5f, chi), (float)kPhYmax);
+  const float cut = __fmul_rn(__fmul_rn(mu, yc), M<float>::rcp(__fadd_rn(1.f, yc)));
+  return make_float4(M<float>::rcp(mu), M<float>::rcp(__fmul_rn(1.5f, chi)), cut, c);
+}
+
 // Per-lane bin accumulators: compensated FP32 sums (FP32 path), FP64 sums.
 template <typename T> struct PhAcc;
 template <> struct PhAcc<float> {
@@ -161,13 +170,15 @@ template <> struct PhAcc<double> {
 };
 
 // Shared memory: phase table, photon table (FP32), bin energies, per-warp
-// partial spectra for the CTA's fixed-order reduction.
+// partial spectra for the CTA's fixed-order reduction, per-warp emitters
+// (FP32).
 template <typename T>
 __host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block) {
   const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
   const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
   const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
-  return tab + pt + e + (size_t)(block / 32) * nb * sizeof(double);
+  const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * sizeof(float4) : 0;
+  return tab + pt + e + (size_t)(block / 32) * nb * sizeof(double) + stage;
 }
 
 // K7.  pref = h alpha a_S/(2 sqrt3 pi); eps_b at the bin centres.
@@ -182,6 +193,8 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
   T* eps = reinterpret_cast<T*>(smem + tb + (sizeof(T) == 4 ? kPhN * sizeof(float4) : 0));
   double* part = reinterpret_cast<double*>(
       reinterpret_cast<unsigned char*>(eps) + (((size_t)nb * sizeof(T) + 15) & ~(size_t)15));
+  float4* stage = reinterpret_cast<float4*>(part + (size_t)(blockDim.x / 32) * nb) +
+                  (threadIdx.x >> 5) * 64;            // FP32: the warp's emitters
   for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (sizeof(T) == 4)
     for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
@@ -221,16 +234,36 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
                        &chi);
         const float c0 = (w0 > 0.f && chi.x > 0.f) ? __fmul_rn(__fmul_rn(prf, w0), M<float>::rcp(__fmul_rn(mu.x, mu.x))) : 0.f;
         const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;
-        unsigned m0 = __ballot_sync(0xffffffffu, c0 > 0.f), m1 = __ballot_sync(0xffffffffu, c1 > 0.f);
-        while (m0 | m1) {
-          const bool first = m0 != 0;
-          const int s = __ffs(first ? m0 : m1) - 1;
-          if (first) m0 &= m0 - 1; else m1 &= m1 - 1;
-          const float ms = __shfl_sync(0xffffffffu, first ? mu.x : mu.y, s);
-          const float cs = __shfl_sync(0xffffffffu, first ? chi.x : chi.y, s);
-          const float cc = __shfl_sync(0xffffffffu, first ? c0 : c1, s);
-          photon_add<float>(ptab, eps, nb, ms, cs, cc, acc);
+        // the warp's 64 emitters of this cell, staged once: {1/mu, 2/(3 chi),
+        // energy cut (y = ymax), c}; a cut of 0 marks no emission
+        const float4 e0 = emitter(mu.x, chi.x, c0), e1 = emitter(mu.y, chi.y, c1);
+        stage[lane] = e0;
+        stage[32 + lane] = e1;
+        float emax = fmaxf(e0.z, e1.z);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        __syncwarp();
+        // lane b of group k: its energy against every emitter (independent
+        // evaluations, summed plainly over the 64, then compensated)
+#pragma unroll
+        for (int k = 0; k < kPhK; ++k) {
+          if (32 * k >= nb || !(eps[32 * k] < emax)) break;
+          const int b = 32 * k + lane;
+          const float e = b < nb ? eps[b] : 3.4e38f;
+          float part = 0.f;
+#pragma unroll 4
+          for (int q = 0; q < 64; ++q) {
+            const float4 em = stage[q];
+            if (e < em.z) {
+              const float xi = __fmul_rn(e, em.x);
+              const float r1 = M<float>::rcp(__fsub_rn(1.f, xi));
+              const float y = __fmul_rn(__fmul_rn(em.y, xi), r1);
+              part = __fmaf_rn(em.w, synch_F(ptab, xi, r1, y), part);
+            }
+          }
+          acc.add(k, part);
         }
+        __syncwarp();
       }
     }
   } else {
@@ -319,18 +352,21 @@ int32_t check_pbins(const qs_bins* b) {
   return QS_OK;
 }
 
-int photon_grid(int sms, int block, int grid_req, int64_t n) {
-  const int64_t per = 2 * (int64_t)block;                 // samples per CTA pass
-  int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * 2;
+// Largest grid a call may use (the workspace holds one partial spectrum per
+// CTA): the requested grid, else four CTAs per SM; never more CTAs than
+// samples in passes of two per thread.
+int photon_gmax(int sms, int block, int grid_req, int64_t n) {
+  const int64_t per = 2 * (int64_t)block;
+  int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * 4;
   const int64_t need = (n + per - 1) / per;
   if (g > need) g = need;
-  if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
   return (int)(g < 1 ? 1 : g);
 }
 
 template <typename T, int VAR>
-int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int grid, size_t smem,
-                      double* partials, cudaStream_t st) {
+int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_io, size_t smem,
+                      double* partials, cudaStream_t st, const qs_exec* ex) {
+  int grid = *grid_io;
   auto kern = k_photon<T, VAR>;
   static bool attr[64] = {};
   int dev = 0;
@@ -341,8 +377,26 @@ int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int grid, s
       return detail::cuda_fail();
     attr[dev] = true;
   }
+  // persistent grid: the CTAs that fit at once (unless a grid was requested)
+  if (!(ex && ex->grid > 0)) {
+    int occ = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess ||
+        detail::device_sms(&sms) != QS_OK)
+      return detail::cuda_fail();
+    const int g = sms * (occ > 0 ? occ : 1);
+    if (g < grid) grid = g;
+  }
+  *grid_io = grid;
+  // optional events around the kernel (qs_exec ev_start/ev_stop)
+  if (ex && ex->ev_start &&
+      cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_start), st) != cudaSuccess)
+    return QS_ERR_CUDA;
   kern<<<grid, block, smem, st>>>(p, pb->n_bins, pb->lo, pb->hi, pb->log_spaced, partials);
-  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  if (ex && ex->ev_stop &&
+      cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_stop), st) != cudaSuccess)
+    return QS_ERR_CUDA;
+  return QS_OK;
 }
 
 }  // namespace
@@ -358,7 +412,7 @@ extern "C" size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec*
   if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
   if (block > 256) block = 256;
   if (device_sms(&sms) != QS_OK) return 0;
-  const int g = photon_grid(sms, block, grid, n);
+  const int g = photon_gmax(sms, block, grid, n);
   return align_up((size_t)g * pbins->n_bins * sizeof(double), 256);
 }
 
@@ -377,8 +431,9 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
-  const int g = photon_grid(sms, block, grid, samples->n);
-  const size_t need = align_up((size_t)g * pbins->n_bins * sizeof(double), 256);
+  const int gmax = photon_gmax(sms, block, grid, samples->n);
+  int g = gmax;
+  const size_t need = align_up((size_t)gmax * pbins->n_bins * sizeof(double), 256);
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < need) return QS_ERR_WORKSPACE;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if (prec == QS_F32 && (st = photon_table(cs))) return st;
@@ -390,11 +445,11 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
                                      : photon_smem<float>(p.n_phase, pbins->n_bins, block);
   if (smem > (size_t)kSmemLimit) return QS_ERR_INVALID_ARG;
   if (prec == QS_F64)
-    st = loc ? launch_photon<double, kVarCell>(p, pbins, block, g, smem, part, cs)
-             : launch_photon<double, 0>(p, pbins, block, g, smem, part, cs);
+    st = loc ? launch_photon<double, kVarCell>(p, pbins, block, &g, smem, part, cs, exec)
+             : launch_photon<double, 0>(p, pbins, block, &g, smem, part, cs, exec);
   else
-    st = loc ? launch_photon<float, kVarCell>(p, pbins, block, g, smem, part, cs)
-             : launch_photon<float, 0>(p, pbins, block, g, smem, part, cs);
+    st = loc ? launch_photon<float, kVarCell>(p, pbins, block, &g, smem, part, cs, exec)
+             : launch_photon<float, 0>(p, pbins, block, &g, smem, part, cs, exec);
   if (st) return st;
   k_photon_final<<<(pbins->n_bins + 127) / 128, 128, 0, cs>>>(g, pbins->n_bins, part, d_spectrum);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
