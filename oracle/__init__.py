@@ -93,6 +93,7 @@ def lib():
                                               C.POINTER(QsoBins), C.c_int64, C.POINTER(_DP),
                                               _DP, _DP]
             L.qso_photon_spectrum.restype = C.c_int
+            L.qso_pw_reconstruct.argtypes = [C.c_int, C.c_int, C.c_int, _DP, _DP, _DP]
             L.qso_qfp_rates.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double, _DP]
             L.qso_qfp_integrate.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_double, _DP, _DP]
@@ -303,4 +304,17 @@ def photon_spectrum(laser, beam, pbins, xi, w=None) -> np.ndarray:
                                    C.byref(_bins(pbins)), n, ptrs, _ptr(w64), _ptr(out))
     if rc != 0:
         raise ValueError("photon spectrum needs the quantum model and valid bins")
+    return out
+
+
+def pw_reconstruct(hist, pw) -> np.ndarray:
+    """Eq. 5: out[s, b] = sum_k hist[s, k] pw[k, b] (hist: shots x a-bins,
+    pw: a-bins x energy bins)."""
+    hist = np.ascontiguousarray(np.atleast_2d(hist), dtype=np.float64)
+    pw = np.ascontiguousarray(pw, dtype=np.float64)
+    ns, na = hist.shape
+    nb = pw.shape[1]
+    assert pw.shape[0] == na
+    out = np.zeros((ns, nb))
+    lib().qso_pw_reconstruct(ns, na, nb, _ptr(hist), _ptr(pw), _ptr(out))
     return out

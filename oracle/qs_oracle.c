@@ -33,6 +33,8 @@
  *   qso_photon_spectrum  pinned (energy balance with the electrons' loss
  *                        to the Gaunt fit's accuracy; exact moments of
  *                        the spectrum; classical synchrotron limit)
+ *   qso_pw_reconstruct   pinned (converges to the direct 3D spectrum at
+ *                        first order in the a-grid spacing, classical model)
  *   per-cell focus       pinned (adaptive quadrature of Eq. 3's exponent
  *                        along the electron's path; reduces to the crossing
  *                        focus for a straight path in a long focus)
@@ -961,4 +963,22 @@ int qso_photon_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* p
     for (int b = 0; b < nb; ++b) out[b] = qso_val(&acc[b]);
     free(eps); free(mu_cell); free(chi_cell); free(acc);
     return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Plane-wave reconstruction (Eq. 5): the 3D spectrum of a beam is the sum
+ * over a uniform set of effective amplitudes a_k of the plane-wave spectrum
+ * at a_k weighted by the beam's a_eff distribution,
+ *   out[s][b] = sum_k hist[s][k] pw[k][b]
+ * (k ascending, compensated), for n_shots histograms at once.
+ * ------------------------------------------------------------------------ */
+void qso_pw_reconstruct(int n_shots, int n_a, int n_bins, const double* hist, const double* pw,
+                        double* out) {
+    for (int sh = 0; sh < n_shots; ++sh)
+        for (int b = 0; b < n_bins; ++b) {
+            qso_sum acc = {0.0, 0.0};
+            for (int k = 0; k < n_a; ++k)
+                qso_add(&acc, hist[(size_t)sh * n_a + k] * pw[(size_t)k * n_bins + b]);
+            out[(size_t)sh * n_bins + b] = qso_val(&acc);
+        }
 }
