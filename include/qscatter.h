@@ -413,6 +413,22 @@ int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
                            const qs_exec* exec, double* d_spectrum, void* d_workspace,
                            size_t ws_bytes, void* stream);
 
+/*
+ * qs_pw_reconstruct: plane-wave reconstruction, Eq. 5 (Sec. 3.2): the 3D
+ * spectrum of a beam is the sum, over a uniform set of effective amplitudes
+ * a_k, of the plane-wave spectrum at a_k weighted by the beam's a_eff
+ * distribution:
+ *   d_out[s][b] = sum_k d_hist[s][k] d_pw[k][b],   k ascending,
+ * for n_shots beams at once.  d_hist: n_shots x n_a doubles (e.g. the a_eff
+ * histograms of qs_scatter, a_k the bin centres); d_pw: n_a x n_bins doubles
+ * (plane-wave spectra per unit weight at the a_k, e.g. from a qs_scatter_batch
+ * sweep with a0 = a_k over a beam of zero size at the focus); d_out:
+ * n_shots x n_bins doubles.  All device pointers, row-major.  FP64 sums in a
+ * fixed order.  n_shots <= 524280.  Errors: QS_ERR_INVALID_ARG, QS_ERR_CUDA.
+ */
+int32_t qs_pw_reconstruct(int32_t n_shots, int32_t n_a, int32_t n_bins, const double* d_hist,
+                          const double* d_pw, double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -137,6 +137,8 @@ def _lib():
                                              C.POINTER(qs_samples), C.POINTER(qs_bins),
                                              C.POINTER(qs_exec), _VP, _VP, C.c_size_t, _VP]
             L.qs_photon_spectrum.restype = C.c_int32
+            L.qs_pw_reconstruct.argtypes = [C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]
+            L.qs_pw_reconstruct.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -459,6 +461,45 @@ class Batch:
 
     def moments_dicts(self) -> list[dict]:
         return [dict(zip(MOMENT_FIELDS, row)) for row in self.moments.cpu().tolist()]
+
+
+# ---- plane-wave reconstruction (Eq. 5) ------------------------------------
+
+def pw_table(laser, beam, bins, n_a: int, a_max: float, xi, w=None, precision="f32",
+             stream=None) -> torch.Tensor:
+    """Plane-wave spectra per unit weight, n_a x bins.n_bins, at the a-bin
+    centres a_k = (k + 1/2) a_max / n_a (those of an a_eff histogram with
+    n_aeff = n_a, aeff_max = a_max): one qs_scatter_batch sweep over the
+    shared samples xi, each shot the laser at a0 = a_k with no misalignment
+    and the beam reduced to its energy distribution at the focus."""
+    from dataclasses import replace
+    lasers = [replace(laser, a0=(k + 0.5) * a_max / n_a, dx_um=0.0, dy_um=0.0, delay_fs=0.0,
+                      variant=0) for k in range(n_a)]
+    b0 = replace(beam, sigma_x_um=0.0, sigma_y_um=0.0, sigma_z_um=0.0, div_rad=0.0, dx_um=0.0,
+                 dy_um=0.0)
+    sb = _inputs.Bins(n_bins=bins.n_bins, lo=bins.lo, hi=bins.hi, log_spaced=bins.log_spaced)
+    n = int(xi[0].numel())
+    bt = Batch(lasers, [b0] * n_a, None, sb, n, xi[0].device, precision=precision)
+    bt.run(xi, w, stream=stream)
+    W = bt.moments[:, 0].clamp_min(1e-300)
+    return bt.spectra / W[:, None]
+
+
+def qs_pw_reconstruct(hist, pw, out=None, stream=None) -> torch.Tensor:
+    """Eq. 5 on the device: out[s, b] = sum_k hist[s, k] pw[k, b] (hist: shots
+    x n_a or one histogram, pw: n_a x bins; float64 device tensors)."""
+    h = hist.reshape(-1, hist.shape[-1]).to(torch.float64).contiguous()
+    p = pw.to(torch.float64).contiguous()
+    ns, na = h.shape
+    nb = p.shape[1]
+    if p.shape[0] != na:
+        raise QsError(QS_ERR_INVALID_ARG, "qs_pw_reconstruct")
+    if out is None:
+        out = torch.zeros(ns, nb, dtype=torch.float64, device=p.device)
+    st = _lib().qs_pw_reconstruct(ns, na, nb, h.data_ptr(), p.data_ptr(), out.data_ptr(),
+                                  _stream_ptr(stream))
+    _check(st, "qs_pw_reconstruct")
+    return out
 
 
 # ---- host-resident samples ------------------------------------------------
