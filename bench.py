@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--cell-n", type=int, default=1 << 24)
     ap.add_argument("--no-photon", action="store_true", help="skip the photon-spectrum measurement")
     ap.add_argument("--photon-n", type=int, default=1 << 19)
+    ap.add_argument("--no-pw", action="store_true", help="skip the plane-wave reconstruction")
     return ap.parse_args()
 
 
@@ -355,6 +356,44 @@ def bench_photon(dev, rank, n=1 << 19, steps=2):
             "workload": "mc2p19_photon_qfp512"}
 
 
+def bench_pw(dev, rank, n_pw=1 << 20, n_hist=4096, steps=3):
+    """Plane-wave reconstruction (Eq. 5): a 61-point plane-wave table (a0
+    from 0 to 12 in steps of 0.2, as in Sec. 3.2; quantum model, 512 cells,
+    2^20 samples per amplitude, 512 energy bins) from one batched sweep, then
+    4096 a_eff histograms contracted with it."""
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.full_qfp(n_pw)
+    bins = wl.bins
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed + 7919 * rank)
+    xi = [torch.randn(n_pw, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    n_a, a_max = 61, 12.2
+    hist = torch.rand(n_hist, n_a, generator=gen, device=dev, dtype=torch.float64)
+    pw = B.pw_table(wl.laser, wl.beam, bins, n_a, a_max, xi)
+    out = B.qs_pw_reconstruct(hist, pw)
+    torch.cuda.synchronize()
+    a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t_t = t_r = 0.0
+    for _ in range(steps):
+        a.record()
+        pw = B.pw_table(wl.laser, wl.beam, bins, n_a, a_max, xi)
+        m.record()
+        B.qs_pw_reconstruct(hist, pw, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        t_t += a.elapsed_time(m)
+        t_r += m.elapsed_time(b)
+    t_t /= steps
+    t_r /= steps
+    return {"metric": "plane-wave table + reconstruction ms", "value": t_t + t_r, "unit": "ms",
+            "table_ms": t_t, "reconstruct_ms": t_r, "n_amplitudes": n_a,
+            "samples_per_amplitude": n_pw, "n_histograms": n_hist, "energy_bins": bins.n_bins,
+            "table_sample_evals_per_s": n_a * n_pw / (t_t * 1e-3),
+            "workload": "pw61_2p20_qfp512_x4096"}
+
+
 def bench_batch(dev, rank, steps=3, n_shots=4096):
     """4096 shots, sample counts log-uniform in [1e3, 1e6], per-shot laser and
     beam drawn from seed, quantum model with 512 phase cells, FP32 with FP64
@@ -602,6 +641,7 @@ def main():
     cell = None if args.no_cell else bench_variant(dev, rank, 1, n=args.cell_n)
     cyc = None if args.no_cell else bench_variant(dev, rank, 2, n=args.cell_n)
     phot = None if args.no_photon else bench_photon(dev, rank, n=args.photon_n)
+    pwr = None if args.no_pw else bench_pw(dev, rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -627,6 +667,7 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
                 "cell_focus": cell, "cycle_chi": cyc, "photon": phot,
+                "pw_reconstruction": pwr,
                 "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:
