@@ -93,6 +93,10 @@ def lib():
                                               C.POINTER(QsoBins), C.c_int64, C.POINTER(_DP),
                                               _DP, _DP]
             L.qso_photon_spectrum.restype = C.c_int
+            L.qso_photon_spectrum2.argtypes = [C.POINTER(QsoLaser), C.POINTER(QsoBeam),
+                                               C.POINTER(QsoBins), C.c_int64, C.POINTER(_DP),
+                                               _DP, _DP, _DP]
+            L.qso_photon_spectrum2.restype = C.c_int
             L.qso_pw_reconstruct.argtypes = [C.c_int, C.c_int, C.c_int, _DP, _DP, _DP]
             L.qso_qfp_rates.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double, _DP]
             L.qso_qfp_integrate.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double,
@@ -291,6 +295,23 @@ def photon_rate(aS: float, mu: float, chi: float, eps: float) -> float:
     """Photons per unit phase and unit photon energy (m c^2) of an electron of
     mean energy mu at chi (LCFA quantum-synchrotron spectrum)."""
     return lib().qso_photon_rate(float(aS), float(mu), float(chi), float(eps))
+
+
+def photon_spectrum_angles(laser, beam, pbins, xi, w=None):
+    """(S, T): the photon spectrum and its angle-weighted moments T[0] (x,
+    the polarisation axis) and T[1] (y); T/S is the mean square photon angle
+    at each bin centre (Eq. 7)."""
+    n = next(len(a) for a in xi if a is not None)
+    arrs, ptrs = _streams(xi, n)
+    w64 = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(int(pbins.n_bins))
+    th = np.zeros(2 * int(pbins.n_bins))
+    rc = lib().qso_photon_spectrum2(C.byref(_laser(laser)), C.byref(_beam(beam)),
+                                    C.byref(_bins(pbins)), n, ptrs, _ptr(w64), _ptr(out),
+                                    _ptr(th))
+    if rc != 0:
+        raise ValueError("photon spectrum needs the quantum model and valid bins")
+    return out, th.reshape(2, -1)
 
 
 def photon_spectrum(laser, beam, pbins, xi, w=None) -> np.ndarray:

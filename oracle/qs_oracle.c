@@ -932,8 +932,24 @@ double qso_photon_rate(double aS, double mu, double chi, double eps) {
 /* Photon spectrum of the beam (quantum model; returns 1 for the classical
    model or invalid bins).  pb: n_bins, lo, hi, log_spaced of the photon
    energy axis (eps in m c^2); out: n_bins values at the bin centres. */
+/* Photon divergence (Eq. 7): photons leave along the emitting electron's
+   direction, which in cell j is its initial angle plus the transverse
+   oscillation in the linearly polarised field (rms A_j/(sqrt2 mu_j) along x,
+   the polarisation axis), within the emission cone ~1/mu_j per axis (the
+   paper's "~1/gamma"); theta2 (optional, 2 x n_bins) receives
+     T_x(eps_b) = sum_i w_i sum_j h rate_ij(eps_b) (thx0^2 + A_j^2/(2 mu_j^2) + 1/mu_j^2)
+     T_y(eps_b) = sum_i w_i sum_j h rate_ij(eps_b) (thy0^2 + 1/mu_j^2)
+   so that T/S is the mean square photon angle per axis at eps_b. */
+int qso_photon_spectrum2(const qso_laser* L, const qso_beam* B, const qso_bins* pb, int64_t n,
+                         const double* const* xi, const double* w, double* out, double* theta2);
+
 int qso_photon_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* pb, int64_t n,
                         const double* const* xi, const double* w, double* out) {
+    return qso_photon_spectrum2(L, B, pb, n, xi, w, out, NULL);
+}
+
+int qso_photon_spectrum2(const qso_laser* L, const qso_beam* B, const qso_bins* pb, int64_t n,
+                         const double* const* xi, const double* w, double* out, double* theta2) {
     int nb = pb->n_bins, N = L->n_phase;
     if (L->model == 0 || nb <= 0 || !(pb->hi > pb->lo) || (pb->log_spaced && !(pb->lo > 0.0)))
         return 1;
@@ -943,7 +959,7 @@ int qso_photon_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* p
     double* eps = (double*)malloc(sizeof(double) * (size_t)nb);
     double* mu_cell = (double*)malloc(sizeof(double) * (size_t)N);
     double* chi_cell = (double*)malloc(sizeof(double) * (size_t)N);
-    qso_sum* acc = (qso_sum*)calloc((size_t)nb, sizeof(qso_sum));
+    qso_sum* acc = (qso_sum*)calloc((size_t)nb * 3, sizeof(qso_sum));
     if (!eps || !mu_cell || !chi_cell || !acc) return 1;
     for (int b = 0; b < nb; ++b)
         eps[b] = pb->log_spaced ? pb->lo * pow(pb->hi / pb->lo, (b + 0.5) / nb)
@@ -956,11 +972,24 @@ int qso_photon_spectrum(const qso_laser* L, const qso_beam* B, const qso_bins* p
         qso_sample s;
         qso_sample_eval_x(L, B, NULL, v, &s, mu_cell, chi_cell);
         if (!isfinite(s.mu)) continue;
-        for (int j = 0; j < N; ++j)
-            for (int b = 0; b < nb; ++b)
-                qso_add(&acc[b], wi * h * qso_photon_rate(aS, mu_cell[j], chi_cell[j], eps[b]));
+        double thx0 = B->div_rad * v[4], thy0 = B->div_rad * v[5];
+        for (int j = 0; j < N; ++j) {
+            double mu = mu_cell[j], chi = chi_cell[j];
+            /* A_j/mu_j from chi_j = sqrt2 mu_j A_j / a_S */
+            double am = chi * aS / (sqrt(2.0) * mu * mu);
+            double tx2 = thx0 * thx0 + 0.5 * am * am + 1.0 / (mu * mu);
+            double ty2 = thy0 * thy0 + 1.0 / (mu * mu);
+            for (int b = 0; b < nb; ++b) {
+                double r = wi * h * qso_photon_rate(aS, mu, chi, eps[b]);
+                qso_add(&acc[b], r);
+                qso_add(&acc[nb + b], r * tx2);
+                qso_add(&acc[2 * nb + b], r * ty2);
+            }
+        }
     }
     for (int b = 0; b < nb; ++b) out[b] = qso_val(&acc[b]);
+    if (theta2)
+        for (int b = 0; b < 2 * nb; ++b) theta2[b] = qso_val(&acc[nb + b]);
     free(eps); free(mu_cell); free(chi_cell); free(acc);
     return 0;
 }

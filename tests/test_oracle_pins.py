@@ -373,6 +373,25 @@ def test_beam_photon_spectrum_energy_balance():
     assert abs(e_ph / e_el - 1) < 0.03, (e_ph, e_el)
 
 
+def test_photon_divergence_plane_wave_sin2_closed_form():
+    """Eq. 7 in a plane wave with a sin^2 envelope, classical regime: photons
+    are emitted in proportion to chi ~ A, so their mean square angle along
+    the polarisation is <A^2/(2 mu^2)> weighted by A, a0^2 (int G^3/int G)
+    /(2 gamma^2) = (5/16) a0^2/gamma^2 (Beta integrals of sin^2n), plus the
+    1/gamma^2 cone; across it the cone alone."""
+    g0, a0 = 1000.0, 2.0
+    L = I.Laser(a0=a0, w0_um=3.0, envelope=I.ENV_SIN2, model=I.MODEL_QFP, n_phase=256)
+    Bpw = I.Beam(gamma_mean=g0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+                 sigma_z_um=0.0, div_rad=0.0)
+    pb = I.Bins(n_bins=240, lo=1e-9, hi=g0, log_spaced=1)
+    S, T = oracle.photon_spectrum_angles(L, Bpw, pb, [np.zeros(1)] * 8)
+    edges = pb.lo * (pb.hi / pb.lo) ** (np.arange(241) / 240)
+    de = np.diff(edges)
+    N, Tx, Ty = (S * de).sum(), (T[0] * de).sum(), (T[1] * de).sum()
+    assert abs(Tx / N * g0 ** 2 / (5 / 16 * a0 ** 2 + 1) - 1) < 0.02
+    assert abs(Ty / N * g0 ** 2 - 1) < 0.02
+
+
 # plane-wave reconstruction (Eq. 5)
 
 def test_pw_reconstruction_converges_to_direct_spectrum():
