@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 5
+#define QS_VERSION 6
 
 typedef enum {
     QS_OK = 0,
@@ -403,6 +403,13 @@ int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
  * (one launch and a wait: make that call before any stream capture; a
  * capturing first call returns QS_ERR_UNSUPPORTED).  Sums are in a fixed
  * order (repeatable bit for bit).  Workspace: qs_photon_workspace_bytes.
+ * Photon divergence (Eq. 7): d_theta2 (optional, device, 2 x n_bins doubles,
+ * n_bins <= 256 when given) receives the same sums weighted by the photon's
+ * mean square angle per axis, photons leaving along the emitting electron:
+ *   x (polarisation): thx0^2 + A_j^2/(2 mu_j^2) + 1/mu_j^2,   y: thy0^2 + 1/mu_j^2
+ * (initial angle, the rms transverse oscillation in the linearly polarised
+ * field, the emission cone ~1/gamma the paper names); sum_b T_x/sum_b S over
+ * the bins above a threshold is the mean square photon angle there.
  * Errors: QS_ERR_INVALID_ARG (descriptors, the classical model),
  * QS_ERR_UNSUPPORTED (QS_VARIANT_CYCLE_CHI), QS_ERR_WORKSPACE, QS_ERR_CUDA.
  */
@@ -410,8 +417,8 @@ size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec* exec, int6
 
 int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
                            const qs_samples* samples, const qs_bins* pbins,
-                           const qs_exec* exec, double* d_spectrum, void* d_workspace,
-                           size_t ws_bytes, void* stream);
+                           const qs_exec* exec, double* d_spectrum, double* d_theta2,
+                           void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
  * qs_pw_reconstruct: plane-wave reconstruction, Eq. 5 (Sec. 3.2): the 3D

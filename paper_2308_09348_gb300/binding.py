@@ -135,7 +135,7 @@ def _lib():
             L.qs_photon_workspace_bytes.restype = C.c_size_t
             L.qs_photon_spectrum.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_beam),
                                              C.POINTER(qs_samples), C.POINTER(qs_bins),
-                                             C.POINTER(qs_exec), _VP, _VP, C.c_size_t, _VP]
+                                             C.POINTER(qs_exec), _VP, _VP, _VP, C.c_size_t, _VP]
             L.qs_photon_spectrum.restype = C.c_int32
             L.qs_pw_reconstruct.argtypes = [C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]
             L.qs_pw_reconstruct.restype = C.c_int32
@@ -350,10 +350,12 @@ def qs_scatter_noalloc(laser, beam, xi, bins, w=None, precision="f32", out: Outp
 
 
 def qs_photon_spectrum(laser, beam, xi, pbins, w=None, precision="f32", out=None,
-                       workspace=None, block=0, grid=0, stream=None,
-                       kernel_events=None) -> torch.Tensor:
+                       workspace=None, block=0, grid=0, stream=None, kernel_events=None,
+                       theta2=None):
     """Photon spectrum dN/deps (eps in m c^2) of the beam at the centres of
-    the photon-energy bins ``pbins`` (n_bins, lo, hi, log_spaced)."""
+    the photon-energy bins ``pbins`` (n_bins, lo, hi, log_spaced).  With
+    ``theta2`` (a 2 x n_bins float64 device tensor, or True to allocate one)
+    also the angle-weighted sums of Eq. 7; returns (spectrum, theta2) then."""
     s, keep = make_samples(xi, w)
     dev = keep[0].device
     Bn = make_bins(pbins)
@@ -366,11 +368,13 @@ def qs_photon_spectrum(laser, beam, xi, pbins, w=None, precision="f32", out=None
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     L, B = make_laser(laser), make_beam(beam)
+    if theta2 is True:
+        theta2 = torch.zeros(2, int(pbins.n_bins), dtype=torch.float64, device=dev)
     st = _lib().qs_photon_spectrum(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
-                                   out.data_ptr(), workspace.data_ptr(), nbytes,
-                                   _stream_ptr(stream))
+                                   out.data_ptr(), None if theta2 is None else theta2.data_ptr(),
+                                   workspace.data_ptr(), nbytes, _stream_ptr(stream))
     _check(st, "qs_photon_spectrum")
-    return out
+    return out if theta2 is None else (out, theta2)
 
 
 GRAD_PARAMS = ("a0", "w0_um", "dx_um", "dy_um", "delay_fs", "gamma_mean", "rel_spread", "div_rad")

@@ -110,34 +110,45 @@ __device__ __forceinline__ double synch_F_d(double xi, double y) {
   return (1.0 - xi + 1.0 / (1.0 - xi)) * k23 - ki13;
 }
 
-// One emitting sample seen by the whole warp: mean energy mu, chi, and the
-// factor c = w h alpha a_S/(2 sqrt3 pi mu^2); adds c F(eps_b/mu, chi) to the
-// lane's bins.  Bins are ascending in eps; groups of 32 whose first energy
-// lies beyond the cut (y > ymax) are skipped by the whole warp.
-template <typename T, typename A>
-__device__ __forceinline__ void photon_add(const float4* __restrict__ tab, const T* __restrict__ eps,
-                                           int nb, T mu, T chi, T c, A& acc) {
-  const int lane = threadIdx.x & 31;
-  const T imu = (T)1 / mu, gy = (T)2 / ((T)3 * chi);
-  const T yc = (T)1.5 * chi * (T)kPhYmax;              // xi/(1 - xi) below this
-  const T ecut = mu * yc / ((T)1 + yc);
+// Angular moments (Eq. 7): photons leave along the emitting electron's
+// direction, in cell j its initial angle plus the transverse oscillation in
+// the linearly polarised field (rms A_j/(sqrt2 mu_j) along x, the
+// polarisation axis), within the emission cone ~1/mu_j per axis:
+//   theta_x^2 = thx0^2 + A_j^2/(2 mu_j^2) + 1/mu_j^2,
+//   theta_y^2 = thy0^2 + 1/mu_j^2,
+// with A_j/mu_j = chi_j/(cchi mu_j^2) (chi = cchi A mu).  With ANG the
+// kernel also sums the rates times these into T_x, T_y per bin.
+constexpr int kPhMaxBinsAng = 256;
+
+// Per-lane bin accumulators (NA = 3 sets with ANG: S, T_x, T_y): compensated
+// FP32 sums (FP32 path), FP64 sums.
+template <typename T, bool ANG> struct PhAcc;
+template <bool ANG> struct PhAcc<float, ANG> {
+  static constexpr int NA = ANG ? 3 : 1, K = ANG ? kPhMaxBinsAng / 32 : kPhK;
+  float s[NA][K], c[NA][K];
+  __device__ __forceinline__ void init() {
 #pragma unroll
-  for (int k = 0; k < kPhK; ++k) {                     // unrolled: acc stays in registers
-    if (32 * k >= nb || !(eps[32 * k] < ecut)) break;
-    const int b = 32 * k + lane;
-    if (b < nb && eps[b] < ecut) {
-      const T xi = eps[b] * imu;
-      if constexpr (sizeof(T) == 4) {
-        const float r1 = M<float>::rcp(__fsub_rn(1.f, xi));
-        const float y = __fmul_rn(__fmul_rn(gy, xi), r1);
-        acc.add(k, __fmul_rn(c, synch_F(tab, xi, r1, y)));
-      } else {
-        const double y = gy * xi / (1.0 - xi);
-        acc.add(k, c * synch_F_d(xi, y));
-      }
-    }
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[m][k] = c[m][k] = 0.f;
   }
-}
+  __device__ __forceinline__ void add(int m, int k, float x) { kahan(s[m][k], c[m][k], x); }
+  __device__ __forceinline__ double get(int m, int k) const {
+    return (double)s[m][k] - (double)c[m][k];
+  }
+};
+template <bool ANG> struct PhAcc<double, ANG> {
+  static constexpr int NA = ANG ? 3 : 1, K = ANG ? kPhMaxBinsAng / 32 : kPhK;
+  double s[NA][K];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[m][k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int m, int k, double x) { s[m][k] += x; }
+  __device__ __forceinline__ double get(int m, int k) const { return s[m][k]; }
+};
 
 // FP32 emitter of one cell: {1/mu, 2/(3 chi), eps cut where y = ymax, c}
 // (a zero cut when c = 0: nothing emitted).
@@ -148,44 +159,27 @@ __device__ __forceinline__ float4 emitter(float mu, float chi, float c) {
   return make_float4(M<float>::rcp(mu), M<float>::rcp(__fmul_rn(1.5f, chi)), cut, c);
 }
 
-// Per-lane bin accumulators: compensated FP32 sums (FP32 path), FP64 sums.
-template <typename T> struct PhAcc;
-template <> struct PhAcc<float> {
-  float s[kPhK], c[kPhK];
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int k = 0; k < kPhK; ++k) s[k] = c[k] = 0.f;
-  }
-  __device__ __forceinline__ void add(int k, float x) { kahan(s[k], c[k], x); }
-  __device__ __forceinline__ double get(int k) const { return (double)s[k] - (double)c[k]; }
-};
-template <> struct PhAcc<double> {
-  double s[kPhK];
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int k = 0; k < kPhK; ++k) s[k] = 0.0;
-  }
-  __device__ __forceinline__ void add(int k, double x) { s[k] += x; }
-  __device__ __forceinline__ double get(int k) const { return s[k]; }
-};
-
 // Shared memory: phase table, photon table (FP32), bin energies, per-warp
 // partial spectra for the CTA's fixed-order reduction, per-warp emitters
 // (FP32).
 template <typename T>
-__host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block) {
+__host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block, bool ang) {
   const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
   const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
   const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
-  const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * sizeof(float4) : 0;
-  return tab + pt + e + (size_t)(block / 32) * nb * sizeof(double) + stage;
+  const size_t stage =
+      sizeof(T) == 4 ? (size_t)(block / 32) * 64 * (sizeof(float4) + sizeof(float2)) : 0;
+  return tab + pt + e + (size_t)(block / 32) * (ang ? 3 : 1) * nb * sizeof(double) + stage;
 }
 
-// K7.  pref = h alpha a_S/(2 sqrt3 pi); eps_b at the bin centres.
-template <typename T, int VAR>
+// K7.  pref = h alpha a_S/(2 sqrt3 pi); eps_b at the bin centres.  Per-CTA
+// partials: NA x nb doubles (S, then T_x, T_y with ANG).
+template <typename T, int VAR, bool ANG>
 __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double lo, double hi,
                                                 int log_spaced, double* __restrict__ partials) {
   using TT = typename Tab<T>::type;
+  using Acc = PhAcc<T, ANG>;
+  constexpr int NA = Acc::NA, KB = Acc::K;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t tb = ((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15;
   TT* tab = reinterpret_cast<TT*>(smem);
@@ -193,8 +187,10 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
   T* eps = reinterpret_cast<T*>(smem + tb + (sizeof(T) == 4 ? kPhN * sizeof(float4) : 0));
   double* part = reinterpret_cast<double*>(
       reinterpret_cast<unsigned char*>(eps) + (((size_t)nb * sizeof(T) + 15) & ~(size_t)15));
-  float4* stage = reinterpret_cast<float4*>(part + (size_t)(blockDim.x / 32) * nb) +
-                  (threadIdx.x >> 5) * 64;            // FP32: the warp's emitters
+  const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* stage = reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) + warp * 64;
+  float2* stageA = reinterpret_cast<float2*>(reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) +
+                                             nwarp * 64) + warp * 64;
   for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (sizeof(T) == 4)
     for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
@@ -205,22 +201,21 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
 
   const double pref = p.h * kAlpha / (2.0 * 1.7320508075688772935 * 3.14159265358979323846 *
                                       p.cchi / 1.4142135623730950488);   // h alpha a_S/(2 sqrt3 pi)
-  PhAcc<T> acc;
+  Acc acc;
   acc.init();
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (sizeof(T) == 4) {
-    const float prf = (float)pref;
+    const float prf = (float)pref, icchi = (float)(1.0 / p.cchi);
     // two samples per thread through the packed scheme, warp by warp
     for (int64_t kb = t0 - lane; 2 * kb < p.n; kb += stride) {
       const int64_t k = kb + lane, i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
-      const bool act = i0 < p.n;
-      float g0f = 1.f, g1f = 1.f, tx, ty, a0 = 0.f, a1 = 0.f, w0 = 0.f, w1 = 0.f;
+      float g0f = 1.f, g1f = 1.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, a0 = 0.f, a1 = 0.f;
+      float w0 = 0.f, w1 = 0.f;
       Path<float> P0{}, P1{};
-      if (act) {
-        a0 = focus<float>(p, i0, g0f, tx, ty, (VAR & kVarCell) ? &P0 : nullptr);
-        a1 = focus<float>(p, i1, g1f, tx, ty, (VAR & kVarCell) ? &P1 : nullptr);
+      if (i0 < p.n) {
+        a0 = focus<float>(p, i0, g0f, tx0, ty0, (VAR & kVarCell) ? &P0 : nullptr);
+        a1 = focus<float>(p, i1, g1f, tx1, ty1, (VAR & kVarCell) ? &P1 : nullptr);
         w0 = p.weighted ? load_t<float>(p.w, i0, p.dtype) : 1.f;
         w1 = i1 != i0 ? (p.weighted ? load_t<float>(p.w, i1, p.dtype) : 1.f) : 0.f;
         if (!(w0 >= 0.f) || !isfinite(w0) || !isfinite(a0) || !isfinite(g0f)) w0 = 0.f;
@@ -234,11 +229,22 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
                        &chi);
         const float c0 = (w0 > 0.f && chi.x > 0.f) ? __fmul_rn(__fmul_rn(prf, w0), M<float>::rcp(__fmul_rn(mu.x, mu.x))) : 0.f;
         const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;
-        // the warp's 64 emitters of this cell, staged once: {1/mu, 2/(3 chi),
-        // energy cut (y = ymax), c}; a cut of 0 marks no emission
+        // the warp's 64 emitters of this cell, staged once
         const float4 e0 = emitter(mu.x, chi.x, c0), e1 = emitter(mu.y, chi.y, c1);
         stage[lane] = e0;
         stage[32 + lane] = e1;
+        if constexpr (ANG) {
+          // mean square angles (A/mu = chi/(cchi mu^2)), times c
+          const float am0 = __fmul_rn(__fmul_rn(chi.x, icchi), __fmul_rn(e0.x, e0.x));
+          const float am1 = __fmul_rn(__fmul_rn(chi.y, icchi), __fmul_rn(e1.x, e1.x));
+          const float cone0 = __fmul_rn(e0.x, e0.x), cone1 = __fmul_rn(e1.x, e1.x);
+          stageA[lane] = make_float2(
+              __fmul_rn(c0, __fmaf_rn(tx0, tx0, __fmaf_rn(0.5f, __fmul_rn(am0, am0), cone0))),
+              __fmul_rn(c0, __fmaf_rn(ty0, ty0, cone0)));
+          stageA[32 + lane] = make_float2(
+              __fmul_rn(c1, __fmaf_rn(tx1, tx1, __fmaf_rn(0.5f, __fmul_rn(am1, am1), cone1))),
+              __fmul_rn(c1, __fmaf_rn(ty1, ty1, cone1)));
+        }
         float emax = fmaxf(e0.z, e1.z);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -246,11 +252,11 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
         // lane b of group k: its energy against every emitter (independent
         // evaluations, summed plainly over the 64, then compensated)
 #pragma unroll
-        for (int k = 0; k < kPhK; ++k) {
-          if (32 * k >= nb || !(eps[32 * k] < emax)) break;
-          const int b = 32 * k + lane;
+        for (int kk = 0; kk < KB; ++kk) {
+          if (32 * kk >= nb || !(eps[32 * kk] < emax)) break;
+          const int b = 32 * kk + lane;
           const float e = b < nb ? eps[b] : 3.4e38f;
-          float part = 0.f;
+          float ps = 0.f, px = 0.f, py = 0.f;
 #pragma unroll 4
           for (int q = 0; q < 64; ++q) {
             const float4 em = stage[q];
@@ -258,18 +264,29 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
               const float xi = __fmul_rn(e, em.x);
               const float r1 = M<float>::rcp(__fsub_rn(1.f, xi));
               const float y = __fmul_rn(__fmul_rn(em.y, xi), r1);
-              part = __fmaf_rn(em.w, synch_F(ptab, xi, r1, y), part);
+              const float F = synch_F(ptab, xi, r1, y);
+              ps = __fmaf_rn(em.w, F, ps);
+              if constexpr (ANG) {
+                const float2 ea = stageA[q];
+                px = __fmaf_rn(ea.x, F, px);
+                py = __fmaf_rn(ea.y, F, py);
+              }
             }
           }
-          acc.add(k, part);
+          acc.add(0, kk, ps);
+          if constexpr (ANG) {
+            acc.add(1, kk, px);
+            acc.add(2, kk, py);
+          }
         }
         __syncwarp();
       }
     }
   } else {
+    const double icchi = 1.0 / p.cchi;
     for (int64_t ib = t0 - lane; ib < p.n; ib += stride) {
       const int64_t i = ib + lane;
-      double g0 = 1.0, tx, ty, a = 0.0, w = 0.0;
+      double g0 = 1.0, tx = 0.0, ty = 0.0, a = 0.0, w = 0.0;
       Path<double> P{};
       if (i < p.n) {
         a = focus<double>(p, i, g0, tx, ty, (VAR & kVarCell) ? &P : nullptr);
@@ -282,42 +299,68 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
         qfp_cell<VAR>(p, reinterpret_cast<const double*>(tab)[j], j, a, g0, P, du, V, gprev, &mu,
                       &chi);
         const double c = (w > 0.0 && chi > 0.0) ? pref * w / (mu * mu) : 0.0;
+        double cx = 0.0, cy = 0.0;
+        if (ANG && c > 0.0) {
+          const double am = chi * icchi / (mu * mu), cone = 1.0 / (mu * mu);
+          cx = c * (tx * tx + 0.5 * am * am + cone);
+          cy = c * (ty * ty + cone);
+        }
         unsigned m = __ballot_sync(0xffffffffu, c > 0.0);
         while (m) {
           const int s = __ffs(m) - 1;
           m &= m - 1;
-          photon_add<double>(nullptr, eps, nb, __shfl_sync(0xffffffffu, mu, s),
-                             __shfl_sync(0xffffffffu, chi, s), __shfl_sync(0xffffffffu, c, s),
-                             acc);
+          const double ms = __shfl_sync(0xffffffffu, mu, s), xs = __shfl_sync(0xffffffffu, chi, s);
+          const double cs = __shfl_sync(0xffffffffu, c, s);
+          const double cxs = __shfl_sync(0xffffffffu, cx, s), cys = __shfl_sync(0xffffffffu, cy, s);
+          const double imu = 1.0 / ms, gy = 2.0 / (3.0 * xs), yc = 1.5 * xs * kPhYmax;
+          const double ecut = ms * yc / (1.0 + yc);
+#pragma unroll
+          for (int kk = 0; kk < KB; ++kk) {
+            if (32 * kk >= nb || !(eps[32 * kk] < ecut)) break;
+            const int b = 32 * kk + lane;
+            if (b < nb && eps[b] < ecut) {
+              const double xi = eps[b] * imu;
+              const double F = synch_F_d(xi, gy * xi / (1.0 - xi));
+              acc.add(0, kk, cs * F);
+              if constexpr (ANG) {
+                acc.add(1, kk, cxs * F);
+                acc.add(2, kk, cys * F);
+              }
+            }
+          }
         }
       }
     }
   }
 
   // fixed-order reduction: lanes own distinct bins; warps in order
-  const int warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kPhK; ++k)
-    if (32 * k + lane < nb) part[warp * nb + 32 * k + lane] = acc.get(k);
+  for (int m = 0; m < NA; ++m)
+#pragma unroll
+    for (int kk = 0; kk < KB; ++kk)
+      if (32 * kk + lane < nb) part[(warp * NA + m) * nb + 32 * kk + lane] = acc.get(m, kk);
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    double s = 0.0;
-    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += part[wv * nb + b];
-    partials[(size_t)blockIdx.x * nb + b] = s;
+  for (int mb = threadIdx.x; mb < NA * nb; mb += blockDim.x) {
+    double sum = 0.0;
+    for (int wv = 0; wv < nwarp; ++wv) sum += part[wv * NA * nb + mb];
+    partials[(size_t)blockIdx.x * NA * nb + mb] = sum;
   }
 }
 
-// K8: CTA partials in CTA order (compensated).
-__global__ void k_photon_final(int grid, int nb, const double* __restrict__ partials,
-                               double* __restrict__ out) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+// K8: CTA partials in CTA order (compensated); entry m of NA goes to the
+// spectrum (m = 0) or theta2 (m = 1, 2).
+__global__ void k_photon_final(int grid, int nb, int na, const double* __restrict__ partials,
+                               double* __restrict__ out, double* __restrict__ theta2) {
+  for (int mb = blockIdx.x * blockDim.x + threadIdx.x; mb < na * nb;
+       mb += gridDim.x * blockDim.x) {
     double s = 0.0, c = 0.0;
     for (int g = 0; g < grid; ++g) {
-      const double x = partials[(size_t)g * nb + b], t = s + x;
+      const double x = partials[(size_t)g * na * nb + mb], t = s + x;
       c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
       s = t;
     }
-    out[b] = s + c;
+    if (mb < nb) out[mb] = s + c;
+    else theta2[mb - nb] = s + c;
   }
 }
 
@@ -363,11 +406,11 @@ int photon_gmax(int sms, int block, int grid_req, int64_t n) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T, int VAR>
+template <typename T, int VAR, bool ANG>
 int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_io, size_t smem,
                       double* partials, cudaStream_t st, const qs_exec* ex) {
   int grid = *grid_io;
-  auto kern = k_photon<T, VAR>;
+  auto kern = k_photon<T, VAR, ANG>;
   static bool attr[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
@@ -413,13 +456,14 @@ extern "C" size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec*
   if (block > 256) block = 256;
   if (device_sms(&sms) != QS_OK) return 0;
   const int g = photon_gmax(sms, block, grid, n);
-  return align_up((size_t)g * pbins->n_bins * sizeof(double), 256);
+  return align_up((size_t)g * 3 * pbins->n_bins * sizeof(double), 256);
 }
 
 extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
                                       const qs_samples* samples, const qs_bins* pbins,
                                       const qs_exec* exec, double* d_spectrum,
-                                      void* d_workspace, size_t ws_bytes, void* stream) {
+                                      double* d_theta2, void* d_workspace, size_t ws_bytes,
+                                      void* stream) {
   int32_t st;
   if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
       (st = validate_samples(samples)) || (st = check_pbins(pbins)))
@@ -427,13 +471,15 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   if (laser->model != QS_MODEL_QFP) return QS_ERR_INVALID_ARG;
   if (laser->variant & ~QS_VARIANT_CELL_FOCUS) return QS_ERR_UNSUPPORTED;
   if (!d_spectrum) return QS_ERR_INVALID_ARG;
+  const bool ang = d_theta2 != nullptr;
+  if (ang && pbins->n_bins > kPhMaxBinsAng) return QS_ERR_INVALID_ARG;
   int prec, wbits, block, grid, sms;
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
   const int gmax = photon_gmax(sms, block, grid, samples->n);
   int g = gmax;
-  const size_t need = align_up((size_t)gmax * pbins->n_bins * sizeof(double), 256);
+  const size_t need = align_up((size_t)gmax * 3 * pbins->n_bins * sizeof(double), 256);
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < need) return QS_ERR_WORKSPACE;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if (prec == QS_F32 && (st = photon_table(cs))) return st;
@@ -441,16 +487,27 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   fill_params(p, laser, beam, samples, nullptr, wbits);
   double* part = static_cast<double*>(d_workspace);
   const bool loc = (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
-  const size_t smem = prec == QS_F64 ? photon_smem<double>(p.n_phase, pbins->n_bins, block)
-                                     : photon_smem<float>(p.n_phase, pbins->n_bins, block);
+  const size_t smem = prec == QS_F64 ? photon_smem<double>(p.n_phase, pbins->n_bins, block, ang)
+                                     : photon_smem<float>(p.n_phase, pbins->n_bins, block, ang);
   if (smem > (size_t)kSmemLimit) return QS_ERR_INVALID_ARG;
-  if (prec == QS_F64)
-    st = loc ? launch_photon<double, kVarCell>(p, pbins, block, &g, smem, part, cs, exec)
-             : launch_photon<double, 0>(p, pbins, block, &g, smem, part, cs, exec);
-  else
-    st = loc ? launch_photon<float, kVarCell>(p, pbins, block, &g, smem, part, cs, exec)
-             : launch_photon<float, 0>(p, pbins, block, &g, smem, part, cs, exec);
+  if (prec == QS_F64) {
+    if (ang)
+      st = loc ? launch_photon<double, kVarCell, true>(p, pbins, block, &g, smem, part, cs, exec)
+               : launch_photon<double, 0, true>(p, pbins, block, &g, smem, part, cs, exec);
+    else
+      st = loc ? launch_photon<double, kVarCell, false>(p, pbins, block, &g, smem, part, cs, exec)
+               : launch_photon<double, 0, false>(p, pbins, block, &g, smem, part, cs, exec);
+  } else {
+    if (ang)
+      st = loc ? launch_photon<float, kVarCell, true>(p, pbins, block, &g, smem, part, cs, exec)
+               : launch_photon<float, 0, true>(p, pbins, block, &g, smem, part, cs, exec);
+    else
+      st = loc ? launch_photon<float, kVarCell, false>(p, pbins, block, &g, smem, part, cs, exec)
+               : launch_photon<float, 0, false>(p, pbins, block, &g, smem, part, cs, exec);
+  }
   if (st) return st;
-  k_photon_final<<<(pbins->n_bins + 127) / 128, 128, 0, cs>>>(g, pbins->n_bins, part, d_spectrum);
+  const int na = ang ? 3 : 1;
+  k_photon_final<<<(na * pbins->n_bins + 127) / 128, 128, 0, cs>>>(g, pbins->n_bins, na, part,
+                                                                    d_spectrum, d_theta2);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }

@@ -105,6 +105,39 @@ def test_energy_balance_with_the_electron_loss():
     assert abs(e_ph / e_el - 1) < 0.03
 
 
+@pytest.mark.parametrize("prec,n", [("f64", 6), ("f32", 101)])
+def test_angular_moments_match_oracle(prec, n):
+    """Eq. 7's angle-weighted sums beside the spectrum, against the oracle."""
+    L, Bm, xi = _case(n)
+    xt, _ = _dev(xi)
+    S, T = B.qs_photon_spectrum(L, Bm, xt, PB, precision=prec, theta2=True)
+    S, T = S.cpu().numpy(), T.cpu().numpy()
+    Sr, Tr = oracle.photon_spectrum_angles(L, Bm, PB, [a.astype(np.float64) for a in xi])
+    tol = 1e-10 if prec == "f64" else 1e-4
+    for a, r in ((S, Sr), (T[0], Tr[0]), (T[1], Tr[1])):
+        assert np.abs(a - r).sum() / np.abs(r).sum() < tol
+    # mean square angles are of order (a/gamma)^2 along x, (1/gamma)^2 + div^2 along y
+    assert (T[0] * S).sum() > (T[1] * S).sum() > 0
+
+
+def test_plane_wave_photon_divergence_closed_form():
+    """Plane wave with a sin^2 envelope, classical regime: photon-number
+    weighted mean square angle (5/16 a0^2 + 1)/gamma^2 along the
+    polarisation, 1/gamma^2 across (FP32 path, all photons)."""
+    g0, a0 = 1000.0, 2.0
+    L = I.Laser(a0=a0, w0_um=3.0, envelope=I.ENV_SIN2, model=I.MODEL_QFP, n_phase=256)
+    Bpw = I.Beam(gamma_mean=g0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+                 sigma_z_um=0.0, div_rad=0.0)
+    pb = I.Bins(n_bins=240, lo=1e-9, hi=g0, log_spaced=1)
+    xt = [torch.zeros(64, device="cuda") for _ in range(8)]
+    S, T = B.qs_photon_spectrum(L, Bpw, xt, pb, theta2=True)
+    S, T = S.cpu().numpy(), T.cpu().numpy()
+    de = np.diff(pb.lo * (pb.hi / pb.lo) ** (np.arange(241) / 240))
+    N = (S * de).sum()
+    assert abs((T[0] * de).sum() / N * g0 ** 2 / (5 / 16 * a0 ** 2 + 1) - 1) < 0.02
+    assert abs((T[1] * de).sum() / N * g0 ** 2 - 1) < 0.02
+
+
 def test_rejected_requests():
     L, Bm, xi = _case(10)
     xt, _ = _dev(xi)
@@ -113,6 +146,8 @@ def test_rejected_requests():
     with pytest.raises(QsError) as e:
         B.qs_photon_spectrum(I.Laser(**{**L.__dict__, "variant": I.VAR_CYCLE_CHI}), Bm, xt, PB)
     assert e.value.status == B.QS_ERR_UNSUPPORTED
+    with pytest.raises(QsError):          # angular sums: at most 256 bins
+        B.qs_photon_spectrum(L, Bm, xt, I.Bins(n_bins=300, lo=0.0, hi=1.0), theta2=True)
     for pb in (I.Bins(n_bins=0, lo=0.0, hi=1.0), I.Bins(n_bins=513, lo=0.0, hi=1.0),
                I.Bins(n_bins=8, lo=0.0, hi=1.0, log_spaced=1), I.Bins(n_bins=8, lo=2.0, hi=1.0)):
         with pytest.raises(QsError):
