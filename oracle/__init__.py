@@ -98,6 +98,11 @@ def lib():
                                                _DP, _DP, _DP]
             L.qso_photon_spectrum2.restype = C.c_int
             L.qso_pw_reconstruct.argtypes = [C.c_int, C.c_int, C.c_int, _DP, _DP, _DP]
+            L.qso_bessel_i0.argtypes = [C.c_double]
+            L.qso_bessel_i0.restype = C.c_double
+            L.qso_analytic_aeff.argtypes = [C.POINTER(QsoLaser), C.c_int, _DP, C.c_int, _DP, _DP]
+            L.qso_analytic_ll.argtypes = [C.POINTER(QsoLaser), C.c_int, _DP, C.c_double, C.c_int,
+                                          _DP, _DP]
             L.qso_qfp_rates.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double, _DP]
             L.qso_qfp_integrate.argtypes = [C.POINTER(QsoLaser), C.c_double, C.c_double, C.c_double,
                                             C.c_double, C.c_double, _DP, _DP]
@@ -338,4 +343,35 @@ def pw_reconstruct(hist, pw) -> np.ndarray:
     assert pw.shape[0] == na
     out = np.zeros((ns, nb))
     lib().qso_pw_reconstruct(ns, na, nb, _ptr(hist), _ptr(pw), _ptr(out))
+    return out
+
+
+GEOMETRIES = {"short": 0, "thin": 1, "wide": 2}
+
+
+def bessel_i0(x: float) -> float:
+    return lib().qso_bessel_i0(float(x))
+
+
+def _geom_par(radius=0.0, length=0.0, d_perp=0.0, d_par=0.0, n=1.0):
+    return np.array([radius, length, d_perp, d_par, n], dtype=np.float64)
+
+
+def analytic_aeff(laser, geom, a, **par) -> np.ndarray:
+    """Table 1: dN/da_eff on the grid ``a`` for an idealised beam ("short":
+    radius R in the collision plane; "thin": on axis, flat-top length; "wide":
+    uniform density n across the laser) with offsets d_perp, d_par."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros_like(a)
+    lib().qso_analytic_aeff(C.byref(_laser(laser)), GEOMETRIES[geom], _ptr(_geom_par(**par)),
+                            a.size, _ptr(a), _ptr(out))
+    return out
+
+
+def analytic_ll(laser, geom, gamma0, g, **par) -> np.ndarray:
+    """Table 2 (via Eq. 6): the classical final-energy density dN/dgamma."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros_like(g)
+    lib().qso_analytic_ll(C.byref(_laser(laser)), GEOMETRIES[geom], _ptr(_geom_par(**par)),
+                          float(gamma0), g.size, _ptr(g), _ptr(out))
     return out

@@ -33,6 +33,8 @@
  *   qso_photon_spectrum  pinned (energy balance with the electrons' loss
  *                        to the Gaunt fit's accuracy; exact moments of
  *                        the spectrum; classical synchrotron limit)
+ *   qso_analytic_*       pinned (Monte Carlo histograms of the oracle's own
+ *                        beams for every geometry; I0 against scipy)
  *   qso_pw_reconstruct   pinned (converges to the direct 3D spectrum at
  *                        first order in the a-grid spacing, classical model)
  *   per-cell focus       pinned (adaptive quadrature of Eq. 3's exponent
@@ -1010,4 +1012,101 @@ void qso_pw_reconstruct(int n_shots, int n_a, int n_bins, const double* hist, co
                 qso_add(&acc, hist[(size_t)sh * n_a + k] * pw[(size_t)k * n_bins + b]);
             out[(size_t)sh * n_bins + b] = qso_val(&acc);
         }
+}
+
+/* ------------------------------------------------------------------------
+ * Analytic distributions (Table 1, Table 2 via Eq. 6) for idealised beams,
+ * evaluated on a grid.  Geometry: the collision plane sits at d_par from the
+ * focal plane (z_R = pi W0^2/lambda, W = W0 sqrt(1 + d_par^2/z_R^2),
+ * a_par = a0 W0/W); transverse offset d_perp of the beam centre from the
+ * laser axis.
+ *   short beam (all electrons in the collision plane, Gaussian transverse
+ *     density ~ exp(-rho^2/R^2)): a = a_par exp(-rho'^2/W^2) with rho' the
+ *     distance to the axis, whose square has the offset (Rice) distribution,
+ *     so dN/da = N (W^2/R^2)(1/a)(a/a_par)^(W^2/R^2)
+ *                  I0(2 (d_perp/R)(W/R) sqrt(ln(a_par/a))) exp(-d_perp^2/R^2),
+ *     0 < a < a_par (the printed theta(a - a_par) read with its support the
+ *     right way round);
+ *   thin beam (on the axis, flat-top length L): collision positions uniform
+ *     on [z-, z+], z+- = d_par +- L/4 (the crossing is at half the lag),
+ *     a = a0/sqrt(1 + z^2/z_R^2), each root z = +-z_a, z_a = z_R
+ *     sqrt(a0^2/a^2 - 1), inside [z-, z+] adds (2N z_R/L)(a0^2/a^2)/
+ *     sqrt(a0^2 - a^2);
+ *   wide beam (uniform density n_b across the laser, flat-top length L):
+ *     per collision plane z the area where a_eff > a grows as pi W0^2 q
+ *     ln(...), so dN/da = (2 pi n_b W0^2/a) int q(z) dz over [z-, z+]
+ *     clipped to |z| < z_a, q = 1 + z^2/z_R^2 (the factor 2: unit length
+ *     of beam is half a unit of collision position).
+ * Classical spectrum: gamma_f(a) = gamma0/(1 + c_RR gamma0 a^2) (Eq. 3) is
+ * monotone, so dN/dgamma = (dN/da)(a(gamma)) / (2 a c_RR gamma^2) with
+ * a(gamma) = sqrt((gamma0 - gamma)/(c_RR gamma0 gamma)).
+ * geom: 0 short, 1 thin, 2 wide; par: radius R, length L, d_perp, d_par,
+ * N (or n_b for the wide beam).
+ * ------------------------------------------------------------------------ */
+
+/* I0 by its power series (x <= 30) or its asymptotic expansion. */
+double qso_bessel_i0(double x) {
+    x = fabs(x);
+    if (x <= 30.0) {
+        double t = 1.0, s = 1.0, q = 0.25 * x * x;
+        for (int k = 1; k < 200; ++k) {
+            t *= q / ((double)k * k);
+            s += t;
+            if (t < 1e-17 * s) break;
+        }
+        return s;
+    }
+    double y = 1.0 / (8.0 * x), t = 1.0, s = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        t *= (2.0 * k - 1.0) * (2.0 * k - 1.0) * y / k;
+        s += t;
+        if (fabs(t) < 1e-17) break;
+    }
+    return exp(x) / sqrt(2.0 * QSO_PI * x) * s;
+}
+
+static double qso_aeff_density(const qso_laser* L, int geom, const double* par, double a) {
+    double c[10];
+    qso_constants(L, c);
+    double zR = c[2], a0 = L->a0, W0 = L->w0_um;
+    double R = par[0], Lb = par[1], dperp = par[2], dpar = par[3], nb = par[4];
+    if (!(a > 0.0)) return 0.0;
+    if (geom == 0) {
+        double W = W0 * sqrt(1.0 + dpar * dpar / (zR * zR)), apar = a0 * W0 / W;
+        if (!(a < apar)) return 0.0;
+        double k = W * W / (R * R);
+        return nb * k / a * pow(a / apar, k) *
+               qso_bessel_i0(2.0 * (dperp / R) * (W / R) * sqrt(log(apar / a))) *
+               exp(-dperp * dperp / (R * R));
+    }
+    if (!(a < a0)) return 0.0;
+    double za = zR * sqrt(a0 * a0 / (a * a) - 1.0);
+    double zm = dpar - Lb / 4.0, zp = dpar + Lb / 4.0;
+    if (geom == 1) {
+        int roots = (za >= zm && za <= zp) + (-za >= zm && -za <= zp);
+        return roots * (2.0 * nb * zR / Lb) * (a0 * a0 / (a * a)) / sqrt(a0 * a0 - a * a);
+    }
+    double lo = zm > -za ? zm : -za, hi = zp < za ? zp : za;
+    if (!(hi > lo)) return 0.0;
+    double Fh = hi * (1.0 + hi * hi / (3.0 * zR * zR)), Fl = lo * (1.0 + lo * lo / (3.0 * zR * zR));
+    return 2.0 * QSO_PI * nb * W0 * W0 / a * (Fh - Fl);
+}
+
+void qso_analytic_aeff(const qso_laser* L, int geom, const double* par, int n, const double* a,
+                       double* out) {
+    for (int i = 0; i < n; ++i) out[i] = qso_aeff_density(L, geom, par, a[i]);
+}
+
+void qso_analytic_ll(const qso_laser* L, int geom, const double* par, double gamma0, int n,
+                     const double* g, double* out) {
+    double c[10];
+    qso_constants(L, c);
+    double cRR = c[9];
+    for (int i = 0; i < n; ++i) {
+        double gm = g[i];
+        out[i] = 0.0;
+        if (!(gm > 0.0) || !(gm < gamma0)) continue;
+        double a = sqrt((gamma0 - gm) / (cRR * gamma0 * gm));
+        out[i] = qso_aeff_density(L, geom, par, a) / (2.0 * a * cRR * gm * gm);
+    }
 }

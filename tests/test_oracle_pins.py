@@ -757,6 +757,89 @@ def test_table2_thin_beam_ll_spectrum():
     _hist_vs_density(r["spectrum"], edges, dens, n)
 
 
+# the analytic fast path: Table 1 / Table 2 closed forms evaluated on a grid
+
+def test_bessel_i0_vs_scipy():
+    for x in (0.0, 1e-3, 0.5, 3.0, 29.9, 30.1, 100.0, 600.0):
+        assert abs(oracle.bessel_i0(x) / i0(x) - 1) < 1e-14, x
+
+
+@pytest.mark.parametrize("case", ["aligned", "offset", "delay"])
+def test_analytic_short_beam_vs_monte_carlo(case):
+    n, sigma, a0, w0, lam = 1 << 16, 1.5, 12.0, 2.0, 1.0
+    dx = 2.0 if case == "offset" else 0.0
+    delay = 60.0 if case == "delay" else 0.0
+    L, B, xi = _short_beam_inputs(n, 21, sigma, dx=dx, delay=delay, a0=a0, w0=w0, lam=lam)
+    r = oracle.scatter(L, B, I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=48, aeff_max=a0), xi)
+    par = dict(radius=math.sqrt(2) * sigma, d_perp=dx, d_par=-0.299792458 * delay / 2, n=n)
+    edges = np.linspace(0, a0, 49)
+    _hist_vs_density(r["aeff_hist"], edges,
+                     lambda a: float(oracle.analytic_aeff(L, "short", [a], **par)[0]) / n, n)
+
+
+def test_analytic_thin_beam_vs_monte_carlo_with_offset():
+    """Thin beam with the collision centre off the focal plane (one branch
+    leaves the beam's span)."""
+    n, a0, w0, lam, Lb, dpar = 1 << 16, 12.0, 2.0, 1.0, 60.0, 9.0
+    L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, model=I.MODEL_LL,
+                delay_fs=-2 * dpar / 0.299792458)
+    B = I.Beam(gamma_mean=5000.0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+               sigma_z_um=Lb / (2 * math.sqrt(3)))
+    xi = I.sample_streams(n, 22, dtype=np.float64)
+    xi[2] = I.rng(97).uniform(-math.sqrt(3), math.sqrt(3), n)
+    r = oracle.scatter(L, B, I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=64, aeff_max=a0), xi)
+    edges = np.linspace(0, a0, 65)
+    par = dict(length=Lb, d_par=dpar, n=n)
+    _hist_vs_density(r["aeff_hist"], edges,
+                     lambda a: float(oracle.analytic_aeff(L, "thin", [a], **par)[0]) / n, n)
+
+
+def test_analytic_wide_beam_vs_monte_carlo():
+    """Wide beam: uniform density across a box much wider than the spot,
+    flat-top length, collision centre off the focal plane."""
+    n, a0, w0, lam, Lb, dpar, X = 1 << 17, 12.0, 2.0, 1.0, 60.0, 6.0, 12.0
+    L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, model=I.MODEL_LL,
+                delay_fs=-2 * dpar / 0.299792458)
+    B = I.Beam(gamma_mean=5000.0, rel_spread=0.0, sigma_x_um=X, sigma_y_um=X,
+               sigma_z_um=Lb / (2 * math.sqrt(3)))
+    xi = I.sample_streams(n, 23, dtype=np.float64)
+    g = I.rng(96)
+    xi[0], xi[1] = g.uniform(-1, 1, n), g.uniform(-1, 1, n)
+    xi[2] = g.uniform(-math.sqrt(3), math.sqrt(3), n)
+    r = oracle.scatter(L, B, I.Bins(n_bins=1, lo=0, hi=1e9, n_aeff=48, aeff_max=a0), xi)
+    nb = n / ((2 * X) ** 2 * Lb)
+    edges = np.linspace(0, a0, 49)
+    par = dict(length=Lb, d_par=dpar, n=nb)
+    # bins above 1.5: the box covers every electron with a_eff > 1.5
+    dens = lambda a: float(oracle.analytic_aeff(L, "wide", [a], **par)[0]) / n
+    _hist_vs_density(r["aeff_hist"][6:], edges[6:], dens, n)
+
+
+@pytest.mark.parametrize("geom", ["short", "thin"])
+def test_analytic_ll_spectrum_vs_monte_carlo(geom):
+    """Table 2 via Eq. 6: the classical spectrum of the short and thin beams."""
+    n, a0, w0, lam, g0 = 1 << 16, 12.0, 2.0, 0.8, 5000.0
+    if geom == "short":
+        sigma = 1.5
+        L, B, xi = _short_beam_inputs(n, 24, sigma, a0=a0, w0=w0, lam=lam)
+        par = dict(radius=math.sqrt(2) * sigma, n=n)
+    else:
+        Lb = 60.0
+        L = I.Laser(lambda_um=lam, a0=a0, w0_um=w0, model=I.MODEL_LL)
+        B = I.Beam(gamma_mean=g0, rel_spread=0.0, sigma_x_um=0.0, sigma_y_um=0.0,
+                   sigma_z_um=Lb / (2 * math.sqrt(3)))
+        xi = I.sample_streams(n, 25, dtype=np.float64)
+        xi[2] = I.rng(95).uniform(-math.sqrt(3), math.sqrt(3), n)
+        par = dict(length=Lb, n=n)
+    cRR = oracle.constants(L)["cRR"]
+    gmin = g0 / (1 + cRR * g0 * a0 ** 2)
+    bins = I.Bins(n_bins=48, lo=gmin * 0.98, hi=g0 * 1.0001)
+    r = oracle.scatter(L, B, bins, xi)
+    edges = np.linspace(bins.lo, bins.hi, 49)
+    _hist_vs_density(r["spectrum"], edges,
+                     lambda g: float(oracle.analytic_ll(L, geom, g0, [g], **par)[0]) / n, n)
+
+
 # --------------------------------------------------------------------------
 # invariants of the whole-beam integration
 # --------------------------------------------------------------------------
