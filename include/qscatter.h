@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 6
+#define QS_VERSION 7
 
 typedef enum {
     QS_OK = 0,
@@ -435,6 +435,46 @@ int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam,
  */
 int32_t qs_pw_reconstruct(int32_t n_shots, int32_t n_a, int32_t n_bins, const double* d_hist,
                           const double* d_pw, double* d_out, void* stream);
+
+/*
+ * Analytic fast path (Table 1; Table 2 via Eq. 6): distributions of
+ * idealised beams evaluated on a grid, as a cross-check of the Monte Carlo
+ * integration.  Geometry (qs_geometry): the collision centre sits d_par_um
+ * from the focal plane (W = W0 sqrt(1 + d_par^2/z_R^2), z_R = pi W0^2/lambda,
+ * a_par = a0 W0/W) and d_perp_um from the laser axis;
+ *   QS_GEOM_SHORT  all electrons in the collision plane, transverse density
+ *                  ~ exp(-rho^2/R^2), R = radius_um (R = sqrt2 sigma), count
+ *                  = N:  dN/da = N (W^2/R^2)(1/a)(a/a_par)^(W^2/R^2)
+ *                  I0(2 (d_perp/R)(W/R) sqrt(ln(a_par/a))) exp(-d_perp^2/R^2)
+ *                  for 0 < a < a_par (the table's theta read with its
+ *                  support the right way round);
+ *   QS_GEOM_THIN   on the axis, flat-top length L = length_um, count = N:
+ *                  collision positions uniform on [d_par - L/4, d_par + L/4]
+ *                  (the crossing is at half the lag); each of z = +-z_R
+ *                  sqrt(a0^2/a^2 - 1) inside adds (2N z_R/L)(a0^2/a^2)/
+ *                  sqrt(a0^2 - a^2);
+ *   QS_GEOM_WIDE   uniform density n_b = count (per um^3) across the laser,
+ *                  flat-top length L: dN/da = (2 pi n_b W0^2/a) times the
+ *                  integral of 1 + z^2/z_R^2 over the collision positions
+ *                  with a_eff(z) > a.
+ * qs_analytic_aeff writes dN/da at the n points d_a; qs_analytic_ll_spectrum
+ * the classical final-energy density dN/dgamma = (dN/da)(a(gamma)) /
+ * |dgamma/da| with gamma = gamma0/(1 + c_RR gamma0 a^2) (Eq. 3, c_RR from the
+ * laser as in qs_scatter) at the n energies d_gamma.  Device arrays; FP64.
+ * Errors: QS_ERR_INVALID_ARG, QS_ERR_CUDA.
+ */
+typedef enum { QS_GEOM_SHORT = 0, QS_GEOM_THIN = 1, QS_GEOM_WIDE = 2 } qs_geometry_kind;
+
+typedef struct qs_geometry {
+    int32_t kind, reserved;
+    double radius_um, length_um, d_perp_um, d_par_um, count;
+} qs_geometry;
+
+int32_t qs_analytic_aeff(const qs_laser* laser, const qs_geometry* geom, int64_t n,
+                         const double* d_a, double* d_out, void* stream);
+
+int32_t qs_analytic_ll_spectrum(const qs_laser* laser, const qs_geometry* geom, double gamma0,
+                                int64_t n, const double* d_gamma, double* d_out, void* stream);
 
 #ifdef __cplusplus
 }

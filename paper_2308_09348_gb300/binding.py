@@ -73,6 +73,20 @@ class qs_exec(C.Structure):
                 ("reserved", C.c_int32), ("ev_start", C.c_void_p), ("ev_stop", C.c_void_p)]
 
 
+class qs_geometry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("radius_um", C.c_double),
+                ("length_um", C.c_double), ("d_perp_um", C.c_double), ("d_par_um", C.c_double),
+                ("count", C.c_double)]
+
+
+GEOMETRIES = {"short": 0, "thin": 1, "wide": 2}
+
+
+def make_geometry(geom, radius=0.0, length=0.0, d_perp=0.0, d_par=0.0, n=1.0) -> qs_geometry:
+    return qs_geometry(GEOMETRIES[geom], 0, float(radius), float(length), float(d_perp),
+                       float(d_par), float(n))
+
+
 class qs_sample_out(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("gamma0", "aeff", "mu", "V", "theta_e", "theta_x",
                                           "theta_y", "gamma_out", "bin", "ix", "iy", "abin")]
@@ -139,6 +153,12 @@ def _lib():
             L.qs_photon_spectrum.restype = C.c_int32
             L.qs_pw_reconstruct.argtypes = [C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]
             L.qs_pw_reconstruct.restype = C.c_int32
+            L.qs_analytic_aeff.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_geometry),
+                                           C.c_int64, _VP, _VP, _VP]
+            L.qs_analytic_aeff.restype = C.c_int32
+            L.qs_analytic_ll_spectrum.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_geometry),
+                                                  C.c_double, C.c_int64, _VP, _VP, _VP]
+            L.qs_analytic_ll_spectrum.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -503,6 +523,33 @@ def qs_pw_reconstruct(hist, pw, out=None, stream=None) -> torch.Tensor:
     st = _lib().qs_pw_reconstruct(ns, na, nb, h.data_ptr(), p.data_ptr(), out.data_ptr(),
                                   _stream_ptr(stream))
     _check(st, "qs_pw_reconstruct")
+    return out
+
+
+# ---- analytic fast path (Table 1, Table 2) ---------------------------------
+
+def analytic_aeff(laser, geom, a, stream=None, **par) -> torch.Tensor:
+    """Table 1 dN/da_eff on the device grid ``a`` (float64) for an idealised
+    beam: "short" (radius, d_perp, d_par, n), "thin" or "wide" (length,
+    d_par, n; n is the density for "wide")."""
+    x = a.to(torch.float64).contiguous()
+    out = torch.empty_like(x)
+    g = make_geometry(geom, **par)
+    st = _lib().qs_analytic_aeff(C.byref(make_laser(laser)), C.byref(g), x.numel(),
+                                 x.data_ptr(), out.data_ptr(), _stream_ptr(stream))
+    _check(st, "qs_analytic_aeff")
+    return out
+
+
+def analytic_ll(laser, geom, gamma0, g, stream=None, **par) -> torch.Tensor:
+    """Table 2 (Eq. 6 with Eq. 3): the classical dN/dgamma on the device grid ``g``."""
+    x = g.to(torch.float64).contiguous()
+    out = torch.empty_like(x)
+    geo = make_geometry(geom, **par)
+    st = _lib().qs_analytic_ll_spectrum(C.byref(make_laser(laser)), C.byref(geo), float(gamma0),
+                                        x.numel(), x.data_ptr(), out.data_ptr(),
+                                        _stream_ptr(stream))
+    _check(st, "qs_analytic_ll_spectrum")
     return out
 
 
