@@ -625,6 +625,11 @@ def main():
         achieved, peak_v = mufu_ops / t_k / 1e12, peak_mufu / 1e12
     else:
         achieved, peak_v = fma_ops / t_k / 1e12, peak_fma / 1e12
+    # the same bound with the unit rates measured on this GPU now (per SM per
+    # clock at the maximum clock): 4 lg2 + 1 rcp + 3 ex2 per sample-step
+    ur = B.unit_rates()
+    t_meas = steps_total * (4 / ur["lg2"] + 1 / ur["rcp"] + 3 / ur["ex2"]) / (
+        ur["sms"] * ur["sm_max_mhz"] * 1e6)
     tr = TRAFFIC_BY_SOURCE.get(kernel_source_hash())
     roof = {"bound": "alu", "pipe": bound_pipe, "achieved": achieved, "peak": peak_v,
             "unit": "Top/s", "frac": t_bound / t_k,
@@ -632,7 +637,9 @@ def main():
             "kernel": "k_scatter<float>", "kernel_ms": kern_ms,
             "peak_source": f"{sms} SMs x {MUFU_SLOTS_PER_SM if bound_pipe == 'mufu' else FMA_LANES_PER_SM}"
                            f" per clock x {fmax_mhz:.0f} MHz (max SM clock)",
-            "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k}
+            "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k,
+            "measured_unit_rates": {k: round(v, 3) for k, v in ur.items()},
+            "frac_of_measured_mufu_rates": t_meas / t_k}
 
     batch = None if args.no_batch else bench_batch(dev, rank, n_shots=args.batch_shots)
     grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 7
+#define QS_VERSION 8
 
 typedef enum {
     QS_OK = 0,
@@ -475,6 +475,21 @@ int32_t qs_analytic_aeff(const qs_laser* laser, const qs_geometry* geom, int64_t
 
 int32_t qs_analytic_ll_spectrum(const qs_laser* laser, const qs_geometry* geom, double gamma0,
                                 int64_t n, const double* d_gamma, double* d_out, void* stream);
+
+/*
+ * qs_unit_rates: throughput probe of the pipes the kernels are bound by (no
+ * counterpart in the paper; it supplies the roofline denominators).
+ * rates[0..6] (host): FP32 FMA, MUFU lg2, ex2, rcp (the .approx forms the
+ * FP32 path issues), FP64 FMA, each in operations per SM per clock at the
+ * device's maximum SM clock (a throttled clock reads as a lower rate), then
+ * the SM count and that clock in MHz.  d_scratch: device memory of
+ * qs_unit_rates_scratch_bytes() bytes.  Runs a few milliseconds of
+ * dependent-chain kernels on `stream` and waits for them.
+ * Errors: QS_ERR_INVALID_ARG, QS_ERR_WORKSPACE, QS_ERR_CUDA.
+ */
+size_t qs_unit_rates_scratch_bytes(void);
+
+int32_t qs_unit_rates(double* rates, void* d_scratch, size_t scratch_bytes, void* stream);
 
 #ifdef __cplusplus
 }

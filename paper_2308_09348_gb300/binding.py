@@ -159,6 +159,9 @@ def _lib():
             L.qs_analytic_ll_spectrum.argtypes = [C.POINTER(qs_laser), C.POINTER(qs_geometry),
                                                   C.c_double, C.c_int64, _VP, _VP, _VP]
             L.qs_analytic_ll_spectrum.restype = C.c_int32
+            L.qs_unit_rates_scratch_bytes.restype = C.c_size_t
+            L.qs_unit_rates.argtypes = [C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
+            L.qs_unit_rates.restype = C.c_int32
             _LIB = L
     return _LIB
 
@@ -524,6 +527,23 @@ def qs_pw_reconstruct(hist, pw, out=None, stream=None) -> torch.Tensor:
                                   _stream_ptr(stream))
     _check(st, "qs_pw_reconstruct")
     return out
+
+
+# ---- unit rates -----------------------------------------------------------
+
+UNIT_RATE_FIELDS = ("fma", "lg2", "ex2", "rcp", "dfma", "sms", "sm_max_mhz")
+
+
+def unit_rates(stream=None) -> dict:
+    """Measured operations per SM per clock of the FP32 FMA, MUFU lg2 / ex2 /
+    rcp and FP64 FMA pipes (at the maximum SM clock), the SM count and that
+    clock (qs_unit_rates)."""
+    nbytes = int(_lib().qs_unit_rates_scratch_bytes())
+    scratch = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    out = (C.c_double * 7)()
+    st = _lib().qs_unit_rates(out, scratch.data_ptr(), nbytes, _stream_ptr(stream))
+    _check(st, "qs_unit_rates")
+    return dict(zip(UNIT_RATE_FIELDS, list(out)))
 
 
 # ---- analytic fast path (Table 1, Table 2) ---------------------------------

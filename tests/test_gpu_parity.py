@@ -562,3 +562,12 @@ def test_full_size_quantum_workload_sampled_parity():
     ref = oracle.evaluate(wl.laser, wl.beam, wl.bins, sub)
     got = {k: v[torch.from_numpy(idx).cuda()] for k, v in rec.items()}
     compare_samples(got, ref, "f32", wl.bins)
+
+
+def test_unit_rates_probe():
+    """The unit-rate probe reports plausible per-SM-per-clock rates."""
+    r = B.unit_rates()
+    print("unit rates:", r)
+    assert r["sms"] > 0 and r["sm_max_mhz"] > 0
+    assert r["fma"] > 64 and r["lg2"] > 8 and r["ex2"] >= 0.9 * r["lg2"] and r["rcp"] > 8
+    assert 0 < r["dfma"] < r["fma"]
