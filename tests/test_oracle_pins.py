@@ -175,9 +175,25 @@ def test_h2_fit_vs_exact_second_moment(exact_moments):
         _, m2 = exact_moments[chi]
         h_exact = m2 / (math.sqrt(3) * math.pi) / (
             (55 / (16 * math.sqrt(3))) * chi * (2 / 3) * chi ** 2)
-        assert abs(oracle.h2(chi) / h_exact - 1) < 0.02, (chi, oracle.h2(chi), h_exact)
+        assert abs(oracle.h2(chi) / h_exact - 1) < 0.006, (chi, oracle.h2(chi), h_exact)
     s = math.log(oracle.h2(2e5) / oracle.h2(1e5)) / math.log(2)
     assert abs(s + 7 / 3) < 0.01
+
+
+def test_h2_fit_wide_range():
+    """The fit's stated range, 1e-5 <= chi <= 300, at its ends and beyond
+    the fixture's points."""
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for chi in (1e-5, 1e-4, 0.1, 30.0, 100.0, 300.0):
+            _, m2 = _exact_moments(chi)
+            h_exact = m2 / (math.sqrt(3) * math.pi) / (
+                (55 / (16 * math.sqrt(3))) * chi * (2 / 3) * chi ** 2)
+            assert abs(oracle.h2(chi) / h_exact - 1) < 0.006, (chi, oracle.h2(chi), h_exact)
+    # decreasing from h(0) = 1
+    hs = np.array([oracle.h2(c) for c in np.logspace(-6, 6, 400)])
+    assert np.all(np.diff(hs) < 0) and hs[0] < 1.0
 
 
 def test_fp_rates_absolute_vs_exact_spectrum(exact_moments):
