@@ -30,20 +30,22 @@ METRIC = "beam-sample evals/s"
 UNIT = "samples/s"
 
 # Arithmetic per phase cell of the QFP integration (FP32 path), counted from
-# the model's expression: 4 base-2 logarithms (two logs, two powers), 1
-# reciprocal (the mean energy) and 3 base-2 exponentials (two powers, and
-# 1/(1+1.7 chi) as the exponential of a logarithm already taken) on the MUFU
-# pipe, where an ex2 issues at twice the rate of lg2/rcp on this GPU (half a
-# slot); and 42 FMA-pipe operations (add, mul, fma).
-QFP_FMA_OPS_PER_STEP = 42
-QFP_MUFU_SLOTS_PER_STEP = 4 + 1 + 3 * 0.5
+# the model's expression: 2 base-2 logarithms (ln(1+1.7 chi) and that of the
+# Gaunt polynomial B), 2 reciprocals (the mean energy, and 1/((1+1.7 chi) D)
+# which gives both 1/(1+1.7 chi) and the second-moment fit's 1/D) and 1 base-2
+# exponential (B^(-1/3)) on the MUFU pipe, where an ex2 issues at twice the
+# rate of lg2/rcp on this GPU (half a slot); and 40 FMA-pipe operations (add,
+# mul, fma).
+QFP_FMA_OPS_PER_STEP = 40
+QFP_MUFU_SLOTS_PER_STEP = 2 + 2 + 1 * 0.5
+QFP_MUFU_MIX = {"lg2": 2, "rcp": 2, "ex2": 1}
 FMA_LANES_PER_SM = 128
 MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"fa82680b2c452c00": 8 * (269.90e6 + 3.74e6)}
+TRAFFIC_BY_SOURCE = {"064d260ab0ca6552": 8 * (268.66e6 + 3.41e6)}
 
 
 def parse():
@@ -324,10 +326,13 @@ def bench_variant(dev, rank, variant, n=1 << 24, steps=3):
             "kernel_ms": kms, "n_samples": n, "n_phase": L.n_phase,
             "workload": wl.name + ("_cellfocus" if variant == I.VAR_CELL_FOCUS else "_cyclechi")}
     if variant == I.VAR_CELL_FOCUS:
-        line["roofline"] = {"bound": "alu", "pipe": "mufu" if t_mufu >= t_fma else "fma",
-                            "achieved": CELL_MUFU_SLOTS_PER_STEP * steps_total / t / 1e12,
-                            "peak": peak_mufu / 1e12, "unit": "Top/s",
-                            "frac": max(t_mufu, t_fma) / t}
+        mufu = t_mufu >= t_fma
+        ops = (CELL_MUFU_SLOTS_PER_STEP if mufu else CELL_FMA_OPS_PER_STEP) * steps_total
+        line["roofline"] = {"bound": "alu", "pipe": "mufu" if mufu else "fma",
+                            "achieved": ops / t / 1e12,
+                            "peak": (peak_mufu if mufu else peak_fma) / 1e12, "unit": "Top/s",
+                            "frac": max(t_mufu, t_fma) / t,
+                            "mufu_frac": t_mufu / t, "fma_frac": t_fma / t}
     return line
 
 
@@ -626,10 +631,11 @@ def main():
     else:
         achieved, peak_v = fma_ops / t_k / 1e12, peak_fma / 1e12
     # the same bound with the unit rates measured on this GPU now (per SM per
-    # clock at the maximum clock): 4 lg2 + 1 rcp + 3 ex2 per sample-step
+    # clock at the maximum clock)
     ur = B.unit_rates()
-    t_meas = steps_total * (4 / ur["lg2"] + 1 / ur["rcp"] + 3 / ur["ex2"]) / (
-        ur["sms"] * ur["sm_max_mhz"] * 1e6)
+    sm_clk = ur["sms"] * ur["sm_max_mhz"] * 1e6
+    t_meas_mufu = steps_total * sum(c / ur[k] for k, c in QFP_MUFU_MIX.items()) / sm_clk
+    t_meas_fma = steps_total * QFP_FMA_OPS_PER_STEP / ur["fma"] / sm_clk
     tr = TRAFFIC_BY_SOURCE.get(kernel_source_hash())
     roof = {"bound": "alu", "pipe": bound_pipe, "achieved": achieved, "peak": peak_v,
             "unit": "Top/s", "frac": t_bound / t_k,
@@ -639,7 +645,9 @@ def main():
                            f" per clock x {fmax_mhz:.0f} MHz (max SM clock)",
             "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k,
             "measured_unit_rates": {k: round(v, 3) for k, v in ur.items()},
-            "frac_of_measured_mufu_rates": t_meas / t_k}
+            "frac_of_measured_rates": max(t_meas_mufu, t_meas_fma) / t_k,
+            "mufu_frac_of_measured": t_meas_mufu / t_k,
+            "fma_frac_of_measured": t_meas_fma / t_k}
 
     batch = None if args.no_batch else bench_batch(dev, rank, n_shots=args.batch_shots)
     grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)

@@ -215,12 +215,21 @@ constexpr int kVarCycle = 2;   // cycle-resolved chi
 // Gauss-Legendre rule over the quarter period; FP32 path: cubic Hermite
 // interpolation in u = log2(1 + chi/chi_s) on kCycN nodes tabulated (in
 // FP64) from the same rule: relative error below 1e-8 for chi up to
-// chi_s (2^U - 1) = 327 (chi_s resolves the steep start of h at 1/12.93).
+// chi_s (2^U - 1) = 327 (chi_s resolves the steep start of h below chi = 0.1).
 constexpr int kCycGL = 128;
 constexpr int kCycN = 512;
 constexpr double kCycChiS = 0.02;
 constexpr double kCycU = 14.0;
 constexpr double kCycDu = kCycU / (kCycN - 1);
+
+// Second-moment factor of the diffusion coefficient (Eq. 6 reading): the
+// Gaunt fit g times a rational function, h = g N / D with
+//   N = 1 + 4.26 chi + 0.494 chi^2,  D = 1 + 12.32 chi + 17.44 chi^2 + 1.63 chi^3
+// (within 0.57 % of the exact quantum-synchrotron second moment for
+// 1e-5 <= chi <= 300; h ~ chi^(-7/3) at large chi).
+constexpr double kHA1 = 4.26, kHA2 = 0.494;
+constexpr double kHB1 = 12.32, kHB2 = 17.44, kHB3 = 1.63;
+constexpr double kC55 = 55.0 / (16.0 * 1.7320508075688772935);   // D2 prefactor
 
 // Closed forms of the fits (Eq. 6 reading): g, g', g'' and h, h'.
 __device__ __forceinline__ void gaunt_d(double x, double& g, double& g1, double& g2) {
@@ -233,12 +242,14 @@ __device__ __forceinline__ void gaunt_d(double x, double& g, double& g1, double&
   g1 = (-2.0 / 3.0) * g * iB * B1;
   g2 = (10.0 / 9.0) * g * iB * iB * B1 * B1 - (2.0 / 3.0) * g * iB * B2;
 }
-__device__ __forceinline__ void h2_d(double x, double& h, double& h1) {
-  const double L = log1p(12.93 * x);
-  const double B = 1.0 + (1.0 + 4.1 * x) * L + 4.75 * x * x;
-  const double B1 = 4.1 * L + 12.93 * (1.0 + 4.1 * x) / (1.0 + 12.93 * x) + 9.5 * x;
-  h = pow(B, -7.0 / 6.0);
-  h1 = (-7.0 / 6.0) * h * B1 / B;
+// h = g N / D from g and g' (FP64).
+__device__ __forceinline__ void h2_d(double x, double g, double g1, double& h, double& h1) {
+  const double N = 1.0 + x * (kHA1 + kHA2 * x), N1 = kHA1 + 2.0 * kHA2 * x;
+  const double D = 1.0 + x * (kHB1 + x * (kHB2 + kHB3 * x));
+  const double D1 = kHB1 + x * (2.0 * kHB2 + 3.0 * kHB3 * x);
+  const double R = N / D;
+  h = g * R;
+  h1 = g1 * R + g * (N1 - R * D1) / D;
 }
 
 // FP64 path: G, S, H and the chi-derivatives G', S' = 3G' + chi G'', H'
@@ -255,7 +266,7 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
     const double x = r2 * chi * c, c2 = 2.0 * c * c;
     double g, g1, g2, h, h1;
     gaunt_d(x, g, g1, g2);
-    h2_d(x, h, h1);
+    h2_d(x, g, g1, h, h1);
     sg += w * c2 * g;
     sg1 += w * c2 * g1 * r2 * c;
     sg2 += w * c2 * g2 * 2.0 * c * c;
@@ -327,7 +338,7 @@ __device__ __forceinline__ T a_cell(const Params& p, const Path<T>& g, T s) {
 // rates at each cell midpoint, midpoint state predicted with the previous
 // cell's Gaunt factor, frozen-rate Taylor step for the linear variance ODE.
 //   g(chi)  = B^(-2/3), B  = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
-//   h2(chi) = B2^(-7/6), B2 = 1 + (1+4.1 chi) ln(1+12.93 chi) + 4.75 chi^2
+//   h2(chi) = g N / D (the rational second-moment fit above)
 //   K = (2/3) R_c A^2, D1 = -K mu^2 g, dD1/dgamma = -K mu (2g + chi g'),
 //   D2 = (55/(16 sqrt3)) K mu^3 chi h2.
 // Returns du = 1/mu_f - 1/gamma0 and V_f.  FP64 path: written as the
@@ -372,9 +383,9 @@ __device__ __forceinline__ void qfp_cell(const Params& p, double Gj, int j, doub
                   __dmul_rn(dB, chi));
     sf = __fma_rn(2.0, g, chig1);
     // second-moment factor
-    const double L2 = __dmul_rn(LN2, log2(__fma_rn(12.93, chi, 1.0)));
-    const double B2 = __fma_rn(__fma_rn(4.1, chi, 1.0), L2, __fma_rn(__dmul_rn(4.75, chi), chi, 1.0));
-    h2 = exp2(__dmul_rn(-7.0 / 6.0, log2(B2)));
+    const double N = __fma_rn(__fma_rn(kHA2, chi, kHA1), chi, 1.0);
+    const double D = __fma_rn(__fma_rn(__fma_rn(kHB3, chi, kHB2), chi, kHB1), chi, 1.0);
+    h2 = __dmul_rn(g, N / D);
   }
   // updates
   du = __fma_rn(hK, g, du);
@@ -431,7 +442,7 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
 // the scheme (which also hands out the cell's midpoint energy and chi, for
 // the photon spectrum):
 struct PairConst {
-  float2 c1, ca, g0, zq0, xs, ys, tx, ty;
+  float2 c1, ca, ig0, zq0, xs, ys, tx, ty;     // ig0 = 1/gamma0
 };
 struct PairState {
   float2 du, V, gph;
@@ -443,7 +454,7 @@ __device__ __forceinline__ PairConst pair_const(const Params& p, float2 a, float
   PairConst k;
   k.c1 = LOC ? f2(p.f.hcK) : mul2(mul2(f2(p.f.hcK), a), a);
   k.ca = LOC ? f2(p.f.cchi) : mul2(f2(p.f.cchi), a);
-  k.g0 = g0;
+  k.ig0 = make_float2(__frcp_rn(g0.x), __frcp_rn(g0.y));
   k.zq0 = make_float2(P0.zq, P1.zq);
   k.xs = make_float2(P0.xs, P1.xs);
   k.ys = make_float2(P0.ys, P1.ys);
@@ -458,11 +469,8 @@ __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, cons
                                           const float2* __restrict__ cB, float2* mu_out = nullptr,
                                           float2* chi_out = nullptr) {
   const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
-  const float2 C816 = f2((float)(4.8 * 1.7));
-  const float2 C41 = f2((float)(4.1 * 0.69314718055994530942));   // 4.1 ln2
-  const float2 LN2 = f2(0.69314718055994530942f);
-  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
-  const float2 ONE = f2(1.f), TWO = f2(2.f), HALF = f2(0.5f);
+  const float2 C55 = f2((float)kC55);
+  const float2 ONE = f2(1.f), HALF = f2(0.5f);
   const float2 G = make_float2(gg.x, gg.y);
   float2 hK, cg;
   if constexpr ((VAR & kVarCell) != 0) {
@@ -481,36 +489,49 @@ __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, cons
     hK = mul2(k.c1, make_float2(gg.z, gg.w));
     cg = mul2(k.ca, G);
   }
-  const float2 dum = fma2(hK, st.gph, st.du);
-  const float2 mu = mul2(k.g0, rcpx2(fma2(k.g0, dum, ONE)));
+  // 1/mu = 1/gamma0 + du at the cell midpoint (predicted)
+  const float2 mu = rcpx2(__fadd2_rn(fma2(hK, st.gph, st.du), k.ig0));
   const float2 chi = mul2(cg, mu);
   if (mu_out) *mu_out = mu;
   if (chi_out) *chi_out = chi;
-  float2 g, s, h2;
+  // g, -2 (2g + chi g') and (55/(16 sqrt3)) h (or their cycle means)
+  float2 g, s2, h2c;
   if constexpr ((VAR & kVarCycle) != 0) {
+    float2 s, h2;
     cycle_lookup(cA, cB, chi.x, g.x, s.x, h2.x);
     cycle_lookup(cA, cB, chi.y, g.y, s.y, h2.y);
+    s2 = mul2(f2(-2.f), s);
+    h2c = mul2(C55, h2);
   } else {
-    const float2 chi2 = mul2(chi, chi);
     // Gaunt factor: B = 1 + 4.8 (1+chi) ln(1+1.7 chi) + 2.44 chi^2
-    const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
-    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(f2(2.44f), chi2, ONE));
+    const float2 x1 = fma2(f2(1.7f), chi, ONE);
+    const float2 l1 = lg2x2(x1);
+    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(mul2(f2(2.44f), chi), chi, ONE));
     const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));           // B^(-1/3)
     g = mul2(t, t);
-    // chi g' = -(2/3) g (dB/B) chi with 1/B = t^3
-    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));                // 1/(1+1.7 chi)
-    const float2 dB = fma2(C48, l1, fma2(fma2(C816, chi, C816), r1, mul2(f2(4.88f), chi)));
-    s = mul2(g, fma2(mul2(mul2(g, t), dB), mul2(f2(-2.f / 3.f), chi), TWO));
-    // second-moment factor h2 = B2^(-7/6)
-    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
-    const float2 B2 = fma2(fma2(C41, chi, LN2), l2, fma2(f2(4.75f), chi2, ONE));
-    h2 = ex2x2(mul2(f2(-7.f / 6.f), lg2x2(B2)));
+    // one reciprocal 1/(x1 D) gives both 1/(1+1.7 chi) and 1/D (x1 D < 2^126
+    // for chi < 1e9)
+    const float2 Nc = fma2(fma2(f2((float)(kC55 * kHA2)), chi, f2((float)(kC55 * kHA1))), chi,
+                           C55);
+    const float2 D = fma2(fma2(fma2(f2((float)kHB3), chi, f2((float)kHB2)), chi,
+                               f2((float)kHB1)), chi, ONE);
+    const float2 inv = rcpx2(mul2(x1, D));
+    const float2 r1 = mul2(D, inv);                                    // 1/(1+1.7 chi)
+    // -2 chi g' = (4/3) g chi B'/B with 1/B = g t and
+    // B' = 4.8 ln(1+1.7 chi) + 4.8 + 3.36/(1+1.7 chi) + 4.88 chi
+    const float2 dB = fma2(f2((float)(4.0 / 3.0 * 4.8 * 0.69314718055994530942)), l1,
+                           fma2(f2((float)(4.0 / 3.0 * 4.88)), chi,
+                                fma2(f2((float)(4.0 / 3.0 * 3.36)), r1,
+                                     f2((float)(4.0 / 3.0 * 4.8)))));
+    s2 = mul2(g, fma2(mul2(mul2(g, t), dB), chi, f2(-4.f)));
+    // second-moment factor with the D2 constant, h2c = (55/(16 sqrt3)) g N / D
+    h2c = mul2(mul2(g, Nc), mul2(x1, inv));
   }
   // updates
   st.du = fma2(hK, g, st.du);
   const float2 hKmu = mul2(hK, mu);
-  const float2 hlam = mul2(mul2(f2(-2.f), hKmu), s);
-  const float2 hD2 = mul2(C55, mul2(mul2(mul2(hKmu, chi), mul2(mu, mu)), h2));
+  const float2 hlam = mul2(hKmu, s2);
+  const float2 hD2 = mul2(mul2(hKmu, mul2(mu, chi)), mul2(mu, h2c));
   const float2 hr = fma2(hlam, st.V, hD2);
   st.V = fma2(hr, fma2(HALF, hlam, ONE), st.V);
   st.gph = mul2(HALF, g);

@@ -43,8 +43,8 @@ __device__ __forceinline__ void tab_g(const double* t, int j, double& G, double&
 //   g'' = (10/9) B^(-8/3) B'^2 - (2/3) B^(-5/3) B'',
 //   B' = 4.8 ln(1+1.7chi) + 8.16 (1+chi)/(1+1.7chi) + 4.88 chi,
 //   B'' = 8.16/(1+1.7chi) - 5.712/(1+1.7chi)^2 + 4.88,
-//   h2 = B2^(-7/6), h2' = -(7/6) h2 B2'/B2,
-//   B2' = 4.1 ln(1+12.93chi) + 12.93 (1+4.1chi)/(1+12.93chi) + 9.5 chi.
+//   h2 = g R, R = N/D (the rational second-moment fit),
+//   h2' = g' R + g (N' - R D')/D.
 template <typename T>
 __device__ __forceinline__ void qfp_tangent(const Params& p,
                                             const typename Tab<T>::type* __restrict__ tab, T a,
@@ -87,15 +87,14 @@ __device__ __forceinline__ void qfp_tangent(const Params& p,
     const T s = (T)2 * g + chi * gp;
     const T s_chi = (T)3 * gp + chi * gpp;
     // second-moment factor and derivative
-    const T l2 = M<T>::lg2((T)1 + (T)12.93 * chi);
-    const T L2 = LN2 * l2;
-    const T r2 = M<T>::ex2(-l2);
-    const T B2 = (T)1 + ((T)1 + (T)4.1 * chi) * L2 + (T)4.75 * chi * chi;
-    const T lb2 = M<T>::lg2(B2);
-    const T h2 = M<T>::ex2((T)(-7.0 / 6.0) * lb2);
-    const T iB2 = M<T>::ex2(-lb2);
-    const T B2p = (T)4.1 * L2 + (T)12.93 * ((T)1 + (T)4.1 * chi) * r2 + (T)9.5 * chi;
-    const T h2p = (T)(-7.0 / 6.0) * h2 * iB2 * B2p;
+    const T Nh = (T)1 + chi * ((T)kHA1 + (T)kHA2 * chi);
+    const T Dh = (T)1 + chi * ((T)kHB1 + chi * ((T)kHB2 + (T)kHB3 * chi));
+    const T iD = M<T>::rcp(Dh);
+    const T R = Nh * iD;
+    const T Rp = ((T)kHA1 + (T)(2.0 * kHA2) * chi -
+                  R * ((T)kHB1 + chi * ((T)(2.0 * kHB2) + (T)(3.0 * kHB3) * chi))) * iD;
+    const T h2 = g * R;
+    const T h2p = gp * R + g * Rp;
     // mean
     const T du_n = du + hK * g;
     const T du_a_n = du_a + hK_a * g + hK * gp * chi_a;
@@ -173,17 +172,18 @@ __device__ __forceinline__ void qfp_tangent_x2(const Params& p, const float4* __
         mul2(giB, fma2(mul2(mul2(f2(10.f / 9.f), iB), Bp), Bp, mul2(f2(-2.f / 3.f), Bpp)));
     const float2 s = fma2(chi, gp, mul2(f2(2.f), g));
     const float2 s_chi = fma2(chi, gpp, mul2(THREE, gp));
-    // second-moment factor and derivative
-    const float2 l2 = lg2x2(fma2(f2(12.93f), chi, ONE));
-    const float2 L2 = mul2(LN2, l2);
-    const float2 r2 = ex2x2(make_float2(-l2.x, -l2.y));
-    const float2 o41 = fma2(f2(4.1f), chi, ONE);
-    const float2 B2 = fma2(o41, L2, fma2(mul2(f2(4.75f), chi), chi, ONE));
-    const float2 lb2 = lg2x2(B2);
-    const float2 h2 = ex2x2(mul2(f2(-7.f / 6.f), lb2));
-    const float2 iB2 = ex2x2(make_float2(-lb2.x, -lb2.y));
-    const float2 B2p = fma2(f2(4.1f), L2, fma2(mul2(f2(12.93f), o41), r2, mul2(f2(9.5f), chi)));
-    const float2 h2p = mul2(mul2(mul2(f2(-7.f / 6.f), h2), iB2), B2p);
+    // second-moment factor and derivative: h2 = g R, R = N/D
+    const float2 Nh = fma2(fma2(f2((float)kHA2), chi, f2((float)kHA1)), chi, ONE);
+    const float2 Dh = fma2(fma2(fma2(f2((float)kHB3), chi, f2((float)kHB2)), chi,
+                                f2((float)kHB1)), chi, ONE);
+    const float2 iD = rcpx2(Dh);
+    const float2 R = mul2(Nh, iD);
+    const float2 Np = fma2(f2((float)(2.0 * kHA2)), chi, f2((float)kHA1));
+    const float2 Dp = fma2(fma2(f2((float)(3.0 * kHB3)), chi, f2((float)(2.0 * kHB2))), chi,
+                           f2((float)kHB1));
+    const float2 Rp = mul2(fma2(make_float2(-R.x, -R.y), Dp, Np), iD);
+    const float2 h2 = mul2(g, R);
+    const float2 h2p = fma2(gp, R, mul2(g, Rp));
     // mean
     const float2 hKgp = mul2(hK, gp);
     const float2 du_n = fma2(hK, g, du);
