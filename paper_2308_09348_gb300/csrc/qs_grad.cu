@@ -430,7 +430,7 @@ __device__ __forceinline__ void grad_loop(const Params& p,
 constexpr int kGradStageBins = 8192;
 
 template <typename T, bool QFP>
-__global__ void __launch_bounds__(256) k_grad(const Params p, const qs_moments* __restrict__ mom,
+__global__ void __launch_bounds__(512) k_grad(const Params p, const qs_moments* __restrict__ mom,
                                               const double* __restrict__ dLdm,
                                               const double* __restrict__ dLdS) {
   using TT = typename Tab<T>::type;
@@ -557,7 +557,6 @@ extern "C" int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam,
   if (laser->variant != 0) return QS_ERR_UNSUPPORTED;
   int prec, wbits, block, grid, sms;
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
-  if (block > 256) block = 256;
   if (!d_moments || !d_dL_dmoments || !d_grad8) return QS_ERR_INVALID_ARG;
   if (d_dL_dsmooth && !(bins->smooth_sigma_bins > 0)) return QS_ERR_INVALID_ARG;
   if ((st = device_sms(&sms))) return st;
@@ -570,16 +569,20 @@ extern "C" int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam,
   p.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(d_workspace) + pl.off_part);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   const bool qfp = laser->model == QS_MODEL_QFP;
+  // FP32 QFP, block left open: one 512-thread CTA per SM (118 registers).
+  // CTAs that share an SM are served oldest first and finish far apart, so
+  // a single CTA keeps all its warps resident to the end of the launch.
+  const int kblock = (!(exec && exec->block) && prec == QS_F32 && qfp) ? 512 : block;
   int g = 1;
   if (prec == QS_F64)
-    st = qfp ? launch_grad<double, true>(p, block, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
+    st = qfp ? launch_grad<double, true>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
                                          d_dL_dsmooth, cs, &g)
-             : launch_grad<double, false>(p, block, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
+             : launch_grad<double, false>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
                                           d_dL_dsmooth, cs, &g);
   else
-    st = qfp ? launch_grad<float, true>(p, block, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
+    st = qfp ? launch_grad<float, true>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
                                         d_dL_dsmooth, cs, &g)
-             : launch_grad<float, false>(p, block, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
+             : launch_grad<float, false>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
                                          d_dL_dsmooth, cs, &g);
   if (st) return st;
   k_grad_final<<<1, 32, 0, cs>>>(p, g, d_grad8);

@@ -164,12 +164,30 @@ using namespace detail;
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
 // VAR: model variant bits (kVarCell, kVarCycle).
-// Register budget per thread (blocks of up to 512 threads): FP32 QFP 64
-// (two 256-thread CTAs or more per SM for the MUFU-bound loop), FP32
-// classical 80 (three 256-thread CTAs per SM keep enough loads in flight
-// for the HBM-bound path), FP32 variants 80, FP64 128.
+// Register budget per thread: FP32 QFP 64 (one 1024-thread CTA per SM for
+// the pipe-bound loop), FP32 classical 80 (three 256-thread CTAs per SM keep
+// enough loads in flight for the HBM-bound path), FP32 variants 80 (one
+// 768-thread CTA per SM), FP64 128.
 template <typename T, bool QFP, int VAR>
 constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 64 : 80);
+
+// Block size of k_scatter when the caller leaves it open.  The FP32 paths
+// that integrate phase cells are bound by the FMA and MUFU pipes.  CTAs that
+// share an SM are served oldest first, so with four 256-thread CTAs per SM
+// the first one finishes at ~40 % of the launch and the SM ends it with a
+// quarter of its warps (22.9 of 32 warps resident on average).  One CTA per
+// SM that fills the register file keeps every warp resident to the end:
+// 1024 threads at 64 registers, 768 at 80.  The classical and FP64 paths
+// keep 256-thread CTAs.
+int scatter_block(const qs_exec* e, int block, int prec, bool qfp, int variant) {
+  if ((e && e->block) || prec != QS_F32 || !(qfp || (variant & QS_VARIANT_CELL_FOCUS)))
+    return block;
+  const int regs = (qfp && variant == 0) ? kScatterRegs<float, true, 0>
+                                         : kScatterRegs<float, true, 1>;
+  // warps are granted registers in groups of four
+  const int b = ((65536 / (regs * 32)) & ~3) * 32;
+  return b > 1024 ? 1024 : b;
+}
 
 // Shared memory of the phase table and, FP32 cycle-resolved chi, the cycle
 // tables behind it.
@@ -676,8 +694,9 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
     return QS_ERR_WORKSPACE;
   const bool qfp = laser->model == QS_MODEL_QFP;
   const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
+  const int kblock = scatter_block(exec, block, prec, qfp, laser->variant);
   const Smem sm = smem_plan(pl, prec, cells ? laser->n_phase : 0, laser->variant,
-                            samples->w != nullptr, block);
+                            samples->w != nullptr, kblock);
 
   Params p;
   fill_params(p, laser, beam, samples, bins, wbits);
@@ -695,9 +714,9 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return cuda_fail();
   int g = 1;
   if (prec == QS_F64)
-    st = launch_scatter_prec<double>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);
+    st = launch_scatter_prec<double>(p, qfp, sm, kblock, sms, grid, pl.gmax, cs, &g, exec);
   else
-    st = launch_scatter_prec<float>(p, qfp, sm, block, sms, grid, pl.gmax, cs, &g, exec);
+    st = launch_scatter_prec<float>(p, qfp, sm, kblock, sms, grid, pl.gmax, cs, &g, exec);
   if (st) return st;
   k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_spec_smooth,
                                  d_moments);
@@ -913,8 +932,9 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   if ((st = host_pipe(&pipe))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
   const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
+  const int kblock = scatter_block(exec, block, prec, qfp, laser->variant);
   const Smem sm = smem_plan(hp.pl, prec, cells ? laser->n_phase : 0, laser->variant,
-                            h_samples->w != nullptr, block);
+                            h_samples->w != nullptr, kblock);
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Params p;
@@ -964,9 +984,9 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
     int g = 1;
     const qs_exec* ex = (c == 0) ? exec : nullptr;
     if (prec == QS_F64)
-      st = launch_scatter_prec<double>(pc, qfp, sm, block, sms, grid, hp.pl.gmax, cs, &g, ex);
+      st = launch_scatter_prec<double>(pc, qfp, sm, kblock, sms, grid, hp.pl.gmax, cs, &g, ex);
     else
-      st = launch_scatter_prec<float>(pc, qfp, sm, block, sms, grid, hp.pl.gmax, cs, &g, ex);
+      st = launch_scatter_prec<float>(pc, qfp, sm, kblock, sms, grid, hp.pl.gmax, cs, &g, ex);
     if (st) return st;
     if (cudaEventRecord(pipe->consumed[b], cs) != cudaSuccess) return cuda_fail();
   }
