@@ -263,10 +263,13 @@ int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_sam
  * but serialises the copies).  Results equal qs_scatter's: identical
  * histograms, moments up to the order of the reduction.
  *   h_samples   qs_samples whose xi[] and w point to host memory
- *   chunk       samples per chunk, a positive multiple of 1024 (0 = 1<<22)
+ *   chunk       samples per chunk, a positive multiple of 1024; or 0: chunks
+ *               of whole waves of the FP32 launch (2048 samples per SM), the
+ *               first one wave and each next three times the last, up to
+ *               2^23 samples, so that the first copy is short
  *   h_*         host output buffers (same sizes and rules as qs_scatter)
  *   d_workspace qs_host_workspace_bytes(...) bytes of device memory
- * The first call on a device creates one copy stream and four events that
+ * The first call on a device creates one copy stream and five events that
  * are kept until the process exits (no device memory is allocated).
  */
 size_t qs_host_workspace_bytes(const qs_bins* bins, const qs_exec* exec, const qs_samples* h_samples,

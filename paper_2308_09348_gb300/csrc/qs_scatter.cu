@@ -860,16 +860,38 @@ int32_t host_pipe(HostPipe** out) {
 struct HostPlan {
   Plan pl;               // accumulators; partial slots for n_chunks * gmax CTAs
   int64_t chunk = 0, n_chunks = 0;
+  int64_t wave = 0;      // automatic schedule: first chunk, growth x3 up to chunk
   int n_streams = 0;     // present sample streams (+ weights)
   size_t esz = 4, off_out = 0, off_stage = 0, stage_bytes = 0, bytes = 0;
   size_t out_spec = 0, out_map = 0, out_aeff = 0, out_smooth = 0, out_mom = 0;
 };
 
+// Automatic chunking (chunk = 0): whole waves of the FP32 cell-integrating
+// launch (two samples per thread, one 1024-thread CTA per SM), so that no
+// chunk ends on a partly idle pass over the grid; the first chunk is one
+// wave and each next one three times the last, up to 2^23 samples, so the
+// copy of chunk c+1 (~4x faster per sample than its evaluation) hides
+// behind chunk c from the start.
+int64_t next_chunk(const HostPlan& hp, int64_t last) {
+  if (!hp.wave) return hp.chunk;
+  if (last == 0) return hp.wave;
+  return last * 3 < hp.chunk ? last * 3 : hp.chunk;
+}
+
 bool host_plan(HostPlan& hp, const qs_bins* b, int block, int grid, int sms,
                const qs_samples* s, int64_t chunk) {
-  hp.chunk = chunk > 0 ? chunk : ((int64_t)1 << 22);
+  if (chunk > 0) {
+    hp.chunk = chunk;
+    hp.wave = 0;
+  } else {
+    hp.wave = (int64_t)2048 * sms;
+    const int64_t cap = ((int64_t)1 << 23) / hp.wave;
+    hp.chunk = (cap > 0 ? cap : 1) * hp.wave;
+  }
   if (hp.chunk % 1024) return false;
-  hp.n_chunks = s->n > 0 ? (s->n + hp.chunk - 1) / hp.chunk : 0;
+  hp.n_chunks = 0;
+  for (int64_t left = s->n, len = 0; left > 0; left -= len, ++hp.n_chunks)
+    len = next_chunk(hp, len);
   make_plan(hp.pl, b, block, grid, sms);
   // partial slots for every chunk's CTAs (the plan's region holds one chunk)
   const size_t part_bytes = (size_t)(hp.n_chunks > 0 ? hp.n_chunks : 1) * hp.pl.gmax * kNumMom * 8;
@@ -959,10 +981,11 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   for (int k = 0; k < 8; ++k)
     if (h_samples->xi[k]) hsrc[ns++] = h_samples->xi[k];
   if (h_samples->w) hsrc[ns++] = h_samples->w;
-  for (int64_t c = 0; c < hp.n_chunks; ++c) {
+  int64_t i0 = 0, len = 0;
+  for (int64_t c = 0; c < hp.n_chunks; ++c, i0 += len) {
     const int b = (int)(c & 1);
-    const int64_t i0 = c * hp.chunk;
-    const int64_t cn = (h_samples->n - i0) < hp.chunk ? (h_samples->n - i0) : hp.chunk;
+    len = next_chunk(hp, len);
+    const int64_t cn = (h_samples->n - i0) < len ? (h_samples->n - i0) : len;
     unsigned char* stage = ws + hp.off_stage + (size_t)b * hp.n_streams * hp.stage_bytes;
     if (c >= 2 && cudaStreamWaitEvent(pipe->copy, pipe->consumed[b], 0) != cudaSuccess)
       return cuda_fail();

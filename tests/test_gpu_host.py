@@ -42,6 +42,27 @@ def test_host_equals_device(chunk, prec, model):
                                rtol=1e-13 if prec == "f64" else 1e-8)
 
 
+def test_host_automatic_chunks_span_the_ramp():
+    """chunk = 0: chunks of whole waves (2048 samples per SM) growing x3 up
+    to 2^23 samples; n spans the 1-, 3- and 9-wave chunks, full chunks and a
+    ragged tail."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    wave = 2048 * sms
+    n = 13 * wave + (1 << 23) // wave * wave + 12_345
+    wl = I.full_qfp(n)
+    L = I.Laser(**{**wl.laser.__dict__, "n_phase": 32})
+    xi, _ = I.workload_inputs(wl, n)
+    xh = [torch.from_numpy(a).pin_memory() for a in xi]
+    ref = B.qs_scatter(L, wl.beam, [x.cuda() for x in xh], wl.bins)
+    out = B.qs_scatter_host(L, wl.beam, xh, wl.bins, chunk=0)
+    torch.cuda.synchronize()
+    assert torch.equal(out.spectrum, ref.spectrum.cpu())
+    assert torch.equal(out.divmap, ref.divmap.cpu())
+    assert torch.equal(out.aeff_hist, ref.aeff_hist.cpu())
+    assert out.moments[0].item() == n
+    np.testing.assert_allclose(out.moments.numpy(), ref.moments.cpu().numpy(), rtol=1e-8)
+
+
 def test_host_pageable_memory_and_repeat():
     n = 5000
     wl = I.full_qfp(n)
