@@ -1149,6 +1149,81 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
   return true;
 }
 
+// Four classical samples (FP32, no variance or electron angle terms) into
+// the moment sums and histograms: the four contributions to each sum are
+// added plainly and folded into the compensated sum once.  If any of the
+// four is non-finite or has a negative weight, each goes through
+// accumulate_w instead (same skip rule).  W: weights present (else 1).
+template <typename H, bool SHIST, bool W>
+__device__ __forceinline__ void accumulate4_ll(const Params& p, const SampleF (&s)[4],
+                                               const float4 w4, AccF& A, H* hs, H* hm, H* ha,
+                                               int64_t nspec, int64_t nmap, int64_t naeff) {
+  const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    ok = ok && isfinite(s[k].mu_hi) && isfinite(s[k].tx) &&
+         (!W || (isfinite(w[k]) && w[k] >= 0.f));
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      accumulate_w<H, SHIST, false>(p, s[k], W ? w[k] : 1.f, A, hs, hm, ha, nspec, nmap, naeff);
+    return;
+  }
+  if (isnan(A.shift)) A.shift = s[0].mu_hi;
+  float t0 = 0.f, t1 = 0.f, t2 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f, t7 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float d = __fsub_rn(s[k].mu_hi, A.shift);
+    if (W) {
+      const float wd = __fmul_rn(w[k], d);
+      t0 = __fadd_rn(t0, w[k]);
+      t1 = __fadd_rn(t1, wd);
+      t2 = __fmaf_rn(wd, d, t2);
+      t4 = __fmaf_rn(__fmul_rn(w[k], s[k].thx0), s[k].thx0, t4);
+      t5 = __fmaf_rn(__fmul_rn(w[k], s[k].thy0), s[k].thy0, t5);
+      t6 = __fmaf_rn(w[k], s[k].aeff, t6);
+      t7 = __fmaf_rn(w[k], s[k].g0, t7);
+    } else {
+      t1 = __fadd_rn(t1, d);
+      t2 = __fmaf_rn(d, d, t2);
+      t4 = __fmaf_rn(s[k].thx0, s[k].thx0, t4);
+      t5 = __fmaf_rn(s[k].thy0, s[k].thy0, t5);
+      t6 = __fadd_rn(t6, s[k].aeff);
+      t7 = __fadd_rn(t7, s[k].g0);
+    }
+  }
+  kahan(A.s[0], A.c[0], W ? t0 : 4.f);
+  kahan(A.s[1], A.c[1], t1);
+  kahan(A.s[2], A.c[2], t2);
+  kahan(A.s[4], A.c[4], t4);
+  kahan(A.s[5], A.c[5], t5);
+  kahan(A.s[6], A.c[6], t6);
+  kahan(A.s[7], A.c[7], t7);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    // w 2^bits is exact in FP32, so this equals the FP64 path's rounding
+    const unsigned long long q = W ? f2u64_rn(__fmul_rn(w[k], p.f.wscale)) : 1ull;
+    if (nspec) {
+      const int b = energy_bin_f32(p, s[k].go_hi, s[k].go_lo);
+      const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+      if (SHIST) atomicAdd(&hs[slot], (H)q);
+      else atomicAdd(&p.acc_spec[slot], q);
+    }
+    if (nmap) {
+      const int c = map_cell_f32(p, s[k].tx, s[k].ty);
+      const int64_t slot = c < 0 ? nmap - 1 : c;
+      if (SHIST) atomicAdd(&hm[slot], (H)q);
+      else atomicAdd(&p.acc_map[slot], q);
+    }
+    if (naeff) {
+      const int slot = aeff_bin_f32(p, s[k].aeff);
+      if (SHIST) atomicAdd(&ha[slot], (H)q);
+      else atomicAdd(&p.acc_aeff[slot], q);
+    }
+  }
+}
+
 template <typename T, typename H, bool SHIST>
 __device__ __forceinline__ bool accumulate(const Params& p, const SampleF& s, int64_t i, AccF& A,
                                            H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,

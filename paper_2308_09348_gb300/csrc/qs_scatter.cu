@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 namespace qs {
 
@@ -290,21 +291,26 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       if (p.weighted) vec = vec && ((uintptr_t)p.w & 15) == 0;
       if (vec) {
         const int64_t n4 = p.n >> 2;
-        for (int64_t k = t0; k < n4; k += stride) {
-          float4 v[6];
+        // the four samples' moment contributions are summed, then folded into
+        // the compensated sums once (accumulate4_ll); unit weights specialised
+        auto run = [&](auto weighted) {
+          constexpr bool W = decltype(weighted)::value;
+          for (int64_t k = t0; k < n4; k += stride) {
+            float4 v[6];
 #pragma unroll
-          for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
-          const float4 wv = p.weighted ? __ldg(static_cast<const float4*>(p.w) + k)
-                                       : make_float4(1.f, 1.f, 1.f, 1.f);
-          const SampleF s0 = eval_ll_f32_xi(p, v[0].x, v[1].x, v[2].x, v[3].x, v[4].x, v[5].x);
-          accumulate_w<H, SHIST, false>(p, s0, wv.x, acc, hs, hm, ha, nspec, nmap, naeff);
-          const SampleF s1 = eval_ll_f32_xi(p, v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y);
-          accumulate_w<H, SHIST, false>(p, s1, wv.y, acc, hs, hm, ha, nspec, nmap, naeff);
-          const SampleF s2 = eval_ll_f32_xi(p, v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z);
-          accumulate_w<H, SHIST, false>(p, s2, wv.z, acc, hs, hm, ha, nspec, nmap, naeff);
-          const SampleF s3 = eval_ll_f32_xi(p, v[0].w, v[1].w, v[2].w, v[3].w, v[4].w, v[5].w);
-          accumulate_w<H, SHIST, false>(p, s3, wv.w, acc, hs, hm, ha, nspec, nmap, naeff);
-        }
+            for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
+            const float4 wv = W ? __ldg(static_cast<const float4*>(p.w) + k)
+                                : make_float4(1.f, 1.f, 1.f, 1.f);
+            const SampleF s4[4] = {
+                eval_ll_f32_xi(p, v[0].x, v[1].x, v[2].x, v[3].x, v[4].x, v[5].x),
+                eval_ll_f32_xi(p, v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y),
+                eval_ll_f32_xi(p, v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z),
+                eval_ll_f32_xi(p, v[0].w, v[1].w, v[2].w, v[3].w, v[4].w, v[5].w)};
+            accumulate4_ll<H, SHIST, W>(p, s4, wv, acc, hs, hm, ha, nspec, nmap, naeff);
+          }
+        };
+        if (p.weighted) run(std::true_type{});
+        else run(std::false_type{});
         i = 4 * n4 + t0;
       }
     }

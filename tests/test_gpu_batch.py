@@ -11,7 +11,11 @@ from paper_2308_09348_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 # agreement of moments between different sample partitions of one problem
-MOM_RTOL = {"f64": 1e-12, "f32": 1e-8}
+# GPU path against GPU path: the FP32 classical single-shot path sums each
+# group of four samples before its compensated step, the batch path adds
+# sample by sample, so the FP32 moments differ by the rounding of those
+# groupings (a couple of FP32 ulps, 2^-24 = 6e-8)
+MOM_RTOL = {"f64": 1e-12, "f32": 1e-7}
 
 
 @pytest.fixture(scope="module", autouse=True)
