@@ -65,7 +65,6 @@ struct Params {
   // Hermite tables of (G, S) and H over u = log2(1 + chi/chi_s) (FP32 path)
   const double* cyc_gl;
   const float4* cyc_a;
-  const float2* cyc_b;
   // FP32 path, log-spaced bins: t = lg2(gamma) * log2_scale - log2_offset
   float log2_scale, log2_offset;
   // FP32 copies of the per-sample constants, each the double above rounded
@@ -213,9 +212,11 @@ constexpr int kVarCycle = 2;   // cycle-resolved chi
 // means G = <2 cos^2 g(chi(psi))>, S = 2G + chi G', H = <2 sqrt2 |cos|^3
 // h(chi(psi))> in place of g, 2g + chi g', h.  FP64 path: a 128-point
 // Gauss-Legendre rule over the quarter period; FP32 path: cubic Hermite
-// interpolation in u = log2(1 + chi/chi_s) on kCycN nodes tabulated (in
-// FP64) from the same rule: relative error below 1e-8 for chi up to
-// chi_s (2^U - 1) = 327 (chi_s resolves the steep start of h below chi = 0.1).
+// interpolation in u = log2(1 + chi/chi_s) of G and H on kCycN nodes
+// tabulated (in FP64) from the same rule, S = 2G + chi G' from the
+// derivative of G's interpolant: relative error below 1e-9 (G, H) and
+// 3e-7 (S) for chi up to chi_s (2^U - 1) = 327 (chi_s resolves the steep
+// start of h below chi = 0.1).
 constexpr int kCycGL = 128;
 constexpr int kCycN = 512;
 constexpr double kCycChiS = 0.02;
@@ -283,8 +284,7 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
 
 // FP32 path: one lane's cubic Hermite lookup.  A[n] = {G, G_u du, S, S_u du},
 // B[n] = {H, H_u du} at u_n = n du (the derivatives in u, times the spacing).
-__device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A,
-                                             const float2* __restrict__ B, float chi, float& G,
+__device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float chi, float& G,
                                              float& S, float& H) {
   const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
   const float x = fminf(fmaxf(__fmul_rn(u, (float)(1.0 / kCycDu)), 0.f),
@@ -301,11 +301,19 @@ __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A,
   const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));       // 3t^2 - 2t^3
   const float h11 = __fmaf_rn(t2, t, -t2);                         // t^3 - t^2
   const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);              // t - 2t^2 + t^3
+  // t-derivatives of the basis: 6t - 6t^2, 1 - 4t + 3t^2, 3t^2 - 2t
+  const float d01 = __fmul_rn(6.f, __fsub_rn(t, t2));
+  const float d10 = __fmaf_rn(3.f, t2, __fmaf_rn(-4.f, t, 1.f));
+  const float d11 = __fmaf_rn(3.f, t2, __fmul_rn(-2.f, t));
   const float4 a0 = A[idx], a1 = A[idx + 1];
-  const float2 b0 = B[idx], b1 = B[idx + 1];
-  G = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, __fsub_rn(a1.x, a0.x), a0.x)));
-  S = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
-  H = __fmaf_rn(h11, b1.y, __fmaf_rn(h10, b0.y, __fmaf_rn(h01, __fsub_rn(b1.x, b0.x), b0.x)));
+  const float dG = __fsub_rn(a1.x, a0.x);
+  G = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, dG, a0.x)));
+  H = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
+  // chi G' = (dG/dt) chi / (du ln2 (chi + chi_s)), from the same interpolant
+  const float Gt = __fmaf_rn(d11, a1.y, __fmaf_rn(d10, a0.y, __fmul_rn(d01, dG)));
+  const float k = __fmul_rn(chi, M<float>::rcp(__fmul_rn(
+                                     (float)(kCycDu * 0.69314718055994530942), __fadd_rn(chi, (float)kCycChiS))));
+  S = __fmaf_rn(Gt, k, __fmul_rn(2.f, G));
 }
 
 // Per-cell focus (QS_VARIANT_CELL_FOCUS): Eq. 2 evaluated in
@@ -438,7 +446,7 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
 // VAR & kVarCell: per-cell focus; the table then holds {G, G, s_j, s_j} and
 // the two samples' paths give the per-cell amplitudes (same operations as
 // a_cell).  VAR & kVarCycle: cycle-resolved factors from the Hermite tables
-// cA, cB (shared memory).  The pair's constants and state, and one cell of
+// cA (shared memory).  The pair's constants and state, and one cell of
 // the scheme (which also hands out the cell's midpoint energy and chi, for
 // the photon spectrum):
 struct PairConst {
@@ -466,7 +474,7 @@ __device__ __forceinline__ PairConst pair_const(const Params& p, float2 a, float
 template <int VAR>
 __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, const PairConst& k,
                                           PairState& st, const float4* __restrict__ cA,
-                                          const float2* __restrict__ cB, float2* mu_out = nullptr,
+                                          float2* mu_out = nullptr,
                                           float2* chi_out = nullptr) {
   const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));   // 4.8 ln2
   const float2 C55 = f2((float)kC55);
@@ -498,8 +506,8 @@ __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, cons
   float2 g, s2, h2c;
   if constexpr ((VAR & kVarCycle) != 0) {
     float2 s, h2;
-    cycle_lookup(cA, cB, chi.x, g.x, s.x, h2.x);
-    cycle_lookup(cA, cB, chi.y, g.y, s.y, h2.y);
+    cycle_lookup(cA, chi.x, g.x, s.x, h2.x);
+    cycle_lookup(cA, chi.y, g.y, s.y, h2.y);
     s2 = mul2(f2(-2.f), s);
     h2c = mul2(C55, h2);
   } else {
@@ -542,13 +550,12 @@ __device__ __forceinline__ void qfp_integrate_f32x2(const Params& p,
                                                     const float4* __restrict__ tab, float2 a,
                                                     float2 g0, float2& du_out, float2& V_out,
                                                     const Path<float>& P0, const Path<float>& P1,
-                                                    const float4* __restrict__ cA = nullptr,
-                                                    const float2* __restrict__ cB = nullptr) {
+                                                    const float4* __restrict__ cA = nullptr) {
   const PairConst k = pair_const<VAR>(p, a, g0, P0, P1);
   PairState st{f2(0.f), f2(0.f), f2(0.5f)};
   const int N = p.n_phase;
 #pragma unroll 2
-  for (int j = 0; j < N; ++j) pair_cell<VAR>(p, tab[j], k, st, cA, cB);
+  for (int j = 0; j < N; ++j) pair_cell<VAR>(p, tab[j], k, st, cA);
   du_out = st.du;
   V_out = st.V;
 }
@@ -696,8 +703,7 @@ __device__ __forceinline__ void finish_f32(const Params& p, int64_t i, float g0,
 template <int VAR = 0>
 __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4* __restrict__ tab,
                                                   int64_t i0, int64_t i1, SampleF& s0,
-                                                  SampleF& s1, const float4* cA = nullptr,
-                                                  const float2* cB = nullptr) {
+                                                  SampleF& s1, const float4* cA = nullptr) {
   constexpr bool LOC = (VAR & kVarCell) != 0;
   float g0f, g1f, tx0, ty0, tx1, ty1;
   Path<float> P0{}, P1{};
@@ -705,7 +711,7 @@ __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4*
   const float a1 = focus<float>(p, i1, g1f, tx1, ty1, LOC ? &P1 : nullptr);
   float2 du, V;
   qfp_integrate_f32x2<VAR>(p, tab, make_float2(a0, a1), make_float2(g0f, g1f), du, V, P0, P1,
-                           cA, cB);
+                           cA);
   finish_f32(p, i0, g0f, a0, tx0, ty0, du.x, V.x, s0);
   finish_f32(p, i1, g1f, a1, tx1, ty1, du.y, V.y, s1);
 }
@@ -760,12 +766,12 @@ __device__ __forceinline__ SampleF eval_ll_f32_cells(const Params& p,
 template <typename T, bool QFP, int VAR = 0>
 __device__ __forceinline__ typename SampleT<T>::type eval_one(
     const Params& p, const typename Tab<T>::type* __restrict__ tab, int64_t i,
-    const float4* cA = nullptr, const float2* cB = nullptr) {
+    const float4* cA = nullptr) {
   if constexpr (sizeof(T) == 8) {
     return eval_sample<QFP, VAR>(p, reinterpret_cast<const double*>(tab), i);
   } else if constexpr (QFP) {
     SampleF s0, s1;
-    eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1, cA, cB);
+    eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i, i, s0, s1, cA);
     return s0;
   } else if constexpr ((VAR & kVarCell) != 0) {
     return eval_ll_f32_cells(p, reinterpret_cast<const float4*>(tab), i);

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
       PairState st{f2(0.f), f2(0.f), f2(0.5f)};
       for (int j = 0; j < p.n_phase; ++j) {
         float2 mu, chi;
-        pair_cell<VAR>(p, reinterpret_cast<const float4*>(tab)[j], kc, st, nullptr, nullptr, &mu,
+        pair_cell<VAR>(p, reinterpret_cast<const float4*>(tab)[j], kc, st, nullptr, &mu,
                        &chi);
         const float c0 = (w0 > 0.f && chi.x > 0.f) ? __fmul_rn(__fmul_rn(prf, w0), M<float>::rcp(__fmul_rn(mu.x, mu.x))) : 0.f;
         const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;

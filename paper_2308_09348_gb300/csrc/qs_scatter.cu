@@ -129,7 +129,7 @@ Smem smem_plan(const Plan& pl, int precision, int cells, int variant, bool weigh
   // {G, G, s_j, s_j} (FP32 path); then the cycle tables
   const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16) +
                      ((variant & QS_VARIANT_CYCLE_CHI) && precision == QS_F32
-                          ? (size_t)kCycN * (sizeof(float4) + sizeof(float2))
+                          ? (size_t)kCycN * sizeof(float4)
                           : 0);
   const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
   const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
@@ -198,11 +198,11 @@ __device__ __forceinline__ size_t table_bytes(const Params& p) {
   constexpr bool cells = QFP || (VAR & kVarCell);
   constexpr bool cyc = sizeof(T) == 4 && (VAR & kVarCycle);
   return (cells ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0) +
-         (cyc ? (size_t)kCycN * (sizeof(float4) + sizeof(float2)) : 0);
+         (cyc ? (size_t)kCycN * sizeof(float4) : 0);
 }
 template <typename T, bool QFP, int VAR>
 __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem,
-                                            const float4** cA, const float2** cB) {
+                                            const float4** cA) {
   using TT = typename Tab<T>::type;
   TT* tab = reinterpret_cast<TT*>(smem);
   if (QFP || (VAR & kVarCell))
@@ -210,13 +210,8 @@ __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem
   if constexpr (sizeof(T) == 4 && (VAR & kVarCycle)) {
     float4* A = reinterpret_cast<float4*>(smem + (((size_t)p.n_phase * sizeof(TT) + 15) &
                                                   ~(size_t)15));
-    float2* B = reinterpret_cast<float2*>(A + kCycN);
-    for (int j = threadIdx.x; j < kCycN; j += blockDim.x) {
-      A[j] = p.cyc_a[j];
-      B[j] = p.cyc_b[j];
-    }
+    for (int j = threadIdx.x; j < kCycN; j += blockDim.x) A[j] = p.cyc_a[j];
     *cA = A;
-    *cB = B;
   }
 }
 
@@ -228,7 +223,6 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
   const size_t tab_bytes = table_bytes<T, QFP, VAR>(p);
   TT* tab = reinterpret_cast<TT*>(smem);
   const float4* cA = nullptr;
-  const float2* cB = nullptr;
   double* red = reinterpret_cast<double*>(smem + tab_bytes);
   H* sh = reinterpret_cast<H*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumMom * sizeof(double));
   const int64_t nspec = p.n_bins > 0 ? (int64_t)p.n_bins + 2 : 0;
@@ -243,7 +237,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
   unsigned long long* ssm = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(sh) + hist_bytes);
   unsigned long long* hsm = nsm ? (p.smooth_in_smem ? ssm : p.acc_smooth) : nullptr;
 
-  load_tables<T, QFP, VAR>(p, smem, &cA, &cB);
+  load_tables<T, QFP, VAR>(p, smem, &cA);
   if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
   if (nsm && p.smooth_in_smem)
@@ -267,7 +261,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       bool ok0 = false, ok1 = false;
       if (i0 < p.n) {
         SampleF s0, s1;
-        eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA, cB);
+        eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
         ok0 = accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
         if (i1 != i0)
           ok1 = accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
@@ -319,7 +313,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       typename DepT<T>::type d;
       bool ok = false;
       if (ii < p.n) {
-        const auto s = eval_one<T, QFP, VAR>(p, tab, ii, cA, cB);
+        const auto s = eval_one<T, QFP, VAR>(p, tab, ii, cA);
         ok = accumulate<T, H, SHIST>(p, s, ii, acc, hs, hm, ha, nspec, nmap, naeff);
         dep_set(d, s);
       }
@@ -475,8 +469,7 @@ __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
   extern __shared__ __align__(16) unsigned char smem[];
   TT* tab = reinterpret_cast<TT*>(smem);
   const float4* cA = nullptr;
-  const float2* cB = nullptr;
-  load_tables<T, QFP, VAR>(p, smem, &cA, &cB);
+  load_tables<T, QFP, VAR>(p, smem, &cA);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -484,13 +477,13 @@ __global__ void __launch_bounds__(256) k_eval(const Params p, qs_sample_out o) {
     for (int64_t k = t0; 2 * k < p.n; k += stride) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
       SampleF s0, s1;
-      eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA, cB);
+      eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
       write_record(p, o, s0, i0);
       if (i1 != i0) write_record(p, o, s1, i1);
     }
   } else {
     for (int64_t i = t0; i < p.n; i += stride)
-      write_record(p, o, eval_one<T, QFP, VAR>(p, tab, i, cA, cB), i);
+      write_record(p, o, eval_one<T, QFP, VAR>(p, tab, i, cA), i);
   }
 }
 
@@ -500,14 +493,13 @@ namespace {
 // built once per device by k_cycle_setup (FP64) and kept for the process.
 __device__ double g_cyc_gl[2 * kCycGL];
 __device__ float4 g_cyc_a[kCycN];
-__device__ float2 g_cyc_b[kCycN];
 
 // One CTA of kCycGL/2 threads: thread i finds the i-th root z of P_n (n =
 // kCycGL) by Newton's method from cos(pi (i + 3/4)/(n + 1/2)) and its
 // mirror; psi = (pi/4)(1 -+ z) on the quarter period, weight 2/((1 - z^2)
 // P_n'(z)^2) times pi/4 times the 2/pi of the cycle mean.  Then the table
-// nodes u_n = n du, chi_n = chi_s (2^u_n - 1): G, S, H with their
-// u-derivatives (dchi/du = ln2 (chi + chi_s)) times du.
+// nodes u_n = n du, chi_n = chi_s (2^u_n - 1): {G, dG/du du, H, dH/du du}
+// (dchi/du = ln2 (chi + chi_s)); S comes from G's interpolant.
 __global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
   __shared__ double gl[2 * kCycGL];
   const int n = kCycGL, i = threadIdx.x;
@@ -534,10 +526,9 @@ __global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
   for (int m = i; m < kCycN; m += blockDim.x) {
     const double u = m * kCycDu, chi = kCycChiS * (exp2(u) - 1.0);
     const double dchi = 0.69314718055994530942 * (chi + kCycChiS) * kCycDu;
-    double G, S, H, dG, dS, dH;
-    cycle_factors_d(gl, chi, G, S, H, &dG, &dS, &dH);
-    g_cyc_a[m] = make_float4((float)G, (float)(dG * dchi), (float)S, (float)(dS * dchi));
-    g_cyc_b[m] = make_float2((float)H, (float)(dH * dchi));
+    double G, S, H, dG, dH;
+    cycle_factors_d(gl, chi, G, S, H, &dG, nullptr, &dH);
+    g_cyc_a[m] = make_float4((float)G, (float)(dG * dchi), (float)H, (float)(dH * dchi));
   }
 }
 
@@ -560,14 +551,12 @@ int32_t cycle_tables(Params& p, cudaStream_t st) {
       return cuda_fail();
     g_cyc_ready[dev] = true;
   }
-  void *gl = nullptr, *a = nullptr, *b = nullptr;
+  void *gl = nullptr, *a = nullptr;
   if (cudaGetSymbolAddress(&gl, g_cyc_gl) != cudaSuccess ||
-      cudaGetSymbolAddress(&a, g_cyc_a) != cudaSuccess ||
-      cudaGetSymbolAddress(&b, g_cyc_b) != cudaSuccess)
+      cudaGetSymbolAddress(&a, g_cyc_a) != cudaSuccess)
     return cuda_fail();
   p.cyc_gl = static_cast<const double*>(gl);
   p.cyc_a = static_cast<const float4*>(a);
-  p.cyc_b = static_cast<const float2*>(b);
   return QS_OK;
 }
 
@@ -583,7 +572,7 @@ int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
   if (dev >= 0 && dev < 64 && !attr[dev]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxPhase * (int)sizeof(float4) +
-                                 kCycN * (int)(sizeof(float4) + sizeof(float2))) != cudaSuccess)
+                                 kCycN * (int)sizeof(float4)) != cudaSuccess)
       return cuda_fail();
     attr[dev] = true;
   }
@@ -754,7 +743,7 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
                          ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
                          : 0) +
                     ((var & QS_VARIANT_CYCLE_CHI) && prec == QS_F32
-                         ? (size_t)kCycN * (sizeof(float4) + sizeof(float2))
+                         ? (size_t)kCycN * sizeof(float4)
                          : 0);
   int32_t est;
   if (prec == QS_F64) {
