@@ -45,7 +45,7 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"c00bc96143c70783": 8 * (268.57e6 + 3.79e6)}
+TRAFFIC_BY_SOURCE = {"cae873b9b4858fee": 8 * (268.67e6 + 3.88e6)}
 
 
 def parse():

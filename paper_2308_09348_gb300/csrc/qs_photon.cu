@@ -25,7 +25,8 @@ namespace qs {
 
 constexpr int kPhMaxBins = 512;               // photon-energy bins (16 per lane)
 constexpr int kPhK = kPhMaxBins / 32;
-constexpr int kPhN = 1024;                    // table nodes in u = log2 y
+constexpr int kPhN = 256;                     // table nodes in u = log2 y (du = 0.18: lanes on
+                                              // consecutive log-spaced bins share nodes)
 constexpr double kPhUmin = -40.0, kPhUmax = 6.0;
 constexpr double kPhDu = (kPhUmax - kPhUmin) / (kPhN - 1);
 constexpr double kPhYmax = 60.0;              // F ~ e^-y: photons beyond are dropped
@@ -379,7 +380,7 @@ int32_t photon_table(cudaStream_t st) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return detail::cuda_fail();
   if (cap != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
-  k_photon_setup<<<kPhN / 256, 256, 0, st>>>();
+  k_photon_setup<<<(kPhN + 255) / 256, 256, 0, st>>>();
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
     return detail::cuda_fail();
   g_ph_ready[dev] = true;
