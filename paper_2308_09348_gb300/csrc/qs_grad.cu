@@ -127,17 +127,21 @@ __device__ __forceinline__ void qfp_tangent(const Params& p,
 
 // Packed FP32 version of qfp_tangent for two samples at once (f32x2 FMA-pipe
 // instructions, per-sample MUFU), the same recursion written with explicit
-// fused multiply-adds.
+// fused multiply-adds and the forward step's forms: 1/mu = 1/gamma0 + du at
+// the midpoint, so mu_a = -mu^2 du_a and mu_g = mu^2 (1/gamma0^2 - du_g);
+// B' = 4.8 ln(1+1.7 chi) + 4.8 + 3.36/(1+1.7 chi) + 4.88 chi; the factor -2
+// of the variance rate folded into s and s' and the D2 constant into h.
 __device__ __forceinline__ void qfp_tangent_x2(const Params& p, const float4* __restrict__ tab,
                                                float2 a, float2 g0, QfpTan<float>& o0,
                                                QfpTan<float>& o1) {
-  const float2 ONE = f2(1.f), HALF = f2(0.5f), THREE = f2(3.f), M2 = f2(-2.f);
-  const float2 LN2 = f2(0.69314718055994530942f);
-  const float2 C55 = f2((float)(55.0 / (16.0 * 1.7320508075688772935)));
+  const float2 ONE = f2(1.f), HALF = f2(0.5f), THREE = f2(3.f);
+  const float2 C48 = f2((float)(4.8 * 0.69314718055994530942));      // 4.8 ln2
+  const float C55 = (float)kC55;
   const float hcK = p.f.h * p.f.cK;
   const float2 c1 = mul2(mul2(f2(hcK), a), a), c1a = mul2(f2(2.f * hcK), a);
   const float2 CCHI = f2(p.f.cchi), ca = mul2(CCHI, a);
-  const float2 NG0 = make_float2(-g0.x, -g0.y);
+  const float2 ig0 = make_float2(__frcp_rn(g0.x), __frcp_rn(g0.y));
+  const float2 ig02 = mul2(ig0, ig0);
   float2 du = f2(0.f), V = f2(0.f), gph = HALF, du_a = f2(0.f), du_g = f2(0.f), V_a = f2(0.f),
          V_g = f2(0.f), gph_a = f2(0.f), gph_g = f2(0.f);
   const int N = p.n_phase;
@@ -148,37 +152,36 @@ __device__ __forceinline__ void qfp_tangent_x2(const Params& p, const float4* __
     const float2 dum = fma2(hK, gph, du);
     const float2 dum_a = fma2(hK, gph_a, fma2(hK_a, gph, du_a));
     const float2 dum_g = fma2(hK, gph_g, du_g);
-    const float2 r = rcpx2(fma2(g0, dum, ONE));
-    const float2 mu = mul2(g0, r);
-    const float2 nmur = mul2(NG0, mul2(r, r));                        // -mu r
-    const float2 mu_a = mul2(mul2(nmur, g0), dum_a);
-    const float2 mu_g = fma2(nmur, fma2(g0, dum_g, dum), r);
+    const float2 mu = rcpx2(__fadd2_rn(dum, ig0));
+    const float2 m2 = mul2(mu, mu);
+    const float2 mu_a = mul2(make_float2(-m2.x, -m2.y), dum_a);
+    const float2 mu_g = mul2(m2, fma2(dum_g, f2(-1.f), ig02));
     const float2 cg = mul2(ca, G);
     const float2 chi = mul2(cg, mu);
     const float2 chi_a = fma2(mul2(CCHI, G), mu, mul2(cg, mu_a));
     const float2 chi_g = mul2(cg, mu_g);
     // Gaunt factor and derivatives
     const float2 l1 = lg2x2(fma2(f2(1.7f), chi, ONE));
-    const float2 L1 = mul2(LN2, l1);
-    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));
-    const float2 opc = __fadd2_rn(chi, ONE);
-    const float2 B = fma2(mul2(f2(4.8f), opc), L1, fma2(mul2(f2(2.44f), chi), chi, ONE));
+    const float2 r1 = ex2x2(make_float2(-l1.x, -l1.y));              // 1/(1+1.7 chi)
+    const float2 B = fma2(fma2(C48, chi, C48), l1, fma2(mul2(f2(2.44f), chi), chi, ONE));
     const float2 t = ex2x2(mul2(f2(-1.f / 3.f), lg2x2(B)));
     const float2 g = mul2(t, t), iB = mul2(g, t), giB = mul2(g, iB);
-    const float2 Bp = fma2(f2(4.8f), L1, fma2(mul2(f2(8.16f), opc), r1, mul2(f2(4.88f), chi)));
+    const float2 Bp = fma2(C48, l1, fma2(f2(4.88f), chi, fma2(f2(3.36f), r1, f2(4.8f))));
     const float2 Bpp = fma2(fma2(f2(-5.712f), r1, f2(8.16f)), r1, f2(4.88f));
     const float2 gp = mul2(mul2(f2(-2.f / 3.f), giB), Bp);
-    const float2 gpp =
-        mul2(giB, fma2(mul2(mul2(f2(10.f / 9.f), iB), Bp), Bp, mul2(f2(-2.f / 3.f), Bpp)));
-    const float2 s = fma2(chi, gp, mul2(f2(2.f), g));
-    const float2 s_chi = fma2(chi, gpp, mul2(THREE, gp));
-    // second-moment factor and derivative: h2 = g R, R = N/D
-    const float2 Nh = fma2(fma2(f2((float)kHA2), chi, f2((float)kHA1)), chi, ONE);
+    // -2 g'' and -2 (2g + chi g'), -2 (3g' + chi g'')
+    const float2 gpp2 =
+        mul2(giB, fma2(mul2(mul2(f2(-20.f / 9.f), iB), Bp), Bp, mul2(f2(4.f / 3.f), Bpp)));
+    const float2 s2 = fma2(chi, mul2(f2(-2.f), gp), mul2(f2(-4.f), g));
+    const float2 s2_chi = fma2(chi, gpp2, mul2(f2(-6.f), gp));
+    // second-moment factor (times the D2 constant) and derivative: h = g R, R = N/D
+    const float2 Nh = fma2(fma2(f2((float)(kC55 * kHA2)), chi, f2((float)(kC55 * kHA1))), chi,
+                           f2(C55));
     const float2 Dh = fma2(fma2(fma2(f2((float)kHB3), chi, f2((float)kHB2)), chi,
                                 f2((float)kHB1)), chi, ONE);
     const float2 iD = rcpx2(Dh);
     const float2 R = mul2(Nh, iD);
-    const float2 Np = fma2(f2((float)(2.0 * kHA2)), chi, f2((float)kHA1));
+    const float2 Np = fma2(f2((float)(2.0 * kC55 * kHA2)), chi, f2((float)(kC55 * kHA1)));
     const float2 Dp = fma2(fma2(f2((float)(3.0 * kHB3)), chi, f2((float)(2.0 * kHB2))), chi,
                            f2((float)kHB1));
     const float2 Rp = mul2(fma2(make_float2(-R.x, -R.y), Dp, Np), iD);
@@ -190,16 +193,16 @@ __device__ __forceinline__ void qfp_tangent_x2(const Params& p, const float4* __
     const float2 du_a_n = fma2(hKgp, chi_a, fma2(hK_a, g, du_a));
     const float2 du_g_n = fma2(hKgp, chi_g, du_g);
     // variance
-    const float2 hKmu = mul2(hK, mu), hKmus = mul2(hKmu, s_chi);
-    const float2 hlam = mul2(mul2(M2, hKmu), s);
-    const float2 hlam_a = mul2(M2, fma2(hKmus, chi_a, mul2(s, fma2(hK_a, mu, mul2(hK, mu_a)))));
-    const float2 hlam_g = mul2(M2, fma2(hKmus, chi_g, mul2(mul2(hK, mu_g), s)));
-    const float2 m2 = mul2(mu, mu), chih2 = mul2(chi, h2), C55m2 = mul2(C55, m2);
-    const float2 hD2 = mul2(mul2(C55m2, hKmu), chih2);
+    const float2 hKmu = mul2(hK, mu), hKmus = mul2(hKmu, s2_chi);
+    const float2 hlam = mul2(hKmu, s2);
+    const float2 hlam_a = fma2(hKmus, chi_a, mul2(s2, fma2(hK_a, mu, mul2(hK, mu_a))));
+    const float2 hlam_g = fma2(hKmus, chi_g, mul2(mul2(hK, mu_g), s2));
+    const float2 chih2 = mul2(chi, h2);
+    const float2 hD2 = mul2(mul2(m2, hKmu), chih2);
     const float2 hh = fma2(chi, h2p, h2);
     const float2 hK3 = mul2(THREE, hK), hKmuh = mul2(hKmu, hh);
-    const float2 hD2_a = mul2(C55m2, fma2(fma2(hK_a, mu, mul2(hK3, mu_a)), chih2, mul2(hKmuh, chi_a)));
-    const float2 hD2_g = mul2(C55m2, fma2(mul2(hK3, mu_g), chih2, mul2(hKmuh, chi_g)));
+    const float2 hD2_a = mul2(m2, fma2(fma2(hK_a, mu, mul2(hK3, mu_a)), chih2, mul2(hKmuh, chi_a)));
+    const float2 hD2_g = mul2(m2, fma2(mul2(hK3, mu_g), chih2, mul2(hKmuh, chi_g)));
     const float2 hr = fma2(hlam, V, hD2);
     const float2 hr_a = fma2(hlam, V_a, fma2(hlam_a, V, hD2_a));
     const float2 hr_g = fma2(hlam, V_g, fma2(hlam_g, V, hD2_g));
