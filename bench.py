@@ -45,7 +45,7 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"cae873b9b4858fee": 8 * (268.67e6 + 3.88e6)}
+TRAFFIC_BY_SOURCE = {"ab1efdac78770f0e": 8 * (268.81e6 + 4.05e6)}
 
 
 def parse():
@@ -634,6 +634,21 @@ def main():
             B.qs_scatter_host(wl.laser, wl.beam, host, wl.bins, precision=args.precision,
                               out=hout)
 
+        # this box's pinned host-to-device copy rate (one stream, 512 MB):
+        # the end-to-end step is copy-bound when it falls below ~50 GB/s
+        hb = host[0][:1 << 27] if host[0].numel() >= 1 << 27 else host[0]
+        db = torch.empty_like(hb, device=dev)
+        db.copy_(hb, non_blocking=True)
+        torch.cuda.synchronize()
+        ca, cb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ca.record(stream)
+        for _ in range(3):
+            db.copy_(hb, non_blocking=True)
+        cb.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * hb.numel() * hb.element_size() / (ca.elapsed_time(cb) * 1e-3) / 1e9
+        del db
+
         e2e_step()
         torch.cuda.synchronize()
         k2 = max(2, args.steps // 2)
@@ -658,7 +673,8 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                "api": "qs_scatter_host (pinned host samples, automatic chunks: whole waves, "
                       "growing x3 to 2^23; copy/compute overlap)",
-               "spectrum_equals_device_path": same, "clocks": e2e_clocks}
+               "spectrum_equals_device_path": same, "clocks": e2e_clocks,
+               "h2d_copy_gbs": h2d_gbs}
         del host, hout
 
     # ---- plain FP64 GPU path, same samples --------------------------------

@@ -264,7 +264,7 @@ int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam, const qs_sam
  * histograms, moments up to the order of the reduction.
  *   h_samples   qs_samples whose xi[] and w point to host memory
  *   chunk       samples per chunk, a positive multiple of 1024; or 0: chunks
- *               of whole waves of the FP32 launch (2048 samples per SM), the
+ *               of whole waves of the FP32 launch (1792 samples per SM), the
  *               first one wave and each next three times the last, up to
  *               2^23 samples, so that the first copy is short
  *   h_*         host output buffers (same sizes and rules as qs_scatter)

@@ -165,12 +165,14 @@ using namespace detail;
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
 // VAR: model variant bits (kVarCell, kVarCycle).
-// Register budget per thread: FP32 QFP 64 (one 1024-thread CTA per SM for
-// the pipe-bound loop), FP32 classical 80 (three 256-thread CTAs per SM keep
-// enough loads in flight for the HBM-bound path), FP32 variants 80 (one
-// 768-thread CTA per SM), FP64 128.
+// Register budget per thread: FP32 QFP 72 (one 896-thread CTA per SM for
+// the pipe-bound loop: at 64 registers and 1024 threads the packed
+// constants are re-materialised on the FMA pipe every cell, 4 % slower),
+// FP32 classical 80 (three 256-thread CTAs per SM keep enough loads in
+// flight for the HBM-bound path), FP32 variants 80 (one 768-thread CTA per
+// SM), FP64 128.
 template <typename T, bool QFP, int VAR>
-constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 64 : 80);
+constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 72 : 80);
 
 // Block size of k_scatter when the caller leaves it open.  The FP32 paths
 // that integrate phase cells are bound by the FMA and MUFU pipes.  CTAs that
@@ -178,7 +180,7 @@ constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 64 : 80
 // the first one finishes at ~40 % of the launch and the SM ends it with a
 // quarter of its warps (22.9 of 32 warps resident on average).  One CTA per
 // SM that fills the register file keeps every warp resident to the end:
-// 1024 threads at 64 registers, 768 at 80.  The classical and FP64 paths
+// 896 threads at 72 registers, 768 at 80.  The classical and FP64 paths
 // keep 256-thread CTAs.
 int scatter_block(const qs_exec* e, int block, int prec, bool qfp, int variant) {
   if ((e && e->block) || prec != QS_F32 || !(qfp || (variant & QS_VARIANT_CELL_FOCUS)))
@@ -862,7 +864,7 @@ struct HostPlan {
 };
 
 // Automatic chunking (chunk = 0): whole waves of the FP32 cell-integrating
-// launch (two samples per thread, one 1024-thread CTA per SM), so that no
+// launch (two samples per thread, one scatter_block-sized CTA per SM), so that no
 // chunk ends on a partly idle pass over the grid; the first chunk is one
 // wave and each next one three times the last, up to 2^23 samples, so the
 // copy of chunk c+1 (~4x faster per sample than its evaluation) hides
@@ -879,7 +881,7 @@ bool host_plan(HostPlan& hp, const qs_bins* b, int block, int grid, int sms,
     hp.chunk = chunk;
     hp.wave = 0;
   } else {
-    hp.wave = (int64_t)2048 * sms;
+    hp.wave = (int64_t)2 * scatter_block(nullptr, 0, QS_F32, true, 0) * sms;
     const int64_t cap = ((int64_t)1 << 23) / hp.wave;
     hp.chunk = (cap > 0 ? cap : 1) * hp.wave;
   }

@@ -43,11 +43,11 @@ def test_host_equals_device(chunk, prec, model):
 
 
 def test_host_automatic_chunks_span_the_ramp():
-    """chunk = 0: chunks of whole waves (2048 samples per SM) growing x3 up
+    """chunk = 0: chunks of whole waves (1792 samples per SM) growing x3 up
     to 2^23 samples; n spans the 1-, 3- and 9-wave chunks, full chunks and a
     ragged tail."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    wave = 2048 * sms
+    wave = 1792 * sms
     n = 13 * wave + (1 << 23) // wave * wave + 12_345
     wl = I.full_qfp(n)
     L = I.Laser(**{**wl.laser.__dict__, "n_phase": 32})
