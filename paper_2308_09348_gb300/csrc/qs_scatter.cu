@@ -165,14 +165,17 @@ using namespace detail;
 // arithmetic type; H: shared-memory histogram counter (u32 counts or u64
 // fixed-point weights); QFP: model; SHIST: histograms in shared memory.
 // VAR: model variant bits (kVarCell, kVarCycle).
-// Register budget per thread: FP32 QFP 72 (one 896-thread CTA per SM for
-// the pipe-bound loop: at 64 registers and 1024 threads the packed
-// constants are re-materialised on the FMA pipe every cell, 4 % slower),
-// FP32 classical 80 (three 256-thread CTAs per SM keep enough loads in
-// flight for the HBM-bound path), FP32 variants 80 (one 768-thread CTA per
-// SM), FP64 128.
+// Register budget per thread: FP32 QFP and per-cell focus 72 (one
+// 896-thread CTA per SM for the pipe-bound loop: at 64 registers and 1024
+// threads the packed constants are re-materialised on the FMA pipe every
+// cell, 4 % slower), FP32 cycle-resolved chi 80 (one 768-thread CTA per SM;
+// it spills at 72), FP32 classical 80 (three 256-thread CTAs per SM keep
+// enough loads in flight for the HBM-bound path), FP64 128.
+constexpr int scatter_regs(bool f64, bool qfp, int var) {
+  return f64 ? 128 : ((var & kVarCycle) ? 80 : ((qfp || var != 0) ? 72 : 80));
+}
 template <typename T, bool QFP, int VAR>
-constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 72 : 80);
+constexpr int kScatterRegs = scatter_regs(sizeof(T) == 8, QFP, VAR);
 
 // Block size of k_scatter when the caller leaves it open.  The FP32 paths
 // that integrate phase cells are bound by the FMA and MUFU pipes.  CTAs that
@@ -180,13 +183,12 @@ constexpr int kScatterRegs = sizeof(T) == 8 ? 128 : ((QFP && VAR == 0) ? 72 : 80
 // the first one finishes at ~40 % of the launch and the SM ends it with a
 // quarter of its warps (22.9 of 32 warps resident on average).  One CTA per
 // SM that fills the register file keeps every warp resident to the end:
-// 896 threads at 72 registers, 768 at 80.  The classical and FP64 paths
-// keep 256-thread CTAs.
+// 896 threads at 72 registers, 768 at 80 (cycle-resolved chi).  The
+// classical and FP64 paths keep 256-thread CTAs.
 int scatter_block(const qs_exec* e, int block, int prec, bool qfp, int variant) {
   if ((e && e->block) || prec != QS_F32 || !(qfp || (variant & QS_VARIANT_CELL_FOCUS)))
     return block;
-  const int regs = (qfp && variant == 0) ? kScatterRegs<float, true, 0>
-                                         : kScatterRegs<float, true, 1>;
+  const int regs = scatter_regs(false, qfp, variant);
   // warps are granted registers in groups of four
   const int b = ((65536 / (regs * 32)) & ~3) * 32;
   return b > 1024 ? 1024 : b;
