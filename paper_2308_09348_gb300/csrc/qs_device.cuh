@@ -289,15 +289,12 @@ __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float
   const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
   const float x = fminf(fmaxf(__fmul_rn(u, (float)(1.0 / kCycDu)), 0.f),
                         (float)(kCycN - 1) - 1e-3f);
-  // floor without a conversion instruction: x + 2^23 rounds x to an integer
-  const float xm = __fadd_rn(x, 8388608.f);
-  float r = __fsub_rn(xm, 8388608.f);
-  int idx = __float_as_int(xm) - 0x4B000000;
-  if (r > x) {
-    r = __fsub_rn(r, 1.f);
-    idx -= 1;
-  }
-  const float t = __fsub_rn(x, r), t2 = __fmul_rn(t, t);
+  // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
+  // (x - 1/2 in [-1/2, kCycN - 1.501] keeps the sum in [2^23, 2^24), where
+  // the float spacing is 1), so idx in [0, kCycN - 2] and t = x - idx in [0, 1]
+  const float xm = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.f);
+  const int idx = __float_as_int(xm) - 0x4B400000;
+  const float t = __fsub_rn(x, __fsub_rn(xm, 12582912.f)), t2 = __fmul_rn(t, t);
   const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));       // 3t^2 - 2t^3
   const float h11 = __fmaf_rn(t2, t, -t2);                         // t^3 - t^2
   const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);              // t - 2t^2 + t^3

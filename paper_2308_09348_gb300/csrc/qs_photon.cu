@@ -78,19 +78,17 @@ __global__ void __launch_bounds__(256) k_photon_setup() {
 
 // FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
 // table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
-__device__ __forceinline__ float synch_F(const float4* __restrict__ T, float xi, float r1,
+__device__ __forceinline__ float synch_F(const float4* __restrict__ T, float om, float r1,
                                          float y) {
   const float u = M<float>::lg2(y);
-  const float x = fminf(fmaxf(__fmul_rn(__fsub_rn(u, (float)kPhUmin), (float)(1.0 / kPhDu)), 0.f),
+  const float x = fminf(fmaxf(__fmaf_rn(u, (float)(1.0 / kPhDu), (float)(-kPhUmin / kPhDu)), 0.f),
                         (float)(kPhN - 1) - 1e-3f);
-  const float xm = __fadd_rn(x, 8388608.f);          // floor without a conversion
-  float r = __fsub_rn(xm, 8388608.f);
-  int idx = __float_as_int(xm) - 0x4B000000;
-  if (r > x) {
-    r = __fsub_rn(r, 1.f);
-    idx -= 1;
-  }
-  const float t = __fsub_rn(x, r), t2 = __fmul_rn(t, t);
+  // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
+  // (x - 1/2 in [-1/2, kPhN - 1.501] keeps the sum in [2^23, 2^24), where the
+  // float spacing is 1), so idx in [0, kPhN - 2] and t = x - idx in [0, 1]
+  const float xm = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.f);
+  const int idx = __float_as_int(xm) - 0x4B400000;
+  const float t = __fsub_rn(x, __fsub_rn(xm, 12582912.f)), t2 = __fmul_rn(t, t);
   const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));
   const float h11 = __fmaf_rn(t2, t, -t2);
   const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);
@@ -100,8 +98,8 @@ __device__ __forceinline__ float synch_F(const float4* __restrict__ T, float xi,
   const float ylog = __fmul_rn(y, (float)kLog2e);
   const float k23 = M<float>::ex2(__fsub_rn(__fmaf_rn(-2.f / 3.f, u, q23), ylog));
   const float ki13 = M<float>::ex2(__fsub_rn(q13, ylog));
-  // 1 - xi + 1/(1 - xi), with r1 = 1/(1 - xi)
-  return __fmaf_rn(__fadd_rn(__fsub_rn(1.f, xi), r1), k23, -ki13);
+  // 1 - xi + 1/(1 - xi), with om = 1 - xi and r1 = 1/om
+  return __fmaf_rn(__fadd_rn(om, r1), k23, -ki13);
 }
 
 // FP64: the same F from the integrals.
@@ -263,9 +261,10 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
             const float4 em = stage[q];
             if (e < em.z) {
               const float xi = __fmul_rn(e, em.x);
-              const float r1 = M<float>::rcp(__fsub_rn(1.f, xi));
+              const float om = __fsub_rn(1.f, xi);
+              const float r1 = M<float>::rcp(om);
               const float y = __fmul_rn(__fmul_rn(em.y, xi), r1);
-              const float F = synch_F(ptab, xi, r1, y);
+              const float F = synch_F(ptab, om, r1, y);
               ps = __fmaf_rn(em.w, F, ps);
               if constexpr (ANG) {
                 const float2 ea = stageA[q];
