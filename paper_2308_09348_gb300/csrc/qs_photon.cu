@@ -78,28 +78,46 @@ __global__ void __launch_bounds__(256) k_photon_setup() {
 
 // FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
 // table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
-__device__ __forceinline__ float synch_F(const float4* __restrict__ T, float om, float r1,
-                                         float y) {
-  const float u = M<float>::lg2(y);
-  const float x = fminf(fmaxf(__fmaf_rn(u, (float)(1.0 / kPhDu), (float)(-kPhUmin / kPhDu)), 0.f),
-                        (float)(kPhN - 1) - 1e-3f);
+__device__ __forceinline__ float hermite(float h01, float h10, float h11, float v0, float d0,
+                                         float v1, float d1) {
+  return __fmaf_rn(h11, d1, __fmaf_rn(h10, d0, __fmaf_rn(h01, __fsub_rn(v1, v0), v0)));
+}
+
+// Two photon energies e (two bins of one lane) against one emitter whose
+// {1/mu, 1/mu, 2/(3 chi), 2/(3 chi)} is pq: F for both, packed f32x2 except
+// the table gathers and the Hermite sums.  Bins beyond the emitter's cut
+// (y > ymax, or xi >= 1) give finite or NaN values that the caller discards;
+// their table index stays in range (fmaxf takes 0 over NaN).
+__device__ __forceinline__ float2 synch_F2(const float4* __restrict__ T, float2 e, float4 pq) {
+  const float2 xi = mul2(e, make_float2(pq.x, pq.y));
+  const float2 om = fma2(xi, f2(-1.f), f2(1.f));                      // 1 - xi
+  const float2 r1 = rcpx2(om);
+  const float2 y = mul2(mul2(make_float2(pq.z, pq.w), xi), r1);
+  const float2 u = lg2x2(y);
+  float2 x = fma2(u, f2((float)(1.0 / kPhDu)), f2((float)(-kPhUmin / kPhDu)));
+  x.x = fminf(fmaxf(x.x, 0.f), (float)(kPhN - 1) - 1e-3f);
+  x.y = fminf(fmaxf(x.y, 0.f), (float)(kPhN - 1) - 1e-3f);
   // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
   // (x - 1/2 in [-1/2, kPhN - 1.501] keeps the sum in [2^23, 2^24), where the
-  // float spacing is 1), so idx in [0, kPhN - 2] and t = x - idx in [0, 1]
-  const float xm = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.f);
-  const int idx = __float_as_int(xm) - 0x4B400000;
-  const float t = __fsub_rn(x, __fsub_rn(xm, 12582912.f)), t2 = __fmul_rn(t, t);
-  const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));
-  const float h11 = __fmaf_rn(t2, t, -t2);
-  const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);
-  const float4 a0 = T[idx], a1 = T[idx + 1];
-  const float q23 = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, __fsub_rn(a1.x, a0.x), a0.x)));
-  const float q13 = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
-  const float ylog = __fmul_rn(y, (float)kLog2e);
-  const float k23 = M<float>::ex2(__fsub_rn(__fmaf_rn(-2.f / 3.f, u, q23), ylog));
-  const float ki13 = M<float>::ex2(__fsub_rn(q13, ylog));
-  // 1 - xi + 1/(1 - xi), with om = 1 - xi and r1 = 1/om
-  return __fmaf_rn(__fadd_rn(om, r1), k23, -ki13);
+  // float spacing is 1), so the index is in [0, kPhN - 2] and t = x - index
+  // in [0, 1]
+  const float2 xm = __fadd2_rn(__fadd2_rn(x, f2(-0.5f)), f2(12582912.f));
+  const int i0 = __float_as_int(xm.x) - 0x4B400000, i1 = __float_as_int(xm.y) - 0x4B400000;
+  const float2 t = __fadd2_rn(x, fma2(xm, f2(-1.f), f2(12582912.f)));
+  const float2 t2 = mul2(t, t);
+  const float2 h01 = mul2(t2, fma2(f2(-2.f), t, f2(3.f)));           // 3t^2 - 2t^3
+  const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));              // t^3 - t^2
+  const float2 h10 = __fadd2_rn(fma2(t2, f2(-1.f), t), h11);         // t - 2t^2 + t^3
+  const float4 a0 = T[i0], a1 = T[i0 + 1], b0 = T[i1], b1 = T[i1 + 1];
+  const float2 q23 = make_float2(hermite(h01.x, h10.x, h11.x, a0.x, a0.y, a1.x, a1.y),
+                                 hermite(h01.y, h10.y, h11.y, b0.x, b0.y, b1.x, b1.y));
+  const float2 q13 = make_float2(hermite(h01.x, h10.x, h11.x, a0.z, a0.w, a1.z, a1.w),
+                                 hermite(h01.y, h10.y, h11.y, b0.z, b0.w, b1.z, b1.w));
+  const float2 ny = mul2(y, f2((float)(-kLog2e)));
+  const float2 k23 = ex2x2(__fadd2_rn(fma2(f2(-2.f / 3.f), u, q23), ny));
+  const float2 ki13 = ex2x2(__fadd2_rn(q13, ny));
+  // (1 - xi + 1/(1 - xi)) K_{2/3} - Ki_{1/3}
+  return fma2(ki13, f2(-1.f), mul2(__fadd2_rn(om, r1), k23));
 }
 
 // FP64: the same F from the integrals.
@@ -166,8 +184,7 @@ __host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int 
   const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
   const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
   const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
-  const size_t stage =
-      sizeof(T) == 4 ? (size_t)(block / 32) * 64 * (sizeof(float4) + sizeof(float2)) : 0;
+  const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * 3 * sizeof(float4) : 0;
   return tab + pt + e + (size_t)(block / 32) * (ang ? 3 : 1) * nb * sizeof(double) + stage;
 }
 
@@ -187,9 +204,12 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
   double* part = reinterpret_cast<double*>(
       reinterpret_cast<unsigned char*>(eps) + (((size_t)nb * sizeof(T) + 15) & ~(size_t)15));
   const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* stage = reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) + warp * 64;
-  float2* stageA = reinterpret_cast<float2*>(reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) +
-                                             nwarp * 64) + warp * 64;
+  // per emitter q of the warp: stP[q] = {1/mu, 1/mu, 2/(3chi), 2/(3chi)},
+  // stQ[q] = {c, c, cut, cut}, stA[q] = {c thx^2 term x2, c thy^2 term x2}
+  // (pairs ready for the packed evaluation)
+  float4* stP = reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) + warp * 192;
+  float4* stQ = stP + 64;
+  float4* stA = stP + 128;
   for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (sizeof(T) == 4)
     for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
@@ -230,53 +250,57 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
         const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;
         // the warp's 64 emitters of this cell, staged once
         const float4 e0 = emitter(mu.x, chi.x, c0), e1 = emitter(mu.y, chi.y, c1);
-        stage[lane] = e0;
-        stage[32 + lane] = e1;
+        stP[lane] = make_float4(e0.x, e0.x, e0.y, e0.y);
+        stP[32 + lane] = make_float4(e1.x, e1.x, e1.y, e1.y);
+        stQ[lane] = make_float4(e0.w, e0.w, e0.z, e0.z);
+        stQ[32 + lane] = make_float4(e1.w, e1.w, e1.z, e1.z);
         if constexpr (ANG) {
           // mean square angles (A/mu = chi/(cchi mu^2)), times c
           const float am0 = __fmul_rn(__fmul_rn(chi.x, icchi), __fmul_rn(e0.x, e0.x));
           const float am1 = __fmul_rn(__fmul_rn(chi.y, icchi), __fmul_rn(e1.x, e1.x));
           const float cone0 = __fmul_rn(e0.x, e0.x), cone1 = __fmul_rn(e1.x, e1.x);
-          stageA[lane] = make_float2(
-              __fmul_rn(c0, __fmaf_rn(tx0, tx0, __fmaf_rn(0.5f, __fmul_rn(am0, am0), cone0))),
-              __fmul_rn(c0, __fmaf_rn(ty0, ty0, cone0)));
-          stageA[32 + lane] = make_float2(
-              __fmul_rn(c1, __fmaf_rn(tx1, tx1, __fmaf_rn(0.5f, __fmul_rn(am1, am1), cone1))),
-              __fmul_rn(c1, __fmaf_rn(ty1, ty1, cone1)));
+          const float ax0 = __fmul_rn(c0, __fmaf_rn(tx0, tx0, __fmaf_rn(0.5f, __fmul_rn(am0, am0), cone0)));
+          const float ay0 = __fmul_rn(c0, __fmaf_rn(ty0, ty0, cone0));
+          const float ax1 = __fmul_rn(c1, __fmaf_rn(tx1, tx1, __fmaf_rn(0.5f, __fmul_rn(am1, am1), cone1)));
+          const float ay1 = __fmul_rn(c1, __fmaf_rn(ty1, ty1, cone1));
+          stA[lane] = make_float4(ax0, ax0, ay0, ay0);
+          stA[32 + lane] = make_float4(ax1, ax1, ay1, ay1);
         }
         float emax = fmaxf(e0.z, e1.z);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         __syncwarp();
-        // lane b of group k: its energy against every emitter (independent
-        // evaluations, summed plainly over the 64, then compensated)
+        // lane b takes bins b and b + 32 of each group pair against every
+        // emitter (packed, independent evaluations, summed plainly over the
+        // 64, then compensated)
 #pragma unroll
-        for (int kk = 0; kk < KB; ++kk) {
+        for (int kk = 0; kk < KB; kk += 2) {
           if (32 * kk >= nb || !(eps[32 * kk] < emax)) break;
-          const int b = 32 * kk + lane;
-          const float e = b < nb ? eps[b] : 3.4e38f;
-          float ps = 0.f, px = 0.f, py = 0.f;
-#pragma unroll 4
+          const int b0 = 32 * kk + lane, b1 = b0 + 32;
+          const float2 e = make_float2(b0 < nb ? eps[b0] : 3.4e38f, b1 < nb ? eps[b1] : 3.4e38f);
+          float2 ps = f2(0.f), px = f2(0.f), py = f2(0.f);
+#pragma unroll 2
           for (int q = 0; q < 64; ++q) {
-            const float4 em = stage[q];
-            if (e < em.z) {
-              const float xi = __fmul_rn(e, em.x);
-              const float om = __fsub_rn(1.f, xi);
-              const float r1 = M<float>::rcp(om);
-              const float y = __fmul_rn(__fmul_rn(em.y, xi), r1);
-              const float F = synch_F(ptab, om, r1, y);
-              ps = __fmaf_rn(em.w, F, ps);
+            const float4 qq = stQ[q];
+            const bool in0 = e.x < qq.z, in1 = e.y < qq.z;
+            if (in0 || in1) {
+              const float2 F = synch_F2(ptab, e, stP[q]);
+              const float2 Fm = make_float2(in0 ? F.x : 0.f, in1 ? F.y : 0.f);
+              ps = fma2(make_float2(qq.x, qq.y), Fm, ps);
               if constexpr (ANG) {
-                const float2 ea = stageA[q];
-                px = __fmaf_rn(ea.x, F, px);
-                py = __fmaf_rn(ea.y, F, py);
+                const float4 aq = stA[q];
+                px = fma2(make_float2(aq.x, aq.y), Fm, px);
+                py = fma2(make_float2(aq.z, aq.w), Fm, py);
               }
             }
           }
-          acc.add(0, kk, ps);
+          acc.add(0, kk, ps.x);
+          acc.add(0, kk + 1, ps.y);
           if constexpr (ANG) {
-            acc.add(1, kk, px);
-            acc.add(2, kk, py);
+            acc.add(1, kk, px.x);
+            acc.add(1, kk + 1, px.y);
+            acc.add(2, kk, py.x);
+            acc.add(2, kk + 1, py.y);
           }
         }
         __syncwarp();
