@@ -780,6 +780,9 @@ def main():
                            "l2": "inputs (2.1 GB per GPU) larger than L2; no flush"},
                 "gpu_launches": 2 * args.steps, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "fp64_path": f64,
+                "paper_context": "the paper's own Python tool gives one prediction in a few "
+                                 "minutes on an unspecified personal computer (no per-sample "
+                                 "rate or hardware stated): context, not a baseline",
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
                 "cell_focus": cell, "cycle_chi": cyc, "photon": phot,
                 "pw_reconstruction": pwr,
