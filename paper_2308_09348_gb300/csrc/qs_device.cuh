@@ -730,6 +730,57 @@ __device__ __forceinline__ SampleF eval_ll_f32_xi(const Params& p, float xi0, fl
   return s;
 }
 
+// Two classical samples at once in packed f32x2 arithmetic: the same
+// operations in the same order as focus_xi<float>, the LL closed form and
+// recombine_f2 (a - b as a + (-b), 1 - d and g0 - q0 d as one fma with -1),
+// so each lane rounds exactly as the scalar path does.
+__device__ __forceinline__ void eval_ll_f32x2(const Params& p, float2 xi0, float2 xi1, float2 xi2,
+                                              float2 xi3, float2 xi4, float2 xi5, SampleF& s0,
+                                              SampleF& s1) {
+  const float2 ONE = f2(1.f), M1 = f2(-1.f);
+  // decode and collision geometry (focus_xi)
+  const float2 x = fma2(f2(p.f.sx), xi0, f2(p.f.bdx));
+  const float2 y = fma2(f2(p.f.sy), xi1, f2(p.f.bdy));
+  const float2 z = mul2(f2(p.f.sz), xi2);
+  float2 g0 = p.flat ? fma2(f2(p.f.gspan), xi3, f2(p.f.glo))
+                     : mul2(f2(p.f.gmean), fma2(f2(p.f.spread), xi3, ONE));
+  if (g0.x < 1.f) g0.x = 1.f;
+  if (g0.y < 1.f) g0.y = 1.f;
+  const float2 thx = mul2(f2(p.f.div), xi4), thy = mul2(f2(p.f.div), xi5);
+  const float2 ct = mul2(f2(0.5f), __fadd2_rn(z, f2(p.f.c_delay)));
+  const float2 zs = mul2(f2(0.5f), __fadd2_rn(z, f2(-p.f.c_delay)));
+  const float2 xs = __fadd2_rn(fma2(thx, ct, x), f2(-p.f.ldx));
+  const float2 ys = __fadd2_rn(fma2(thy, ct, y), f2(-p.f.ldy));
+  const float2 rho2 = fma2(xs, xs, mul2(ys, ys));
+  const float2 zq = mul2(zs, f2(p.f.inv_zR));
+  const float2 q = fma2(zq, zq, ONE);
+  const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), rcpx2(q));
+  const float2 a = mul2(mul2(f2(p.f.a0), rsqrtx2(q)),
+                        ex2x2(mul2(f2(-1.4426950408889634074f), E)));
+  // Eq. 3 and the two-float recombination (recombine_f2)
+  const float2 du = mul2(mul2(f2(p.f.cRR), a), a);
+  const float2 pp = mul2(g0, du);
+  const float2 pe = fma2(g0, du, make_float2(-pp.x, -pp.y));
+  const float2 sm = __fadd2_rn(ONE, pp);
+  const float2 bb = __fadd2_rn(sm, M1);
+  const float2 se = __fadd2_rn(fma2(__fadd2_rn(sm, make_float2(-bb.x, -bb.y)), M1, ONE),
+                               fma2(bb, M1, pp));
+  const float2 t = __fadd2_rn(se, pe);
+  const float2 dh = __fadd2_rn(sm, t);
+  const float2 dl = fma2(fma2(sm, M1, dh), M1, t);
+  const float2 r0 = rcpx2(dh);
+  const float2 q0 = mul2(g0, r0);
+  const float2 nq0 = make_float2(-q0.x, -q0.y);
+  const float2 e2 = fma2(nq0, dl, fma2(nq0, dh, g0));
+  const float2 c = mul2(e2, r0);
+  const float2 hi = __fadd2_rn(q0, c);
+  const float2 lo = fma2(fma2(q0, M1, hi), M1, c);
+  s0.g0 = g0.x; s0.aeff = a.x; s0.mu_hi = hi.x; s0.mu_lo = lo.x; s0.V = 0.f; s0.theta_e = 0.f;
+  s0.thx0 = thx.x; s0.thy0 = thy.x; s0.tx = thx.x; s0.ty = thy.x; s0.go_hi = hi.x; s0.go_lo = lo.x;
+  s1.g0 = g0.y; s1.aeff = a.y; s1.mu_hi = hi.y; s1.mu_lo = lo.y; s1.V = 0.f; s1.theta_e = 0.f;
+  s1.thx0 = thx.y; s1.thy0 = thy.y; s1.tx = thx.y; s1.ty = thy.y; s1.go_hi = hi.y; s1.go_lo = lo.y;
+}
+
 __device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
   return eval_ll_f32_xi(p, load_t<float>(p.xi[0], i, p.dtype), load_t<float>(p.xi[1], i, p.dtype),
                         load_t<float>(p.xi[2], i, p.dtype), load_t<float>(p.xi[3], i, p.dtype),

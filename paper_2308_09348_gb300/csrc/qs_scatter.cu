@@ -299,11 +299,15 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
             for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
             const float4 wv = W ? __ldg(static_cast<const float4*>(p.w) + k)
                                 : make_float4(1.f, 1.f, 1.f, 1.f);
-            const SampleF s4[4] = {
-                eval_ll_f32_xi(p, v[0].x, v[1].x, v[2].x, v[3].x, v[4].x, v[5].x),
-                eval_ll_f32_xi(p, v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y),
-                eval_ll_f32_xi(p, v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z),
-                eval_ll_f32_xi(p, v[0].w, v[1].w, v[2].w, v[3].w, v[4].w, v[5].w)};
+            SampleF s4[4];
+#define QS_LO2(c) make_float2(v[c].x, v[c].y)
+#define QS_HI2(c) make_float2(v[c].z, v[c].w)
+            eval_ll_f32x2(p, QS_LO2(0), QS_LO2(1), QS_LO2(2), QS_LO2(3), QS_LO2(4), QS_LO2(5),
+                          s4[0], s4[1]);
+            eval_ll_f32x2(p, QS_HI2(0), QS_HI2(1), QS_HI2(2), QS_HI2(3), QS_HI2(4), QS_HI2(5),
+                          s4[2], s4[3]);
+#undef QS_LO2
+#undef QS_HI2
             accumulate4_ll<H, SHIST, W>(p, s4, wv, acc, hs, hm, ha, nspec, nmap, naeff);
           }
         };
