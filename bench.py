@@ -45,7 +45,7 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.
-TRAFFIC_BY_SOURCE = {"dde3923f62aa8de9": 8 * (268.70e6 + 4.05e6)}
+TRAFFIC_BY_SOURCE = {"549d66af8bcec180": 8 * (268.62e6 + 4.02e6)}
 
 
 def parse():
