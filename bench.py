@@ -40,6 +40,16 @@ QFP_FMA_OPS_PER_STEP = 40
 QFP_MUFU_SLOTS_PER_STEP = 2 + 2 + 1 * 0.5
 QFP_MUFU_MIX = {"lg2": 2, "rcp": 2, "ex2": 1}
 FMA_LANES_PER_SM = 128
+
+# Adjoint (packed tangent recursion, FP32): per sample-step 103 FMA-pipe
+# operations (the forward step with two tangents carried through mu, chi, the
+# Gaunt factor with g' and g'', the second-moment fit with h', and the mean
+# and variance updates) and 5 MUFU slots (2 lg2, 2 rcp, 2 ex2).
+GRAD_FMA_OPS_PER_STEP = 103
+# Photon spectrum (FP32): per (sample, cell, bin) evaluation 32 FMA-pipe
+# operations (24 in the packed part of F and the accumulation, 8 in the two
+# Hermite sums) and 3 MUFU slots (rcp, lg2, 2 ex2).
+PHOTON_FMA_OPS_PER_EVAL = 32
 MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
@@ -274,6 +284,13 @@ def run_reference(args):
     return 0
 
 
+def _fma_peak(dev):
+    """FP32 FMA-pipe lane-operations per second at the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * FMA_LANES_PER_SM * float(peaks().get("sm_max_mhz", 2070.0)) * 1e6
+
+
 def _events(n=2):
     import torch
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -419,9 +436,16 @@ def bench_photon(dev, rank, n=1 << 19, steps=2):
         B.qs_photon_spectrum(wl.laser, wl.beam, xi, pb, out=out, kernel_events=kev[k])
     torch.cuda.synchronize()
     kms = sum(x.elapsed_time(y) for x, y in kev) / steps
+    evals = n * wl.laser.n_phase * pb.n_bins
+    peak = _fma_peak(dev)
     return {"metric": "beam-sample evals/s", "value": n / (kms * 1e-3), "unit": "samples/s",
             "kernel_ms": kms, "n_samples": n, "n_phase": wl.laser.n_phase,
             "photon_bins": "256 log-spaced on [1e-3, 6720] m c^2",
+            "roofline": {"bound": "alu", "pipe": "fma",
+                         "achieved": PHOTON_FMA_OPS_PER_EVAL * evals / (kms * 1e-3) / 1e12,
+                         "peak": peak / 1e12, "unit": "Top/s",
+                         "frac": PHOTON_FMA_OPS_PER_EVAL * evals / peak / (kms * 1e-3),
+                         "evaluations": evals},
             "workload": "mc2p19_photon_qfp512"}
 
 
@@ -544,8 +568,14 @@ def bench_grad(dev, rank, steps=3, n=1 << 24):
         t_b += m.elapsed_time(b)
     t_f /= steps
     t_b /= steps
+    steps_total = n * wl.laser.n_phase
+    peak = _fma_peak(dev)
     return {"metric": "grad evals/s", "value": n / ((t_f + t_b) * 1e-3), "unit": "samples/s",
-            "forward_ms": t_f, "adjoint_ms": t_b, "n_samples": n, "n_phase": 512,
+            "forward_ms": t_f, "adjoint_ms": t_b, "n_samples": n, "n_phase": wl.laser.n_phase,
+            "roofline": {"kernel": "k_grad<float>", "bound": "alu", "pipe": "fma",
+                         "achieved": GRAD_FMA_OPS_PER_STEP * steps_total / (t_b * 1e-3) / 1e12,
+                         "peak": peak / 1e12, "unit": "Top/s",
+                         "frac": GRAD_FMA_OPS_PER_STEP * steps_total / peak / (t_b * 1e-3)},
             "workload": wl.name}
 
 
