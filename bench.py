@@ -627,7 +627,7 @@ def main():
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
     clk.start()
-    time.sleep(0.3)
+    time.sleep(1.0)            # nvidia-smi starts before the timed steps
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -684,7 +684,7 @@ def main():
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(k2 + 1)]
         clk2 = ClockSampler(local)
         clk2.start()
-        time.sleep(0.3)
+        time.sleep(1.0)            # nvidia-smi starts before the timed steps
         torch.cuda.synchronize()
         evs[0].record(stream)
         for k in range(k2):
