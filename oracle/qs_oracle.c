@@ -24,7 +24,11 @@
  *   qso_qfp_integrate    pinned (classical limit == Eq. 3; variance
  *                        transport closed form; library ODE solve)
  *   qso_eval / qso_scatter  pinned (Table 1 / Table 2 closed forms,
- *                        zero intensity, weight conservation, symmetries)
+ *                        zero intensity, weight conservation, symmetries;
+ *                        the moment finalize against the weighted sample
+ *                        moments of the realised energies and angles of
+ *                        2^20 samples; Eq. 8 against the paper's printed
+ *                        coefficient and a log-linear fit of its scaling)
  *   qso_cycle_factors    pinned (small-chi limits and large-chi tails in
  *                        closed form; adaptive quadrature; the cycle mean
  *                        of the exact quantum-synchrotron power)

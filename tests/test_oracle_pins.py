@@ -898,6 +898,107 @@ def test_weight_conservation_and_consistency():
     assert abs(m["div_x"] ** 2 / ((w * (thx0 ** 2 + s["theta_e"] ** 2)).sum() / W) - 1) < 1e-12
 
 
+def _mc_finalize_case(n, seed):
+    """A quantum beam whose energy spread is mostly the per-electron Fokker-
+    Planck variance and whose x divergence is mostly the Eq. 8 broadening,
+    with the initial angles still a visible share, and uneven weights."""
+    L = I.Laser(lambda_um=0.8, a0=40.0, w0_um=4.0, tau_fs=30.0, model=I.MODEL_QFP, dx_um=1.0,
+                delay_fs=10.0, n_phase=16)
+    B = I.Beam(gamma_mean=6000.0, rel_spread=0.002, sigma_x_um=1.0, sigma_y_um=1.0,
+               sigma_z_um=5.0, div_rad=6e-3)
+    bins = I.Bins(n_bins=64, lo=0.0, hi=9000.0)
+    xi = [x.astype(np.float64) for x in I.sample_streams(n, seed)]
+    w = I.rng(seed + 1).uniform(0.25, 1.75, n)
+    return L, B, bins, xi, w
+
+
+@pytest.mark.slow
+def test_moment_finalize_vs_realised_monte_carlo():
+    """The whole-beam moments against the weighted sample moments of the
+    REALISED per-electron outcomes over 2^20 samples (Sec. 1 observables,
+    Eq. 8): the law-of-total-variance spread must equal the spread of the
+    realised energies gamma_out = mu + sqrt(V) xi7, and div_x / div_y the rms
+    of the realised angles theta_x = theta_x0 + theta_e xi6 and theta_y.  The
+    expectations and the Monte Carlo noise are computed here in numpy from
+    the per-sample records; the moment struct is only the thing checked.
+    The case is chosen so that dropping <V> from the spread, dropping either
+    term of div_x, or putting theta_e on the y axis each misses by many
+    standard deviations."""
+    n = 1 << 20
+    L, B, bins, xi, w = _mc_finalize_case(n, seed=0x2308)
+    m = oracle.scatter(L, B, bins, xi, w)["moments"]
+    s = oracle.evaluate(L, B, bins, xi)
+    W = w.sum()
+    g, mu, V = s["gamma_out"], s["mu"], s["V"]
+    # realised sample moments
+    mean_r = (w * g).sum() / W
+    var_r = (w * (g - mean_r) ** 2).sum() / W
+    thx2_r = (w * s["theta_x"] ** 2).sum() / W
+    thy2_r = (w * s["theta_y"] ** 2).sum() / W
+    # the noise of each estimator over xi6, xi7 given the samples' mu, V,
+    # theta_x0, theta_e: mean_r - <mu> = sum w sqrt(V) xi7 / W;
+    # var_r - [<(mu - m)^2> + <V>] = sum w [2 (mu - m) sqrt(V) xi7 + V (xi7^2 - 1)] / W
+    # (+ O(1/N)); thx2_r - <thx0^2 + te^2> = sum w [2 thx0 te xi6 + te^2 (xi6^2 - 1)] / W
+    mu_m = (w * mu).sum() / W
+    d = mu - mu_m
+    sd_mean = math.sqrt((w ** 2 * V).sum()) / W
+    sd_var = math.sqrt((w ** 2 * (4 * d * d * V + 2 * V * V)).sum()) / W
+    thx0 = B.div_rad * xi[4]
+    te = s["theta_e"]
+    sd_thx = math.sqrt((w ** 2 * (4 * thx0 ** 2 * te ** 2 + 2 * te ** 4)).sum()) / W
+    z = 5.0
+    print("mean", m["mean"], mean_r, "spread^2", m["spread"] ** 2, var_r, "+-", sd_var,
+          "div_x^2", m["div_x"] ** 2, thx2_r, "+-", sd_thx)
+    assert abs(m["W"] - W) <= 1e-9 * W
+    assert abs(m["mean"] - mean_r) <= z * sd_mean
+    assert abs(m["spread"] ** 2 - var_r) <= z * sd_var + 1e-6 * var_r
+    assert abs(m["div_x"] ** 2 - thx2_r) <= z * sd_thx
+    # the y angle carries no broadening: exact
+    assert abs(m["div_y"] ** 2 / thy2_r - 1) <= 1e-12
+    assert abs(m["div"] ** 2 / (thx2_r + thy2_r) - 1) <= 10 * z * sd_thx / thx2_r
+    assert abs(m["rel_spread"] - m["spread"] / m["mean"]) <= 1e-15 * m["rel_spread"]
+    # the case discriminates: each plausible slip misses by > 20 sigma
+    assert abs((w * d * d).sum() / W - var_r) > 20 * sd_var          # <V> dropped
+    assert abs((w * V).sum() / W - var_r) > 20 * sd_var              # spread of mu dropped
+    assert abs((w * thx0 ** 2).sum() / W - thx2_r) > 20 * sd_thx      # theta_e dropped
+    assert abs((w * te ** 2).sum() / W - thx2_r) > 20 * sd_thx        # theta_x0 dropped
+    assert (w * te ** 2).sum() / W > 1e-3 * thy2_r                   # theta_e on y (exact check)
+
+
+def test_eq8_coefficient_and_scaling():
+    """Eq. 8: theta_e = kappa sqrt(2/pi) a sigma / gamma^2 per electron, with
+    a -> a_eff, sigma -> sqrt(V), gamma -> mu.  The coefficient is the one the
+    paper prints (tests/golden); a least-squares fit of log theta_e on
+    log a_eff, log sqrt(V) and log mu over a beam with wide ranges of all
+    three must give exponents 1, 1, -2 and the printed coefficient, and the
+    prefactor kappa must scale theta_e linearly."""
+    c_paper = paper_values()["eq8_theta_e_coefficient"]["value"]
+    assert abs(c_paper - math.sqrt(2 / math.pi)) < 1e-15
+    n = 4096
+    L = I.Laser(lambda_um=0.8, a0=60.0, w0_um=3.0, tau_fs=30.0, model=I.MODEL_QFP, n_phase=24)
+    B = I.Beam(gamma_mean=5000.0, rel_spread=0.3, sigma_x_um=3.0, sigma_y_um=3.0,
+               sigma_z_um=20.0, div_rad=1e-3)
+    xi = [x.astype(np.float64) for x in I.sample_streams(n, 77)]
+    s = oracle.evaluate(L, B, None, xi)
+    ok = s["V"] > 0
+    assert ok.mean() > 0.99
+    a, sv, mu, te = s["aeff"][ok], np.sqrt(s["V"][ok]), s["mu"][ok], s["theta_e"][ok]
+    # the three regressors must vary independently over this beam
+    X = np.column_stack([np.ones(a.size), np.log(a), np.log(sv), np.log(mu)])
+    assert np.linalg.cond(X[:, 1:] - X[:, 1:].mean(0)) < 1e3
+    coef, *_ = np.linalg.lstsq(X, np.log(te), rcond=None)
+    print("log-fit coefficients:", coef, "exp(c0):", math.exp(coef[0]))
+    assert np.allclose(coef[1:], [1.0, 1.0, -2.0], atol=1e-9)
+    assert abs(math.exp(coef[0]) / c_paper - 1) < 1e-9
+    L2 = I.Laser(**{**L.__dict__, "div_prefactor": 2.5})
+    s2 = oracle.evaluate(L2, B, None, xi)
+    np.testing.assert_array_equal(s2["mu"], s["mu"])
+    np.testing.assert_allclose(s2["theta_e"], 2.5 * s["theta_e"], rtol=1e-15)
+    # the classical model has no broadening
+    s3 = oracle.evaluate(I.Laser(**{**L.__dict__, "model": I.MODEL_LL}), B, None, xi)
+    assert np.all(s3["theta_e"] == 0)
+
+
 def test_transverse_offset_mirror_symmetry():
     """+dx on a sample set equals -dx on its x-mirrored set, bit for bit;
     the divergence map mirrors in theta_x."""
