@@ -39,15 +39,25 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 8
+#define QS_VERSION 9
 
+/*
+ * Status codes.  QS_ERR_NONFINITE is returned only when the caller asks for
+ * the check (QS_EXEC_CHECK_FINITE in qs_exec.flags): the outputs are then
+ * complete and valid for the samples that entered them, and the status says
+ * that moments.nonfinite > 0 samples were left out.  QS_ERR_TIMEOUT is
+ * reserved: no kernel of this version waits on another CTA, stream or
+ * device, so no entry point returns it.
+ */
 typedef enum {
     QS_OK = 0,
     QS_ERR_INVALID_ARG = 1,   /* a descriptor or pointer failed validation   */
     QS_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed        */
     QS_ERR_WORKSPACE = 3,     /* workspace missing, too small or misaligned  */
     QS_ERR_UNSUPPORTED = 4,   /* valid request this build does not support   */
-    QS_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up          */
+    QS_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait gave up */
+    QS_ERR_NONFINITE = 6      /* samples were excluded as non-finite (checked
+                                 on request, outputs written)                */
 } qs_status;
 
 typedef enum { QS_ENV_GAUSS = 0, QS_ENV_SIN2 = 1 } qs_envelope;
@@ -200,14 +210,25 @@ typedef struct qs_moments {
  *                     multiple of 32.
  *   tile              samples per work item of qs_scatter_batch (0 = 2048;
  *                     a multiple of 64, at most 1<<20); ignored elsewhere.
+ *   flags             QS_EXEC_CHECK_FINITE: after the outputs are written
+ *                     the call waits for its stream, reads the excluded-sample
+ *                     count(s) and returns QS_ERR_NONFINITE if any sample (of
+ *                     any shot) was left out as non-finite or negatively
+ *                     weighted.  The call is then synchronous; requested while
+ *                     the stream is being captured into a graph it returns
+ *                     QS_ERR_UNSUPPORTED before any launch.  Honoured by
+ *                     qs_scatter, qs_scatter_noalloc, qs_scatter_host and
+ *                     qs_scatter_batch; other bits are invalid.
  *   ev_start, ev_stop optional cudaEvent_t handles (as void*): when set, they
  *                     are recorded on the call's stream immediately before and
  *                     after the evaluation kernel, so a caller can time that
  *                     kernel alone.  The caller creates and owns the events.
  */
+#define QS_EXEC_CHECK_FINITE 1
+
 typedef struct qs_exec {
     int32_t precision, weight_frac_bits, block, grid;
-    int32_t tile, reserved;
+    int32_t tile, flags;
     void* ev_start;
     void* ev_stop;
 } qs_exec;
@@ -300,10 +321,12 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *                 device; an invalid shot, or one with n_phase > max_phase,
  *                 gets W = 0 and nonfinite = -1 and no work)
  *   d_offsets     n_shots + 1 non-decreasing int64 (device), offsets[0] >= 0,
- *                 offsets[n_shots] <= samples->n (checked on the device: a
- *                 shot whose range is invalid is treated as invalid); or
- *                 NULL: every shot integrates ALL samples (a parameter sweep,
- *                 e.g. over the delay, on one sampled beam)
+ *                 offsets[n_shots] <= samples->n, checked on the device: a
+ *                 shot whose range leaves [0, samples->n] is invalid, and
+ *                 offsets that decrease anywhere make EVERY shot invalid
+ *                 (no shot then does any work); or NULL: every shot
+ *                 integrates ALL samples (a parameter sweep, e.g. over the
+ *                 delay, on one sampled beam)
  *   samples       the concatenated streams (as for qs_scatter)
  *   bins          energy spectrum only (n_tx = n_aeff = 0, no smoothing);
  *                 shared bin count, range per shot from d_ranges if not NULL
@@ -488,10 +511,12 @@ int32_t qs_analytic_ll_spectrum(const qs_laser* laser, const qs_geometry* geom, 
 /*
  * qs_unit_rates: throughput probe of the pipes the kernels are bound by (no
  * counterpart in the paper; it supplies the roofline denominators).
- * rates[0..6] (host): FP32 FMA, MUFU lg2, ex2, rcp (the .approx forms the
+ * rates[0..7] (host): FP32 FMA, MUFU lg2, ex2, rcp (the .approx forms the
  * FP32 path issues), FP64 FMA, each in operations per SM per clock at the
  * device's maximum SM clock (a throttled clock reads as a lower rate), then
- * the SM count and that clock in MHz.  d_scratch: device memory of
+ * the SM count and that clock in MHz, then the packed f32x2 FMA
+ * (fma.rn.f32x2, the form the FP32 phase integration issues) in
+ * lane-operations (two per instruction) per SM per clock.  d_scratch: device memory of
  * qs_unit_rates_scratch_bytes() bytes.  Runs a few milliseconds of
  * dependent-chain kernels on `stream` and waits for them.
  * Errors: QS_ERR_INVALID_ARG, QS_ERR_WORKSPACE, QS_ERR_CUDA.

@@ -19,8 +19,10 @@ from . import inputs as _inputs
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libqscatter.so")
 
-QS_OK, QS_ERR_INVALID_ARG, QS_ERR_CUDA, QS_ERR_WORKSPACE, QS_ERR_UNSUPPORTED, QS_ERR_TIMEOUT = range(6)
+(QS_OK, QS_ERR_INVALID_ARG, QS_ERR_CUDA, QS_ERR_WORKSPACE, QS_ERR_UNSUPPORTED, QS_ERR_TIMEOUT,
+ QS_ERR_NONFINITE) = range(7)
 QS_F32, QS_F64 = 0, 1
+QS_EXEC_CHECK_FINITE = 1
 
 
 class QsError(RuntimeError):
@@ -70,7 +72,7 @@ class qs_moments(C.Structure):
 class qs_exec(C.Structure):
     _fields_ = [("precision", C.c_int32), ("weight_frac_bits", C.c_int32),
                 ("block", C.c_int32), ("grid", C.c_int32), ("tile", C.c_int32),
-                ("reserved", C.c_int32), ("ev_start", C.c_void_p), ("ev_stop", C.c_void_p)]
+                ("flags", C.c_int32), ("ev_start", C.c_void_p), ("ev_stop", C.c_void_p)]
 
 
 class qs_geometry(C.Structure):
@@ -198,11 +200,12 @@ def _event_handle(ev):
 
 
 def make_exec(precision="f32", weight_frac_bits=0, block=0, grid=0, events=None,
-              tile=0) -> qs_exec:
+              tile=0, check_finite=False) -> qs_exec:
     prec = QS_F64 if precision in ("f64", QS_F64, torch.float64) else QS_F32
     e0, e1 = (None, None) if events is None else (_event_handle(events[0]),
                                                   _event_handle(events[1]))
-    return qs_exec(prec, int(weight_frac_bits), int(block), int(grid), int(tile), 0, e0, e1)
+    flags = QS_EXEC_CHECK_FINITE if check_finite else 0
+    return qs_exec(prec, int(weight_frac_bits), int(block), int(grid), int(tile), flags, e0, e1)
 
 
 def make_samples(xi, w=None) -> tuple[qs_samples, list]:
@@ -296,16 +299,20 @@ def _ptr_or_none(t):
 
 
 def qs_scatter(laser, beam, xi, bins, w=None, precision="f32", out: Outputs | None = None,
-               block=0, grid=0, weight_frac_bits=0, stream=None, kernel_events=None) -> Outputs:
+               block=0, grid=0, weight_frac_bits=0, stream=None, kernel_events=None,
+               check_finite=False) -> Outputs:
     """Integrate the beam phase space: spectra + moments (asynchronous).
 
     ``kernel_events``: optional (start, stop) torch.cuda.Event pair recorded
-    around the evaluation kernel on the call's stream."""
+    around the evaluation kernel on the call's stream.  ``check_finite``:
+    wait for the call and raise QsError (QS_ERR_NONFINITE) if samples were
+    excluded as non-finite (the outputs are written all the same)."""
     s, keep = make_samples(xi, w)
     if out is None:
         out = Outputs(bins, s.n, keep[0].device, precision, block, grid)
     L, B, Bn = make_laser(laser), make_beam(beam), make_bins(bins)
-    E = make_exec(precision, weight_frac_bits, block, grid, kernel_events)
+    E = make_exec(precision, weight_frac_bits, block, grid, kernel_events,
+                  check_finite=check_finite)
     st = _lib().qs_scatter(C.byref(L), C.byref(B), C.byref(s), C.byref(Bn), C.byref(E),
                            _ptr_or_none(out.spectrum), _ptr_or_none(out.divmap),
                            _ptr_or_none(out.aeff_hist), _ptr_or_none(out.spec_smooth),
@@ -531,16 +538,16 @@ def qs_pw_reconstruct(hist, pw, out=None, stream=None) -> torch.Tensor:
 
 # ---- unit rates -----------------------------------------------------------
 
-UNIT_RATE_FIELDS = ("fma", "lg2", "ex2", "rcp", "dfma", "sms", "sm_max_mhz")
+UNIT_RATE_FIELDS = ("fma", "lg2", "ex2", "rcp", "dfma", "sms", "sm_max_mhz", "fma2")
 
 
 def unit_rates(stream=None) -> dict:
     """Measured operations per SM per clock of the FP32 FMA, MUFU lg2 / ex2 /
     rcp and FP64 FMA pipes (at the maximum SM clock), the SM count and that
-    clock (qs_unit_rates)."""
+    clock, and the packed f32x2 FMA in lane-operations (qs_unit_rates)."""
     nbytes = int(_lib().qs_unit_rates_scratch_bytes())
     scratch = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
-    out = (C.c_double * 7)()
+    out = (C.c_double * 8)()
     st = _lib().qs_unit_rates(out, scratch.data_ptr(), nbytes, _stream_ptr(stream))
     _check(st, "qs_unit_rates")
     return dict(zip(UNIT_RATE_FIELDS, list(out)))

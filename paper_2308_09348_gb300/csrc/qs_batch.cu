@@ -36,6 +36,7 @@ struct BatchArgs {
   unsigned long long* acc;      // [n_shots * (n_bins + 2)]
   double* partials;             // [tiles * kNumMom]
   unsigned long long* counter;  // work counter
+  int64_t max_tiles;            // tile slots in the workspace
   int32_t precision, pad;
 };
 
@@ -89,16 +90,25 @@ __global__ void k_btable(const BatchArgs a) {
     table_entry(p, j, static_cast<double*>(a.tables) + (size_t)s * a.max_phase);
 }
 
-// Exclusive prefix sum of tiles[0..n) in place, total in tiles[n].
+// Exclusive prefix sum of tiles[0..n) in place, total in tiles[n].  The
+// per-shot checks of k_bsetup see one shot's range only; here the offsets
+// are checked as a whole: if they decrease anywhere (shot ranges could then
+// overlap), or the tiles would exceed the workspace's slots, every shot is
+// made invalid and the total set to 0, so no shot does any work.
 __global__ void __launch_bounds__(1024) k_bscan(const BatchArgs a) {
   __shared__ int64_t part[1024];
+  __shared__ int s_bad;
   const int n = a.n_shots;
   const int per = (n + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
   int64_t s = 0;
-  for (int i = b0; i < b1; ++i) s += a.tiles[i];
+  int bad = 0;
+  for (int i = b0; i < b1; ++i) {
+    s += a.tiles[i];
+    if (a.offsets && a.offsets[i + 1] < a.offsets[i]) bad = 1;
+  }
   part[threadIdx.x] = s;
-  __syncthreads();
+  bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     int64_t run = 0;
     for (int t = 0; t < (int)blockDim.x; ++t) {
@@ -106,9 +116,17 @@ __global__ void __launch_bounds__(1024) k_bscan(const BatchArgs a) {
       part[t] = run;
       run += v;
     }
-    a.tiles[n] = run;
+    s_bad = bad || run > a.max_tiles;
+    a.tiles[n] = s_bad ? 0 : run;
   }
   __syncthreads();
+  if (s_bad) {
+    for (int i = b0; i < b1; ++i) {
+      a.shot[i].n = -1;
+      a.tiles[i] = 0;
+    }
+    return;
+  }
   int64_t run = part[threadIdx.x];
   for (int i = b0; i < b1; ++i) {
     const int64_t v = a.tiles[i];
@@ -340,15 +358,8 @@ int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaS
                       16;
   if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
   auto kern = k_batch<T, H>;
-  static bool attr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
-        cudaSuccess)
-      return cuda_fail();
-    attr[dev] = true;
-  }
+  static CtxMark smem_mark;
+  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return cuda_fail();
@@ -386,6 +397,8 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
+  const bool check = exec_check_finite(exec);
+  if (check && (st = sync_allowed(static_cast<cudaStream_t>(stream)))) return st;
   BatchPlan bp;
   if (!batch_plan(bp, n_shots, samples->n, bins, max_phase, prec, tile, d_offsets == nullptr))
     return QS_ERR_INVALID_ARG;
@@ -410,6 +423,7 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   a.acc = reinterpret_cast<unsigned long long*>(ws + bp.off_acc);
   a.partials = reinterpret_cast<double*>(ws + bp.off_part);
   a.counter = reinterpret_cast<unsigned long long*>(ws + bp.off_counter);
+  a.max_tiles = bp.max_tiles;
   a.precision = prec;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   // zero the work counter and the histogram accumulators
@@ -431,5 +445,7 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   if (st) return st;
   const int64_t thr = (int64_t)n_shots * 32;
   k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_moments);
-  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  return check ? nonfinite_status(&d_moments[0].nonfinite, n_shots, sizeof(qs_moments), cs)
+               : QS_OK;
 }

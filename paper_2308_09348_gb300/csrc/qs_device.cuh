@@ -878,10 +878,17 @@ __device__ __forceinline__ int aeff_bin(const Params& p, double a) {
   return p.n_aeff;
 }
 
-// FP32-path binning: energy index from the FP64 final energy (uniform bins:
-// one FP64 subtract and multiply; log bins: an FP32 base-2 logarithm), map
-// and a_eff indices in FP32.  Decisions differ from the FP64 path only for
-// values within the FP32 error of a bin edge.
+// FP32-path binning, all in FP32: the energy index from the realised energy
+// as a float pair (hi, lo) -- uniform bins t = ((hi - lo_edge) + lo) inv_w,
+// log bins t = lg2(hi + lo) log2_scale - log2_offset -- and the map and
+// a_eff indices.  Index error: uniform bins, the subtraction is exact when
+// hi lies within a factor 2 of lo_edge and otherwise rounds by half an ulp
+// of hi - lo_edge, the addition of lo and the product by inv_w (itself
+// rounded once) by half an ulp each, so |t - t_exact| <= 2^-23 t + |hi|
+// 2^-24 inv_w; log bins, the MUFU logarithm's error (2^-22 absolute in
+// lg2) times log2_scale.  A sample moves to a neighbouring bin only when
+// its exact t lies within that bound (plus the per-sample error of the
+// energy itself) of an integer; decisions otherwise equal the FP64 path's.
 __device__ __forceinline__ int energy_bin_f32(const Params& p, float gh, float gl) {
   if (!p.log_spaced) {
     const float tf = __fmul_rn(__fadd_rn(__fsub_rn(gh, p.f.lo), gl), p.f.inv_w);
@@ -1115,8 +1122,10 @@ __device__ __forceinline__ bool accumulate(const Params& p, const Sample& s, int
                                            int64_t naeff) {
   double* acc = A.a;
   const double w = p.weighted ? load_elem(p.w, i, p.dtype) : 1.0;
+  // every value that enters a sum or a bin must be finite
   const bool ok = isfinite(s.mu) && isfinite(s.V) && isfinite(s.gout) && isfinite(s.tx) &&
-                  isfinite(w) && w >= 0.0;
+                  isfinite(s.ty) && isfinite(s.aeff) && isfinite(s.gamma0) && isfinite(w) &&
+                  w >= 0.0;
   if (!ok) {
     acc[8] += 1.0;
     return false;
@@ -1161,8 +1170,10 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
                                              H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,
                                              int64_t naeff) {
   const float muf = s.mu_hi;
+  // every value that enters a sum or a bin must be finite
   const bool ok = isfinite(muf) && (!QFP || (isfinite(s.V) && isfinite(s.go_hi))) &&
-                  isfinite(s.tx) && isfinite(w) && w >= 0.f;
+                  isfinite(s.tx) && isfinite(s.ty) && isfinite(s.aeff) && isfinite(s.g0) &&
+                  isfinite(w) && w >= 0.f;
   if (!ok) {
     A.nonfinite = __fadd_rn(A.nonfinite, 1.f);
     return false;
@@ -1217,8 +1228,8 @@ __device__ __forceinline__ void accumulate4_ll(const Params& p, const SampleF (&
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 4; ++k)
-    ok = ok && isfinite(s[k].mu_hi) && isfinite(s[k].tx) &&
-         (!W || (isfinite(w[k]) && w[k] >= 0.f));
+    ok = ok && isfinite(s[k].mu_hi) && isfinite(s[k].tx) && isfinite(s[k].ty) &&
+         isfinite(s[k].aeff) && isfinite(s[k].g0) && (!W || (isfinite(w[k]) && w[k] >= 0.f));
   if (!ok) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)

@@ -527,15 +527,8 @@ int32_t launch_grad(const Params& p, int block, int sms, int grid_req, int gmax,
   const size_t smem = tab + (size_t)(block / 32) * kNumGrad * sizeof(double) +
                       (stage ? (size_t)p.n_bins * sizeof(float) : 0);
   auto kern = k_grad<T, QFP>;
-  static bool attr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
-        cudaSuccess)
-      return cuda_fail();
-    attr[dev] = true;
-  }
+  static CtxMark smem_mark;
+  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return cuda_fail();

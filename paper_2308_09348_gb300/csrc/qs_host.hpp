@@ -19,6 +19,15 @@ int32_t validate_bins(const qs_bins* b);
 int32_t validate_samples(const qs_samples* s);
 int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int* grid);
 int32_t exec_tile(const qs_exec* e, int* tile);
+// QS_EXEC_CHECK_FINITE requested?
+bool exec_check_finite(const qs_exec* e);
+// QS_OK unless `st` is being captured into a graph (QS_ERR_UNSUPPORTED):
+// a call that waits for its stream cannot be captured.
+int32_t sync_allowed(cudaStream_t st);
+// Waits for `st` after copying `count` excluded-sample counts (device
+// doubles `stride` bytes apart) to the host: QS_ERR_NONFINITE if any is > 0.
+int32_t nonfinite_status(const double* d_nonfinite, int64_t count, size_t stride,
+                         cudaStream_t st);
 void fill_params(Params& p, const qs_laser* L, const qs_beam* B, const qs_samples* S,
                  const qs_bins* b, int wbits);
 int32_t device_sms(int* sms);
@@ -48,6 +57,39 @@ int pick_grid(int occ_per_sm, int sms, int block, int grid_req, int64_t n, int g
 inline int32_t cuda_fail() {
   (void)cudaGetLastError();
   return QS_ERR_CUDA;
+}
+
+// The current device and a key of the current CUDA context, unique for the
+// life of the process (the driver's context id, plus one).  What a context
+// owns -- the module's __device__ arrays and their contents, kernel
+// attributes, streams and events -- is cached under this key, so that after
+// a cudaDeviceReset (which destroys the context and reloads the module in
+// the next one) the library rebuilds it instead of using stale addresses or
+// handles.  Makes the device's primary context current if the calling
+// thread has no context yet.
+int32_t current_context(int* dev, unsigned long long* key);
+
+// Per-device "done in this context" marks.
+struct CtxMark {
+  unsigned long long key[64] = {};
+  bool done(int dev, unsigned long long k) const { return key[dev] == k; }
+  void set(int dev, unsigned long long k) { key[dev] = k; }
+};
+
+// Raises kernel f's dynamic shared memory limit to `bytes`, once per
+// context (the attribute lives in the context's copy of the module).
+template <typename F>
+int32_t allow_smem(F f, CtxMark& mark, int bytes) {
+  int dev = 0;
+  unsigned long long key = 0;
+  if (int32_t st = current_context(&dev, &key)) return st;
+  if (!mark.done(dev, key)) {
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+        cudaSuccess)
+      return cuda_fail();
+    mark.set(dev, key);
+  }
+  return QS_OK;
 }
 
 }  // namespace detail

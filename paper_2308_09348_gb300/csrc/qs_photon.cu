@@ -391,22 +391,24 @@ __global__ void k_photon_final(int grid, int nb, int na, const double* __restric
 namespace {
 
 std::mutex g_ph_mu;
-bool g_ph_ready[64] = {};
+detail::CtxMark g_ph_ready;
 
-// The photon table, built on first use on this device (one launch on `st`
-// and a wait for it; not while `st` is being captured).
+// The photon table, built on first use in the device's current context (one
+// launch on `st` and a wait for it; not while `st` is being captured).  A
+// device reset discards it with the context; the next first use rebuilds it.
 int32_t photon_table(cudaStream_t st) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  unsigned long long key = 0;
+  if (int32_t e = detail::current_context(&dev, &key)) return e;
   std::lock_guard<std::mutex> lk(g_ph_mu);
-  if (g_ph_ready[dev]) return QS_OK;
+  if (g_ph_ready.done(dev, key)) return QS_OK;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return detail::cuda_fail();
   if (cap != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
   k_photon_setup<<<(kPhN + 255) / 256, 256, 0, st>>>();
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
     return detail::cuda_fail();
-  g_ph_ready[dev] = true;
+  g_ph_ready.set(dev, key);
   return QS_OK;
 }
 
@@ -435,15 +437,8 @@ int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_i
                       double* partials, cudaStream_t st, const qs_exec* ex) {
   int grid = *grid_io;
   auto kern = k_photon<T, VAR, ANG>;
-  static bool attr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             detail::kSmemLimit) != cudaSuccess)
-      return detail::cuda_fail();
-    attr[dev] = true;
-  }
+  static detail::CtxMark smem_mark;
+  if (int32_t e = detail::allow_smem(kern, smem_mark, detail::kSmemLimit)) return e;
   // persistent grid: the CTAs that fit at once (unless a grid was requested)
   if (!(ex && ex->grid > 0)) {
     int occ = 0, sms = 0;

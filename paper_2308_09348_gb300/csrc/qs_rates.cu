@@ -25,6 +25,25 @@ __global__ void k_rate_fma(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Packed f32x2 FMA (the instruction the FP32 phase integration issues):
+// eight independent float2 chains per thread, 16 steps unrolled; each
+// instruction is two lane-operations.
+__global__ void k_rate_fma2(float* out, int iters) {
+  float2 a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = make_float2(threadIdx.x * 1e-6f + k, k + 0.5f);
+  const float2 m = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = __ffma2_rn(a[k], m, c);
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k].x + a[k].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // OP: 0 lg2, 1 ex2, 2 rcp; each followed by one FADD to stay in range.
 template <int OP>
 __global__ void k_rate_mufu(float* out, int iters) {
@@ -65,7 +84,8 @@ __global__ void k_rate_dfma(double* out, int iters) {
 
 // rates[0..4]: FP32 FMA, lg2, ex2, rcp, FP64 FMA per SM per clock at the
 // device's maximum SM clock; rates[5]: the SM count; rates[6]: that clock in
-// MHz.  The kernels run on `stream` and are waited for; d_scratch: device
+// MHz; rates[7]: packed f32x2 FMA lane-operations (two per instruction) per
+// SM per clock.  The kernels run on `stream` and are waited for; d_scratch: device
 // memory of at least qs_unit_rates_scratch_bytes() bytes.
 extern "C" size_t qs_unit_rates_scratch_bytes(void) {
   int sms = 0;
@@ -113,6 +133,7 @@ extern "C" int32_t qs_unit_rates(double* rates, void* d_scratch, size_t scratch_
   timed([&](int it) { k_rate_mufu<1><<<blocks, threads, 0, st>>>(fo, it); }, 1000, 128.0, &rates[2]);
   timed([&](int it) { k_rate_mufu<2><<<blocks, threads, 0, st>>>(fo, it); }, 1000, 128.0, &rates[3]);
   timed([&](int it) { k_rate_dfma<<<blocks, threads, 0, st>>>(dd, it); }, 100, 64.0, &rates[4]);
+  timed([&](int it) { k_rate_fma2<<<blocks, threads, 0, st>>>(fo, it); }, 2000, 256.0, &rates[7]);
   rates[5] = sms;
   rates[6] = (double)khz / 1e3;
   cudaEventDestroy(a);

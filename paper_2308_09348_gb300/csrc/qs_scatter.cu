@@ -13,10 +13,13 @@
 #include "qs_host.hpp"
 #include "qs_derive.cuh"
 
+#include <cuda.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 namespace qs {
 
@@ -58,6 +61,28 @@ int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int*
   if (*wbits < 0 || *wbits > 52) return QS_ERR_INVALID_ARG;
   if (*block < 32 || *block > 512 || (*block % 32)) return QS_ERR_INVALID_ARG;
   if (*grid < 0) return QS_ERR_INVALID_ARG;
+  if (e && (e->flags & ~QS_EXEC_CHECK_FINITE)) return QS_ERR_INVALID_ARG;
+  return QS_OK;
+}
+
+bool exec_check_finite(const qs_exec* e) { return e && (e->flags & QS_EXEC_CHECK_FINITE); }
+
+int32_t sync_allowed(cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cuda_fail();
+  return cap == cudaStreamCaptureStatusNone ? QS_OK : QS_ERR_UNSUPPORTED;
+}
+
+int32_t nonfinite_status(const double* d_nonfinite, int64_t count, size_t stride,
+                         cudaStream_t st) {
+  std::vector<double> h((size_t)(count > 0 ? count : 0));
+  if (count > 0 && cudaMemcpy2DAsync(h.data(), sizeof(double), d_nonfinite, stride,
+                                     sizeof(double), (size_t)count, cudaMemcpyDeviceToHost,
+                                     st) != cudaSuccess)
+    return cuda_fail();
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail();
+  for (double v : h)
+    if (v > 0.0) return QS_ERR_NONFINITE;
   return QS_OK;
 }
 
@@ -90,6 +115,45 @@ int32_t device_sms(int* sms) {
     g_dev[dev].init = true;
   }
   *sms = g_dev[dev].sms;
+  return QS_OK;
+}
+
+// Driver entry points for the context key, resolved once through the
+// runtime (no link-time dependency on the driver library).
+namespace {
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+std::once_flag g_ctx_once;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+}  // namespace
+
+int32_t current_context(int* dev, unsigned long long* key) {
+  std::call_once(g_ctx_once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f);
+    (void)cudaGetLastError();
+  });
+  if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= 64) return cuda_fail();
+  if (!g_ctx_get_current || !g_ctx_get_id) return QS_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return QS_ERR_CUDA;
+  if (!ctx) {
+    // no context on this thread yet: cudaSetDevice makes the device's
+    // primary context current
+    if (cudaSetDevice(*dev) != cudaSuccess) return cuda_fail();
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return QS_ERR_CUDA;
+  }
+  unsigned long long id = 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return QS_ERR_CUDA;
+  *key = id + 1;
   return QS_OK;
 }
 
@@ -541,23 +605,25 @@ __global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
 }
 
 std::mutex g_cyc_mu;
-bool g_cyc_ready[64] = {};
+CtxMark g_cyc_ready;
 
-// Points p at the cycle tables, building them on first use on this device
-// (one launch on `st`, then a wait for it; not allowed while `st` is being
-// captured into a graph).
+// Points p at the cycle tables, building them on first use in the device's
+// current context (one launch on `st`, then a wait for it; not allowed while
+// `st` is being captured into a graph).  A device reset discards the tables
+// with the context, so the first use in the next context builds them again.
 int32_t cycle_tables(Params& p, cudaStream_t st) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  unsigned long long key = 0;
+  if (int32_t e = current_context(&dev, &key)) return e;
   std::lock_guard<std::mutex> lk(g_cyc_mu);
-  if (!g_cyc_ready[dev]) {
+  if (!g_cyc_ready.done(dev, key)) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cuda_fail();
     if (cap != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
     k_cycle_setup<<<1, kCycGL / 2, 0, st>>>();
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
       return cuda_fail();
-    g_cyc_ready[dev] = true;
+    g_cyc_ready.set(dev, key);
   }
   void *gl = nullptr, *a = nullptr;
   if (cudaGetSymbolAddress(&gl, g_cyc_gl) != cudaSuccess ||
@@ -574,16 +640,9 @@ template <typename T, bool QFP, int VAR>
 int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
                     const qs_sample_out& o) {
   auto kern = k_eval<T, QFP, VAR>;
-  static bool attr[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMaxPhase * (int)sizeof(float4) +
-                                 kCycN * (int)sizeof(float4)) != cudaSuccess)
-      return cuda_fail();
-    attr[dev] = true;
-  }
+  static CtxMark smem_mark;
+  if (int32_t e = allow_smem(kern, smem_mark, kMaxPhase * (int)sizeof(float4) +
+                                 kCycN * (int)sizeof(float4))) return e;
   kern<<<grid, 256, tb, st>>>(p, o);
   return QS_OK;
 }
@@ -592,15 +651,8 @@ template <typename T, typename H, bool QFP, bool SHIST, int VAR = 0>
 int32_t launch_scatter_t(const Params& p, int block, size_t smem, int sms, int grid_req, int gmax,
                          cudaStream_t st, int* grid_out, const qs_exec* ex) {
   auto kern = k_scatter<T, H, QFP, SHIST, VAR>;
-  static bool attr_set[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
-        cudaSuccess)
-      return cuda_fail();
-    attr_set[dev] = true;
-  }
+  static CtxMark smem_mark;
+  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return cuda_fail();
@@ -660,6 +712,7 @@ extern "C" const char* qs_status_string(int32_t s) {
     case QS_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
     case QS_ERR_UNSUPPORTED: return "unsupported";
     case QS_ERR_TIMEOUT: return "device-side wait timed out";
+    case QS_ERR_NONFINITE: return "samples excluded as non-finite (outputs written)";
     default: return "unknown status";
   }
 }
@@ -695,6 +748,9 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   make_plan(pl, bins, block, grid, sms);
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < pl.ws_bytes)
     return QS_ERR_WORKSPACE;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const bool check = exec_check_finite(exec);
+  if (check && (st = sync_allowed(cs))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
   const bool cells = qfp || (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
   const int kblock = scatter_block(exec, block, prec, qfp, laser->variant);
@@ -711,7 +767,6 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.partials = reinterpret_cast<double*>(ws + pl.off_part);
   p.hist_in_smem = sm.hist ? 1 : 0;
   p.smooth_in_smem = sm.smooth ? 1 : 0;
-  cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
 
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return cuda_fail();
@@ -723,7 +778,8 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   if (st) return st;
   k_finalize<<<1, 1024, 0, cs>>>(p, g, d_spectrum, d_divmap, d_aeff_hist, d_spec_smooth,
                                  d_moments);
-  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  return check ? nonfinite_status(&d_moments->nonfinite, 1, sizeof(qs_moments), cs) : QS_OK;
 }
 
 extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
@@ -789,19 +845,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[QS_NOALLOC_SCRA
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};
+CtxMark g_noalloc_mark;
 
 // Device address of g_noalloc_scratch on the current device.  In host code
 // the array's name is only a stand-in for the symbol, never a device
-// address, so it is looked up once per device with that device current.
+// address, so it is looked up with the device current: once per device, and
+// again when the device's context has changed (after a cudaDeviceReset the
+// module, and the array with it, is loaded afresh in the new context).
 int32_t noalloc_scratch(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QS_ERR_CUDA;
+  unsigned long long key = 0;
+  if (int32_t e = current_context(&dev, &key)) return e;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_mark.done(dev, key)) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
-      return QS_ERR_CUDA;
+      return cuda_fail();
     g_noalloc_ptr[dev] = p;
+    g_noalloc_mark.set(dev, key);
   }
   *out = g_noalloc_ptr[dev];
   return QS_OK;
@@ -837,24 +898,28 @@ namespace qs {
 namespace {
 
 struct HostPipe {
-  bool init = false;
+  unsigned long long key = 0;      // context the stream and events belong to
   cudaStream_t copy = nullptr;
   cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
 };
 std::mutex g_pipe_mu;
 HostPipe g_pipe[64];
 
+// The device's copy stream and events, created in the current context (a
+// device reset destroys them with their context; the next call creates new
+// ones).
 int32_t host_pipe(HostPipe** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail();
+  unsigned long long key = 0;
+  if (int32_t e = current_context(&dev, &key)) return e;
   std::lock_guard<std::mutex> lk(g_pipe_mu);
   HostPipe& hp = g_pipe[dev];
-  if (!hp.init) {
+  if (hp.key != key) {
     if (cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail();
     cudaEvent_t* evs[5] = {&hp.start, &hp.copied[0], &hp.copied[1], &hp.consumed[0], &hp.consumed[1]};
     for (cudaEvent_t* e : evs)
       if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return cuda_fail();
-    hp.init = true;
+    hp.key = key;
   }
   *out = &hp;
   return QS_OK;
@@ -953,6 +1018,8 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   if (!host_plan(hp, bins, block, grid, sms, h_samples, chunk)) return QS_ERR_INVALID_ARG;
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < hp.bytes)
     return QS_ERR_WORKSPACE;
+  const bool check = exec_check_finite(exec);
+  if (check && (st = sync_allowed(static_cast<cudaStream_t>(stream)))) return st;
   HostPipe* pipe = nullptr;
   if ((st = host_pipe(&pipe))) return st;
   const bool qfp = laser->model == QS_MODEL_QFP;
@@ -1036,5 +1103,9 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   for (const Out& o : outs)
     if (o.n && cudaMemcpyAsync(o.h, o.d, o.n, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
       return cuda_fail();
+  if (check) {
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return cuda_fail();
+    if (h_moments->nonfinite > 0.0) return QS_ERR_NONFINITE;
+  }
   return QS_OK;
 }

@@ -39,8 +39,8 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.qs_version() == 8
-    for s in range(6):
+    assert lib.qs_version() == 9
+    for s in range(7):
         assert lib.qs_status_string(s)
     assert lib.qs_status_string(99) == b"unknown status"
 
@@ -93,7 +93,8 @@ def test_host_validation_rejects_bad_descriptors(lib):
     assert _call(lib, samples=B.qs_samples(10, xi, None, 1, 0)) == B.QS_ERR_INVALID_ARG
     # exec options
     for e in (B.qs_exec(3, 0, 0, 0), B.qs_exec(0, 60, 0, 0), B.qs_exec(0, 0, 48, 0),
-              B.qs_exec(0, 0, 1024, 0), B.qs_exec(0, 0, 0, -1)):
+              B.qs_exec(0, 0, 1024, 0), B.qs_exec(0, 0, 0, -1),
+              B.qs_exec(0, 0, 0, 0, 0, 2), B.qs_exec(0, 0, 0, 0, 0, -1)):
         assert _call(lib, exe=e) == B.QS_ERR_INVALID_ARG
     # missing moments output
     assert _call(lib, moments=None) == B.QS_ERR_INVALID_ARG

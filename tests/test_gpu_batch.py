@@ -93,6 +93,32 @@ def test_batch_matches_oracle_f64():
         assert np.abs(spectra[s] - ref["spectrum"]).sum() <= 1e-4 * (o1 - o0)
 
 
+def test_batch_matches_oracle_f32_512_cells():
+    """FP32 batch at the benchmarked 512 phase cells against the oracle
+    directly: moments within 1e-5; spectrum bins exact for every sample
+    farther than the FP32 path's error bound from an edge (L1 at most twice
+    the weight of the others)."""
+    from test_gpu_parity import away_from_edges, gout_bound
+    bw, counts, offsets, xi = _small_batch(n_shots=12, seed=16, n_phase=512,
+                                           log10_range=(1.0, 3.0))
+    bt, _, _ = _run_batch(bw, offsets, xi, "f32")
+    mom = bt.moments_dicts()
+    spectra = bt.spectra.cpu().numpy()
+    for s in range(12):
+        o0, o1 = int(offsets[s]), int(offsets[s + 1])
+        if o1 == o0:
+            continue
+        bins = I.Bins(n_bins=bw.bins.n_bins, lo=float(bw.ranges[s, 0]), hi=float(bw.ranges[s, 1]))
+        sub = [a[o0:o1].astype(np.float64) for a in xi]
+        ref = oracle.scatter(bw.lasers[s], bw.beams[s], bins, sub)
+        for k in ("W", "mean", "spread", "div_x", "div_y", "mean_aeff", "mean_gamma0"):
+            assert abs(mom[s][k] - ref["moments"][k]) <= 1e-5 * abs(ref["moments"][k]), (s, k)
+        rec = oracle.evaluate(bw.lasers[s], bw.beams[s], bins, sub)
+        near = ~away_from_edges(rec["gamma_out"], gout_bound(rec, "f32"), bins)
+        l1 = np.abs(spectra[s] - ref["spectrum"]).sum()
+        assert l1 <= 2.0 * near.sum(), (s, l1, int(near.sum()))
+
+
 def test_invalid_shot_is_flagged_and_others_unaffected():
     bw, counts, offsets, xi = _small_batch(n_shots=10, seed=7, log10_range=(2.0, 3.0))
     lasers = list(bw.lasers)
@@ -166,3 +192,31 @@ def test_delay_sweep_over_shared_samples(prec):
                                    rtol=MOM_RTOL[prec])
     # the sweep is symmetric in nothing in particular, but the spectra differ
     assert not torch.equal(bt.spectra[0], bt.spectra[4])
+
+
+def test_decreasing_offsets_invalidate_every_shot():
+    """Offsets that decrease anywhere ([0, N, 0, N, ...]: shot ranges that
+    overlap) make every shot invalid and no shot does any work, whatever the
+    per-shot checks alone would pass; a valid batch on the same workspace
+    afterwards is unaffected."""
+    n_shots = 8
+    bw = I.batch_shots(n_shots, seed=9, log10_range=(3.0, 3.5), n_phase=64, n_bins=64)
+    n = int(bw.offsets[-1])
+    xi = I.sample_streams(n, 909, dtype=np.float32)
+    xt = [torch.from_numpy(a).cuda() for a in xi]
+    bad = np.array([0, n] * (n_shots // 2) + [n], dtype=np.int64)
+    bt = B.Batch(bw.lasers, bw.beams, bad, bw.bins, n, ranges=bw.ranges, precision="f32")
+    bt.spectra.fill_(7.0)
+    bt.run(xt)
+    torch.cuda.synchronize()
+    m = bt.moments.cpu().numpy()
+    assert np.all(m[:, B.MOMENT_FIELDS.index("W")] == 0)
+    assert np.all(m[:, B.MOMENT_FIELDS.index("nonfinite")] == -1)
+    assert np.all(bt.spectra.cpu().numpy() == 0)
+    # the same descriptors with valid offsets, on the same workspace
+    bt.d_offsets = torch.as_tensor(bw.offsets, dtype=torch.int64).cuda()
+    bt.run(xt)
+    torch.cuda.synchronize()
+    m = bt.moments.cpu().numpy()
+    assert np.all(m[:, B.MOMENT_FIELDS.index("nonfinite")] == 0)
+    np.testing.assert_array_equal(m[:, 0], np.diff(bw.offsets).astype(float))

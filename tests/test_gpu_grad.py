@@ -57,11 +57,17 @@ def _gpu_grad(L, Bm, bins, xt, wt, dm, dS, prec):
 SCALE = np.array([20.0, 4.0, 1.0, 1.0, 10.0, 6000.0, 0.08, 1e-3])
 
 
-@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+# FP32 adjoint against the oracle's gradient, parameter-scaled, relative to
+# the largest component: measured ~5e-7 (FP32 tangents over 512 cells)
+GRAD_TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+@pytest.mark.parametrize("model,n_phase", [(I.MODEL_LL, 64), (I.MODEL_QFP, 64),
+                                           (I.MODEL_QFP, 512), (I.MODEL_QFP, 509)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_gradient_matches_oracle(model, prec):
+def test_gradient_matches_oracle(model, n_phase, prec):
     n = 3001
-    wl, L, Bm, bins, xi, w = _setup(n, model)
+    wl, L, Bm, bins, xi, w = _setup(n, model, n_phase=n_phase)
     xt, wt = _dev(xi, w)
     dm, dS = _upstream(bins.n_bins)
     g, out = _gpu_grad(L, Bm, bins, xt, wt, dm, dS, prec)
@@ -71,8 +77,7 @@ def test_gradient_matches_oracle(model, prec):
     gs, rs = g * SCALE, ref["grad"] * SCALE
     err = np.abs(gs - rs) / np.max(np.abs(rs))
     print(f"[{prec}, model {model}] scaled grad rel err per param:", err)
-    tol = 1e-10 if prec == "f64" else 2e-3
-    assert np.all(err <= tol), err
+    assert np.all(err <= GRAD_TOL[prec]), err
     # forward smoothed spectrum against the oracle
     S = out.spec_smooth.cpu().numpy()
     l1 = np.abs(S - ref["smooth"]).sum() / w.astype(np.float64).sum()
@@ -94,7 +99,7 @@ def test_fp32_gradient_with_a_spectrum_too_large_to_stage():
     gs, rs = g * SCALE, ref["grad"] * SCALE
     err = np.abs(gs - rs) / np.max(np.abs(rs))
     print("[f32, 9000 bins] scaled grad rel err per param:", err)
-    assert np.all(err <= 2e-3), err
+    assert np.all(err <= GRAD_TOL["f32"]), err
 
 
 def test_fp64_adjoint_vs_central_differences_of_gpu_forward():
@@ -129,12 +134,12 @@ def test_fp64_adjoint_vs_central_differences_of_gpu_forward():
 
 def test_fp32_adjoint_vs_central_differences_h1e4():
     """FP32 adjoint vs plain central differences (h = 1e-4 relative) of the
-    FP32 forward, common random numbers."""
+    FP32 forward, common random numbers, with the upstream gradient on the
+    moments and on the smoothed spectrum."""
     n = 1 << 16
     wl, L, Bm, bins, xi, w = _setup(n, I.MODEL_QFP, n_phase=128, weighted=False)
     xt, wt = _dev(xi, None)
     dm, dS = _upstream(bins.n_bins, seed=44)
-    dS[:] = 0.0     # moments only: the FD noise of the smoothed spectrum in FP32 is larger
     g, _ = _gpu_grad(L, Bm, bins, xt, wt, dm, dS, "f32")
     prob = F.Problem(L, Bm, bins, xt, None, "f32")
     theta = prob.theta_of()
@@ -142,7 +147,7 @@ def test_fp32_adjoint_vs_central_differences_h1e4():
     def loss(th):
         lz, bm = prob.descriptors(th)
         o = B.qs_scatter(lz, bm, xt, bins, precision="f32")
-        return float((o.moments.cpu().numpy() * dm).sum())
+        return float((o.moments.cpu().numpy() * dm).sum() + (o.spec_smooth.cpu().numpy() * dS).sum())
 
     errs = []
     for k in range(8):
@@ -153,7 +158,7 @@ def test_fp32_adjoint_vs_central_differences_h1e4():
         fd = (loss(tp) - loss(tm)) / (2 * h)
         errs.append(abs(g[k] - fd) * SCALE[k] / np.max(np.abs(g * SCALE)))
     print("fp32 adjoint vs FD, scaled rel err:", errs)
-    assert max(errs) <= 1e-2
+    assert max(errs) <= 1e-3
 
 
 def test_gradient_is_deterministic():

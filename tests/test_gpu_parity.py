@@ -511,6 +511,57 @@ def test_nonfinite_samples_are_excluded_and_counted():
     assert m["nonfinite"] == 2 and m["W"] == n - 2
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
+def test_nonfinite_y_angle_alone_is_excluded(prec, model):
+    """A sample whose only non-finite input is the y-angle variate is left
+    out of every output and counted, as any other non-finite sample (it
+    would otherwise make div_y and div NaN)."""
+    n = 1000
+    wl, L, xi = cfg2(n, model=model)
+    xi = [a.copy() for a in xi]
+    xi[5][[7, 600]] = np.nan
+    xi[4][[11]] = np.inf
+    xt, _ = dev(xi)
+    out = qs_scatter(L, wl.beam, xt, wl.bins, precision=prec)
+    m = out.moments_dict()
+    assert m["nonfinite"] == 3 and m["W"] == n - 3
+    assert all(math.isfinite(m[k]) for k in ("div_x", "div_y", "div", "mean", "spread"))
+    keep = np.ones(n, dtype=bool)
+    keep[[7, 600, 11]] = False
+    ref = oracle.scatter(L, wl.beam, wl.bins, [a[keep] for a in f64(xi)])
+    for k in ("mean", "spread", "div_x", "div_y"):
+        assert abs(m[k] / ref["moments"][k] - 1) <= MOM_TOL[prec], k
+
+
+def test_check_finite_flag_reports_excluded_samples():
+    """QS_EXEC_CHECK_FINITE: the call waits, writes every output and returns
+    QS_ERR_NONFINITE when samples were excluded; QS_OK otherwise; refused
+    (before any launch) on a stream that is being captured."""
+    n = 2000
+    wl, L, xi = cfg2(n)
+    xt, _ = dev(xi)
+    out = B.Outputs(wl.bins, n)
+    qs_scatter(L, wl.beam, xt, wl.bins, out=out, check_finite=True)      # clean: no error
+    clean = out.moments.clone()
+    bad = [a.copy() for a in xi]
+    bad[3][[5]] = np.nan
+    bt, _ = dev(bad)
+    with pytest.raises(QsError) as e:
+        qs_scatter(L, wl.beam, bt, wl.bins, out=out, check_finite=True)
+    assert e.value.status == B.QS_ERR_NONFINITE
+    m = out.moments_dict()                      # outputs written all the same
+    assert m["nonfinite"] == 1 and m["W"] == n - 1 and m["mean"] != 0.0
+    assert not torch.equal(out.moments, clean)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(QsError) as e2:
+        with torch.cuda.graph(g, stream=s):
+            qs_scatter(L, wl.beam, xt, wl.bins, out=out, check_finite=True, stream=s)
+    assert e2.value.status == B.QS_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+
+
 def test_workspace_too_small_is_rejected():
     wl, L, xi = cfg2(100)
     xt, _ = dev(xi)
@@ -603,6 +654,65 @@ def test_full_size_quantum_workload_sampled_parity():
     compare_samples(got, ref, "f32", wl.bins)
 
 
+@pytest.mark.slow
+def test_bench_workload_2p20_matches_oracle_at_the_stated_bars():
+    """The benchmarked configuration (FP32, QFP, 512 cells, 512 energy
+    bins, 128x128 map, 256 a_eff bins) on the first 2^20 samples of the bench
+    workload, against the oracle's per-sample records reduced by their plain
+    definitions: spectrum L1 <= 1e-4 of the total weight with no allowance
+    for samples near a bin edge, moments within 1e-5, the energy bin of every
+    sample farther than its error bound from an edge bit-exact (the fused
+    histogram is compared as a whole, the per-sample records element by
+    element)."""
+    import oracle_pool
+    n = 1 << 20
+    wl = I.full_qfp(n)
+    xi, _ = I.workload_inputs(wl, n)
+    xt, _ = dev(xi)
+    out = qs_scatter(wl.laser, wl.beam, xt, wl.bins, precision="f32")
+    rec = qs_eval_samples(wl.laser, wl.beam, xt, wl.bins, precision="f32")
+    torch.cuda.synchronize()
+    ref = oracle_pool.records(wl.laser, wl.beam, wl.bins, f64(xi))
+    bins = wl.bins
+    # the oracle's histogram and moments from its records (half-open bins,
+    # law of total variance, Eq. 8 term on x)
+    b = ref["bin"]
+    hist = np.bincount(b[(b >= 0) & (b < bins.n_bins)], minlength=bins.n_bins).astype(float)
+    under, over = float((b < 0).sum()), float((b >= bins.n_bins).sum())
+    mean = ref["mu"].mean()
+    spread = math.sqrt(((ref["mu"] - mean) ** 2).mean() + ref["V"].mean())
+    thx0 = wl.beam.div_rad * xi[4].astype(np.float64)
+    thy0 = wl.beam.div_rad * xi[5].astype(np.float64)
+    div_x = math.sqrt((thx0 ** 2 + ref["theta_e"] ** 2).mean())
+    div_y = math.sqrt((thy0 ** 2).mean())
+    expect = dict(W=float(n), mean=mean, spread=spread, rel_spread=spread / mean, div_x=div_x,
+                  div_y=div_y, div=math.hypot(div_x, div_y), mean_aeff=ref["aeff"].mean(),
+                  mean_gamma0=ref["gamma0"].mean())
+    m = out.moments_dict()
+    errs = {k: abs(m[k] / v - 1) for k, v in expect.items()}
+    spec = out.spectrum.cpu().numpy()
+    l1 = np.abs(spec - hist).sum() + abs(m["under"] - under) + abs(m["over"] - over)
+    print("moment rel errors:", errs, "spectrum L1/W:", l1 / n)
+    assert m["nonfinite"] == 0
+    for k, e in errs.items():
+        assert e <= MOM_TOL["f32"], (k, m[k], expect[k])
+    assert l1 <= 1e-4 * n, l1 / n
+    # divergence map and a_eff histogram at the same bar
+    ix, iy = ref["ix"], ref["iy"]
+    inmap = ix >= 0
+    dm = np.bincount((iy * bins.n_tx + ix)[inmap], minlength=bins.n_tx * bins.n_ty)
+    got_dm = out.divmap.cpu().numpy().reshape(-1)
+    assert np.abs(got_dm - dm).sum() + abs(m["map_out"] - (~inmap).sum()) <= 1e-4 * n
+    ah = np.bincount(ref["abin"][ref["abin"] < bins.n_aeff], minlength=bins.n_aeff)
+    assert np.abs(out.aeff_hist.cpu().numpy() - ah).sum() <= 1e-4 * n
+    # every sample farther than its error bound from an energy-bin edge lands
+    # in the oracle's bin
+    g = rec["bin"].cpu().numpy()
+    ok = away_from_edges(ref["gamma_out"], gout_bound(ref, "f32"), bins)
+    print("samples near an energy-bin edge:", int((~ok).sum()), "moved:", int((g != b).sum()))
+    np.testing.assert_array_equal(g[ok], b[ok])
+
+
 def test_unit_rates_probe():
     """The unit-rate probe reports plausible per-SM-per-clock rates."""
     r = B.unit_rates()
@@ -610,3 +720,6 @@ def test_unit_rates_probe():
     assert r["sms"] > 0 and r["sm_max_mhz"] > 0
     assert r["fma"] > 64 and r["lg2"] > 8 and r["ex2"] >= 0.9 * r["lg2"] and r["rcp"] > 8
     assert 0 < r["dfma"] < r["fma"]
+    # the packed f32x2 FMA, in lane-operations (two per instruction)
+    print("packed / scalar FMA lane rate:", r["fma2"] / r["fma"])
+    assert 0.5 * r["fma"] <= r["fma2"] <= 2.5 * r["fma"]
