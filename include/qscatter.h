@@ -328,11 +328,14 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *                 integrates ALL samples (a parameter sweep, e.g. over the
  *                 delay, on one sampled beam)
  *   samples       the concatenated streams (as for qs_scatter)
- *   bins          energy spectrum only (n_tx = n_aeff = 0, no smoothing);
- *                 shared bin count, range per shot from d_ranges if not NULL
- *                 (n_shots pairs {lo, hi}, device) else bins->lo/hi
+ *   bins          energy spectrum and, with smooth_sigma_bins > 0, the
+ *                 kernel-smoothed spectrum (n_tx = n_aeff = 0); shared bin
+ *                 count, range per shot from d_ranges if not NULL (n_shots
+ *                 pairs {lo, hi}, device) else bins->lo/hi
  *   max_phase     upper bound of the shots' n_phase (QFP), 1..4096
  *   d_spectra     n_shots x n_bins doubles (row per shot), or NULL if n_bins == 0
+ *   d_spec_smooth n_shots x n_bins doubles (row per shot) when
+ *                 smooth_sigma_bins > 0, else ignored (may be NULL)
  *   d_moments     n_shots qs_moments
  * The workspace size (qs_batch_workspace_bytes) depends on shared_samples:
  * nonzero for the sweep form (d_offsets == NULL), whose tile slots grow with
@@ -346,8 +349,9 @@ size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins*
 int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_beam* d_beams,
                          const int64_t* d_offsets, const qs_samples* samples,
                          const qs_bins* bins, const double* d_ranges, int32_t max_phase,
-                         const qs_exec* exec, double* d_spectra, qs_moments* d_moments,
-                         void* d_workspace, size_t ws_bytes, void* stream);
+                         const qs_exec* exec, double* d_spectra, double* d_spec_smooth,
+                         qs_moments* d_moments, void* d_workspace, size_t ws_bytes,
+                         void* stream);
 
 /*
  * Parameter order of qs_scatter_grad (the reconstruction use of Sec. 6):
@@ -380,6 +384,32 @@ int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam, const qs_sam
                         const qs_bins* bins, const qs_exec* exec, const qs_moments* d_moments,
                         const double* d_dL_dmoments, const double* d_dL_dsmooth,
                         double* d_grad8, void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * qs_scatter_grad_batch: qs_scatter_grad for every shot of a batch at once
+ * (the reconstruction of Sec. 6 over many shots: a gradient fit of each
+ * shot's parameters), over the same persistent (shot, tile) schedule as
+ * qs_scatter_batch.  Arguments as for qs_scatter_batch (the same workspace,
+ * qs_batch_workspace_bytes, serves both; its forward results are not
+ * needed), plus, per shot s, in device memory:
+ *   d_moments     n_shots forward qs_moments (from qs_scatter_batch)
+ *   d_dL_dmoments n_shots x 13 doubles, dL/d(each qs_moments field) of shot s
+ *                 in row s (W, under, over, map_out, nonfinite ignored)
+ *   d_dL_dsmooth  n_shots x n_bins doubles, dL/d(smoothed spectrum) of shot
+ *                 s in row s, or NULL
+ *   d_grad        n_shots x QS_NUM_GRAD doubles, written (not accumulated),
+ *                 row s the gradient with respect to shot s's parameters
+ * Shot s's gradient equals qs_scatter_grad's for that shot alone, up to the
+ * order of the reduction (tiles in order, then summed per shot); repeated
+ * calls are bit-identical.  Invalid shots (as flagged by qs_scatter_batch)
+ * get zeros.  Model variant 0 only.
+ */
+int32_t qs_scatter_grad_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_beam* d_beams,
+                              const int64_t* d_offsets, const qs_samples* samples,
+                              const qs_bins* bins, const double* d_ranges, int32_t max_phase,
+                              const qs_exec* exec, const qs_moments* d_moments,
+                              const double* d_dL_dmoments, const double* d_dL_dsmooth,
+                              double* d_grad, void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
  * qs_scatter_noalloc: qs_scatter for callers that cannot allocate device

@@ -144,8 +144,14 @@ def _lib():
             L.qs_batch_workspace_bytes.restype = C.c_size_t
             L.qs_scatter_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
                                            C.POINTER(qs_bins), _VP, C.c_int32,
-                                           C.POINTER(qs_exec), _VP, _VP, _VP, C.c_size_t, _VP]
+                                           C.POINTER(qs_exec), _VP, _VP, _VP, _VP, C.c_size_t,
+                                           _VP]
             L.qs_scatter_batch.restype = C.c_int32
+            L.qs_scatter_grad_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
+                                                C.POINTER(qs_bins), _VP, C.c_int32,
+                                                C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP,
+                                                C.c_size_t, _VP]
+            L.qs_scatter_grad_batch.restype = C.c_int32
             L.qs_photon_workspace_bytes.argtypes = [C.POINTER(qs_bins), C.POINTER(qs_exec),
                                                     C.c_int64]
             L.qs_photon_workspace_bytes.restype = C.c_size_t
@@ -443,16 +449,25 @@ def _struct_array_to_device(structs, ctype, device) -> torch.Tensor:
 
 class Batch:
     """Device-side descriptors, outputs and workspace of one qs_scatter_batch
-    problem shape (reusable across calls and capturable in a CUDA graph)."""
+    problem shape (reusable across calls and capturable in a CUDA graph).
+    With ``bins.smooth_sigma_bins > 0`` the kernel-smoothed spectra are
+    produced too, and ``grad`` runs the batched adjoint
+    (qs_scatter_grad_batch) over the same workspace."""
+
+    # columns of the 8 gradient parameters in the device descriptor arrays
+    # viewed as float64 rows (qs_laser: 10 doubles, qs_beam: 11 doubles)
+    LASER_COLS = (1, 2, 4, 5, 6)       # a0, w0_um, dx_um, dy_um, delay_fs
+    BEAM_COLS = (0, 1, 7)              # gamma_mean, rel_spread, div_rad
 
     def __init__(self, lasers, beams, offsets, bins: _inputs.Bins, n_total: int, device=None,
-                 ranges=None, precision="f32", tile=0, block=0, grid=0, max_phase=None):
+                 ranges=None, precision="f32", tile=0, block=0, grid=0, max_phase=None,
+                 grad_block=0):
         dev = device or torch.device("cuda", torch.cuda.current_device())
         self.n_shots = len(lasers)
         assert len(beams) == self.n_shots
         self.bins = bins
         self.precision = precision
-        self.tile, self.block, self.grid = tile, block, grid
+        self.tile, self.block, self.grid, self.grad_block = tile, block, grid, grad_block
         self.max_phase = int(max_phase or max(int(l.n_phase) if l.model == _inputs.MODEL_QFP else 1
                                               for l in lasers))
         self.d_lasers = _struct_array_to_device([make_laser(l) for l in lasers], qs_laser, dev)
@@ -465,8 +480,12 @@ class Batch:
             self.d_offsets = off.to(dev)
         self.d_ranges = None if ranges is None else torch.as_tensor(
             ranges, dtype=torch.float64).reshape(-1, 2).contiguous().to(dev)
-        self.spectra = torch.zeros(self.n_shots, max(bins.n_bins, 0), dtype=torch.float64, device=dev)
+        nb = max(bins.n_bins, 0)
+        self.spectra = torch.zeros(self.n_shots, nb, dtype=torch.float64, device=dev)
+        self.spec_smooth = torch.zeros(self.n_shots, nb if bins.smooth_sigma_bins > 0 else 0,
+                                       dtype=torch.float64, device=dev)
         self.moments = torch.zeros(self.n_shots, len(MOMENT_FIELDS), dtype=torch.float64, device=dev)
+        self.grads = torch.zeros(self.n_shots, len(GRAD_PARAMS), dtype=torch.float64, device=dev)
         e = make_exec(precision, 0, block, grid, None, tile)
         b = make_bins(bins)
         nbytes = _lib().qs_batch_workspace_bytes(self.n_shots, int(n_total), C.byref(b),
@@ -478,20 +497,62 @@ class Batch:
         self.ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
         self.ws_bytes = nbytes
 
-    def run(self, xi, w=None, stream=None):
+    def _common(self):
+        return (self.n_shots, self.d_lasers.data_ptr(), self.d_beams.data_ptr(),
+                self.d_offsets.data_ptr() if self.d_offsets is not None else None)
+
+    def run(self, xi, w=None, stream=None, check_finite=False):
         s, keep = make_samples(xi, w)
         self._keep = keep
         b = make_bins(self.bins)
-        e = make_exec(self.precision, 0, self.block, self.grid, None, self.tile)
+        e = make_exec(self.precision, 0, self.block, self.grid, None, self.tile, check_finite)
         st = _lib().qs_scatter_batch(
-            self.n_shots, self.d_lasers.data_ptr(), self.d_beams.data_ptr(),
-            self.d_offsets.data_ptr() if self.d_offsets is not None else None, C.byref(s),
-            C.byref(b),
+            *self._common(), C.byref(s), C.byref(b),
             self.d_ranges.data_ptr() if self.d_ranges is not None else None, self.max_phase,
             C.byref(e), self.spectra.data_ptr() if self.spectra.numel() else None,
+            self.spec_smooth.data_ptr() if self.spec_smooth.numel() else None,
             self.moments.data_ptr(), self.ws_ptr, self.ws_bytes, _stream_ptr(stream))
         _check(st, "qs_scatter_batch")
         return self
+
+    def grad(self, xi, dL_dmoments, dL_dsmooth=None, w=None, moments=None, out=None,
+             stream=None) -> torch.Tensor:
+        """Per-shot gradients (n_shots x 8, GRAD_PARAMS order) of a loss
+        given its upstream gradient with respect to every shot's 13 moments
+        (n_shots x 13) and smoothed spectrum (n_shots x n_bins); ``moments``:
+        the forward moments (default: those of the last run)."""
+        s, keep = make_samples(xi, w)
+        dev = self.moments.device
+        mom = (self.moments if moments is None else moments).to(dev, torch.float64).contiguous()
+        dm = dL_dmoments.to(dev, torch.float64).contiguous()
+        dS = None if dL_dsmooth is None else dL_dsmooth.to(dev, torch.float64).contiguous()
+        g = self.grads if out is None else out
+        b = make_bins(self.bins)
+        e = make_exec(self.precision, 0, self.grad_block, self.grid, None, self.tile)
+        st = _lib().qs_scatter_grad_batch(
+            *self._common(), C.byref(s), C.byref(b),
+            self.d_ranges.data_ptr() if self.d_ranges is not None else None, self.max_phase,
+            C.byref(e), mom.data_ptr(), dm.data_ptr(),
+            dS.data_ptr() if dS is not None else None, g.data_ptr(), self.ws_ptr, self.ws_bytes,
+            _stream_ptr(stream))
+        _check(st, "qs_scatter_grad_batch")
+        self._keep_grad = (keep, mom, dm, dS)
+        return g
+
+    def params(self) -> torch.Tensor:
+        """The shots' 8 gradient parameters (n_shots x 8, device)."""
+        L = self.d_lasers.view(torch.float64).view(self.n_shots, -1)
+        Bm = self.d_beams.view(torch.float64).view(self.n_shots, -1)
+        return torch.cat([L[:, list(self.LASER_COLS)], Bm[:, list(self.BEAM_COLS)]], dim=1)
+
+    def set_params(self, theta: torch.Tensor):
+        """Writes the shots' 8 gradient parameters (n_shots x 8) into the device
+        descriptors (the other descriptor fields are kept)."""
+        t = theta.to(self.d_lasers.device, torch.float64)
+        L = self.d_lasers.view(torch.float64).view(self.n_shots, -1)
+        Bm = self.d_beams.view(torch.float64).view(self.n_shots, -1)
+        L[:, list(self.LASER_COLS)] = t[:, :5]
+        Bm[:, list(self.BEAM_COLS)] = t[:, 5:]
 
     def moments_dicts(self) -> list[dict]:
         return [dict(zip(MOMENT_FIELDS, row)) for row in self.moments.cpu().tolist()]

@@ -12,12 +12,17 @@
 //               shared-memory histogram into the shot's accumulators.
 // B4 k_bfinal   one warp per shot: partials summed in tile order, histograms
 //               converted, moments written.
+// G3 k_bgrad    (qs_scatter_grad_batch) the adjoint over the same (shot,
+//               tile) schedule: each tile's samples recomputed with tangents,
+//               the tile's 8 gradient partials to its own slot.
+// G4 k_bgfinal  one warp per shot: gradient slots summed in tile order.
 //
 // Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348 (Sec. 3.2: parallel
 // plane-wave runs; Sec. 6: high-repetition-rate data).
 #include "qscatter.h"
 #include "qs_device.cuh"
 #include "qs_derive.cuh"
+#include "qs_grad.cuh"
 #include "qs_host.hpp"
 
 namespace qs {
@@ -34,6 +39,7 @@ struct BatchArgs {
   int64_t* tiles;               // [n_shots + 1] counts, then exclusive offsets
   void* tables;                 // [n_shots * max_phase] float4 (FP32) or double (FP64)
   unsigned long long* acc;      // [n_shots * (n_bins + 2)]
+  unsigned long long* acc_smooth;  // [n_shots * n_bins] (smoothed spectrum) or null
   double* partials;             // [tiles * kNumMom]
   unsigned long long* counter;  // work counter
   int64_t max_tiles;            // tile slots in the workspace
@@ -75,6 +81,7 @@ __global__ void k_bsetup(const BatchArgs a) {
   p.dtype = a.samples.dtype;
   p.weighted = a.samples.w != nullptr;
   p.acc_spec = a.bins.n_bins > 0 ? a.acc + (size_t)s * (a.bins.n_bins + 2) : nullptr;
+  p.acc_smooth = a.acc_smooth ? a.acc_smooth + (size_t)s * a.bins.n_bins : nullptr;
   a.tiles[s] = (p.n + a.tile - 1) / a.tile;
 }
 
@@ -152,8 +159,15 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
       ((size_t)(a.bins.n_bins > 0 ? a.bins.n_bins + 2 : 0) * sizeof(H) + 15) & ~(size_t)15;
   int64_t& s_tile = *reinterpret_cast<int64_t*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes);
   int& s_shot = *reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes + 8);
+  // the tile's smoothed-spectrum accumulators (when smoothing), after the
+  // broadcast slots
+  const int64_t nsm = a.acc_smooth ? (int64_t)a.bins.n_bins : 0;
+  unsigned long long* hsm = nsm ? reinterpret_cast<unsigned long long*>(
+                                      reinterpret_cast<unsigned char*>(hs) + hist_bytes + 16)
+                                : nullptr;
   const int64_t total = a.tiles[a.n_shots];
   const int64_t nspec = a.bins.n_bins > 0 ? (int64_t)a.bins.n_bins + 2 : 0;
+  const int lane = threadIdx.x & 31;
   int cur = -1;
 
   for (;;) {
@@ -191,60 +205,80 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
       cur = s;
     }
     for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x) hs[b] = 0;
+    for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x) hsm[b] = 0;
     __syncthreads();
 
     typename AccT<T>::type acc;
     acc_init(acc);
     const int64_t first = (t - a.tiles[s]) * a.tile;
     const int64_t last = min(p.n, first + a.tile);
+    // loops advance warp by warp (bounds uniform across the lanes), so that
+    // the smoothed deposits run warp-cooperatively after each step
+    bool pairs = false;
     if constexpr (sizeof(T) == 4) {
       if (p.model == QS_MODEL_QFP) {
-        for (int64_t k = first / 2 + threadIdx.x; 2 * k < last; k += blockDim.x) {
+        pairs = true;
+        // FP32 QFP: each thread carries samples 2k and 2k+1 (first is even)
+        for (int64_t kb = first / 2 + threadIdx.x - lane; 2 * kb < last; kb += blockDim.x) {
+          const int64_t k = kb + lane;
           const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
-          SampleF s0, s1;
-          eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-          accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
-          if (i1 != i0)
-            accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
-        }
-      } else {
-        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-          const auto sm = eval_one<T, false>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
+          DepF d0, d1;
+          bool ok0 = false, ok1 = false;
+          if (i0 < last) {
+            SampleF s0, s1;
+            eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
+            ok0 = accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
+            if (i1 != i0)
+              ok1 = accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
+            dep_set(d0, s0);
+            dep_set(d1, s1);
+          }
+          if (hsm) {
+            deposit_warp(p, ok0, d0, i0, hsm);
+            deposit_warp(p, ok1, d1, i1, hsm);
+          }
         }
       }
-    } else {
-      if (p.model == QS_MODEL_QFP) {
-        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-          const auto sm = eval_one<T, true>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
+    }
+    if (!pairs) {
+      for (int64_t ib = first + threadIdx.x - lane; ib < last; ib += blockDim.x) {
+        const int64_t i = ib + lane;
+        typename DepT<T>::type d;
+        bool ok = false;
+        if (i < last) {
+          const auto sm = p.model == QS_MODEL_QFP ? eval_one<T, true>(p, tab, i)
+                                                  : eval_one<T, false>(p, tab, i);
+          ok = accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
+          dep_set(d, sm);
         }
-      } else {
-        for (int64_t i = first + threadIdx.x; i < last; i += blockDim.x) {
-          const auto sm = eval_one<T, false>(p, tab, i);
-          accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
-        }
+        if (hsm) deposit_warp(p, ok, d, i, hsm);
       }
     }
     block_reduce_write(acc, red, a.partials + (size_t)t * kNumMom);
     __syncthreads();
     for (int64_t b = threadIdx.x; b < nspec; b += blockDim.x)
       if (hs[b]) atomicAdd(&p.acc_spec[b], (unsigned long long)hs[b]);
+    for (int64_t b = threadIdx.x; b < nsm; b += blockDim.x)
+      if (hsm[b]) atomicAdd(&p.acc_smooth[b], hsm[b]);
     __syncthreads();
   }
 }
 
 // One warp per shot: moments from its tiles' partials in tile order.
-__global__ void k_bfinal(const BatchArgs a, double* spectra, qs_moments* moments) {
+__global__ void k_bfinal(const BatchArgs a, double* spectra, double* smooth,
+                         qs_moments* moments) {
   const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= a.n_shots) return;
   const Params& p = a.shot[s];
   const int nb = a.bins.n_bins;
+  const bool sm = a.acc_smooth != nullptr;
   qs_moments m;
   memset(&m, 0, sizeof(m));
   if (p.n < 0) {
     for (int b = lane; b < nb; b += 32) spectra[(size_t)s * nb + b] = 0.0;
+    if (sm)
+      for (int b = lane; b < nb; b += 32) smooth[(size_t)s * nb + b] = 0.0;
     if (lane == 0) {
       m.nonfinite = -1.0;
       moments[s] = m;
@@ -282,6 +316,9 @@ __global__ void k_bfinal(const BatchArgs a, double* spectra, qs_moments* moments
   v[2] = __shfl_sync(0xffffffffu, m2_l0, 0);
   const unsigned long long* acc = p.acc_spec;
   for (int b = lane; b < nb; b += 32) spectra[(size_t)s * nb + b] = (double)acc[b] * scale;
+  if (sm)
+    for (int b = lane; b < nb; b += 32)
+      smooth[(size_t)s * nb + b] = (double)p.acc_smooth[b] / p.wscale;
   if (lane == 0) {
     const double W = v[0];
     m.W = W;
@@ -303,6 +340,126 @@ __global__ void k_bfinal(const BatchArgs a, double* spectra, qs_moments* moments
   }
 }
 
+// Largest smoothed spectrum whose upstream gradient the FP32 batched adjoint
+// stages in shared memory (larger ones are read from global memory).
+constexpr int kBGradStageBins = 8192;
+
+// G3: the adjoint of every shot over the (shot, tile) schedule of k_batch.
+// Per tile: the shot's launch constants, envelope table and (FP32, when it
+// fits) its upstream smoothed-spectrum gradient staged in shared memory, the
+// upstream coefficients of its moments in registers; the tile's samples
+// recomputed with tangents exactly as k_grad does; the tile's 8 partials
+// reduced in a fixed order into its own slot.
+//   moms: the forward moments (n_shots); dLdm: n_shots x 13; dLdS: n_shots x
+//   n_bins or null.
+template <typename T>
+__global__ void __launch_bounds__(512) k_bgrad(const BatchArgs a, const qs_moments* __restrict__ moms,
+                                               const double* __restrict__ dLdm,
+                                               const double* __restrict__ dLdS) {
+  using TT = typename Tab<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Params& p = *reinterpret_cast<Params*>(smem);
+  const size_t par_bytes = (sizeof(Params) + 15) & ~(size_t)15;
+  TT* tab = reinterpret_cast<TT*>(smem + par_bytes);
+  const size_t tab_bytes = ((size_t)a.max_phase * sizeof(TT) + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem + par_bytes + tab_bytes);
+  unsigned char* after_red = smem + par_bytes + tab_bytes +
+                             (((size_t)(blockDim.x >> 5) * kNumGrad * sizeof(double) + 15) &
+                              ~(size_t)15);
+  int64_t& s_tile = *reinterpret_cast<int64_t*>(after_red);
+  int& s_shot = *reinterpret_cast<int*>(after_red + 8);
+  const int nb = a.bins.n_bins;
+  const bool smooth = dLdS != nullptr && a.bins.smooth_sigma_bins > 0.0;
+  const bool stage = smooth && sizeof(T) == 4 && nb <= kBGradStageBins;
+  T* sdS = reinterpret_cast<T*>(after_red + 16);
+  const int64_t total = a.tiles[a.n_shots];
+  int cur = -1;
+  Seeds<T> sd{};
+  T w0 = (T)1;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)atomicAdd(a.counter, 1ull);
+      s_tile = t;
+      int sh = -1;
+      if (t < total) {
+        int lo = 0, hi = a.n_shots - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.tiles[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        sh = lo;
+      }
+      s_shot = sh;
+    }
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int s = s_shot;
+    if (t >= total) break;
+    if (s != cur) {
+      const int nw = (int)(sizeof(Params) / 4);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.shot[s]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&p);
+      for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      if (p.model == QS_MODEL_QFP) {
+        const TT* tg = static_cast<const TT*>(a.tables) + (size_t)s * a.max_phase;
+        for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) tab[j] = tg[j];
+      }
+      if (stage)
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) sdS[k] = (T)dLdS[(size_t)s * nb + k];
+      sd = make_seeds<T>(moms + s, dLdm + (size_t)s * 13);
+      w0 = (T)sqrt(1.0 / p.inv_w0sq);
+      cur = s;
+      __syncthreads();
+    }
+    GAcc<T> acc;
+    acc.init();
+    const int64_t first = (t - a.tiles[s]) * a.tile;
+    const int64_t last = min(p.n, first + a.tile);
+    const int64_t tid = threadIdx.x, nthr = blockDim.x;
+    const double* gS = smooth ? dLdS + (size_t)s * nb : nullptr;
+    if (p.model == QS_MODEL_QFP) {
+      if (!smooth)
+        grad_range<T, true, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, first, last, tid, nthr);
+      else if (stage)
+        grad_range<T, true, T>(p, tab, sd, sdS, w0, acc, first, last, tid, nthr);
+      else
+        grad_range<T, true, double>(p, tab, sd, gS, w0, acc, first, last, tid, nthr);
+    } else {
+      if (!smooth)
+        grad_range<T, false, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, first, last, tid, nthr);
+      else if (stage)
+        grad_range<T, false, T>(p, tab, sd, sdS, w0, acc, first, last, tid, nthr);
+      else
+        grad_range<T, false, double>(p, tab, sd, gS, w0, acc, first, last, tid, nthr);
+    }
+    grad_block_reduce(acc, red, a.partials + (size_t)t * kNumMom);
+    __syncthreads();
+  }
+}
+
+// G4: one warp per shot, lane k < 8 sums gradient component k over the
+// shot's tiles in tile order (compensated); invalid shots get zeros.
+__global__ void k_bgfinal(const BatchArgs a, double* grad) {
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= a.n_shots || lane >= kNumGrad) return;
+  const Params& p = a.shot[s];
+  double sm = 0.0, c = 0.0;
+  if (p.n >= 0) {
+    const int64_t t0 = a.tiles[s], t1 = (s + 1 < a.n_shots) ? a.tiles[s + 1] : a.tiles[a.n_shots];
+    for (int64_t t = t0; t < t1; ++t) {
+      const double x = a.partials[(size_t)t * kNumMom + lane];
+      const double u = sm + x;
+      c += fabs(sm) >= fabs(x) ? (sm - u) + x : (x - u) + sm;
+      sm = u;
+    }
+  }
+  grad[(size_t)s * kNumGrad + lane] = sm + c;
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -312,7 +469,7 @@ namespace {
 
 struct BatchPlan {
   size_t off_counter = 0, off_params = 0, off_tiles = 0, off_tables = 0, off_acc = 0,
-         off_part = 0, bytes = 0;
+         off_smooth = 0, off_part = 0, bytes = 0;
   int64_t max_tiles = 0;
 };
 
@@ -331,6 +488,8 @@ bool batch_plan(BatchPlan& bp, int32_t n_shots, int64_t n_total, const qs_bins* 
   off = align_up(off + (size_t)n_shots * max_phase * (precision == QS_F64 ? 8 : 16), 256);
   bp.off_acc = off;
   off = align_up(off + (size_t)n_shots * (bins->n_bins > 0 ? bins->n_bins + 2 : 0) * 8, 256);
+  bp.off_smooth = off;
+  off = align_up(off + (size_t)n_shots * (bins->smooth_sigma_bins > 0 ? bins->n_bins : 0) * 8, 256);
   bp.off_part = off; off = align_up(off + (size_t)bp.max_tiles * kNumMom * 8, 256);
   bp.bytes = off;
   return true;
@@ -342,8 +501,7 @@ int32_t batch_checks(int32_t n_shots, const qs_samples* samples, const qs_bins* 
   int32_t st;
   if (n_shots < 1 || max_phase < 1 || max_phase > kMaxPhase) return QS_ERR_INVALID_ARG;
   if ((st = validate_samples(samples)) || (st = validate_bins(bins))) return st;
-  if (bins->n_tx > 0 || bins->n_aeff > 0 || bins->smooth_sigma_bins > 0)
-    return QS_ERR_UNSUPPORTED;
+  if (bins->n_tx > 0 || bins->n_aeff > 0) return QS_ERR_UNSUPPORTED;
   if ((st = exec_opts(exec, prec, wbits, block, grid))) return st;
   if ((st = exec_tile(exec, tile))) return st;
   return QS_OK;
@@ -355,7 +513,7 @@ int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaS
   const size_t smem = align_up(sizeof(Params), 16) + align_up((size_t)a.max_phase * sizeof(TT), 16) +
                       (size_t)(block / 32) * kNumMom * sizeof(double) +
                       align_up((size_t)(a.bins.n_bins > 0 ? a.bins.n_bins + 2 : 0) * sizeof(H), 16) +
-                      16;
+                      16 + (a.acc_smooth ? (size_t)a.bins.n_bins * 8 : 0);
   if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
   auto kern = k_batch<T, H>;
   static CtxMark smem_mark;
@@ -382,30 +540,24 @@ extern "C" size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, con
   return bp.bytes;
 }
 
-extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
-                                    const qs_beam* d_beams, const int64_t* d_offsets,
-                                    const qs_samples* samples, const qs_bins* bins,
-                                    const double* d_ranges, int32_t max_phase,
-                                    const qs_exec* exec, double* d_spectra,
-                                    qs_moments* d_moments, void* d_workspace, size_t ws_bytes,
-                                    void* stream) {
-  int prec, wbits, block, grid, tile, sms;
-  int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
-                            &tile);
-  if (st) return st;
-  if (!d_lasers || !d_beams || !d_moments) return QS_ERR_INVALID_ARG;
-  if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
-  if (block > 256) block = 256;
-  if ((st = device_sms(&sms))) return st;
-  const bool check = exec_check_finite(exec);
-  if (check && (st = sync_allowed(static_cast<cudaStream_t>(stream)))) return st;
+namespace {
+
+// Device descriptors, workspace layout and the set-up kernels shared by the
+// batched forward and adjoint: validates on the host, fills `a`, zeroes the
+// work counter (and, for the forward, the accumulators) and launches
+// k_bsetup, k_btable and k_bscan on `cs`.
+int32_t batch_prepare(BatchArgs& a, int32_t n_shots, const qs_laser* d_lasers,
+                      const qs_beam* d_beams, const int64_t* d_offsets,
+                      const qs_samples* samples, const qs_bins* bins, const double* d_ranges,
+                      int32_t max_phase, int prec, int wbits, int tile, void* d_workspace,
+                      size_t ws_bytes, bool zero_acc, cudaStream_t cs) {
+  if (!d_lasers || !d_beams) return QS_ERR_INVALID_ARG;
   BatchPlan bp;
   if (!batch_plan(bp, n_shots, samples->n, bins, max_phase, prec, tile, d_offsets == nullptr))
     return QS_ERR_INVALID_ARG;
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < bp.bytes)
     return QS_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(d_workspace);
-  BatchArgs a;
   memset(&a, 0, sizeof(a));
   a.n_shots = n_shots;
   a.max_phase = max_phase;
@@ -421,21 +573,70 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   a.tiles = reinterpret_cast<int64_t*>(ws + bp.off_tiles);
   a.tables = ws + bp.off_tables;
   a.acc = reinterpret_cast<unsigned long long*>(ws + bp.off_acc);
+  a.acc_smooth = bins->smooth_sigma_bins > 0
+                     ? reinterpret_cast<unsigned long long*>(ws + bp.off_smooth)
+                     : nullptr;
   a.partials = reinterpret_cast<double*>(ws + bp.off_part);
   a.counter = reinterpret_cast<unsigned long long*>(ws + bp.off_counter);
   a.max_tiles = bp.max_tiles;
   a.precision = prec;
-  cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  // zero the work counter and the histogram accumulators
   if (cudaMemsetAsync(ws + bp.off_counter, 0, 8, cs) != cudaSuccess) return cuda_fail();
-  if (bp.off_part > bp.off_acc &&
+  if (zero_acc && bp.off_part > bp.off_acc &&
       cudaMemsetAsync(ws + bp.off_acc, 0, bp.off_part - bp.off_acc, cs) != cudaSuccess)
     return cuda_fail();
   k_bsetup<<<(n_shots + 127) / 128, 128, 0, cs>>>(a);
   const int64_t cells = (int64_t)n_shots * max_phase;
   k_btable<<<(unsigned)((cells + 255) / 256), 256, 0, cs>>>(a);
   k_bscan<<<1, 1024, 0, cs>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+template <typename T>
+int32_t launch_bgrad(const BatchArgs& a, int block, int grid_req, int sms, const qs_moments* mom,
+                     const double* dLdm, const double* dLdS, cudaStream_t st) {
+  using TT = typename Tab<T>::type;
+  const bool stage = dLdS && a.bins.smooth_sigma_bins > 0 && sizeof(T) == 4 &&
+                     a.bins.n_bins <= kBGradStageBins;
+  const size_t smem = align_up(sizeof(Params), 16) + align_up((size_t)a.max_phase * sizeof(TT), 16) +
+                      align_up((size_t)(block / 32) * kNumGrad * sizeof(double), 16) + 16 +
+                      (stage ? (size_t)a.bins.n_bins * sizeof(T) : 0);
+  if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
+  auto kern = k_bgrad<T>;
+  static CtxMark smem_mark;
+  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
+    return cuda_fail();
+  const int grid = grid_req > 0 ? grid_req : sms * (occ > 0 ? occ : 1);
+  kern<<<grid, block, smem, st>>>(a, mom, dLdm, dLdS);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
+                                    const qs_beam* d_beams, const int64_t* d_offsets,
+                                    const qs_samples* samples, const qs_bins* bins,
+                                    const double* d_ranges, int32_t max_phase,
+                                    const qs_exec* exec, double* d_spectra,
+                                    double* d_spec_smooth, qs_moments* d_moments,
+                                    void* d_workspace, size_t ws_bytes, void* stream) {
+  int prec, wbits, block, grid, tile, sms;
+  int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
+                            &tile);
+  if (st) return st;
+  if (!d_moments) return QS_ERR_INVALID_ARG;
+  if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
+  if (bins->smooth_sigma_bins > 0 && !d_spec_smooth) return QS_ERR_INVALID_ARG;
+  if (block > 256) block = 256;
+  if ((st = device_sms(&sms))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const bool check = exec_check_finite(exec);
+  if (check && (st = sync_allowed(cs))) return st;
+  BatchArgs a;
+  if ((st = batch_prepare(a, n_shots, d_lasers, d_beams, d_offsets, samples, bins, d_ranges,
+                          max_phase, prec, wbits, tile, d_workspace, ws_bytes, true, cs)))
+    return st;
   if (prec == QS_F64)
     st = samples->w ? launch_batch<double, unsigned long long>(a, block, grid, sms, cs)
                     : launch_batch<double, unsigned int>(a, block, grid, sms, cs);
@@ -444,8 +645,40 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
                     : launch_batch<float, unsigned int>(a, block, grid, sms, cs);
   if (st) return st;
   const int64_t thr = (int64_t)n_shots * 32;
-  k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_moments);
+  k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_spec_smooth, d_moments);
   if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
   return check ? nonfinite_status(&d_moments[0].nonfinite, n_shots, sizeof(qs_moments), cs)
                : QS_OK;
+}
+
+extern "C" int32_t qs_scatter_grad_batch(int32_t n_shots, const qs_laser* d_lasers,
+                                         const qs_beam* d_beams, const int64_t* d_offsets,
+                                         const qs_samples* samples, const qs_bins* bins,
+                                         const double* d_ranges, int32_t max_phase,
+                                         const qs_exec* exec, const qs_moments* d_moments,
+                                         const double* d_dL_dmoments,
+                                         const double* d_dL_dsmooth, double* d_grad,
+                                         void* d_workspace, size_t ws_bytes, void* stream) {
+  int prec, wbits, block, grid, tile, sms;
+  int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
+                            &tile);
+  if (st) return st;
+  if (!d_moments || !d_dL_dmoments || !d_grad) return QS_ERR_INVALID_ARG;
+  if (d_dL_dsmooth && !(bins->smooth_sigma_bins > 0)) return QS_ERR_INVALID_ARG;
+  if ((st = device_sms(&sms))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  // FP32 with the block left open: 512-thread CTAs (one per SM at the
+  // adjoint's register count), as for the single-shot adjoint
+  const int kblock = (!(exec && exec->block) && prec == QS_F32) ? 512 : block;
+  BatchArgs a;
+  if ((st = batch_prepare(a, n_shots, d_lasers, d_beams, d_offsets, samples, bins, d_ranges,
+                          max_phase, prec, wbits, tile, d_workspace, ws_bytes, false, cs)))
+    return st;
+  st = prec == QS_F64
+           ? launch_bgrad<double>(a, kblock, grid, sms, d_moments, d_dL_dmoments, d_dL_dsmooth, cs)
+           : launch_bgrad<float>(a, kblock, grid, sms, d_moments, d_dL_dmoments, d_dL_dsmooth, cs);
+  if (st) return st;
+  const int64_t thr = (int64_t)n_shots * 32;
+  k_bgfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_grad);
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }

@@ -112,7 +112,97 @@ def fit(prob: Problem, theta0: torch.Tensor, target_mom, target_S, steps: int = 
         L = loss_fn(mom, S, target_mom, target_S, mw, spectrum_weight)
         L.backward()
         opt.step()
-        hist.append(float(L))
+        hist.append(float(L.detach()))
         if callback is not None:
-            callback(it, z.detach() * scale, float(L))
+            callback(it, z.detach() * scale, float(L.detach()))
     return (z.detach() * scale), hist
+
+
+# ---- many shots at once ------------------------------------------------------
+
+@dataclass
+class BatchProblem:
+    """Everything fixed during a batched fit: the device descriptors, outputs
+    and workspace of one batch (``binding.Batch``, whose bins carry the
+    smoothing width), the concatenated samples and their weights."""
+    batch: B.Batch
+    xi: list
+    w: torch.Tensor | None = None
+
+
+class BatchScatterFn(torch.autograd.Function):
+    """theta (n_shots, 8) -> (moments (n_shots, 13), smoothed spectra
+    (n_shots, n_bins)): forward qs_scatter_batch, backward
+    qs_scatter_grad_batch (every sample recomputed with tangents)."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, prob: BatchProblem):
+        bt = prob.batch
+        th = theta.detach().to(bt.moments.device, torch.float64)
+        bt.set_params(th)
+        bt.run(prob.xi, prob.w)
+        mom = bt.moments.clone()
+        S = bt.spec_smooth.clone()
+        ctx.prob = prob
+        ctx.save_for_backward(th.clone(), mom)
+        ctx.theta_meta = (theta.dtype, theta.device)
+        return mom, S
+
+    @staticmethod
+    def backward(ctx, g_mom, g_S):
+        th, mom = ctx.saved_tensors
+        prob = ctx.prob
+        bt = prob.batch
+        bt.set_params(th)           # the descriptors of this forward
+        if g_mom is None:
+            g_mom = torch.zeros_like(mom)
+        g = bt.grad(prob.xi, g_mom, g_S, w=prob.w, moments=mom).clone()
+        dt, dev = ctx.theta_meta
+        return g.to(device=dev, dtype=dt), None
+
+
+def loss_batch(mom, S, target_mom, target_S, moment_weights: dict, spectrum_weight: float):
+    """Per-shot loss (n_shots,): loss_fn of every shot, vectorised."""
+    L = torch.zeros(mom.shape[0], dtype=torch.float64, device=mom.device)
+    for k, c in moment_weights.items():
+        i = MOMENT_INDEX[k]
+        ref = target_mom[:, i]
+        L = L + c * ((mom[:, i] - ref) / (ref.abs() + 1e-30)) ** 2
+    if spectrum_weight and S.numel():
+        norm = target_S.sum(dim=1, keepdim=True).clamp_min(1e-30)
+        L = L + spectrum_weight * (((S - target_S) / norm) ** 2).sum(dim=1) * S.shape[1]
+    return L
+
+
+# The beam's mean energy without the laser (mean_gamma0) is part of the
+# batched fit's default loss: a shot's reference measurement.
+BATCH_MOMENT_WEIGHTS = {**DEFAULT_MOMENT_WEIGHTS, "mean_gamma0": 1.0}
+
+
+def fit_batch(prob: BatchProblem, theta0: torch.Tensor, target_mom, target_S, steps: int = 200,
+              lr: float = 0.01, scale: torch.Tensor | None = None, moment_weights=None,
+              spectrum_weight: float = 1.0, lr_decay: float = 1.0, callback=None):
+    """Adam on every shot's theta / scale at once (the shots' losses add, so
+    each shot's parameters follow their own loss).  The learning rate is
+    multiplied by ``lr_decay`` after every step.  Returns (theta, history of
+    the summed loss, final per-shot losses)."""
+    mw = BATCH_MOMENT_WEIGHTS if moment_weights is None else moment_weights
+    scale = theta0.abs().clamp_min(1e-12) if scale is None else scale
+    z = (theta0 / scale).clone().requires_grad_(True)
+    opt = torch.optim.Adam([z], lr=lr)
+    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=lr_decay)
+    hist = []
+    last = None
+    for it in range(steps):
+        opt.zero_grad()
+        mom, S = BatchScatterFn.apply(z * scale, prob)
+        per = loss_batch(mom, S, target_mom, target_S, mw, spectrum_weight)
+        L = per.sum()
+        L.backward()
+        opt.step()
+        sched.step()
+        hist.append(float(L.detach()))
+        last = per.detach()
+        if callback is not None:
+            callback(it, z.detach() * scale, per.detach())
+    return (z.detach() * scale), hist, last
