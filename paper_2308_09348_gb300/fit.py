@@ -206,3 +206,41 @@ def fit_batch(prob: BatchProblem, theta0: torch.Tensor, target_mom, target_S, st
         if callback is not None:
             callback(it, z.detach() * scale, per.detach())
     return (z.detach() * scale), hist, last
+
+
+def fit_batch_multistart(lasers, beams, counts, xi, bins, starts: torch.Tensor, target_mom,
+                         target_S, ranges=None, w=None, precision="f32", **kw):
+    """Batched fit from several starting points per shot at once.
+
+    ``starts`` is (K, n_shots, 8): K starting parameter sets for each of the
+    n_shots shots (descriptor templates ``lasers``/``beams``, sample counts
+    ``counts``, concatenated samples ``xi``).  The K x n_shots problems run as
+    one batch over K copies of the samples (each copy sees its shot's own
+    samples, so a shot's loss is exactly zero at its hidden parameters when
+    the targets come from them), and for every shot the start whose fit ends
+    with the lowest loss is kept: a local minimum (the reflections of the
+    transverse offsets and of the delay leave the loss nearly unchanged)
+    then costs nothing unless every start falls into one.  ``kw`` goes to
+    fit_batch.  Returns (theta (n_shots, 8), final per-shot losses, index
+    of the start kept per shot, history)."""
+    K, n_shots = int(starts.shape[0]), int(starts.shape[1])
+    dev = xi[0].device
+    counts = [int(c) for c in counts]
+    offs = [0]
+    for _ in range(K):
+        for c in counts:
+            offs.append(offs[-1] + c)
+    xk = [None if x is None else x.repeat(K) for x in xi]
+    wk = None if w is None else w.repeat(K)
+    rk = None if ranges is None else list(ranges) * K
+    bt = B.Batch(list(lasers) * K, list(beams) * K, offs, bins, int(offs[-1]), dev, ranges=rk,
+                 precision=precision)
+    prob = BatchProblem(bt, xk, wk)
+    tm = target_mom.repeat(K, 1)
+    tS = target_S.repeat(K, 1)
+    theta, hist, last = fit_batch(prob, starts.reshape(K * n_shots, 8).to(dev, torch.float64),
+                                  tm, tS, **kw)
+    per = last.reshape(K, n_shots)
+    best = per.argmin(dim=0)
+    th = theta.reshape(K, n_shots, 8)[best, torch.arange(n_shots, device=dev)]
+    return th, per.min(dim=0).values, best, hist
