@@ -579,6 +579,84 @@ def bench_grad(dev, rank, steps=3, n=1 << 24):
             "workload": wl.name}
 
 
+def bench_fit256(dev, rank, steps=10, n_shots=256, per=1 << 16):
+    """The batched gradient fit of the reconstruction use: 256 shots of 2^16
+    FP32 samples each (2^24 in all), hidden parameters drawn from the batched
+    configuration's ranges (a0 U[5,50], W0 U[2,10] um, offsets N(0,2) um,
+    delay N(0,30) fs, gamma_mean U[1e3,2e4], spread U[0.01,0.2], 1 mrad),
+    quantum model over 512 cells, loss on the moments and the 2-bin-smoothed
+    256-bin spectrum of every shot; perturbed starts; Adam.  Timed: whole
+    Adam steps (batched forward, batched adjoint, loss, update), and the two
+    batched kernels alone."""
+    import numpy as np
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import fit as F
+    from paper_2308_09348_gb300 import inputs as I
+    g = I.rng(0x23080904 + rank)
+    a0, w0 = g.uniform(5, 50, n_shots), g.uniform(2, 10, n_shots)
+    dx, dy, delay = g.normal(0, 2, n_shots), g.normal(0, 2, n_shots), g.normal(0, 30, n_shots)
+    gm, sp = g.uniform(1e3, 2e4, n_shots), g.uniform(0.01, 0.2, n_shots)
+    lasers = [I.Laser(lambda_um=0.8, a0=a0[k], w0_um=w0[k], tau_fs=30.0, model=I.MODEL_QFP,
+                      dx_um=dx[k], dy_um=dy[k], delay_fs=delay[k], n_phase=512)
+              for k in range(n_shots)]
+    beams = [I.Beam(gamma_mean=gm[k], rel_spread=sp[k], sigma_x_um=3.0, sigma_y_um=3.0,
+                    sigma_z_um=10.0, div_rad=1e-3) for k in range(n_shots)]
+    ranges = np.array([[0.0, 1.2 * gm[k] * (1 + 4 * sp[k])] for k in range(n_shots)])
+    bins = I.Bins(n_bins=256, lo=0.0, hi=1.0, smooth_sigma_bins=2.0)
+    n = n_shots * per
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0x23080904 + 7919 * rank)
+    xi = [torch.randn(n, generator=gen, device=dev, dtype=torch.float32) for _ in range(8)]
+    offsets = np.arange(n_shots + 1, dtype=np.int64) * per
+    bt = B.Batch(lasers, beams, offsets, bins, n, dev, ranges=ranges, precision="f32")
+    prob = F.BatchProblem(bt, xi)
+    hidden = bt.params().clone()
+    with torch.no_grad():
+        tm, tS = F.BatchScatterFn.apply(hidden, prob)
+        tm, tS = tm.clone(), tS.clone()
+    pert = torch.from_numpy(I.rng(77).normal(size=(n_shots, 8))).to(dev).clamp(-2, 2)
+    rel = torch.tensor([0.1, 0.1, 0, 0, 0, 0.05, 0.2, 0.2], dtype=torch.float64, device=dev)
+    absd = torch.tensor([0, 0, 0.3, 0.3, 5.0, 0, 0, 0], dtype=torch.float64, device=dev)
+    start = hidden * (1 + rel * pert) + absd * pert
+    scale = torch.tensor([20.0, 4.0, 2.0, 2.0, 30.0, 6000.0, 0.05, 1e-3], dtype=torch.float64,
+                         device=dev)
+    F.fit_batch(prob, start, tm, tS, steps=2, lr=0.03, scale=scale)        # warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    th, hist, last = F.fit_batch(prob, start, tm, tS, steps=steps, lr=0.03, scale=scale)
+    b.record()
+    torch.cuda.synchronize()
+    ms_step = a.elapsed_time(b) / steps
+    # the batched kernels alone (forward at the start, adjoint of a loss)
+    bt.set_params(start)
+    dm = torch.zeros(n_shots, 13, dtype=torch.float64, device=dev)
+    dm[:, 1] = 1e-3
+    dS = torch.full((n_shots, 256), 1e-3, dtype=torch.float64, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_f = t_b = 0.0
+    for _ in range(3):
+        e[0].record()
+        bt.run(xi)
+        e[1].record()
+        bt.grad(xi, dm, dS)
+        e[2].record()
+        torch.cuda.synchronize()
+        t_f += e[0].elapsed_time(e[1]) / 3
+        t_b += e[1].elapsed_time(e[2]) / 3
+    steps_total = n * 512
+    peak = _fma_peak(dev)
+    return {"metric": "fit shots/s", "value": n_shots / (ms_step * 1e-3), "unit": "shot-steps/s",
+            "ms_per_adam_step": ms_step, "n_shots": n_shots, "samples_per_shot": per,
+            "n_phase": 512, "steps": steps, "loss_first_last": [hist[0], hist[-1]],
+            "batched_forward_ms": t_f, "batched_adjoint_ms": t_b,
+            "grad_samples_per_s": n / ((t_f + t_b) * 1e-3),
+            "adjoint_roofline": {"kernel": "k_bgrad<float>", "bound": "alu", "pipe": "fma",
+                                 "frac": GRAD_FMA_OPS_PER_STEP * steps_total / peak / (t_b * 1e-3)},
+            "workload": "fit256_2p16_qfp512"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -776,6 +854,8 @@ def main():
 
     batch = None if args.no_batch else bench_batch(dev, rank, n_shots=args.batch_shots)
     grad = None if args.no_grad else bench_grad(dev, rank, n=args.grad_n)
+    if grad is not None:
+        grad["fit256"] = bench_fit256(dev, rank)
     broad = None if args.no_broadband else bench_broadband(dev, rank, args.broadband_n)
     ll = None if args.no_ll else bench_ll(dev, rank, n=args.ll_n)
     cell = None if args.no_cell else bench_variant(dev, rank, 1, n=args.cell_n)
