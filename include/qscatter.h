@@ -208,8 +208,11 @@ typedef struct qs_moments {
  *                     threads; 256 threads elsewhere; the grid sized to the
  *                     resident CTAs).  A caller's block is 32..512, a
  *                     multiple of 32.
- *   tile              samples per work item of qs_scatter_batch (0 = 2048;
- *                     a multiple of 64, at most 1<<20); ignored elsewhere.
+ *   tile              samples per work item of qs_scatter_batch (0 = 2048)
+ *                     and of qs_scatter_grad_batch (0 = the largest power of
+ *                     two up to 8192 that leaves about eight work items per
+ *                     resident CTA); a multiple of 64, at most 1<<20;
+ *                     ignored elsewhere.
  *   flags             QS_EXEC_CHECK_FINITE: after the outputs are written
  *                     the call waits for its stream, reads the excluded-sample
  *                     count(s) and returns QS_ERR_NONFINITE if any sample (of

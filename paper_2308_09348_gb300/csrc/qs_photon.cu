@@ -78,10 +78,6 @@ __global__ void __launch_bounds__(256) k_photon_setup() {
 
 // FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
 // table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
-__device__ __forceinline__ float hermite(float h01, float h10, float h11, float v0, float d0,
-                                         float v1, float d1) {
-  return __fmaf_rn(h11, d1, __fmaf_rn(h10, d0, __fmaf_rn(h01, __fsub_rn(v1, v0), v0)));
-}
 
 // Two photon energies e (two bins of one lane) against one emitter whose
 // {1/mu, 1/mu, 2/(3 chi), 2/(3 chi)} is pq: F for both, packed f32x2 except
@@ -109,10 +105,18 @@ __device__ __forceinline__ float2 synch_F2(const float4* __restrict__ T, float2 
   const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));              // t^3 - t^2
   const float2 h10 = __fadd2_rn(fma2(t2, f2(-1.f), t), h11);         // t - 2t^2 + t^3
   const float4 a0 = T[i0], a1 = T[i0 + 1], b0 = T[i1], b1 = T[i1 + 1];
-  const float2 q23 = make_float2(hermite(h01.x, h10.x, h11.x, a0.x, a0.y, a1.x, a1.y),
-                                 hermite(h01.y, h10.y, h11.y, b0.x, b0.y, b1.x, b1.y));
-  const float2 q13 = make_float2(hermite(h01.x, h10.x, h11.x, a0.z, a0.w, a1.z, a1.w),
-                                 hermite(h01.y, h10.y, h11.y, b0.z, b0.w, b1.z, b1.w));
+  // the two cubic Hermite sums, packed over the two bins (the operations of
+  // hermite() in the same order, so each lane rounds as the scalar form)
+  const float2 q23 = fma2(h11, make_float2(a1.y, b1.y),
+                          fma2(h10, make_float2(a0.y, b0.y),
+                               fma2(h01, __fadd2_rn(make_float2(a1.x, b1.x),
+                                                    make_float2(-a0.x, -b0.x)),
+                                    make_float2(a0.x, b0.x))));
+  const float2 q13 = fma2(h11, make_float2(a1.w, b1.w),
+                          fma2(h10, make_float2(a0.w, b0.w),
+                               fma2(h01, __fadd2_rn(make_float2(a1.z, b1.z),
+                                                    make_float2(-a0.z, -b0.z)),
+                                    make_float2(a0.z, b0.z))));
   const float2 ny = mul2(y, f2((float)(-kLog2e)));
   const float2 k23 = ex2x2(__fadd2_rn(fma2(f2(-2.f / 3.f), u, q23), ny));
   const float2 ki13 = ex2x2(__fadd2_rn(q13, ny));
@@ -139,9 +143,9 @@ constexpr int kPhMaxBinsAng = 256;
 
 // Per-lane bin accumulators (NA = 3 sets with ANG: S, T_x, T_y): compensated
 // FP32 sums (FP32 path), FP64 sums.
-template <typename T, bool ANG> struct PhAcc;
-template <bool ANG> struct PhAcc<float, ANG> {
-  static constexpr int NA = ANG ? 3 : 1, K = ANG ? kPhMaxBinsAng / 32 : kPhK;
+template <typename T, bool ANG, int KB> struct PhAcc;
+template <bool ANG, int KB> struct PhAcc<float, ANG, KB> {
+  static constexpr int NA = ANG ? 3 : 1, K = KB;
   float s[NA][K], c[NA][K];
   __device__ __forceinline__ void init() {
 #pragma unroll
@@ -154,8 +158,8 @@ template <bool ANG> struct PhAcc<float, ANG> {
     return (double)s[m][k] - (double)c[m][k];
   }
 };
-template <bool ANG> struct PhAcc<double, ANG> {
-  static constexpr int NA = ANG ? 3 : 1, K = ANG ? kPhMaxBinsAng / 32 : kPhK;
+template <bool ANG, int KB> struct PhAcc<double, ANG, KB> {
+  static constexpr int NA = ANG ? 3 : 1, K = KB;
   double s[NA][K];
   __device__ __forceinline__ void init() {
 #pragma unroll
@@ -176,26 +180,38 @@ __device__ __forceinline__ float4 emitter(float mu, float chi, float c) {
   return make_float4(M<float>::rcp(mu), M<float>::rcp(__fmul_rn(1.5f, chi)), cut, c);
 }
 
+// FP32 path: the per-thread state of the sample pair (the pair's constants
+// and the scheme's state, weights and initial angles) lives in shared
+// memory between cells, one float per field and thread (field-major, so
+// that a warp's accesses are conflict-free): only the bin sums and the
+// evaluation itself then occupy registers in the bin loop.
+//   0-5   c1, ca, ig0 (PairConst, two lanes each)   6-11  du, V, gph (PairState)
+//   12-13 w0, w1      14-17 tx0, ty0, tx1, ty1      18-27 zq0, xs, ys, tx, ty
+//   (PairConst of the per-cell focus)
+__host__ __device__ constexpr int ph_state_fields(int var) { return (var & 1) ? 28 : 18; }
+
 // Shared memory: phase table, photon table (FP32), bin energies, per-warp
-// partial spectra for the CTA's fixed-order reduction, per-warp emitters
-// (FP32).
+// partial spectra for the CTA's fixed-order reduction, per-warp emitters and
+// the per-thread state (FP32).
 template <typename T>
-__host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block, bool ang) {
+__host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block, bool ang,
+                                                       int var) {
   const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
   const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
   const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
-  const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * 3 * sizeof(float4) : 0;
-  return tab + pt + e + (size_t)(block / 32) * (ang ? 3 : 1) * nb * sizeof(double) + stage;
+  const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * (ang ? 3 : 2) * sizeof(float4) : 0;
+  const size_t state = sizeof(T) == 4 ? (size_t)ph_state_fields(var) * block * sizeof(float) : 0;
+  return tab + pt + e + (size_t)(block / 32) * (ang ? 3 : 1) * nb * sizeof(double) + stage + state;
 }
 
 // K7.  pref = h alpha a_S/(2 sqrt3 pi); eps_b at the bin centres.  Per-CTA
 // partials: NA x nb doubles (S, then T_x, T_y with ANG).
-template <typename T, int VAR, bool ANG>
-__global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double lo, double hi,
+template <typename T, int VAR, bool ANG, int KB>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ? 3 : 2)) k_photon(const Params p, int nb, double lo, double hi,
                                                 int log_spaced, double* __restrict__ partials) {
   using TT = typename Tab<T>::type;
-  using Acc = PhAcc<T, ANG>;
-  constexpr int NA = Acc::NA, KB = Acc::K;
+  using Acc = PhAcc<T, ANG, KB>;
+  constexpr int NA = Acc::NA;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t tb = ((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15;
   TT* tab = reinterpret_cast<TT*>(smem);
@@ -207,9 +223,19 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
   // per emitter q of the warp: stP[q] = {1/mu, 1/mu, 2/(3chi), 2/(3chi)},
   // stQ[q] = {c, c, cut, cut}, stA[q] = {c thx^2 term x2, c thy^2 term x2}
   // (pairs ready for the packed evaluation)
-  float4* stP = reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) + warp * 192;
+  constexpr int NST = ANG ? 3 : 2;
+  float4* stP = reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) + warp * 64 * NST;
   float4* stQ = stP + 64;
   float4* stA = stP + 128;
+  float* tst = reinterpret_cast<float*>(reinterpret_cast<float4*>(part + (size_t)nwarp * NA * nb) +
+                                        (size_t)nwarp * 64 * NST);
+  auto ldf = [&](int f) { return tst[f * blockDim.x + threadIdx.x]; };
+  auto stf = [&](int f, float v) { tst[f * blockDim.x + threadIdx.x] = v; };
+  auto ld2 = [&](int f) { return make_float2(ldf(f), ldf(f + 1)); };
+  auto st2 = [&](int f, float2 v) {
+    stf(f, v.x);
+    stf(f + 1, v.y);
+  };
   for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (sizeof(T) == 4)
     for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
@@ -228,24 +254,65 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
     const float prf = (float)pref, icchi = (float)(1.0 / p.cchi);
     // two samples per thread through the packed scheme, warp by warp
     for (int64_t kb = t0 - lane; 2 * kb < p.n; kb += stride) {
-      const int64_t k = kb + lane, i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
-      float g0f = 1.f, g1f = 1.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, a0 = 0.f, a1 = 0.f;
-      float w0 = 0.f, w1 = 0.f;
-      Path<float> P0{}, P1{};
-      if (i0 < p.n) {
-        a0 = focus<float>(p, i0, g0f, tx0, ty0, (VAR & kVarCell) ? &P0 : nullptr);
-        a1 = focus<float>(p, i1, g1f, tx1, ty1, (VAR & kVarCell) ? &P1 : nullptr);
-        w0 = p.weighted ? load_t<float>(p.w, i0, p.dtype) : 1.f;
-        w1 = i1 != i0 ? (p.weighted ? load_t<float>(p.w, i1, p.dtype) : 1.f) : 0.f;
-        if (!(w0 >= 0.f) || !isfinite(w0) || !isfinite(a0) || !isfinite(g0f)) w0 = 0.f;
-        if (!(w1 >= 0.f) || !isfinite(w1) || !isfinite(a1) || !isfinite(g1f)) w1 = 0.f;
+      {
+        const int64_t k = kb + lane, i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+        float g0f = 1.f, g1f = 1.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, a0 = 0.f,
+              a1 = 0.f;
+        float w0 = 0.f, w1 = 0.f;
+        Path<float> P0{}, P1{};
+        if (i0 < p.n) {
+          a0 = focus<float>(p, i0, g0f, tx0, ty0, (VAR & kVarCell) ? &P0 : nullptr);
+          a1 = focus<float>(p, i1, g1f, tx1, ty1, (VAR & kVarCell) ? &P1 : nullptr);
+          w0 = p.weighted ? load_t<float>(p.w, i0, p.dtype) : 1.f;
+          w1 = i1 != i0 ? (p.weighted ? load_t<float>(p.w, i1, p.dtype) : 1.f) : 0.f;
+          if (!(w0 >= 0.f) || !isfinite(w0) || !isfinite(a0) || !isfinite(g0f)) w0 = 0.f;
+          if (!(w1 >= 0.f) || !isfinite(w1) || !isfinite(a1) || !isfinite(g1f)) w1 = 0.f;
+        }
+        const PairConst kc =
+            pair_const<VAR>(p, make_float2(a0, a1), make_float2(g0f, g1f), P0, P1);
+        st2(0, kc.c1);
+        st2(2, kc.ca);
+        st2(4, kc.ig0);
+        st2(6, f2(0.f));
+        st2(8, f2(0.f));
+        st2(10, f2(0.5f));
+        stf(12, w0);
+        stf(13, w1);
+        if (ANG) {
+          stf(14, tx0);
+          stf(15, ty0);
+          stf(16, tx1);
+          stf(17, ty1);
+        }
+        if (VAR & kVarCell) {
+          st2(18, kc.zq0);
+          st2(20, kc.xs);
+          st2(22, kc.ys);
+          st2(24, kc.tx);
+          st2(26, kc.ty);
+        }
       }
-      const PairConst kc = pair_const<VAR>(p, make_float2(a0, a1), make_float2(g0f, g1f), P0, P1);
-      PairState st{f2(0.f), f2(0.f), f2(0.5f)};
       for (int j = 0; j < p.n_phase; ++j) {
         float2 mu, chi;
-        pair_cell<VAR>(p, reinterpret_cast<const float4*>(tab)[j], kc, st, nullptr, &mu,
-                       &chi);
+        {
+          PairConst kc;
+          kc.c1 = ld2(0);
+          kc.ca = ld2(2);
+          kc.ig0 = ld2(4);
+          if (VAR & kVarCell) {
+            kc.zq0 = ld2(18);
+            kc.xs = ld2(20);
+            kc.ys = ld2(22);
+            kc.tx = ld2(24);
+            kc.ty = ld2(26);
+          }
+          PairState st{ld2(6), ld2(8), ld2(10)};
+          pair_cell<VAR>(p, reinterpret_cast<const float4*>(tab)[j], kc, st, nullptr, &mu, &chi);
+          st2(6, st.du);
+          st2(8, st.V);
+          st2(10, st.gph);
+        }
+        const float w0 = ldf(12), w1 = ldf(13);
         const float c0 = (w0 > 0.f && chi.x > 0.f) ? __fmul_rn(__fmul_rn(prf, w0), M<float>::rcp(__fmul_rn(mu.x, mu.x))) : 0.f;
         const float c1 = (w1 > 0.f && chi.y > 0.f) ? __fmul_rn(__fmul_rn(prf, w1), M<float>::rcp(__fmul_rn(mu.y, mu.y))) : 0.f;
         // the warp's 64 emitters of this cell, staged once
@@ -256,6 +323,7 @@ __global__ void __launch_bounds__(256) k_photon(const Params p, int nb, double l
         stQ[32 + lane] = make_float4(e1.w, e1.w, e1.z, e1.z);
         if constexpr (ANG) {
           // mean square angles (A/mu = chi/(cchi mu^2)), times c
+          const float tx0 = ldf(14), ty0 = ldf(15), tx1 = ldf(16), ty1 = ldf(17);
           const float am0 = __fmul_rn(__fmul_rn(chi.x, icchi), __fmul_rn(e0.x, e0.x));
           const float am1 = __fmul_rn(__fmul_rn(chi.y, icchi), __fmul_rn(e1.x, e1.x));
           const float cone0 = __fmul_rn(e0.x, e0.x), cone1 = __fmul_rn(e1.x, e1.x);
@@ -432,11 +500,11 @@ int photon_gmax(int sms, int block, int grid_req, int64_t n) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T, int VAR, bool ANG>
-int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_io, size_t smem,
-                      double* partials, cudaStream_t st, const qs_exec* ex) {
+template <typename T, int VAR, bool ANG, int KB>
+int32_t launch_photon_kb(const Params& p, const qs_bins* pb, int block, int* grid_io, size_t smem,
+                         double* partials, cudaStream_t st, const qs_exec* ex) {
   int grid = *grid_io;
-  auto kern = k_photon<T, VAR, ANG>;
+  auto kern = k_photon<T, VAR, ANG, KB>;
   static detail::CtxMark smem_mark;
   if (int32_t e = detail::allow_smem(kern, smem_mark, detail::kSmemLimit)) return e;
   // persistent grid: the CTAs that fit at once (unless a grid was requested)
@@ -459,6 +527,20 @@ int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_i
       cudaEventRecord(static_cast<cudaEvent_t>(ex->ev_stop), st) != cudaSuccess)
     return QS_ERR_CUDA;
   return QS_OK;
+}
+
+// Bin groups per lane: 8 (up to 256 bins, and always with the angular sums),
+// else 16 (up to 512 bins).
+template <typename T, int VAR, bool ANG>
+int32_t launch_photon(const Params& p, const qs_bins* pb, int block, int* grid_io, size_t smem,
+                      double* partials, cudaStream_t st, const qs_exec* ex) {
+  if constexpr (ANG) {
+    return launch_photon_kb<T, VAR, ANG, 8>(p, pb, block, grid_io, smem, partials, st, ex);
+  } else {
+    if (pb->n_bins <= 256)
+      return launch_photon_kb<T, VAR, ANG, 8>(p, pb, block, grid_io, smem, partials, st, ex);
+    return launch_photon_kb<T, VAR, ANG, 16>(p, pb, block, grid_io, smem, partials, st, ex);
+  }
 }
 
 }  // namespace
@@ -506,8 +588,9 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   fill_params(p, laser, beam, samples, nullptr, wbits);
   double* part = static_cast<double*>(d_workspace);
   const bool loc = (laser->variant & QS_VARIANT_CELL_FOCUS) != 0;
-  const size_t smem = prec == QS_F64 ? photon_smem<double>(p.n_phase, pbins->n_bins, block, ang)
-                                     : photon_smem<float>(p.n_phase, pbins->n_bins, block, ang);
+  const size_t smem =
+      prec == QS_F64 ? photon_smem<double>(p.n_phase, pbins->n_bins, block, ang, laser->variant)
+                     : photon_smem<float>(p.n_phase, pbins->n_bins, block, ang, laser->variant);
   if (smem > (size_t)kSmemLimit) return QS_ERR_INVALID_ARG;
   if (prec == QS_F64) {
     if (ang)
