@@ -20,11 +20,11 @@
 
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 namespace qs {
 
 constexpr int kPhMaxBins = 512;               // photon-energy bins (16 per lane)
-constexpr int kPhK = kPhMaxBins / 32;
 constexpr int kPhN = 256;                     // table nodes in u = log2 y (du = 0.18: lanes on
                                               // consecutive log-spaced bins share nodes)
 constexpr double kPhUmin = -40.0, kPhUmax = 6.0;
@@ -252,10 +252,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (sizeof(T) == 4) {
     const float prf = (float)pref, icchi = (float)(1.0 / p.cchi);
-    // two samples per thread through the packed scheme, warp by warp
-    for (int64_t kb = t0 - lane; 2 * kb < p.n; kb += stride) {
+    // Work items of one warp: 64 consecutive samples (two per lane, packed)
+    // against one group of 64 bins (bins 32 kk + lane for kk = 2 g, 2 g + 1),
+    // spread over all warps of the grid in turn.  Splitting the bins this way
+    // repeats a sample's phase integration once per group (well under 1 % of
+    // the work) and gives enough small items to keep every warp busy to the
+    // end of the launch.
+    const int G = (nb + 63) / 64;
+    const int64_t items = (p.n + 63) / 64 * G;
+    const int64_t W = (int64_t)gridDim.x * nwarp;
+    for (int64_t it = (int64_t)blockIdx.x * nwarp + warp; it < items; it += W) {
+      const int64_t chunk = it / G;
+      const int grp = (int)(it - chunk * G);
       {
-        const int64_t k = kb + lane, i0 = 2 * k, i1 = (2 * k + 1 < p.n) ? 2 * k + 1 : 2 * k;
+        const int64_t i0 = 64 * chunk + 2 * lane, i1 = (i0 + 1 < p.n) ? i0 + 1 : i0;
         float g0f = 1.f, g1f = 1.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, a0 = 0.f,
               a1 = 0.f;
         float w0 = 0.f, w1 = 0.f;
@@ -338,12 +348,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         __syncwarp();
-        // lane b takes bins b and b + 32 of each group pair against every
+        // lane b takes bins b and b + 32 of the item's group against every
         // emitter (packed, independent evaluations, summed plainly over the
-        // 64, then compensated)
-#pragma unroll
-        for (int kk = 0; kk < KB; kk += 2) {
-          if (32 * kk >= nb || !(eps[32 * kk] < emax)) break;
+        // 64, then compensated); the group index is made a compile-time
+        // constant so that the bin sums stay in registers
+        auto group = [&](auto KK) {
+          constexpr int kk = decltype(KK)::value;
+          if (!(eps[32 * kk] < emax)) return;
           const int b0 = 32 * kk + lane, b1 = b0 + 32;
           const float2 e = make_float2(b0 < nb ? eps[b0] : 3.4e38f, b1 < nb ? eps[b1] : 3.4e38f);
           float2 ps = f2(0.f), px = f2(0.f), py = f2(0.f);
@@ -370,6 +381,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
             acc.add(2, kk, py.x);
             acc.add(2, kk + 1, py.y);
           }
+        };
+        using std::integral_constant;
+        switch (grp) {
+          case 0: group(integral_constant<int, 0>{}); break;
+          case 1: group(integral_constant<int, 2>{}); break;
+          case 2: group(integral_constant<int, 4>{}); break;
+          case 3: group(integral_constant<int, 6>{}); break;
+          default:
+            if constexpr (KB > 8) {
+              switch (grp) {
+                case 4: group(integral_constant<int, 8>{}); break;
+                case 5: group(integral_constant<int, 10>{}); break;
+                case 6: group(integral_constant<int, 12>{}); break;
+                default: group(integral_constant<int, 14>{}); break;
+              }
+            }
         }
         __syncwarp();
       }
@@ -491,11 +518,15 @@ int32_t check_pbins(const qs_bins* b) {
 
 // Largest grid a call may use (the workspace holds one partial spectrum per
 // CTA): the requested grid, else four CTAs per SM; never more CTAs than
-// samples in passes of two per thread.
-int photon_gmax(int sms, int block, int grid_req, int64_t n) {
-  const int64_t per = 2 * (int64_t)block;
+// there is work for.
+int photon_gmax(int sms, int block, int grid_req, int64_t n, int nb) {
   int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * 4;
-  const int64_t need = (n + per - 1) / per;
+  // FP32: warp items of 64 samples x 64 bins; FP64: one sample per thread
+  const int64_t items = (n + 63) / 64 * ((nb + 63) / 64);
+  const int64_t nw = block / 32;
+  int64_t need = (items + nw - 1) / nw;
+  const int64_t need64 = (n + block - 1) / block;
+  if (need64 > need) need = need64;
   if (g > need) g = need;
   return (int)(g < 1 ? 1 : g);
 }
@@ -556,7 +587,7 @@ extern "C" size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec*
   if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
   if (block > 256) block = 256;
   if (device_sms(&sms) != QS_OK) return 0;
-  const int g = photon_gmax(sms, block, grid, n);
+  const int g = photon_gmax(sms, block, grid, n, pbins->n_bins);
   return align_up((size_t)g * 3 * pbins->n_bins * sizeof(double), 256);
 }
 
@@ -578,7 +609,7 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
-  const int gmax = photon_gmax(sms, block, grid, samples->n);
+  const int gmax = photon_gmax(sms, block, grid, samples->n, pbins->n_bins);
   int g = gmax;
   const size_t need = align_up((size_t)gmax * 3 * pbins->n_bins * sizeof(double), 256);
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < need) return QS_ERR_WORKSPACE;
