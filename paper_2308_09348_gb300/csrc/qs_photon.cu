@@ -6,8 +6,9 @@
 //                    every cell the locally-constant-field quantum-
 //                    synchrotron spectrum at the cell's (mu, chi) is added
 //                    to the photon-energy bins, warp-cooperatively (each
-//                    lane owns bins b = lane + 32 k and takes the warp's
-//                    samples one at a time); per-CTA partials in fixed order.
+//                    lane owns bins b = lane + 32 k and takes the warp's 64
+//                    emitters of the cell one at a time); per-CTA partials in
+//                    fixed order.
 // K8 k_photon_final  one CTA: partials summed in CTA order.
 //
 // Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348, Sec. 4 (cumulative
@@ -25,6 +26,7 @@
 namespace qs {
 
 constexpr int kPhMaxBins = 512;               // photon-energy bins (16 per lane)
+constexpr int kPhK = kPhMaxBins / 32;
 constexpr int kPhN = 256;                     // table nodes in u = log2 y (du = 0.18: lanes on
                                               // consecutive log-spaced bins share nodes)
 constexpr double kPhUmin = -40.0, kPhUmax = 6.0;
@@ -78,6 +80,10 @@ __global__ void __launch_bounds__(256) k_photon_setup() {
 
 // FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
 // table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
+__device__ __forceinline__ float hermite(float h01, float h10, float h11, float v0, float d0,
+                                         float v1, float d1) {
+  return __fmaf_rn(h11, d1, __fmaf_rn(h10, d0, __fmaf_rn(h01, __fsub_rn(v1, v0), v0)));
+}
 
 // Two photon energies e (two bins of one lane) against one emitter whose
 // {1/mu, 1/mu, 2/(3 chi), 2/(3 chi)} is pq: F for both, packed f32x2 except
@@ -105,18 +111,10 @@ __device__ __forceinline__ float2 synch_F2(const float4* __restrict__ T, float2 
   const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));              // t^3 - t^2
   const float2 h10 = __fadd2_rn(fma2(t2, f2(-1.f), t), h11);         // t - 2t^2 + t^3
   const float4 a0 = T[i0], a1 = T[i0 + 1], b0 = T[i1], b1 = T[i1 + 1];
-  // the two cubic Hermite sums, packed over the two bins (the operations of
-  // hermite() in the same order, so each lane rounds as the scalar form)
-  const float2 q23 = fma2(h11, make_float2(a1.y, b1.y),
-                          fma2(h10, make_float2(a0.y, b0.y),
-                               fma2(h01, __fadd2_rn(make_float2(a1.x, b1.x),
-                                                    make_float2(-a0.x, -b0.x)),
-                                    make_float2(a0.x, b0.x))));
-  const float2 q13 = fma2(h11, make_float2(a1.w, b1.w),
-                          fma2(h10, make_float2(a0.w, b0.w),
-                               fma2(h01, __fadd2_rn(make_float2(a1.z, b1.z),
-                                                    make_float2(-a0.z, -b0.z)),
-                                    make_float2(a0.z, b0.z))));
+  const float2 q23 = make_float2(hermite(h01.x, h10.x, h11.x, a0.x, a0.y, a1.x, a1.y),
+                                 hermite(h01.y, h10.y, h11.y, b0.x, b0.y, b1.x, b1.y));
+  const float2 q13 = make_float2(hermite(h01.x, h10.x, h11.x, a0.z, a0.w, a1.z, a1.w),
+                                 hermite(h01.y, h10.y, h11.y, b0.z, b0.w, b1.z, b1.w));
   const float2 ny = mul2(y, f2((float)(-kLog2e)));
   const float2 k23 = ex2x2(__fadd2_rn(fma2(f2(-2.f / 3.f), u, q23), ny));
   const float2 ki13 = ex2x2(__fadd2_rn(q13, ny));
@@ -156,6 +154,34 @@ template <bool ANG, int KB> struct PhAcc<float, ANG, KB> {
   __device__ __forceinline__ void add(int m, int k, float x) { kahan(s[m][k], c[m][k], x); }
   __device__ __forceinline__ double get(int m, int k) const {
     return (double)s[m][k] - (double)c[m][k];
+  }
+};
+// FP32: the compensated sums in shared memory instead of registers, one
+// {sum, compensation} float pair per (warp, set, bin), in the 8-byte slots
+// of the CTA's per-warp partial spectra (which are written only after the
+// sums are final, by the same lane, at the same address).
+template <bool ANG, int KB> struct PhAccSm {
+  static constexpr int NA = ANG ? 3 : 1, K = KB;
+  float2* slot;    // this warp's part[(warp * NA + m) * nb + b] viewed as float2
+  int nb, lane;
+  __device__ __forceinline__ void init(double* part_warp, int nb_, int lane_) {
+    slot = reinterpret_cast<float2*>(part_warp);
+    nb = nb_;
+    lane = lane_;
+#pragma unroll
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (32 * k + lane < nb) slot[m * nb + 32 * k + lane] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void add(int m, int k, float x) {
+    float2 v = slot[m * nb + 32 * k + lane];
+    kahan(v.x, v.y, x);
+    slot[m * nb + 32 * k + lane] = v;
+  }
+  __device__ __forceinline__ double get(int m, int k) const {
+    const float2 v = slot[m * nb + 32 * k + lane];
+    return (double)v.x - (double)v.y;
   }
 };
 template <bool ANG, int KB> struct PhAcc<double, ANG, KB> {
@@ -210,7 +236,7 @@ template <typename T, int VAR, bool ANG, int KB>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ? 3 : 2)) k_photon(const Params p, int nb, double lo, double hi,
                                                 int log_spaced, double* __restrict__ partials) {
   using TT = typename Tab<T>::type;
-  using Acc = PhAcc<T, ANG, KB>;
+  using Acc = std::conditional_t<sizeof(T) == 4, PhAccSm<ANG, KB>, PhAcc<T, ANG, KB>>;
   constexpr int NA = Acc::NA;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t tb = ((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15;
@@ -247,25 +273,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
   const double pref = p.h * kAlpha / (2.0 * 1.7320508075688772935 * 3.14159265358979323846 *
                                       p.cchi / 1.4142135623730950488);   // h alpha a_S/(2 sqrt3 pi)
   Acc acc;
-  acc.init();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(T) == 4) acc.init(part + (size_t)warp * NA * nb, nb, lane);
+  else acc.init();
   if constexpr (sizeof(T) == 4) {
     const float prf = (float)pref, icchi = (float)(1.0 / p.cchi);
-    // Work items of one warp: 64 consecutive samples (two per lane, packed)
-    // against one group of 64 bins (bins 32 kk + lane for kk = 2 g, 2 g + 1),
-    // spread over all warps of the grid in turn.  Splitting the bins this way
-    // repeats a sample's phase integration once per group (well under 1 % of
-    // the work) and gives enough small items to keep every warp busy to the
-    // end of the launch.
-    const int G = (nb + 63) / 64;
-    const int64_t items = (p.n + 63) / 64 * G;
+    // work items of one warp: 64 consecutive samples, two per lane (packed),
+    // dealt to the grid's warps in turn
+    const int64_t items = (p.n + 63) / 64;
     const int64_t W = (int64_t)gridDim.x * nwarp;
     for (int64_t it = (int64_t)blockIdx.x * nwarp + warp; it < items; it += W) {
-      const int64_t chunk = it / G;
-      const int grp = (int)(it - chunk * G);
       {
-        const int64_t i0 = 64 * chunk + 2 * lane, i1 = (i0 + 1 < p.n) ? i0 + 1 : i0;
+        const int64_t i0 = 64 * it + 2 * lane, i1 = (i0 + 1 < p.n) ? i0 + 1 : i0;
         float g0f = 1.f, g1f = 1.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, a0 = 0.f,
               a1 = 0.f;
         float w0 = 0.f, w1 = 0.f;
@@ -348,29 +366,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         __syncwarp();
-        // lane b takes bins b and b + 32 of the item's group against every
+        // lane b takes bins b and b + 32 of each group pair against every
         // emitter (packed, independent evaluations, summed plainly over the
-        // 64, then compensated); the group index is made a compile-time
-        // constant so that the bin sums stay in registers
-        auto group = [&](auto KK) {
-          constexpr int kk = decltype(KK)::value;
-          if (!(eps[32 * kk] < emax)) return;
+        // 64, then compensated in shared memory).  No branch on the cut:
+        // bins beyond an emitter's cut are evaluated and dropped by the
+        // select (the clamped table index keeps every read in the table), so
+        // the unrolled evaluations of consecutive emitters interleave.
+#pragma unroll
+        for (int kk = 0; kk < KB; kk += 2) {
+          if (32 * kk >= nb || !(eps[32 * kk] < emax)) break;
           const int b0 = 32 * kk + lane, b1 = b0 + 32;
           const float2 e = make_float2(b0 < nb ? eps[b0] : 3.4e38f, b1 < nb ? eps[b1] : 3.4e38f);
           float2 ps = f2(0.f), px = f2(0.f), py = f2(0.f);
-#pragma unroll 2
+#pragma unroll 4
           for (int q = 0; q < 64; ++q) {
             const float4 qq = stQ[q];
             const bool in0 = e.x < qq.z, in1 = e.y < qq.z;
-            if (in0 || in1) {
-              const float2 F = synch_F2(ptab, e, stP[q]);
-              const float2 Fm = make_float2(in0 ? F.x : 0.f, in1 ? F.y : 0.f);
-              ps = fma2(make_float2(qq.x, qq.y), Fm, ps);
-              if constexpr (ANG) {
-                const float4 aq = stA[q];
-                px = fma2(make_float2(aq.x, aq.y), Fm, px);
-                py = fma2(make_float2(aq.z, aq.w), Fm, py);
-              }
+            const float2 F = synch_F2(ptab, e, stP[q]);
+            const float2 Fm = make_float2(in0 ? F.x : 0.f, in1 ? F.y : 0.f);
+            ps = fma2(make_float2(qq.x, qq.y), Fm, ps);
+            if constexpr (ANG) {
+              const float4 aq = stA[q];
+              px = fma2(make_float2(aq.x, aq.y), Fm, px);
+              py = fma2(make_float2(aq.z, aq.w), Fm, py);
             }
           }
           acc.add(0, kk, ps.x);
@@ -381,27 +399,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
             acc.add(2, kk, py.x);
             acc.add(2, kk + 1, py.y);
           }
-        };
-        using std::integral_constant;
-        switch (grp) {
-          case 0: group(integral_constant<int, 0>{}); break;
-          case 1: group(integral_constant<int, 2>{}); break;
-          case 2: group(integral_constant<int, 4>{}); break;
-          case 3: group(integral_constant<int, 6>{}); break;
-          default:
-            if constexpr (KB > 8) {
-              switch (grp) {
-                case 4: group(integral_constant<int, 8>{}); break;
-                case 5: group(integral_constant<int, 10>{}); break;
-                case 6: group(integral_constant<int, 12>{}); break;
-                default: group(integral_constant<int, 14>{}); break;
-              }
-            }
         }
         __syncwarp();
       }
     }
   } else {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double icchi = 1.0 / p.cchi;
     for (int64_t ib = t0 - lane; ib < p.n; ib += stride) {
       const int64_t i = ib + lane;
@@ -518,15 +522,11 @@ int32_t check_pbins(const qs_bins* b) {
 
 // Largest grid a call may use (the workspace holds one partial spectrum per
 // CTA): the requested grid, else four CTAs per SM; never more CTAs than
-// there is work for.
-int photon_gmax(int sms, int block, int grid_req, int64_t n, int nb) {
+// samples in passes of two per thread.
+int photon_gmax(int sms, int block, int grid_req, int64_t n) {
+  const int64_t per = 2 * (int64_t)block;
   int64_t g = grid_req > 0 ? grid_req : (int64_t)sms * 4;
-  // FP32: warp items of 64 samples x 64 bins; FP64: one sample per thread
-  const int64_t items = (n + 63) / 64 * ((nb + 63) / 64);
-  const int64_t nw = block / 32;
-  int64_t need = (items + nw - 1) / nw;
-  const int64_t need64 = (n + block - 1) / block;
-  if (need64 > need) need = need64;
+  const int64_t need = (n + per - 1) / per;
   if (g > need) g = need;
   return (int)(g < 1 ? 1 : g);
 }
@@ -587,7 +587,7 @@ extern "C" size_t qs_photon_workspace_bytes(const qs_bins* pbins, const qs_exec*
   if (exec_opts(exec, &prec, &wbits, &block, &grid) != QS_OK) return 0;
   if (block > 256) block = 256;
   if (device_sms(&sms) != QS_OK) return 0;
-  const int g = photon_gmax(sms, block, grid, n, pbins->n_bins);
+  const int g = photon_gmax(sms, block, grid, n);
   return align_up((size_t)g * 3 * pbins->n_bins * sizeof(double), 256);
 }
 
@@ -609,7 +609,7 @@ extern "C" int32_t qs_photon_spectrum(const qs_laser* laser, const qs_beam* beam
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
-  const int gmax = photon_gmax(sms, block, grid, samples->n, pbins->n_bins);
+  const int gmax = photon_gmax(sms, block, grid, samples->n);
   int g = gmax;
   const size_t need = align_up((size_t)gmax * 3 * pbins->n_bins * sizeof(double), 256);
   if (!d_workspace || ((uintptr_t)d_workspace % 256) || ws_bytes < need) return QS_ERR_WORKSPACE;
