@@ -371,6 +371,16 @@ def bench_ll(dev, rank, n=1 << 26, steps=5):
 # the path: one rsqrt (a full MUFU slot) and one ex2 (half a slot), and a net
 # 14 FMA-pipe operations.
 CELL_MUFU_SLOTS_PER_STEP = QFP_MUFU_SLOTS_PER_STEP + 1 + 0.5
+# Cycle-resolved chi (FP32): the packed update without the Gaunt and
+# second-moment fits (17 packed FMA-pipe instructions per pair of samples: 17
+# lane-operations per sample) plus the per-sample table lookup (34 FMA-pipe
+# operations: index, Hermite basis and its derivative, G, H, dG, S) = 51; MUFU:
+# the mean-energy reciprocal, the lookup's lg2 and its reciprocal = 3 slots;
+# shared memory: two 16-byte gathers per sample, 2 x 16 / 128 = 0.25
+# wavefronts per sample-step at one 128-byte wavefront per SM and clock.
+CYC_FMA_OPS_PER_STEP = 17 + 34
+CYC_MUFU_SLOTS_PER_STEP = 3
+CYC_SMEM_WAVEFRONTS_PER_STEP = 0.25
 CELL_FMA_OPS_PER_STEP = QFP_FMA_OPS_PER_STEP + 14
 
 
@@ -414,6 +424,22 @@ def bench_variant(dev, rank, variant, n=1 << 24, steps=3):
                             "peak": (peak_mufu if mufu else peak_fma) / 1e12, "unit": "Top/s",
                             "frac": max(t_mufu, t_fma) / t,
                             "mufu_frac": t_mufu / t, "fma_frac": t_fma / t}
+    else:
+        # cycle-resolved chi: per sample-step the packed state update and, per
+        # sample, the Hermite lookup of (G, H) with S from G's derivative;
+        # two 16-byte shared-memory gathers (the node-pair tables), i.e.
+        # 0.25 wavefronts of 128 B per sample-step without bank conflicts
+        sms = props.multi_processor_count
+        t_fma = CYC_FMA_OPS_PER_STEP * steps_total / peak_fma
+        t_mufu = CYC_MUFU_SLOTS_PER_STEP * steps_total / peak_mufu
+        t_smem = CYC_SMEM_WAVEFRONTS_PER_STEP * steps_total / (sms * fmax)
+        pipe = max((t_fma, "fma"), (t_mufu, "mufu"), (t_smem, "smem"))[1]
+        line["roofline"] = {"bound": "alu", "pipe": pipe,
+                            "achieved": CYC_FMA_OPS_PER_STEP * steps_total / t / 1e12,
+                            "peak": peak_fma / 1e12, "unit": "Top/s",
+                            "frac": max(t_fma, t_mufu, t_smem) / t,
+                            "fma_frac": t_fma / t, "mufu_frac": t_mufu / t,
+                            "smem_wavefront_frac": t_smem / t}
     return line
 
 

@@ -282,8 +282,11 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
   if (dH) *dH = sh1;
 }
 
-// FP32 path: one lane's cubic Hermite lookup.  A[n] = {G, G_u du, S, S_u du},
-// B[n] = {H, H_u du} at u_n = n du (the derivatives in u, times the spacing).
+// FP32 path: one lane's cubic Hermite lookup in the shared-memory tables of
+// node pairs (one 16-byte load per function instead of one per node):
+//   A[n]         = {G_n, dG_n, G_{n+1}, dG_{n+1}}
+//   A[kCycN + n] = {H_n, dH_n, H_{n+1}, dH_{n+1}},
+// at u_n = n du, the derivatives in u times the spacing.
 __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float chi, float& G,
                                              float& S, float& H) {
   const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
@@ -302,12 +305,12 @@ __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float
   const float d01 = __fmul_rn(6.f, __fsub_rn(t, t2));
   const float d10 = __fmaf_rn(3.f, t2, __fmaf_rn(-4.f, t, 1.f));
   const float d11 = __fmaf_rn(3.f, t2, __fmul_rn(-2.f, t));
-  const float4 a0 = A[idx], a1 = A[idx + 1];
-  const float dG = __fsub_rn(a1.x, a0.x);
-  G = __fmaf_rn(h11, a1.y, __fmaf_rn(h10, a0.y, __fmaf_rn(h01, dG, a0.x)));
-  H = __fmaf_rn(h11, a1.w, __fmaf_rn(h10, a0.w, __fmaf_rn(h01, __fsub_rn(a1.z, a0.z), a0.z)));
+  const float4 g = A[idx], h = A[kCycN + idx];
+  const float dG = __fsub_rn(g.z, g.x);
+  G = __fmaf_rn(h11, g.w, __fmaf_rn(h10, g.y, __fmaf_rn(h01, dG, g.x)));
+  H = __fmaf_rn(h11, h.w, __fmaf_rn(h10, h.y, __fmaf_rn(h01, __fsub_rn(h.z, h.x), h.x)));
   // chi G' = (dG/dt) chi / (du ln2 (chi + chi_s)), from the same interpolant
-  const float Gt = __fmaf_rn(d11, a1.y, __fmaf_rn(d10, a0.y, __fmul_rn(d01, dG)));
+  const float Gt = __fmaf_rn(d11, g.w, __fmaf_rn(d10, g.y, __fmul_rn(d01, dG)));
   const float k = __fmul_rn(chi, M<float>::rcp(__fmul_rn(
                                      (float)(kCycDu * 0.69314718055994530942), __fadd_rn(chi, (float)kCycChiS))));
   S = __fmaf_rn(Gt, k, __fmul_rn(2.f, G));
@@ -714,6 +717,18 @@ __device__ __forceinline__ void eval_pair_f32_qfp(const Params& p, const float4*
   finish_f32(p, i1, g1f, a1, tx1, ty1, du.y, V.y, s1);
 }
 
+// Classical closed form in FP32: mu = g0 / (1 + g0 du) from one reciprocal
+// of the rounded denominator, corrected once with its FMA residual (within
+// about two FP32 ulps; mu == g0 exactly when du == 0).  Unlike the phase
+// integration, the closed form carries no accumulated error that a
+// two-float recombination would have to preserve.
+__device__ __forceinline__ float recombine_f1(float g0, float du) {
+  const float d = __fmaf_rn(g0, du, 1.f);
+  const float r0 = M<float>::rcp(d);
+  const float q0 = __fmul_rn(g0, r0);
+  return __fmaf_rn(__fmaf_rn(-q0, d, g0), r0, q0);
+}
+
 // FP32 classical path (Eq. 3 as 1/gamma_f - 1/gamma0 = c_RR a^2).
 __device__ __forceinline__ SampleF eval_ll_f32_xi(const Params& p, float xi0, float xi1,
                                                   float xi2, float xi3, float xi4, float xi5) {
@@ -721,23 +736,22 @@ __device__ __forceinline__ SampleF eval_ll_f32_xi(const Params& p, float xi0, fl
   float gamma0, thx, thy;
   const float a = focus_xi<float>(p, xi0, xi1, xi2, xi3, xi4, xi5, gamma0, thx, thy);
   const float du = __fmul_rn(__fmul_rn(p.f.cRR, a), a);
-  float hi, lo;
-  recombine_f2(gamma0, du, hi, lo);
-  s.g0 = gamma0; s.aeff = a; s.mu_hi = hi; s.mu_lo = lo; s.V = 0.f; s.theta_e = 0.f;
+  const float mu = recombine_f1(gamma0, du);
+  s.g0 = gamma0; s.aeff = a; s.mu_hi = mu; s.mu_lo = 0.f; s.V = 0.f; s.theta_e = 0.f;
   s.thx0 = thx; s.thy0 = thy; s.tx = thx; s.ty = thy;
-  s.go_hi = hi;
-  s.go_lo = lo;
+  s.go_hi = mu;
+  s.go_lo = 0.f;
   return s;
 }
 
 // Two classical samples at once in packed f32x2 arithmetic: the same
 // operations in the same order as focus_xi<float>, the LL closed form and
-// recombine_f2 (a - b as a + (-b), 1 - d and g0 - q0 d as one fma with -1),
-// so each lane rounds exactly as the scalar path does.
+// recombine_f1 (a - b as a + (-b), g0 - q0 d as one fma of -q0), so each
+// lane rounds exactly as the scalar path does.
 __device__ __forceinline__ void eval_ll_f32x2(const Params& p, float2 xi0, float2 xi1, float2 xi2,
                                               float2 xi3, float2 xi4, float2 xi5, SampleF& s0,
                                               SampleF& s1) {
-  const float2 ONE = f2(1.f), M1 = f2(-1.f);
+  const float2 ONE = f2(1.f);
   // decode and collision geometry (focus_xi)
   const float2 x = fma2(f2(p.f.sx), xi0, f2(p.f.bdx));
   const float2 y = fma2(f2(p.f.sy), xi1, f2(p.f.bdy));
@@ -757,28 +771,16 @@ __device__ __forceinline__ void eval_ll_f32x2(const Params& p, float2 xi0, float
   const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), rcpx2(q));
   const float2 a = mul2(mul2(f2(p.f.a0), rsqrtx2(q)),
                         ex2x2(mul2(f2(-1.4426950408889634074f), E)));
-  // Eq. 3 and the two-float recombination (recombine_f2)
+  // Eq. 3 and the recombination (recombine_f1)
   const float2 du = mul2(mul2(f2(p.f.cRR), a), a);
-  const float2 pp = mul2(g0, du);
-  const float2 pe = fma2(g0, du, make_float2(-pp.x, -pp.y));
-  const float2 sm = __fadd2_rn(ONE, pp);
-  const float2 bb = __fadd2_rn(sm, M1);
-  const float2 se = __fadd2_rn(fma2(__fadd2_rn(sm, make_float2(-bb.x, -bb.y)), M1, ONE),
-                               fma2(bb, M1, pp));
-  const float2 t = __fadd2_rn(se, pe);
-  const float2 dh = __fadd2_rn(sm, t);
-  const float2 dl = fma2(fma2(sm, M1, dh), M1, t);
-  const float2 r0 = rcpx2(dh);
+  const float2 d = fma2(g0, du, ONE);
+  const float2 r0 = rcpx2(d);
   const float2 q0 = mul2(g0, r0);
-  const float2 nq0 = make_float2(-q0.x, -q0.y);
-  const float2 e2 = fma2(nq0, dl, fma2(nq0, dh, g0));
-  const float2 c = mul2(e2, r0);
-  const float2 hi = __fadd2_rn(q0, c);
-  const float2 lo = fma2(fma2(q0, M1, hi), M1, c);
-  s0.g0 = g0.x; s0.aeff = a.x; s0.mu_hi = hi.x; s0.mu_lo = lo.x; s0.V = 0.f; s0.theta_e = 0.f;
-  s0.thx0 = thx.x; s0.thy0 = thy.x; s0.tx = thx.x; s0.ty = thy.x; s0.go_hi = hi.x; s0.go_lo = lo.x;
-  s1.g0 = g0.y; s1.aeff = a.y; s1.mu_hi = hi.y; s1.mu_lo = lo.y; s1.V = 0.f; s1.theta_e = 0.f;
-  s1.thx0 = thx.y; s1.thy0 = thy.y; s1.tx = thx.y; s1.ty = thy.y; s1.go_hi = hi.y; s1.go_lo = lo.y;
+  const float2 mu = fma2(fma2(make_float2(-q0.x, -q0.y), d, g0), r0, q0);
+  s0.g0 = g0.x; s0.aeff = a.x; s0.mu_hi = mu.x; s0.mu_lo = 0.f; s0.V = 0.f; s0.theta_e = 0.f;
+  s0.thx0 = thx.x; s0.thy0 = thy.x; s0.tx = thx.x; s0.ty = thy.x; s0.go_hi = mu.x; s0.go_lo = 0.f;
+  s1.g0 = g0.y; s1.aeff = a.y; s1.mu_hi = mu.y; s1.mu_lo = 0.f; s1.V = 0.f; s1.theta_e = 0.f;
+  s1.thx0 = thx.y; s1.thy0 = thy.y; s1.tx = thx.y; s1.ty = thy.y; s1.go_hi = mu.y; s1.go_lo = 0.f;
 }
 
 __device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {

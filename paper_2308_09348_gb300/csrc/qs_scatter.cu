@@ -193,7 +193,7 @@ Smem smem_plan(const Plan& pl, int precision, int cells, int variant, bool weigh
   // {G, G, s_j, s_j} (FP32 path); then the cycle tables
   const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16) +
                      ((variant & QS_VARIANT_CYCLE_CHI) && precision == QS_F32
-                          ? (size_t)kCycN * sizeof(float4)
+                          ? (size_t)2 * kCycN * sizeof(float4)
                           : 0);
   const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
   const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
@@ -266,7 +266,7 @@ __device__ __forceinline__ size_t table_bytes(const Params& p) {
   constexpr bool cells = QFP || (VAR & kVarCell);
   constexpr bool cyc = sizeof(T) == 4 && (VAR & kVarCycle);
   return (cells ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0) +
-         (cyc ? (size_t)kCycN * sizeof(float4) : 0);
+         (cyc ? (size_t)2 * kCycN * sizeof(float4) : 0);
 }
 template <typename T, bool QFP, int VAR>
 __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem,
@@ -278,7 +278,12 @@ __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem
   if constexpr (sizeof(T) == 4 && (VAR & kVarCycle)) {
     float4* A = reinterpret_cast<float4*>(smem + (((size_t)p.n_phase * sizeof(TT) + 15) &
                                                   ~(size_t)15));
-    for (int j = threadIdx.x; j < kCycN; j += blockDim.x) A[j] = p.cyc_a[j];
+    // node-pair tables: {G_n, dG_n, G_n+1, dG_n+1}, then {H_n, dH_n, H_n+1, dH_n+1}
+    for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
+      const float4 a = p.cyc_a[j], b = p.cyc_a[j + 1];
+      A[j] = make_float4(a.x, a.y, b.x, b.y);
+      A[kCycN + j] = make_float4(a.z, a.w, b.z, b.w);
+    }
     *cA = A;
   }
 }
@@ -358,6 +363,25 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
         auto run = [&](auto weighted) {
           constexpr bool W = decltype(weighted)::value;
           for (int64_t k = t0; k < n4; k += stride) {
+            // lane 0 asks L2 for the warp's blocks of every stream two
+            // iterations ahead (bulk prefetch, no registers held), so that
+            // the loads below find their lines in L2 instead of waiting on
+            // DRAM; the range is clamped to the streams
+            if (lane == 0) {
+              const int64_t kn = k + 2 * stride;
+              if (kn < n4) {
+                const uint32_t bytes = (uint32_t)((n4 - kn < 32 ? n4 - kn : 32) * 16);
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                  const void* base = c < 6 ? p.xi[c] : (W ? p.w : nullptr);
+                  if (base)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                                     __cvta_generic_to_global(static_cast<const float4*>(base) + kn)),
+                                 "r"(bytes)
+                                 : "memory");
+                }
+              }
+            }
             float4 v[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
@@ -642,7 +666,7 @@ int32_t launch_eval(int grid, size_t tb, cudaStream_t st, const Params& p,
   auto kern = k_eval<T, QFP, VAR>;
   static CtxMark smem_mark;
   if (int32_t e = allow_smem(kern, smem_mark, kMaxPhase * (int)sizeof(float4) +
-                                 kCycN * (int)sizeof(float4))) return e;
+                                 2 * kCycN * (int)sizeof(float4))) return e;
   kern<<<grid, 256, tb, st>>>(p, o);
   return QS_OK;
 }
@@ -807,7 +831,7 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
                          ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
                          : 0) +
                     ((var & QS_VARIANT_CYCLE_CHI) && prec == QS_F32
-                         ? (size_t)kCycN * sizeof(float4)
+                         ? (size_t)2 * kCycN * sizeof(float4)
                          : 0);
   int32_t est;
   if (prec == QS_F64) {
