@@ -175,6 +175,7 @@ template <bool ANG, int KB> struct PhAccSm {
         if (32 * k + lane < nb) slot[m * nb + 32 * k + lane] = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ void add(int m, int k, float x) {
+    if (32 * k + lane >= nb) return;       // lanes past the last bin own no slot
     float2 v = slot[m * nb + 32 * k + lane];
     kahan(v.x, v.y, x);
     slot[m * nb + 32 * k + lane] = v;

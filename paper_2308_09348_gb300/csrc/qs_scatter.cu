@@ -363,25 +363,6 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
         auto run = [&](auto weighted) {
           constexpr bool W = decltype(weighted)::value;
           for (int64_t k = t0; k < n4; k += stride) {
-            // lane 0 asks L2 for the warp's blocks of every stream two
-            // iterations ahead (bulk prefetch, no registers held), so that
-            // the loads below find their lines in L2 instead of waiting on
-            // DRAM; the range is clamped to the streams
-            if (lane == 0) {
-              const int64_t kn = k + 2 * stride;
-              if (kn < n4) {
-                const uint32_t bytes = (uint32_t)((n4 - kn < 32 ? n4 - kn : 32) * 16);
-#pragma unroll
-                for (int c = 0; c < 7; ++c) {
-                  const void* base = c < 6 ? p.xi[c] : (W ? p.w : nullptr);
-                  if (base)
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
-                                     __cvta_generic_to_global(static_cast<const float4*>(base) + kn)),
-                                 "r"(bytes)
-                                 : "memory");
-                }
-              }
-            }
             float4 v[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
