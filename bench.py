@@ -38,6 +38,15 @@ UNIT = "samples/s"
 # mul, fma).
 QFP_FMA_OPS_PER_STEP = 40
 QFP_MUFU_SLOTS_PER_STEP = 2 + 2 + 1 * 0.5
+# The same cell counted from the oracle's expression of the model, evaluated
+# as written with loop invariants hoisted and products fused into adds
+# (oracle/op_count.py, checked by tests/test_op_count.py): 50 FMA-pipe
+# operations and 6.5 MUFU slots.  The kernel reaches the same quantities
+# with fewer (one reciprocal of (1 + 1.7 chi) D for both quotients, B' from
+# the logarithm already taken, g' from g and B^(-1/3), the 1/gamma state),
+# so the roofline against its own 40 is the lower, conservative fraction.
+ORACLE_CELL_FMA_OPS = 50
+ORACLE_CELL_MUFU_SLOTS = 6.5
 QFP_MUFU_MIX = {"lg2": 2, "rcp": 2, "ex2": 1}
 FMA_LANES_PER_SM = 128
 
@@ -864,7 +873,9 @@ def main():
     ur = B.unit_rates()
     sm_clk = ur["sms"] * ur["sm_max_mhz"] * 1e6
     t_meas_mufu = steps_total * sum(c / ur[k] for k, c in QFP_MUFU_MIX.items()) / sm_clk
-    t_meas_fma = steps_total * QFP_FMA_OPS_PER_STEP / ur["fma"] / sm_clk
+    # the FMA pipe's measured rate for the instruction the loop issues (the
+    # packed f32x2 FMA), in lane-operations
+    t_meas_fma = steps_total * QFP_FMA_OPS_PER_STEP / ur.get("fma2", ur["fma"]) / sm_clk
     tr = TRAFFIC_BY_SOURCE.get(kernel_source_hash())
     roof = {"bound": "alu", "pipe": bound_pipe, "achieved": achieved, "peak": peak_v,
             "unit": "Top/s", "frac": t_bound / t_k,
@@ -875,6 +886,14 @@ def main():
             "fma_frac": (fma_ops / peak_fma) / t_k, "mufu_frac": (mufu_ops / peak_mufu) / t_k,
             "measured_unit_rates": {k: round(v, 3) for k, v in ur.items()},
             "frac_of_measured_rates": max(t_meas_mufu, t_meas_fma) / t_k,
+            "ops_per_sample_step": {"fma_pipe": QFP_FMA_OPS_PER_STEP,
+                                    "mufu_slots": QFP_MUFU_SLOTS_PER_STEP,
+                                    "source": "the FP32 kernel's packed instructions"},
+            "oracle_expression_ops_per_sample_step": {"fma_pipe": ORACLE_CELL_FMA_OPS,
+                                                      "mufu_slots": ORACLE_CELL_MUFU_SLOTS},
+            "frac_vs_oracle_expression_count":
+                max(ORACLE_CELL_FMA_OPS * steps_total / peak_fma,
+                    ORACLE_CELL_MUFU_SLOTS * steps_total / peak_mufu) / t_k,
             "mufu_frac_of_measured": t_meas_mufu / t_k,
             "fma_frac_of_measured": t_meas_fma / t_k}
 
