@@ -104,7 +104,13 @@ typedef enum { QS_F32 = 0, QS_F64 = 1 } qs_dtype;
  *                  <2 cos^2 psi g(chi(psi))>, 2g + chi g' -> 2G + chi G',
  *                  h -> H(chi) = <2 sqrt2 |cos psi|^3 h(chi(psi))> (Eq. 6
  *                  written for the instantaneous field).
- *                  The gradient and batched entry points support variant 0.
+ *                  Every entry point takes every variant (the adjoint
+ *                  carries its tangents).  QS_VARIANT_CYCLE_CHI reads
+ *                  device tables of G and H that the first call using
+ *                  them on a device (context) builds: one launch and a
+ *                  wait, so make that call before any stream capture
+ *                  (what a capturing first call does is stated per entry
+ *                  point).
  */
 typedef struct qs_laser {
     double lambda_um, a0, w0_um, tau_fs;
@@ -335,7 +341,8 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *                 kernel-smoothed spectrum (n_tx = n_aeff = 0); shared bin
  *                 count, range per shot from d_ranges if not NULL (n_shots
  *                 pairs {lo, hi}, device) else bins->lo/hi
- *   max_phase     upper bound of the shots' n_phase (QFP), 1..4096
+ *   max_phase     upper bound of the n_phase of the shots that use phase
+ *                 cells (QS_MODEL_QFP or QS_VARIANT_CELL_FOCUS), 1..4096
  *   d_spectra     n_shots x n_bins doubles (row per shot), or NULL if n_bins == 0
  *   d_spec_smooth n_shots x n_bins doubles (row per shot) when
  *                 smooth_sigma_bins > 0, else ignored (may be NULL)
@@ -343,8 +350,13 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  * The workspace size (qs_batch_workspace_bytes) depends on shared_samples:
  * nonzero for the sweep form (d_offsets == NULL), whose tile slots grow with
  * n_shots x n_total / tile.
- * The call is a fixed sequence of one memset and five kernels on the stream
- * and contains no host synchronisation.
+ * Shots may mix the models and the variants; shots with a variant run in a
+ * second persistent launch over the same (shot, tile) schedule.  The call
+ * is a fixed sequence of two memsets and six kernels on the stream and
+ * contains no host synchronisation, except that the first call on a device
+ * (context) builds the QS_VARIANT_CYCLE_CHI tables (one launch and a wait);
+ * a first call made while the stream is being captured skips them, and its
+ * QS_VARIANT_CYCLE_CHI shots are invalid (W = 0, nonfinite = -1).
  */
 size_t qs_batch_workspace_bytes(int32_t n_shots, int64_t n_total, const qs_bins* bins,
                                 int32_t max_phase, const qs_exec* exec, int32_t shared_samples);
@@ -369,9 +381,16 @@ enum { QS_G_A0 = 0, QS_G_W0, QS_G_DX, QS_G_DY, QS_G_DELAY, QS_G_GAMMA, QS_G_SPRE
  * above, given the upstream gradient of L with respect to the outputs of
  * qs_scatter (adjoint of Eqs. 2, 3, 6, 8 and of the moment and smoothed-
  * spectrum reductions).  Every sample's forward evaluation is recomputed
- * with two tangents (d/d a_eff, d/d gamma0) carried through the discretised
- * phase integration -- the exact derivative of the discrete scheme -- and
- * nothing per sample is stored between the forward and this call.
+ * with tangents carried through the discretised phase integration -- the
+ * exact derivative of the discrete scheme -- and nothing per sample is
+ * stored between the forward and this call: two tangents (d/d a_eff,
+ * d/d gamma0) for variant 0 and QS_VARIANT_CYCLE_CHI (whose Gaunt and
+ * diffusion factors carry their chi-derivatives); seven under
+ * QS_VARIANT_CELL_FOCUS, whose per-cell amplitudes depend on the laser's
+ * parameters individually (d/d ln a0, W0, dx, dy, delay, divergence,
+ * gamma0).  A QS_VARIANT_CYCLE_CHI call made while the stream is being
+ * captured, before the tables exist on the device, returns
+ * QS_ERR_UNSUPPORTED before any launch.
  *   d_moments     the forward qs_moments of the same call (device)
  *   d_dL_dmoments 13 doubles (device), dL/d(each qs_moments field) in field
  *                 order; W, under, over, map_out and nonfinite do not
@@ -405,7 +424,8 @@ int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam, const qs_sam
  * Shot s's gradient equals qs_scatter_grad's for that shot alone, up to the
  * order of the reduction (tiles in order, then summed per shot); repeated
  * calls are bit-identical.  Invalid shots (as flagged by qs_scatter_batch)
- * get zeros.  Model variant 0 only.
+ * get zeros.  Shots may mix the models and the variants, as in
+ * qs_scatter_batch.
  */
 int32_t qs_scatter_grad_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_beam* d_beams,
                               const int64_t* d_offsets, const qs_samples* samples,

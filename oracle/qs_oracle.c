@@ -708,6 +708,39 @@ static qd qd_gaunt_prime(qd chi) {
     return qd_scale(qd_mul(qd_pow(B, -5.0 / 3.0), dB), -2.0 / 3.0);
 }
 
+/* Cycle-resolved factors (variant bit 1) in dual arithmetic: the same
+   128-point Gauss-Legendre cycle means as qso_cycle_factors, of the dual
+   Gaunt factor, its derivative and the second-moment factor. */
+static void qd_cycle_factors(qd chi, qd* G, qd* S, qd* H) {
+    static double x[QSO_CYC_N], w[QSO_CYC_N];
+    static int ready = 0;
+    if (!ready) {
+        qso_gauss_legendre(QSO_CYC_N, 0.0, 0.5 * QSO_PI, x, w);
+        ready = 1;
+    }
+    qd sg = qd_c(0.0), sd = qd_c(0.0), sh = qd_c(0.0);
+    for (int k = 0; k < QSO_CYC_N; ++k) {
+        double cp = cos(x[k]);
+        qd ci = qd_scale(chi, sqrt(2.0) * cp);
+        sg = qd_add(sg, qd_scale(qd_gaunt(ci), w[k] * 2.0 * cp * cp));
+        sd = qd_add(sd, qd_scale(qd_gaunt_prime(ci), w[k] * 2.0 * cp * cp * sqrt(2.0) * cp));
+        sh = qd_add(sh, qd_scale(qd_h2(ci), w[k] * 2.0 * sqrt(2.0) * cp * cp * cp));
+    }
+    double nrm = 2.0 / QSO_PI;
+    *G = qd_scale(sg, nrm);
+    *S = qd_add(qd_scale(*G, 2.0), qd_mul(chi, qd_scale(sd, nrm)));
+    *H = qd_scale(sh, nrm);
+}
+
+/* Eq. 2 at (zz, xx, yy) in dual arithmetic (per-cell focus). */
+static qd qd_focus(qd a0, qd w0, qd zR, qd zz, qd xx, qd yy) {
+    qd zq = qd_div(zz, zR);
+    qd q = qd_addc(qd_mul(zq, zq), 1.0);
+    qd rho2 = qd_add(qd_mul(xx, xx), qd_mul(yy, yy));
+    return qd_mul(qd_div(a0, qd_sqrt(q)),
+                  qd_exp(qd_scale(qd_div(rho2, qd_mul(qd_mul(w0, w0), q)), -1.0)));
+}
+
 typedef struct {
     qd gamma0, aeff, mu, V, theta_e, thx0, thy0, gout;
 } qso_dsample;
@@ -740,23 +773,51 @@ static void qso_sample_dual(const qso_laser* L, const qso_beam* B, const double*
     qd aeff = qd_mul(qd_div(a0, qd_sqrt(q)),
                      qd_exp(qd_scale(qd_div(rho2, qd_mul(qd_mul(w0, w0), q)), -1.0)));
     qd mu, V = qd_c(0.0);
-    if (L->model == 0) {
+    int N = L->n_phase;
+    double h = (c[8] - c[7]) / (double)N;
+    int cellf = (L->variant & 1) != 0, cyc = (L->variant & 2) != 0;
+    /* per-cell focus: the local amplitude of cell j along the path (as in
+       qso_focus_cells) in dual arithmetic */
+    double phic = qso_peak_phase(L, c);
+    if (L->model == 0 && !cellf) {
         mu = qd_div(gamma0, qd_addc(qd_scale(qd_mul(gamma0, qd_mul(aeff, aeff)), c[9]), 1.0));
+    } else if (L->model == 0) {
+        /* Eq. 3's exponent cell by cell (as in qso_sample_eval_x) */
+        qd acc = qd_c(0.0);
+        for (int j = 0; j < N; ++j) {
+            double phi = c[7] + ((double)j + 0.5) * h, sj = (phi - phic) / (2.0 * c[0]);
+            qd aj = qd_focus(a0, w0, zR, qd_addc(zs, -sj), qd_add(xs, qd_scale(thx, sj)),
+                             qd_add(ys, qd_scale(thy, sj)));
+            qd A = qd_scale(aj, qso_envelope(L, c, phi));
+            acc = qd_add(acc, qd_mul(A, A));
+        }
+        qd du = qd_scale(acc, (2.0 / 3.0) * c[3] * h);
+        mu = qd_div(gamma0, qd_addc(qd_mul(gamma0, du), 1.0));
     } else {
-        int N = L->n_phase;
-        double h = (c[8] - c[7]) / (double)N;
         qd du = qd_c(0.0), g_prev = qd_c(1.0);
         for (int j = 0; j < N; ++j) {
-            double G = qso_envelope(L, c, c[7] + ((double)j + 0.5) * h);
-            qd A = qd_scale(aeff, G);
+            double phi = c[7] + ((double)j + 0.5) * h;
+            double G = qso_envelope(L, c, phi);
+            qd aj = aeff;
+            if (cellf) {
+                double sj = (phi - phic) / (2.0 * c[0]);
+                aj = qd_focus(a0, w0, zR, qd_addc(zs, -sj), qd_add(xs, qd_scale(thx, sj)),
+                              qd_add(ys, qd_scale(thy, sj)));
+            }
+            qd A = qd_scale(aj, G);
             qd K = qd_scale(qd_mul(A, A), (2.0 / 3.0) * c[3]);
             qd du_mid = qd_add(du, qd_scale(qd_mul(K, g_prev), 0.5 * h));
             qd m = qd_div(gamma0, qd_addc(qd_mul(gamma0, du_mid), 1.0));
             qd chi = qd_scale(qd_mul(m, A), sqrt(2.0) / c[4]);
-            qd g = qd_gaunt(chi);
-            qd gp = qd_gaunt_prime(chi);
-            qd h2 = qd_h2(chi);
-            qd lam = qd_scale(qd_mul(qd_mul(K, m), qd_add(qd_scale(g, 2.0), qd_mul(chi, gp))), -2.0);
+            qd g, sfac, h2;
+            if (cyc) {
+                qd_cycle_factors(chi, &g, &sfac, &h2);
+            } else {
+                g = qd_gaunt(chi);
+                h2 = qd_h2(chi);
+                sfac = qd_add(qd_scale(g, 2.0), qd_mul(chi, qd_gaunt_prime(chi)));
+            }
+            qd lam = qd_scale(qd_mul(qd_mul(K, m), sfac), -2.0);
             qd D2 = qd_scale(qd_mul(qd_mul(qd_mul(K, qd_mul(m, qd_mul(m, m))), chi), h2),
                              55.0 / (16.0 * sqrt(3.0)));
             qd rv = qd_add(qd_mul(lam, V), D2);
@@ -794,7 +855,6 @@ int qso_grad(const qso_laser* L, const qso_beam* B, const qso_bins* bins, double
              const double* dL_dS, double* grad8, double* smooth, qso_moments* m) {
     int nb = bins->n_bins;
     if (nb <= 0 || bins->log_spaced || !(sigma_bins > 0)) return 1;
-    if (L->variant) return 1;              /* gradient of variant 0 only          */
     qd* S = (qd*)calloc((size_t)nb, sizeof(qd));
     if (!S) return 1;
     for (int k = 0; k < nb; ++k) S[k] = qd_c(0.0);

@@ -468,8 +468,10 @@ class Batch:
         self.bins = bins
         self.precision = precision
         self.tile, self.block, self.grid, self.grad_block = tile, block, grid, grad_block
-        self.max_phase = int(max_phase or max(int(l.n_phase) if l.model == _inputs.MODEL_QFP else 1
-                                              for l in lasers))
+        # phase cells are used by the quantum model and by the per-cell focus
+        self.max_phase = int(max_phase or max(
+            int(l.n_phase) if (l.model == _inputs.MODEL_QFP or l.variant & _inputs.VAR_CELL_FOCUS)
+            else 1 for l in lasers))
         self.d_lasers = _struct_array_to_device([make_laser(l) for l in lasers], qs_laser, dev)
         self.d_beams = _struct_array_to_device([make_beam(b) for b in beams], qs_beam, dev)
         if offsets is None:          # parameter sweep: every shot uses all samples

@@ -25,6 +25,8 @@
 #include "qs_grad.cuh"
 #include "qs_host.hpp"
 
+#include <type_traits>
+
 namespace qs {
 
 struct BatchArgs {
@@ -41,8 +43,12 @@ struct BatchArgs {
   unsigned long long* acc;      // [n_shots * (n_bins + 2)]
   unsigned long long* acc_smooth;  // [n_shots * n_bins] (smoothed spectrum) or null
   double* partials;             // [tiles * kNumMom]
-  unsigned long long* counter;  // work counter
+  unsigned long long* counter;  // [0] work counter of the variant-0 kernels,
+                                // [1] that of the model-variant kernels,
+                                // [2] nonzero if any shot uses a model variant
   int64_t max_tiles;            // tile slots in the workspace
+  const double* cyc_gl;         // cycle-resolved chi tables of this context
+  const float4* cyc_a;          // (null: shots with that variant are invalid)
   int32_t precision, pad;
 };
 
@@ -60,11 +66,14 @@ __global__ void k_bsetup(const BatchArgs a) {
   // shared samples (parameter sweep) when no offsets are given
   const int64_t o0 = a.offsets ? a.offsets[s] : 0;
   const int64_t o1 = a.offsets ? a.offsets[s + 1] : a.samples.n;
-  // (batched shots use model variant 0; a shot with another one is flagged)
-  bool ok = check_laser(L) == QS_OK && L.variant == 0 &&
+  // a model variant runs in its own kernels; cycle-resolved chi needs this
+  // context's tables
+  const bool cells = L.model == QS_MODEL_QFP || (L.variant & QS_VARIANT_CELL_FOCUS);
+  bool ok = check_laser(L) == QS_OK &&
+            (!(L.variant & QS_VARIANT_CYCLE_CHI) || (a.cyc_a && a.cyc_gl)) &&
             check_beam(B) == QS_OK && check_bins(b) == QS_OK &&
             o0 >= 0 && o1 >= o0 && o1 <= a.samples.n &&
-            (L.model != QS_MODEL_QFP || L.n_phase <= a.max_phase);
+            (!cells || L.n_phase <= a.max_phase);
   if (!ok) {
     memset(&p, 0, sizeof(Params));
     p.n = -1;                    // invalid shot
@@ -82,7 +91,10 @@ __global__ void k_bsetup(const BatchArgs a) {
   p.weighted = a.samples.w != nullptr;
   p.acc_spec = a.bins.n_bins > 0 ? a.acc + (size_t)s * (a.bins.n_bins + 2) : nullptr;
   p.acc_smooth = a.acc_smooth ? a.acc_smooth + (size_t)s * a.bins.n_bins : nullptr;
+  p.cyc_gl = a.cyc_gl;
+  p.cyc_a = a.cyc_a;
   a.tiles[s] = (p.n + a.tile - 1) / a.tile;
+  if (L.variant != 0 && a.tiles[s] > 0) a.counter[2] = 1ull;
 }
 
 __global__ void k_btable(const BatchArgs a) {
@@ -90,7 +102,7 @@ __global__ void k_btable(const BatchArgs a) {
   const int s = (int)(idx / a.max_phase), j = (int)(idx % a.max_phase);
   if (s >= a.n_shots) return;
   const Params& p = a.shot[s];
-  if (p.n < 0 || p.model != QS_MODEL_QFP || j >= p.n_phase) return;
+  if (p.n < 0 || !(p.model == QS_MODEL_QFP || p.focus) || j >= p.n_phase) return;
   if (a.precision == QS_F32)
     table_entry(p, j, static_cast<float4*>(a.tables) + (size_t)s * a.max_phase);
   else
@@ -142,8 +154,19 @@ __global__ void __launch_bounds__(1024) k_bscan(const BatchArgs a) {
   }
 }
 
-template <typename T, typename H>
-__global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const BatchArgs a) {
+// The tiles of one kind of shot: VARK = false the shots of the paper's model
+// (variant 0), VARK = true those with a model variant (the per-cell focus,
+// cycle-resolved chi: longer per-sample code, its own kernel so that the
+// variant-0 kernel keeps its register budget).  Each kernel pulls tiles from
+// its own counter and passes over the other kind's.
+template <bool VARK>
+__device__ __forceinline__ bool tile_of_kind(const Params& p) {
+  return ((p.focus != 0) || (p.cycle != 0)) == VARK;
+}
+
+template <typename T, typename H, bool VARK>
+__global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
+    k_batch(const BatchArgs a) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   Params& p = *reinterpret_cast<Params*>(smem);
@@ -165,26 +188,36 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
   unsigned long long* hsm = nsm ? reinterpret_cast<unsigned long long*>(
                                       reinterpret_cast<unsigned char*>(hs) + hist_bytes + 16)
                                 : nullptr;
+  // FP32 cycle-resolved chi: the node-pair Hermite tables after the
+  // smoothed-spectrum accumulators
+  float4* cA = VARK ? reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes +
+                                                16 + ((nsm * 8 + 15) & ~(int64_t)15))
+                    : nullptr;
   const int64_t total = a.tiles[a.n_shots];
   const int64_t nspec = a.bins.n_bins > 0 ? (int64_t)a.bins.n_bins + 2 : 0;
   const int lane = threadIdx.x & 31;
   int cur = -1;
+  if (VARK && a.counter[2] == 0ull) return;        // no shot uses a variant
 
   for (;;) {
     if (threadIdx.x == 0) {
-      const int64_t t = (int64_t)atomicAdd(a.counter, 1ull);
-      s_tile = t;
-      int s = -1;
-      if (t < total) {
-        // last shot whose first tile is <= t (shots with no tiles are skipped)
-        int lo = 0, hi = a.n_shots - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.tiles[mid] <= t) lo = mid;
-          else hi = mid - 1;
+      int64_t t;
+      int s;
+      do {
+        t = (int64_t)atomicAdd(a.counter + (VARK ? 1 : 0), 1ull);
+        s = -1;
+        if (t < total) {
+          // last shot whose first tile is <= t (shots with no tiles are skipped)
+          int lo = 0, hi = a.n_shots - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.tiles[mid] <= t) lo = mid;
+            else hi = mid - 1;
+          }
+          s = lo;
         }
-        s = lo;
-      }
+      } while (t < total && !tile_of_kind<VARK>(a.shot[s]));
+      s_tile = t;
       s_shot = s;
     }
     __syncthreads();
@@ -198,9 +231,16 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
       uint32_t* dst = reinterpret_cast<uint32_t*>(&p);
       for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
       __syncthreads();
-      if (p.model == QS_MODEL_QFP) {
+      if (p.model == QS_MODEL_QFP || p.focus) {
         const TT* tg = static_cast<const TT*>(a.tables) + (size_t)s * a.max_phase;
         for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) tab[j] = tg[j];
+      }
+      if (VARK && sizeof(T) == 4 && p.cycle) {
+        for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
+          const float4 u = p.cyc_a[j], v = p.cyc_a[j + 1];
+          cA[j] = make_float4(u.x, u.y, v.x, v.y);
+          cA[kCycN + j] = make_float4(u.z, u.w, v.z, v.w);
+        }
       }
       cur = s;
     }
@@ -214,44 +254,56 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4) ? 2 : 1) k_batch(const B
     const int64_t last = min(p.n, first + a.tile);
     // loops advance warp by warp (bounds uniform across the lanes), so that
     // the smoothed deposits run warp-cooperatively after each step
-    bool pairs = false;
-    if constexpr (sizeof(T) == 4) {
-      if (p.model == QS_MODEL_QFP) {
-        pairs = true;
-        // FP32 QFP: each thread carries samples 2k and 2k+1 (first is even)
-        for (int64_t kb = first / 2 + threadIdx.x - lane; 2 * kb < last; kb += blockDim.x) {
-          const int64_t k = kb + lane;
-          const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
-          DepF d0, d1;
-          bool ok0 = false, ok1 = false;
-          if (i0 < last) {
-            SampleF s0, s1;
-            eval_pair_f32_qfp(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1);
-            ok0 = accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
-            if (i1 != i0)
-              ok1 = accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
-            dep_set(d0, s0);
-            dep_set(d1, s1);
-          }
-          if (hsm) {
-            deposit_warp(p, ok0, d0, i0, hsm);
-            deposit_warp(p, ok1, d1, i1, hsm);
+    auto run = [&](auto tvar) {
+      constexpr int VAR = decltype(tvar)::value;
+      bool pairs = false;
+      if constexpr (sizeof(T) == 4) {
+        if (p.model == QS_MODEL_QFP) {
+          pairs = true;
+          // FP32 QFP: each thread carries samples 2k and 2k+1 (first is even)
+          for (int64_t kb = first / 2 + threadIdx.x - lane; 2 * kb < last; kb += blockDim.x) {
+            const int64_t k = kb + lane;
+            const int64_t i0 = 2 * k, i1 = (2 * k + 1 < last) ? 2 * k + 1 : 2 * k;
+            DepF d0, d1;
+            bool ok0 = false, ok1 = false;
+            if (i0 < last) {
+              SampleF s0, s1;
+              eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
+              ok0 = accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
+              if (i1 != i0)
+                ok1 = accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
+              dep_set(d0, s0);
+              dep_set(d1, s1);
+            }
+            if (hsm) {
+              deposit_warp(p, ok0, d0, i0, hsm);
+              deposit_warp(p, ok1, d1, i1, hsm);
+            }
           }
         }
       }
-    }
-    if (!pairs) {
-      for (int64_t ib = first + threadIdx.x - lane; ib < last; ib += blockDim.x) {
-        const int64_t i = ib + lane;
-        typename DepT<T>::type d;
-        bool ok = false;
-        if (i < last) {
-          const auto sm = p.model == QS_MODEL_QFP ? eval_one<T, true>(p, tab, i)
-                                                  : eval_one<T, false>(p, tab, i);
-          ok = accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
-          dep_set(d, sm);
+      if (!pairs) {
+        for (int64_t ib = first + threadIdx.x - lane; ib < last; ib += blockDim.x) {
+          const int64_t i = ib + lane;
+          typename DepT<T>::type d;
+          bool ok = false;
+          if (i < last) {
+            const auto sm = p.model == QS_MODEL_QFP ? eval_one<T, true, VAR>(p, tab, i, cA)
+                                                    : eval_one<T, false, VAR & kVarCell>(p, tab, i, cA);
+            ok = accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
+            dep_set(d, sm);
+          }
+          if (hsm) deposit_warp(p, ok, d, i, hsm);
         }
-        if (hsm) deposit_warp(p, ok, d, i, hsm);
+      }
+    };
+    if constexpr (!VARK) {
+      run(std::integral_constant<int, 0>{});
+    } else {
+      switch ((p.focus ? kVarCell : 0) | (p.cycle ? kVarCycle : 0)) {
+        case kVarCell: run(std::integral_constant<int, kVarCell>{}); break;
+        case kVarCycle: run(std::integral_constant<int, kVarCycle>{}); break;
+        default: run(std::integral_constant<int, kVarCell | kVarCycle>{}); break;
       }
     }
     block_reduce_write(acc, red, a.partials + (size_t)t * kNumMom);
@@ -352,10 +404,10 @@ constexpr int kBGradStageBins = 8192;
 // reduced in a fixed order into its own slot.
 //   moms: the forward moments (n_shots); dLdm: n_shots x 13; dLdS: n_shots x
 //   n_bins or null.
-template <typename T>
-__global__ void __launch_bounds__(512) k_bgrad(const BatchArgs a, const qs_moments* __restrict__ moms,
-                                               const double* __restrict__ dLdm,
-                                               const double* __restrict__ dLdS) {
+template <typename T, bool VARK>
+__global__ void __launch_bounds__(VARK ? 256 : 512)
+    k_bgrad(const BatchArgs a, const qs_moments* __restrict__ moms,
+            const double* __restrict__ dLdm, const double* __restrict__ dLdS) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   Params& p = *reinterpret_cast<Params*>(smem);
@@ -372,25 +424,33 @@ __global__ void __launch_bounds__(512) k_bgrad(const BatchArgs a, const qs_momen
   const bool smooth = dLdS != nullptr && a.bins.smooth_sigma_bins > 0.0;
   const bool stage = smooth && sizeof(T) == 4 && nb <= kBGradStageBins;
   T* sdS = reinterpret_cast<T*>(after_red + 16);
+  // FP32 cycle-resolved chi: the node-pair Hermite tables after the stage
+  float4* cA = reinterpret_cast<float4*>(
+      after_red + 16 + (((stage ? (size_t)nb * sizeof(T) : 0) + 15) & ~(size_t)15));
   const int64_t total = a.tiles[a.n_shots];
   int cur = -1;
   Seeds<T> sd{};
   T w0 = (T)1;
+  if (VARK && a.counter[2] == 0ull) return;        // no shot uses a variant
 
   for (;;) {
     if (threadIdx.x == 0) {
-      const int64_t t = (int64_t)atomicAdd(a.counter, 1ull);
-      s_tile = t;
-      int sh = -1;
-      if (t < total) {
-        int lo = 0, hi = a.n_shots - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.tiles[mid] <= t) lo = mid;
-          else hi = mid - 1;
+      int64_t t;
+      int sh;
+      do {
+        t = (int64_t)atomicAdd(a.counter + (VARK ? 1 : 0), 1ull);
+        sh = -1;
+        if (t < total) {
+          int lo = 0, hi = a.n_shots - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.tiles[mid] <= t) lo = mid;
+            else hi = mid - 1;
+          }
+          sh = lo;
         }
-        sh = lo;
-      }
+      } while (t < total && !tile_of_kind<VARK>(a.shot[sh]));
+      s_tile = t;
       s_shot = sh;
     }
     __syncthreads();
@@ -403,9 +463,16 @@ __global__ void __launch_bounds__(512) k_bgrad(const BatchArgs a, const qs_momen
       uint32_t* dst = reinterpret_cast<uint32_t*>(&p);
       for (int k = threadIdx.x; k < nw; k += blockDim.x) dst[k] = src[k];
       __syncthreads();
-      if (p.model == QS_MODEL_QFP) {
+      if (p.model == QS_MODEL_QFP || p.focus) {
         const TT* tg = static_cast<const TT*>(a.tables) + (size_t)s * a.max_phase;
         for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) tab[j] = tg[j];
+      }
+      if (VARK && sizeof(T) == 4 && p.cycle) {
+        for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
+          const float4 u = p.cyc_a[j], v = p.cyc_a[j + 1];
+          cA[j] = make_float4(u.x, u.y, v.x, v.y);
+          cA[kCycN + j] = make_float4(u.z, u.w, v.z, v.w);
+        }
       }
       if (stage)
         for (int k = threadIdx.x; k < nb; k += blockDim.x) sdS[k] = (T)dLdS[(size_t)s * nb + k];
@@ -420,20 +487,29 @@ __global__ void __launch_bounds__(512) k_bgrad(const BatchArgs a, const qs_momen
     const int64_t last = min(p.n, first + a.tile);
     const int64_t tid = threadIdx.x, nthr = blockDim.x;
     const double* gS = smooth ? dLdS + (size_t)s * nb : nullptr;
-    if (p.model == QS_MODEL_QFP) {
+    auto run = [&](auto tqfp, auto tvar) {
+      constexpr bool Q = decltype(tqfp)::value;
+      constexpr int VAR = decltype(tvar)::value;
       if (!smooth)
-        grad_range<T, true, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, first, last, tid, nthr);
+        grad_range<T, Q, T, VAR>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, first, last,
+                                 tid, nthr, cA);
       else if (stage)
-        grad_range<T, true, T>(p, tab, sd, sdS, w0, acc, first, last, tid, nthr);
+        grad_range<T, Q, T, VAR>(p, tab, sd, sdS, w0, acc, first, last, tid, nthr, cA);
       else
-        grad_range<T, true, double>(p, tab, sd, gS, w0, acc, first, last, tid, nthr);
+        grad_range<T, Q, double, VAR>(p, tab, sd, gS, w0, acc, first, last, tid, nthr, cA);
+    };
+    using std::integral_constant;
+    using Tr = std::true_type;
+    using Fa = std::false_type;
+    if constexpr (!VARK) {
+      if (p.model == QS_MODEL_QFP) run(Tr{}, integral_constant<int, 0>{});
+      else run(Fa{}, integral_constant<int, 0>{});
     } else {
-      if (!smooth)
-        grad_range<T, false, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, first, last, tid, nthr);
-      else if (stage)
-        grad_range<T, false, T>(p, tab, sd, sdS, w0, acc, first, last, tid, nthr);
-      else
-        grad_range<T, false, double>(p, tab, sd, gS, w0, acc, first, last, tid, nthr);
+      const int var = (p.focus ? kVarCell : 0) | (p.cycle ? kVarCycle : 0);
+      if (p.model != QS_MODEL_QFP) run(Fa{}, integral_constant<int, kVarCell>{});
+      else if (var == kVarCell) run(Tr{}, integral_constant<int, kVarCell>{});
+      else if (var == kVarCycle) run(Tr{}, integral_constant<int, kVarCycle>{});
+      else run(Tr{}, integral_constant<int, kVarCell | kVarCycle>{});
     }
     grad_block_reduce(acc, red, a.partials + (size_t)t * kNumMom);
     __syncthreads();
@@ -481,7 +557,7 @@ bool batch_plan(BatchPlan& bp, int32_t n_shots, int64_t n_total, const qs_bins* 
   bp.max_tiles = shared ? (int64_t)n_shots * ((n_total + tile - 1) / tile) + 1
                         : n_total / tile + n_shots + 1;
   size_t off = 0;
-  bp.off_counter = off; off = align_up(off + 8, 256);
+  bp.off_counter = off; off = align_up(off + 3 * 8, 256);
   bp.off_params = off; off = align_up(off + (size_t)n_shots * sizeof(Params), 256);
   bp.off_tiles = off; off = align_up(off + (size_t)(n_shots + 1) * 8, 256);
   bp.off_tables = off;
@@ -508,22 +584,32 @@ int32_t batch_checks(int32_t n_shots, const qs_samples* samples, const qs_bins* 
 }
 
 template <typename T, typename H>
-int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaStream_t st) {
+int32_t launch_batch_kind(const BatchArgs& a, int block, int grid_req, int sms, cudaStream_t st,
+                          bool vark) {
   using TT = typename Tab<T>::type;
   const size_t smem = align_up(sizeof(Params), 16) + align_up((size_t)a.max_phase * sizeof(TT), 16) +
                       (size_t)(block / 32) * kNumMom * sizeof(double) +
                       align_up((size_t)(a.bins.n_bins > 0 ? a.bins.n_bins + 2 : 0) * sizeof(H), 16) +
-                      16 + (a.acc_smooth ? (size_t)a.bins.n_bins * 8 : 0);
+                      16 + (a.acc_smooth ? align_up((size_t)a.bins.n_bins * 8, 16) : 0) +
+                      (vark && sizeof(T) == 4 ? (size_t)2 * kCycN * sizeof(float4) : 0);
   if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
-  auto kern = k_batch<T, H>;
-  static CtxMark smem_mark;
-  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
+  auto kern = vark ? k_batch<T, H, true> : k_batch<T, H, false>;
+  static CtxMark smem_mark[2];
+  if (int32_t e = allow_smem(kern, smem_mark[vark ? 1 : 0], kSmemLimit)) return e;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return cuda_fail();
   const int grid = grid_req > 0 ? grid_req : sms * (occ > 0 ? occ : 1);
   kern<<<grid, block, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+// The variant-0 kernel, then the model-variant kernel (which returns at once
+// when no shot uses a variant).
+template <typename T, typename H>
+int32_t launch_batch(const BatchArgs& a, int block, int grid_req, int sms, cudaStream_t st) {
+  if (int32_t e = launch_batch_kind<T, H>(a, block, grid_req, sms, st, false)) return e;
+  return launch_batch_kind<T, H>(a, block, grid_req, sms, st, true);
 }
 
 }  // namespace
@@ -580,7 +666,19 @@ int32_t batch_prepare(BatchArgs& a, int32_t n_shots, const qs_laser* d_lasers,
   a.counter = reinterpret_cast<unsigned long long*>(ws + bp.off_counter);
   a.max_tiles = bp.max_tiles;
   a.precision = prec;
-  if (cudaMemsetAsync(ws + bp.off_counter, 0, 8, cs) != cudaSuccess) return cuda_fail();
+  // this context's cycle-resolved chi tables, built here on first use unless
+  // the stream is being captured (then shots with that variant are invalid)
+  {
+    Params tp;
+    const int32_t e = cycle_tables(tp, cs);
+    if (e == QS_OK) {
+      a.cyc_gl = tp.cyc_gl;
+      a.cyc_a = tp.cyc_a;
+    } else if (e != QS_ERR_UNSUPPORTED) {
+      return e;
+    }
+  }
+  if (cudaMemsetAsync(ws + bp.off_counter, 0, 3 * 8, cs) != cudaSuccess) return cuda_fail();
   if (zero_acc && bp.off_part > bp.off_acc &&
       cudaMemsetAsync(ws + bp.off_acc, 0, bp.off_part - bp.off_acc, cs) != cudaSuccess)
     return cuda_fail();
@@ -592,24 +690,35 @@ int32_t batch_prepare(BatchArgs& a, int32_t n_shots, const qs_laser* d_lasers,
 }
 
 template <typename T>
-int32_t launch_bgrad(const BatchArgs& a, int block, int grid_req, int sms, const qs_moments* mom,
-                     const double* dLdm, const double* dLdS, cudaStream_t st) {
+int32_t launch_bgrad_kind(const BatchArgs& a, int block, int grid_req, int sms,
+                          const qs_moments* mom, const double* dLdm, const double* dLdS,
+                          cudaStream_t st, bool vark) {
   using TT = typename Tab<T>::type;
   const bool stage = dLdS && a.bins.smooth_sigma_bins > 0 && sizeof(T) == 4 &&
                      a.bins.n_bins <= kBGradStageBins;
+  if (vark && block > 256) block = 256;
   const size_t smem = align_up(sizeof(Params), 16) + align_up((size_t)a.max_phase * sizeof(TT), 16) +
                       align_up((size_t)(block / 32) * kNumGrad * sizeof(double), 16) + 16 +
-                      (stage ? (size_t)a.bins.n_bins * sizeof(T) : 0);
+                      align_up(stage ? (size_t)a.bins.n_bins * sizeof(T) : 0, 16) +
+                      (vark && sizeof(T) == 4 ? (size_t)2 * kCycN * sizeof(float4) : 0);
   if (smem > (size_t)kSmemLimit) return QS_ERR_UNSUPPORTED;
-  auto kern = k_bgrad<T>;
-  static CtxMark smem_mark;
-  if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
+  auto kern = vark ? k_bgrad<T, true> : k_bgrad<T, false>;
+  static CtxMark smem_mark[2];
+  if (int32_t e = allow_smem(kern, smem_mark[vark ? 1 : 0], kSmemLimit)) return e;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess)
     return cuda_fail();
   const int grid = grid_req > 0 ? grid_req : sms * (occ > 0 ? occ : 1);
   kern<<<grid, block, smem, st>>>(a, mom, dLdm, dLdS);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+template <typename T>
+int32_t launch_bgrad(const BatchArgs& a, int block, int grid_req, int sms, const qs_moments* mom,
+                     const double* dLdm, const double* dLdS, cudaStream_t st) {
+  if (int32_t e = launch_bgrad_kind<T>(a, block, grid_req, sms, mom, dLdm, dLdS, st, false))
+    return e;
+  return launch_bgrad_kind<T>(a, block, grid_req, sms, mom, dLdm, dLdS, st, true);
 }
 
 }  // namespace

@@ -16,6 +16,7 @@
 #include "qs_host.hpp"
 
 #include <cmath>
+#include <type_traits>
 
 namespace qs {
 
@@ -23,18 +24,40 @@ namespace qs {
 // memory (FP32 path); larger ones are read from global memory.
 constexpr int kGradStageBins = 8192;
 
-template <typename T, bool QFP>
-__global__ void __launch_bounds__(512) k_grad(const Params p, const qs_moments* __restrict__ mom,
-                                              const double* __restrict__ dLdm,
-                                              const double* __restrict__ dLdS) {
+// Shared memory of k_grad: the phase table (the quantum model or the
+// per-cell focus), FP32 cycle-resolved chi's node-pair Hermite tables, the
+// reduction scratch and (FP32) the staged upstream spectrum gradient.
+template <typename T, bool QFP, int VAR>
+__host__ __device__ constexpr bool grad_has_table() { return QFP || (VAR & kVarCell) != 0; }
+template <typename T, int VAR>
+__host__ __device__ constexpr size_t grad_cyc_bytes() {
+  return (sizeof(T) == 4 && (VAR & kVarCycle) != 0) ? (size_t)2 * kCycN * sizeof(float4) : 0;
+}
+
+template <typename T, bool QFP, int VAR>
+__global__ void __launch_bounds__(VAR == 0 ? 512 : 256)
+    k_grad(const Params p, const qs_moments* __restrict__ mom, const double* __restrict__ dLdm,
+           const double* __restrict__ dLdS) {
   using TT = typename Tab<T>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   TT* tab = reinterpret_cast<TT*>(smem);
-  const size_t tab_bytes = QFP ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
-  double* red = reinterpret_cast<double*>(smem + tab_bytes);
-  T* sdS = reinterpret_cast<T*>(smem + tab_bytes + (size_t)(blockDim.x >> 5) * kNumGrad * sizeof(double));
-  if (QFP)
+  const size_t tab_bytes =
+      grad_has_table<T, QFP, VAR>() ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0;
+  float4* cA = reinterpret_cast<float4*>(smem + tab_bytes);
+  const size_t cyc_bytes = grad_cyc_bytes<T, VAR>();
+  double* red = reinterpret_cast<double*>(smem + tab_bytes + cyc_bytes);
+  T* sdS = reinterpret_cast<T*>(smem + tab_bytes + cyc_bytes +
+                                (size_t)(blockDim.x >> 5) * kNumGrad * sizeof(double));
+  if (grad_has_table<T, QFP, VAR>())
     for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
+  if constexpr (grad_cyc_bytes<T, VAR>() > 0) {
+    // node-pair tables {G_n, dG_n, G_n+1, dG_n+1}, then {H_n, dH_n, H_n+1, dH_n+1}
+    for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
+      const float4 a = p.cyc_a[j], b = p.cyc_a[j + 1];
+      cA[j] = make_float4(a.x, a.y, b.x, b.y);
+      cA[kCycN + j] = make_float4(a.z, a.w, b.z, b.w);
+    }
+  }
   // FP32 path: the upstream gradient of the smoothed spectrum staged in
   // shared memory as floats when it is small
   const bool smooth = dLdS != nullptr && p.smooth_sigma > 0.0;
@@ -51,11 +74,12 @@ __global__ void __launch_bounds__(512) k_grad(const Params p, const qs_moments* 
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   if (!smooth)
-    grad_range<T, QFP, T>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, 0, p.n, tid, nthr);
+    grad_range<T, QFP, T, VAR>(p, tab, sd, static_cast<const T*>(nullptr), w0, acc, 0, p.n, tid,
+                               nthr, cA);
   else if (sizeof(T) == 4 && p.n_bins <= kGradStageBins)
-    grad_range<T, QFP, T>(p, tab, sd, sdS, w0, acc, 0, p.n, tid, nthr);
+    grad_range<T, QFP, T, VAR>(p, tab, sd, sdS, w0, acc, 0, p.n, tid, nthr, cA);
   else
-    grad_range<T, QFP, double>(p, tab, sd, dLdS, w0, acc, 0, p.n, tid, nthr);
+    grad_range<T, QFP, double, VAR>(p, tab, sd, dLdS, w0, acc, 0, p.n, tid, nthr, cA);
 
   // fixed-order block reduction into this CTA's slot
   grad_block_reduce(acc, red, p.partials + (size_t)blockIdx.x * kNumMom);
@@ -81,17 +105,19 @@ using namespace qs::detail;
 
 namespace {
 
-template <typename T, bool QFP>
+template <typename T, bool QFP, int VAR>
 int32_t launch_grad(const Params& p, int block, int sms, int grid_req, int gmax,
                     const qs_moments* mom, const double* dLdm, const double* dLdS,
                     cudaStream_t st, int* grid_out) {
   using TT = typename Tab<T>::type;
-  const size_t tab = QFP ? align_up((size_t)p.n_phase * sizeof(TT), 16) : 0;
+  const size_t tab =
+      grad_has_table<T, QFP, VAR>() ? align_up((size_t)p.n_phase * sizeof(TT), 16) : 0;
   const bool stage = sizeof(T) == 4 && dLdS != nullptr && p.smooth_sigma > 0.0 &&
                      p.n_bins <= kGradStageBins;
-  const size_t smem = tab + (size_t)(block / 32) * kNumGrad * sizeof(double) +
+  const size_t smem = tab + grad_cyc_bytes<T, VAR>() +
+                      (size_t)(block / 32) * kNumGrad * sizeof(double) +
                       (stage ? (size_t)p.n_bins * sizeof(float) : 0);
-  auto kern = k_grad<T, QFP>;
+  auto kern = k_grad<T, QFP, VAR>;
   static CtxMark smem_mark;
   if (int32_t e = allow_smem(kern, smem_mark, kSmemLimit)) return e;
   int occ = 0;
@@ -115,7 +141,6 @@ extern "C" int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam,
   if ((st = validate_laser(laser)) || (st = validate_beam(beam)) ||
       (st = validate_samples(samples)) || (st = validate_bins(bins)))
     return st;
-  if (laser->variant != 0) return QS_ERR_UNSUPPORTED;
   int prec, wbits, block, grid, sms;
   if ((st = exec_opts(exec, &prec, &wbits, &block, &grid))) return st;
   if (!d_moments || !d_dL_dmoments || !d_grad8) return QS_ERR_INVALID_ARG;
@@ -130,21 +155,39 @@ extern "C" int32_t qs_scatter_grad(const qs_laser* laser, const qs_beam* beam,
   p.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(d_workspace) + pl.off_part);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   const bool qfp = laser->model == QS_MODEL_QFP;
-  // FP32 QFP, block left open: one 512-thread CTA per SM (118 registers).
-  // CTAs that share an SM are served oldest first and finish far apart, so
-  // a single CTA keeps all its warps resident to the end of the launch.
-  const int kblock = (!(exec && exec->block) && prec == QS_F32 && qfp) ? 512 : block;
+  const int var = laser->variant;
+  if ((var & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
+  // FP32 QFP variant 0, block left open: one 512-thread CTA per SM (118
+  // registers).  CTAs that share an SM are served oldest first and finish far
+  // apart, so a single CTA keeps all its warps resident to the end of the
+  // launch.  The model variants carry more tangents: 256-thread CTAs.
+  int kblock = block;
+  if (!(exec && exec->block) && prec == QS_F32 && qfp && var == 0) kblock = 512;
+  if (var != 0 && kblock > 256) kblock = 256;
   int g = 1;
-  if (prec == QS_F64)
-    st = qfp ? launch_grad<double, true>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
-                                         d_dL_dsmooth, cs, &g)
-             : launch_grad<double, false>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
-                                          d_dL_dsmooth, cs, &g);
-  else
-    st = qfp ? launch_grad<float, true>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
-                                        d_dL_dsmooth, cs, &g)
-             : launch_grad<float, false>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
-                                         d_dL_dsmooth, cs, &g);
+  auto run = [&](auto tq, auto tqfp, auto tvar) {
+    using T = decltype(tq);
+    constexpr bool Q = decltype(tqfp)::value;
+    constexpr int VAR = decltype(tvar)::value;
+    return launch_grad<T, Q, VAR>(p, kblock, sms, grid, pl.gmax, d_moments, d_dL_dmoments,
+                                  d_dL_dsmooth, cs, &g);
+  };
+  using std::integral_constant;
+  using F = std::false_type;
+  using Tr = std::true_type;
+  auto by_var = [&](auto tq) {
+    if (!qfp) {
+      if (var & QS_VARIANT_CELL_FOCUS) return run(tq, F{}, integral_constant<int, 1>{});
+      return run(tq, F{}, integral_constant<int, 0>{});
+    }
+    switch (var) {
+      case 1: return run(tq, Tr{}, integral_constant<int, 1>{});
+      case 2: return run(tq, Tr{}, integral_constant<int, 2>{});
+      case 3: return run(tq, Tr{}, integral_constant<int, 3>{});
+      default: return run(tq, Tr{}, integral_constant<int, 0>{});
+    }
+  };
+  st = prec == QS_F64 ? by_var(0.0) : by_var(0.0f);
   if (st) return st;
   k_grad_final<<<1, 32, 0, cs>>>(p, g, d_grad8);
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;

@@ -1,9 +1,11 @@
 // qs_grad.cuh -- device side of the adjoint of the beam phase-space
 // integration, shared by the single-shot (qs_scatter_grad) and batched
 // (qs_scatter_grad_batch) kernels: the discretised phase integration with
-// two tangents (d/d a_eff, d/d gamma0), a sample's decode and focus with the
-// derivatives of ln a_eff, the sample's share of the upstream gradient and
-// the chain rule to the 8 parameters, and the fixed-order reductions.
+// two tangents (d/d a_eff, d/d gamma0), or seven for the per-cell focus
+// (every cell's amplitude depends on the geometry in its own way), a
+// sample's decode and focus with the derivatives of ln a_eff, the sample's
+// share of the upstream gradient and the chain rule to the 8 parameters, and
+// the fixed-order reductions.
 //
 // Paper: Amaro & Vranic, "QScatter", arXiv 2308.09348 -- Eqs. 2, 3, 6, 8 and
 // the reconstruction use of Sec. 6.
@@ -42,11 +44,93 @@ __device__ __forceinline__ void tab_g(const double* t, int j, double& G, double&
 //   B'' = 8.16/(1+1.7chi) - 5.712/(1+1.7chi)^2 + 4.88,
 //   h2 = g R, R = N/D (the rational second-moment fit),
 //   h2' = g' R + g (N' - R D')/D.
-template <typename T>
+// Cycle-resolved factors and their chi-derivatives (QS_VARIANT_CYCLE_CHI):
+// g -> G, g' -> G', 2g + chi g' -> S = 2G + chi G', its derivative
+// S' = 3G' + chi G'', h -> H, h' -> H'.  FP64: the Gauss-Legendre cycle
+// means; FP32: the node-pair Hermite tables (shared memory), differentiated
+// through the interpolant in u = log2(1 + chi/chi_s):
+//   dG/dchi = G_u u',  d2G/dchi2 = G_uu u'^2 + G_u u'',
+//   u' = 1/(ln2 (chi + chi_s)),  u'' = -ln2 u'^2.
+__device__ __forceinline__ void cycle_derivs(const Params& p, const float4* __restrict__ A,
+                                             double chi, double& g, double& gp, double& s,
+                                             double& s_chi, double& h2, double& h2p) {
+  (void)A;
+  double dG, dS, dH;
+  cycle_factors_d(p.cyc_gl, chi, g, s, h2, &dG, &dS, &dH);
+  gp = dG;
+  s_chi = dS;
+  h2p = dH;
+}
+__device__ __forceinline__ void cycle_derivs(const Params& p, const float4* __restrict__ A,
+                                             float chi, float& g, float& gp, float& s,
+                                             float& s_chi, float& h2, float& h2p) {
+  (void)p;
+  const float LN2 = 0.69314718055994530942f;
+  const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
+  const float x = fminf(fmaxf(u * (float)(1.0 / kCycDu), 0.f), (float)(kCycN - 1) - 1e-3f);
+  const float xm = (x - 0.5f) + 12582912.f;
+  const int idx = __float_as_int(xm) - 0x4B400000;
+  const float t = x - (xm - 12582912.f), t2 = t * t;
+  const float4 gg = A[idx], hh = A[kCycN + idx];
+  const float dGv = gg.z - gg.x, dHv = hh.z - hh.x;
+  // value, t-derivative and second t-derivative of the cubic Hermite basis
+  const float h01 = t2 * (3.f - 2.f * t), h10 = t - 2.f * t2 + t2 * t, h11 = t2 * t - t2;
+  const float d01 = 6.f * (t - t2), d10 = 1.f - 4.f * t + 3.f * t2, d11 = 3.f * t2 - 2.f * t;
+  const float e01 = 6.f - 12.f * t, e10 = 6.f * t - 4.f, e11 = 6.f * t - 2.f;
+  g = gg.x + h01 * dGv + h10 * gg.y + h11 * gg.w;
+  h2 = hh.x + h01 * dHv + h10 * hh.y + h11 * hh.w;
+  const float Gt = d01 * dGv + d10 * gg.y + d11 * gg.w;
+  const float Gtt = e01 * dGv + e10 * gg.y + e11 * gg.w;
+  const float Ht = d01 * dHv + d10 * hh.y + d11 * hh.w;
+  const float up = M<float>::rcp(LN2 * (chi + (float)kCycChiS));      // du/dchi
+  const float idu = (float)(1.0 / kCycDu);
+  gp = Gt * idu * up;
+  const float gpp = Gtt * idu * idu * up * up - Gt * idu * LN2 * up * up;
+  h2p = Ht * idu * up;
+  s = 2.f * g + chi * gp;
+  s_chi = 3.f * gp + chi * gpp;
+}
+
+// g, g', 2g + chi g', its chi-derivative, h and h' at chi: the closed forms
+// of the fits, or (VAR & kVarCycle) their cycle means.
+template <typename T, int VAR>
+__device__ __forceinline__ void cell_factors(const Params& p, const float4* __restrict__ cA, T chi,
+                                             T& g, T& gp, T& s, T& s_chi, T& h2, T& h2p) {
+  if constexpr ((VAR & kVarCycle) != 0) {
+    cycle_derivs(p, cA, chi, g, gp, s, s_chi, h2, h2p);
+  } else {
+    const T LN2 = (T)0.69314718055994530942;
+    const T x1 = (T)1 + (T)1.7 * chi;
+    const T l1 = M<T>::lg2(x1);
+    const T L1 = LN2 * l1;
+    const T r1 = M<T>::ex2(-l1);
+    const T opc = (T)1 + chi;
+    const T B = (T)1 + (T)4.8 * opc * L1 + (T)2.44 * chi * chi;
+    const T t = M<T>::ex2((T)(-1.0 / 3.0) * M<T>::lg2(B));
+    g = t * t;
+    const T iB = t * t * t;
+    const T Bp = (T)4.8 * L1 + (T)8.16 * opc * r1 + (T)4.88 * chi;
+    const T Bpp = (T)8.16 * r1 - (T)5.712 * r1 * r1 + (T)4.88;
+    gp = (T)(-2.0 / 3.0) * g * iB * Bp;
+    const T gpp = (T)(10.0 / 9.0) * g * iB * iB * Bp * Bp - (T)(2.0 / 3.0) * g * iB * Bpp;
+    s = (T)2 * g + chi * gp;
+    s_chi = (T)3 * gp + chi * gpp;
+    const T Nh = (T)1 + chi * ((T)kHA1 + (T)kHA2 * chi);
+    const T Dh = (T)1 + chi * ((T)kHB1 + chi * ((T)kHB2 + (T)kHB3 * chi));
+    const T iD = M<T>::rcp(Dh);
+    const T R = Nh * iD;
+    const T Rp = ((T)kHA1 + (T)(2.0 * kHA2) * chi -
+                  R * ((T)kHB1 + chi * ((T)(2.0 * kHB2) + (T)(3.0 * kHB3) * chi))) * iD;
+    h2 = g * R;
+    h2p = gp * R + g * Rp;
+  }
+}
+
+template <typename T, int VAR = 0>
 __device__ __forceinline__ void qfp_tangent(const Params& p,
                                             const typename Tab<T>::type* __restrict__ tab, T a,
-                                            T g0, QfpTan<T>& o) {
-  const T LN2 = (T)0.69314718055994530942;
+                                            T g0, QfpTan<T>& o,
+                                            const float4* __restrict__ cA = nullptr) {
   const T C55 = (T)(55.0 / (16.0 * 1.7320508075688772935));
   const T h = (T)p.h, cK = (T)p.cK, cchi = (T)p.cchi;
   const T c1 = h * cK * a * a, c1a = (T)2 * h * cK * a;
@@ -68,30 +152,9 @@ __device__ __forceinline__ void qfp_tangent(const Params& p,
     const T chi = cg * mu;
     const T chi_a = cchi * G * mu + cg * mu_a;
     const T chi_g = cg * mu_g;
-    // Gaunt factor and derivatives
-    const T x1 = (T)1 + (T)1.7 * chi;
-    const T l1 = M<T>::lg2(x1);
-    const T L1 = LN2 * l1;
-    const T r1 = M<T>::ex2(-l1);
-    const T opc = (T)1 + chi;
-    const T B = (T)1 + (T)4.8 * opc * L1 + (T)2.44 * chi * chi;
-    const T t = M<T>::ex2((T)(-1.0 / 3.0) * M<T>::lg2(B));
-    const T g = t * t, iB = t * t * t;
-    const T Bp = (T)4.8 * L1 + (T)8.16 * opc * r1 + (T)4.88 * chi;
-    const T Bpp = (T)8.16 * r1 - (T)5.712 * r1 * r1 + (T)4.88;
-    const T gp = (T)(-2.0 / 3.0) * g * iB * Bp;
-    const T gpp = (T)(10.0 / 9.0) * g * iB * iB * Bp * Bp - (T)(2.0 / 3.0) * g * iB * Bpp;
-    const T s = (T)2 * g + chi * gp;
-    const T s_chi = (T)3 * gp + chi * gpp;
-    // second-moment factor and derivative
-    const T Nh = (T)1 + chi * ((T)kHA1 + (T)kHA2 * chi);
-    const T Dh = (T)1 + chi * ((T)kHB1 + chi * ((T)kHB2 + (T)kHB3 * chi));
-    const T iD = M<T>::rcp(Dh);
-    const T R = Nh * iD;
-    const T Rp = ((T)kHA1 + (T)(2.0 * kHA2) * chi -
-                  R * ((T)kHB1 + chi * ((T)(2.0 * kHB2) + (T)(3.0 * kHB3) * chi))) * iD;
-    const T h2 = g * R;
-    const T h2p = gp * R + g * Rp;
+    // Gaunt and second-moment factors and their derivatives
+    T g, gp, s, s_chi, h2, h2p;
+    cell_factors<T, VAR>(p, cA, chi, g, gp, s, s_chi, h2, h2p);
     // mean
     const T du_n = du + hK * g;
     const T du_a_n = du_a + hK_a * g + hK * gp * chi_a;
@@ -230,6 +293,7 @@ template <typename T>
 struct GFront {
   T w, xi3, xi4, xi5, gamma0, a, a_over_a0;
   T dla_w0, dla_dx, dla_dy, dla_thx, dla_thy, dla_del, thx, thy;
+  T zq, xs, ys, ct, w0;        // crossing geometry (per-cell focus)
   bool ok, clamped;
 };
 
@@ -281,6 +345,124 @@ __device__ __forceinline__ void grad_front(const Params& p, int64_t i, T w0, GFr
   f.dla_del = (E - (T)0.5) * dq_del * rq - drho_del * iw2 * rq;
   const T dq_w0 = (T)-4 * zq * zq / w0;                // dq/dW0 (z_R ~ W0^2)
   f.dla_w0 = (T)-0.5 * dq_w0 * rq + E * ((T)2 / w0 + dq_w0 * rq);
+  f.zq = zq;
+  f.xs = xs;
+  f.ys = ys;
+  f.ct = ct;
+  f.w0 = w0;
+}
+
+// Per-cell focus (QS_VARIANT_CELL_FOCUS): the local amplitude a_j of a cell
+// at shift s along the path (Eq. 2 at z* - s, xs + theta_x s, ys + theta_y s)
+// and d ln a_j / d(ln a0, W0, dx, dy, delay, div), from
+//   ln a_j = ln a0 - (1/2) ln q_j - E_j,  q_j = 1 + zq_j^2,  E_j = rho_j^2/(W0^2 q_j):
+//   W0    (E - 1/2) q'/q + 2E/W0 with q' = -4 zq_j^2/W0 (z_R ~ W0^2)
+//   dx    2 x_j/(W0^2 q_j),  dy the same with y_j
+//   delay (E - 1/2) q'/q - rho'/(W0^2 q) with q' = -c zq_j/z_R,
+//         rho' = c (x_j theta_x + y_j theta_y) (the crossing moves by c/2)
+//   div   -2 (x_j xi4 + y_j xi5)(ct + s)/(W0^2 q_j)
+template <typename T>
+__device__ __forceinline__ T cell_amp(const Params& p, const GFront<T>& f, T s, T (&e)[6]) {
+  const T izR = QS_PV(T, inv_zR), iw2 = QS_PV(T, inv_w0sq);
+  const T zq = f.zq - s * izR;
+  const T q = (T)1 + zq * zq, rq = M<T>::rcp(q);
+  const T xj = f.xs + f.thx * s, yj = f.ys + f.thy * s;
+  const T E = (xj * xj + yj * yj) * iw2 * rq;
+  T ex;
+  if constexpr (sizeof(T) == 4) ex = M<T>::ex2(-(T)1.4426950408889634074 * E);
+  else ex = exp(-E);
+  const T aj = QS_PV(T, a0) * M<T>::rsqrt(q) * ex;
+  const T k2 = (T)2 * iw2 * rq;
+  const T cc = (T)0.299792458;
+  e[0] = (T)1;
+  e[1] = (E - (T)0.5) * ((T)-4 * zq * zq / f.w0) * rq + (T)2 * E / f.w0;
+  e[2] = k2 * xj;
+  e[3] = k2 * yj;
+  e[4] = (E - (T)0.5) * (-cc * zq * izR) * rq - cc * (xj * f.thx + yj * f.thy) * iw2 * rq;
+  e[5] = -k2 * (xj * f.xi4 + yj * f.xi5) * (f.ct + s);
+  return aj;
+}
+
+// Tangents of the per-cell-focus model with respect to ln a0, W0, dx, dy,
+// delay, div (each through every cell's a_j) and gamma0: the recursion of
+// qfp_tangent with a per-cell relative perturbation e_k of the field
+// (dhK = 2 hK e_k, dchi = chi e_k + cg dmu), or, for the classical model,
+// Eq. 3's exponent summed cell by cell.
+constexpr int kNT = 7;
+template <typename T> struct FocTan {
+  T du, V, du_t[kNT], V_t[kNT];
+};
+
+template <typename T, bool QFP, int VAR>
+__device__ __forceinline__ void focus_tangent(const Params& p,
+                                              const typename Tab<T>::type* __restrict__ tab,
+                                              const GFront<T>& f, FocTan<T>& o,
+                                              const float4* __restrict__ cA) {
+  const T C55 = (T)(55.0 / (16.0 * 1.7320508075688772935));
+  const T hcK = (T)p.h * (T)p.cK, cchi = (T)p.cchi, g0 = f.gamma0;
+  T du = 0, V = 0, gph = (T)0.5;
+  T du_t[kNT], V_t[kNT], gph_t[kNT];
+#pragma unroll
+  for (int k = 0; k < kNT; ++k) du_t[k] = V_t[k] = gph_t[k] = (T)0;
+  const int N = p.n_phase;
+  for (int j = 0; j < N; ++j) {
+    T G, sj;
+    if constexpr (sizeof(T) == 4) {
+      const float4 e4 = reinterpret_cast<const float4*>(tab)[j];
+      G = e4.x;
+      sj = e4.z;
+    } else {
+      G = reinterpret_cast<const double*>(tab)[j];
+      sj = cell_shift(p, j);
+    }
+    T e[6];
+    const T A = cell_amp<T>(p, f, sj, e) * G;
+    const T hK = hcK * A * A;
+    if constexpr (!QFP) {
+      du += hK;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) du_t[k] += (T)2 * hK * e[k];
+      continue;
+    } else {
+      const T dum = du + hK * gph;
+      const T r = M<T>::rcp((T)1 + g0 * dum);
+      const T mu = g0 * r;
+      const T cg = cchi * A;
+      const T chi = cg * mu;
+      T g, gp, s, s_chi, h2, h2p;
+      cell_factors<T, VAR>(p, cA, chi, g, gp, s, s_chi, h2, h2p);
+      const T hKmu = hK * mu;
+      const T hlam = (T)-2 * hKmu * s;
+      const T m2 = mu * mu;
+      const T hD2 = C55 * hKmu * m2 * chi * h2;
+      const T hh = h2 + chi * h2p;
+      const T hr = hlam * V + hD2;
+      const T fac = (T)1 + (T)0.5 * hlam;
+#pragma unroll
+      for (int k = 0; k < kNT; ++k) {
+        const T dhK = k < 6 ? (T)2 * hK * e[k < 6 ? k : 0] : (T)0;
+        const T dum_k = du_t[k] + dhK * gph + hK * gph_t[k];
+        const T mu_k = k < 6 ? -mu * r * g0 * dum_k : r - mu * r * (dum + g0 * dum_k);
+        const T chi_k = (k < 6 ? chi * e[k < 6 ? k : 0] : (T)0) + cg * mu_k;
+        du_t[k] = du_t[k] + dhK * g + hK * gp * chi_k;
+        const T hlam_k = (T)-2 * (dhK * mu * s + hK * mu_k * s + hKmu * s_chi * chi_k);
+        const T hD2_k = C55 * m2 * ((dhK * mu + (T)3 * hK * mu_k) * chi * h2 + hKmu * chi_k * hh);
+        const T hr_k = hlam_k * V + hlam * V_t[k] + hD2_k;
+        V_t[k] = V_t[k] + hr_k * fac + (T)0.5 * hr * hlam_k;
+        gph_t[k] = (T)0.5 * gp * chi_k;
+      }
+      du = du + hK * g;
+      V = V + hr * fac;
+      gph = (T)0.5 * g;
+    }
+  }
+  o.du = du;
+  o.V = V;
+#pragma unroll
+  for (int k = 0; k < kNT; ++k) {
+    o.du_t[k] = du_t[k];
+    o.V_t[k] = V_t[k];
+  }
 }
 
 // Per-thread gradient partials: FP64 sums (FP64 path), compensated FP32
@@ -303,28 +485,23 @@ template <> struct GAcc<float> {
   __device__ __forceinline__ double get(int k) const { return (double)s[k] - (double)c[k]; }
 };
 
-// The model with its tangents, the sample's outputs, its share of dL/d(outputs)
-// (adjoint of rows a8-a9) and the chain rule to the parameters (rows a4-a6).
-// dLdS: upstream gradient of the smoothed spectrum (NULL: none).
+// dL/d(the sample's outputs) from the upstream gradient (adjoint of rows
+// a8-a9 and of the smoothed spectrum), and through Eq. 8 (theta_e = kappa_s
+// a sqrt(V) / mu^2, a the crossing a_eff): the sample's share of dL/d mu,
+// dL/d V, dL/d a_eff (directly), dL/d gamma0 (directly) and dL/d theta_x0,
+// theta_y0.  False if the sample's result is not finite (it then adds
+// nothing, as the forward excluded it).
+template <typename T>
+struct GOut {
+  T g_mu, g_V, g_a, g_g0, g_thx, g_thy;
+};
+
 template <typename T, bool QFP, typename S>
-__device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
-                                          const S* __restrict__ dLdS, int64_t i,
-                                          const GFront<T>& f, const QfpTan<T>& o, GAcc<T>& acc) {
-  const T g0 = f.gamma0, a = f.a;
-  T mu, V = 0, mu_a, mu_g, V_a = 0, V_g = 0;
-  if (!QFP) {
-    mu = g0 / ((T)1 + QS_PV(T, cRR) * g0 * a * a);
-    mu_a = -mu * mu * (T)2 * QS_PV(T, cRR) * a;
-    mu_g = mu * mu / (g0 * g0);
-  } else {
-    mu = g0 / ((T)1 + g0 * o.du);
-    mu_a = -mu * mu * o.du_a;
-    mu_g = mu * mu * ((T)1 / (g0 * g0) - o.du_g);
-    V = o.V;
-    V_a = o.V_a;
-    V_g = o.V_g;
-  }
-  if (!isfinite(mu) || !isfinite(V)) return;
+__device__ __forceinline__ bool sample_upstream(const Params& p, const Seeds<T>& sd,
+                                                const S* __restrict__ dLdS, int64_t i,
+                                                const GFront<T>& f, T mu, T V, GOut<T>& go) {
+  const T a = f.a;
+  if (!isfinite(mu) || !isfinite(V)) return false;
   // outputs of the sample (row a6)
   T theta_e = 0, gout = mu, sv = 0;
   const T xi7 = QFP ? load_t<T>(p.xi[7], i, p.dtype) : (T)0;
@@ -365,10 +542,10 @@ __device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
   T g_V = (sd.spread > (T)0 ? sd.gSp * wn * (T)0.5 / sd.spread : (T)0);
   if (QFP && V > (T)0) g_V += g_out * xi7 * (T)0.5 / sv;
   const T g_te = sd.gDx * wn * theta_e * sd.dxr;
-  const T g_thx = sd.gDx * wn * f.thx * sd.dxr;
-  const T g_thy = sd.gDy * wn * f.thy * sd.dyr;
+  go.g_thx = sd.gDx * wn * f.thx * sd.dxr;
+  go.g_thy = sd.gDy * wn * f.thy * sd.dyr;
   T g_a = sd.gA * wn;
-  T g_g0 = sd.gG0 * wn;
+  go.g_g0 = sd.gG0 * wn;
   // theta_e = kappa_s a sqrt(V) / mu^2
   if (QFP && V > (T)0) {
     const T ks = QS_PV(T, kappa_s);
@@ -376,9 +553,39 @@ __device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
     g_V += g_te * ks * a * (T)0.5 / (sv * mu * mu);
     g_mu += g_te * ((T)-2 * theta_e / mu);
   }
+  go.g_mu = g_mu;
+  go.g_V = g_V;
+  go.g_a = g_a;
+  return true;
+}
+
+// The model with its tangents, the sample's outputs, its share of dL/d(outputs)
+// and the chain rule to the parameters (rows a4-a6), for the model whose
+// phase integration sees a_eff in every cell (variant 0, cycle-resolved chi):
+// (mu, V) = F(a_eff, gamma0), and a_eff carries the parameters' dependence.
+template <typename T, bool QFP, typename S>
+__device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
+                                          const S* __restrict__ dLdS, int64_t i,
+                                          const GFront<T>& f, const QfpTan<T>& o, GAcc<T>& acc) {
+  const T g0 = f.gamma0, a = f.a;
+  T mu, V = 0, mu_a, mu_g, V_a = 0, V_g = 0;
+  if (!QFP) {
+    mu = g0 / ((T)1 + QS_PV(T, cRR) * g0 * a * a);
+    mu_a = -mu * mu * (T)2 * QS_PV(T, cRR) * a;
+    mu_g = mu * mu / (g0 * g0);
+  } else {
+    mu = g0 / ((T)1 + g0 * o.du);
+    mu_a = -mu * mu * o.du_a;
+    mu_g = mu * mu * ((T)1 / (g0 * g0) - o.du_g);
+    V = o.V;
+    V_a = o.V_a;
+    V_g = o.V_g;
+  }
+  GOut<T> go;
+  if (!sample_upstream<T, QFP, S>(p, sd, dLdS, i, f, mu, V, go)) return;
   // (mu, V) = F(a, gamma0)
-  g_a += g_mu * mu_a + g_V * V_a;
-  g_g0 += g_mu * mu_g + g_V * V_g;
+  const T g_a = go.g_a + go.g_mu * mu_a + go.g_V * V_a;
+  const T g_g0 = go.g_g0 + go.g_mu * mu_g + go.g_V * V_g;
   // chain to the parameters
   const T ga = g_a * a;                                 // dL/d ln a
   acc.add(QS_G_A0, QS_PV(T, a0) > (T)0 ? g_a * f.a_over_a0 : (T)0);
@@ -390,7 +597,42 @@ __device__ __forceinline__ void grad_back(const Params& p, const Seeds<T>& sd,
     acc.add(QS_G_GAMMA, g_g0 * ((T)1 + QS_PV(T, spread) * f.xi3));
     acc.add(QS_G_SPREAD, g_g0 * QS_PV(T, gmean) * f.xi3);
   }
-  acc.add(QS_G_DIV, (g_thx + ga * f.dla_thx) * f.xi4 + (g_thy + ga * f.dla_thy) * f.xi5);
+  acc.add(QS_G_DIV, (go.g_thx + ga * f.dla_thx) * f.xi4 + (go.g_thy + ga * f.dla_thy) * f.xi5);
+}
+
+// The same for the per-cell focus: mu and V depend on the parameters through
+// every cell's a_j (the seven tangents of focus_tangent), while a_eff at the
+// crossing still enters Eq. 8 and the a_eff moment directly.
+template <typename T, bool QFP, typename S>
+__device__ __forceinline__ void grad_back_focus(const Params& p, const Seeds<T>& sd,
+                                                const S* __restrict__ dLdS, int64_t i,
+                                                const GFront<T>& f, const FocTan<T>& o,
+                                                GAcc<T>& acc) {
+  const T g0 = f.gamma0, a = f.a;
+  const T mu = g0 / ((T)1 + g0 * o.du);
+  const T m2 = mu * mu;
+  const T V = QFP ? o.V : (T)0;
+  GOut<T> go;
+  if (!sample_upstream<T, QFP, S>(p, sd, dLdS, i, f, mu, V, go)) return;
+  // d(mu, V)/d theta_k through the cells (k: ln a0, W0, dx, dy, delay, div)
+  T gk[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) gk[k] = go.g_mu * (-m2 * o.du_t[k]) + (QFP ? go.g_V * o.V_t[k] : (T)0);
+  const T g_g0 = go.g_g0 + go.g_mu * m2 * ((T)1 / (g0 * g0) - o.du_t[6]) +
+                 (QFP ? go.g_V * o.V_t[6] : (T)0);
+  const T ga = go.g_a * a;                              // direct dL/d ln a_eff
+  const T a0v = QS_PV(T, a0);
+  acc.add(QS_G_A0, a0v > (T)0 ? go.g_a * f.a_over_a0 + gk[0] / a0v : (T)0);
+  acc.add(QS_G_W0, ga * f.dla_w0 + gk[1]);
+  acc.add(QS_G_DX, ga * f.dla_dx + gk[2]);
+  acc.add(QS_G_DY, ga * f.dla_dy + gk[3]);
+  acc.add(QS_G_DELAY, ga * f.dla_del + gk[4]);
+  if (!p.flat && !f.clamped) {
+    acc.add(QS_G_GAMMA, g_g0 * ((T)1 + QS_PV(T, spread) * f.xi3));
+    acc.add(QS_G_SPREAD, g_g0 * QS_PV(T, gmean) * f.xi3);
+  }
+  acc.add(QS_G_DIV,
+          (go.g_thx + ga * f.dla_thx) * f.xi4 + (go.g_thy + ga * f.dla_thy) * f.xi5 + gk[5]);
 }
 
 // Upstream coefficients from the forward moments and dL/d(moments):
@@ -421,13 +663,33 @@ __device__ __forceinline__ Seeds<T> make_seeds(const qs_moments* __restrict__ mo
 // Samples [begin, end) of one launch's samples, thread `tid` of `nthr`:
 // FP32 QFP takes two samples per thread through the packed tangent
 // integration (begin even), the other paths one.
-template <typename T, bool QFP, typename S>
+template <typename T, bool QFP, typename S, int VAR = 0>
 __device__ __forceinline__ void grad_range(const Params& p,
                                            const typename Tab<T>::type* __restrict__ tab,
                                            const Seeds<T>& sd, const S* dS, T w0, GAcc<T>& acc,
                                            int64_t begin, int64_t end, int64_t tid,
-                                           int64_t nthr) {
-  if constexpr (QFP && sizeof(T) == 4) {
+                                           int64_t nthr, const float4* __restrict__ cA = nullptr) {
+  if constexpr ((VAR & kVarCell) != 0) {
+    // per-cell focus: one sample at a time, seven tangents
+    for (int64_t i = begin + tid; i < end; i += nthr) {
+      GFront<T> f;
+      grad_front<T>(p, i, w0, f);
+      if (!f.ok) continue;
+      FocTan<T> o;
+      focus_tangent<T, QFP, VAR>(p, tab, f, o, cA);
+      grad_back_focus<T, QFP, S>(p, sd, dS, i, f, o, acc);
+    }
+  } else if constexpr ((VAR & kVarCycle) != 0) {
+    // cycle-resolved chi: one sample at a time, the two tangents
+    for (int64_t i = begin + tid; i < end; i += nthr) {
+      GFront<T> f;
+      grad_front<T>(p, i, w0, f);
+      if (!f.ok) continue;
+      QfpTan<T> o{};
+      qfp_tangent<T, VAR>(p, tab, f.a, f.gamma0, o, cA);
+      grad_back<T, QFP, S>(p, sd, dS, i, f, o, acc);
+    }
+  } else if constexpr (QFP && sizeof(T) == 4) {
     for (int64_t k = begin / 2 + tid; 2 * k < end; k += nthr) {
       const int64_t i0 = 2 * k, i1 = (2 * k + 1 < end) ? 2 * k + 1 : 2 * k;
       GFront<T> f0, f1;

@@ -19,6 +19,10 @@ int32_t validate_bins(const qs_bins* b);
 int32_t validate_samples(const qs_samples* s);
 int32_t exec_opts(const qs_exec* e, int* precision, int* wbits, int* block, int* grid);
 int32_t exec_tile(const qs_exec* e, int* tile);
+// Points p at the cycle-resolved chi tables of the current context, building
+// them on first use there (one launch on `st` and a wait; QS_ERR_UNSUPPORTED
+// while `st` is being captured).
+int32_t cycle_tables(Params& p, cudaStream_t st);
 // QS_EXEC_CHECK_FINITE requested?
 bool exec_check_finite(const qs_exec* e);
 // QS_OK unless `st` is being captured into a graph (QS_ERR_UNSUPPORTED):

@@ -616,7 +616,7 @@ CtxMark g_cyc_ready;
 // current context (one launch on `st`, then a wait for it; not allowed while
 // `st` is being captured into a graph).  A device reset discards the tables
 // with the context, so the first use in the next context builds them again.
-int32_t cycle_tables(Params& p, cudaStream_t st) {
+int32_t cycle_tables_impl(Params& p, cudaStream_t st) {
   int dev = 0;
   unsigned long long key = 0;
   if (int32_t e = current_context(&dev, &key)) return e;
@@ -700,6 +700,10 @@ int32_t launch_scatter_prec(const Params& p, bool qfp, const Smem& sm, int block
 }
 
 }  // namespace
+
+namespace detail {
+int32_t cycle_tables(Params& p, cudaStream_t st) { return cycle_tables_impl(p, st); }
+}  // namespace detail
 }  // namespace qs
 
 // ---------------------------------------------------------------------------
@@ -772,7 +776,7 @@ extern "C" int32_t qs_scatter(const qs_laser* laser, const qs_beam* beam,
   p.partials = reinterpret_cast<double*>(ws + pl.off_part);
   p.hist_in_smem = sm.hist ? 1 : 0;
   p.smooth_in_smem = sm.smooth ? 1 : 0;
-  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
+  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = detail::cycle_tables(p, cs))) return st;
 
   if (cudaMemsetAsync(ws, 0, pl.off_part, cs) != cudaSuccess) return cuda_fail();
   int g = 1;
@@ -807,7 +811,7 @@ extern "C" int32_t qs_eval_samples(const qs_laser* laser, const qs_beam* beam,
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   const bool qfp = laser->model == QS_MODEL_QFP;
   const int var = laser->variant;
-  if ((var & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
+  if ((var & QS_VARIANT_CYCLE_CHI) && (st = detail::cycle_tables(p, cs))) return st;
   const size_t tb = ((qfp || (var & QS_VARIANT_CELL_FOCUS))
                          ? (size_t)p.n_phase * (prec == QS_F64 ? sizeof(double) : sizeof(float4))
                          : 0) +
@@ -1036,7 +1040,7 @@ extern "C" int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam,
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Params p;
   fill_params(p, laser, beam, h_samples, bins, wbits);
-  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = cycle_tables(p, cs))) return st;
+  if ((laser->variant & QS_VARIANT_CYCLE_CHI) && (st = detail::cycle_tables(p, cs))) return st;
   p.acc_spec = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_spec);
   p.acc_map = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_map);
   p.acc_aeff = reinterpret_cast<unsigned long long*>(ws + hp.pl.off_aeff);

@@ -204,27 +204,101 @@ def test_cycle_resolved_chi_scatter_matches_oracle():
     compare_scatter(out, ref, "f32", float(n), inputs=(L, wl.beam, wl.bins, xi, None))
 
 
-def test_per_cell_focus_gradient_is_unsupported_and_batch_shot_flagged():
-    n = 300
-    wl, L, xi = cfg2(n, n_phase=64, variant=I.VAR_CELL_FOCUS)
-    xt, _ = dev(xi)
-    out = qs_scatter(L, wl.beam, xt, wl.bins, precision="f32")
-    with pytest.raises(QsError):
-        B.qs_scatter_grad(L, wl.beam, xt, wl.bins, out.moments,
-                          torch.zeros(13, dtype=torch.float64), None, precision="f32", out=out)
-    bw = I.batch_shots(3, seed=21, log10_range=(2.0, 2.5), n_phase=64, n_bins=32)
-    lasers = list(bw.lasers)
-    lasers[1] = I.Laser(**{**lasers[1].__dict__, "variant": I.VAR_CELL_FOCUS})
-    offsets = np.zeros(4, dtype=np.int64)
+VARIANT_CASES = [(I.MODEL_LL, I.VAR_CELL_FOCUS), (I.MODEL_QFP, I.VAR_CELL_FOCUS),
+                 (I.MODEL_QFP, I.VAR_CYCLE_CHI), (I.MODEL_QFP, I.VAR_CELL_FOCUS | I.VAR_CYCLE_CHI)]
+
+
+def _variant_case(n, model, variant, n_phase=48):
+    """The bench laser with a tighter focus and a wider divergence, so that
+    the path through the focus matters (the per-cell focus), and a strong
+    field (chi ~ 1: the cycle-resolved factors differ from the rms ones)."""
+    wl, L, xi = cfg2(n, n_phase=n_phase, model=model, variant=variant, w0_um=2.0)
+    beam = I.Beam(**{**wl.beam.__dict__, "div_rad": 5e-3})
+    bins = I.Bins(n_bins=128, lo=0.0, hi=6720.0, smooth_sigma_bins=2.0)
+    return wl, L, beam, bins, xi
+
+
+GRAD_SCALE = np.array([30.0, 2.0, 1.0, 1.0, 10.0, 4000.0, 0.1, 5e-3])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("model,variant", VARIANT_CASES)
+def test_variant_gradient_matches_oracle(prec, model, variant):
+    """qs_scatter_grad for the model variants (seven tangents through the
+    per-cell amplitudes; the cycle-resolved factors and their chi-derivatives)
+    against the oracle's dual-number gradient, parameter-scaled relative to
+    the largest component: FP64 1e-10, FP32 1e-4 (the FP32 cycle factors come
+    from the Hermite tables, 3e-7 in S, and the seven FP32 tangents sum over
+    the cells without compensation)."""
+    n = 1001 if not variant & I.VAR_CYCLE_CHI else 401
+    wl, L, beam, bins, xi = _variant_case(n, model, variant)
+    w = I.rng(41).uniform(0.5, 1.5, n).astype(np.float32)
+    xt, wt = dev(xi, w)
+    rg = I.rng(42)
+    dm = np.zeros(13)
+    for k, sc in (("mean", 1e-3), ("spread", 1e-3), ("div_x", 1e3), ("div_y", 1e3), ("div", 1e3),
+                  ("mean_aeff", 1.0), ("mean_gamma0", 1e-3), ("rel_spread", 1.0)):
+        dm[B.MOMENT_FIELDS.index(k)] = rg.normal() * sc
+    dS = rg.normal(size=bins.n_bins) * 1e-3
+    out = qs_scatter(L, beam, xt, bins, w=wt, precision=prec)
+    g = B.qs_scatter_grad(L, beam, xt, bins, out.moments, torch.from_numpy(dm),
+                          torch.from_numpy(dS), w=wt, precision=prec, out=out).cpu().numpy()
+    ref = oracle.grad(L, beam, bins, bins.smooth_sigma_bins, f64(xi), w.astype(np.float64),
+                      dL_dm=dm, dL_dS=dS)
+    rs = ref["grad"] * GRAD_SCALE
+    err = np.abs(g * GRAD_SCALE - rs) / np.max(np.abs(rs))
+    print(f"[{prec}, model {model}, variant {variant}] scaled grad rel err:", err)
+    assert np.all(err <= (1e-10 if prec == "f64" else 1e-4)), err
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batch_with_model_variants_equals_single_shot_calls(prec):
+    """A batch mixing the paper's model with both variants (and the classical
+    model with the per-cell focus): every shot equals its single-shot call
+    (histograms exactly, moments to the batch's partition rounding), and the
+    batched adjoint equals the single-shot adjoint shot by shot."""
+    bw = I.batch_shots(8, seed=21, log10_range=(2.3, 3.0), n_phase=48, n_bins=64, model_mix=True)
+    variants = [0, I.VAR_CELL_FOCUS, I.VAR_CYCLE_CHI, I.VAR_CELL_FOCUS | I.VAR_CYCLE_CHI,
+                0, I.VAR_CELL_FOCUS, I.VAR_CYCLE_CHI, I.VAR_CELL_FOCUS]
+    lasers = []
+    for k, L0 in enumerate(bw.lasers):
+        v = variants[k]
+        model = I.MODEL_QFP if (v & I.VAR_CYCLE_CHI or k % 2 == 0) else L0.model
+        lasers.append(I.Laser(**{**L0.__dict__, "variant": v, "model": model, "w0_um": 2.5}))
+    beams = [I.Beam(**{**b.__dict__, "div_rad": 5e-3}) for b in bw.beams]
+    bins = I.Bins(n_bins=64, lo=0.0, hi=1.0, smooth_sigma_bins=2.0)
+    offsets = np.zeros(9, dtype=np.int64)
     offsets[1:] = np.cumsum(bw.counts)
-    xs = [torch.from_numpy(a).cuda() for a in I.sample_streams(int(offsets[-1]), 22,
-                                                                 dtype=np.float32)]
-    bt = B.Batch(lasers, bw.beams, offsets, bw.bins, int(offsets[-1]), ranges=bw.ranges)
+    n = int(offsets[-1])
+    xs = [torch.from_numpy(a).cuda() for a in I.sample_streams(n, 22, dtype=np.float32)]
+    bt = B.Batch(lasers, beams, offsets, bins, n, ranges=bw.ranges, precision=prec)
     bt.run(xs)
+    rg = I.rng(23)
+    dm = np.zeros((8, 13))
+    dm[:, 1] = rg.normal(size=8) * 1e-3
+    dm[:, 2] = rg.normal(size=8) * 1e-3
+    dm[:, 4] = rg.normal(size=8) * 1e3
+    dS = rg.normal(size=(8, 64)) * 1e-3
+    gb = bt.grad(xs, torch.from_numpy(dm), torch.from_numpy(dS)).cpu().numpy()
     torch.cuda.synchronize()
-    m = bt.moments.cpu().numpy()
-    assert m[1, 0] == 0 and m[1, B.MOMENT_FIELDS.index("nonfinite")] == -1
-    assert m[0, 0] > 0 and m[2, 0] > 0
+    mom = bt.moments.cpu().numpy()
+    assert np.all(mom[:, B.MOMENT_FIELDS.index("nonfinite")] == 0), mom[:, -1]
+    for s_ in range(8):
+        o0, o1 = int(offsets[s_]), int(offsets[s_ + 1])
+        b_s = I.Bins(**{**bins.__dict__, "lo": float(bw.ranges[s_, 0]),
+                        "hi": float(bw.ranges[s_, 1])})
+        sub = [x[o0:o1] for x in xs]
+        ref = qs_scatter(lasers[s_], beams[s_], sub, b_s, precision=prec)
+        gr = B.qs_scatter_grad(lasers[s_], beams[s_], sub, b_s, ref.moments,
+                               torch.from_numpy(dm[s_]), torch.from_numpy(dS[s_]),
+                               precision=prec, out=ref).cpu().numpy()
+        torch.cuda.synchronize()
+        assert torch.equal(bt.spectra[s_], ref.spectrum), s_
+        assert torch.equal(bt.spec_smooth[s_], ref.spec_smooth), s_
+        np.testing.assert_allclose(mom[s_], ref.moments.cpu().numpy(),
+                                   rtol=1e-12 if prec == "f64" else 1e-7, atol=1e-300)
+        err = np.abs((gb[s_] - gr) * GRAD_SCALE) / max(np.max(np.abs(gr * GRAD_SCALE)), 1e-300)
+        assert np.all(err <= (1e-12 if prec == "f64" else 1e-6)), (s_, lasers[s_].variant, err)
 
 
 # ---------------------------------------------------------------------------

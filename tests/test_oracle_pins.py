@@ -1092,12 +1092,26 @@ def _perturbed(L, B, name, value):
     return L, I.Beam(**{**B.__dict__, name: value})
 
 
-@pytest.mark.parametrize("model", [I.MODEL_LL, I.MODEL_QFP])
-def test_oracle_gradient_vs_central_differences(model):
-    n = 300
+@pytest.mark.parametrize("model,variant", [(I.MODEL_LL, 0), (I.MODEL_QFP, 0),
+                                           (I.MODEL_LL, I.VAR_CELL_FOCUS),
+                                           (I.MODEL_QFP, I.VAR_CELL_FOCUS),
+                                           (I.MODEL_QFP, I.VAR_CYCLE_CHI),
+                                           (I.MODEL_QFP, I.VAR_CELL_FOCUS | I.VAR_CYCLE_CHI)])
+def test_oracle_gradient_vs_central_differences(model, variant):
+    """The oracle's dual-number gradient (every step differentiated in dual
+    arithmetic, the model variants included) against Richardson central
+    differences of its plain forward (a separate code path)."""
+    n = 300 if not variant & I.VAR_CYCLE_CHI else 120
     wl = I.full_qfp(n)
-    L = I.Laser(**{**wl.laser.__dict__, "model": model, "n_phase": 48, "dy_um": 0.7})
+    L = I.Laser(**{**wl.laser.__dict__, "model": model, "n_phase": 48, "dy_um": 0.7,
+                   "variant": variant})
+    if variant & I.VAR_CELL_FOCUS:
+        # a focus tight enough that the path through it matters, and angles
+        # that move the electron sideways over the pulse
+        L = I.Laser(**{**L.__dict__, "w0_um": 2.0})
     B = wl.beam
+    if variant & I.VAR_CELL_FOCUS:
+        B = I.Beam(**{**B.__dict__, "div_rad": 5e-3})
     xi, _ = I.workload_inputs(wl, n)
     xi = [a.astype(np.float64) for a in xi]
     w = I.rng(31).uniform(0.5, 1.5, n)
@@ -1114,7 +1128,7 @@ def test_oracle_gradient_vs_central_differences(model):
     dS = rg.normal(size=bins.n_bins) * 1e-2
     g = oracle.grad(L, B, bins, sigma, xi, w, dL_dm=dm, dL_dS=dS)["grad"]
     scale = {"a0": 30.0, "w0_um": 2.5, "dx_um": 1.0, "dy_um": 1.0, "delay_fs": 10.0,
-             "gamma_mean": 4000.0, "rel_spread": 0.1, "div_rad": 1e-3}
+             "gamma_mean": 4000.0, "rel_spread": 0.1, "div_rad": B.div_rad}
     for k, name in enumerate(oracle.GRAD_PARAMS):
         base = getattr(L, name) if name in LASER_PARAMS else getattr(B, name)
         h = 1e-4 * scale[name]
