@@ -194,6 +194,22 @@ def cpu_oracle_rate(wl, xi_host, seconds=12.0, chunk=2048):
     return done / dt, done, dt
 
 
+def cpu_oracle_gh32():
+    """The oracle's full run of the 32^3 Gauss-Hermite grid (classical LL,
+    32768 weighted FP64 nodes, 256-bin spectrum) on one host thread."""
+    from paper_2308_09348_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    wl = I.tiny_gauss_hermite()
+    xi, w = I.workload_inputs(wl)
+    oracle.scatter(wl.laser, wl.beam, wl.bins, xi, w)          # warm (page-in, libm)
+    t0 = time.perf_counter()
+    oracle.scatter(wl.laser, wl.beam, wl.bins, xi, w)
+    dt = time.perf_counter() - t0
+    return {"value": wl.n / dt, "unit": "samples/s", "cores": 1, "seconds": dt,
+            "sample": f"all {wl.n} nodes of the {wl.name} workload (one thread, FP64 C oracle)"}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -348,6 +364,34 @@ def bench_broadband(dev, rank, n, sweep_n=1 << 20, n_delays=512, steps=2):
                           "sample_evals_per_s": n_delays * sweep_n / (ms2 * 1e-3),
                           "ms_per_launch": ms2, "n_delays": n_delays,
                           "shared_samples": sweep_n, "delay_range_fs": [-100.0, 100.0]}
+    return res
+
+
+def bench_gh32(dev, rank, steps=20):
+    """The 32^3 Gauss-Hermite grid (classical LL, 32768 weighted nodes,
+    256-bin spectrum, mean and rms energy): one qs_scatter call per step on
+    inputs resident in HBM, FP64 and FP32 (launch-bound at this size)."""
+    import torch
+    from paper_2308_09348_gb300 import binding as B
+    from paper_2308_09348_gb300 import inputs as I
+    wl = I.tiny_gauss_hermite()
+    xi, w = I.workload_inputs(wl)
+    res = {"workload": wl.name, "n_samples": wl.n, "unit": "samples/s"}
+    for prec, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        xt = [torch.from_numpy(a).to(dev, dt) for a in xi]
+        wt = torch.from_numpy(w).to(dev, dt)
+        out = B.Outputs(wl.bins, wl.n, dev, prec)
+        for _ in range(3):
+            B.qs_scatter(wl.laser, wl.beam, xt, wl.bins, w=wt, precision=prec, out=out)
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        for _ in range(steps):
+            B.qs_scatter(wl.laser, wl.beam, xt, wl.bins, w=wt, precision=prec, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        res[prec] = {"value": wl.n / (ms * 1e-3), "ms_per_call": ms}
     return res
 
 
@@ -907,6 +951,7 @@ def main():
     cyc = None if args.no_cell else bench_variant(dev, rank, 2, n=args.cell_n)
     phot = None if args.no_photon else bench_photon(dev, rank, n=args.photon_n)
     pwr = None if args.no_pw else bench_pw(dev, rank)
+    gh = bench_gh32(dev, rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -920,7 +965,8 @@ def main():
                "sample": f"first {done} samples of the workload ({dt:.1f} s, FP64 C oracle, "
                          f"{procs} processes)",
                "single_core": {"value": rate1, "cores": 1,
-                               "sample": f"first {done1} samples ({dt1:.1f} s, one thread)"}}
+                               "sample": f"first {done1} samples ({dt1:.1f} s, one thread)"},
+               "gh32_full": cpu_oracle_gh32()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -940,7 +986,7 @@ def main():
                                  "rate or hardware stated): context, not a baseline",
                 "batch_shots": batch, "grad": grad, "broadband": broad, "classical_ll": ll,
                 "cell_focus": cell, "cycle_chi": cyc, "photon": phot,
-                "pw_reconstruction": pwr,
+                "pw_reconstruction": pwr, "gauss_hermite_32": gh,
                 "gpu": props.name}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -744,14 +744,19 @@ __device__ __forceinline__ SampleF eval_ll_f32_xi(const Params& p, float xi0, fl
   return s;
 }
 
+// Two classical samples in the lanes of float2 values.
+struct LL2 {
+  float2 g0, a, mu, thx, thy;
+};
+
 // Two classical samples at once in packed f32x2 arithmetic: the same
 // operations in the same order as focus_xi<float>, the LL closed form and
 // recombine_f1 (a - b as a + (-b), g0 - q0 d as one fma of -q0), so each
 // lane rounds exactly as the scalar path does.
-__device__ __forceinline__ void eval_ll_f32x2(const Params& p, float2 xi0, float2 xi1, float2 xi2,
-                                              float2 xi3, float2 xi4, float2 xi5, SampleF& s0,
-                                              SampleF& s1) {
+__device__ __forceinline__ LL2 eval_ll_pair(const Params& p, float2 xi0, float2 xi1, float2 xi2,
+                                            float2 xi3, float2 xi4, float2 xi5) {
   const float2 ONE = f2(1.f);
+  LL2 r;
   // decode and collision geometry (focus_xi)
   const float2 x = fma2(f2(p.f.sx), xi0, f2(p.f.bdx));
   const float2 y = fma2(f2(p.f.sy), xi1, f2(p.f.bdy));
@@ -760,27 +765,39 @@ __device__ __forceinline__ void eval_ll_f32x2(const Params& p, float2 xi0, float
                      : mul2(f2(p.f.gmean), fma2(f2(p.f.spread), xi3, ONE));
   if (g0.x < 1.f) g0.x = 1.f;
   if (g0.y < 1.f) g0.y = 1.f;
-  const float2 thx = mul2(f2(p.f.div), xi4), thy = mul2(f2(p.f.div), xi5);
+  r.g0 = g0;
+  r.thx = mul2(f2(p.f.div), xi4);
+  r.thy = mul2(f2(p.f.div), xi5);
   const float2 ct = mul2(f2(0.5f), __fadd2_rn(z, f2(p.f.c_delay)));
   const float2 zs = mul2(f2(0.5f), __fadd2_rn(z, f2(-p.f.c_delay)));
-  const float2 xs = __fadd2_rn(fma2(thx, ct, x), f2(-p.f.ldx));
-  const float2 ys = __fadd2_rn(fma2(thy, ct, y), f2(-p.f.ldy));
+  const float2 xs = __fadd2_rn(fma2(r.thx, ct, x), f2(-p.f.ldx));
+  const float2 ys = __fadd2_rn(fma2(r.thy, ct, y), f2(-p.f.ldy));
   const float2 rho2 = fma2(xs, xs, mul2(ys, ys));
   const float2 zq = mul2(zs, f2(p.f.inv_zR));
   const float2 q = fma2(zq, zq, ONE);
   const float2 E = mul2(mul2(rho2, f2(p.f.inv_w0sq)), rcpx2(q));
-  const float2 a = mul2(mul2(f2(p.f.a0), rsqrtx2(q)),
-                        ex2x2(mul2(f2(-1.4426950408889634074f), E)));
+  r.a = mul2(mul2(f2(p.f.a0), rsqrtx2(q)), ex2x2(mul2(f2(-1.4426950408889634074f), E)));
   // Eq. 3 and the recombination (recombine_f1)
-  const float2 du = mul2(mul2(f2(p.f.cRR), a), a);
+  const float2 du = mul2(mul2(f2(p.f.cRR), r.a), r.a);
   const float2 d = fma2(g0, du, ONE);
   const float2 r0 = rcpx2(d);
   const float2 q0 = mul2(g0, r0);
-  const float2 mu = fma2(fma2(make_float2(-q0.x, -q0.y), d, g0), r0, q0);
-  s0.g0 = g0.x; s0.aeff = a.x; s0.mu_hi = mu.x; s0.mu_lo = 0.f; s0.V = 0.f; s0.theta_e = 0.f;
-  s0.thx0 = thx.x; s0.thy0 = thy.x; s0.tx = thx.x; s0.ty = thy.x; s0.go_hi = mu.x; s0.go_lo = 0.f;
-  s1.g0 = g0.y; s1.aeff = a.y; s1.mu_hi = mu.y; s1.mu_lo = 0.f; s1.V = 0.f; s1.theta_e = 0.f;
-  s1.thx0 = thx.y; s1.thy0 = thy.y; s1.tx = thx.y; s1.ty = thy.y; s1.go_hi = mu.y; s1.go_lo = 0.f;
+  r.mu = fma2(fma2(make_float2(-q0.x, -q0.y), d, g0), r0, q0);
+  return r;
+}
+
+// Lane k of a pair as the scalar path's record.
+__device__ __forceinline__ SampleF ll_sample(const LL2& P, int k) {
+  SampleF s;
+  s.g0 = k ? P.g0.y : P.g0.x;
+  s.aeff = k ? P.a.y : P.a.x;
+  s.mu_hi = s.go_hi = k ? P.mu.y : P.mu.x;
+  s.mu_lo = s.go_lo = 0.f;
+  s.V = 0.f;
+  s.theta_e = 0.f;
+  s.thx0 = s.tx = k ? P.thx.y : P.thx.x;
+  s.thy0 = s.ty = k ? P.thy.y : P.thy.x;
+  return s;
 }
 
 __device__ __forceinline__ SampleF eval_ll_f32(const Params& p, int64_t i) {
@@ -921,6 +938,36 @@ __device__ __forceinline__ int aeff_bin_f32(const Params& p, float a) {
   return p.n_aeff;
 }
 
+// |x| < inf: isfinite's value (false for +-inf and NaN) as one compare.
+__device__ __forceinline__ bool finitef(float x) { return fabsf(x) < __int_as_float(0x7f800000); }
+
+// Accumulator slot of a spectrum bin coordinate t (FP32 paths): bins
+// [0, n_bins), n_bins below the range, n_bins + 1 above -- the slots
+// energy_bin_f32 leads to, from a floor conversion and one unsigned compare
+// (t >= n_bins saturates to or past n_bins; t is never NaN here).
+__device__ __forceinline__ int spec_slot(const Params& p, float t) {
+  const int b = __float2int_rd(t);
+  return (unsigned)b < (unsigned)p.n_bins ? b : (b < 0 ? p.n_bins : p.n_bins + 1);
+}
+// Bin coordinate of a single-float energy (the classical model's
+// gamma_out = mu has no low part): energy_bin_f32's arithmetic without it.
+__device__ __forceinline__ float energy_coord_f1(const Params& p, float g) {
+  if (!p.log_spaced) return __fmul_rn(__fsub_rn(g, p.f.lo), p.f.inv_w);
+  return (g > 0.f) ? __fsub_rn(__fmul_rn(M<float>::lg2(g), p.log2_scale), p.log2_offset) : -1.f;
+}
+// Map slot from the map coordinates fx = (tx + theta_max) tsx, fy (as
+// map_cell_f32 forms them; finite): the cell, or nmap - 1 outside the map.
+__device__ __forceinline__ int map_slot(const Params& p, float fx, float fy, int nmap) {
+  const int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
+  return ((unsigned)ix < (unsigned)p.n_tx && (unsigned)iy < (unsigned)p.n_ty)
+             ? iy * p.n_tx + ix : nmap - 1;
+}
+// a_eff slot from f = a_eff a_scale (a_eff >= 0, finite): the bin, or n_aeff.
+__device__ __forceinline__ int aeff_slot(const Params& p, float f) {
+  const int b = __float2int_rd(f);
+  return (unsigned)b < (unsigned)p.n_aeff ? b : p.n_aeff;
+}
+
 // Merge of two (weight, mean, central sum of squares) triples (the parallel
 // form of the variance recurrence): exact when one side is empty, no
 // cancellation between large raw moments.
@@ -1040,56 +1087,87 @@ __device__ __forceinline__ void warp_reduce(const AccD& acc, double (&v)[kNumMom
     for (int k = 3; k < kNumMom; ++k) v[k] += u[k];
   }
 }
-// FP32 path: the plain sums travel the tree as float pairs, and the energy
-// moments as FP64 sums (W, S1, S2) about the lower lane's shift: merging b
-// into a moves b's sums to a's shift s_a with d = s_b - s_a,
-//   S1 += S1_b + W_b d,   S2 += S2_b + 2 d S1_b + W_b d^2,
-// which needs no division (the FP64 pipe of this GPU issues slowly).
-__device__ __forceinline__ void warp_reduce(const AccF& acc, double (&v)[kNumMom]) {
+// (h, l) = a b for unevaluated float pairs (relative error ~2^-44): the
+// leading product exactly by FMA, the cross terms rounded.
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& h,
+                                         float& l) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  const float t = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  h = __fadd_rn(p, t);
+  l = __fsub_rn(t, __fsub_rn(h, p));
+}
+
+// FP32 path's sums on their way through the reduction tree, all as float
+// pairs: W = sum w, S1 = sum w (mu - sh), S2 = sum w (mu - sh)^2 about the
+// shift sh, the five plain sums, and the excluded-sample count.  The tree
+// runs on the FP32 pipes only (the FP64 pipe of this GPU issues 2 lanes per
+// SM and clock, so an FP64 tree would be the launch's tail).
+struct PairMom {
+  float Wh, Wl, S1h, S1l, S2h, S2l, sh;
   float h[5], l[5];
+  float nf;
+};
+constexpr int kPairMomFloats = 18;        // one warp's record in the red buffer
+static_assert(kPairMomFloats * 4 <= kNumMom * 8, "a warp record fits its moment slot");
+
+__device__ __forceinline__ PairMom pair_mom(const AccF& A) {
+  PairMom m;
+  two_sum(A.s[0], -A.c[0], m.Wh, m.Wl);
+  two_sum(A.s[1], -A.c[1], m.S1h, m.S1l);
+  two_sum(A.s[2], -A.c[2], m.S2h, m.S2l);
 #pragma unroll
-  for (int k = 0; k < 5; ++k) two_sum(acc.s[k + 3], -acc.c[k + 3], h[k], l[k]);
-  float nf = acc.nonfinite;
-  double W = (double)acc.s[0] - (double)acc.c[0];
-  double S1 = (double)acc.s[1] - (double)acc.c[1];
-  double S2 = (double)acc.s[2] - (double)acc.c[2];
-  double sh = W > 0.0 ? (double)acc.shift : 0.0;
+  for (int k = 0; k < 5; ++k) two_sum(A.s[k + 3], -A.c[k + 3], m.h[k], m.l[k]);
+  m.sh = m.Wh > 0.f ? A.shift : 0.f;
+  m.nf = A.nonfinite;
+  return m;
+}
+
+// The sums moved to the shift s0, with d = sh - s0 (an exact pair):
+//   S1' = S1 + W d,   S2' = S2 + d (S1 + S1') = S2 + 2 d S1 + W d^2.
+// An empty record (W = 0: S1 = S2 = 0 about any shift) only takes s0.
+__device__ __forceinline__ void pair_reshift(PairMom& m, float s0) {
+  if (m.Wh > 0.f) {
+    float dh, dl, th, tl;
+    two_sum(m.sh, -s0, dh, dl);
+    pair_mul(m.Wh, m.Wl, dh, dl, th, tl);
+    float nh = m.S1h, nl = m.S1l;
+    pair_add(nh, nl, th, tl);
+    float uh = m.S1h, ul = m.S1l;
+    pair_add(uh, ul, nh, nl);
+    pair_mul(dh, dl, uh, ul, th, tl);
+    pair_add(m.S2h, m.S2l, th, tl);
+    m.S1h = nh;
+    m.S1l = nl;
+  }
+  m.sh = s0;
+}
+
+// Fixed-order warp tree of the 32 lanes' records (every lane takes part):
+// each record is first moved to the shift of the lowest lane with weight
+// (when no lane has weight every energy sum is zero and nothing moves), and
+// lane 0 ends with the sum.
+__device__ __forceinline__ void warp_sum(PairMom& m) {
+  const unsigned has = __ballot_sync(0xffffffffu, m.Wh > 0.f);
+  if (has) pair_reshift(m, __shfl_sync(0xffffffffu, m.sh, __ffs(has) - 1));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double Wb = __shfl_down_sync(0xffffffffu, W, o);
-    const double S1b = __shfl_down_sync(0xffffffffu, S1, o);
-    const double S2b = __shfl_down_sync(0xffffffffu, S2, o);
-    const double shb = __shfl_down_sync(0xffffffffu, sh, o);
-    if (Wb > 0.0) {
-      if (W > 0.0) {
-        const double d = shb - sh;
-        const double t = __fma_rn(Wb, d, S1b);
-        S2 = S2 + __fma_rn(d, S1b + t, S2b);
-        S1 = S1 + t;
-        W = W + Wb;
-      } else {
-        W = Wb; S1 = S1b; S2 = S2b; sh = shb;
-      }
-    }
+    float bh = __shfl_down_sync(0xffffffffu, m.Wh, o), bl = __shfl_down_sync(0xffffffffu, m.Wl, o);
+    pair_add(m.Wh, m.Wl, bh, bl);
+    bh = __shfl_down_sync(0xffffffffu, m.S1h, o);
+    bl = __shfl_down_sync(0xffffffffu, m.S1l, o);
+    pair_add(m.S1h, m.S1l, bh, bl);
+    bh = __shfl_down_sync(0xffffffffu, m.S2h, o);
+    bl = __shfl_down_sync(0xffffffffu, m.S2l, o);
+    pair_add(m.S2h, m.S2l, bh, bl);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const float bh = __shfl_down_sync(0xffffffffu, h[k], o);
-      const float bl = __shfl_down_sync(0xffffffffu, l[k], o);
-      pair_add(h[k], l[k], bh, bl);
+      bh = __shfl_down_sync(0xffffffffu, m.h[k], o);
+      bl = __shfl_down_sync(0xffffffffu, m.l[k], o);
+      pair_add(m.h[k], m.l[k], bh, bl);
     }
-    nf = __fadd_rn(nf, __shfl_down_sync(0xffffffffu, nf, o));
+    m.nf = __fadd_rn(m.nf, __shfl_down_sync(0xffffffffu, m.nf, o));
   }
-  v[0] = W;
-  v[1] = 0.0;
-  v[2] = 0.0;
-  if (W > 0.0) {
-    const double q = S1 / W;
-    v[1] = sh + q;
-    v[2] = fmax(S2 - S1 * q, 0.0);
-  }
-#pragma unroll
-  for (int k = 0; k < 5; ++k) v[k + 3] = (double)h[k] + (double)l[k];
-  v[8] = (double)nf;
 }
 
 // Fixed-order block reduction of the per-thread accumulators into one
@@ -1114,6 +1192,58 @@ __device__ __forceinline__ void block_reduce_write(A& acc, double* red, double* 
     out[1] = m;
     out[2] = M2;
     for (int k = 3; k < kNumMom; ++k) out[k] = sm[k];
+  }
+}
+
+// FP32 path: warp trees of float pairs, the warps' records through one more
+// tree in warp 0, and only the slot's final mean and M2 in FP64 (thread 0).
+__device__ __forceinline__ void block_reduce_write(AccF& acc, double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* rf = reinterpret_cast<float*>(red);
+  PairMom m = pair_mom(acc);
+  warp_sum(m);
+  if (lane == 0) {
+    float* r = rf + warp * kPairMomFloats;
+    r[0] = m.Wh; r[1] = m.Wl; r[2] = m.S1h; r[3] = m.S1l; r[4] = m.S2h; r[5] = m.S2l;
+    r[6] = m.sh;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      r[7 + 2 * k] = m.h[k];
+      r[8 + 2 * k] = m.l[k];
+    }
+    r[17] = m.nf;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    PairMom b{};
+    if (lane < (int)(blockDim.x >> 5)) {
+      const float* r = rf + lane * kPairMomFloats;
+      b.Wh = r[0]; b.Wl = r[1]; b.S1h = r[2]; b.S1l = r[3]; b.S2h = r[4]; b.S2l = r[5];
+      b.sh = r[6];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        b.h[k] = r[7 + 2 * k];
+        b.l[k] = r[8 + 2 * k];
+      }
+      b.nf = r[17];
+    }
+    warp_sum(b);
+    if (lane == 0) {
+      const double W = (double)b.Wh + (double)b.Wl;
+      out[0] = W;
+      out[1] = 0.0;
+      out[2] = 0.0;
+      if (W > 0.0) {
+        const double S1 = (double)b.S1h + (double)b.S1l;
+        const double S2 = (double)b.S2h + (double)b.S2l;
+        const double q = S1 / W;
+        out[1] = (double)b.sh + q;
+        out[2] = fmax(S2 - S1 * q, 0.0);
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[k + 3] = (double)b.h[k] + (double)b.l[k];
+      out[8] = (double)b.nf;
+    }
   }
 }
 
@@ -1173,9 +1303,9 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
                                              int64_t naeff) {
   const float muf = s.mu_hi;
   // every value that enters a sum or a bin must be finite
-  const bool ok = isfinite(muf) && (!QFP || (isfinite(s.V) && isfinite(s.go_hi))) &&
-                  isfinite(s.tx) && isfinite(s.ty) && isfinite(s.aeff) && isfinite(s.g0) &&
-                  isfinite(w) && w >= 0.f;
+  const bool ok = finitef(muf) & (!QFP || (finitef(s.V) & finitef(s.go_hi))) &
+                  finitef(s.tx) & finitef(s.ty) & finitef(s.aeff) & finitef(s.g0) &
+                  finitef(w) & (w >= 0.f);
   if (!ok) {
     A.nonfinite = __fadd_rn(A.nonfinite, 1.f);
     return false;
@@ -1198,8 +1328,13 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
   // w 2^bits is exact in FP32, so this equals the FP64 path's rounding
   const unsigned long long q = p.weighted ? f2u64_rn(__fmul_rn(w, p.f.wscale)) : 1ull;
   if (nspec) {
-    const int b = energy_bin_f32(p, s.go_hi, s.go_lo);
-    const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+    int slot;
+    if (QFP) {
+      const int b = energy_bin_f32(p, s.go_hi, s.go_lo);
+      slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
+    } else {
+      slot = spec_slot(p, energy_coord_f1(p, s.go_hi));
+    }
     if (SHIST) atomicAdd(&hs[slot], (H)q);
     else atomicAdd(&p.acc_spec[slot], q);
   }
@@ -1217,79 +1352,129 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
   return true;
 }
 
-// Four classical samples (FP32, no variance or electron angle terms) into
-// the moment sums and histograms: the four contributions to each sum are
-// added plainly and folded into the compensated sum once.  If any of the
+// Plain partial sums of the FP32 classical vector path, packed (lane x:
+// the first sample of each pair, lane y: the second) over a few iterations,
+// then folded into the thread's compensated sums (ll_fold).  t0: weights
+// (count when unweighted), t1, t2: w d and w d^2 about the thread's shift,
+// t4, t5: w thx^2, w thy^2, t6: w a_eff, t7: w gamma0.
+struct LLSums {
+  float2 t0, t1, t2, t4, t5, t6, t7;
+};
+__device__ __forceinline__ void ll_sums_zero(LLSums& T) {
+  T.t0 = T.t1 = T.t2 = T.t4 = T.t5 = T.t6 = T.t7 = make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ void ll_fold(LLSums& T, AccF& A) {
+  kahan(A.s[0], A.c[0], __fadd_rn(T.t0.x, T.t0.y));
+  kahan(A.s[1], A.c[1], __fadd_rn(T.t1.x, T.t1.y));
+  kahan(A.s[2], A.c[2], __fadd_rn(T.t2.x, T.t2.y));
+  kahan(A.s[4], A.c[4], __fadd_rn(T.t4.x, T.t4.y));
+  kahan(A.s[5], A.c[5], __fadd_rn(T.t5.x, T.t5.y));
+  kahan(A.s[6], A.c[6], __fadd_rn(T.t6.x, T.t6.y));
+  kahan(A.s[7], A.c[7], __fadd_rn(T.t7.x, T.t7.y));
+  ll_sums_zero(T);
+}
+// Iterations (four samples each) between folds: a partial sum then holds
+// at most eight terms per lane, far below the compensated sums' error.
+constexpr int kLLFold = 4;
+
+// Histogram deposits of one pair: slots from packed coordinates.  ALL: every
+// histogram present (known at compile time); else the sizes decide.
+template <typename H, bool SHIST, bool W, bool ALL>
+__device__ __forceinline__ void ll_deposit(const Params& p, const LL2& P, float2 w, H* hs, H* hm,
+                                           H* ha, int nspec, int nmap, int naeff) {
+  const unsigned long long q0 = W ? f2u64_rn(__fmul_rn(w.x, p.f.wscale)) : 1ull;
+  const unsigned long long q1 = W ? f2u64_rn(__fmul_rn(w.y, p.f.wscale)) : 1ull;
+  if (ALL || nspec) {
+    int s0, s1;
+    if (!p.log_spaced) {
+      const float2 t = mul2(__fadd2_rn(P.mu, f2(-p.f.lo)), f2(p.f.inv_w));
+      s0 = spec_slot(p, t.x);
+      s1 = spec_slot(p, t.y);
+    } else {
+      s0 = spec_slot(p, energy_coord_f1(p, P.mu.x));
+      s1 = spec_slot(p, energy_coord_f1(p, P.mu.y));
+    }
+    if (SHIST) {
+      atomicAdd(&hs[s0], (H)q0);
+      atomicAdd(&hs[s1], (H)q1);
+    } else {
+      atomicAdd(&p.acc_spec[s0], q0);
+      atomicAdd(&p.acc_spec[s1], q1);
+    }
+  }
+  if (ALL || nmap) {
+    const float2 fx = mul2(__fadd2_rn(P.thx, f2(p.f.tmax)), f2(p.f.tsx));
+    const float2 fy = mul2(__fadd2_rn(P.thy, f2(p.f.tmax)), f2(p.f.tsy));
+    const int c0 = map_slot(p, fx.x, fy.x, nmap), c1 = map_slot(p, fx.y, fy.y, nmap);
+    if (SHIST) {
+      atomicAdd(&hm[c0], (H)q0);
+      atomicAdd(&hm[c1], (H)q1);
+    } else {
+      atomicAdd(&p.acc_map[c0], q0);
+      atomicAdd(&p.acc_map[c1], q1);
+    }
+  }
+  if (ALL || naeff) {
+    const float2 f = mul2(P.a, f2(p.f.a_scale));
+    const int a0 = aeff_slot(p, f.x), a1 = aeff_slot(p, f.y);
+    if (SHIST) {
+      atomicAdd(&ha[a0], (H)q0);
+      atomicAdd(&ha[a1], (H)q1);
+    } else {
+      atomicAdd(&p.acc_aeff[a0], q0);
+      atomicAdd(&p.acc_aeff[a1], q1);
+    }
+  }
+}
+
+// Four classical samples (two pairs; FP32, no variance or electron angle
+// terms) into the packed partial sums and the histograms.  If any of the
 // four is non-finite or has a negative weight, each goes through
 // accumulate_w instead (same skip rule).  W: weights present (else 1).
-template <typename H, bool SHIST, bool W>
-__device__ __forceinline__ void accumulate4_ll(const Params& p, const SampleF (&s)[4],
-                                               const float4 w4, AccF& A, H* hs, H* hm, H* ha,
-                                               int64_t nspec, int64_t nmap, int64_t naeff) {
-  const float w[4] = {w4.x, w4.y, w4.z, w4.w};
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    ok = ok && isfinite(s[k].mu_hi) && isfinite(s[k].tx) && isfinite(s[k].ty) &&
-         isfinite(s[k].aeff) && isfinite(s[k].g0) && (!W || (isfinite(w[k]) && w[k] >= 0.f));
+template <typename H, bool SHIST, bool W, bool ALL>
+__device__ __forceinline__ void accumulate4_ll(const Params& p, const LL2& P0, const LL2& P1,
+                                               const float4 w4, LLSums& T, AccF& A, H* hs,
+                                               H* hm, H* ha, int nspec, int nmap, int naeff) {
+  const float2 w01 = make_float2(w4.x, w4.y), w23 = make_float2(w4.z, w4.w);
+  bool ok = finitef(P0.mu.x) & finitef(P0.mu.y) & finitef(P1.mu.x) & finitef(P1.mu.y) &
+            finitef(P0.thx.x) & finitef(P0.thx.y) & finitef(P1.thx.x) & finitef(P1.thx.y) &
+            finitef(P0.thy.x) & finitef(P0.thy.y) & finitef(P1.thy.x) & finitef(P1.thy.y) &
+            finitef(P0.a.x) & finitef(P0.a.y) & finitef(P1.a.x) & finitef(P1.a.y) &
+            finitef(P0.g0.x) & finitef(P0.g0.y) & finitef(P1.g0.x) & finitef(P1.g0.y);
+  if (W)
+    ok = ok & (w4.x >= 0.f) & (w4.y >= 0.f) & (w4.z >= 0.f) & (w4.w >= 0.f) & finitef(w4.x) &
+         finitef(w4.y) & finitef(w4.z) & finitef(w4.w);
   if (!ok) {
+    const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      accumulate_w<H, SHIST, false>(p, s[k], W ? w[k] : 1.f, A, hs, hm, ha, nspec, nmap, naeff);
+      accumulate_w<H, SHIST, false>(p, ll_sample(k < 2 ? P0 : P1, k & 1), W ? w[k] : 1.f, A, hs,
+                                    hm, ha, nspec, nmap, naeff);
     return;
   }
-  if (isnan(A.shift)) A.shift = s[0].mu_hi;
-  float t0 = 0.f, t1 = 0.f, t2 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f, t7 = 0.f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float d = __fsub_rn(s[k].mu_hi, A.shift);
-    if (W) {
-      const float wd = __fmul_rn(w[k], d);
-      t0 = __fadd_rn(t0, w[k]);
-      t1 = __fadd_rn(t1, wd);
-      t2 = __fmaf_rn(wd, d, t2);
-      t4 = __fmaf_rn(__fmul_rn(w[k], s[k].thx0), s[k].thx0, t4);
-      t5 = __fmaf_rn(__fmul_rn(w[k], s[k].thy0), s[k].thy0, t5);
-      t6 = __fmaf_rn(w[k], s[k].aeff, t6);
-      t7 = __fmaf_rn(w[k], s[k].g0, t7);
-    } else {
-      t1 = __fadd_rn(t1, d);
-      t2 = __fmaf_rn(d, d, t2);
-      t4 = __fmaf_rn(s[k].thx0, s[k].thx0, t4);
-      t5 = __fmaf_rn(s[k].thy0, s[k].thy0, t5);
-      t6 = __fadd_rn(t6, s[k].aeff);
-      t7 = __fadd_rn(t7, s[k].g0);
-    }
+  if (isnan(A.shift)) A.shift = P0.mu.x;
+  const float2 nsh = f2(-A.shift);
+  const float2 d0 = __fadd2_rn(P0.mu, nsh), d1 = __fadd2_rn(P1.mu, nsh);
+  if (W) {
+    const float2 wd0 = mul2(w01, d0), wd1 = mul2(w23, d1);
+    T.t0 = __fadd2_rn(__fadd2_rn(T.t0, w01), w23);
+    T.t1 = __fadd2_rn(__fadd2_rn(T.t1, wd0), wd1);
+    T.t2 = fma2(wd1, d1, fma2(wd0, d0, T.t2));
+    T.t4 = fma2(mul2(w23, P1.thx), P1.thx, fma2(mul2(w01, P0.thx), P0.thx, T.t4));
+    T.t5 = fma2(mul2(w23, P1.thy), P1.thy, fma2(mul2(w01, P0.thy), P0.thy, T.t5));
+    T.t6 = fma2(w23, P1.a, fma2(w01, P0.a, T.t6));
+    T.t7 = fma2(w23, P1.g0, fma2(w01, P0.g0, T.t7));
+  } else {
+    T.t0 = __fadd2_rn(T.t0, f2(2.f));
+    T.t1 = __fadd2_rn(__fadd2_rn(T.t1, d0), d1);
+    T.t2 = fma2(d1, d1, fma2(d0, d0, T.t2));
+    T.t4 = fma2(P1.thx, P1.thx, fma2(P0.thx, P0.thx, T.t4));
+    T.t5 = fma2(P1.thy, P1.thy, fma2(P0.thy, P0.thy, T.t5));
+    T.t6 = __fadd2_rn(__fadd2_rn(T.t6, P0.a), P1.a);
+    T.t7 = __fadd2_rn(__fadd2_rn(T.t7, P0.g0), P1.g0);
   }
-  kahan(A.s[0], A.c[0], W ? t0 : 4.f);
-  kahan(A.s[1], A.c[1], t1);
-  kahan(A.s[2], A.c[2], t2);
-  kahan(A.s[4], A.c[4], t4);
-  kahan(A.s[5], A.c[5], t5);
-  kahan(A.s[6], A.c[6], t6);
-  kahan(A.s[7], A.c[7], t7);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    // w 2^bits is exact in FP32, so this equals the FP64 path's rounding
-    const unsigned long long q = W ? f2u64_rn(__fmul_rn(w[k], p.f.wscale)) : 1ull;
-    if (nspec) {
-      const int b = energy_bin_f32(p, s[k].go_hi, s[k].go_lo);
-      const int slot = b < 0 ? p.n_bins : (b >= p.n_bins ? p.n_bins + 1 : b);
-      if (SHIST) atomicAdd(&hs[slot], (H)q);
-      else atomicAdd(&p.acc_spec[slot], q);
-    }
-    if (nmap) {
-      const int c = map_cell_f32(p, s[k].tx, s[k].ty);
-      const int64_t slot = c < 0 ? nmap - 1 : c;
-      if (SHIST) atomicAdd(&hm[slot], (H)q);
-      else atomicAdd(&p.acc_map[slot], q);
-    }
-    if (naeff) {
-      const int slot = aeff_bin_f32(p, s[k].aeff);
-      if (SHIST) atomicAdd(&ha[slot], (H)q);
-      else atomicAdd(&p.acc_aeff[slot], q);
-    }
-  }
+  ll_deposit<H, SHIST, W, ALL>(p, P0, w01, hs, hm, ha, nspec, nmap, naeff);
+  ll_deposit<H, SHIST, W, ALL>(p, P1, w23, hs, hm, ha, nspec, nmap, naeff);
 }
 
 template <typename T, typename H, bool SHIST>

@@ -358,30 +358,47 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       if (p.weighted) vec = vec && ((uintptr_t)p.w & 15) == 0;
       if (vec) {
         const int64_t n4 = p.n >> 2;
-        // the four samples' moment contributions are summed, then folded into
-        // the compensated sums once (accumulate4_ll); unit weights specialised
-        auto run = [&](auto weighted) {
+        // two packed pairs per iteration; the moment contributions go to
+        // packed partial sums, folded into the compensated sums every
+        // kLLFold iterations (accumulate4_ll, ll_fold); unit weights and the
+        // case with every histogram present are specialised
+        const int ns = (int)nspec, nm = (int)nmap, na = (int)naeff;
+        auto run = [&](auto weighted, auto all_hist) {
           constexpr bool W = decltype(weighted)::value;
+          constexpr bool ALL = decltype(all_hist)::value;
+          LLSums ts;
+          ll_sums_zero(ts);
+          int it = 0;
           for (int64_t k = t0; k < n4; k += stride) {
             float4 v[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) v[c] = __ldg(static_cast<const float4*>(p.xi[c]) + k);
             const float4 wv = W ? __ldg(static_cast<const float4*>(p.w) + k)
                                 : make_float4(1.f, 1.f, 1.f, 1.f);
-            SampleF s4[4];
 #define QS_LO2(c) make_float2(v[c].x, v[c].y)
 #define QS_HI2(c) make_float2(v[c].z, v[c].w)
-            eval_ll_f32x2(p, QS_LO2(0), QS_LO2(1), QS_LO2(2), QS_LO2(3), QS_LO2(4), QS_LO2(5),
-                          s4[0], s4[1]);
-            eval_ll_f32x2(p, QS_HI2(0), QS_HI2(1), QS_HI2(2), QS_HI2(3), QS_HI2(4), QS_HI2(5),
-                          s4[2], s4[3]);
+            const LL2 P0 = eval_ll_pair(p, QS_LO2(0), QS_LO2(1), QS_LO2(2), QS_LO2(3), QS_LO2(4),
+                                        QS_LO2(5));
+            const LL2 P1 = eval_ll_pair(p, QS_HI2(0), QS_HI2(1), QS_HI2(2), QS_HI2(3), QS_HI2(4),
+                                        QS_HI2(5));
 #undef QS_LO2
 #undef QS_HI2
-            accumulate4_ll<H, SHIST, W>(p, s4, wv, acc, hs, hm, ha, nspec, nmap, naeff);
+            accumulate4_ll<H, SHIST, W, ALL>(p, P0, P1, wv, ts, acc, hs, hm, ha, ns, nm, na);
+            if (++it == kLLFold) {
+              ll_fold(ts, acc);
+              it = 0;
+            }
           }
+          ll_fold(ts, acc);
         };
-        if (p.weighted) run(std::true_type{});
-        else run(std::false_type{});
+        const bool all = nspec && nmap && naeff;
+        if (p.weighted) {
+          if (all) run(std::true_type{}, std::true_type{});
+          else run(std::true_type{}, std::false_type{});
+        } else {
+          if (all) run(std::false_type{}, std::true_type{});
+          else run(std::false_type{}, std::false_type{});
+        }
         i = 4 * n4 + t0;
       }
     }
