@@ -55,10 +55,16 @@ FMA_LANES_PER_SM = 128
 # Gaunt factor with g' and g'', the second-moment fit with h', and the mean
 # and variance updates) and 5 MUFU slots (2 lg2, 2 rcp, 2 ex2).
 GRAD_FMA_OPS_PER_STEP = 103
-# Photon spectrum (FP32): per (sample, cell, bin) evaluation 32 FMA-pipe
-# operations (24 in the packed part of F and the accumulation, 8 in the two
-# Hermite sums) and 3 MUFU slots (rcp, lg2, 2 ex2).
-PHOTON_FMA_OPS_PER_EVAL = 32
+# Photon spectrum (FP32): per (sample, cell, bin) evaluation 20 FMA-pipe
+# operations (13 in the packed part of F and the accumulation, 1 saturating
+# table coordinate, 6 in the two Horner sums) and 2.5 MUFU slots (rcp, lg2,
+# one ex2 at half a slot); the two table gathers (16 bytes each from shared
+# memory) took 0.223 shared-memory wavefronts per evaluation in an ncu
+# capture of this workload (consecutive log-spaced bins share intervals), at
+# one wavefront per SM and clock the pipe that binds.
+PHOTON_FMA_OPS_PER_EVAL = 20
+PHOTON_MUFU_SLOTS_PER_EVAL = 2.5
+PHOTON_SMEM_WAVEFRONTS_PER_EVAL = 0.223
 MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
@@ -517,14 +523,22 @@ def bench_photon(dev, rank, n=1 << 19, steps=2):
     kms = sum(x.elapsed_time(y) for x, y in kev) / steps
     evals = n * wl.laser.n_phase * pb.n_bins
     peak = _fma_peak(dev)
+    rate = evals / (kms * 1e-3)
+    clk = peak / FMA_LANES_PER_SM                    # SM x clock per second
     return {"metric": "beam-sample evals/s", "value": n / (kms * 1e-3), "unit": "samples/s",
             "kernel_ms": kms, "n_samples": n, "n_phase": wl.laser.n_phase,
             "photon_bins": "256 log-spaced on [1e-3, 6720] m c^2",
+            "evaluations_per_s": rate,
             "roofline": {"bound": "alu", "pipe": "fma",
-                         "achieved": PHOTON_FMA_OPS_PER_EVAL * evals / (kms * 1e-3) / 1e12,
+                         "achieved": PHOTON_FMA_OPS_PER_EVAL * rate / 1e12,
                          "peak": peak / 1e12, "unit": "Top/s",
-                         "frac": PHOTON_FMA_OPS_PER_EVAL * evals / peak / (kms * 1e-3),
-                         "evaluations": evals},
+                         "frac": PHOTON_FMA_OPS_PER_EVAL * rate / peak,
+                         "evaluations": evals, "ops_per_eval": PHOTON_FMA_OPS_PER_EVAL,
+                         "pipe_fracs": {
+                             "fma": PHOTON_FMA_OPS_PER_EVAL * rate / peak,
+                             "mufu": PHOTON_MUFU_SLOTS_PER_EVAL * rate / (MUFU_SLOTS_PER_SM * clk),
+                             "shared_memory": PHOTON_SMEM_WAVEFRONTS_PER_EVAL * rate / clk},
+                         "binding_pipe": "shared_memory"},
             "workload": "mc2p19_photon_qfp512"}
 
 

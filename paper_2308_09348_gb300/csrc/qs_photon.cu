@@ -26,7 +26,6 @@
 namespace qs {
 
 constexpr int kPhMaxBins = 512;               // photon-energy bins (16 per lane)
-constexpr int kPhK = kPhMaxBins / 32;
 constexpr int kPhN = 256;                     // table nodes in u = log2 y (du = 0.18: lanes on
                                               // consecutive log-spaced bins share nodes)
 constexpr double kPhUmin = -40.0, kPhUmax = 6.0;
@@ -59,67 +58,89 @@ __device__ void bessel_d(double y, double& k23, double& ki13, double* mk23p = nu
   if (k13) *k13 = dt * d;
 }
 
-// Table node n at u_n = umin + n du, y = 2^u: {q23, dq23/du du, q13,
-// dq13/du du} with q23 = log2 K_{2/3} + y log2 e + (2/3) u and
-// q13 = log2 Ki_{1/3} + y log2 e (both O(1) over the range: the small-y
-// power and the large-y exponential are taken out).
-__device__ float4 g_ph_tab[kPhN];
+// Table node values at u_n = umin + n du, y = 2^u, of the two Bessel
+// functions with the large-y exponential taken out: T23 = K_{2/3}(y) e^y and
+// T13 = -Ki_{1/3}(y) e^y (smooth in u: a power of y at small y, y^-1/2 at
+// large y), with their u-derivatives.  The FP32 table holds, per interval
+// [u_n, u_n+1], the cubic Hermite interpolant of each as monomial
+// coefficients in t = (u - u_n)/du:  p(t) = c0 + t (c1 + t (c2 + t c3)),
+//   c0 = v0, c1 = d0, c2 = 3 (v1 - v0) - 2 d0 - d1, c3 = 2 (v0 - v1) + d0 + d1
+// (d = dv/du du), computed in FP64: entry n for T23, kPhN + n for T13 (two
+// separate arrays, so that the ~16 consecutive intervals a warp's lanes
+// read are contiguous: two conflict-free wavefronts per gather).
+__device__ float4 g_ph_tab[2 * kPhN];
+
+__device__ void photon_node(int m, double& v23, double& d23, double& v13, double& d13) {
+  const double u = kPhUmin + m * kPhDu, y = exp2(u), ey = exp(y);
+  double k23, ki13, mk23p, k13;
+  bessel_d(y, k23, ki13, &mk23p, &k13);
+  const double dydu = y * 0.69314718055994530942 * kPhDu;   // dy/du du
+  v23 = k23 * ey;
+  d23 = (k23 - mk23p) * ey * dydu;          // d(K e^y)/dy = (K' + K) e^y
+  v13 = -ki13 * ey;
+  d13 = -(ki13 - k13) * ey * dydu;          // Ki' = -K_{1/3}
+}
+
+__device__ __forceinline__ float4 hermite_coeffs(double v0, double d0, double v1, double d1) {
+  return make_float4((float)v0, (float)d0, (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1),
+                     (float)(2.0 * (v0 - v1) + d0 + d1));
+}
 
 __global__ void __launch_bounds__(256) k_photon_setup() {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < kPhN; m += gridDim.x * blockDim.x) {
-    const double u = kPhUmin + m * kPhDu, y = exp2(u);
-    double k23, ki13, mk23p, k13;
-    bessel_d(y, k23, ki13, &mk23p, &k13);
-    const double q23 = log2(k23) + y * kLog2e + (2.0 / 3.0) * u;
-    const double q13 = log2(ki13) + y * kLog2e;
-    const double d23 = y * (1.0 - mk23p / k23) + 2.0 / 3.0;   // dq23/du
-    const double d13 = y * (1.0 - k13 / ki13);                // dq13/du
-    g_ph_tab[m] = make_float4((float)q23, (float)(d23 * kPhDu), (float)q13, (float)(d13 * kPhDu));
+    if (m == kPhN - 1) {                      // past the last interval: never read
+      g_ph_tab[m] = g_ph_tab[kPhN + m] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    double a0, a1, b0, b1, e0, e1, f0, f1;    // T23, d23 at nodes m, m+1; T13, d13
+    photon_node(m, a0, a1, b0, b1);
+    photon_node(m + 1, e0, e1, f0, f1);
+    g_ph_tab[m] = hermite_coeffs(a0, a1, e0, e1);
+    g_ph_tab[kPhN + m] = hermite_coeffs(b0, b1, f0, f1);
   }
 }
 
-// FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y) from the
-// table (cubic Hermite in u, then one ex2 per function); y in (0, ymax].
-__device__ __forceinline__ float hermite(float h01, float h10, float h11, float v0, float d0,
-                                         float v1, float d1) {
-  return __fmaf_rn(h11, d1, __fmaf_rn(h10, d0, __fmaf_rn(h01, __fsub_rn(v1, v0), v0)));
+// FP32: F(xi, chi) = (1 - xi + 1/(1 - xi)) K_{2/3}(y) - Ki_{1/3}(y)
+//   = e^-y ((1 - xi + 1/(1 - xi)) T23 + T13)
+// from the table (cubic in u by Horner's rule) and one ex2; y in (0, ymax].
+__device__ __forceinline__ float horner(float t, float4 c) {
+  return __fmaf_rn(__fmaf_rn(__fmaf_rn(c.w, t, c.z), t, c.y), t, c.x);
+}
+// x clamped to [0, 1] by the FMA's saturation (NaN gives 0).
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float d;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
 // Two photon energies e (two bins of one lane) against one emitter whose
 // {1/mu, 1/mu, 2/(3 chi), 2/(3 chi)} is pq: F for both, packed f32x2 except
-// the table gathers and the Hermite sums.  Bins beyond the emitter's cut
+// the table gathers and the Horner sums.  Bins beyond the emitter's cut
 // (y > ymax, or xi >= 1) give finite or NaN values that the caller discards;
-// their table index stays in range (fmaxf takes 0 over NaN).
+// their table index stays in range (the saturated coordinate is in [0, 1]).
 __device__ __forceinline__ float2 synch_F2(const float4* __restrict__ T, float2 e, float4 pq) {
+  constexpr float kS = (float)(kPhN - 1) - 1e-3f;            // x = s kS in [0, kPhN - 1)
   const float2 xi = mul2(e, make_float2(pq.x, pq.y));
   const float2 om = fma2(xi, f2(-1.f), f2(1.f));                      // 1 - xi
   const float2 r1 = rcpx2(om);
   const float2 y = mul2(mul2(make_float2(pq.z, pq.w), xi), r1);
   const float2 u = lg2x2(y);
-  float2 x = fma2(u, f2((float)(1.0 / kPhDu)), f2((float)(-kPhUmin / kPhDu)));
-  x.x = fminf(fmaxf(x.x, 0.f), (float)(kPhN - 1) - 1e-3f);
-  x.y = fminf(fmaxf(x.y, 0.f), (float)(kPhN - 1) - 1e-3f);
-  // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
-  // (x - 1/2 in [-1/2, kPhN - 1.501] keeps the sum in [2^23, 2^24), where the
-  // float spacing is 1), so the index is in [0, kPhN - 2] and t = x - index
-  // in [0, 1]
-  const float2 xm = __fadd2_rn(__fadd2_rn(x, f2(-0.5f)), f2(12582912.f));
+  // s = (u - umin) / (umax - umin) saturated to [0, 1]
+  const float sa = (float)(1.0 / (kPhUmax - kPhUmin)), sb = (float)(-kPhUmin / (kPhUmax - kPhUmin));
+  const float2 sx = make_float2(fma_sat(u.x, sa, sb), fma_sat(u.y, sa, sb));
+  // node index for x = s kS: x - 1/2 (rounded once, within 2^-17) rounded
+  // to the nearest integer by adding 1.5 2^23 (the sum lies in [2^23, 2^24),
+  // where the float spacing is 1), so the index is in [0, kPhN - 2] and
+  // t = x - index (one rounding of the exact difference) in [0, 1] up to
+  // 2^-17
+  const float2 xm = __fadd2_rn(fma2(sx, f2(kS), f2(-0.5f)), f2(12582912.f));
   const int i0 = __float_as_int(xm.x) - 0x4B400000, i1 = __float_as_int(xm.y) - 0x4B400000;
-  const float2 t = __fadd2_rn(x, fma2(xm, f2(-1.f), f2(12582912.f)));
-  const float2 t2 = mul2(t, t);
-  const float2 h01 = mul2(t2, fma2(f2(-2.f), t, f2(3.f)));           // 3t^2 - 2t^3
-  const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));              // t^3 - t^2
-  const float2 h10 = __fadd2_rn(fma2(t2, f2(-1.f), t), h11);         // t - 2t^2 + t^3
-  const float4 a0 = T[i0], a1 = T[i0 + 1], b0 = T[i1], b1 = T[i1 + 1];
-  const float2 q23 = make_float2(hermite(h01.x, h10.x, h11.x, a0.x, a0.y, a1.x, a1.y),
-                                 hermite(h01.y, h10.y, h11.y, b0.x, b0.y, b1.x, b1.y));
-  const float2 q13 = make_float2(hermite(h01.x, h10.x, h11.x, a0.z, a0.w, a1.z, a1.w),
-                                 hermite(h01.y, h10.y, h11.y, b0.z, b0.w, b1.z, b1.w));
-  const float2 ny = mul2(y, f2((float)(-kLog2e)));
-  const float2 k23 = ex2x2(__fadd2_rn(fma2(f2(-2.f / 3.f), u, q23), ny));
-  const float2 ki13 = ex2x2(__fadd2_rn(q13, ny));
-  // (1 - xi + 1/(1 - xi)) K_{2/3} - Ki_{1/3}
-  return fma2(ki13, f2(-1.f), mul2(__fadd2_rn(om, r1), k23));
+  const float2 t = fma2(sx, f2(kS), fma2(xm, f2(-1.f), f2(12582912.f)));
+  const float2 k23 = make_float2(horner(t.x, T[i0]), horner(t.y, T[i1]));   // K_{2/3} e^y
+  const float2 nk13 =
+      make_float2(horner(t.x, T[kPhN + i0]), horner(t.y, T[kPhN + i1]));     // -Ki_{1/3} e^y
+  const float2 emy = ex2x2(mul2(y, f2((float)(-kLog2e))));               // e^-y
+  return mul2(emy, fma2(__fadd2_rn(om, r1), k23, nk13));
 }
 
 // FP64: the same F from the integrals.
@@ -224,7 +245,7 @@ template <typename T>
 __host__ __device__ __forceinline__ size_t photon_smem(int n_phase, int nb, int block, bool ang,
                                                        int var) {
   const size_t tab = ((size_t)n_phase * (sizeof(T) == 4 ? 16 : 8) + 15) & ~(size_t)15;
-  const size_t pt = sizeof(T) == 4 ? (size_t)kPhN * sizeof(float4) : 0;
+  const size_t pt = sizeof(T) == 4 ? (size_t)2 * kPhN * sizeof(float4) : 0;
   const size_t e = ((size_t)nb * sizeof(T) + 15) & ~(size_t)15;
   const size_t stage = sizeof(T) == 4 ? (size_t)(block / 32) * 64 * (ang ? 3 : 2) * sizeof(float4) : 0;
   const size_t state = sizeof(T) == 4 ? (size_t)ph_state_fields(var) * block * sizeof(float) : 0;
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
   const size_t tb = ((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15;
   TT* tab = reinterpret_cast<TT*>(smem);
   float4* ptab = reinterpret_cast<float4*>(smem + tb);
-  T* eps = reinterpret_cast<T*>(smem + tb + (sizeof(T) == 4 ? kPhN * sizeof(float4) : 0));
+  T* eps = reinterpret_cast<T*>(smem + tb + (sizeof(T) == 4 ? 2 * kPhN * sizeof(float4) : 0));
   double* part = reinterpret_cast<double*>(
       reinterpret_cast<unsigned char*>(eps) + (((size_t)nb * sizeof(T) + 15) & ~(size_t)15));
   const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -265,7 +286,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
   };
   for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) table_entry(p, j, tab);
   if (sizeof(T) == 4)
-    for (int j = threadIdx.x; j < kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
+    for (int j = threadIdx.x; j < 2 * kPhN; j += blockDim.x) ptab[j] = g_ph_tab[j];
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
     eps[b] = (T)(log_spaced ? lo * exp2(log2(hi / lo) * (b + 0.5) / nb)
                             : lo + (b + 0.5) * (hi - lo) / nb);
@@ -367,38 +388,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : ((KB == 8 && !ANG) ?
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         __syncwarp();
-        // lane b takes bins b and b + 32 of each group pair against every
-        // emitter (packed, independent evaluations, summed plainly over the
-        // 64, then compensated in shared memory).  No branch on the cut:
-        // bins beyond an emitter's cut are evaluated and dropped by the
-        // select (the clamped table index keeps every read in the table), so
-        // the unrolled evaluations of consecutive emitters interleave.
+        // lane b takes bins b + 32 k (k < KB) against every emitter: up to
+        // four bin pairs at a time (packed, independent evaluations) share
+        // each emitter's staged constants; summed plainly over the 64
+        // emitters, then compensated in shared memory.  No branch on the
+        // cut: bins beyond an emitter's cut are evaluated and dropped by the
+        // select (the saturated table coordinate keeps every read in the
+        // table), so the unrolled evaluations interleave.  Bin pairs whose
+        // lowest energy is above every emitter's cut are skipped.
 #pragma unroll
-        for (int kk = 0; kk < KB; kk += 2) {
-          if (32 * kk >= nb || !(eps[32 * kk] < emax)) break;
-          const int b0 = 32 * kk + lane, b1 = b0 + 32;
-          const float2 e = make_float2(b0 < nb ? eps[b0] : 3.4e38f, b1 < nb ? eps[b1] : 3.4e38f);
-          float2 ps = f2(0.f), px = f2(0.f), py = f2(0.f);
-#pragma unroll 4
+        for (int kc = 0; kc < KB; kc += 8) {
+          int np = 0;                                    // active bin pairs (warp-uniform)
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+            if (kc + 2 * k4 < KB && 32 * (kc + 2 * k4) < nb && eps[32 * (kc + 2 * k4)] < emax)
+              np = k4 + 1;
+          if (np == 0) break;
+          float2 e[4], ps[4], px[4], py[4];
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const int b0 = 32 * (kc + 2 * k4) + lane, b1 = b0 + 32;
+            e[k4] = make_float2(b0 < nb ? eps[b0] : 3.4e38f, b1 < nb ? eps[b1] : 3.4e38f);
+            ps[k4] = px[k4] = py[k4] = f2(0.f);
+          }
+#pragma unroll 2
           for (int q = 0; q < 64; ++q) {
-            const float4 qq = stQ[q];
-            const bool in0 = e.x < qq.z, in1 = e.y < qq.z;
-            const float2 F = synch_F2(ptab, e, stP[q]);
-            const float2 Fm = make_float2(in0 ? F.x : 0.f, in1 ? F.y : 0.f);
-            ps = fma2(make_float2(qq.x, qq.y), Fm, ps);
-            if constexpr (ANG) {
-              const float4 aq = stA[q];
-              px = fma2(make_float2(aq.x, aq.y), Fm, px);
-              py = fma2(make_float2(aq.z, aq.w), Fm, py);
+            const float4 qq = stQ[q], pq = stP[q];
+            float4 aq;
+            if constexpr (ANG) aq = stA[q];
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              if (k4 < np) {
+                const float2 F = synch_F2(ptab, e[k4], pq);
+                const float2 Fm = make_float2(e[k4].x < qq.z ? F.x : 0.f,
+                                              e[k4].y < qq.z ? F.y : 0.f);
+                ps[k4] = fma2(make_float2(qq.x, qq.y), Fm, ps[k4]);
+                if constexpr (ANG) {
+                  px[k4] = fma2(make_float2(aq.x, aq.y), Fm, px[k4]);
+                  py[k4] = fma2(make_float2(aq.z, aq.w), Fm, py[k4]);
+                }
+              }
             }
           }
-          acc.add(0, kk, ps.x);
-          acc.add(0, kk + 1, ps.y);
-          if constexpr (ANG) {
-            acc.add(1, kk, px.x);
-            acc.add(1, kk + 1, px.y);
-            acc.add(2, kk, py.x);
-            acc.add(2, kk + 1, py.y);
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            if (k4 < np) {
+              const int kk = kc + 2 * k4;
+              acc.add(0, kk, ps[k4].x);
+              acc.add(0, kk + 1, ps[k4].y);
+              if constexpr (ANG) {
+                acc.add(1, kk, px[k4].x);
+                acc.add(1, kk + 1, px[k4].y);
+                acc.add(2, kk, py[k4].x);
+                acc.add(2, kk + 1, py[k4].y);
+              }
+            }
           }
         }
         __syncwarp();
