@@ -483,7 +483,7 @@ int32_t qs_scatter_noalloc(const qs_laser* laser, const qs_beam* beam,
  * 0 <= lo < hi (lo > 0 when log_spaced); its map, a_eff and smoothing
  * fields are ignored.  Photons with y > 60 (relative weight e^-60) are
  * dropped.  FP64: the Bessel functions from their integral representations
- * (slow: for checks); FP32: cubic Hermite tables of log K in log y (relative
+ * (slow: for checks); FP32: cubic Hermite tables of K e^y in log y (relative
  * error ~3e-7), built on the device by the first FP32 call on that device
  * (one launch and a wait: make that call before any stream capture; a
  * capturing first call returns QS_ERR_UNSUPPORTED).  Sums are in a fixed

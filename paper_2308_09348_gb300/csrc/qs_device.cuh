@@ -206,6 +206,13 @@ __device__ __forceinline__ double op_fma(double a, double b, double c) { return 
 // Model variant bits of the kernels' VAR template argument.
 constexpr int kVarCell = 1;    // per-cell focus
 constexpr int kVarCycle = 2;   // cycle-resolved chi
+// Internal: the FP32 cycle-resolved tables are replicated kCycRep times,
+// interleaved element by element (entry e of copy c at e kCycRep + c), and
+// each lane reads copy lane % kCycRep through its own table pointer: the
+// eight lanes of each quarter-warp phase of a 16-byte shared-memory load
+// then fall in eight distinct bank quads whatever their chi.
+constexpr int kVarCycRep = 4;
+constexpr int kCycRep = 8;
 
 // Cycle-resolved chi (QS_VARIANT_CYCLE_CHI).  Over one cycle of a linearly
 // polarised field chi(psi) = sqrt2 chi |cos psi|; the rates take the cycle
@@ -287,6 +294,7 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
 //   A[n]         = {G_n, dG_n, G_{n+1}, dG_{n+1}}
 //   A[kCycN + n] = {H_n, dH_n, H_{n+1}, dH_{n+1}},
 // at u_n = n du, the derivatives in u times the spacing.
+template <int CR = 1>
 __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float chi, float& G,
                                              float& S, float& H) {
   const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
@@ -305,7 +313,7 @@ __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float
   const float d01 = __fmul_rn(6.f, __fsub_rn(t, t2));
   const float d10 = __fmaf_rn(3.f, t2, __fmaf_rn(-4.f, t, 1.f));
   const float d11 = __fmaf_rn(3.f, t2, __fmul_rn(-2.f, t));
-  const float4 g = A[idx], h = A[kCycN + idx];
+  const float4 g = A[idx * CR], h = A[(kCycN + idx) * CR];
   const float dG = __fsub_rn(g.z, g.x);
   G = __fmaf_rn(h11, g.w, __fmaf_rn(h10, g.y, __fmaf_rn(h01, dG, g.x)));
   H = __fmaf_rn(h11, h.w, __fmaf_rn(h10, h.y, __fmaf_rn(h01, __fsub_rn(h.z, h.x), h.x)));
@@ -506,8 +514,9 @@ __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, cons
   float2 g, s2, h2c;
   if constexpr ((VAR & kVarCycle) != 0) {
     float2 s, h2;
-    cycle_lookup(cA, chi.x, g.x, s.x, h2.x);
-    cycle_lookup(cA, chi.y, g.y, s.y, h2.y);
+    constexpr int CR = (VAR & kVarCycRep) ? kCycRep : 1;
+    cycle_lookup<CR>(cA, chi.x, g.x, s.x, h2.x);
+    cycle_lookup<CR>(cA, chi.y, g.y, s.y, h2.y);
     s2 = mul2(f2(-2.f), s);
     h2c = mul2(C55, h2);
   } else {

@@ -190,10 +190,10 @@ Smem smem_plan(const Plan& pl, int precision, int cells, int variant, bool weigh
   Smem sm;
   const bool cell_focus = variant != 0;
   // table entries: double G (FP64 path) or float4 {G, G, G^2, G^2} or
-  // {G, G, s_j, s_j} (FP32 path); then the cycle tables
+  // {G, G, s_j, s_j} (FP32 path); then the cycle tables (replicated)
   const size_t tab = align_up((size_t)cells * (precision == QS_F64 ? 8 : 16), 16) +
                      ((variant & QS_VARIANT_CYCLE_CHI) && precision == QS_F32
-                          ? (size_t)2 * kCycN * sizeof(float4)
+                          ? (size_t)2 * kCycN * kCycRep * sizeof(float4)
                           : 0);
   const size_t red = (size_t)(block / 32) * kNumMom * sizeof(double);
   const size_t hist = align_up((size_t)(pl.nspec + pl.nmap + pl.naeff) * (weighted ? 8 : 4), 16);
@@ -259,16 +259,16 @@ int scatter_block(const qs_exec* e, int block, int prec, bool qfp, int variant) 
 }
 
 // Shared memory of the phase table and, FP32 cycle-resolved chi, the cycle
-// tables behind it.
-template <typename T, bool QFP, int VAR>
+// tables behind it (REP: replicated kCycRep times, as k_scatter reads them).
+template <typename T, bool QFP, int VAR, bool REP = false>
 __device__ __forceinline__ size_t table_bytes(const Params& p) {
   using TT = typename Tab<T>::type;
   constexpr bool cells = QFP || (VAR & kVarCell);
   constexpr bool cyc = sizeof(T) == 4 && (VAR & kVarCycle);
   return (cells ? (((size_t)p.n_phase * sizeof(TT) + 15) & ~(size_t)15) : 0) +
-         (cyc ? (size_t)2 * kCycN * sizeof(float4) : 0);
+         (cyc ? (size_t)2 * kCycN * (REP ? kCycRep : 1) * sizeof(float4) : 0);
 }
-template <typename T, bool QFP, int VAR>
+template <typename T, bool QFP, int VAR, bool REP = false>
 __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem,
                                             const float4** cA) {
   using TT = typename Tab<T>::type;
@@ -279,12 +279,14 @@ __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem
     float4* A = reinterpret_cast<float4*>(smem + (((size_t)p.n_phase * sizeof(TT) + 15) &
                                                   ~(size_t)15));
     // node-pair tables: {G_n, dG_n, G_n+1, dG_n+1}, then {H_n, dH_n, H_n+1, dH_n+1}
-    for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
+    constexpr int R = REP ? kCycRep : 1;
+    for (int jc = threadIdx.x; jc < (kCycN - 1) * R; jc += blockDim.x) {
+      const int j = jc / R, c = jc - j * R;
       const float4 a = p.cyc_a[j], b = p.cyc_a[j + 1];
-      A[j] = make_float4(a.x, a.y, b.x, b.y);
-      A[kCycN + j] = make_float4(a.z, a.w, b.z, b.w);
+      A[j * R + c] = make_float4(a.x, a.y, b.x, b.y);
+      A[(kCycN + j) * R + c] = make_float4(a.z, a.w, b.z, b.w);
     }
-    *cA = A;
+    *cA = A + (REP ? (threadIdx.x % kCycRep) : 0);
   }
 }
 
@@ -293,7 +295,10 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
   using TT = typename Tab<T>::type;
   constexpr bool LOC = (VAR & kVarCell) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  const size_t tab_bytes = table_bytes<T, QFP, VAR>(p);
+  // FP32 cycle-resolved chi: replicated tables (kVarCycRep)
+  constexpr bool REP = sizeof(T) == 4 && (VAR & kVarCycle) != 0;
+  constexpr int VR = REP ? (VAR | kVarCycRep) : VAR;
+  const size_t tab_bytes = table_bytes<T, QFP, VAR, REP>(p);
   TT* tab = reinterpret_cast<TT*>(smem);
   const float4* cA = nullptr;
   double* red = reinterpret_cast<double*>(smem + tab_bytes);
@@ -310,7 +315,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
   unsigned long long* ssm = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(sh) + hist_bytes);
   unsigned long long* hsm = nsm ? (p.smooth_in_smem ? ssm : p.acc_smooth) : nullptr;
 
-  load_tables<T, QFP, VAR>(p, smem, &cA);
+  load_tables<T, QFP, VAR, REP>(p, smem, &cA);
   if (SHIST)
     for (int64_t b = threadIdx.x; b < nspec + nmap + naeff; b += blockDim.x) sh[b] = 0;
   if (nsm && p.smooth_in_smem)
@@ -334,7 +339,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       bool ok0 = false, ok1 = false;
       if (i0 < p.n) {
         SampleF s0, s1;
-        eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
+        eval_pair_f32_qfp<VR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
         ok0 = accumulate<T, H, SHIST>(p, s0, i0, acc, hs, hm, ha, nspec, nmap, naeff);
         if (i1 != i0)
           ok1 = accumulate<T, H, SHIST>(p, s1, i1, acc, hs, hm, ha, nspec, nmap, naeff);
@@ -407,7 +412,7 @@ __global__ void __maxnreg__((kScatterRegs<T, QFP, VAR>)) k_scatter(const Params 
       typename DepT<T>::type d;
       bool ok = false;
       if (ii < p.n) {
-        const auto s = eval_one<T, QFP, VAR>(p, tab, ii, cA);
+        const auto s = eval_one<T, QFP, VR>(p, tab, ii, cA);
         ok = accumulate<T, H, SHIST>(p, s, ii, acc, hs, hm, ha, nspec, nmap, naeff);
         dep_set(d, s);
       }
