@@ -69,8 +69,9 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
 # capture, keyed by the hash of the kernel sources it was taken with; any
-# other source version reports null.
-TRAFFIC_BY_SOURCE = {"549d66af8bcec180": 8 * (268.62e6 + 4.02e6)}
+# other source version reports null.  The capture ran 2^23 samples (read
+# and write both grow with the sample count), scaled by 8 to the 2^26 launch.
+TRAFFIC_BY_SOURCE = {"a7fef076616ce060": 8 * (269.31e6 + 3.75e6)}
 
 
 def parse():
