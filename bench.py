@@ -950,7 +950,10 @@ def main():
                                     "source": "the FP32 kernel's packed instructions"},
             "oracle_expression_ops_per_sample_step": {"fma_pipe": ORACLE_CELL_FMA_OPS,
                                                       "mufu_slots": ORACLE_CELL_MUFU_SLOTS},
-            "frac_vs_oracle_expression_count":
+            # time the oracle expression's operation count needs at the pipes'
+            # peaks over the kernel's time: above 1 when the kernel computes
+            # the cell with fewer operations than the expression as written
+            "oracle_expression_bound_over_kernel_time":
                 max(ORACLE_CELL_FMA_OPS * steps_total / peak_fma,
                     ORACLE_CELL_MUFU_SLOTS * steps_total / peak_mufu) / t_k,
             "mufu_frac_of_measured": t_meas_mufu / t_k,
