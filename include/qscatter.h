@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define QS_VERSION 9
+#define QS_VERSION 10
 
 /*
  * Status codes.  QS_ERR_NONFINITE is returned only when the caller asks for
@@ -337,19 +337,30 @@ int32_t qs_scatter_host(const qs_laser* laser, const qs_beam* beam, const qs_sam
  *                 integrates ALL samples (a parameter sweep, e.g. over the
  *                 delay, on one sampled beam)
  *   samples       the concatenated streams (as for qs_scatter)
- *   bins          energy spectrum and, with smooth_sigma_bins > 0, the
- *                 kernel-smoothed spectrum (n_tx = n_aeff = 0); shared bin
- *                 count, range per shot from d_ranges if not NULL (n_shots
- *                 pairs {lo, hi}, device) else bins->lo/hi
+ *   bins          energy spectrum, with smooth_sigma_bins > 0 the
+ *                 kernel-smoothed spectrum, with n_tx > 0 the divergence map
+ *                 and with n_aeff > 0 the a_eff histogram of every shot;
+ *                 shared bin counts and map extent, energy range per shot
+ *                 from d_ranges if not NULL (n_shots pairs {lo, hi}, device)
+ *                 else bins->lo/hi
  *   max_phase     upper bound of the n_phase of the shots that use phase
  *                 cells (QS_MODEL_QFP or QS_VARIANT_CELL_FOCUS), 1..4096
  *   d_spectra     n_shots x n_bins doubles (row per shot), or NULL if n_bins == 0
  *   d_spec_smooth n_shots x n_bins doubles (row per shot) when
  *                 smooth_sigma_bins > 0, else ignored (may be NULL)
+ *   d_divmaps     n_shots x n_tx x n_ty doubles (map of shot s at offset
+ *                 s n_tx n_ty, layout as qs_scatter's) when n_tx > 0, else
+ *                 ignored (may be NULL); the weight outside shot s's map in
+ *                 its moments' map_out
+ *   d_aeff_hists  n_shots x n_aeff doubles (row per shot) when n_aeff > 0,
+ *                 else ignored (may be NULL)
  *   d_moments     n_shots qs_moments
  * The workspace size (qs_batch_workspace_bytes) depends on shared_samples:
  * nonzero for the sweep form (d_offsets == NULL), whose tile slots grow with
- * n_shots x n_total / tile.
+ * n_shots x n_total / tile.  The maps and a_eff histograms are accumulated in
+ * the workspace (8 bytes per bin and shot: 537 MB for 4096 shots of a
+ * 128 x 128 map) with global integer atomics; the energy spectrum per tile in
+ * shared memory.
  * Shots may mix the models and the variants; shots with a variant run in a
  * second persistent launch over the same (shot, tile) schedule.  The call
  * is a fixed sequence of two memsets and six kernels on the stream and
@@ -365,8 +376,8 @@ int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers, const qs_bea
                          const int64_t* d_offsets, const qs_samples* samples,
                          const qs_bins* bins, const double* d_ranges, int32_t max_phase,
                          const qs_exec* exec, double* d_spectra, double* d_spec_smooth,
-                         qs_moments* d_moments, void* d_workspace, size_t ws_bytes,
-                         void* stream);
+                         double* d_divmaps, double* d_aeff_hists, qs_moments* d_moments,
+                         void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
  * Parameter order of qs_scatter_grad (the reconstruction use of Sec. 6):

@@ -144,8 +144,8 @@ def _lib():
             L.qs_batch_workspace_bytes.restype = C.c_size_t
             L.qs_scatter_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
                                            C.POINTER(qs_bins), _VP, C.c_int32,
-                                           C.POINTER(qs_exec), _VP, _VP, _VP, _VP, C.c_size_t,
-                                           _VP]
+                                           C.POINTER(qs_exec), _VP, _VP, _VP, _VP, _VP, _VP,
+                                           C.c_size_t, _VP]
             L.qs_scatter_batch.restype = C.c_int32
             L.qs_scatter_grad_batch.argtypes = [C.c_int32, _VP, _VP, _VP, C.POINTER(qs_samples),
                                                 C.POINTER(qs_bins), _VP, C.c_int32,
@@ -486,6 +486,12 @@ class Batch:
         self.spectra = torch.zeros(self.n_shots, nb, dtype=torch.float64, device=dev)
         self.spec_smooth = torch.zeros(self.n_shots, nb if bins.smooth_sigma_bins > 0 else 0,
                                        dtype=torch.float64, device=dev)
+        # per-shot divergence maps (n_shots x n_ty x n_tx, each laid out as
+        # qs_scatter's map) and a_eff histograms, when the bins ask for them
+        self.divmaps = torch.zeros(self.n_shots, max(bins.n_ty, 0) if bins.n_tx > 0 else 0,
+                                   max(bins.n_tx, 0), dtype=torch.float64, device=dev)
+        self.aeff_hists = torch.zeros(self.n_shots, max(bins.n_aeff, 0), dtype=torch.float64,
+                                      device=dev)
         self.moments = torch.zeros(self.n_shots, len(MOMENT_FIELDS), dtype=torch.float64, device=dev)
         self.grads = torch.zeros(self.n_shots, len(GRAD_PARAMS), dtype=torch.float64, device=dev)
         e = make_exec(precision, 0, block, grid, None, tile)
@@ -513,6 +519,8 @@ class Batch:
             self.d_ranges.data_ptr() if self.d_ranges is not None else None, self.max_phase,
             C.byref(e), self.spectra.data_ptr() if self.spectra.numel() else None,
             self.spec_smooth.data_ptr() if self.spec_smooth.numel() else None,
+            self.divmaps.data_ptr() if self.divmaps.numel() else None,
+            self.aeff_hists.data_ptr() if self.aeff_hists.numel() else None,
             self.moments.data_ptr(), self.ws_ptr, self.ws_bytes, _stream_ptr(stream))
         _check(st, "qs_scatter_batch")
         return self

@@ -42,6 +42,8 @@ struct BatchArgs {
   void* tables;                 // [n_shots * max_phase] float4 (FP32) or double (FP64)
   unsigned long long* acc;      // [n_shots * (n_bins + 2)]
   unsigned long long* acc_smooth;  // [n_shots * n_bins] (smoothed spectrum) or null
+  unsigned long long* acc_map;     // [n_shots * (n_tx n_ty + 1)] (divergence maps) or null
+  unsigned long long* acc_aeff;    // [n_shots * (n_aeff + 1)] (a_eff histograms) or null
   double* partials;             // [tiles * kNumMom]
   unsigned long long* counter;  // [0] work counter of the variant-0 kernels,
                                 // [1] that of the model-variant kernels,
@@ -91,6 +93,9 @@ __global__ void k_bsetup(const BatchArgs a) {
   p.weighted = a.samples.w != nullptr;
   p.acc_spec = a.bins.n_bins > 0 ? a.acc + (size_t)s * (a.bins.n_bins + 2) : nullptr;
   p.acc_smooth = a.acc_smooth ? a.acc_smooth + (size_t)s * a.bins.n_bins : nullptr;
+  p.acc_map = a.acc_map ? a.acc_map + (size_t)s * ((size_t)a.bins.n_tx * a.bins.n_ty + 1)
+                        : nullptr;
+  p.acc_aeff = a.acc_aeff ? a.acc_aeff + (size_t)s * (a.bins.n_aeff + 1) : nullptr;
   p.cyc_gl = a.cyc_gl;
   p.cyc_a = a.cyc_a;
   a.tiles[s] = (p.n + a.tile - 1) / a.tile;
@@ -195,6 +200,9 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
                     : nullptr;
   const int64_t total = a.tiles[a.n_shots];
   const int64_t nspec = a.bins.n_bins > 0 ? (int64_t)a.bins.n_bins + 2 : 0;
+  // per-shot divergence map and a_eff histogram: global accumulators
+  const int64_t nmap = a.acc_map ? (int64_t)a.bins.n_tx * a.bins.n_ty + 1 : 0;
+  const int64_t naeff = a.acc_aeff ? (int64_t)a.bins.n_aeff + 1 : 0;
   const int lane = threadIdx.x & 31;
   int cur = -1;
   if (VARK && a.counter[2] == 0ull) return;        // no shot uses a variant
@@ -269,9 +277,9 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
             if (i0 < last) {
               SampleF s0, s1;
               eval_pair_f32_qfp<VAR>(p, reinterpret_cast<const float4*>(tab), i0, i1, s0, s1, cA);
-              ok0 = accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, 0, 0);
+              ok0 = accumulate<T, H, true>(p, s0, i0, acc, hs, nullptr, nullptr, nspec, nmap, naeff);
               if (i1 != i0)
-                ok1 = accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, 0, 0);
+                ok1 = accumulate<T, H, true>(p, s1, i1, acc, hs, nullptr, nullptr, nspec, nmap, naeff);
               dep_set(d0, s0);
               dep_set(d1, s1);
             }
@@ -290,7 +298,7 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
           if (i < last) {
             const auto sm = p.model == QS_MODEL_QFP ? eval_one<T, true, VAR>(p, tab, i, cA)
                                                     : eval_one<T, false, VAR & kVarCell>(p, tab, i, cA);
-            ok = accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, 0, 0);
+            ok = accumulate<T, H, true>(p, sm, i, acc, hs, nullptr, nullptr, nspec, nmap, naeff);
             dep_set(d, sm);
           }
           if (hsm) deposit_warp(p, ok, d, i, hsm);
@@ -317,20 +325,24 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
 }
 
 // One warp per shot: moments from its tiles' partials in tile order.
-__global__ void k_bfinal(const BatchArgs a, double* spectra, double* smooth,
-                         qs_moments* moments) {
+__global__ void k_bfinal(const BatchArgs a, double* spectra, double* smooth, double* divmaps,
+                         double* aeff_hists, qs_moments* moments) {
   const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= a.n_shots) return;
   const Params& p = a.shot[s];
   const int nb = a.bins.n_bins;
   const bool sm = a.acc_smooth != nullptr;
+  const int64_t nm = a.acc_map ? (int64_t)a.bins.n_tx * a.bins.n_ty : 0;
+  const int na = a.acc_aeff ? a.bins.n_aeff : 0;
   qs_moments m;
   memset(&m, 0, sizeof(m));
   if (p.n < 0) {
     for (int b = lane; b < nb; b += 32) spectra[(size_t)s * nb + b] = 0.0;
     if (sm)
       for (int b = lane; b < nb; b += 32) smooth[(size_t)s * nb + b] = 0.0;
+    for (int64_t b = lane; b < nm; b += 32) divmaps[(size_t)s * nm + b] = 0.0;
+    for (int b = lane; b < na; b += 32) aeff_hists[(size_t)s * na + b] = 0.0;
     if (lane == 0) {
       m.nonfinite = -1.0;
       moments[s] = m;
@@ -371,6 +383,8 @@ __global__ void k_bfinal(const BatchArgs a, double* spectra, double* smooth,
   if (sm)
     for (int b = lane; b < nb; b += 32)
       smooth[(size_t)s * nb + b] = (double)p.acc_smooth[b] / p.wscale;
+  for (int64_t b = lane; b < nm; b += 32) divmaps[(size_t)s * nm + b] = (double)p.acc_map[b] * scale;
+  for (int b = lane; b < na; b += 32) aeff_hists[(size_t)s * na + b] = (double)p.acc_aeff[b] * scale;
   if (lane == 0) {
     const double W = v[0];
     m.W = W;
@@ -387,6 +401,7 @@ __global__ void k_bfinal(const BatchArgs a, double* spectra, double* smooth,
     }
     m.under = nb > 0 ? (double)acc[nb] * scale : 0.0;
     m.over = nb > 0 ? (double)acc[nb + 1] * scale : 0.0;
+    m.map_out = nm ? (double)p.acc_map[nm] * scale : 0.0;
     m.nonfinite = v[8];
     moments[s] = m;
   }
@@ -545,7 +560,7 @@ namespace {
 
 struct BatchPlan {
   size_t off_counter = 0, off_params = 0, off_tiles = 0, off_tables = 0, off_acc = 0,
-         off_smooth = 0, off_part = 0, bytes = 0;
+         off_smooth = 0, off_map = 0, off_aeff = 0, off_part = 0, bytes = 0;
   int64_t max_tiles = 0;
 };
 
@@ -566,6 +581,11 @@ bool batch_plan(BatchPlan& bp, int32_t n_shots, int64_t n_total, const qs_bins* 
   off = align_up(off + (size_t)n_shots * (bins->n_bins > 0 ? bins->n_bins + 2 : 0) * 8, 256);
   bp.off_smooth = off;
   off = align_up(off + (size_t)n_shots * (bins->smooth_sigma_bins > 0 ? bins->n_bins : 0) * 8, 256);
+  bp.off_map = off;
+  off = align_up(off + (size_t)n_shots *
+                           (bins->n_tx > 0 ? (size_t)bins->n_tx * bins->n_ty + 1 : 0) * 8, 256);
+  bp.off_aeff = off;
+  off = align_up(off + (size_t)n_shots * (bins->n_aeff > 0 ? bins->n_aeff + 1 : 0) * 8, 256);
   bp.off_part = off; off = align_up(off + (size_t)bp.max_tiles * kNumMom * 8, 256);
   bp.bytes = off;
   return true;
@@ -577,7 +597,6 @@ int32_t batch_checks(int32_t n_shots, const qs_samples* samples, const qs_bins* 
   int32_t st;
   if (n_shots < 1 || max_phase < 1 || max_phase > kMaxPhase) return QS_ERR_INVALID_ARG;
   if ((st = validate_samples(samples)) || (st = validate_bins(bins))) return st;
-  if (bins->n_tx > 0 || bins->n_aeff > 0) return QS_ERR_UNSUPPORTED;
   if ((st = exec_opts(exec, prec, wbits, block, grid))) return st;
   if ((st = exec_tile(exec, tile))) return st;
   return QS_OK;
@@ -662,6 +681,8 @@ int32_t batch_prepare(BatchArgs& a, int32_t n_shots, const qs_laser* d_lasers,
   a.acc_smooth = bins->smooth_sigma_bins > 0
                      ? reinterpret_cast<unsigned long long*>(ws + bp.off_smooth)
                      : nullptr;
+  a.acc_map = bins->n_tx > 0 ? reinterpret_cast<unsigned long long*>(ws + bp.off_map) : nullptr;
+  a.acc_aeff = bins->n_aeff > 0 ? reinterpret_cast<unsigned long long*>(ws + bp.off_aeff) : nullptr;
   a.partials = reinterpret_cast<double*>(ws + bp.off_part);
   a.counter = reinterpret_cast<unsigned long long*>(ws + bp.off_counter);
   a.max_tiles = bp.max_tiles;
@@ -728,7 +749,8 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
                                     const qs_samples* samples, const qs_bins* bins,
                                     const double* d_ranges, int32_t max_phase,
                                     const qs_exec* exec, double* d_spectra,
-                                    double* d_spec_smooth, qs_moments* d_moments,
+                                    double* d_spec_smooth, double* d_divmaps,
+                                    double* d_aeff_hists, qs_moments* d_moments,
                                     void* d_workspace, size_t ws_bytes, void* stream) {
   int prec, wbits, block, grid, tile, sms;
   int32_t st = batch_checks(n_shots, samples, bins, max_phase, exec, &prec, &wbits, &block, &grid,
@@ -737,6 +759,8 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
   if (!d_moments) return QS_ERR_INVALID_ARG;
   if (bins->n_bins > 0 && !d_spectra) return QS_ERR_INVALID_ARG;
   if (bins->smooth_sigma_bins > 0 && !d_spec_smooth) return QS_ERR_INVALID_ARG;
+  if ((bins->n_tx > 0 && !d_divmaps) || (bins->n_aeff > 0 && !d_aeff_hists))
+    return QS_ERR_INVALID_ARG;
   if (block > 256) block = 256;
   if ((st = device_sms(&sms))) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -754,7 +778,8 @@ extern "C" int32_t qs_scatter_batch(int32_t n_shots, const qs_laser* d_lasers,
                     : launch_batch<float, unsigned int>(a, block, grid, sms, cs);
   if (st) return st;
   const int64_t thr = (int64_t)n_shots * 32;
-  k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_spec_smooth, d_moments);
+  k_bfinal<<<(unsigned)((thr + 255) / 256), 256, 0, cs>>>(a, d_spectra, d_spec_smooth, d_divmaps,
+                                                          d_aeff_hists, d_moments);
   if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
   return check ? nonfinite_status(&d_moments[0].nonfinite, n_shots, sizeof(qs_moments), cs)
                : QS_OK;

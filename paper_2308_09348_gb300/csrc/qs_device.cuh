@@ -1257,6 +1257,9 @@ __device__ __forceinline__ void block_reduce_write(AccF& acc, double* red, doubl
 }
 
 // One evaluated sample into the moment partials and histograms (rows a7-a8).
+// SHIST: the histograms in shared memory (hs, hm, ha); a null hm or ha keeps
+// that histogram in the global accumulators (p.acc_map, p.acc_aeff), as the
+// batch does with its per-shot maps.
 template <typename T, typename H, bool SHIST>
 __device__ __forceinline__ bool accumulate(const Params& p, const Sample& s, int64_t i, AccD& A,
                                            H* hs, H* hm, H* ha, int64_t nspec, int64_t nmap,
@@ -1292,12 +1295,12 @@ __device__ __forceinline__ bool accumulate(const Params& p, const Sample& s, int
   if (nmap) {
     const int c = map_cell(p, s.tx, s.ty, nullptr, nullptr);
     const int64_t slot = c < 0 ? nmap - 1 : c;
-    if (SHIST) atomicAdd(&hm[slot], (H)q);
+    if (SHIST && hm) atomicAdd(&hm[slot], (H)q);
     else atomicAdd(&p.acc_map[slot], q);
   }
   if (naeff) {
     const int slot = aeff_bin(p, s.aeff);
-    if (SHIST) atomicAdd(&ha[slot], (H)q);
+    if (SHIST && ha) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
   return true;
@@ -1350,12 +1353,12 @@ __device__ __forceinline__ bool accumulate_w(const Params& p, const SampleF& s, 
   if (nmap) {
     const int c = map_cell_f32(p, s.tx, s.ty);
     const int64_t slot = c < 0 ? nmap - 1 : c;
-    if (SHIST) atomicAdd(&hm[slot], (H)q);
+    if (SHIST && hm) atomicAdd(&hm[slot], (H)q);
     else atomicAdd(&p.acc_map[slot], q);
   }
   if (naeff) {
     const int slot = aeff_bin_f32(p, s.aeff);
-    if (SHIST) atomicAdd(&ha[slot], (H)q);
+    if (SHIST && ha) atomicAdd(&ha[slot], (H)q);
     else atomicAdd(&p.acc_aeff[slot], q);
   }
   return true;

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.qs_version() == 9
+    assert lib.qs_version() == 10
     for s in range(7):
         assert lib.qs_status_string(s)
     assert lib.qs_status_string(99) == b"unknown status"

@@ -76,6 +76,55 @@ def test_batch_equals_single_shot_calls(prec, weighted):
         np.testing.assert_allclose(mom[s], r, rtol=MOM_RTOL[prec], atol=1e-300)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_batch_divergence_maps_and_aeff_histograms_equal_single_shot_calls(prec, weighted):
+    """Per-shot divergence maps (64 x 48 over +-10 mrad) and a_eff
+    histograms (40 bins on [0, 50]) beside the spectra: every shot's map,
+    a_eff histogram and weight outside its map equal its single-shot call
+    exactly (integer accumulation of the same per-sample bins), quantum and
+    classical shots, ragged and empty shots; the batched adjoint accepts the
+    same bins."""
+    bw, counts, offsets, xi = _small_batch(n_shots=21, seed=8)
+    bins = I.Bins(n_bins=bw.bins.n_bins, lo=0.0, hi=1.0, n_tx=64, n_ty=48, theta_max=10e-3,
+                  n_aeff=40, aeff_max=50.0)
+    xt = [torch.from_numpy(a).cuda() for a in xi]
+    w = I.rng(78).uniform(0.5, 1.5, len(xi[0])).astype(np.float32) if weighted else None
+    wt = None if w is None else torch.from_numpy(w).cuda()
+    bt = B.Batch(bw.lasers, bw.beams, offsets, bins, len(xi[0]), ranges=bw.ranges,
+                 precision=prec)
+    bt.run(xt, wt)
+    torch.cuda.synchronize()
+    assert bt.divmaps.shape == (21, 48, 64) and bt.aeff_hists.shape == (21, 40)
+    mom = bt.moments.cpu().numpy()
+    i_out = B.MOMENT_FIELDS.index("map_out")
+    nonzero = 0
+    for s in range(21):
+        o0, o1 = int(offsets[s]), int(offsets[s + 1])
+        if o1 == o0:
+            assert torch.count_nonzero(bt.divmaps[s]) == 0 and mom[s, 0] == 0
+            continue
+        b_s = I.Bins(**{**bins.__dict__, "lo": float(bw.ranges[s, 0]),
+                        "hi": float(bw.ranges[s, 1])})
+        ref = B.qs_scatter(bw.lasers[s], bw.beams[s], [x[o0:o1] for x in xt], b_s,
+                           w=None if wt is None else wt[o0:o1], precision=prec)
+        r = ref.result()
+        torch.cuda.synchronize()
+        assert torch.equal(bt.divmaps[s], r["divmap"]), s
+        assert torch.equal(bt.aeff_hists[s], r["aeff_hist"]), s
+        assert torch.equal(bt.spectra[s], r["spectrum"]), s
+        assert mom[s, i_out] == r["moments"]["map_out"], s
+        nonzero += int(torch.count_nonzero(bt.divmaps[s]) > 0)
+    assert nonzero >= 10
+    # the batched adjoint takes the same bins (maps and a_eff histograms do
+    # not enter the gradient)
+    dm = torch.zeros(21, 13, dtype=torch.float64)
+    dm[:, 1] = 1e-3
+    g = bt.grad(xt, dm, w=wt)
+    torch.cuda.synchronize()
+    assert torch.isfinite(g).all()
+
+
 def test_batch_matches_oracle_f64():
     bw, counts, offsets, xi = _small_batch(n_shots=12, seed=6, log10_range=(1.0, 3.0))
     bt, _, _ = _run_batch(bw, offsets, xi, "f64")
