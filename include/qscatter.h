@@ -216,8 +216,8 @@ typedef struct qs_moments {
  *                     multiple of 32.
  *   tile              samples per work item of qs_scatter_batch (0 = 2048)
  *                     and of qs_scatter_grad_batch (0 = the largest power of
- *                     two up to 8192 that leaves about eight work items per
- *                     resident CTA); a multiple of 64, at most 1<<20;
+ *                     two up to 8192 that leaves at least sixteen work items
+ *                     per resident CTA); a multiple of 64, at most 1<<20;
  *                     ignored elsewhere.
  *   flags             QS_EXEC_CHECK_FINITE: after the outputs are written
  *                     the call waits for its stream, reads the excluded-sample

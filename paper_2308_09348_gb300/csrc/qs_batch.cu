@@ -805,10 +805,13 @@ extern "C" int32_t qs_scatter_grad_batch(int32_t n_shots, const qs_laser* d_lase
   // adjoint's register count), as for the single-shot adjoint
   const int kblock = (!(exec && exec->block) && prec == QS_F32) ? 512 : block;
   // tile left open: the largest power of two up to 8192 samples that still
-  // gives every resident CTA about eight tiles (fewer shot and table stagings
-  // and tile reductions per sample than the forward's default 2048)
+  // gives every resident CTA (one per SM) at least sixteen tiles: fewer shot
+  // and table stagings and tile reductions per sample than the forward's
+  // default 2048, and a last round of tiles short against the launch (256
+  // shots of 2^16 samples: 4096-sample tiles, 0.800 of the FMA-pipe bound
+  // against 0.785 with 8192)
   if (!(exec && exec->tile))
-    while (tile < 8192 && samples->n / (2 * (int64_t)tile) >= 8 * (int64_t)sms) tile *= 2;
+    while (tile < 8192 && samples->n / (2 * (int64_t)tile) >= 16 * (int64_t)sms) tile *= 2;
   BatchArgs a;
   if ((st = batch_prepare(a, n_shots, d_lasers, d_beams, d_offsets, samples, bins, d_ranges,
                           max_phase, prec, wbits, tile, d_workspace, ws_bytes, false, cs)))
