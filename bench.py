@@ -71,7 +71,7 @@ MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 # capture, keyed by the hash of the kernel sources it was taken with; any
 # other source version reports null.  The capture ran 2^23 samples (read
 # and write both grow with the sample count), scaled by 8 to the 2^26 launch.
-TRAFFIC_BY_SOURCE = {"a7fef076616ce060": 8 * (269.31e6 + 3.75e6)}
+TRAFFIC_BY_SOURCE = {"dcb37ae78931e9cc": 8 * (269.64e6 + 3.03e6)}
 
 
 def parse():
