@@ -201,19 +201,20 @@ typedef struct qs_moments {
 
 /*
  * Execution options (NULL = defaults).
- *   precision         QS_F32: per-sample arithmetic in FP32 (the final energy
- *                     recombined as a float pair, ~2^-44 relative; per-thread
- *                     moment sums compensated in FP32, FP64 from the warp
- *                     level up); QS_F64: everything in FP64.
+ *   precision         QS_F32: per-sample arithmetic in FP32 (the quantum
+ *                     model's final energy recombined as a float pair, ~2^-44
+ *                     relative; per-thread moment sums compensated in FP32,
+ *                     reduction trees in float pairs, each CTA's slot in
+ *                     FP64); QS_F64: everything in FP64.
  *   weight_frac_bits  fixed-point fraction bits of the weighted histograms
  *                     (0 = 32).  Each weight is rounded to a multiple of
  *                     2^-bits; every bin must stay below 2^(63-bits).
  *   block, grid       launch shape of the evaluation kernel (0 = chosen by the
- *                     library: for the FP32 phase-integrating paths one CTA
- *                     per SM that fills the register file, 896 or 768
- *                     threads; 256 threads elsewhere; the grid sized to the
- *                     resident CTAs).  A caller's block is 32..512, a
- *                     multiple of 32.
+ *                     library: for the FP32 paths one CTA per SM, 896
+ *                     threads (quantum model) or 768 (model variants, and
+ *                     the classical model); 256 threads elsewhere; the grid
+ *                     sized to the resident CTAs).  A caller's block is
+ *                     32..512, a multiple of 32.
  *   tile              samples per work item of qs_scatter_batch (0 = 2048)
  *                     and of qs_scatter_grad_batch (0 = the largest power of
  *                     two up to 8192 that leaves at least sixteen work items
