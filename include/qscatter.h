@@ -211,8 +211,9 @@ typedef struct qs_moments {
  *                     2^-bits; every bin must stay below 2^(63-bits).
  *   block, grid       launch shape of the evaluation kernel (0 = chosen by the
  *                     library: for the FP32 paths one CTA per SM, 896
- *                     threads (quantum model) or 768 (model variants, and
- *                     the classical model); 256 threads elsewhere; the grid
+ *                     threads (quantum model, per-cell focus) or 768
+ *                     (cycle-resolved chi, classical model); 256 threads
+ *                     elsewhere; the grid
  *                     sized to the resident CTAs).  A caller's block is
  *                     32..512, a multiple of 32.
  *   tile              samples per work item of qs_scatter_batch (0 = 2048)
