@@ -294,6 +294,14 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
 //   A[n]         = {G_n, dG_n, G_{n+1}, dG_{n+1}}
 //   A[kCycN + n] = {H_n, dH_n, H_{n+1}, dH_{n+1}},
 // at u_n = n du, the derivatives in u times the spacing.
+// a b + c rounded once and clamped to [0, 1] by the FMA's saturation (a NaN
+// gives 0).
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float d;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 template <int CR = 1>
 __device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float chi, float& G,
                                              float& S, float& H) {
@@ -451,6 +459,49 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
   return make_float2(M<float>::rsqrt(x.x), M<float>::rsqrt(x.y));
 }
 
+// The same lookup for the two samples of a pair: the table coordinate, the
+// Hermite basis with its derivative and the factor of S in packed f32x2
+// arithmetic, the gathers and the sums with the gathered nodes per sample.
+// The coordinate x = u/du is clamped to [0, kS] by saturating
+// s = u/(du kS) to [0, 1] (x = s kS; a NaN gives 0).
+template <int CR = 1>
+__device__ __forceinline__ void cycle_lookup2(const float4* __restrict__ A, float2 chi,
+                                              float2& G, float2& S, float2& H) {
+  constexpr float kS = (float)(kCycN - 1) - 1e-3f;
+  const float2 u = lg2x2(fma2(chi, f2((float)(1.0 / kCycChiS)), f2(1.f)));
+  const float sa = (float)(1.0 / (kCycDu * kS));
+  const float2 sx = make_float2(fma_sat(u.x, sa, 0.f), fma_sat(u.y, sa, 0.f));
+  // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
+  // (the sum lies in [2^23, 2^24), where the float spacing is 1), so idx is
+  // in [0, kCycN - 2] and t = x - idx in [0, 1] (up to the rounding of x - 1/2)
+  const float2 xm = __fadd2_rn(fma2(sx, f2(kS), f2(-0.5f)), f2(12582912.f));
+  const int i0 = __float_as_int(xm.x) - 0x4B400000, i1 = __float_as_int(xm.y) - 0x4B400000;
+  const float2 t = fma2(sx, f2(kS), fma2(xm, f2(-1.f), f2(12582912.f)));
+  const float2 t2 = mul2(t, t);
+  const float2 tt = fma2(t2, f2(-1.f), t);                          // t - t^2
+  const float2 h01 = mul2(t2, fma2(f2(-2.f), t, f2(3.f)));          // 3t^2 - 2t^3
+  const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));             // t^3 - t^2
+  const float2 h10 = __fadd2_rn(tt, h11);                           // t - 2t^2 + t^3
+  // t-derivatives of the basis: 6t - 6t^2, 1 - 4t + 3t^2, 3t^2 - 2t
+  const float2 d01 = mul2(f2(6.f), tt);
+  const float2 d10 = fma2(f2(3.f), t2, fma2(f2(-4.f), t, f2(1.f)));
+  const float2 d11 = fma2(f2(3.f), t2, mul2(f2(-2.f), t));
+  // chi G' = (dG/dt) chi / (du ln2 (chi + chi_s))
+  const float2 k = mul2(chi, rcpx2(mul2(f2((float)(kCycDu * 0.69314718055994530942)),
+                                        __fadd2_rn(chi, f2((float)kCycChiS)))));
+  const float4 ga = A[i0 * CR], ha = A[(kCycN + i0) * CR];
+  const float4 gb = A[i1 * CR], hb = A[(kCycN + i1) * CR];
+  const float dGa = __fsub_rn(ga.z, ga.x), dGb = __fsub_rn(gb.z, gb.x);
+  G.x = __fmaf_rn(h11.x, ga.w, __fmaf_rn(h10.x, ga.y, __fmaf_rn(h01.x, dGa, ga.x)));
+  G.y = __fmaf_rn(h11.y, gb.w, __fmaf_rn(h10.y, gb.y, __fmaf_rn(h01.y, dGb, gb.x)));
+  H.x = __fmaf_rn(h11.x, ha.w, __fmaf_rn(h10.x, ha.y, __fmaf_rn(h01.x, __fsub_rn(ha.z, ha.x), ha.x)));
+  H.y = __fmaf_rn(h11.y, hb.w, __fmaf_rn(h10.y, hb.y, __fmaf_rn(h01.y, __fsub_rn(hb.z, hb.x), hb.x)));
+  const float gta = __fmaf_rn(d11.x, ga.w, __fmaf_rn(d10.x, ga.y, __fmul_rn(d01.x, dGa)));
+  const float gtb = __fmaf_rn(d11.y, gb.w, __fmaf_rn(d10.y, gb.y, __fmul_rn(d01.y, dGb)));
+  S.x = __fmaf_rn(gta, k.x, __fadd_rn(G.x, G.x));
+  S.y = __fmaf_rn(gtb, k.y, __fadd_rn(G.y, G.y));
+}
+
 // VAR & kVarCell: per-cell focus; the table then holds {G, G, s_j, s_j} and
 // the two samples' paths give the per-cell amplitudes (same operations as
 // a_cell).  VAR & kVarCycle: cycle-resolved factors from the Hermite tables
@@ -515,8 +566,7 @@ __device__ __forceinline__ void pair_cell(const Params& p, const float4 gg, cons
   if constexpr ((VAR & kVarCycle) != 0) {
     float2 s, h2;
     constexpr int CR = (VAR & kVarCycRep) ? kCycRep : 1;
-    cycle_lookup<CR>(cA, chi.x, g.x, s.x, h2.x);
-    cycle_lookup<CR>(cA, chi.y, g.y, s.y, h2.y);
+    cycle_lookup2<CR>(cA, chi, g, s, h2);
     s2 = mul2(f2(-2.f), s);
     h2c = mul2(C55, h2);
   } else {

@@ -106,12 +106,6 @@ __global__ void __launch_bounds__(256) k_photon_setup() {
 __device__ __forceinline__ float horner(float t, float4 c) {
   return __fmaf_rn(__fmaf_rn(__fmaf_rn(c.w, t, c.z), t, c.y), t, c.x);
 }
-// x clamped to [0, 1] by the FMA's saturation (NaN gives 0).
-__device__ __forceinline__ float fma_sat(float a, float b, float c) {
-  float d;
-  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-  return d;
-}
 
 // Two photon energies e (two bins of one lane) against one emitter whose
 // {1/mu, 1/mu, 2/(3 chi), 2/(3 chi)} is pq: F for both, packed f32x2 except
@@ -125,8 +119,9 @@ __device__ __forceinline__ float2 synch_F2(const float4* __restrict__ T, float2 
   const float2 r1 = rcpx2(om);
   const float2 y = mul2(mul2(make_float2(pq.z, pq.w), xi), r1);
   const float2 u = lg2x2(y);
-  // s = (u - umin) / (umax - umin) saturated to [0, 1]
-  const float sa = (float)(1.0 / (kPhUmax - kPhUmin)), sb = (float)(-kPhUmin / (kPhUmax - kPhUmin));
+  // x = (u - umin)/du clamped to [0, kS]: s = (u - umin)/(du kS) saturated
+  // to [0, 1], then x = s kS
+  const float sa = (float)(1.0 / (kPhDu * kS)), sb = (float)(-kPhUmin / (kPhDu * kS));
   const float2 sx = make_float2(fma_sat(u.x, sa, sb), fma_sat(u.y, sa, sb));
   // node index for x = s kS: x - 1/2 (rounded once, within 2^-17) rounded
   // to the nearest integer by adding 1.5 2^23 (the sum lies in [2^23, 2^24),
