@@ -672,6 +672,25 @@ def test_launch_shapes_agree(block, grid):
     np.testing.assert_allclose(om, rm, rtol=1e-8)
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_classical_launch_shapes_agree(weighted):
+    """The FP32 classical path's default launch (one 768-thread CTA per SM)
+    against caller-chosen shapes (256 and 512 threads, a small grid): the
+    same integer histograms, moments within the FP32 path's partition bar."""
+    n = 4 * 50001 + 3
+    wl, L, xi = cfg2(n, model=I.MODEL_LL)
+    w = I.rng(19).uniform(0.25, 2.0, n).astype(np.float32) if weighted else None
+    xt, wt = dev(xi, w)
+    ref = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision="f32")
+    for block, grid in ((256, 0), (512, 0), (256, 7)):
+        o = qs_scatter(L, wl.beam, xt, wl.bins, w=wt, precision="f32", block=block, grid=grid)
+        torch.cuda.synchronize()
+        assert torch.equal(ref.spectrum, o.spectrum), (block, grid)
+        assert torch.equal(ref.divmap, o.divmap), (block, grid)
+        assert torch.equal(ref.aeff_hist, o.aeff_hist), (block, grid)
+        np.testing.assert_allclose(o.moments.cpu().numpy(), ref.moments.cpu().numpy(), rtol=1e-8)
+
+
 def test_graph_capture_replay():
     wl, L, xi = cfg2(8000)
     xt, _ = dev(xi)
