@@ -451,7 +451,9 @@ class Batch:
     """Device-side descriptors, outputs and workspace of one qs_scatter_batch
     problem shape (reusable across calls and capturable in a CUDA graph).
     With ``bins.smooth_sigma_bins > 0`` the kernel-smoothed spectra are
-    produced too, and ``grad`` runs the batched adjoint
+    produced too, with ``bins.n_tx > 0`` the divergence maps (``divmaps``,
+    n_shots x n_ty x n_tx) and with ``bins.n_aeff > 0`` the a_eff histograms
+    (``aeff_hists``); ``grad`` runs the batched adjoint
     (qs_scatter_grad_batch) over the same workspace."""
 
     # columns of the 8 gradient parameters in the device descriptor arrays

@@ -9,7 +9,10 @@
 //               stages the tile's shot constants and table in shared memory,
 //               evaluates the samples exactly as k_scatter does, writes the
 //               tile's moment partials to the tile's own slot and merges its
-//               shared-memory histogram into the shot's accumulators.
+//               shared-memory spectrum into the shot's accumulators (the
+//               shot's divergence map and a_eff histogram take global
+//               integer atomics directly).  Launched twice over the same
+//               schedule: the paper's model, then the model variants.
 // B4 k_bfinal   one warp per shot: partials summed in tile order, histograms
 //               converted, moments written.
 // G3 k_bgrad    (qs_scatter_grad_batch) the adjoint over the same (shot,
