@@ -217,6 +217,24 @@ def cpu_oracle_gh32():
             "sample": f"all {wl.n} nodes of the {wl.name} workload (one thread, FP64 C oracle)"}
 
 
+def cpu_oracle_discretization(wl, xi_host, n=256):
+    """Discretisation error of the workload's phase grid: the oracle's
+    continuum-accurate mode (n_phase, 2 n_phase, 4 n_phase cells and
+    Richardson) on the first n samples, relative to the extrapolated
+    continuum (median, 99th percentile and largest over the samples)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    sub = [a[:n].astype(np.float64) for a in xi_host]
+    r = oracle.continuum(wl.laser, wl.beam, sub, levels=3)
+    out = {"n_phase": r["n_phase"], "grids": r["grids"], "samples": n}
+    for f in ("mu", "V"):
+        e = r["err_" + f][np.isfinite(r["err_" + f])]
+        out["rel_err_" + f] = {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+                               "max": float(e.max())}
+    return out
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -984,7 +1002,8 @@ def main():
                          f"{procs} processes)",
                "single_core": {"value": rate1, "cores": 1,
                                "sample": f"first {done1} samples ({dt1:.1f} s, one thread)"},
-               "gh32_full": cpu_oracle_gh32()}
+               "gh32_full": cpu_oracle_gh32(),
+               "discretization": cpu_oracle_discretization(wl, xi_host)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
