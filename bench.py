@@ -602,7 +602,9 @@ def bench_pw(dev, rank, n_pw=1 << 20, n_hist=4096, steps=3):
 def bench_batch(dev, rank, steps=3, n_shots=4096):
     """4096 shots, sample counts log-uniform in [1e3, 1e6], per-shot laser and
     beam drawn from seed, quantum model with 512 phase cells, FP32 with FP64
-    moments, one persistent launch per step; schedule from the autotuner."""
+    moments, one persistent launch per step; schedule from the autotuner.
+    Beside it the same shots with the classical and quantum models
+    alternating (``mixed_models``)."""
     import torch
     from paper_2308_09348_gb300 import binding as B
     from paper_2308_09348_gb300 import inputs as I
@@ -634,12 +636,32 @@ def bench_batch(dev, rank, steps=3, n_shots=4096):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     bad = int((bt.moments[:, B.MOMENT_FIELDS.index("nonfinite")] != 0).sum())
+    del bt
+    # the same shots and samples with the models alternating (even shots
+    # quantum, odd shots classical) in one launch, same schedule
+    bm = I.batch_shots(n_shots, model_mix=True)
+    btm = B.Batch(bm.lasers, bm.beams, bm.offsets, bm.bins, n, dev, ranges=bm.ranges,
+                  precision="f32", block=best[0], tile=best[1])
+    btm.run(xi)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        btm.run(xi)
+    b.record()
+    torch.cuda.synchronize()
+    ms_mix = a.elapsed_time(b) / steps
+    bad_mix = int((btm.moments[:, B.MOMENT_FIELDS.index("nonfinite")] != 0).sum())
+    del btm
     return {"metric": "shots/s", "value": n_shots / (ms * 1e-3), "unit": "shots/s",
             "samples_per_s": n / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
             "n_shots": n_shots, "n_samples": n, "n_phase": 512, "schedule": {"block": best[0],
                                                                              "tile": best[1]},
             "tuned_ms": {f"{k[0]}x{k[1]}": v for k, v in times.items()},
-            "shots_flagged": bad, "workload": bw.name}
+            "shots_flagged": bad, "workload": bw.name,
+            "mixed_models": {"value": n_shots / (ms_mix * 1e-3), "unit": "shots/s",
+                             "samples_per_s": n / (ms_mix * 1e-3), "ms_per_step": ms_mix,
+                             "shots_flagged": bad_mix,
+                             "models": "even shots quantum (512 cells), odd shots classical"}}
 
 
 def bench_grad(dev, rank, steps=3, n=1 << 24):
