@@ -66,8 +66,11 @@ def test_fp32_matches_oracle_and_is_repeatable():
     big = ref > 1e-6 * ref.max()
     rel = np.max(np.abs(S[big] / ref[big] - 1))
     print("FP32 photon spectrum L1 rel:", l1, "max rel (significant bins):", rel)
-    assert l1 < 1e-4
-    assert rel < 1e-3
+    # measured 3.0e-7 and 3.8e-7: the Bessel table's interpolation (2.3e-7)
+    # and the FP32 table coordinate (~1e-6 in F); a table coordinate off by
+    # 1e-3 of a node, or a coarser table, would read ~1e-5
+    assert l1 < 2e-6
+    assert rel < 3e-6
 
 
 def test_uniform_bins_edge_sizes_and_launch_shapes():
@@ -113,9 +116,11 @@ def test_angular_moments_match_oracle(prec, n):
     S, T = B.qs_photon_spectrum(L, Bm, xt, PB, precision=prec, theta2=True)
     S, T = S.cpu().numpy(), T.cpu().numpy()
     Sr, Tr = oracle.photon_spectrum_angles(L, Bm, PB, [a.astype(np.float64) for a in xi])
-    tol = 1e-10 if prec == "f64" else 1e-4
+    tol = 1e-10 if prec == "f64" else 2e-6
     for a, r in ((S, Sr), (T[0], Tr[0]), (T[1], Tr[1])):
-        assert np.abs(a - r).sum() / np.abs(r).sum() < tol
+        l1 = np.abs(a - r).sum() / np.abs(r).sum()
+        print(f"[{prec}] photon angular sums L1 rel: {l1:.3e}")
+        assert l1 < tol
     # mean square angles are of order (a/gamma)^2 along x, (1/gamma)^2 + div^2 along y
     assert (T[0] * S).sum() > (T[1] * S).sum() > 0
 
