@@ -227,9 +227,9 @@ def test_variant_gradient_matches_oracle(prec, model, variant):
     """qs_scatter_grad for the model variants (seven tangents through the
     per-cell amplitudes; the cycle-resolved factors and their chi-derivatives)
     against the oracle's dual-number gradient, parameter-scaled relative to
-    the largest component: FP64 1e-10, FP32 1e-4 (the FP32 cycle factors come
-    from the Hermite tables, 3e-7 in S, and the seven FP32 tangents sum over
-    the cells without compensation)."""
+    the largest component: FP64 1e-10, FP32 5e-7 (measured 2.4e-8 to 5.7e-8:
+    the FP32 cycle factors come from the Hermite tables, 3e-7 in S, and the
+    seven FP32 tangents sum over the cells without compensation)."""
     n = 1001 if not variant & I.VAR_CYCLE_CHI else 401
     wl, L, beam, bins, xi = _variant_case(n, model, variant)
     w = I.rng(41).uniform(0.5, 1.5, n).astype(np.float32)
@@ -247,8 +247,8 @@ def test_variant_gradient_matches_oracle(prec, model, variant):
                       dL_dm=dm, dL_dS=dS)
     rs = ref["grad"] * GRAD_SCALE
     err = np.abs(g * GRAD_SCALE - rs) / np.max(np.abs(rs))
-    print(f"[{prec}, model {model}, variant {variant}] scaled grad rel err:", err)
-    assert np.all(err <= (1e-10 if prec == "f64" else 1e-4)), err
+    print(f"[{prec}, model {model}, variant {variant}] scaled grad rel err: max {err.max():.3e}")
+    assert np.all(err <= (1e-10 if prec == "f64" else 5e-7)), err
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
