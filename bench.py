@@ -65,6 +65,12 @@ GRAD_FMA_OPS_PER_STEP = 103
 PHOTON_FMA_OPS_PER_EVAL = 20
 PHOTON_MUFU_SLOTS_PER_EVAL = 2.5
 PHOTON_SMEM_WAVEFRONTS_PER_EVAL = 0.223
+# The bound of the photon kernel: its two 16-byte table reads per evaluation
+# against the shared-memory data pipe (fewer wavefronts than bytes / 128 are
+# served, 0.223 instead of 0.25 per evaluation, because neighbouring lanes'
+# reads of the same entry merge).
+PHOTON_TABLE_BYTES_PER_EVAL = 32
+SMEM_BYTES_PER_SM_CLOCK = 128
 MUFU_SLOTS_PER_SM = 16      # lg2/rcp per SM per clock (measured)
 
 # DRAM traffic of one k_scatter launch on the bench workload from an ncu
@@ -544,20 +550,25 @@ def bench_photon(dev, rank, n=1 << 19, steps=2):
     peak = _fma_peak(dev)
     rate = evals / (kms * 1e-3)
     clk = peak / FMA_LANES_PER_SM                    # SM x clock per second
+    # shared-memory data pipe: one 128-byte wavefront per SM and clock
+    smem_peak = clk * SMEM_BYTES_PER_SM_CLOCK
     return {"metric": "beam-sample evals/s", "value": n / (kms * 1e-3), "unit": "samples/s",
             "kernel_ms": kms, "n_samples": n, "n_phase": wl.laser.n_phase,
             "photon_bins": "256 log-spaced on [1e-3, 6720] m c^2",
             "evaluations_per_s": rate,
-            "roofline": {"bound": "alu", "pipe": "fma",
-                         "achieved": PHOTON_FMA_OPS_PER_EVAL * rate / 1e12,
-                         "peak": peak / 1e12, "unit": "Top/s",
-                         "frac": PHOTON_FMA_OPS_PER_EVAL * rate / peak,
-                         "evaluations": evals, "ops_per_eval": PHOTON_FMA_OPS_PER_EVAL,
+            "roofline": {"bound": "smem", "pipe": "shared-memory data pipe (table reads)",
+                         "achieved": PHOTON_TABLE_BYTES_PER_EVAL * rate / 1e12,
+                         "peak": smem_peak / 1e12, "unit": "TB/s",
+                         "frac": PHOTON_TABLE_BYTES_PER_EVAL * rate / smem_peak,
+                         "peak_source": "152 SMs x 128 B per clock x 2070 MHz (derived)",
+                         "evaluations": evals, "bytes_per_eval": PHOTON_TABLE_BYTES_PER_EVAL,
                          "pipe_fracs": {
+                             "shared_memory_bytes": PHOTON_TABLE_BYTES_PER_EVAL * rate / smem_peak,
+                             "shared_memory_wavefronts":
+                                 PHOTON_SMEM_WAVEFRONTS_PER_EVAL * rate / clk,
                              "fma": PHOTON_FMA_OPS_PER_EVAL * rate / peak,
-                             "mufu": PHOTON_MUFU_SLOTS_PER_EVAL * rate / (MUFU_SLOTS_PER_SM * clk),
-                             "shared_memory": PHOTON_SMEM_WAVEFRONTS_PER_EVAL * rate / clk},
-                         "binding_pipe": "shared_memory"},
+                             "mufu": PHOTON_MUFU_SLOTS_PER_EVAL * rate / (MUFU_SLOTS_PER_SM * clk)},
+                         "fma_ops_per_eval": PHOTON_FMA_OPS_PER_EVAL},
             "workload": "mc2p19_photon_qfp512"}
 
 
