@@ -457,12 +457,13 @@ def bench_ll(dev, rank, n=1 << 26, steps=5):
 CELL_MUFU_SLOTS_PER_STEP = QFP_MUFU_SLOTS_PER_STEP + 1 + 0.5
 # Cycle-resolved chi (FP32): the packed update without the Gaunt and
 # second-moment fits (17 packed FMA-pipe instructions per pair of samples: 17
-# lane-operations per sample) plus the per-sample table lookup (34 FMA-pipe
-# operations: index, Hermite basis and its derivative, G, H, dG, S) = 51; MUFU:
-# the mean-energy reciprocal, the lookup's lg2 and its reciprocal = 3 slots;
-# shared memory: two 16-byte gathers per sample, 2 x 16 / 128 = 0.25
+# lane-operations per sample) plus the per-sample table lookup (19 FMA-pipe
+# operations: the table coordinate 6, the factor of S 3, G and its
+# t-derivative by synthetic division 5, H by Horner 3, S 2) = 36; MUFU: the
+# mean-energy reciprocal, the lookup's lg2 and its reciprocal = 3 slots;
+# shared memory: two 16-byte reads per sample, 2 x 16 / 128 = 0.25
 # wavefronts per sample-step at one 128-byte wavefront per SM and clock.
-CYC_FMA_OPS_PER_STEP = 17 + 34
+CYC_FMA_OPS_PER_STEP = 17 + 19
 CYC_MUFU_SLOTS_PER_STEP = 3
 CYC_SMEM_WAVEFRONTS_PER_STEP = 0.25
 CELL_FMA_OPS_PER_STEP = QFP_FMA_OPS_PER_STEP + 14

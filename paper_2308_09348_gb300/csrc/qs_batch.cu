@@ -54,6 +54,7 @@ struct BatchArgs {
   int64_t max_tiles;            // tile slots in the workspace
   const double* cyc_gl;         // cycle-resolved chi tables of this context
   const float4* cyc_a;          // (null: shots with that variant are invalid)
+  const float4* cyc_m;
   int32_t precision, pad;
 };
 
@@ -75,7 +76,7 @@ __global__ void k_bsetup(const BatchArgs a) {
   // context's tables
   const bool cells = L.model == QS_MODEL_QFP || (L.variant & QS_VARIANT_CELL_FOCUS);
   bool ok = check_laser(L) == QS_OK &&
-            (!(L.variant & QS_VARIANT_CYCLE_CHI) || (a.cyc_a && a.cyc_gl)) &&
+            (!(L.variant & QS_VARIANT_CYCLE_CHI) || (a.cyc_a && a.cyc_m && a.cyc_gl)) &&
             check_beam(B) == QS_OK && check_bins(b) == QS_OK &&
             o0 >= 0 && o1 >= o0 && o1 <= a.samples.n &&
             (!cells || L.n_phase <= a.max_phase);
@@ -101,6 +102,7 @@ __global__ void k_bsetup(const BatchArgs a) {
   p.acc_aeff = a.acc_aeff ? a.acc_aeff + (size_t)s * (a.bins.n_aeff + 1) : nullptr;
   p.cyc_gl = a.cyc_gl;
   p.cyc_a = a.cyc_a;
+  p.cyc_m = a.cyc_m;
   a.tiles[s] = (p.n + a.tile - 1) / a.tile;
   if (L.variant != 0 && a.tiles[s] > 0) a.counter[2] = 1ull;
 }
@@ -196,8 +198,8 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
   unsigned long long* hsm = nsm ? reinterpret_cast<unsigned long long*>(
                                       reinterpret_cast<unsigned char*>(hs) + hist_bytes + 16)
                                 : nullptr;
-  // FP32 cycle-resolved chi: the node-pair Hermite tables after the
-  // smoothed-spectrum accumulators
+  // FP32 cycle-resolved chi: the per-interval monomial tables of G and H
+  // after the smoothed-spectrum accumulators
   float4* cA = VARK ? reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(hs) + hist_bytes +
                                                 16 + ((nsm * 8 + 15) & ~(int64_t)15))
                     : nullptr;
@@ -247,10 +249,10 @@ __global__ void __launch_bounds__(VARK ? 256 : 512, sizeof(T) == 4 ? 2 : 1)
         for (int j = threadIdx.x; j < p.n_phase; j += blockDim.x) tab[j] = tg[j];
       }
       if (VARK && sizeof(T) == 4 && p.cycle) {
+        // per-interval monomial coefficients of G and H (the forward lookup)
         for (int j = threadIdx.x; j < kCycN - 1; j += blockDim.x) {
-          const float4 u = p.cyc_a[j], v = p.cyc_a[j + 1];
-          cA[j] = make_float4(u.x, u.y, v.x, v.y);
-          cA[kCycN + j] = make_float4(u.z, u.w, v.z, v.w);
+          cA[j] = p.cyc_m[j];
+          cA[kCycN + j] = p.cyc_m[kCycN + j];
         }
       }
       cur = s;
@@ -698,6 +700,7 @@ int32_t batch_prepare(BatchArgs& a, int32_t n_shots, const qs_laser* d_lasers,
     if (e == QS_OK) {
       a.cyc_gl = tp.cyc_gl;
       a.cyc_a = tp.cyc_a;
+      a.cyc_m = tp.cyc_m;
     } else if (e != QS_ERR_UNSUPPORTED) {
       return e;
     }

@@ -64,7 +64,8 @@ struct Params {
   // cycle-resolved chi: Gauss-Legendre cos(psi_k) and weights (FP64 path),
   // Hermite tables of (G, S) and H over u = log2(1 + chi/chi_s) (FP32 path)
   const double* cyc_gl;
-  const float4* cyc_a;
+  const float4* cyc_a;          // per node {G, dG du, H, dH du} (adjoint)
+  const float4* cyc_m;          // per interval monomial coefficients of G, then H
   // FP32 path, log-spaced bins: t = lg2(gamma) * log2_scale - log2_offset
   float log2_scale, log2_offset;
   // FP32 copies of the per-sample constants, each the double above rounded
@@ -289,47 +290,12 @@ __device__ __forceinline__ void cycle_factors_d(const double* __restrict__ gl, d
   if (dH) *dH = sh1;
 }
 
-// FP32 path: one lane's cubic Hermite lookup in the shared-memory tables of
-// node pairs (one 16-byte load per function instead of one per node):
-//   A[n]         = {G_n, dG_n, G_{n+1}, dG_{n+1}}
-//   A[kCycN + n] = {H_n, dH_n, H_{n+1}, dH_{n+1}},
-// at u_n = n du, the derivatives in u times the spacing.
 // a b + c rounded once and clamped to [0, 1] by the FMA's saturation (a NaN
 // gives 0).
 __device__ __forceinline__ float fma_sat(float a, float b, float c) {
   float d;
   asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
   return d;
-}
-
-template <int CR = 1>
-__device__ __forceinline__ void cycle_lookup(const float4* __restrict__ A, float chi, float& G,
-                                             float& S, float& H) {
-  const float u = M<float>::lg2(__fmaf_rn(chi, (float)(1.0 / kCycChiS), 1.f));
-  const float x = fminf(fmaxf(__fmul_rn(u, (float)(1.0 / kCycDu)), 0.f),
-                        (float)(kCycN - 1) - 1e-3f);
-  // node index: x - 1/2 rounded to the nearest integer by adding 1.5 2^23
-  // (x - 1/2 in [-1/2, kCycN - 1.501] keeps the sum in [2^23, 2^24), where
-  // the float spacing is 1), so idx in [0, kCycN - 2] and t = x - idx in [0, 1]
-  const float xm = __fadd_rn(__fsub_rn(x, 0.5f), 12582912.f);
-  const int idx = __float_as_int(xm) - 0x4B400000;
-  const float t = __fsub_rn(x, __fsub_rn(xm, 12582912.f)), t2 = __fmul_rn(t, t);
-  const float h01 = __fmul_rn(t2, __fmaf_rn(-2.f, t, 3.f));       // 3t^2 - 2t^3
-  const float h11 = __fmaf_rn(t2, t, -t2);                         // t^3 - t^2
-  const float h10 = __fadd_rn(__fsub_rn(t, t2), h11);              // t - 2t^2 + t^3
-  // t-derivatives of the basis: 6t - 6t^2, 1 - 4t + 3t^2, 3t^2 - 2t
-  const float d01 = __fmul_rn(6.f, __fsub_rn(t, t2));
-  const float d10 = __fmaf_rn(3.f, t2, __fmaf_rn(-4.f, t, 1.f));
-  const float d11 = __fmaf_rn(3.f, t2, __fmul_rn(-2.f, t));
-  const float4 g = A[idx * CR], h = A[(kCycN + idx) * CR];
-  const float dG = __fsub_rn(g.z, g.x);
-  G = __fmaf_rn(h11, g.w, __fmaf_rn(h10, g.y, __fmaf_rn(h01, dG, g.x)));
-  H = __fmaf_rn(h11, h.w, __fmaf_rn(h10, h.y, __fmaf_rn(h01, __fsub_rn(h.z, h.x), h.x)));
-  // chi G' = (dG/dt) chi / (du ln2 (chi + chi_s)), from the same interpolant
-  const float Gt = __fmaf_rn(d11, g.w, __fmaf_rn(d10, g.y, __fmul_rn(d01, dG)));
-  const float k = __fmul_rn(chi, M<float>::rcp(__fmul_rn(
-                                     (float)(kCycDu * 0.69314718055994530942), __fadd_rn(chi, (float)kCycChiS))));
-  S = __fmaf_rn(Gt, k, __fmul_rn(2.f, G));
 }
 
 // Per-cell focus (QS_VARIANT_CELL_FOCUS): Eq. 2 evaluated in
@@ -459,11 +425,13 @@ __device__ __forceinline__ float2 rsqrtx2(float2 x) {
   return make_float2(M<float>::rsqrt(x.x), M<float>::rsqrt(x.y));
 }
 
-// The same lookup for the two samples of a pair: the table coordinate, the
-// Hermite basis with its derivative and the factor of S in packed f32x2
-// arithmetic, the gathers and the sums with the gathered nodes per sample.
-// The coordinate x = u/du is clamped to [0, kS] by saturating
-// s = u/(du kS) to [0, 1] (x = s kS; a NaN gives 0).
+// The cycle lookup for the two samples of a pair: the table coordinate and
+// the factor of S in packed f32x2 arithmetic; per sample one 16-byte entry
+// of monomial coefficients for G and one for H (the cubic Hermite
+// interpolants of interval idx in t = x - idx), G and its t-derivative by
+// synthetic division (5 FMAs), H by Horner's rule (3).  The coordinate
+// x = u/du is clamped to [0, kS] by saturating s = u/(du kS) to [0, 1]
+// (x = s kS; a NaN gives 0).
 template <int CR = 1>
 __device__ __forceinline__ void cycle_lookup2(const float4* __restrict__ A, float2 chi,
                                               float2& G, float2& S, float2& H) {
@@ -477,27 +445,20 @@ __device__ __forceinline__ void cycle_lookup2(const float4* __restrict__ A, floa
   const float2 xm = __fadd2_rn(fma2(sx, f2(kS), f2(-0.5f)), f2(12582912.f));
   const int i0 = __float_as_int(xm.x) - 0x4B400000, i1 = __float_as_int(xm.y) - 0x4B400000;
   const float2 t = fma2(sx, f2(kS), fma2(xm, f2(-1.f), f2(12582912.f)));
-  const float2 t2 = mul2(t, t);
-  const float2 tt = fma2(t2, f2(-1.f), t);                          // t - t^2
-  const float2 h01 = mul2(t2, fma2(f2(-2.f), t, f2(3.f)));          // 3t^2 - 2t^3
-  const float2 h11 = mul2(t2, __fadd2_rn(t, f2(-1.f)));             // t^3 - t^2
-  const float2 h10 = __fadd2_rn(tt, h11);                           // t - 2t^2 + t^3
-  // t-derivatives of the basis: 6t - 6t^2, 1 - 4t + 3t^2, 3t^2 - 2t
-  const float2 d01 = mul2(f2(6.f), tt);
-  const float2 d10 = fma2(f2(3.f), t2, fma2(f2(-4.f), t, f2(1.f)));
-  const float2 d11 = fma2(f2(3.f), t2, mul2(f2(-2.f), t));
   // chi G' = (dG/dt) chi / (du ln2 (chi + chi_s))
   const float2 k = mul2(chi, rcpx2(mul2(f2((float)(kCycDu * 0.69314718055994530942)),
                                         __fadd2_rn(chi, f2((float)kCycChiS)))));
   const float4 ga = A[i0 * CR], ha = A[(kCycN + i0) * CR];
   const float4 gb = A[i1 * CR], hb = A[(kCycN + i1) * CR];
-  const float dGa = __fsub_rn(ga.z, ga.x), dGb = __fsub_rn(gb.z, gb.x);
-  G.x = __fmaf_rn(h11.x, ga.w, __fmaf_rn(h10.x, ga.y, __fmaf_rn(h01.x, dGa, ga.x)));
-  G.y = __fmaf_rn(h11.y, gb.w, __fmaf_rn(h10.y, gb.y, __fmaf_rn(h01.y, dGb, gb.x)));
-  H.x = __fmaf_rn(h11.x, ha.w, __fmaf_rn(h10.x, ha.y, __fmaf_rn(h01.x, __fsub_rn(ha.z, ha.x), ha.x)));
-  H.y = __fmaf_rn(h11.y, hb.w, __fmaf_rn(h10.y, hb.y, __fmaf_rn(h01.y, __fsub_rn(hb.z, hb.x), hb.x)));
-  const float gta = __fmaf_rn(d11.x, ga.w, __fmaf_rn(d10.x, ga.y, __fmul_rn(d01.x, dGa)));
-  const float gtb = __fmaf_rn(d11.y, gb.w, __fmaf_rn(d10.y, gb.y, __fmul_rn(d01.y, dGb)));
+  // p = c3 t^3 + c2 t^2 + c1 t + c0 and dp/dt, one pass
+  const float pa2 = __fmaf_rn(ga.w, t.x, ga.z), pb2 = __fmaf_rn(gb.w, t.y, gb.z);
+  const float pa1 = __fmaf_rn(pa2, t.x, ga.y), pb1 = __fmaf_rn(pb2, t.y, gb.y);
+  const float da1 = __fmaf_rn(ga.w, t.x, pa2), db1 = __fmaf_rn(gb.w, t.y, pb2);
+  G.x = __fmaf_rn(pa1, t.x, ga.x);
+  G.y = __fmaf_rn(pb1, t.y, gb.x);
+  const float gta = __fmaf_rn(da1, t.x, pa1), gtb = __fmaf_rn(db1, t.y, pb1);
+  H.x = __fmaf_rn(__fmaf_rn(__fmaf_rn(ha.w, t.x, ha.z), t.x, ha.y), t.x, ha.x);
+  H.y = __fmaf_rn(__fmaf_rn(__fmaf_rn(hb.w, t.y, hb.z), t.y, hb.y), t.y, hb.x);
   S.x = __fmaf_rn(gta, k.x, __fadd_rn(G.x, G.x));
   S.y = __fmaf_rn(gtb, k.y, __fadd_rn(G.y, G.y));
 }

@@ -280,13 +280,12 @@ __device__ __forceinline__ void load_tables(const Params& p, unsigned char* smem
   if constexpr (sizeof(T) == 4 && (VAR & kVarCycle)) {
     float4* A = reinterpret_cast<float4*>(smem + (((size_t)p.n_phase * sizeof(TT) + 15) &
                                                   ~(size_t)15));
-    // node-pair tables: {G_n, dG_n, G_n+1, dG_n+1}, then {H_n, dH_n, H_n+1, dH_n+1}
+    // per-interval monomial coefficients of G, then of H
     constexpr int R = REP ? kCycRep : 1;
     for (int jc = threadIdx.x; jc < (kCycN - 1) * R; jc += blockDim.x) {
       const int j = jc / R, c = jc - j * R;
-      const float4 a = p.cyc_a[j], b = p.cyc_a[j + 1];
-      A[j * R + c] = make_float4(a.x, a.y, b.x, b.y);
-      A[(kCycN + j) * R + c] = make_float4(a.z, a.w, b.z, b.w);
+      A[j * R + c] = p.cyc_m[j];
+      A[(kCycN + j) * R + c] = p.cyc_m[kCycN + j];
     }
     *cA = A + (REP ? (threadIdx.x % kCycRep) : 0);
   }
@@ -594,15 +593,21 @@ namespace {
 // built once per device by k_cycle_setup (FP64) and kept for the process.
 __device__ double g_cyc_gl[2 * kCycGL];
 __device__ float4 g_cyc_a[kCycN];
+__device__ float4 g_cyc_m[2 * kCycN];
 
 // One CTA of kCycGL/2 threads: thread i finds the i-th root z of P_n (n =
 // kCycGL) by Newton's method from cos(pi (i + 3/4)/(n + 1/2)) and its
 // mirror; psi = (pi/4)(1 -+ z) on the quarter period, weight 2/((1 - z^2)
 // P_n'(z)^2) times pi/4 times the 2/pi of the cycle mean.  Then the table
 // nodes u_n = n du, chi_n = chi_s (2^u_n - 1): {G, dG/du du, H, dH/du du}
-// (dchi/du = ln2 (chi + chi_s)); S comes from G's interpolant.
+// (dchi/du = ln2 (chi + chi_s)); S comes from G's interpolant.  From the
+// same FP64 node values, per interval n the cubic Hermite interpolants of G
+// and H as monomial coefficients in t = u/du - n (c0 = v0, c1 = d0,
+// c2 = 3 (v1 - v0) - 2 d0 - d1, c3 = 2 (v0 - v1) + d0 + d1), for the lookup
+// by Horner's rule: entry n for G, kCycN + n for H.
 __global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
   __shared__ double gl[2 * kCycGL];
+  __shared__ double nv[4][kCycN];                    // G, dG du, H, dH du per node
   const int n = kCycGL, i = threadIdx.x;
   double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
   for (int it = 0; it < 100; ++it) {
@@ -630,6 +635,24 @@ __global__ void __launch_bounds__(kCycGL / 2) k_cycle_setup() {
     double G, S, H, dG, dH;
     cycle_factors_d(gl, chi, G, S, H, &dG, nullptr, &dH);
     g_cyc_a[m] = make_float4((float)G, (float)(dG * dchi), (float)H, (float)(dH * dchi));
+    nv[0][m] = G;
+    nv[1][m] = dG * dchi;
+    nv[2][m] = H;
+    nv[3][m] = dH * dchi;
+  }
+  __syncthreads();
+  for (int m = i; m < kCycN; m += blockDim.x) {
+    if (m == kCycN - 1) {                            // past the last interval: never read
+      g_cyc_m[m] = g_cyc_m[kCycN + m] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    for (int f = 0; f < 2; ++f) {
+      const double v0 = nv[2 * f][m], d0 = nv[2 * f + 1][m];
+      const double v1 = nv[2 * f][m + 1], d1 = nv[2 * f + 1][m + 1];
+      g_cyc_m[f * kCycN + m] = make_float4((float)v0, (float)d0,
+                                           (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1),
+                                           (float)(2.0 * (v0 - v1) + d0 + d1));
+    }
   }
 }
 
@@ -654,12 +677,14 @@ int32_t cycle_tables_impl(Params& p, cudaStream_t st) {
       return cuda_fail();
     g_cyc_ready.set(dev, key);
   }
-  void *gl = nullptr, *a = nullptr;
+  void *gl = nullptr, *a = nullptr, *mc = nullptr;
   if (cudaGetSymbolAddress(&gl, g_cyc_gl) != cudaSuccess ||
-      cudaGetSymbolAddress(&a, g_cyc_a) != cudaSuccess)
+      cudaGetSymbolAddress(&a, g_cyc_a) != cudaSuccess ||
+      cudaGetSymbolAddress(&mc, g_cyc_m) != cudaSuccess)
     return cuda_fail();
   p.cyc_gl = static_cast<const double*>(gl);
   p.cyc_a = static_cast<const float4*>(a);
+  p.cyc_m = static_cast<const float4*>(mc);
   return QS_OK;
 }
 
